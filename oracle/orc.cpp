@@ -1,0 +1,1229 @@
+// Plain FP64 CPU oracle of the block-based multiresolution (MR) Euler method of
+// Hoppe, Adami & Adams, "A modular massively parallel computing environment for
+// three-dimensional multiresolution simulations of compressible flows"
+// (arXiv:2012.04385).
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call
+// this file: only the test suite, the smoke check and the CPU-baseline leg of the
+// benchmark use it.  It shares no code, header, table or constant generator with
+// the CUDA library; the two are written independently from the paper.
+//
+// Build rules: C++17, scalar double, -ffp-contract=off (no fused multiply-add, so
+// every formula rounds in the order written), OpenMP only over independent blocks.
+// Every reduction runs in a fixed order, so results do not depend on the thread
+// count.
+//
+// Evaluation order.  Every formula below is evaluated left to right exactly as
+// written; the order is part of the oracle's definition (the paper fixes none).
+//
+// Pins (tests/test_oracle_*.py): free-stream preservation, conservation on
+// periodic domains, the exact Sod solution, 5th-order convergence on an advected
+// density wave, L.R = I and the Roe property of the eigensystem, WENO5/linear
+// special cases, A(P(u)) = u and quartic reproduction of P, the Morton
+// neighbour example of Fig. (NeighborLookup) and brute force in all 26
+// directions, tag invariants.  Parity unpinned: the Roe/LLF per-field switch
+// and the detail norm are readings (the paper names them without a formula);
+// they are pinned only indirectly (free-stream, conservation, Sod, convergence).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// Block geometry (Sec. 3 and Sec. 5: 16^3 internal cells, four halo cells per side).
+constexpr int NB = 16;
+constexpr int HW = 4;
+constexpr int NS = NB + 2 * HW;              // 24 stored cells per edge
+constexpr int NCELL = NS * NS * NS;          // 13824
+constexpr int NINT = NB * NB * NB;           // 4096
+constexpr int NV = 5;                        // rho, rho u, rho v, rho w, E
+constexpr int NFACE = NB * NB;               // 256 faces per block side
+constexpr int NSHADOW = 7;                   // shadow levels of the 64-bit id (Sec. 3)
+constexpr uint64_t MASK56 = (1ull << 56) - 1;
+
+constexpr int BC_ZERO_GRADIENT = 0, BC_PERIODIC = 1, BC_SYMMETRY = 2;
+constexpr int RECON_WENO = 0, RECON_LINEAR = 2;
+constexpr int8_t TAG_KEEP = 0, TAG_REFINE = 1, TAG_COARSEN = -1;
+
+inline int sidx(int i, int j, int k) { return ((k + HW) * NS + (j + HW)) * NS + (i + HW); }
+inline int iidx(int i, int j, int k) { return (k * NB + j) * NB + i; }
+inline int floordiv2(int i) { return (i >= 0) ? i / 2 : -((-i + 1) / 2); }
+
+}  // namespace
+
+extern "C" {
+
+// Run configuration.  Mirrors the physical set-up of the paper's runs (Sec. 5);
+// laid out int32 first, then double, so that a ctypes Structure can build it.
+struct orc_config {
+  int32_t n_instances;
+  int32_t base_blocks[3];
+  int32_t lmax[256];
+  int32_t bc[6];          // x-, x+, y-, y+, z-, z+
+  int32_t recon;          // 0 = WENO5-JS, 2 = linear 5th-order upwind everywhere
+  int32_t n_threads;      // 0 = OpenMP default
+  double domain_lo[3];
+  double dx0;             // level-0 cell size
+  double gamma, B, cfl;
+  double gravity[3];
+  double eps;             // threshold at l_max (Eq. UserEpsilon already applied)
+};
+
+}  // extern "C"
+
+namespace {
+
+struct Node {
+  uint64_t key = 0;
+  int inst = 0, level = 0;
+  int64_t X[3] = {0, 0, 0};   // block coordinates on its level
+  bool leaf = true;
+  std::vector<double> u;      // [5][24^3] conserved state incl. halo
+  std::vector<double> un;     // [5][16^3] u^n of the current RK step
+  std::vector<double> L;      // [5][16^3] right-hand side
+  std::vector<double> face;   // [6][5][16][16] boundary-face fluxes
+  void alloc() {
+    u.assign((size_t)NV * NCELL, 0.0);
+    un.assign((size_t)NV * NINT, 0.0);
+    L.assign((size_t)NV * NINT, 0.0);
+    face.assign((size_t)6 * NV * NFACE, 0.0);
+  }
+};
+
+struct Ctx {
+  orc_config c;
+  std::map<uint64_t, Node> nodes;   // ascending key = (instance, level, Morton)
+};
+
+// ---------------------------------------------------------------- Morton ids
+// Sec. 3, Eq. (MortonBits)/(AlpacaBits): 3 bits per level (bit 0 = x, bit 1 = y,
+// bit 2 = z), the finest level in the lowest group, a headbit above the top
+// group, seven shadow levels carrying the level-0 block coordinates.  In batched
+// runs the instance number sits in bits 56..63.
+uint64_t make_key(int inst, int level, const int64_t X[3]) {
+  int ng = NSHADOW + level;
+  uint64_t m = 0;
+  for (int b = 0; b < ng; ++b)
+    for (int d = 0; d < 3; ++d) m |= (uint64_t)((X[d] >> b) & 1) << (3 * b + d);
+  return ((uint64_t)inst << 56) | (1ull << (3 * ng)) | m;
+}
+
+int key_level(uint64_t key) {
+  uint64_t m = key & MASK56;
+  int h = 63 - __builtin_clzll(m);
+  return h / 3 - NSHADOW;
+}
+
+// Alg. (NeighborLookup): the same-level neighbour one step along axis d.  The
+// headbit is removed, every third bit starting at d is processed from the right
+// with  bit <- bit XNOR f  and  f <- bit OR f  (positive direction) or
+// f <- (NOT bit) OR f  (negative direction), and the headbit is put back.  A
+// carry out of the top group, or a result on a shadow position beyond the base
+// grid, is the domain boundary; periodic axes wrap within the base grid.
+bool axis_step(const orc_config& c, uint64_t key, int d, int sign, uint64_t* out) {
+  uint64_t inst = key >> 56;
+  uint64_t m = key & MASK56;
+  int level = key_level(key);
+  int nbits = 3 * (NSHADOW + level);
+  uint64_t head = 1ull << nbits;
+  uint64_t id = m ^ head;
+  int f = 0;
+  for (int i = d; i < nbits; i += 3) {
+    int bit = (int)((id >> i) & 1);
+    int nbit = !(bit ^ f);
+    id = (id & ~(1ull << i)) | ((uint64_t)nbit << i);
+    f = (sign > 0) ? (nbit | f) : ((!nbit) | f);
+  }
+  int64_t x = 0;
+  for (int b = 0; b < NSHADOW + level; ++b) x |= (int64_t)((id >> (3 * b + d)) & 1) << b;
+  int64_t nl = (int64_t)c.base_blocks[d] << level;
+  if (f == 0 || x >= nl) {
+    if (c.bc[2 * d] != BC_PERIODIC) return false;
+    x = (sign > 0) ? 0 : nl - 1;
+    for (int b = 0; b < NSHADOW + level; ++b) {
+      int i = 3 * b + d;
+      id = (id & ~(1ull << i)) | ((uint64_t)((x >> b) & 1) << i);
+    }
+  }
+  *out = (inst << 56) | head | id;
+  return true;
+}
+
+// Diagonal neighbours by concatenating the axis steps (Sec. 3).
+bool neighbour(const orc_config& c, uint64_t key, int sx, int sy, int sz, uint64_t* out) {
+  int s[3] = {sx, sy, sz};
+  uint64_t k = key;
+  for (int d = 0; d < 3; ++d) {
+    if (s[d] == 0) continue;
+    if (!axis_step(c, k, d, s[d], &k)) return false;
+  }
+  *out = k;
+  return true;
+}
+
+// ------------------------------------------------------------ EOS and fluxes
+// Eq. (Euler) with the stiffened-gas EOS, Eq. (StiffenedGas):
+// p = (gamma-1) rho e - gamma B,  E = rho e + 1/2 rho |v|^2,  c^2 = gamma (p+B)/rho.
+struct Prim { double rho, vel[3], p, c, E; };
+
+Prim prim_of(const double U[5], double g, double B) {
+  Prim q;
+  q.rho = U[0];
+  q.vel[0] = U[1] / q.rho;
+  q.vel[1] = U[2] / q.rho;
+  q.vel[2] = U[3] / q.rho;
+  double q2 = (q.vel[0] * q.vel[0] + q.vel[1] * q.vel[1]) + q.vel[2] * q.vel[2];
+  q.p = (g - 1.0) * (U[4] - 0.5 * q.rho * q2) - g * B;
+  q.c = std::sqrt(g * (q.p + B) / q.rho);
+  q.E = U[4];
+  return q;
+}
+
+// Rotated frame for direction d: (rho, m_n, m_t1, m_t2, E) with the tangential
+// axes in cyclic order, so that one set of x-direction formulas serves all three.
+inline int rot_axis(int d, int j) { return (d + j) % 3; }  // j = 0 normal, 1, 2 tangential
+
+void rotate(const double U[5], int d, double R[5]) {
+  R[0] = U[0];
+  R[1] = U[1 + rot_axis(d, 0)];
+  R[2] = U[1 + rot_axis(d, 1)];
+  R[3] = U[1 + rot_axis(d, 2)];
+  R[4] = U[4];
+}
+
+void unrotate(const double R[5], int d, double U[5]) {
+  U[0] = R[0];
+  U[1 + rot_axis(d, 0)] = R[1];
+  U[1 + rot_axis(d, 1)] = R[2];
+  U[1 + rot_axis(d, 2)] = R[3];
+  U[4] = R[4];
+}
+
+// Physical flux along d in the rotated frame: (m_n, m_n u_n + p, m_n u_t1, m_n u_t2, u_n (E + p)).
+void flux_rot(const double Ur[5], const Prim& q, int d, double F[5]) {
+  double un = q.vel[rot_axis(d, 0)];
+  double ut1 = q.vel[rot_axis(d, 1)];
+  double ut2 = q.vel[rot_axis(d, 2)];
+  F[0] = Ur[1];
+  F[1] = Ur[1] * un + q.p;
+  F[2] = Ur[1] * ut1;
+  F[3] = Ur[1] * ut2;
+  F[4] = un * (Ur[4] + q.p);
+}
+
+// Roe average at a face and its eigensystem in the rotated frame (Roe 1981,
+// named in Sec. 2.2).  Rows of Lm are left eigenvectors, columns of Rm right
+// eigenvectors, lam the eigenvalues (u-c, u, u, u, u+c).
+struct Eigen { double Lm[5][5], Rm[5][5], lam[5]; };
+
+Eigen roe_eigen(const Prim& a, const Prim& b, int d, double g) {
+  double sL = std::sqrt(a.rho), sR = std::sqrt(b.rho);
+  double den = sL + sR;
+  double un = (sL * a.vel[rot_axis(d, 0)] + sR * b.vel[rot_axis(d, 0)]) / den;
+  double ut1 = (sL * a.vel[rot_axis(d, 1)] + sR * b.vel[rot_axis(d, 1)]) / den;
+  double ut2 = (sL * a.vel[rot_axis(d, 2)] + sR * b.vel[rot_axis(d, 2)]) / den;
+  double HL = (a.E + a.p) / a.rho, HR = (b.E + b.p) / b.rho;
+  double H = (sL * HL + sR * HR) / den;
+  double q2 = (un * un + ut1 * ut1) + ut2 * ut2;
+  double c2 = (g - 1.0) * (H - 0.5 * q2);
+  double c = std::sqrt(c2);
+  double ic = 1.0 / c;
+  double b1 = (g - 1.0) / c2;
+  double b2 = 0.5 * b1 * q2;
+  Eigen e;
+  double l0[5] = {0.5 * (b2 + un * ic), 0.5 * (-b1 * un - ic), 0.5 * (-b1 * ut1), 0.5 * (-b1 * ut2), 0.5 * b1};
+  double l1[5] = {1.0 - b2, b1 * un, b1 * ut1, b1 * ut2, -b1};
+  double l2[5] = {-ut1, 0.0, 1.0, 0.0, 0.0};
+  double l3[5] = {-ut2, 0.0, 0.0, 1.0, 0.0};
+  double l4[5] = {0.5 * (b2 - un * ic), 0.5 * (-b1 * un + ic), 0.5 * (-b1 * ut1), 0.5 * (-b1 * ut2), 0.5 * b1};
+  double r0[5] = {1.0, un - c, ut1, ut2, H - un * c};
+  double r1[5] = {1.0, un, ut1, ut2, 0.5 * q2};
+  double r2[5] = {0.0, 0.0, 1.0, 0.0, ut1};
+  double r3[5] = {0.0, 0.0, 0.0, 1.0, ut2};
+  double r4[5] = {1.0, un + c, ut1, ut2, H + un * c};
+  const double* ls[5] = {l0, l1, l2, l3, l4};
+  const double* rs[5] = {r0, r1, r2, r3, r4};
+  for (int k = 0; k < 5; ++k)
+    for (int j = 0; j < 5; ++j) {
+      e.Lm[k][j] = ls[k][j];
+      e.Rm[j][k] = rs[k][j];
+    }
+  e.lam[0] = un - c;
+  e.lam[1] = un;
+  e.lam[2] = un;
+  e.lam[3] = un;
+  e.lam[4] = un + c;
+  return e;
+}
+
+// WENO5-JS (Jiang & Shu 1996, cited in Sec. 2.2) reconstructing the value at
+// the right face of the middle cell of (a, b, c, d, e); epsilon = 1e-6, linear
+// weights (0.1, 0.6, 0.3).
+double weno5(double a, double b, double c, double d, double e) {
+  const double eps = 1e-6;
+  double t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;
+  double beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  t1 = (b - 2.0 * c) + d;
+  t2 = b - d;
+  double beta1 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  t1 = (c - 2.0 * d) + e;
+  t2 = (3.0 * c - 4.0 * d) + e;
+  double beta2 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  double a0 = 0.1 / ((eps + beta0) * (eps + beta0));
+  double a1 = 0.6 / ((eps + beta1) * (eps + beta1));
+  double a2 = 0.3 / ((eps + beta2) * (eps + beta2));
+  double sum = (a0 + a1) + a2;
+  double q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
+  double q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
+  double q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
+  return ((a0 * q0 + a1 * q1) + a2 * q2) / sum;
+}
+
+// The same three candidate stencils combined with the linear weights: the
+// 5th-order upwind reconstruction.
+double linear5(double a, double b, double c, double d, double e) {
+  double q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
+  double q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
+  double q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
+  return (0.1 * q0 + 0.6 * q1) + 0.3 * q2;
+}
+
+inline double recon5(int mode, double a, double b, double c, double d, double e) {
+  return (mode == RECON_LINEAR) ? linear5(a, b, c, d, e) : weno5(a, b, c, d, e);
+}
+
+// Numerical flux at the face between cells 2 and 3 of a six-cell stencil
+// (cells i-2 .. i+3), along direction d, returned in the lab frame.
+// Characteristic-wise reconstruction: v = L U, g = L F(U) with the Roe
+// matrices of the face; per field k, Roe upwinding when the cell eigenvalues on
+// both sides and the Roe eigenvalue share a strict sign, else the local
+// Lax-Friedrichs split with alpha = max(|lam_k(U_i)|, |lam_k(U_{i+1})|) from
+// the two cells sharing the face (Sec. 2.2); F = R g_hat.
+void face_flux(const double U6[6][5], int d, double g, double B, int mode, double Fout[5]) {
+  Prim q[6];
+  double Ur[6][5], Fr[6][5];
+  for (int m = 0; m < 6; ++m) {
+    q[m] = prim_of(U6[m], g, B);
+    rotate(U6[m], d, Ur[m]);
+    flux_rot(Ur[m], q[m], d, Fr[m]);
+  }
+  Eigen e = roe_eigen(q[2], q[3], d, g);
+  double v[5][6], gc[5][6];
+  for (int k = 0; k < 5; ++k)
+    for (int m = 0; m < 6; ++m) {
+      double sv = e.Lm[k][0] * Ur[m][0];
+      double sg = e.Lm[k][0] * Fr[m][0];
+      for (int j = 1; j < 5; ++j) {
+        sv = sv + e.Lm[k][j] * Ur[m][j];
+        sg = sg + e.Lm[k][j] * Fr[m][j];
+      }
+      v[k][m] = sv;
+      gc[k][m] = sg;
+    }
+  double unL = q[2].vel[d], unR = q[3].vel[d];
+  double lamL[5] = {unL - q[2].c, unL, unL, unL, unL + q[2].c};
+  double lamR[5] = {unR - q[3].c, unR, unR, unR, unR + q[3].c};
+  double gh[5];
+  for (int k = 0; k < 5; ++k) {
+    double lL = lamL[k], lR = lamR[k], lt = e.lam[k];
+    const double* G = gc[k];
+    if (lL > 0.0 && lR > 0.0 && lt > 0.0) {
+      gh[k] = recon5(mode, G[0], G[1], G[2], G[3], G[4]);
+    } else if (lL < 0.0 && lR < 0.0 && lt < 0.0) {
+      gh[k] = recon5(mode, G[5], G[4], G[3], G[2], G[1]);
+    } else {
+      double alpha = std::max(std::fabs(lL), std::fabs(lR));
+      double fp[6], fm[6];
+      for (int m = 0; m < 6; ++m) {
+        fp[m] = 0.5 * (G[m] + alpha * v[k][m]);
+        fm[m] = 0.5 * (G[m] - alpha * v[k][m]);
+      }
+      gh[k] = recon5(mode, fp[0], fp[1], fp[2], fp[3], fp[4]) + recon5(mode, fm[5], fm[4], fm[3], fm[2], fm[1]);
+    }
+  }
+  double Fr_hat[5];
+  for (int j = 0; j < 5; ++j) {
+    double s = e.Rm[j][0] * gh[0];
+    for (int k = 1; k < 5; ++k) s = s + e.Rm[j][k] * gh[k];
+    Fr_hat[j] = s;
+  }
+  unrotate(Fr_hat, d, Fout);
+}
+
+// ------------------------------------------------------------ MR operators
+// Prediction, Eq. (Prediction) with the Q-terms of the appendix.  c0 = -22/128,
+// c1 = 3/128, c_pq = c_p c_q, c_rpq = c_r c_p c_q, where index 0 belongs to an
+// offset of one parent cell and index 1 to an offset of two.  Q_z is read with
+// u_{i,j,k+2} (the printed u_{i+2,j,k+2} breaks the symmetry with Q_x and Q_y).
+// The lower child half along an axis takes the sign +1, the upper -1.
+struct Stencil {
+  const double* P;
+  int i, j, k;
+  double at(int a, int b, int c) const { return P[sidx(i + a, j + b, k + c)]; }
+};
+
+const double C0 = -22.0 / 128.0, C1 = 3.0 / 128.0;
+inline double cidx(int off) { return off == 1 ? C0 : C1; }
+
+// c_pq [ (u(+p,+q) + u(-p,-q)) - (u(-p,+q) + u(+p,-q)) ] on the axis pair (A, B)
+double mix2(const Stencil& s, int A, int Bx, int p, int q) {
+  auto u = [&](int sp, int sq) {
+    int o[3] = {0, 0, 0};
+    o[A] = sp * p;
+    o[Bx] = sq * q;
+    return s.at(o[0], o[1], o[2]);
+  };
+  return (u(1, 1) + u(-1, -1)) - (u(-1, 1) + u(1, -1));
+}
+
+// sum over the four sign triples of positive parity of u(s) - u(-s)
+double mix3(const Stencil& s, int p, int q, int r) {
+  const int sg[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, -1, 1}, {-1, 1, -1}};
+  double acc = 0.0;
+  for (int t = 0; t < 4; ++t) {
+    double term = s.at(sg[t][0] * p, sg[t][1] * q, sg[t][2] * r) - s.at(-sg[t][0] * p, -sg[t][1] * q, -sg[t][2] * r);
+    acc = (t == 0) ? term : acc + term;
+  }
+  return acc;
+}
+
+struct QTerms { double u, Qx, Qy, Qz, Qxy, Qxz, Qyz, Qxyz; };
+
+QTerms qterms(const double* P, int i, int j, int k) {
+  Stencil s{P, i, j, k};
+  QTerms t;
+  t.u = s.at(0, 0, 0);
+  t.Qx = C0 * (s.at(1, 0, 0) - s.at(-1, 0, 0)) + C1 * (s.at(2, 0, 0) - s.at(-2, 0, 0));
+  t.Qy = C0 * (s.at(0, 1, 0) - s.at(0, -1, 0)) + C1 * (s.at(0, 2, 0) - s.at(0, -2, 0));
+  t.Qz = C0 * (s.at(0, 0, 1) - s.at(0, 0, -1)) + C1 * (s.at(0, 0, 2) - s.at(0, 0, -2));
+  const int pq[4][2] = {{1, 1}, {2, 2}, {1, 2}, {2, 1}};   // c00, c11, c01, c10
+  double qxy = 0, qxz = 0, qyz = 0;
+  for (int t2 = 0; t2 < 4; ++t2) {
+    int p = pq[t2][0], q = pq[t2][1];
+    double cc = cidx(p) * cidx(q);
+    double a = cc * mix2(s, 0, 1, p, q), b = cc * mix2(s, 0, 2, p, q), c = cc * mix2(s, 1, 2, p, q);
+    qxy = (t2 == 0) ? a : qxy + a;
+    qxz = (t2 == 0) ? b : qxz + b;
+    qyz = (t2 == 0) ? c : qyz + c;
+  }
+  t.Qxy = qxy;
+  t.Qxz = qxz;
+  t.Qyz = qyz;
+  // c000, c111, c001, c110, c011, c100, c010, c101 (offsets x, y, z)
+  const int pqr[8][3] = {{1, 1, 1}, {2, 2, 2}, {1, 1, 2}, {2, 2, 1}, {1, 2, 2}, {2, 1, 1}, {1, 2, 1}, {2, 1, 2}};
+  double qxyz = 0;
+  for (int t3 = 0; t3 < 8; ++t3) {
+    int p = pqr[t3][0], q = pqr[t3][1], r = pqr[t3][2];
+    double cc = cidx(p) * cidx(q) * cidx(r);
+    double a = cc * mix3(s, p, q, r);
+    qxyz = (t3 == 0) ? a : qxyz + a;
+  }
+  t.Qxyz = qxyz;
+  return t;
+}
+
+inline double predict_from(const QTerms& t, double sx, double sy, double sz) {
+  return t.u + sx * t.Qx + sy * t.Qy + sz * t.Qz + (sx * sy) * t.Qxy + (sx * sz) * t.Qxz + (sy * sz) * t.Qyz +
+         (sx * sy * sz) * t.Qxyz;
+}
+
+// Value of fine cell (i, j, k) (stored index of child `ch`, i.e. in [-4, 20)^3)
+// predicted from the parent's stored array P of one variable.
+double predict_cell(const double* P, int ch, int i, int j, int k) {
+  int c[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+  int f[3] = {i, j, k}, p[3];
+  double s[3];
+  for (int d = 0; d < 3; ++d) {
+    int h = floordiv2(f[d]);
+    p[d] = 8 * c[d] + h;
+    s[d] = (f[d] - 2 * h == 0) ? 1.0 : -1.0;
+  }
+  QTerms t = qterms(P, p[0], p[1], p[2]);
+  return predict_from(t, s[0], s[1], s[2]);
+}
+
+// ------------------------------------------------------------ context helpers
+double dx_of(const Ctx& C, int level) { return std::ldexp(C.c.dx0, -level); }
+
+bool is_outside_region(const Ctx& C, const Node& n, int sx, int sy, int sz) {
+  int s[3] = {sx, sy, sz};
+  for (int d = 0; d < 3; ++d) {
+    if (s[d] == 0) continue;
+    int64_t nl = (int64_t)C.c.base_blocks[d] << n.level;
+    bool edge = (s[d] < 0) ? (n.X[d] == 0) : (n.X[d] == nl - 1);
+    if (edge && C.c.bc[2 * d + (s[d] > 0 ? 1 : 0)] != BC_PERIODIC) return true;
+  }
+  return false;
+}
+
+std::vector<Node*> nodes_at(Ctx& C, int level, bool leaves_only) {
+  std::vector<Node*> v;
+  for (auto& kv : C.nodes)
+    if ((level < 0 || kv.second.level == level) && (!leaves_only || kv.second.leaf)) v.push_back(&kv.second);
+  return v;
+}
+
+int max_level(const Ctx& C) {
+  int m = 0;
+  for (auto& kv : C.nodes) m = std::max(m, kv.second.level);
+  return m;
+}
+
+Node* find(Ctx& C, uint64_t key) {
+  auto it = C.nodes.find(key);
+  return it == C.nodes.end() ? nullptr : &it->second;
+}
+
+Node* parent_of(Ctx& C, const Node& n) {
+  if (n.level == 0) return nullptr;
+  uint64_t inst = n.key >> 56;
+  uint64_t pk = ((n.key & MASK56) >> 3) | (inst << 56);
+  return find(C, pk);
+}
+
+int child_index(const Node& n) { return (int)(n.key & 7); }
+
+// ------------------------------------------------------------ halo fill
+// Sec. 3 (Fig. MrCommunicationMesh) and Alg. (ComputeLoop): a halo region facing
+// a same-level node (brother or cousin, leaf or not) is a copy of its internal
+// cells; a region facing no same-level node is predicted from the block's own
+// parent; a region beyond the domain boundary takes the boundary condition.
+// Levels are processed coarse to fine because prediction reads the parent's halo.
+void apply_bc(const Ctx& C, Node& n) {
+  for (int d = 0; d < 3; ++d) {
+    for (int side = 0; side < 2; ++side) {
+      int bc = C.c.bc[2 * d + side];
+      if (bc == BC_PERIODIC) continue;
+      int64_t nl = (int64_t)C.c.base_blocks[d] << n.level;
+      if (side == 0 && n.X[d] != 0) continue;
+      if (side == 1 && n.X[d] != nl - 1) continue;
+      for (int k = -HW; k < NB + HW; ++k)
+        for (int j = -HW; j < NB + HW; ++j)
+          for (int i = -HW; i < NB + HW; ++i) {
+            int c[3] = {i, j, k};
+            int a = c[d];
+            bool ghost = (side == 0) ? (a < 0) : (a >= NB);
+            if (!ghost) continue;
+            int src[3] = {i, j, k};
+            if (bc == BC_ZERO_GRADIENT) src[d] = (side == 0) ? 0 : NB - 1;
+            else src[d] = (side == 0) ? (-1 - a) : (2 * NB - 1 - a);
+            for (int v = 0; v < NV; ++v) {
+              double val = n.u[(size_t)v * NCELL + sidx(src[0], src[1], src[2])];
+              if (bc == BC_SYMMETRY && v == 1 + d) val = -val;
+              n.u[(size_t)v * NCELL + sidx(i, j, k)] = val;
+            }
+          }
+    }
+  }
+}
+
+void fill_node(Ctx& C, Node& n) {
+  // resolve the 26 regions
+  int kind[27];          // 0 outside, 1 copy, 2 predict
+  const Node* src[27];
+  for (int sz = -1; sz <= 1; ++sz)
+    for (int sy = -1; sy <= 1; ++sy)
+      for (int sx = -1; sx <= 1; ++sx) {
+        int r = (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
+        src[r] = nullptr;
+        kind[r] = 0;
+        if (r == 13) continue;
+        if (is_outside_region(C, n, sx, sy, sz)) continue;
+        uint64_t nk;
+        bool ok = neighbour(C.c, n.key, sx, sy, sz, &nk);
+        if (!ok) continue;
+        Node* nb = find(C, nk);
+        if (nb) {
+          kind[r] = 1;
+          src[r] = nb;
+        } else {
+          kind[r] = 2;
+        }
+      }
+  Node* par = parent_of(C, n);
+  int ch = child_index(n);
+  for (int k = -HW; k < NB + HW; ++k)
+    for (int j = -HW; j < NB + HW; ++j)
+      for (int i = -HW; i < NB + HW; ++i) {
+        int sx = i < 0 ? -1 : (i >= NB ? 1 : 0);
+        int sy = j < 0 ? -1 : (j >= NB ? 1 : 0);
+        int sz = k < 0 ? -1 : (k >= NB ? 1 : 0);
+        int r = (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
+        if (r == 13 || kind[r] == 0) continue;
+        for (int v = 0; v < NV; ++v) {
+          double val;
+          if (kind[r] == 1) {
+            val = src[r]->u[(size_t)v * NCELL + sidx(i - NB * sx, j - NB * sy, k - NB * sz)];
+          } else {
+            val = predict_cell(&par->u[(size_t)v * NCELL], ch, i, j, k);
+          }
+          n.u[(size_t)v * NCELL + sidx(i, j, k)] = val;
+        }
+      }
+  apply_bc(C, n);
+}
+
+void fill_halos(Ctx& C) {
+  int lm = max_level(C);
+  for (int l = 0; l <= lm; ++l) {
+    std::vector<Node*> v = nodes_at(C, l, false);
+#pragma omp parallel for schedule(dynamic)
+    for (long t = 0; t < (long)v.size(); ++t) fill_node(C, *v[t]);
+  }
+}
+
+// ------------------------------------------------------------ right-hand side
+// Sec. 2.2: dimension-by-dimension face fluxes; L = -sum_d (F_{+1/2} - F_{-1/2})/dx
+// evaluated as ((Fx_lo - Fx_hi) + (Fy_lo - Fy_hi) + (Fz_lo - Fz_hi)) / dx, plus the
+// gravity source S = (0, rho g, m . g) of Eq. (Euler) when gravity is set.
+void leaf_rhs(const Ctx& C, Node& n) {
+  double g = C.c.gamma, B = C.c.B;
+  double dx = dx_of(C, n.level);
+  // flux[d][v][face along d][t] for every face of the block (17 per pencil)
+  std::vector<double> F((size_t)3 * NV * (NB + 1) * NFACE);
+  auto fidx = [&](int d, int v, int f, int a, int b) {
+    return ((((size_t)d * NV + v) * (NB + 1) + f) * NB + b) * NB + a;
+  };
+  for (int d = 0; d < 3; ++d) {
+    for (int b = 0; b < NB; ++b)
+      for (int a = 0; a < NB; ++a)
+        for (int f = 0; f <= NB; ++f) {
+          double U6[6][5];
+          for (int m = 0; m < 6; ++m) {
+            int along = f - 3 + m;
+            int c[3];
+            c[d] = along;
+            c[(d == 0) ? 1 : 0] = a;
+            c[(d == 2) ? 1 : 2] = b;
+            for (int v = 0; v < NV; ++v) U6[m][v] = n.u[(size_t)v * NCELL + sidx(c[0], c[1], c[2])];
+          }
+          double Fo[5];
+          face_flux(U6, d, g, B, C.c.recon, Fo);
+          for (int v = 0; v < NV; ++v) F[fidx(d, v, f, a, b)] = Fo[v];
+        }
+  }
+  // tangential index pairs: d=0 -> (y, z), d=1 -> (x, z), d=2 -> (x, y)
+  for (int k = 0; k < NB; ++k)
+    for (int j = 0; j < NB; ++j)
+      for (int i = 0; i < NB; ++i)
+        for (int v = 0; v < NV; ++v) {
+          double acc = F[fidx(0, v, i, j, k)] - F[fidx(0, v, i + 1, j, k)];
+          acc = acc + (F[fidx(1, v, j, i, k)] - F[fidx(1, v, j + 1, i, k)]);
+          acc = acc + (F[fidx(2, v, k, i, j)] - F[fidx(2, v, k + 1, i, j)]);
+          double Lv = acc / dx;
+          n.L[(size_t)v * NINT + iidx(i, j, k)] = Lv;
+        }
+  double gx = C.c.gravity[0], gy = C.c.gravity[1], gz = C.c.gravity[2];
+  if (gx != 0.0 || gy != 0.0 || gz != 0.0) {
+    for (int k = 0; k < NB; ++k)
+      for (int j = 0; j < NB; ++j)
+        for (int i = 0; i < NB; ++i) {
+          int s = sidx(i, j, k), t = iidx(i, j, k);
+          double rho = n.u[s], mx = n.u[NCELL + s], my = n.u[2 * NCELL + s], mz = n.u[3 * NCELL + s];
+          n.L[(size_t)1 * NINT + t] = n.L[(size_t)1 * NINT + t] + rho * gx;
+          n.L[(size_t)2 * NINT + t] = n.L[(size_t)2 * NINT + t] + rho * gy;
+          n.L[(size_t)3 * NINT + t] = n.L[(size_t)3 * NINT + t] + rho * gz;
+          n.L[(size_t)4 * NINT + t] = n.L[(size_t)4 * NINT + t] + ((mx * gx + my * gy) + mz * gz);
+        }
+  }
+  // boundary-face fluxes for the jump correction: side 2d at face 0, 2d+1 at face 16
+  for (int d = 0; d < 3; ++d)
+    for (int v = 0; v < NV; ++v)
+      for (int b = 0; b < NB; ++b)
+        for (int a = 0; a < NB; ++a) {
+          n.face[(((size_t)(2 * d) * NV + v) * NB + b) * NB + a] = F[fidx(d, v, 0, a, b)];
+          n.face[(((size_t)(2 * d + 1) * NV + v) * NB + b) * NB + a] = F[fidx(d, v, NB, a, b)];
+        }
+}
+
+void compute_L_all(Ctx& C) {
+  std::vector<Node*> v = nodes_at(C, -1, true);
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < (long)v.size(); ++t) leaf_rhs(C, *v[t]);
+}
+
+// Face fluxes of internal nodes: the mean of the four child faces covering each
+// parent face cell, bottom-up (the face buffers that keep jumps conservative,
+// Sec. 4 and Alg. (ComputeLoop) averaging of F).  Tangential axes (t1, t2):
+// x-faces (y, z), y-faces (x, z), z-faces (x, y).
+void average_faces(Ctx& C) {
+  int lm = max_level(C);
+  for (int l = lm - 1; l >= 0; --l) {
+    std::vector<Node*> v = nodes_at(C, l, false);
+#pragma omp parallel for schedule(dynamic)
+    for (long t = 0; t < (long)v.size(); ++t) {
+      Node& P = *v[t];
+      if (P.leaf) continue;
+      uint64_t inst = P.key >> 56;
+      for (int s = 0; s < 6; ++s) {
+        int d = s / 2, hi = s & 1;
+        int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+        for (int bb = 0; bb < NB; ++bb)
+          for (int aa = 0; aa < NB; ++aa) {
+            int ct1 = aa / 8, ct2 = bb / 8;
+            int cb[3];
+            cb[d] = hi;
+            cb[t1] = ct1;
+            cb[t2] = ct2;
+            int ch = cb[0] | (cb[1] << 1) | (cb[2] << 2);
+            uint64_t ck = (((P.key & MASK56) << 3) | (uint64_t)ch) | (inst << 56);
+            const Node* c = find(C, ck);
+            int fa = 2 * (aa - 8 * ct1), fb = 2 * (bb - 8 * ct2);
+            for (int v2 = 0; v2 < NV; ++v2) {
+              auto f = [&](int x, int y) { return c->face[(((size_t)s * NV + v2) * NB + fb + y) * NB + fa + x]; };
+              double val = 0.25 * ((f(0, 0) + f(1, 0)) + (f(0, 1) + f(1, 1)));
+              P.face[(((size_t)s * NV + v2) * NB + bb) * NB + aa] = val;
+            }
+          }
+      }
+    }
+  }
+}
+
+// Jump correction (Sec. 4 and Alg. (ComputeLoop)): a leaf face that touches a
+// finer region replaces its own flux by the averaged fine flux.  Applied to the
+// stage result, as the paper adjusts coarse cell values after integration:
+// u += b_s (dt dL), dL = (F_coarse - F_fine)/dx on an upper face and
+// (F_fine - F_coarse)/dx on a lower face; sides in the order x-, x+, y-, y+, z-, z+.
+// With target_L the same correction is added to L instead (L += dL).
+void jump_correct(Ctx& C, bool target_L, double bs, const double* dt) {
+  std::vector<Node*> v = nodes_at(C, -1, true);
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < (long)v.size(); ++t) {
+    Node& n = *v[t];
+    double dx = dx_of(C, n.level);
+    for (int s = 0; s < 6; ++s) {
+      int d = s / 2, hi = s & 1;
+      uint64_t nk;
+      if (!axis_step(C.c, n.key, d, hi ? 1 : -1, &nk)) continue;
+      const Node* nb = find(C, nk);
+      if (!nb || nb->leaf) continue;
+      int so = s ^ 1;
+      int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+      for (int bb = 0; bb < NB; ++bb)
+        for (int aa = 0; aa < NB; ++aa) {
+          int c[3];
+          c[d] = hi ? NB - 1 : 0;
+          c[t1] = aa;
+          c[t2] = bb;
+          for (int v2 = 0; v2 < NV; ++v2) {
+            double Fc = n.face[(((size_t)s * NV + v2) * NB + bb) * NB + aa];
+            double Ff = nb->face[(((size_t)so * NV + v2) * NB + bb) * NB + aa];
+            double dL = hi ? (Fc - Ff) / dx : (Ff - Fc) / dx;
+            if (target_L) {
+              double& Lr = n.L[(size_t)v2 * NINT + iidx(c[0], c[1], c[2])];
+              Lr = Lr + dL;
+            } else {
+              double& ur = n.u[(size_t)v2 * NCELL + sidx(c[0], c[1], c[2])];
+              ur = ur + bs * (dt[n.inst] * dL);
+            }
+          }
+        }
+    }
+  }
+}
+
+// ------------------------------------------------------------ time integration
+// TVD-RK3 in Shu-Osher form: u1 = un + dt L(un); u2 = 3/4 un + 1/4 (u1 + dt L(u1));
+// u3 = 1/3 un + 2/3 (u2 + dt L(u2)); evaluated as t = u + dt L, out = a un + b t.
+const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
+const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
+
+void rk_update(Ctx& C, int s, const double* dt) {
+  std::vector<Node*> v = nodes_at(C, -1, true);
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < (long)v.size(); ++t) {
+    Node& n = *v[t];
+    double h = dt[n.inst];
+    for (int var = 0; var < NV; ++var)
+      for (int k = 0; k < NB; ++k)
+        for (int j = 0; j < NB; ++j)
+          for (int i = 0; i < NB; ++i) {
+            size_t si = (size_t)var * NCELL + sidx(i, j, k);
+            size_t ii = (size_t)var * NINT + iidx(i, j, k);
+            if (s == 0) n.un[ii] = n.u[si];
+            double tt = n.u[si] + h * n.L[ii];
+            n.u[si] = (s == 0) ? tt : (RK_A[s] * n.un[ii] + RK_B[s] * tt);
+          }
+  }
+}
+
+// Averaging, Eq. (Averaging): a parent cell is the mean of its eight children,
+// summed pairwise in Morton order ((c0+c1)+(c2+c3))+((c4+c5)+(c6+c7)), levels
+// from fine to coarse.
+void project(Ctx& C) {
+  int lm = max_level(C);
+  for (int l = lm - 1; l >= 0; --l) {
+    std::vector<Node*> v = nodes_at(C, l, false);
+#pragma omp parallel for schedule(dynamic)
+    for (long t = 0; t < (long)v.size(); ++t) {
+      Node& P = *v[t];
+      if (P.leaf) continue;
+      uint64_t inst = P.key >> 56;
+      const Node* ch[8];
+      for (int c = 0; c < 8; ++c) ch[c] = find(C, (((P.key & MASK56) << 3) | (uint64_t)c) | (inst << 56));
+      for (int K = 0; K < NB; ++K)
+        for (int J = 0; J < NB; ++J)
+          for (int I = 0; I < NB; ++I) {
+            int o = (I / 8) | ((J / 8) << 1) | ((K / 8) << 2);
+            const Node* c = ch[o];
+            int fi = 2 * (I - 8 * (I / 8)), fj = 2 * (J - 8 * (J / 8)), fk = 2 * (K - 8 * (K / 8));
+            for (int v2 = 0; v2 < NV; ++v2) {
+              const double* u = &c->u[(size_t)v2 * NCELL];
+              double c0 = u[sidx(fi, fj, fk)], c1 = u[sidx(fi + 1, fj, fk)];
+              double c2 = u[sidx(fi, fj + 1, fk)], c3 = u[sidx(fi + 1, fj + 1, fk)];
+              double c4 = u[sidx(fi, fj, fk + 1)], c5 = u[sidx(fi + 1, fj, fk + 1)];
+              double c6 = u[sidx(fi, fj + 1, fk + 1)], c7 = u[sidx(fi + 1, fj + 1, fk + 1)];
+              P.u[(size_t)v2 * NCELL + sidx(I, J, K)] = 0.125 * (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7)));
+            }
+          }
+    }
+  }
+}
+
+// Eq. (Cfl): dt = CFL dx_lmax / ( max|u|+c + max|v|+c + max|w|+c ), each maximum
+// over all leaf internal cells of the instance, summed in x, y, z order.
+void cfl_dt(Ctx& C, double* dt) {
+  int ni = C.c.n_instances;
+  std::vector<double> sm((size_t)ni * 3, 0.0);
+  for (auto& kv : C.nodes) {
+    Node& n = kv.second;
+    if (!n.leaf) continue;
+    for (int k = 0; k < NB; ++k)
+      for (int j = 0; j < NB; ++j)
+        for (int i = 0; i < NB; ++i) {
+          double U[5];
+          for (int v = 0; v < NV; ++v) U[v] = n.u[(size_t)v * NCELL + sidx(i, j, k)];
+          Prim q = prim_of(U, C.c.gamma, C.c.B);
+          for (int d = 0; d < 3; ++d) sm[(size_t)n.inst * 3 + d] = std::max(sm[(size_t)n.inst * 3 + d], std::fabs(q.vel[d]) + q.c);
+        }
+  }
+  for (int i = 0; i < ni; ++i) {
+    double dxl = dx_of(C, C.c.lmax[i]);
+    dt[i] = C.c.cfl * dxl / ((sm[(size_t)i * 3] + sm[(size_t)i * 3 + 1]) + sm[(size_t)i * 3 + 2]);
+  }
+}
+
+// ------------------------------------------------------------ MR analysis
+// Eq. (DetailFunction): d = u_B - P(u_parent) over the block including its halo
+// (Sec. 3; ghost cells beyond a non-periodic domain boundary are not cells of
+// the domain and are left out).  Block norm (l-infinity, relative to the fine
+// value, over rho and E): delta_B = max |d_v| / |u_v|.  Eq. (LevelWiseEpsilon)
+// with D = 3: eps_l = 2^{-3 (lmax - l)} eps.
+double block_delta(Ctx& C, Node& n) {
+  Node* P = parent_of(C, n);
+  int ch = child_index(n);
+  double delta = 0.0;
+  const int vars[2] = {0, 4};
+  for (int k = -HW; k < NB + HW; ++k)
+    for (int j = -HW; j < NB + HW; ++j)
+      for (int i = -HW; i < NB + HW; ++i) {
+        int sx = i < 0 ? -1 : (i >= NB ? 1 : 0);
+        int sy = j < 0 ? -1 : (j >= NB ? 1 : 0);
+        int sz = k < 0 ? -1 : (k >= NB ? 1 : 0);
+        bool ghost = false;
+        int s[3] = {sx, sy, sz};
+        for (int d = 0; d < 3; ++d) {
+          if (s[d] == 0) continue;
+          int64_t nl = (int64_t)C.c.base_blocks[d] << n.level;
+          bool edge = (s[d] < 0) ? (n.X[d] == 0) : (n.X[d] == nl - 1);
+          if (edge && C.c.bc[2 * d + (s[d] > 0 ? 1 : 0)] != BC_PERIODIC) ghost = true;
+        }
+        if (ghost) continue;
+        for (int vi = 0; vi < 2; ++vi) {
+          int v = vars[vi];
+          double uf = n.u[(size_t)v * NCELL + sidx(i, j, k)];
+          double pr = predict_cell(&P->u[(size_t)v * NCELL], ch, i, j, k);
+          double r = std::fabs(uf - pr) / std::fabs(uf);
+          delta = std::max(delta, r);
+        }
+      }
+  return delta;
+}
+
+// Tags (Eq. (Thresholding)): REFINE if delta > eps_l and l < lmax; a sibling
+// group is COARSENED if all eight are leaves at level >= 2 (no node on level 1
+// is ever coarsened, Sec. 4) with delta < eps_l; equality keeps the block.
+void predict_and_tag(Ctx& C, int allow_refine, int8_t* tags, double* deltas) {
+  std::vector<Node*> leaves = nodes_at(C, -1, true);
+  std::vector<double> dl(leaves.size(), 0.0);
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < (long)leaves.size(); ++t)
+    if (leaves[t]->level >= 1) dl[t] = block_delta(C, *leaves[t]);
+  std::map<uint64_t, size_t> pos;
+  for (size_t t = 0; t < leaves.size(); ++t) pos[leaves[t]->key] = t;
+  for (size_t t = 0; t < leaves.size(); ++t) {
+    Node& n = *leaves[t];
+    int8_t tag = TAG_KEEP;
+    if (n.level >= 1) {
+      int lmx = C.c.lmax[n.inst];
+      double el = std::ldexp(C.c.eps, -3 * (lmx - n.level));
+      if (allow_refine && dl[t] > el && n.level < lmx) {
+        tag = TAG_REFINE;
+      } else if (n.level >= 2) {
+        bool all = true;
+        uint64_t inst = n.key >> 56;
+        uint64_t pk = (n.key & MASK56) >> 3;
+        for (int c = 0; c < 8 && all; ++c) {
+          uint64_t sk = ((pk << 3) | (uint64_t)c) | (inst << 56);
+          auto it = pos.find(sk);
+          if (it == pos.end()) { all = false; break; }
+          if (!(dl[it->second] < el)) all = false;
+        }
+        if (all) tag = TAG_COARSEN;
+      }
+    }
+    tags[t] = tag;
+    if (deltas) deltas[t] = dl[t];
+  }
+}
+
+void create_child(Ctx& C, Node& P, int ch) {
+  Node c;
+  c.inst = P.inst;
+  c.level = P.level + 1;
+  for (int d = 0; d < 3; ++d) c.X[d] = 2 * P.X[d] + ((ch >> d) & 1);
+  c.key = make_key(c.inst, c.level, c.X);
+  c.leaf = true;
+  c.alloc();
+  for (int v = 0; v < NV; ++v)
+    for (int k = -HW; k < NB + HW; ++k)
+      for (int j = -HW; j < NB + HW; ++j)
+        for (int i = -HW; i < NB + HW; ++i)
+          c.u[(size_t)v * NCELL + sidx(i, j, k)] = predict_cell(&P.u[(size_t)v * NCELL], ch, i, j, k);
+  C.nodes.emplace(c.key, std::move(c));
+}
+
+// Refinement creates the eight children from the prediction of the parent over
+// their whole stored range; coarsening removes a complete sibling group (the
+// parent already holds their average).  Refinements are applied before
+// coarsenings, each in ascending key order.
+int64_t remesh(Ctx& C, const int8_t* tags) {
+  std::vector<Node*> leaves = nodes_at(C, -1, true);
+  std::vector<uint64_t> ref, coarse_parents;
+  std::map<uint64_t, int> ccount;
+  for (size_t t = 0; t < leaves.size(); ++t) {
+    Node& n = *leaves[t];
+    if (tags[t] == TAG_REFINE && n.level < C.c.lmax[n.inst]) ref.push_back(n.key);
+    if (tags[t] == TAG_COARSEN && n.level >= 2) {
+      uint64_t inst = n.key >> 56;
+      uint64_t pk = ((n.key & MASK56) >> 3) | (inst << 56);
+      ccount[pk] += 1;
+    }
+  }
+  for (auto& kv : ccount)
+    if (kv.second == 8) coarse_parents.push_back(kv.first);
+  for (uint64_t k : ref) {
+    Node* P = find(C, k);
+    for (int ch = 0; ch < 8; ++ch) create_child(C, *P, ch);
+    P = find(C, k);
+    P->leaf = false;
+  }
+  for (uint64_t pk : coarse_parents) {
+    uint64_t inst = pk >> 56;
+    for (int ch = 0; ch < 8; ++ch) C.nodes.erase((((pk & MASK56) << 3) | (uint64_t)ch) | (inst << 56));
+    find(C, pk)->leaf = true;
+  }
+  int64_t nl = 0;
+  for (auto& kv : C.nodes) nl += kv.second.leaf ? 1 : 0;
+  return nl;
+}
+
+// Conservation sums: per instance, sum over leaves (key order) of the cell sum
+// (storage order) times dx^3.
+void sums(Ctx& C, double* out) {
+  int ni = C.c.n_instances;
+  for (int i = 0; i < ni * NV; ++i) out[i] = 0.0;
+  for (auto& kv : C.nodes) {
+    Node& n = kv.second;
+    if (!n.leaf) continue;
+    double dx = dx_of(C, n.level);
+    double vol = dx * dx * dx;
+    for (int v = 0; v < NV; ++v) {
+      double s = 0.0;
+      for (int k = 0; k < NB; ++k)
+        for (int j = 0; j < NB; ++j)
+          for (int i = 0; i < NB; ++i) s = s + n.u[(size_t)v * NCELL + sidx(i, j, k)];
+      out[(size_t)n.inst * NV + v] = out[(size_t)n.inst * NV + v] + s * vol;
+    }
+  }
+}
+
+void stage(Ctx& C, int s, const double* dt) {
+  fill_halos(C);
+  compute_L_all(C);
+  average_faces(C);
+  rk_update(C, s, dt);
+  jump_correct(C, false, RK_B[s], dt);
+  project(C);
+}
+
+bool any_mr(const Ctx& C) {
+  for (int i = 0; i < C.c.n_instances; ++i)
+    if (C.c.lmax[i] > 0) return true;
+  return false;
+}
+
+}  // namespace
+
+// =============================================================== C interface
+extern "C" {
+
+void* orc_create(const orc_config* cfg) {
+  Ctx* C = new Ctx();
+  C->c = *cfg;
+#ifdef _OPENMP
+  if (cfg->n_threads > 0) omp_set_num_threads(cfg->n_threads);
+#endif
+  for (int inst = 0; inst < cfg->n_instances; ++inst)
+    for (int64_t z = 0; z < cfg->base_blocks[2]; ++z)
+      for (int64_t y = 0; y < cfg->base_blocks[1]; ++y)
+        for (int64_t x = 0; x < cfg->base_blocks[0]; ++x) {
+          Node n;
+          n.inst = inst;
+          n.level = 0;
+          n.X[0] = x;
+          n.X[1] = y;
+          n.X[2] = z;
+          n.key = make_key(inst, 0, n.X);
+          n.leaf = true;
+          n.alloc();
+          C->nodes.emplace(n.key, std::move(n));
+        }
+  return C;
+}
+
+void orc_destroy(void* h) { delete (Ctx*)h; }
+
+int64_t orc_list(void* h, int32_t level, int32_t leaves_only, uint64_t* keys, int64_t cap) {
+  Ctx& C = *(Ctx*)h;
+  int64_t n = 0;
+  for (auto& kv : C.nodes) {
+    const Node& nd = kv.second;
+    if (level >= 0 && nd.level != level) continue;
+    if (leaves_only && !nd.leaf) continue;
+    if (keys && n < cap) keys[n] = nd.key;
+    ++n;
+  }
+  return n;
+}
+
+// Block geometry in the same order as orc_list: geo[n][4] = (level, X, Y, Z),
+// block coordinates on that level.
+int64_t orc_list_geometry(void* h, int32_t level, int32_t leaves_only, int64_t* geo, int64_t cap) {
+  Ctx& C = *(Ctx*)h;
+  int64_t n = 0;
+  for (auto& kv : C.nodes) {
+    const Node& nd = kv.second;
+    if (level >= 0 && nd.level != level) continue;
+    if (leaves_only && !nd.leaf) continue;
+    if (geo && n < cap) {
+      geo[4 * n] = nd.level;
+      geo[4 * n + 1] = nd.X[0];
+      geo[4 * n + 2] = nd.X[1];
+      geo[4 * n + 3] = nd.X[2];
+    }
+    ++n;
+  }
+  return n;
+}
+
+// prim: [n][5][16][16][16] primitive (rho, u, v, w, p) of the internal cells.
+int orc_set_state(void* h, const uint64_t* keys, int64_t n, const double* prim) {
+  Ctx& C = *(Ctx*)h;
+  double g = C.c.gamma, B = C.c.B;
+  for (int64_t b = 0; b < n; ++b) {
+    Node* nd = find(C, keys[b]);
+    if (!nd) return -1;
+    const double* P = prim + (size_t)b * NV * NINT;
+    for (int k = 0; k < NB; ++k)
+      for (int j = 0; j < NB; ++j)
+        for (int i = 0; i < NB; ++i) {
+          int t = iidx(i, j, k), s = sidx(i, j, k);
+          double rho = P[t], u = P[NINT + t], v = P[2 * NINT + t], w = P[3 * NINT + t], p = P[4 * NINT + t];
+          double q2 = (u * u + v * v) + w * w;
+          nd->u[s] = rho;
+          nd->u[NCELL + s] = rho * u;
+          nd->u[2 * NCELL + s] = rho * v;
+          nd->u[3 * NCELL + s] = rho * w;
+          nd->u[4 * NCELL + s] = (p + g * B) / (g - 1.0) + 0.5 * rho * q2;
+        }
+  }
+  return 0;
+}
+
+// Conserved state written directly (internal cells), [n][5][16^3].
+int orc_set_cons(void* h, const uint64_t* keys, int64_t n, const double* cons) {
+  Ctx& C = *(Ctx*)h;
+  for (int64_t b = 0; b < n; ++b) {
+    Node* nd = find(C, keys[b]);
+    if (!nd) return -1;
+    for (int v = 0; v < NV; ++v)
+      for (int k = 0; k < NB; ++k)
+        for (int j = 0; j < NB; ++j)
+          for (int i = 0; i < NB; ++i)
+            nd->u[(size_t)v * NCELL + sidx(i, j, k)] = cons[((size_t)b * NV + v) * NINT + iidx(i, j, k)];
+  }
+  return 0;
+}
+
+// cons: [n][5][16^3] (with_halo = 0) or [n][5][24^3] (with_halo = 1).
+int orc_get_state(void* h, const uint64_t* keys, int64_t n, double* cons, int32_t with_halo) {
+  Ctx& C = *(Ctx*)h;
+  for (int64_t b = 0; b < n; ++b) {
+    Node* nd = find(C, keys[b]);
+    if (!nd) return -1;
+    if (with_halo) {
+      std::memcpy(cons + (size_t)b * NV * NCELL, nd->u.data(), sizeof(double) * NV * NCELL);
+    } else {
+      for (int v = 0; v < NV; ++v)
+        for (int k = 0; k < NB; ++k)
+          for (int j = 0; j < NB; ++j)
+            for (int i = 0; i < NB; ++i)
+              cons[((size_t)b * NV + v) * NINT + iidx(i, j, k)] = nd->u[(size_t)v * NCELL + sidx(i, j, k)];
+    }
+  }
+  return 0;
+}
+
+void orc_fill_halos(void* h) { fill_halos(*(Ctx*)h); }
+
+// L of every leaf (leaf order) including the jump correction: [nleaves][5][16^3].
+void orc_compute_rhs(void* h, double* L) {
+  Ctx& C = *(Ctx*)h;
+  compute_L_all(C);
+  average_faces(C);
+  jump_correct(C, true, 1.0, nullptr);
+  if (L) {
+    size_t b = 0;
+    for (auto& kv : C.nodes) {
+      if (!kv.second.leaf) continue;
+      std::memcpy(L + b * NV * NINT, kv.second.L.data(), sizeof(double) * NV * NINT);
+      ++b;
+    }
+  }
+}
+
+// One TVD-RK3 stage on the leaves: L, update, jump correction (halos must be filled).
+void orc_rk_stage(void* h, int32_t s, const double* dt) {
+  Ctx& C = *(Ctx*)h;
+  compute_L_all(C);
+  average_faces(C);
+  rk_update(C, s, dt);
+  jump_correct(C, false, RK_B[s], dt);
+}
+
+void orc_project(void* h) { project(*(Ctx*)h); }
+void orc_cfl_dt(void* h, double* dt) { cfl_dt(*(Ctx*)h, dt); }
+void orc_predict_and_tag(void* h, int32_t allow_refine, int8_t* tags, double* deltas) {
+  predict_and_tag(*(Ctx*)h, allow_refine, tags, deltas);
+}
+int64_t orc_remesh(void* h, const int8_t* tags) { return remesh(*(Ctx*)h, tags); }
+void orc_sums(void* h, double* out) { sums(*(Ctx*)h, out); }
+
+// nsteps full steps: CFL, three stages, then (with MR) analysis and remesh.
+// dt_hist (nullable) receives [nsteps][n_instances].
+void orc_step(void* h, int32_t nsteps, double* dt_hist) {
+  Ctx& C = *(Ctx*)h;
+  std::vector<double> dt((size_t)C.c.n_instances);
+  for (int st = 0; st < nsteps; ++st) {
+    cfl_dt(C, dt.data());
+    if (dt_hist) std::memcpy(dt_hist + (size_t)st * C.c.n_instances, dt.data(), sizeof(double) * C.c.n_instances);
+    for (int s = 0; s < 3; ++s) stage(C, s, dt.data());
+    if (any_mr(C)) {
+      fill_halos(C);
+      std::vector<int8_t> tags((size_t)orc_list(h, -1, 1, nullptr, 0));
+      predict_and_tag(C, 1, tags.data(), nullptr);
+      remesh(C, tags.data());
+    }
+  }
+}
+
+// Same-level neighbour by Alg. (NeighborLookup): returns 1 and the id, or 0 at
+// a non-periodic domain boundary.
+int32_t orc_neighbor(const orc_config* cfg, uint64_t key, int32_t sx, int32_t sy, int32_t sz, uint64_t* out) {
+  return neighbour(*cfg, key, sx, sy, sz, out) ? 1 : 0;
+}
+
+uint64_t orc_make_key(int32_t inst, int32_t level, int64_t x, int64_t y, int64_t z) {
+  int64_t X[3] = {x, y, z};
+  return make_key(inst, level, X);
+}
+
+int32_t orc_key_level(uint64_t key) { return key_level(key); }
+
+// ---- pure functions exported for the pins
+double orc_weno5(const double* f) { return weno5(f[0], f[1], f[2], f[3], f[4]); }
+double orc_linear5(const double* f) { return linear5(f[0], f[1], f[2], f[3], f[4]); }
+
+void orc_flux(const double* U, int32_t d, double g, double B, double* F) {
+  Prim q = prim_of(U, g, B);
+  double Ur[5], Fr[5];
+  rotate(U, d, Ur);
+  flux_rot(Ur, q, d, Fr);
+  unrotate(Fr, d, F);
+}
+
+// Rotated-frame eigensystem of the Roe average between UL and UR (lab-frame
+// conserved states) along d; Lm, Rm row-major 5x5.
+void orc_roe_eigen(const double* UL, const double* UR, int32_t d, double g, double B, double* Lm, double* Rm,
+                   double* lam) {
+  Prim a = prim_of(UL, g, B), b = prim_of(UR, g, B);
+  Eigen e = roe_eigen(a, b, d, g);
+  for (int i = 0; i < 5; ++i) {
+    lam[i] = e.lam[i];
+    for (int j = 0; j < 5; ++j) {
+      Lm[i * 5 + j] = e.Lm[i][j];
+      Rm[i * 5 + j] = e.Rm[i][j];
+    }
+  }
+}
+
+void orc_face_flux(const double* U6, int32_t d, double g, double B, int32_t mode, double* F) {
+  double U[6][5];
+  for (int m = 0; m < 6; ++m)
+    for (int v = 0; v < 5; ++v) U[m][v] = U6[m * 5 + v];
+  face_flux(U, d, g, B, mode, F);
+}
+
+// Child `ch` (bit 0 x, bit 1 y, bit 2 z) predicted over its whole stored range
+// from a parent's stored array (one variable, 24^3).
+void orc_predict_block(const double* parent, int32_t ch, double* child) {
+  for (int k = -HW; k < NB + HW; ++k)
+    for (int j = -HW; j < NB + HW; ++j)
+      for (int i = -HW; i < NB + HW; ++i) child[sidx(i, j, k)] = predict_cell(parent, ch, i, j, k);
+}
+
+// Parent internal cells (16^3) from the eight children's stored arrays (8 x 24^3).
+void orc_average_block(const double* children, double* parent) {
+  for (int K = 0; K < NB; ++K)
+    for (int J = 0; J < NB; ++J)
+      for (int I = 0; I < NB; ++I) {
+        int o = (I / 8) | ((J / 8) << 1) | ((K / 8) << 2);
+        const double* u = children + (size_t)o * NCELL;
+        int fi = 2 * (I - 8 * (I / 8)), fj = 2 * (J - 8 * (J / 8)), fk = 2 * (K - 8 * (K / 8));
+        double c0 = u[sidx(fi, fj, fk)], c1 = u[sidx(fi + 1, fj, fk)];
+        double c2 = u[sidx(fi, fj + 1, fk)], c3 = u[sidx(fi + 1, fj + 1, fk)];
+        double c4 = u[sidx(fi, fj, fk + 1)], c5 = u[sidx(fi + 1, fj, fk + 1)];
+        double c6 = u[sidx(fi, fj + 1, fk + 1)], c7 = u[sidx(fi + 1, fj + 1, fk + 1)];
+        parent[iidx(I, J, K)] = 0.125 * (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7)));
+      }
+}
+
+int32_t orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+}  // extern "C"

@@ -1,0 +1,441 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms,
+invariants, special cases that reduce to textbook results, the exact Riemann
+solution and brute force on small inputs.  No GPU needed.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact_riemann as er
+from paper_2012_04385_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ------------------------------------------------------------------ helpers
+def cell_avgs_poly(coeffs, edges):
+    """Cell averages of the 1D polynomial sum c_k x^k over consecutive cells."""
+    out = []
+    for a, b in zip(edges[:-1], edges[1:]):
+        s = 0.0
+        for k, c in enumerate(coeffs):
+            s += c * (b ** (k + 1) - a ** (k + 1)) / ((k + 1) * (b - a))
+        out.append(s)
+    return np.array(out)
+
+
+def poly_at(coeffs, x):
+    return sum(c * x ** k for k, c in enumerate(coeffs))
+
+
+def run_fixed_dt(o, dt, t_end):
+    """Advance with a fixed dt (last step clipped to t_end), three stages per step."""
+    t = 0.0
+    ni = o.cfg.n_instances
+    while t < t_end - 1e-14:
+        h = min(dt, t_end - t)
+        for s in range(3):
+            o.fill_halos()
+            o.rk_stage(s, np.full(ni, h))
+            o.project()
+        t += h
+    return t
+
+
+def interleave(x, y, z, nbits):
+    m = 0
+    for b in range(nbits):
+        m |= ((x >> b) & 1) << (3 * b) | ((y >> b) & 1) << (3 * b + 1) | ((z >> b) & 1) << (3 * b + 2)
+    return m
+
+
+# ------------------------------------------------------------------ WENO5 / linear
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_weno_exact_on_quadratics(deg):
+    """Each candidate stencil reproduces a quadratic, so any convex weights do."""
+    rng = np.random.default_rng(deg)
+    for _ in range(20):
+        c = rng.uniform(-2, 2, deg + 1)
+        h = rng.uniform(0.01, 0.5)
+        edges = (np.arange(6) - 2.5) * h           # cells -2..2, interface at h/2
+        f = cell_avgs_poly(c, edges)
+        exact = poly_at(c, 0.5 * h)
+        scale = max(1.0, np.abs(f).max())
+        assert abs(oracle.weno5(f) - exact) <= 1e-13 * scale
+        assert abs(oracle.linear5(f) - exact) <= 1e-13 * scale
+
+
+def test_linear_exact_on_quartics_and_weno_not():
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        c = rng.uniform(-2, 2, 5)
+        edges = (np.arange(6) - 2.5) * 0.3
+        f = cell_avgs_poly(c, edges)
+        exact = poly_at(c, 0.15)
+        assert abs(oracle.linear5(f) - exact) <= 1e-13 * max(1.0, np.abs(f).max())
+
+
+def test_weno_mirror_and_discontinuity():
+    """A step: WENO keeps the value of the smooth side (no over/undershoot),
+    the linear scheme oscillates."""
+    f = np.array([1.0, 1.0, 0.0, 0.0, 0.0])
+    w = oracle.weno5(f)
+    assert abs(w) < 1e-3
+    assert oracle.linear5(f) < -0.1          # (2 - 13) / 60
+
+
+# ------------------------------------------------------------------ eigensystem
+def _rand_cons(rng, g=1.4):
+    rho = rng.uniform(0.1, 3)
+    u = rng.uniform(-2, 2, 3)
+    p = rng.uniform(0.1, 3)
+    return np.array([rho, rho * u[0], rho * u[1], rho * u[2], p / (g - 1) + 0.5 * rho * u @ u])
+
+
+def _rot(U, d):
+    return np.array([U[0], U[1 + d], U[1 + (d + 1) % 3], U[1 + (d + 2) % 3], U[4]])
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_eigensystem_inverse_and_roe_property(d):
+    rng = np.random.default_rng(10 + d)
+    for _ in range(50):
+        UL, UR = _rand_cons(rng), _rand_cons(rng)
+        Lm, Rm, lam = oracle.roe_eigen(UL, UR, d)
+        assert np.abs(Lm @ Rm - np.eye(5)).max() < 1e-12
+        A = Rm @ np.diag(lam) @ Lm
+        dF = _rot(oracle.flux(UR, d), d) - _rot(oracle.flux(UL, d), d)
+        lhs = A @ (_rot(UR, d) - _rot(UL, d))
+        assert np.abs(lhs - dF).max() < 1e-11 * max(1.0, np.abs(dF).max())
+
+
+def test_face_flux_consistency():
+    """Six equal cells: the numerical flux is the physical flux F(U)."""
+    rng = np.random.default_rng(3)
+    for d in range(3):
+        for _ in range(10):
+            U = _rand_cons(rng)
+            F = oracle.face_flux(np.tile(U, (6, 1)), d)
+            assert np.abs(F - oracle.flux(U, d)).max() < 1e-12 * max(1.0, np.abs(F).max())
+
+
+# ------------------------------------------------------------------ MR operators
+def test_average_of_prediction_is_identity():
+    """A(P(u)) = u (Sec. 2.3): within 4 ulp of the parent value per cell."""
+    rng = np.random.default_rng(11)
+    parent = rng.uniform(0.5, 2.0, (24, 24, 24))
+    kids = np.stack([oracle.predict_block(parent, c) for c in range(8)])
+    back = oracle.average_block(kids)
+    interior = parent[4:20, 4:20, 4:20]
+    ulp = np.spacing(np.abs(interior))
+    assert (np.abs(back - interior) <= 4 * ulp).all()
+
+
+def _avg3(c, lo, h):
+    """Cell averages over the cube grid starting at lo with spacing h of
+    sum_{a,b,c} C[a,b,c] x^a y^b z^c, on index grid [k][j][i] (24^3)."""
+    n = 24
+    e = lo + np.arange(n + 1) * h
+    mom = np.array([[(e[i + 1] ** (a + 1) - e[i] ** (a + 1)) / ((a + 1) * h) for i in range(n)] for a in range(5)])
+    # value[k, j, i] = sum C[a,b,c] mom[a,i] mom[b,j] mom[c,k]
+    return np.einsum("abc,ai,bj,ck->kji", c, mom, mom, mom)
+
+
+def test_prediction_reproduces_quartics():
+    """P is tensor-product quartic: exact on cell averages of x^a y^b z^c, a,b,c <= 4."""
+    rng = np.random.default_rng(12)
+    C = rng.uniform(-1, 1, (5, 5, 5))
+    H = 1.0 / 16
+    parent = _avg3(C, -4 * H, H)                 # parent stored cells, cell (0,0,0) at [0, H)
+    for ch in range(8):
+        cx, cy, cz = ch & 1, (ch >> 1) & 1, (ch >> 2) & 1
+        h = H / 2
+        lo = np.array([cx, cy, cz]) * 8 * H - 4 * h
+        # child grid origins differ per axis; build with separate einsum
+        n = 24
+        moms = []
+        for d in range(3):
+            e = lo[d] + np.arange(n + 1) * h
+            moms.append(np.array([[(e[i + 1] ** (a + 1) - e[i] ** (a + 1)) / ((a + 1) * h) for i in range(n)]
+                                 for a in range(5)]))
+        exact = np.einsum("abc,ai,bj,ck->kji", C, moms[0], moms[1], moms[2])
+        pred = oracle.predict_block(parent, ch)
+        # the prediction is valid where the parent stencil (+-2 cells) is inside the stored range
+        assert np.abs(pred - exact).max() < 1e-12 * max(1.0, np.abs(exact).max())
+
+
+def test_prediction_is_tensor_product_of_1d_rule():
+    """The Q-term form equals the tensor product of the 1D conservative
+    interpolation u_child = sum_m w_m u_{i+m}, w = (-3, 22, 128, -22, 3)/128
+    (lower child), mirrored for the upper child."""
+    rng = np.random.default_rng(13)
+    parent = rng.uniform(-1, 1, (24, 24, 24))
+    wl = np.array([-3.0, 22.0, 128.0, -22.0, 3.0]) / 128.0
+    wu = wl[::-1]
+    for ch in (0, 5, 7):
+        pred = oracle.predict_block(parent, ch)
+        c = [(ch >> d) & 1 for d in range(3)]
+        for _ in range(30):
+            f = rng.integers(-4, 20, 3)          # fine stored index (x, y, z)
+            p = [8 * c[d] + (f[d] // 2) for d in range(3)]
+            sub = [f[d] - 2 * (f[d] // 2) for d in range(3)]
+            w = [wl if sub[d] == 0 else wu for d in range(3)]
+            val = 0.0
+            for a, b, cc in itertools.product(range(5), repeat=3):
+                val += w[0][a] * w[1][b] * w[2][cc] * parent[p[2] + cc - 2 + 4, p[1] + b - 2 + 4, p[0] + a - 2 + 4]
+            got = pred[f[2] + 4, f[1] + 4, f[0] + 4]
+            assert abs(got - val) < 1e-13 * 40
+
+
+# ------------------------------------------------------------------ Morton ids
+def test_morton_neighbour_paper_example():
+    """Fig. (NeighborLookup): the z+ neighbour of 001 111 is 101 011, of 000 is 100."""
+    cfg = I.RunConfig(base_blocks=(2, 2, 2), lmax=(2,))
+    o = oracle.Oracle(cfg)
+    k = oracle.make_key(0, 1, 3, 1, 1)
+    assert k & 0o77 == 0b001111
+    n = o.neighbor(k, 0, 0, 1)
+    assert n is not None and n & 0o77 == 0b101011
+    assert oracle.key_level(n) == 1
+    k0 = oracle.make_key(0, 0, 0, 0, 0)
+    assert k0 & 0o7 == 0b000
+    assert o.neighbor(k0, 0, 0, 1) & 0o7 == 0b100
+    # headbit: level 1 keys have it at bit 3 * (7 + 1)
+    assert k >> 24 == 1
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_morton_neighbours_brute_force(periodic):
+    bc = (I.BC_PERIODIC,) * 6 if periodic else (I.BC_ZERO_GRADIENT,) * 6
+    cfg = I.RunConfig(base_blocks=(3, 2, 4), lmax=(3,), bc=bc, n_instances=2)
+    o = oracle.Oracle(cfg)
+    rng = np.random.default_rng(1 + periodic)
+    for _ in range(2):      # two random refinements
+        o.fill_halos()
+        tags = (rng.uniform(size=o.n_leaves()) < 0.3).astype(np.int8)
+        o.remesh(tags)
+    keys = o.keys(leaves_only=False)
+    geo = o.geometry(leaves_only=False)
+    nb = np.array(cfg.base_blocks)
+    for key, (lvl, X, Y, Z) in zip(keys, geo):
+        inst = int(key) >> 56
+        n = nb << lvl
+        for s in itertools.product((-1, 0, 1), repeat=3):
+            if s == (0, 0, 0):
+                continue
+            c = np.array([X, Y, Z]) + np.array(s)
+            if periodic:
+                c = c % n
+                inside = True
+            else:
+                inside = ((c >= 0) & (c < n)).all()
+            got = o.neighbor(int(key), *s)
+            if not inside:
+                assert got is None
+                continue
+            nbits = 7 + lvl
+            exp = (inst << 56) | (1 << (3 * nbits)) | interleave(int(c[0]), int(c[1]), int(c[2]), nbits)
+            assert got == exp
+
+
+# ------------------------------------------------------------------ invariants
+def _jump_tree(cfg, ic):
+    """Level 0 -> all level 1 -> a few blocks at levels 2 and 3 (jumps of 1 and 2)."""
+    o = oracle.Oracle(cfg)
+    o.set_state(o.keys(), ic(cfg, o.geometry()))
+    for sel in (lambda g: np.ones(len(g), bool), lambda g: (g[:, 1] == 1) & (g[:, 2] <= 1),
+                lambda g: (g[:, 0] == 2) & (g[:, 1] == 2)):
+        o.fill_halos()
+        g = o.geometry()
+        o.remesh(sel(g).astype(np.int8))
+        o.set_state(o.keys(), ic(cfg, o.geometry()))
+    o.project()
+    return o
+
+
+def test_free_stream_with_jumps():
+    cfg = I.explosion_config(lmax=3)
+    o = _jump_tree(cfg, I.ic_uniform)
+    assert len(set(o.geometry()[:, 0])) == 3
+    o.fill_halos()
+    L = o.compute_rhs()
+    assert np.count_nonzero(L) == 0                 # bitwise zero
+    U0 = o.get_state()
+    dts = o.step(3)
+    U1 = o.get_state()
+    assert (dts > 0).all()
+    for v in range(5):
+        vals = np.unique(U1[:, v])
+        assert vals.size == 1                         # identical in every cell
+        ref = U0[0, v, 0, 0, 0]
+        assert abs(vals[0] - ref) <= 2 * 3 * np.spacing(abs(ref)) + 1e-300
+
+
+def test_conservation_periodic_with_jumps():
+    cfg = I.periodic_config(base=(2, 2, 2), lmax=2, eps=1e-4)
+    o = oracle.Oracle(cfg)
+    o.set_state(o.keys(), I.ic_random_smooth(cfg, o.geometry()))
+    o.fill_halos()
+    o.remesh(np.ones(o.n_leaves(), np.int8))
+    o.set_state(o.keys(), I.ic_random_smooth(cfg, o.geometry()))
+    o.project()
+    o.fill_halos()
+    g = o.geometry()
+    o.remesh(((g[:, 1] == 1) & (g[:, 2] == 2)).astype(np.int8))
+    assert len(set(o.geometry()[:, 0])) == 2
+    s0 = o.sums()
+    o.step(6)
+    s1 = o.sums()
+    scale = np.abs(o.get_state()).max(axis=(0, 2, 3, 4)) * 1.0  # per-variable magnitude x unit volume
+    assert (np.abs(s1 - s0) <= 1e-13 * np.maximum(np.abs(s0), scale)).all(), (s1 - s0)
+
+
+def test_sod_exact_solution_and_transverse_momentum():
+    """Sec. 5.1: Sod along x converges to the exact solution; rho v, rho w stay 0."""
+    tox = dict(l.split() for l in open(os.path.join(HERE, "golden", "toro_test1.txt")) if l[0] != "#")
+    ps, us = er.star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+    assert abs(ps - float(tox["p_star"])) < 5e-6 and abs(us - float(tox["u_star"])) < 5e-6
+    t_end = 0.1
+    errs = []
+    for nx in (32, 64, 128):
+        nbx = nx // 16
+        cfg = I.sod_config(base_blocks=(nbx, 1, 1), dx0=1.0 / nx)
+        o = oracle.Oracle(cfg)
+        o.set_state(o.keys(), I.ic_sod(cfg, o.geometry()))
+        run_fixed_dt(o, 0.2 / nx, t_end)
+        U = o.get_state()
+        geo = o.geometry()
+        assert np.count_nonzero(U[:, 2]) == 0 and np.count_nonzero(U[:, 3]) == 0
+        rho = np.zeros(nx)
+        for b, (lvl, X, Y, Z) in enumerate(geo):
+            rho[X * 16:(X + 1) * 16] = U[b, 0, 0, 0, :]
+        # every (y, z) pencil identical
+        assert np.ptp(U[:, 0], axis=(1, 2)).max() == 0.0
+        edges = np.arange(nx + 1) / nx
+        ex = er.cell_average_density((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.5, t_end, edges)
+        errs.append(np.abs(rho - ex).mean())
+    assert errs[0] < 0.02
+    assert errs[1] < errs[0] * 0.8 and errs[2] < errs[1] * 0.8, errs
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_fifth_order_convergence_density_wave(axis):
+    """Smooth advected density wave, exact cell averages; observed L1 order."""
+    errs = []
+    t_end = 0.05
+    for n in (32, 64, 128):
+        base = [1, 1, 1]
+        base[axis] = n // 16
+        cfg = I.periodic_config(base=tuple(base))
+        cfg.dx0 = 1.0 / n
+        o = oracle.Oracle(cfg)
+        o.set_state(o.keys(), I.ic_density_wave(cfg, o.geometry(), axis=axis))
+        dt = 0.5 * (1.0 / n) ** (5.0 / 3.0)
+        run_fixed_dt(o, dt, t_end)
+        U = o.get_state()
+        ex = I.ic_density_wave(cfg, o.geometry(), axis=axis, t=t_end)[:, 0]
+        errs.append(np.abs(U[:, 0] - ex).mean())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    print("density wave axis", axis, "L1 errors", errs, "orders", orders)
+    assert min(orders) >= 4.7, (errs, orders)
+
+
+def test_tags_uniform_state_collapses_to_level1():
+    cfg = I.explosion_config(lmax=3)
+    o = _jump_tree(cfg, I.ic_uniform)
+    o.fill_halos()
+    tags, delta = o.predict_and_tag()
+    assert (tags != oracle.TAG_REFINE).all()
+    assert (delta == 0).all()
+    o.remesh(tags)
+    o.fill_halos()
+    tags, _ = o.predict_and_tag()
+    o.remesh(tags)
+    assert set(o.geometry()[:, 0]) == {1}
+
+
+def test_tags_quartic_field_no_refinement():
+    """Details of a tensor-product quartic vanish, so nothing refines."""
+    cfg = I.explosion_config(lmax=3, eps=1e-8)
+    rng = np.random.default_rng(4)
+    C = rng.uniform(-0.1, 0.1, (5, 5, 5))
+    C[0, 0, 0] = 2.0
+
+    def ic(cfg_, geo):
+        out = np.zeros((len(geo), 5, 16, 16, 16))
+        for b, (lvl, X, Y, Z) in enumerate(geo):
+            h = cfg_.dx0 * 0.5 ** lvl
+            moms = []
+            for d, X0 in enumerate((X, Y, Z)):
+                e = (X0 * 16 + np.arange(17)) * h
+                moms.append(np.array([[(e[i + 1] ** (a + 1) - e[i] ** (a + 1)) / ((a + 1) * h) for i in range(16)]
+                                      for a in range(5)]))
+            out[b, 0] = np.einsum("abc,ai,bj,ck->kji", C, *moms)
+        out[:, 4] = out[:, 0] + 1.0
+        return out
+
+    o = _jump_tree(cfg, ic)
+    o.fill_halos()
+    tags, delta = o.predict_and_tag()
+    # parents touching the zero-gradient boundary see ghost values in their stencils;
+    # away from it the details vanish to rounding
+    g = o.geometry()
+    nb = np.array(cfg.base_blocks)
+    interior = []
+    for lvl, X, Y, Z in g:
+        if lvl == 0:
+            interior.append(False)
+            continue
+        P = np.array([X, Y, Z]) // 2
+        n = nb << (lvl - 1)
+        interior.append(bool(((P > 0) & (P < n - 1)).all()))
+    interior = np.array(interior)
+    assert interior.sum() >= 8
+    assert delta[interior].max() < 1e-12
+    assert (tags[interior] != oracle.TAG_REFINE).all()
+
+
+def test_tags_refine_at_discontinuity_and_valid_octree():
+    cfg = I.explosion_config(lmax=2, dx0=1.0 / 32.0)
+    o = oracle.Oracle(cfg)
+    o.set_state(o.keys(), I.ic_explosion(cfg, o.geometry(), r0=0.25))
+    for m in range(1, cfg.lmax_of(0) + 1):
+        o.fill_halos()
+        g = o.geometry()
+        o.remesh((g[:, 0] == m - 1).astype(np.int8))
+        o.set_state(o.keys(), I.ic_explosion(cfg, o.geometry(), r0=0.25))
+        if m > 1:
+            o.fill_halos()
+            tags, _ = o.predict_and_tag(allow_refine=False)
+            o.remesh(tags)
+    o.project()
+    g = o.geometry()
+    lm = cfg.lmax_of(0)
+    assert g[:, 0].max() == lm and g[:, 0].min() >= 1
+    assert (g[:, 0] < lm).any()
+    # blocks crossing the sphere r = 0.25 are at the finest level
+    h = cfg.dx0 * 0.5 ** lm
+    for lvl, X, Y, Z in g:
+        hb = cfg.dx0 * 0.5 ** lvl * 16
+        lo = np.array([X, Y, Z]) * hb
+        corners = lo[None, :] + hb * np.array(list(itertools.product((0, 1), repeat=3)))
+        r = np.linalg.norm(corners - 0.5, axis=1)
+        if r.min() < 0.25 - 2 * h and r.max() > 0.25 + 2 * h:
+            assert lvl == lm
+    # valid octree: every internal node has its 8 children
+    allk = set(int(k) for k in o.keys(leaves_only=False))
+    leaves = set(int(k) for k in o.keys())
+    for k in allk - leaves:
+        inst, m = k >> 56, k & ((1 << 56) - 1)
+        for c in range(8):
+            assert ((inst << 56) | (m << 3) | c) in allk
+    for k in allk:
+        m = k & ((1 << 56) - 1)
+        if oracle.key_level(k) > 0:
+            assert (k >> 56 << 56) | (m >> 3) in allk
