@@ -1,0 +1,224 @@
+/*
+ * mrb — GB300-native hot path of the block-based multiresolution (MR) method
+ * for the 3D Euler equations of Hoppe, Adami & Adams, "A modular massively
+ * parallel computing environment for three-dimensional multiresolution
+ * simulations of compressible flows" (arXiv:2012.04385).
+ *
+ * C ABI of libmrb.so.  Every call is extern "C", takes plain pointers and
+ * sizes, returns an int status (MRB_OK = 0) and never throws.  The message of
+ * the last failure is available from mrb_last_error().
+ *
+ * Memory.  The block pool (all heavy per-block data) is a device arena that
+ * the caller allocates and owns (size from mrb_pool_bytes) and passes to
+ * mrb_init_blocks; the library never frees it.  The library allocates only
+ * small internal arrays (topology, work lists, reduction scratch) and frees
+ * them in mrb_destroy.  Arguments documented "device" are device pointers
+ * owned by the caller; "host" pointers are ordinary host memory.
+ *
+ * Streams.  Every call enqueues its work on cfg.stream (a cudaStream_t, NULL =
+ * legacy default stream) and returns without synchronising, except
+ * mrb_remesh, mrb_list_blocks/mrb_n_blocks (host topology only), mrb_sync and
+ * mrb_destroy.  Kernel-side failures set a sticky device status word that
+ * mrb_sync and mrb_remesh return and mrb_status reads.
+ *
+ * Layouts.  A block holds 16^3 internal cells (IC) and four halo cells per
+ * side (Sec. 3 of the paper), 24^3 stored cells.  Per-block arrays are
+ * structure-of-arrays, variable-major: [5][z][y][x] with x fastest.  The
+ * conserved variables are (rho, rho u, rho v, rho w, E); primitive inputs are
+ * (rho, u, v, w, p).  Blocks are identified by 64-bit modified Morton ids
+ * (Sec. 3, Eq. MortonBits/AlpacaBits): 3 bits per level (x in bit 0, y in bit
+ * 1, z in bit 2), finest level in the lowest group, a headbit above the top
+ * group, 7 shadow levels holding the level-0 block coordinates, and the
+ * instance number in bits 56..63.  Block lists are always in ascending id
+ * order, which is (instance, level, Morton) order.
+ */
+#ifndef MRB_H
+#define MRB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MRB_OK 0
+#define MRB_EINVAL 1      /* bad argument (null, out of range, unknown id)           */
+#define MRB_ENOMEM 2      /* internal allocation failed                              */
+#define MRB_ECAPACITY 3   /* block pool or a list buffer too small                   */
+#define MRB_ECUDA 4       /* a CUDA runtime call failed                              */
+#define MRB_ETIMEOUT 5    /* a bounded device wait gave up                           */
+#define MRB_ENONPHYS 6    /* non-physical state (rho <= 0, p + B <= 0 or NaN)        */
+
+/* boundary conditions, per side x-, x+, y-, y+, z-, z+ */
+#define MRB_BC_ZERO_GRADIENT 0
+#define MRB_BC_PERIODIC 1
+#define MRB_BC_SYMMETRY 2
+
+/* arithmetic of the bulk reconstruction/flux work */
+#define MRB_FP64 0        /* everything in FP64                                      */
+#define MRB_FP32_ACC64 1  /* FP32 reconstruction and flux, FP64 state, update,
+                             conservation sums and time-step reduction             */
+
+/* reconstruction */
+#define MRB_RECON_WENO5 0     /* WENO5-JS everywhere                                 */
+#define MRB_RECON_LEARNED 1   /* per-face MLP chooses linear 5th order or WENO5-JS   */
+#define MRB_RECON_LINEAR5 2   /* linear 5th-order upwind everywhere (tests)          */
+
+/* refinement tags, one int8 per leaf in leaf order */
+#define MRB_TAG_KEEP 0
+#define MRB_TAG_REFINE 1
+#define MRB_TAG_COARSEN (-1)
+
+#define MRB_MAX_INSTANCES 256
+#define MRB_MAX_LEVEL 11
+
+typedef struct mrb_config {
+  int32_t n_instances;             /* independent simulations in one pool, <= 256         */
+  int32_t base_blocks[3];          /* level-0 blocks per axis, each <= 128                 */
+  int32_t lmax[MRB_MAX_INSTANCES]; /* finest level per instance, <= MRB_MAX_LEVEL          */
+  int32_t bc[6];                   /* MRB_BC_* per side; periodic must be set on both sides*/
+  int32_t precision;               /* MRB_FP64 | MRB_FP32_ACC64                            */
+  int32_t recon;                   /* MRB_RECON_*                                          */
+  int32_t pad0;
+  int32_t pad1;
+  double domain_lo[3];             /* lower corner of the domain                           */
+  double dx0;                      /* level-0 cell size (block edge = 16 dx0)              */
+  double gamma, B;                 /* stiffened-gas EOS, Eq. (StiffenedGas)                */
+  double cfl;                      /* CFL number k of Eq. (Cfl)                            */
+  double gravity[3];               /* body force in S(U) of Eq. (Euler); zero = none       */
+  double eps;                      /* detail threshold at l_max (Eq. UserEpsilon applied)  */
+  const void* mlp_weights;         /* device, learned selector weights (see mrb_mlp_*)     */
+  double mlp_tau;                  /* logit threshold of the learned selector              */
+  void* stream;                    /* cudaStream_t for all work                            */
+} mrb_config;
+
+typedef struct mrb_ctx mrb_ctx;
+
+/* Bytes of block pool needed for `n_slots` blocks (leaves and internal nodes
+ * together).  Per block: two stage buffers with halo (2 x 5 x 24^3 doubles),
+ * the u^n buffer of the RK step (5 x 16^3) and six face-flux buffers
+ * (6 x 5 x 16^2), 256-byte aligned.  Returns 0 for a bad config. */
+size_t mrb_pool_bytes(const mrb_config* cfg, int64_t n_slots);
+
+/* Create a context: checks the config, builds the level-0 topology of every
+ * instance (Alg. Initialization, "initialize topology for level l0"; all
+ * level-0 blocks are leaves) inside the caller's pool (device, pool_bytes
+ * bytes, 256-byte aligned).  *out receives the context.  Errors: EINVAL,
+ * ECAPACITY (pool smaller than the level-0 blocks), ENOMEM, ECUDA. */
+int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ctx** out);
+
+/* Number of blocks (level < 0: all levels; leaves_only: leaves only). */
+int mrb_n_blocks(mrb_ctx* ctx, int32_t level, int32_t leaves_only, int64_t* n);
+
+/* Ids (host, [cap]) and geometry (host, nullable, [cap][4] = level, X, Y, Z
+ * block coordinates on that level) of the selected blocks in ascending id
+ * order; *n receives the count.  ECAPACITY if cap is too small. */
+int mrb_list_blocks(mrb_ctx* ctx, int32_t level, int32_t leaves_only, uint64_t* keys_host, int64_t* geo_host,
+                    int64_t cap, int64_t* n);
+
+/* Impose a state on the internal cells of the listed blocks (Alg.
+ * Initialization, "impose initial condition"): prim_dev [n][5][16][16][16]
+ * primitive (rho, u, v, w, p), converted with E = (p + gamma B)/(gamma - 1) +
+ * rho |v|^2 / 2.  keys_host: ids of existing blocks.  EINVAL on unknown id. */
+int mrb_set_state(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, const double* prim_dev);
+
+/* Impose a conserved state (device, [n][5][16^3], the layout mrb_get_state
+ * returns) on the internal cells of the listed blocks: restart from a saved
+ * state continues bit for bit.  EINVAL on unknown id. */
+int mrb_set_cons(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, const double* cons_dev);
+
+/* Conserved state of the listed blocks into cons_dev: [n][5][16^3] internal
+ * cells (with_halo = 0) or [n][5][24^3] stored cells (with_halo = 1). */
+int mrb_get_state(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, double* cons_dev, int32_t with_halo);
+
+/* Halo fill of every node (Sec. 3, Fig. MrCommunicationMesh): a halo region
+ * facing a same-level node (brother or cousin) is a copy of its internal
+ * cells, one facing no same-level node is predicted from the block's parent
+ * by Eq. (Prediction), and cells beyond a non-periodic domain boundary take
+ * the boundary condition (zero gradient, or mirror with negated normal
+ * momentum).  Levels are filled coarse to fine. */
+int mrb_fill_halos(mrb_ctx* ctx);
+
+/* Right-hand side L(U) = -sum_d dF_d/dx_l + S(U) of every leaf (Eq. Euler,
+ * Sec. 2.2: characteristic WENO5-JS, Roe flux with local Lax-Friedrichs
+ * fallback per field), with the jump flux correction applied (Sec. 4), into
+ * rhs_dev [n_leaves][5][16^3] in leaf order.  Inspection form: the time
+ * stepping uses the fused mrb_rk_stage.  Halos must be filled. */
+int mrb_compute_rhs(mrb_ctx* ctx, double* rhs_dev);
+
+/* One TVD-RK3 stage (stage = 0, 1, 2) on every leaf, fused with the
+ * right-hand side: u1 = un + dt L(un), u2 = 3/4 un + 1/4 (u1 + dt L(u1)),
+ * u3 = 1/3 un + 2/3 (u2 + dt L(u2)), followed by the jump flux correction of
+ * coarse cells next to finer leaves (Sec. 4, Alg. ComputeLoop).  dt_dev:
+ * device [n_instances] time steps (from mrb_cfl_dt).  Halos must be filled. */
+int mrb_rk_stage(mrb_ctx* ctx, int32_t stage, const double* dt_dev);
+
+/* Time step of Eq. (Cfl) per instance: dt = CFL dx_lmax /
+ * (max|u|+c + max|v|+c + max|w|+c) over the internal cells of its leaves,
+ * into dt_dev (device, [n_instances]).  The maxima are exact. */
+int mrb_cfl_dt(mrb_ctx* ctx, double* dt_dev);
+
+/* Averaging, Eq. (Averaging): every internal node's cells become the mean of
+ * their eight children, levels fine to coarse. */
+int mrb_mr_project(mrb_ctx* ctx);
+
+/* MR analysis (Eq. DetailFunction, Thresholding, LevelWiseEpsilon): for every
+ * leaf at level >= 1 the details d = u - P(u_parent) over its internal and
+ * halo cells (not ghost cells beyond a non-periodic boundary), block norm
+ * delta = max over cells and over rho, E of |d| / |u|, threshold
+ * eps_l = 2^(-3 (lmax - l)) eps.  Tags (device, [n_leaves] int8, leaf order):
+ * REFINE if delta > eps_l and l < lmax (only when allow_refine), COARSEN for
+ * a complete group of eight sibling leaves at level >= 2 all below eps_l,
+ * else KEEP.  delta_dev (device, [n_leaves], nullable) receives delta.
+ * Halos and the projection must be current. */
+int mrb_mr_predict_and_tag(mrb_ctx* ctx, int32_t allow_refine, int8_t* tags_dev, double* delta_dev);
+
+/* Apply tags (device, [n_leaves] int8, leaf order; as from
+ * mrb_mr_predict_and_tag or built by the caller): REFINE creates the eight
+ * children, each predicted from the parent over its 24^3 stored cells;
+ * COARSEN removes a complete sibling group (the parent already holds their
+ * average).  Invalid tags (REFINE at lmax, partial COARSEN groups) are
+ * ignored.  Rebuilds ids, leaf lists and the 26-neighbour table.
+ * Synchronises the stream.  *n_leaves (nullable) receives the leaf count.
+ * ECAPACITY when the pool has no free block left (the tree is unchanged). */
+int mrb_remesh(mrb_ctx* ctx, const int8_t* tags_dev, int64_t* n_leaves);
+
+/* nsteps complete steps: dt from Eq. (Cfl), three fused stages each preceded
+ * by the halo fill and followed by the averaging, then (when any lmax > 0)
+ * halo fill, MR analysis and remesh.  dt_hist_dev (device, nullable)
+ * receives [nsteps][n_instances] time steps.  The stage sequence is replayed
+ * from a CUDA graph. */
+int mrb_step(mrb_ctx* ctx, int32_t nsteps, double* dt_hist_dev);
+
+/* Conserved totals per instance: sum over leaves of U dx_l^3, [n_instances][5]
+ * into sums_dev (device), in a fixed reduction order. */
+int mrb_sums(mrb_ctx* ctx, double* sums_dev);
+
+/* Same-level neighbour ids of the listed blocks in the 26 directions
+ * (index (dz+1)*9 + (dy+1)*3 + (dx+1), centre skipped), host [n][27]:
+ * the id, or 0 where no same-level block exists, or 1 beyond a non-periodic
+ * boundary (ids always have a headbit, so 0 and 1 are never ids). */
+int mrb_neighbors(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, uint64_t* nbr_host);
+
+/* Profiling.  mrb_profile(ctx, 1) starts recording CUDA events around every
+ * launch of the fused stage kernel (the dominant kernel, on cfg.stream, also
+ * inside the replayed step graph) and resets the counters; 0 stops.
+ * mrb_profile_read synchronises and returns the summed duration of those
+ * launches (ms), their number, and the number of kernel launches the library
+ * issued since profiling started (graph replays count their kernel nodes).
+ * Any pointer may be null. */
+int mrb_profile(mrb_ctx* ctx, int32_t enable);
+int mrb_profile_read(mrb_ctx* ctx, double* stage_kernel_ms, int64_t* stage_kernel_launches, int64_t* kernel_launches);
+
+int mrb_status(mrb_ctx* ctx);   /* sticky device status (synchronises)       */
+int mrb_sync(mrb_ctx* ctx);     /* synchronise the stream, return status     */
+int mrb_destroy(mrb_ctx* ctx);  /* free internal arrays (not the pool)       */
+const char* mrb_last_error(mrb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRB_H */

@@ -886,7 +886,7 @@ void predict_and_tag(Ctx& C, int allow_refine, int8_t* tags, double* deltas) {
   }
 }
 
-void create_child(Ctx& C, Node& P, int ch) {
+Node make_child(const Node& P, int ch) {
   Node c;
   c.inst = P.inst;
   c.level = P.level + 1;
@@ -899,7 +899,7 @@ void create_child(Ctx& C, Node& P, int ch) {
       for (int j = -HW; j < NB + HW; ++j)
         for (int i = -HW; i < NB + HW; ++i)
           c.u[(size_t)v * NCELL + sidx(i, j, k)] = predict_cell(&P.u[(size_t)v * NCELL], ch, i, j, k);
-  C.nodes.emplace(c.key, std::move(c));
+  return c;
 }
 
 // Refinement creates the eight children from the prediction of the parent over
@@ -921,12 +921,11 @@ int64_t remesh(Ctx& C, const int8_t* tags) {
   }
   for (auto& kv : ccount)
     if (kv.second == 8) coarse_parents.push_back(kv.first);
-  for (uint64_t k : ref) {
-    Node* P = find(C, k);
-    for (int ch = 0; ch < 8; ++ch) create_child(C, *P, ch);
-    P = find(C, k);
-    P->leaf = false;
-  }
+  std::vector<Node> made(ref.size() * 8);
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < (long)made.size(); ++t) made[t] = make_child(*find(C, ref[t / 8]), (int)(t % 8));
+  for (size_t t = 0; t < made.size(); ++t) C.nodes.emplace(made[t].key, std::move(made[t]));
+  for (uint64_t k : ref) find(C, k)->leaf = false;
   for (uint64_t pk : coarse_parents) {
     uint64_t inst = pk >> 56;
     for (int ch = 0; ch < 8; ++ch) C.nodes.erase((((pk & MASK56) << 3) | (uint64_t)ch) | (inst << 56));

@@ -1,0 +1,616 @@
+// FP64 kernels of the block-based MR Euler hot path (arXiv:2012.04385): halo
+// fill, fused RHS + TVD-RK3 stage, face-flux averaging and jump correction,
+// averaging (projection), CFL reduction, MR details and tags, refinement
+// prediction, neighbour table, conservation sums, state import/export.
+//
+// Built with -fmad=false: every double is the correctly rounded result of the
+// operation order written here.
+#include "rhs.cuh"
+
+namespace mrb {
+
+long long g_kernel_launches = 0;
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+__device__ __forceinline__ int region_of(int i, int j, int k) {
+  int sx = i < 0 ? -1 : (i >= NB ? 1 : 0);
+  int sy = j < 0 ? -1 : (j >= NB ? 1 : 0);
+  int sz = k < 0 ? -1 : (k >= NB ? 1 : 0);
+  return (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
+}
+
+// ---------------------------------------------------------------- state in/out
+__global__ void k_set_state(Topo t, Phys p, Pool pool, int cur, const int32_t* __restrict__ nodes, int n,
+                            const double* __restrict__ prim) {
+  const double g = p.gamma, B = p.B;
+  const size_t total = (size_t)n * NINT;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / NINT), c = (int)(e % NINT);
+    const int i = c % 16, j = (c / 16) % 16, k = c / 256;
+    const double* P = prim + (size_t)b * NV * NINT;
+    double rho = P[c], u = P[NINT + c], v = P[2 * NINT + c], w = P[3 * NINT + c], pr = P[4 * NINT + c];
+    double q2 = (u * u + v * v) + w * w;
+    double* U = pool.buf[cur] + (size_t)t.slot[nodes[b]] * SLOT_U;
+    const int s = sidx(i, j, k);
+    U[s] = rho;
+    U[NCELL + s] = rho * u;
+    U[2 * NCELL + s] = rho * v;
+    U[3 * NCELL + s] = rho * w;
+    U[4 * NCELL + s] = (pr + g * B) / (g - 1.0) + 0.5 * rho * q2;
+  }
+}
+
+void launch_set_state(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* nodes, int n,
+                      const double* prim, cudaStream_t st) {
+  if (n <= 0) return;
+  k_set_state<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, nodes, n, prim);
+  ++g_kernel_launches;
+}
+
+__global__ void k_set_cons(Topo t, Pool pool, int cur, const int32_t* __restrict__ nodes, int n,
+                           const double* __restrict__ cons) {
+  const size_t total = (size_t)n * NV * NINT;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / ((size_t)NV * NINT));
+    const int r = (int)(e % ((size_t)NV * NINT));
+    const int v = r / NINT, c = r % NINT;
+    double* U = pool.buf[cur] + (size_t)t.slot[nodes[b]] * SLOT_U + (size_t)v * NCELL;
+    U[sidx(c % 16, (c / 16) % 16, c / 256)] = cons[e];
+  }
+}
+
+void launch_set_cons(const Topo& t, const Pool& pool, int cur, const int32_t* nodes, int n, const double* cons,
+                     cudaStream_t st) {
+  if (n <= 0) return;
+  k_set_cons<<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, nodes, n, cons);
+  ++g_kernel_launches;
+}
+
+__global__ void k_get_state(Topo t, Pool pool, int cur, const int32_t* __restrict__ nodes, int n,
+                            double* __restrict__ out, int with_halo) {
+  const int per = with_halo ? NCELL : NINT;
+  const size_t total = (size_t)n * NV * per;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / ((size_t)NV * per));
+    const int r = (int)(e % ((size_t)NV * per));
+    const int v = r / per, c = r % per;
+    const double* U = pool.buf[cur] + (size_t)t.slot[nodes[b]] * SLOT_U + (size_t)v * NCELL;
+    int s;
+    if (with_halo) s = c;
+    else s = sidx(c % 16, (c / 16) % 16, c / 256);
+    out[e] = U[s];
+  }
+}
+
+void launch_get_state(const Topo& t, const Pool& pool, int cur, const int32_t* nodes, int n, double* out,
+                      int with_halo, cudaStream_t st) {
+  if (n <= 0) return;
+  k_get_state<<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, nodes, n, out, with_halo);
+  ++g_kernel_launches;
+}
+
+// ---------------------------------------------------------------- halo fill
+// One CTA per node of `level`: every halo cell is copied from the same-level
+// neighbour of its region, or predicted from the node's parent, or left for
+// the boundary passes (x-, x+, y-, y+, z-, z+ in that order), which copy from
+// the block's own cells: zero gradient clamps, symmetry mirrors and negates
+// the normal momentum.
+__global__ void __launch_bounds__(256) k_fill_level(Topo t, Phys p, Pool pool, int cur, int level) {
+  const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
+  double* buf = pool.buf[cur];
+  __shared__ int kind[27];
+  __shared__ int src_slot[27];
+  for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
+    const int node = t.lvl_nodes[w];
+    double* u = buf + (size_t)t.slot[node] * SLOT_U;
+    const int par = t.parent[node];
+    const double* P = (par >= 0) ? buf + (size_t)t.slot[par] * SLOT_U : nullptr;
+    const int ch = (int)(t.keys[node] & 7ull);
+    __syncthreads();
+    if (threadIdx.x < 27) {
+      const int nb = t.nbr[(size_t)node * 27 + threadIdx.x];
+      kind[threadIdx.x] = (nb >= 0) ? 1 : ((nb == -1 && P != nullptr) ? 2 : 0);
+      src_slot[threadIdx.x] = (nb >= 0) ? t.slot[nb] : -1;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NCELL; idx += blockDim.x) {
+      const int i = idx % NS - HW, j = (idx / NS) % NS - HW, k = idx / (NS * NS) - HW;
+      const int r = region_of(i, j, k);
+      if (r == 13) continue;
+      const int kd = kind[r];
+      if (kd == 1) {
+        const int sx = r % 3 - 1, sy = (r / 3) % 3 - 1, sz = r / 9 - 1;
+        const double* s = buf + (size_t)src_slot[r] * SLOT_U;
+        const int off = idx - NB * (sx + NS * sy + NS * NS * sz);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v * NCELL + idx] = s[v * NCELL + off];
+      } else if (kd == 2) {
+#pragma unroll 1
+        for (int v = 0; v < NV; ++v) u[v * NCELL + idx] = predict_cell(P + v * NCELL, ch, i, j, k);
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll 1
+      for (int side = 0; side < 2; ++side) {
+        const int bc = p.bc[2 * d + side];
+        if (bc == 1) continue;
+        const int nl = p.nb[d] << level;
+        const int Xd = t.X[(size_t)node * 3 + d];
+        if (side == 0 && Xd != 0) continue;
+        if (side == 1 && Xd != nl - 1) continue;
+        for (int idx = threadIdx.x; idx < NCELL; idx += blockDim.x) {
+          int c[3] = {idx % NS - HW, (idx / NS) % NS - HW, idx / (NS * NS) - HW};
+          const int a = c[d];
+          const bool ghost = (side == 0) ? (a < 0) : (a >= NB);
+          if (!ghost) continue;
+          int sc[3] = {c[0], c[1], c[2]};
+          if (bc == 0) sc[d] = (side == 0) ? 0 : NB - 1;
+          else sc[d] = (side == 0) ? (-1 - a) : (2 * NB - 1 - a);
+          const int sidx_ = sidx(sc[0], sc[1], sc[2]);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            double val = u[v * NCELL + sidx_];
+            if (bc == 2 && v == 1 + d) val = -val;
+            u[v * NCELL + idx] = val;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st) {
+  k_fill_level<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, level);
+  ++g_kernel_launches;
+}
+
+// ---------------------------------------------------------------- RHS + RK (FP64)
+void launch_rhs_rk_f64(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
+                       double* rhs_out, cudaStream_t st) {
+  launch_rhs_rk_impl<double>(t, p, pool, cur, stage, dt, rhs_out, st);
+}
+
+// ---------------------------------------------------------------- face fluxes of internal nodes
+// parent face cell = mean of the 2 x 2 covering child face cells, levels fine to coarse
+__global__ void k_face_avg_level(Topo t, Pool pool, int level) {
+  const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
+  for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
+    const int node = t.lvl_nodes[w];
+    const int c0 = t.child0[node];
+    if (c0 < 0) continue;
+    double* F = pool.face + (size_t)t.slot[node] * SLOT_F;
+    for (int e = threadIdx.x; e < 6 * NFACE; e += blockDim.x) {
+      const int s = e / NFACE, aa = e % 16, bb = (e / 16) % 16;
+      const int d = s / 2, hi = s & 1;
+      const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+      const int ct1 = aa / 8, ct2 = bb / 8;
+      int cb[3];
+      cb[d] = hi;
+      cb[t1] = ct1;
+      cb[t2] = ct2;
+      const int ch = cb[0] | (cb[1] << 1) | (cb[2] << 2);
+      const double* C = pool.face + (size_t)t.slot[c0 + ch] * SLOT_F;
+      const int fa = 2 * (aa - 8 * ct1), fbb = 2 * (bb - 8 * ct2);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double* cf = C + (s * NV + v) * NFACE;
+        double f00 = cf[fbb * NB + fa], f10 = cf[fbb * NB + fa + 1];
+        double f01 = cf[(fbb + 1) * NB + fa], f11 = cf[(fbb + 1) * NB + fa + 1];
+        F[(s * NV + v) * NFACE + bb * NB + aa] = 0.25 * ((f00 + f10) + (f01 + f11));
+      }
+    }
+  }
+}
+
+void launch_face_avg_level(const Topo& t, const Pool& pool, int level, cudaStream_t st) {
+  k_face_avg_level<<<sm_count() * 4, 256, 0, st>>>(t, pool, level);
+  ++g_kernel_launches;
+}
+
+// ---------------------------------------------------------------- jump correction
+// A leaf face whose same-level neighbour is refined takes the averaged fine
+// flux: dL = (F_c - F_f)/dx on an upper face, (F_f - F_c)/dx on a lower one,
+// applied to the stage result as u += b_s (dt dL) (or added to L in the
+// inspection form), sides x-, x+, y-, y+, z-, z+ in order.
+__global__ void k_jump(Topo t, Phys p, Pool pool, int target, int stage, const double* __restrict__ dt,
+                       double* __restrict__ rhs_out) {
+  const int nleaves = t.cnt[CNT_NLEAVES];
+  for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
+    const int node = t.leaves[li];
+    const double* Fc_all = pool.face + (size_t)t.slot[node] * SLOT_F;
+    const double dx = ldexp(p.dx0, -t.level[node]);
+    const double h = dt ? dt[t.inst[node]] : 0.0;
+    const double bs = kRkB[stage];
+    double* U = pool.buf[target] + (size_t)t.slot[node] * SLOT_U;
+#pragma unroll 1
+    for (int s = 0; s < 6; ++s) {
+      const int d = s / 2, hi = s & 1;
+      int sv[3] = {0, 0, 0};
+      sv[d] = hi ? 1 : -1;
+      const int r = (sv[2] + 1) * 9 + (sv[1] + 1) * 3 + (sv[0] + 1);
+      const int nb = t.nbr[(size_t)node * 27 + r];
+      if (nb < 0 || t.child0[nb] < 0) continue;
+      const double* Ff_all = pool.face + (size_t)t.slot[nb] * SLOT_F;
+      const int so = s ^ 1;
+      const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+      for (int e = threadIdx.x; e < NFACE; e += blockDim.x) {
+        const int aa = e % 16, bb = e / 16;
+        int c[3];
+        c[d] = hi ? NB - 1 : 0;
+        c[t1] = aa;
+        c[t2] = bb;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const double Fc = Fc_all[(s * NV + v) * NFACE + e];
+          const double Ff = Ff_all[(so * NV + v) * NFACE + e];
+          const double dL = hi ? (Fc - Ff) / dx : (Ff - Fc) / dx;
+          if (rhs_out) {
+            double& Lr = rhs_out[((size_t)li * NV + v) * NINT + iidx(c[0], c[1], c[2])];
+            Lr = Lr + dL;
+          } else {
+            double& ur = U[v * NCELL + sidx(c[0], c[1], c[2])];
+            ur = ur + bs * (h * dL);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+void launch_jump(const Topo& t, const Phys& p, const Pool& pool, int target, int stage, const double* dt,
+                 double* rhs_out, cudaStream_t st) {
+  k_jump<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, target, stage, dt, rhs_out);
+  ++g_kernel_launches;
+}
+
+// ---------------------------------------------------------------- averaging
+__global__ void k_project_level(Topo t, Pool pool, int buf, int level) {
+  const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
+  double* B = pool.buf[buf];
+  for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
+    const int node = t.lvl_nodes[w];
+    const int c0 = t.child0[node];
+    if (c0 < 0) continue;
+    double* P = B + (size_t)t.slot[node] * SLOT_U;
+    for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
+      const int I = e % 16, J = (e / 16) % 16, K = e / 256;
+      const int o = (I / 8) | ((J / 8) << 1) | ((K / 8) << 2);
+      const double* C = B + (size_t)t.slot[c0 + o] * SLOT_U;
+      const int fi = 2 * (I - 8 * (I / 8)), fj = 2 * (J - 8 * (J / 8)), fk = 2 * (K - 8 * (K / 8));
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double* u = C + v * NCELL;
+        double c0v = u[sidx(fi, fj, fk)], c1v = u[sidx(fi + 1, fj, fk)];
+        double c2v = u[sidx(fi, fj + 1, fk)], c3v = u[sidx(fi + 1, fj + 1, fk)];
+        double c4v = u[sidx(fi, fj, fk + 1)], c5v = u[sidx(fi + 1, fj, fk + 1)];
+        double c6v = u[sidx(fi, fj + 1, fk + 1)], c7v = u[sidx(fi + 1, fj + 1, fk + 1)];
+        P[v * NCELL + sidx(I, J, K)] = 0.125 * (((c0v + c1v) + (c2v + c3v)) + ((c4v + c5v) + (c6v + c7v)));
+      }
+    }
+  }
+}
+
+void launch_project_level(const Topo& t, const Pool& pool, int buf, int level, cudaStream_t st) {
+  k_project_level<<<sm_count() * 4, 256, 0, st>>>(t, pool, buf, level);
+  ++g_kernel_launches;
+}
+
+// ---------------------------------------------------------------- CFL
+__device__ __forceinline__ void block_max3(double v[3], double* sh) {
+  // sh: [3][8] for 256 threads
+  for (int q = 0; q < 3; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int q = 0; q < 3; ++q) sh[q * 8 + wid] = v[q];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int q = 0; q < 3; ++q) {
+      double x = (lane < 8) ? sh[q * 8 + lane] : 0.0;
+      for (int o = 4; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+      v[q] = x;
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_cfl(Topo t, Phys p, Pool pool, int cur,
+                                             unsigned long long* __restrict__ smax, int* __restrict__ status) {
+  __shared__ double sh[24];
+  const int nleaves = t.cnt[CNT_NLEAVES];
+  for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
+    const int node = t.leaves[li];
+    const double* U = pool.buf[cur] + (size_t)t.slot[node] * SLOT_U;
+    double m[3] = {0.0, 0.0, 0.0};
+    bool bad = false;
+    for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
+      const int s = sidx(e % 16, (e / 16) % 16, e / 256);
+      double Uc[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Uc[v] = U[v * NCELL + s];
+      Prim<double> q = prim_of<double>(Uc, p.gamma, p.B);
+      if (!(q.rho > 0.0) || !(q.p + p.B > 0.0)) bad = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) m[d] = fmax(m[d], fabs(q.vel[d]) + q.c);
+    }
+    if (bad) atomicExch(status, (int)ST_NONPHYS);
+    block_max3(m, sh);
+    if (threadIdx.x == 0) {
+      const int inst = t.inst[node];
+      for (int d = 0; d < 3; ++d) atomicMax(&smax[inst * 3 + d], (unsigned long long)__double_as_longlong(m[d]));
+    }
+  }
+}
+
+__global__ void k_cfl_finish(Phys p, const unsigned long long* __restrict__ smax, double* __restrict__ dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.n_inst) return;
+  const double s0 = __longlong_as_double((long long)smax[i * 3]);
+  const double s1 = __longlong_as_double((long long)smax[i * 3 + 1]);
+  const double s2 = __longlong_as_double((long long)smax[i * 3 + 2]);
+  const double dxl = ldexp(p.dx0, -p.lmax[i]);
+  dt[i] = p.cfl * dxl / ((s0 + s1) + s2);
+}
+
+void launch_cfl(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax, double* dt,
+                int* status, cudaStream_t st) {
+  cudaMemsetAsync(smax, 0, sizeof(unsigned long long) * 3 * p.n_inst, st);
+  k_cfl<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, smax, status);
+  ++g_kernel_launches;
+  k_cfl_finish<<<(p.n_inst + 127) / 128, 128, 0, st>>>(p, smax, dt);
+  ++g_kernel_launches;
+}
+
+// ---------------------------------------------------------------- MR details and tags
+// delta of a leaf at level >= 1: max over its stored cells that are not ghost
+// cells and over rho, E of |u - P(u_parent)| / |u|; the eight fine cells of a
+// parent cell share one evaluation of the Q-terms.
+__global__ void __launch_bounds__(256) k_delta(Topo t, Phys p, Pool pool, int cur, double* __restrict__ delta_node) {
+  __shared__ double sh[8];
+  const int nleaves = t.cnt[CNT_NLEAVES];
+  const double* B = pool.buf[cur];
+  for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
+    const int node = t.leaves[li];
+    const int lvl = t.level[node];
+    if (lvl == 0) {
+      if (threadIdx.x == 0) delta_node[node] = 0.0;
+      continue;
+    }
+    const int par = t.parent[node];
+    const double* U = B + (size_t)t.slot[node] * SLOT_U;
+    const double* P = B + (size_t)t.slot[par] * SLOT_U;
+    const int ch = (int)(t.keys[node] & 7ull);
+    int cb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+    // ghost test per axis and side
+    bool gl[3], gh[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int nl = p.nb[d] << lvl;
+      const int Xd = t.X[(size_t)node * 3 + d];
+      gl[d] = (Xd == 0) && (p.bc[2 * d] != 1);
+      gh[d] = (Xd == nl - 1) && (p.bc[2 * d + 1] != 1);
+    }
+    double m = 0.0;
+    for (int e = threadIdx.x; e < 12 * 12 * 12; e += blockDim.x) {
+      const int pi = 8 * cb[0] - 2 + e % 12, pj = 8 * cb[1] - 2 + (e / 12) % 12, pk = 8 * cb[2] - 2 + e / 144;
+#pragma unroll 1
+      for (int vi = 0; vi < 2; ++vi) {
+        const int v = vi == 0 ? 0 : 4;
+        const QTerms q = qterms(P + v * NCELL, pi, pj, pk);
+#pragma unroll
+        for (int sub = 0; sub < 8; ++sub) {
+          const int a = sub & 1, b = (sub >> 1) & 1, c = (sub >> 2) & 1;
+          const int fi = 2 * (pi - 8 * cb[0]) + a, fj = 2 * (pj - 8 * cb[1]) + b, fk = 2 * (pk - 8 * cb[2]) + c;
+          const bool ghost = (fi < 0 && gl[0]) || (fi >= NB && gh[0]) || (fj < 0 && gl[1]) || (fj >= NB && gh[1]) ||
+                             (fk < 0 && gl[2]) || (fk >= NB && gh[2]);
+          if (ghost) continue;
+          const double pr = predict_from(q, a ? -1.0 : 1.0, b ? -1.0 : 1.0, c ? -1.0 : 1.0);
+          const double uf = U[v * NCELL + sidx(fi, fj, fk)];
+          const double r = fabs(uf - pr) / fabs(uf);
+          m = fmax(m, r);
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double x = sh[0];
+      for (int q = 1; q < (int)(blockDim.x >> 5); ++q) x = fmax(x, sh[q]);
+      delta_node[node] = x;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_tags(Topo t, Phys p, const double* __restrict__ delta_node, int allow_refine,
+                       int8_t* __restrict__ tags, double* __restrict__ delta_leaf) {
+  const int nleaves = t.cnt[CNT_NLEAVES];
+  for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < nleaves; li += gridDim.x * blockDim.x) {
+    const int node = t.leaves[li];
+    const int lvl = t.level[node];
+    const double dl = (lvl >= 1) ? delta_node[node] : 0.0;
+    int8_t tag = 0;
+    if (lvl >= 1) {
+      const int lmx = p.lmax[t.inst[node]];
+      const double el = ldexp(p.eps, -3 * (lmx - lvl));
+      if (allow_refine && dl > el && lvl < lmx) {
+        tag = 1;
+      } else if (lvl >= 2) {
+        const int c0 = t.child0[t.parent[node]];
+        bool all = true;
+        for (int c = 0; c < 8; ++c) {
+          const int sn = c0 + c;
+          if (t.child0[sn] >= 0 || !(delta_node[sn] < el)) {
+            all = false;
+            break;
+          }
+        }
+        if (all) tag = -1;
+      }
+    }
+    tags[li] = tag;
+    if (delta_leaf) delta_leaf[li] = dl;
+  }
+}
+
+void launch_delta_tags(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node,
+                       int allow_refine, int8_t* tags, double* delta_leaf, int n_leaves_cap, cudaStream_t st) {
+  k_delta<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, delta_node);
+  ++g_kernel_launches;
+  k_tags<<<(n_leaves_cap + 255) / 256, 256, 0, st>>>(t, p, delta_node, allow_refine, tags, delta_leaf);
+  ++g_kernel_launches;
+}
+
+// ---------------------------------------------------------------- refinement
+// New child: every stored cell predicted from the parent (Eq. Prediction).
+__global__ void __launch_bounds__(256) k_refine_fill(Topo t, Pool pool, int cur, const int32_t* __restrict__ pairs,
+                                                     int n) {
+  double* B = pool.buf[cur];
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const int child = pairs[2 * w], par = pairs[2 * w + 1];
+    double* U = B + (size_t)t.slot[child] * SLOT_U;
+    const double* P = B + (size_t)t.slot[par] * SLOT_U;
+    const int ch = (int)(t.keys[child] & 7ull);
+    const int cb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+    for (int e = threadIdx.x; e < 12 * 12 * 12 * NV; e += blockDim.x) {
+      const int v = e / 1728, r = e % 1728;
+      const int pi = 8 * cb[0] - 2 + r % 12, pj = 8 * cb[1] - 2 + (r / 12) % 12, pk = 8 * cb[2] - 2 + r / 144;
+      const QTerms q = qterms(P + v * NCELL, pi, pj, pk);
+#pragma unroll
+      for (int sub = 0; sub < 8; ++sub) {
+        const int a = sub & 1, b = (sub >> 1) & 1, c = (sub >> 2) & 1;
+        const int fi = 2 * (pi - 8 * cb[0]) + a, fj = 2 * (pj - 8 * cb[1]) + b, fk = 2 * (pk - 8 * cb[2]) + c;
+        U[v * NCELL + sidx(fi, fj, fk)] = predict_from(q, a ? -1.0 : 1.0, b ? -1.0 : 1.0, c ? -1.0 : 1.0);
+      }
+    }
+  }
+}
+
+void launch_refine_fill(const Topo& t, const Pool& pool, int cur, const int32_t* pairs, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_refine_fill<<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, pairs, n);
+  ++g_kernel_launches;
+}
+
+// ---------------------------------------------------------------- neighbour table
+// Same-level neighbour of every node in the 26 directions from block
+// coordinates: outside a non-periodic boundary -> -2; otherwise the id of the
+// (wrapped) neighbour position is looked up by binary search in the sorted ids
+// (-1 when no node of that level exists there).
+__device__ __forceinline__ uint64_t make_key_dev(int inst, int level, const int X[3]) {
+  const int ng = 7 + level;
+  uint64_t m = 0;
+  for (int b = 0; b < ng; ++b)
+    for (int d = 0; d < 3; ++d) m |= (uint64_t)((X[d] >> b) & 1) << (3 * b + d);
+  return ((uint64_t)inst << 56) | (1ull << (3 * ng)) | m;
+}
+
+__global__ void k_nbr(Topo t, Phys p, int32_t* __restrict__ nbr_out) {
+  const int nn = t.cnt[CNT_NNODES];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn * 27; e += gridDim.x * blockDim.x) {
+    const int node = e / 27, r = e % 27;
+    if (r == 13) {
+      nbr_out[e] = node;
+      continue;
+    }
+    const int s[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+    const int lvl = t.level[node];
+    int X[3];
+    bool outside = false;
+    for (int d = 0; d < 3; ++d) {
+      const int nl = p.nb[d] << lvl;
+      int x = t.X[(size_t)node * 3 + d] + s[d];
+      if (x < 0 || x >= nl) {
+        if (p.bc[2 * d] == 1) x = (x + nl) % nl;
+        else outside = true;
+      }
+      X[d] = x;
+    }
+    if (outside) {
+      nbr_out[e] = -2;
+      continue;
+    }
+    const uint64_t key = make_key_dev(t.inst[node], lvl, X);
+    int lo = 0, hi = nn - 1, found = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const uint64_t km = t.keys[mid];
+      if (km == key) { found = mid; break; }
+      if (km < key) lo = mid + 1;
+      else hi = mid - 1;
+    }
+    nbr_out[e] = found;
+  }
+}
+
+void launch_nbr(const Topo& t, const Phys& p, int32_t* nbr_out, int nnodes_cap, cudaStream_t st) {
+  const int n = nnodes_cap * 27;
+  k_nbr<<<(n + 255) / 256, 256, 0, st>>>(t, p, nbr_out);
+  ++g_kernel_launches;
+}
+
+// ---------------------------------------------------------------- conservation sums
+__global__ void __launch_bounds__(256) k_sums_partial(Topo t, Phys p, Pool pool, int cur, double* __restrict__ partial) {
+  __shared__ double sh[5][8];
+  const int nleaves = t.cnt[CNT_NLEAVES];
+  for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
+    const int node = t.leaves[li];
+    const double* U = pool.buf[cur] + (size_t)t.slot[node] * SLOT_U;
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
+      const int c = sidx(e % 16, (e / 16) % 16, e / 256);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s[v] += U[v * NCELL + c];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+      for (int o = 16; o > 0; o >>= 1) s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
+    if ((threadIdx.x & 31) == 0)
+      for (int v = 0; v < 5; ++v) sh[v][threadIdx.x >> 5] = s[v];
+    __syncthreads();
+    if (threadIdx.x < 5) {
+      double x = 0.0;
+      for (int q = 0; q < 8; ++q) x += sh[threadIdx.x][q];
+      const double dx = ldexp(p.dx0, -t.level[node]);
+      partial[(size_t)li * 5 + threadIdx.x] = x * (dx * dx * dx);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_sums_finish(Topo t, Phys p, const double* __restrict__ partial, double* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.n_inst * 5) return;
+  const int inst = e / 5, v = e % 5;
+  const int nleaves = t.cnt[CNT_NLEAVES];
+  double acc = 0.0;
+  for (int li = 0; li < nleaves; ++li)
+    if (t.inst[t.leaves[li]] == inst) acc += partial[(size_t)li * 5 + v];
+  out[e] = acc;
+}
+
+void launch_sums(const Topo& t, const Phys& p, const Pool& pool, int cur, double* partial, double* out,
+                 int nleaves_cap, cudaStream_t st) {
+  (void)nleaves_cap;
+  k_sums_partial<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, partial);
+  ++g_kernel_launches;
+  k_sums_finish<<<(p.n_inst * 5 + 127) / 128, 128, 0, st>>>(t, p, partial, out);
+  ++g_kernel_launches;
+}
+
+}  // namespace mrb

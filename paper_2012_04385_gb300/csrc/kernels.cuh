@@ -1,0 +1,81 @@
+// Kernels of the block-based MR Euler hot path (arXiv:2012.04385) and their
+// launch interface.  Work lists, node arrays and counts live in device memory,
+// so every kernel runs a grid-stride loop over a count it reads on the device;
+// the same launch stays valid when remeshing changes the tree (which is what
+// lets the stage sequence be replayed from a CUDA graph).
+#pragma once
+
+#include "physics.cuh"
+
+namespace mrb {
+
+constexpr int MAXL = 11;              // deepest level
+constexpr int CNT_NNODES = 0, CNT_NLEAVES = 1, CNT_LVL = 2;   // lvl offsets at CNT_LVL + l, l = 0..MAXL+1
+constexpr int CNT_SIZE = CNT_LVL + MAXL + 2;
+
+enum : int { ST_OK = 0, ST_NONPHYS = 6 };
+
+// Node arrays, in ascending id order (instance, level, Morton).
+struct Topo {
+  const uint64_t* keys;
+  const int32_t* slot;     // pool slot of the node
+  const int32_t* level;
+  const int32_t* inst;
+  const int32_t* X;        // [n][3] block coordinates on the node's level
+  const int32_t* parent;   // node index or -1
+  const int32_t* child0;   // first of 8 consecutive children, or -1 for a leaf
+  const int32_t* nbr;      // [n][27] same-level neighbour node, -1 none, -2 beyond the boundary
+  const int32_t* leaves;   // leaf node indices, ascending id
+  const int32_t* lvl_nodes;// node indices grouped by level
+  const int32_t* cnt;      // counts, see CNT_*
+};
+
+struct Phys {
+  double gamma, B, cfl, dx0, eps;
+  double grav[3];
+  int bc[6];
+  int nb[3];
+  int n_inst;
+  int recon;
+  int has_grav;
+  const int32_t* lmax;     // device [n_inst]
+};
+
+struct Pool {
+  double* buf[2];          // stage buffers, [slot][5][24^3]
+  double* un;              // u^n, [slot][5][16^3]
+  double* face;            // face fluxes, [slot][6][5][16][16]
+};
+
+__device__ __forceinline__ double ldexp_(double x, int e) { return ldexp(x, e); }
+
+// ---------------------------------------------------------------- launches
+// (defined in kern_f64.cu / kern_f32.cu; all asynchronous on `st`)
+void launch_set_state(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* nodes, int n,
+                      const double* prim, cudaStream_t st);
+void launch_set_cons(const Topo& t, const Pool& pool, int cur, const int32_t* nodes, int n, const double* cons,
+                     cudaStream_t st);
+void launch_get_state(const Topo& t, const Pool& pool, int cur, const int32_t* nodes, int n, double* out,
+                      int with_halo, cudaStream_t st);
+void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st);
+void launch_rhs_rk_f64(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
+                       double* rhs_out, cudaStream_t st);
+void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
+                       double* rhs_out, cudaStream_t st);
+void launch_face_avg_level(const Topo& t, const Pool& pool, int level, cudaStream_t st);
+void launch_jump(const Topo& t, const Phys& p, const Pool& pool, int target, int stage, const double* dt,
+                 double* rhs_out, cudaStream_t st);
+void launch_project_level(const Topo& t, const Pool& pool, int buf, int level, cudaStream_t st);
+void launch_cfl(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax, double* dt,
+                int* status, cudaStream_t st);
+void launch_delta_tags(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node,
+                       int allow_refine, int8_t* tags, double* delta_leaf, int n_leaves_cap, cudaStream_t st);
+void launch_refine_fill(const Topo& t, const Pool& pool, int cur, const int32_t* pairs, int n, cudaStream_t st);
+void launch_nbr(const Topo& t, const Phys& p, int32_t* nbr_out, int nnodes_cap, cudaStream_t st);
+void launch_sums(const Topo& t, const Phys& p, const Pool& pool, int cur, double* partial, double* out,
+                 int nleaves_cap, cudaStream_t st);
+int sm_count();
+// kernel launches issued by this process (host-side counter, bumped by every launch_* wrapper)
+extern long long g_kernel_launches;
+
+}  // namespace mrb

@@ -1,0 +1,304 @@
+// Device physics of the block-based MR Euler method (arXiv:2012.04385):
+// stiffened-gas EOS and Euler fluxes (Eq. Euler, Eq. StiffenedGas), the Roe
+// eigensystem, WENO5-JS / linear 5th-order reconstruction in characteristic
+// variables with the Roe / local Lax-Friedrichs switch per field (Sec. 2.2),
+// and the 5th-order conservative prediction of Eq. (Prediction) with the
+// appendix Q-terms.
+//
+// Every formula is written in one fixed evaluation order.  The FP64 kernels are
+// compiled without FMA contraction (-fmad=false), so each double result is the
+// correctly rounded value of that exact sequence of operations; the mixed
+// kernels instantiate the same templates with R = float and may contract.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mrb {
+
+constexpr int NB = 16;                 // internal cells per block edge
+constexpr int HW = 4;                  // halo width
+constexpr int NS = NB + 2 * HW;        // 24 stored cells per edge
+constexpr int NCELL = NS * NS * NS;    // 13824
+constexpr int NINT = NB * NB * NB;     // 4096
+constexpr int NV = 5;
+constexpr int NFACE = NB * NB;         // 256
+constexpr int SLOT_U = NV * NCELL;     // doubles per stage buffer
+constexpr int SLOT_N = NV * NINT;      // doubles per u^n buffer
+constexpr int SLOT_F = 6 * NV * NFACE; // doubles per face-flux set
+
+__host__ __device__ __forceinline__ int sidx(int i, int j, int k) { return ((k + HW) * NS + (j + HW)) * NS + (i + HW); }
+__host__ __device__ __forceinline__ int iidx(int i, int j, int k) { return (k * NB + j) * NB + i; }
+
+template <class R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return sqrtf(x); }
+template <class R> __device__ __forceinline__ R rabs(R x);
+template <> __device__ __forceinline__ double rabs<double>(double x) { return fabs(x); }
+template <> __device__ __forceinline__ float rabs<float>(float x) { return fabsf(x); }
+template <class R> __device__ __forceinline__ R rmax(R a, R b);
+template <> __device__ __forceinline__ double rmax<double>(double a, double b) { return fmax(a, b); }
+template <> __device__ __forceinline__ float rmax<float>(float a, float b) { return fmaxf(a, b); }
+
+// ---------------------------------------------------------------- EOS
+template <class R> struct Prim {
+  R rho, vel[3], p, c, E;
+};
+
+// p = (gamma - 1)(E - rho |v|^2 / 2) - gamma B,  c = sqrt(gamma (p + B) / rho)
+template <class R> __device__ __forceinline__ Prim<R> prim_of(const R U[5], R g, R B) {
+  Prim<R> q;
+  q.rho = U[0];
+  q.vel[0] = U[1] / q.rho;
+  q.vel[1] = U[2] / q.rho;
+  q.vel[2] = U[3] / q.rho;
+  R q2 = (q.vel[0] * q.vel[0] + q.vel[1] * q.vel[1]) + q.vel[2] * q.vel[2];
+  q.p = (g - R(1.0)) * (U[4] - R(0.5) * q.rho * q2) - g * B;
+  q.c = rsqrt_<R>(g * (q.p + B) / q.rho);
+  q.E = U[4];
+  return q;
+}
+
+__host__ __device__ __forceinline__ int rot_axis(int d, int j) { return (d + j) % 3; }
+
+// ---------------------------------------------------------------- WENO5-JS
+// Jiang & Shu (1996): value at the right face of the middle cell of
+// (a, b, c, d, e), epsilon = 1e-6, linear weights (0.1, 0.6, 0.3).
+template <class R> __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e) {
+  const R eps = R(1e-6);
+  R t1 = (a - R(2.0) * b) + c, t2 = (a - R(4.0) * b) + R(3.0) * c;
+  R beta0 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+  t1 = (b - R(2.0) * c) + d;
+  t2 = b - d;
+  R beta1 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+  t1 = (c - R(2.0) * d) + e;
+  t2 = (R(3.0) * c - R(4.0) * d) + e;
+  R beta2 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+  R a0 = R(0.1) / ((eps + beta0) * (eps + beta0));
+  R a1 = R(0.6) / ((eps + beta1) * (eps + beta1));
+  R a2 = R(0.3) / ((eps + beta2) * (eps + beta2));
+  R sum = (a0 + a1) + a2;
+  R q0 = ((R(2.0) * a - R(7.0) * b) + R(11.0) * c) / R(6.0);
+  R q1 = ((-b + R(5.0) * c) + R(2.0) * d) / R(6.0);
+  R q2 = ((R(2.0) * c + R(5.0) * d) - e) / R(6.0);
+  return ((a0 * q0 + a1 * q1) + a2 * q2) / sum;
+}
+
+template <class R> __device__ __forceinline__ R linear5(R a, R b, R c, R d, R e) {
+  R q0 = ((R(2.0) * a - R(7.0) * b) + R(11.0) * c) / R(6.0);
+  R q1 = ((-b + R(5.0) * c) + R(2.0) * d) / R(6.0);
+  R q2 = ((R(2.0) * c + R(5.0) * d) - e) / R(6.0);
+  return (R(0.1) * q0 + R(0.6) * q1) + R(0.3) * q2;
+}
+
+template <class R> __device__ __forceinline__ R recon5(bool lin, R a, R b, R c, R d, R e) {
+  return lin ? linear5<R>(a, b, c, d, e) : weno5<R>(a, b, c, d, e);
+}
+
+// ---------------------------------------------------------------- face flux
+// Numerical flux at the face between cells 2 and 3 of U6 (cells i-2 .. i+3
+// along d, lab-frame conserved states), returned in the lab frame.  Rotated
+// frame (rho, m_n, m_t1, m_t2, E) with cyclic tangential axes.  Roe averages
+// and the eigensystem of the face project the six cells to characteristic
+// variables v = L U and fluxes g = L F(U); per field k the flux is upwinded
+// when lam_k of both face cells and the Roe lam_k share a strict sign,
+// otherwise split with alpha = max(|lam_k(U_i)|, |lam_k(U_i+1)|); F = R g.
+template <class R>
+__device__ __forceinline__ void face_flux(const R U6[6][5], int d, R g, R B, bool lin, R Fout[5]) {
+  const int a0 = rot_axis(d, 0), a1 = rot_axis(d, 1), a2 = rot_axis(d, 2);
+  R Ur[6][5], Fr[6][5];
+  R unL, cL, unR, cR;
+  Prim<R> qL, qR;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    Prim<R> q = prim_of<R>(U6[m], g, B);
+    Ur[m][0] = U6[m][0];
+    Ur[m][1] = U6[m][1 + a0];
+    Ur[m][2] = U6[m][1 + a1];
+    Ur[m][3] = U6[m][1 + a2];
+    Ur[m][4] = U6[m][4];
+    R un = q.vel[a0], ut1 = q.vel[a1], ut2 = q.vel[a2];
+    Fr[m][0] = Ur[m][1];
+    Fr[m][1] = Ur[m][1] * un + q.p;
+    Fr[m][2] = Ur[m][1] * ut1;
+    Fr[m][3] = Ur[m][1] * ut2;
+    Fr[m][4] = un * (Ur[m][4] + q.p);
+    if (m == 2) qL = q;
+    if (m == 3) qR = q;
+  }
+  unL = qL.vel[d];
+  cL = qL.c;
+  unR = qR.vel[d];
+  cR = qR.c;
+  // Roe average
+  R sL = rsqrt_<R>(qL.rho), sR = rsqrt_<R>(qR.rho);
+  R den = sL + sR;
+  R un = (sL * qL.vel[a0] + sR * qR.vel[a0]) / den;
+  R ut1 = (sL * qL.vel[a1] + sR * qR.vel[a1]) / den;
+  R ut2 = (sL * qL.vel[a2] + sR * qR.vel[a2]) / den;
+  R HL = (qL.E + qL.p) / qL.rho, HR = (qR.E + qR.p) / qR.rho;
+  R H = (sL * HL + sR * HR) / den;
+  R q2 = (un * un + ut1 * ut1) + ut2 * ut2;
+  R c2 = (g - R(1.0)) * (H - R(0.5) * q2);
+  R c = rsqrt_<R>(c2);
+  R ic = R(1.0) / c;
+  R b1 = (g - R(1.0)) / c2;
+  R b2 = R(0.5) * b1 * q2;
+  R Fh[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    R l[5], r[5];
+    if (k == 0) {
+      l[0] = R(0.5) * (b2 + un * ic); l[1] = R(0.5) * (-b1 * un - ic); l[2] = R(0.5) * (-b1 * ut1);
+      l[3] = R(0.5) * (-b1 * ut2); l[4] = R(0.5) * b1;
+      r[0] = R(1.0); r[1] = un - c; r[2] = ut1; r[3] = ut2; r[4] = H - un * c;
+    } else if (k == 1) {
+      l[0] = R(1.0) - b2; l[1] = b1 * un; l[2] = b1 * ut1; l[3] = b1 * ut2; l[4] = -b1;
+      r[0] = R(1.0); r[1] = un; r[2] = ut1; r[3] = ut2; r[4] = R(0.5) * q2;
+    } else if (k == 2) {
+      l[0] = -ut1; l[1] = R(0.0); l[2] = R(1.0); l[3] = R(0.0); l[4] = R(0.0);
+      r[0] = R(0.0); r[1] = R(0.0); r[2] = R(1.0); r[3] = R(0.0); r[4] = ut1;
+    } else if (k == 3) {
+      l[0] = -ut2; l[1] = R(0.0); l[2] = R(0.0); l[3] = R(1.0); l[4] = R(0.0);
+      r[0] = R(0.0); r[1] = R(0.0); r[2] = R(0.0); r[3] = R(1.0); r[4] = ut2;
+    } else {
+      l[0] = R(0.5) * (b2 - un * ic); l[1] = R(0.5) * (-b1 * un + ic); l[2] = R(0.5) * (-b1 * ut1);
+      l[3] = R(0.5) * (-b1 * ut2); l[4] = R(0.5) * b1;
+      r[0] = R(1.0); r[1] = un + c; r[2] = ut1; r[3] = ut2; r[4] = H + un * c;
+    }
+    R v[6], G[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      R sv = l[0] * Ur[m][0];
+      R sg = l[0] * Fr[m][0];
+#pragma unroll
+      for (int j = 1; j < 5; ++j) {
+        sv = sv + l[j] * Ur[m][j];
+        sg = sg + l[j] * Fr[m][j];
+      }
+      v[m] = sv;
+      G[m] = sg;
+    }
+    R lL, lR, lt;
+    if (k == 0) { lL = unL - cL; lR = unR - cR; lt = un - c; }
+    else if (k == 4) { lL = unL + cL; lR = unR + cR; lt = un + c; }
+    else { lL = unL; lR = unR; lt = un; }
+    R gh;
+    if (lL > R(0.0) && lR > R(0.0) && lt > R(0.0)) {
+      gh = recon5<R>(lin, G[0], G[1], G[2], G[3], G[4]);
+    } else if (lL < R(0.0) && lR < R(0.0) && lt < R(0.0)) {
+      gh = recon5<R>(lin, G[5], G[4], G[3], G[2], G[1]);
+    } else {
+      R alpha = rmax<R>(rabs<R>(lL), rabs<R>(lR));
+      R fp[6], fm[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        fp[m] = R(0.5) * (G[m] + alpha * v[m]);
+        fm[m] = R(0.5) * (G[m] - alpha * v[m]);
+      }
+      gh = recon5<R>(lin, fp[0], fp[1], fp[2], fp[3], fp[4]) + recon5<R>(lin, fm[5], fm[4], fm[3], fm[2], fm[1]);
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) Fh[j] = (k == 0) ? r[j] * gh : Fh[j] + r[j] * gh;
+  }
+  Fout[0] = Fh[0];
+  Fout[1 + a0] = Fh[1];
+  Fout[1 + a1] = Fh[2];
+  Fout[1 + a2] = Fh[3];
+  Fout[4] = Fh[4];
+}
+
+// ---------------------------------------------------------------- prediction
+// Eq. (Prediction) with the appendix Q-terms: c0 = -22/128, c1 = 3/128,
+// c_pq = c_p c_q, c_rpq = c_r c_p c_q (index 0 for an offset of one parent
+// cell, 1 for two); Q_z read with u_{i,j,k+2}.  The child half below the
+// parent centre along an axis takes +Q, the upper half -Q.
+struct QTerms {
+  double u, Qx, Qy, Qz, Qxy, Qxz, Qyz, Qxyz;
+};
+
+__device__ __forceinline__ double qcoef(int off) { return off == 1 ? (-22.0 / 128.0) : (3.0 / 128.0); }
+
+// P points at a parent's stored array of one variable; (i, j, k) the parent cell
+__device__ __forceinline__ double pat(const double* P, int i, int j, int k) { return P[sidx(i, j, k)]; }
+
+__device__ __forceinline__ double mix2(const double* P, int i, int j, int k, int A, int Bx, int p, int q) {
+  int o1[3] = {0, 0, 0}, o2[3] = {0, 0, 0}, o3[3] = {0, 0, 0}, o4[3] = {0, 0, 0};
+  o1[A] = p; o1[Bx] = q;      // (+p, +q)
+  o2[A] = -p; o2[Bx] = -q;    // (-p, -q)
+  o3[A] = -p; o3[Bx] = q;     // (-p, +q)
+  o4[A] = p; o4[Bx] = -q;     // (+p, -q)
+  return (pat(P, i + o1[0], j + o1[1], k + o1[2]) + pat(P, i + o2[0], j + o2[1], k + o2[2])) -
+         (pat(P, i + o3[0], j + o3[1], k + o3[2]) + pat(P, i + o4[0], j + o4[1], k + o4[2]));
+}
+
+__device__ __forceinline__ double mix3(const double* P, int i, int j, int k, int p, int q, int r) {
+  const int sg[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, -1, 1}, {-1, 1, -1}};
+  double acc = 0.0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    double term = pat(P, i + sg[t][0] * p, j + sg[t][1] * q, k + sg[t][2] * r) -
+                  pat(P, i - sg[t][0] * p, j - sg[t][1] * q, k - sg[t][2] * r);
+    acc = (t == 0) ? term : acc + term;
+  }
+  return acc;
+}
+
+__device__ __forceinline__ QTerms qterms(const double* P, int i, int j, int k) {
+  const double C0 = -22.0 / 128.0, C1 = 3.0 / 128.0;
+  QTerms t;
+  t.u = pat(P, i, j, k);
+  t.Qx = C0 * (pat(P, i + 1, j, k) - pat(P, i - 1, j, k)) + C1 * (pat(P, i + 2, j, k) - pat(P, i - 2, j, k));
+  t.Qy = C0 * (pat(P, i, j + 1, k) - pat(P, i, j - 1, k)) + C1 * (pat(P, i, j + 2, k) - pat(P, i, j - 2, k));
+  t.Qz = C0 * (pat(P, i, j, k + 1) - pat(P, i, j, k - 1)) + C1 * (pat(P, i, j, k + 2) - pat(P, i, j, k - 2));
+  const int pq[4][2] = {{1, 1}, {2, 2}, {1, 2}, {2, 1}};
+  double qxy = 0.0, qxz = 0.0, qyz = 0.0;
+#pragma unroll
+  for (int t2 = 0; t2 < 4; ++t2) {
+    int p = pq[t2][0], q = pq[t2][1];
+    double cc = qcoef(p) * qcoef(q);
+    double a = cc * mix2(P, i, j, k, 0, 1, p, q);
+    double b = cc * mix2(P, i, j, k, 0, 2, p, q);
+    double c = cc * mix2(P, i, j, k, 1, 2, p, q);
+    qxy = (t2 == 0) ? a : qxy + a;
+    qxz = (t2 == 0) ? b : qxz + b;
+    qyz = (t2 == 0) ? c : qyz + c;
+  }
+  t.Qxy = qxy;
+  t.Qxz = qxz;
+  t.Qyz = qyz;
+  const int pqr[8][3] = {{1, 1, 1}, {2, 2, 2}, {1, 1, 2}, {2, 2, 1}, {1, 2, 2}, {2, 1, 1}, {1, 2, 1}, {2, 1, 2}};
+  double qxyz = 0.0;
+#pragma unroll
+  for (int t3 = 0; t3 < 8; ++t3) {
+    int p = pqr[t3][0], q = pqr[t3][1], r = pqr[t3][2];
+    double cc = qcoef(p) * qcoef(q) * qcoef(r);
+    double a = cc * mix3(P, i, j, k, p, q, r);
+    qxyz = (t3 == 0) ? a : qxyz + a;
+  }
+  t.Qxyz = qxyz;
+  return t;
+}
+
+__device__ __forceinline__ double predict_from(const QTerms& t, double sx, double sy, double sz) {
+  return t.u + sx * t.Qx + sy * t.Qy + sz * t.Qz + (sx * sy) * t.Qxy + (sx * sz) * t.Qxz + (sy * sz) * t.Qyz +
+         (sx * sy * sz) * t.Qxyz;
+}
+
+__device__ __forceinline__ int floordiv2(int i) { return (i >= 0) ? (i >> 1) : -((-i + 1) >> 1); }
+
+// fine stored cell (i, j, k) of child `ch` predicted from its parent's array P
+__device__ __forceinline__ double predict_cell(const double* P, int ch, int i, int j, int k) {
+  int f[3] = {i, j, k}, p[3];
+  double s[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int h = floordiv2(f[d]);
+    p[d] = 8 * ((ch >> d) & 1) + h;
+    s[d] = (f[d] - 2 * h == 0) ? 1.0 : -1.0;
+  }
+  QTerms t = qterms(P, p[0], p[1], p[2]);
+  return predict_from(t, s[0], s[1], s[2]);
+}
+
+}  // namespace mrb

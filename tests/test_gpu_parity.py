@@ -1,0 +1,298 @@
+"""GPU parity: every C-ABI call against the CPU oracle on the same seeded inputs.
+
+FP64 kernels follow the oracle's operation order without FMA contraction, so
+integer work (tags, tree, neighbour ids) must match bit for bit and floating
+point per cell within 1e-11 relative (|a - b| <= 1e-11 max(|b|, s_v), s_v the
+largest magnitude of variable v); the tests also report how many cells are
+not bit-identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2012_04385_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2012_04385_gb300 import mrb  # noqa: E402
+
+REL = 1e-11
+
+
+def close(gpu, ref, rel=REL, what=""):
+    gpu = np.asarray(gpu)
+    ref = np.asarray(ref)
+    assert gpu.shape == ref.shape, (gpu.shape, ref.shape)
+    if ref.ndim >= 2 and ref.shape[1] == 5:
+        scale = np.abs(ref).max(axis=tuple(i for i in range(ref.ndim) if i != 1), keepdims=True)
+    else:
+        scale = np.abs(ref).max()
+    assert np.isfinite(ref).all(), f"{what}: reference has non-finite values"
+    assert np.isfinite(gpu).all(), f"{what}: GPU result has non-finite values"
+    tol = rel * np.maximum(np.abs(ref), scale)
+    bad = np.abs(gpu - ref) > tol
+    nexact = np.count_nonzero(gpu != ref)
+    print(f"{what}: {ref.size} values, {nexact} not bit-identical, max abs diff {np.abs(gpu - ref).max():.3e}")
+    assert not bad.any(), f"{what}: {np.count_nonzero(bad)} values beyond tolerance"
+    return nexact
+
+
+def make_pair(cfg, ic, plans=(), n_slots=None):
+    """Oracle and GPU context with the same tree: level-0 state, then for each
+    plan (geo -> bool mask of leaves to refine) a halo fill, remesh and the
+    initial condition on the new leaves."""
+    o = oracle.Oracle(cfg)
+    if n_slots is None:
+        n_slots = int(np.prod(cfg.base_blocks)) * cfg.n_instances * 80
+    g = mrb.Context(cfg, n_slots)
+    ko, go = o.keys(), o.geometry()
+    kg, gg = g.list_blocks()
+    assert np.array_equal(ko, kg) and np.array_equal(go, gg)
+    o.set_state(ko, ic(cfg, go, ko))
+    g.set_state(kg, ic(cfg, gg, kg))
+    for plan in plans:
+        o.fill_halos()
+        g.fill_halos()
+        mask = plan(o.geometry()).astype(np.int8)
+        o.remesh(mask)
+        g.remesh(mask)
+        ko, go = o.keys(), o.geometry()
+        kg, gg = g.list_blocks()
+        assert np.array_equal(ko, kg) and np.array_equal(go, gg)
+        o.set_state(ko, ic(cfg, go, ko))
+        g.set_state(kg, ic(cfg, gg, kg))
+    o.project()
+    g.mr_project()
+    return o, g
+
+
+def rnd(seed, mild=False):
+    """Independent random states per cell; `mild` keeps them close enough that
+    predicted halo values stay physical (rho, p > 0) across resolution jumps."""
+    def ic(cfg, geo, keys):
+        if mild:
+            return I.random_states(len(geo), seed=seed, rho=(1.0, 1.5), p=(1.0, 1.5), vmax=0.3)
+        return I.random_states(len(geo), seed=seed)
+    return ic
+
+
+def wrap(f, **kw):
+    return lambda cfg, geo, keys: f(cfg, geo, **kw)
+
+
+ALL = lambda geo: np.ones(len(geo), bool)           # noqa: E731
+SOME = lambda geo: (geo[:, 1] % 3 == 1) & (geo[:, 2] <= 1)   # noqa: E731
+
+
+def both_nodes(o, g):
+    k = o.keys(leaves_only=False)
+    assert np.array_equal(k, g.keys(leaves_only=False))
+    return k
+
+
+# ------------------------------------------------------------------ state and topology
+def test_state_roundtrip_and_topology():
+    cfg = I.explosion_config(lmax=3)
+    o, g = make_pair(cfg, rnd(1), (ALL, SOME, lambda geo: (geo[:, 0] == 2) & (geo[:, 1] % 2 == 0)))
+    k = both_nodes(o, g)
+    assert len(set(o.geometry()[:, 0])) == 3
+    got = g.get_state(o.keys()).cpu().numpy()
+    assert np.array_equal(got, o.get_state())
+    nb = g.neighbors(k)
+    for b, key in enumerate(k):
+        for r in range(27):
+            if r == 13:
+                continue
+            s = (r % 3 - 1, (r // 3) % 3 - 1, r // 9 - 1)
+            exp = o.neighbor(int(key), *s)
+            if exp is None:
+                assert nb[b, r] == 1
+            elif exp in set(int(x) for x in k):
+                assert int(nb[b, r]) == exp
+            else:
+                assert nb[b, r] == 0
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_fill_halos_bit_exact(periodic):
+    bc = (I.BC_PERIODIC,) * 6 if periodic else (I.BC_ZERO_GRADIENT, I.BC_SYMMETRY, I.BC_PERIODIC, I.BC_PERIODIC,
+                                                I.BC_SYMMETRY, I.BC_ZERO_GRADIENT)
+    cfg = I.explosion_config(lmax=3, bc=bc)
+    o, g = make_pair(cfg, rnd(2), (ALL, SOME, lambda geo: (geo[:, 0] == 2) & (geo[:, 1] % 2 == 0)))
+    o.fill_halos()
+    g.fill_halos()
+    k = both_nodes(o, g)
+    ref = o.get_state(k, with_halo=True)
+    got = g.get_state(k, with_halo=True).cpu().numpy()
+    assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
+
+
+def test_project_bit_exact():
+    cfg = I.explosion_config(lmax=2)
+    o, g = make_pair(cfg, rnd(3), (ALL, SOME))
+    k = both_nodes(o, g)
+    assert np.array_equal(g.get_state(k).cpu().numpy(), o.get_state(k))
+
+
+# ------------------------------------------------------------------ RHS, stages, CFL
+@pytest.mark.parametrize("recon", [I.RECON_WENO, I.RECON_LINEAR])
+def test_compute_rhs_random_states_with_jumps(recon):
+    cfg = I.explosion_config(lmax=3, recon=recon)
+    o, g = make_pair(cfg, rnd(4, mild=True), (ALL, SOME, lambda geo: (geo[:, 0] == 2) & (geo[:, 1] % 2 == 0)))
+    o.fill_halos()
+    g.fill_halos()
+    ref = o.compute_rhs()
+    got = g.compute_rhs().cpu().numpy()
+    close(got, ref, what="rhs")
+
+
+def test_compute_rhs_gravity_and_stiffened_gas():
+    cfg = I.rt_config(lmax=1, base_blocks=(1, 1, 2), B=0.3, gamma=4.4)
+    o, g = make_pair(cfg, rnd(5, mild=True), (SOME,))
+    o.fill_halos()
+    g.fill_halos()
+    close(g.compute_rhs().cpu().numpy(), o.compute_rhs(), what="rhs gravity")
+
+
+def test_cfl_bit_exact():
+    cfg = I.ensemble_config(n=3)
+    o, g = make_pair(cfg, rnd(6), (ALL,))
+    dt_o = o.cfl_dt()
+    dt_g = g.cfl_dt().cpu().numpy()
+    assert np.array_equal(dt_o, dt_g)
+
+
+def test_rk_stages_with_jumps():
+    cfg = I.explosion_config(lmax=2)
+    o, g = make_pair(cfg, wrap(I.ic_random_smooth), (ALL, SOME))
+    dt = o.cfl_dt()
+    dtg = torch.tensor(dt, device="cuda")
+    for s in range(3):
+        o.fill_halos()
+        g.fill_halos()
+        o.rk_stage(s, dt)
+        g.rk_stage(s, dtg)
+        o.project()
+        g.mr_project()
+    k = both_nodes(o, g)
+    close(g.get_state(k).cpu().numpy(), o.get_state(k), what="3 stages")
+
+
+def test_sod_20_steps_fp64():
+    """Plain single-level Sod: 2x2x2 blocks of 16^3, FP64, 20 steps."""
+    cfg = I.sod_config()
+    o, g = make_pair(cfg, wrap(I.ic_sod))
+    dts_o = o.step(20)
+    dts_g = torch.empty((20, 1), dtype=torch.float64, device="cuda")
+    g.step(20, dts_g)
+    assert np.array_equal(dts_g.cpu().numpy(), dts_o)
+    k = o.keys()
+    got = g.get_state(k).cpu().numpy()
+    ref = o.get_state(k)
+    close(got, ref, what="sod 20 steps")
+    assert np.count_nonzero(got[:, 2]) == 0 and np.count_nonzero(got[:, 3]) == 0
+
+
+# ------------------------------------------------------------------ MR analysis and remesh
+def test_tags_and_deltas_bit_exact():
+    cfg = I.explosion_config(lmax=3)
+    o, g = make_pair(cfg, wrap(I.ic_explosion, r0=0.2), (ALL, lambda geo: (geo[:, 1] <= 1) & (geo[:, 2] <= 1)),
+                     n_slots=4680)
+    o.fill_halos()
+    g.fill_halos()
+    to, do = o.predict_and_tag()
+    tg, dg = g.mr_predict_and_tag()
+    assert np.array_equal(tg.cpu().numpy(), to)
+    assert np.array_equal(dg.cpu().numpy(), do)
+    assert (to == oracle.TAG_REFINE).any() and (to == oracle.TAG_COARSEN).any()
+    o.remesh(to)
+    g.remesh(tg)
+    k = both_nodes(o, g)
+    o.fill_halos()
+    g.fill_halos()
+    assert np.array_equal(g.get_state(k, with_halo=True).cpu().numpy(), o.get_state(k, with_halo=True))
+
+
+def test_explosion_mr_steps():
+    """Spherical explosion with MR (levels 0..2): 4 full steps with remeshing."""
+    cfg = I.explosion_config(lmax=2)
+    o = oracle.Oracle(cfg)
+    g = mrb.Context(cfg, 8 * 80)
+    # Alg. (Initialization) on both sides
+    mrb.init_tree(g, lambda c, geo: I.ic_explosion(c, geo))
+    o.set_state(o.keys(), I.ic_explosion(cfg, o.geometry()))
+    for m in range(1, 3):
+        o.fill_halos()
+        geo = o.geometry()
+        o.remesh((geo[:, 0] == m - 1).astype(np.int8))
+        o.set_state(o.keys(level=m), I.ic_explosion(cfg, o.geometry(level=m)))
+        if m > 1:
+            o.fill_halos()
+            t, _ = o.predict_and_tag(allow_refine=False)
+            o.remesh(t)
+    o.project()
+    assert np.array_equal(o.keys(leaves_only=False), g.keys(leaves_only=False))
+    dts_o = o.step(4)
+    dts_g = torch.empty((4, 1), dtype=torch.float64, device="cuda")
+    g.step(4, dts_g)
+    assert np.array_equal(o.keys(leaves_only=False), g.keys(leaves_only=False))
+    k = o.keys()
+    close(g.get_state(k).cpu().numpy(), o.get_state(k), what="explosion MR 4 steps")
+    close(dts_g.cpu().numpy(), dts_o, what="dt")
+
+
+def test_conservation_sums():
+    cfg = I.periodic_config(base=(2, 2, 2), lmax=1)
+    o, g = make_pair(cfg, wrap(I.ic_random_smooth), (SOME,))
+    s0 = g.sums().cpu().numpy()
+    close(s0, o.sums(), rel=1e-13, what="sums")
+    g.step(3)
+    s1 = g.sums().cpu().numpy()
+    scale = np.abs(s0).max(axis=1, keepdims=True)
+    assert (np.abs(s1 - s0) <= 1e-13 * np.maximum(np.abs(s0), scale)).all()
+
+
+# ------------------------------------------------------------------ errors and edge cases
+def test_errors_and_edge_cases():
+    cfg = I.sod_config(lmax=(1,))
+    g = mrb.Context(cfg, 8)
+    with pytest.raises(mrb.MrbError) as e:
+        g.set_state(np.array([12345], np.uint64), np.zeros((1, 5, 16, 16, 16)))
+    assert e.value.code == mrb.MRB_EINVAL
+    g.set_state(np.zeros(0, np.uint64), np.zeros((0, 5, 16, 16, 16)))   # empty list is fine
+    k, geo = g.list_blocks()
+    g.set_state(k, I.ic_sod(cfg, geo))
+    g.fill_halos()
+    with pytest.raises(mrb.MrbError) as e:                 # pool holds exactly the 8 level-0 blocks
+        g.remesh(np.ones(8, np.int8))
+    assert e.value.code == mrb.MRB_ECAPACITY
+    assert g.n_leaves() == 8                                 # tree unchanged
+    # non-physical state is reported through the sticky status
+    bad = I.ic_sod(cfg, geo)
+    bad[0, 4, 3, 3, 3] = -1.0
+    g.set_state(k, bad)
+    g.cfl_dt()
+    assert g.status() == mrb.MRB_ENONPHYS
+    with pytest.raises(mrb.MrbError):
+        mrb.Context(cfg, 4)                                  # smaller than the level-0 blocks
+
+
+def test_fp32_bulk_path_error_vs_oracle():
+    """Mixed precision: FP32 reconstruction and fluxes, FP64 state and update."""
+    cfg = I.sod_config(precision=I.FP32_ACC64)
+    o = oracle.Oracle(I.sod_config())
+    g = mrb.Context(cfg, 8)
+    k, geo = g.list_blocks()
+    o.set_state(k, I.ic_sod(cfg, geo))
+    g.set_state(k, I.ic_sod(cfg, geo))
+    o.step(20)
+    g.step(20)
+    got = g.get_state(k).cpu().numpy()
+    ref = o.get_state(k)
+    l1 = np.abs(got[:, 0] - ref[:, 0]).sum() / np.abs(ref[:, 0]).sum()
+    print("fp32 bulk L1 density error vs FP64 oracle:", l1)
+    assert l1 < 1e-5
