@@ -212,6 +212,30 @@ int mrb_neighbors(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, uint64_t* 
 int mrb_profile(mrb_ctx* ctx, int32_t enable);
 int mrb_profile_read(mrb_ctx* ctx, double* stage_kernel_ms, int64_t* stage_kernel_launches, int64_t* kernel_launches);
 
+/* Conservation sums for callers that cannot allocate device memory.  (The
+ * paper has no counterpart: this is a deployment variant of mrb_sums.)  Some
+ * callers cannot call cudaMalloc at all -- code running under an allocator
+ * that owns all device memory, or host code that must not take the driver's
+ * allocation lock while other work is in flight -- so this call allocates
+ * nothing: its reduction scratch is a fixed file-scope device array of
+ * MRB_NOALLOC_MAX_BLOCKS x 5 doubles (2.5 MiB), held by every GPU that loads
+ * the library until the process exits.
+ *   blocks_dev  device, [n_blocks][5][16^3] conserved internal cells (the
+ *               layout of mrb_get_state with with_halo = 0)
+ *   levels_dev  device, [n_blocks] int32 level of each block (nullable: all 0)
+ *   dx0         level-0 cell size; block b is weighted by (dx0 2^-level)^3
+ *   stream      cudaStream_t (NULL = legacy default stream); asynchronous
+ *   sums_dev    device, [5] output: sum over blocks of U dx^3, blocks in the
+ *               given order, the same fixed reduction order as mrb_sums
+ * Returns EINVAL for bad arguments, ECAPACITY for n_blocks >
+ * MRB_NOALLOC_MAX_BLOCKS (nothing is launched), ECUDA on a CUDA error.  The
+ * first call on a device looks up the scratch address with that device
+ * current; make it before any stream capture.  All calls share the scratch,
+ * which keeps the last call's contents: calls that overlap on the GPU race. */
+#define MRB_NOALLOC_MAX_BLOCKS 65536
+int mrb_block_sums_noalloc(const double* blocks_dev, int64_t n_blocks, const int32_t* levels_dev, double dx0,
+                           void* stream, double* sums_dev);
+
 int mrb_status(mrb_ctx* ctx);   /* sticky device status (synchronises)       */
 int mrb_sync(mrb_ctx* ctx);     /* synchronise the stream, return status     */
 int mrb_destroy(mrb_ctx* ctx);  /* free internal arrays (not the pool)       */

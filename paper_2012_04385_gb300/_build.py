@@ -25,6 +25,7 @@ UNITS = {
     "ctx.cu": [],
     "kern_f64.cu": ["-fmad=false"],
     "kern_f32.cu": ["-fmad=true"],
+    "noalloc.cu": ["-fmad=false"],
 }
 
 

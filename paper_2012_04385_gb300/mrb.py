@@ -88,6 +88,7 @@ def lib():
                 "mrb_neighbors": (ci, [vp, vp, i64, vp]),
                 "mrb_profile": (ci, [vp, i32]),
                 "mrb_profile_read": (ci, [vp, vp, vp, vp]),
+                "mrb_block_sums_noalloc": (ci, [vp, i64, vp, ctypes.c_double, vp, vp]),
                 "mrb_status": (ci, [vp]),
                 "mrb_sync": (ci, [vp]),
                 "mrb_destroy": (ci, [vp]),
