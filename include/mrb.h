@@ -236,6 +236,14 @@ int mrb_profile_read(mrb_ctx* ctx, double* stage_kernel_ms, int64_t* stage_kerne
 int mrb_block_sums_noalloc(const double* blocks_dev, int64_t n_blocks, const int32_t* levels_dev, double dx0,
                            void* stream, double* sums_dev);
 
+/* Throughput microbenchmarks of the current GPU (dependent-chain loops on
+ * every SM): out[0] FP32 FMA TFLOP/s, out[1] FP64 FMA TFLOP/s, out[2]
+ * double->float and out[3] float->double conversions (10^12 per s), out[4]
+ * reciprocal square roots (10^12 per s), out[5] SM count, out[6] SM clock
+ * (MHz) the device reports.  n >= 7.  Synchronises the device; allocates 64
+ * bytes of scratch. */
+int mrb_measure_peaks(double* out, int32_t n);
+
 int mrb_status(mrb_ctx* ctx);   /* sticky device status (synchronises)       */
 int mrb_sync(mrb_ctx* ctx);     /* synchronise the stream, return status     */
 int mrb_destroy(mrb_ctx* ctx);  /* free internal arrays (not the pool)       */

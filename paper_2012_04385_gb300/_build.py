@@ -24,8 +24,9 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 UNITS = {
     "ctx.cu": [],
     "kern_f64.cu": ["-fmad=false"],
-    "kern_f32.cu": ["-fmad=true"],
+    "kern_f32.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "noalloc.cu": ["-fmad=false"],
+    "peaks.cu": ["-fmad=true"],
 }
 
 

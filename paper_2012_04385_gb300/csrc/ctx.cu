@@ -453,6 +453,7 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     for (int s = 0; s < 6; ++s) p.bc[s] = cfg->bc[s];
     p.n_inst = cfg->n_instances;
     p.recon = cfg->recon;
+    p.precision = cfg->precision;
     c->max_lmax = 0;
     for (int i = 0; i < cfg->n_instances; ++i) c->max_lmax = std::max(c->max_lmax, (int)cfg->lmax[i]);
     c->d_keys = c->dalloc<uint64_t>(n);

@@ -1,13 +1,92 @@
-// Mixed-precision stage kernel (MRB_FP32_ACC64): reconstruction and fluxes in
-// FP32 from the FP64 state; flux differences, the right-hand side and the
-// TVD-RK3 update in FP64.  Built with FMA contraction enabled.
-#include "rhs.cuh"
+// Mixed-precision stage kernel (MRB_FP32_ACC64): reconstruction, fluxes and
+// flux differences in FP32 from the FP64 state; the TVD-RK3 update of the FP64
+// state in FP64.  Built with FMA contraction and the fast FP32 reciprocal and
+// square-root approximations.
+#include "mr.cuh"
+#include "stage_f32.cuh"
 
 namespace mrb {
 
+template <bool LIN>
+static void launch_stage_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
+                             double* rhs_out, cudaStream_t st) {
+  static int grid = 0;
+  if (grid == 0) {
+    cudaFuncSetAttribute(k_stage_f32<LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SF_SMEM);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_f32<LIN>, SF_THREADS, SF_SMEM);
+    grid = sm_count() * (per_sm < 1 ? 1 : per_sm);
+  }
+  k_stage_f32<LIN><<<grid, SF_THREADS, SF_SMEM, st>>>(t, p, pool, cur, stage, dt, rhs_out);
+  ++g_kernel_launches;
+}
+
 void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
                        double* rhs_out, cudaStream_t st) {
-  launch_rhs_rk_impl<float>(t, p, pool, cur, stage, dt, rhs_out, st);
+  if (p.recon == 2) launch_stage_f32<true>(t, p, pool, cur, stage, dt, rhs_out, st);
+  else launch_stage_f32<false>(t, p, pool, cur, stage, dt, rhs_out, st);
+}
+
+void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st) {
+  k_fill_level_t<float><<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, level);
+  ++g_kernel_launches;
+}
+
+void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, cudaStream_t st) {
+  k_delta_t<float><<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, delta_node);
+  ++g_kernel_launches;
+}
+
+// Per-instance maxima of |u_d| + c over the leaves' internal cells: speeds in
+// FP32, maxima (exact) and the time step of Eq. (Cfl) in FP64.
+__global__ void __launch_bounds__(256) k_cfl_f32(Topo t, Phys p, Pool pool, int cur,
+                                                 unsigned long long* __restrict__ smax, int* __restrict__ status) {
+  __shared__ float sh[3][8];
+  const int nleaves = t.cnt[CNT_NLEAVES];
+  const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
+  for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
+    const int node = t.leaves[li];
+    const double* U = pool.buf[cur] + (size_t)t.slot[node] * SLOT_U;
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+    bool bad = false;
+    for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
+      const int s = sidx(e % 16, (e / 16) % 16, e / 256);
+      const float r = d2f_fast(U[s]), ir = frcp(r);
+      const float vx = d2f_fast(U[NCELL + s]) * ir, vy = d2f_fast(U[2 * NCELL + s]) * ir;
+      const float vz = d2f_fast(U[3 * NCELL + s]) * ir;
+      const float q2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+      const float pr = fmaf(gm1, fmaf(-0.5f * r, q2, d2f_fast(U[4 * NCELL + s])), -g * B);
+      if (!(r > 0.f) || !(pr + B > 0.f)) bad = true;
+      const float c = sqrtf(g * (pr + B) * ir);
+      m0 = fmaxf(m0, fabsf(vx) + c);
+      m1 = fmaxf(m1, fabsf(vy) + c);
+      m2 = fmaxf(m2, fabsf(vz) + c);
+    }
+    if (bad) atomicExch(status, (int)ST_NONPHYS);
+    for (int o = 16; o > 0; o >>= 1) {
+      m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+      m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+      m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sh[0][threadIdx.x >> 5] = m0;
+      sh[1][threadIdx.x >> 5] = m1;
+      sh[2][threadIdx.x >> 5] = m2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      float x = sh[threadIdx.x][0];
+      for (int q = 1; q < 8; ++q) x = fmaxf(x, sh[threadIdx.x][q]);
+      atomicMax(&smax[t.inst[node] * 3 + threadIdx.x], (unsigned long long)__double_as_longlong(f2d_fast(x)));
+    }
+    __syncthreads();
+  }
+}
+
+void launch_cfl_speeds_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax,
+                           int* status, cudaStream_t st) {
+  k_cfl_f32<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, smax, status);
+  ++g_kernel_launches;
 }
 
 }  // namespace mrb

@@ -5,6 +5,7 @@
 //
 // Built with -fmad=false: every double is the correctly rounded result of the
 // operation order written here.
+#include "mr.cuh"
 #include "rhs.cuh"
 
 namespace mrb {
@@ -20,13 +21,6 @@ int sm_count() {
     if (n <= 0) n = 1;
   }
   return n;
-}
-
-__device__ __forceinline__ int region_of(int i, int j, int k) {
-  int sx = i < 0 ? -1 : (i >= NB ? 1 : 0);
-  int sy = j < 0 ? -1 : (j >= NB ? 1 : 0);
-  int sz = k < 0 ? -1 : (k >= NB ? 1 : 0);
-  return (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
 }
 
 // ---------------------------------------------------------------- state in/out
@@ -99,81 +93,13 @@ void launch_get_state(const Topo& t, const Pool& pool, int cur, const int32_t* n
   ++g_kernel_launches;
 }
 
-// ---------------------------------------------------------------- halo fill
-// One CTA per node of `level`: every halo cell is copied from the same-level
-// neighbour of its region, or predicted from the node's parent, or left for
-// the boundary passes (x-, x+, y-, y+, z-, z+ in that order), which copy from
-// the block's own cells: zero gradient clamps, symmetry mirrors and negates
-// the normal momentum.
-__global__ void __launch_bounds__(256) k_fill_level(Topo t, Phys p, Pool pool, int cur, int level) {
-  const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
-  double* buf = pool.buf[cur];
-  __shared__ int kind[27];
-  __shared__ int src_slot[27];
-  for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
-    const int node = t.lvl_nodes[w];
-    double* u = buf + (size_t)t.slot[node] * SLOT_U;
-    const int par = t.parent[node];
-    const double* P = (par >= 0) ? buf + (size_t)t.slot[par] * SLOT_U : nullptr;
-    const int ch = (int)(t.keys[node] & 7ull);
-    __syncthreads();
-    if (threadIdx.x < 27) {
-      const int nb = t.nbr[(size_t)node * 27 + threadIdx.x];
-      kind[threadIdx.x] = (nb >= 0) ? 1 : ((nb == -1 && P != nullptr) ? 2 : 0);
-      src_slot[threadIdx.x] = (nb >= 0) ? t.slot[nb] : -1;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < NCELL; idx += blockDim.x) {
-      const int i = idx % NS - HW, j = (idx / NS) % NS - HW, k = idx / (NS * NS) - HW;
-      const int r = region_of(i, j, k);
-      if (r == 13) continue;
-      const int kd = kind[r];
-      if (kd == 1) {
-        const int sx = r % 3 - 1, sy = (r / 3) % 3 - 1, sz = r / 9 - 1;
-        const double* s = buf + (size_t)src_slot[r] * SLOT_U;
-        const int off = idx - NB * (sx + NS * sy + NS * NS * sz);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) u[v * NCELL + idx] = s[v * NCELL + off];
-      } else if (kd == 2) {
-#pragma unroll 1
-        for (int v = 0; v < NV; ++v) u[v * NCELL + idx] = predict_cell(P + v * NCELL, ch, i, j, k);
-      }
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-#pragma unroll 1
-      for (int side = 0; side < 2; ++side) {
-        const int bc = p.bc[2 * d + side];
-        if (bc == 1) continue;
-        const int nl = p.nb[d] << level;
-        const int Xd = t.X[(size_t)node * 3 + d];
-        if (side == 0 && Xd != 0) continue;
-        if (side == 1 && Xd != nl - 1) continue;
-        for (int idx = threadIdx.x; idx < NCELL; idx += blockDim.x) {
-          int c[3] = {idx % NS - HW, (idx / NS) % NS - HW, idx / (NS * NS) - HW};
-          const int a = c[d];
-          const bool ghost = (side == 0) ? (a < 0) : (a >= NB);
-          if (!ghost) continue;
-          int sc[3] = {c[0], c[1], c[2]};
-          if (bc == 0) sc[d] = (side == 0) ? 0 : NB - 1;
-          else sc[d] = (side == 0) ? (-1 - a) : (2 * NB - 1 - a);
-          const int sidx_ = sidx(sc[0], sc[1], sc[2]);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            double val = u[v * NCELL + sidx_];
-            if (bc == 2 && v == 1 + d) val = -val;
-            u[v * NCELL + idx] = val;
-          }
-        }
-        __syncthreads();
-      }
-    }
-  }
-}
-
+// ---------------------------------------------------------------- halo fill (mr.cuh)
 void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st) {
-  k_fill_level<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, level);
+  if (p.precision == 1) {
+    launch_fill_level_f32(t, p, pool, cur, level, st);
+    return;
+  }
+  k_fill_level_t<double><<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, level);
   ++g_kernel_launches;
 }
 
@@ -369,74 +295,16 @@ __global__ void k_cfl_finish(Phys p, const unsigned long long* __restrict__ smax
 void launch_cfl(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax, double* dt,
                 int* status, cudaStream_t st) {
   cudaMemsetAsync(smax, 0, sizeof(unsigned long long) * 3 * p.n_inst, st);
-  k_cfl<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, smax, status);
-  ++g_kernel_launches;
+  if (p.precision == 1) launch_cfl_speeds_f32(t, p, pool, cur, smax, status, st);
+  else {
+    k_cfl<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, smax, status);
+    ++g_kernel_launches;
+  }
   k_cfl_finish<<<(p.n_inst + 127) / 128, 128, 0, st>>>(p, smax, dt);
   ++g_kernel_launches;
 }
 
-// ---------------------------------------------------------------- MR details and tags
-// delta of a leaf at level >= 1: max over its stored cells that are not ghost
-// cells and over rho, E of |u - P(u_parent)| / |u|; the eight fine cells of a
-// parent cell share one evaluation of the Q-terms.
-__global__ void __launch_bounds__(256) k_delta(Topo t, Phys p, Pool pool, int cur, double* __restrict__ delta_node) {
-  __shared__ double sh[8];
-  const int nleaves = t.cnt[CNT_NLEAVES];
-  const double* B = pool.buf[cur];
-  for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
-    const int node = t.leaves[li];
-    const int lvl = t.level[node];
-    if (lvl == 0) {
-      if (threadIdx.x == 0) delta_node[node] = 0.0;
-      continue;
-    }
-    const int par = t.parent[node];
-    const double* U = B + (size_t)t.slot[node] * SLOT_U;
-    const double* P = B + (size_t)t.slot[par] * SLOT_U;
-    const int ch = (int)(t.keys[node] & 7ull);
-    int cb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
-    // ghost test per axis and side
-    bool gl[3], gh[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int nl = p.nb[d] << lvl;
-      const int Xd = t.X[(size_t)node * 3 + d];
-      gl[d] = (Xd == 0) && (p.bc[2 * d] != 1);
-      gh[d] = (Xd == nl - 1) && (p.bc[2 * d + 1] != 1);
-    }
-    double m = 0.0;
-    for (int e = threadIdx.x; e < 12 * 12 * 12; e += blockDim.x) {
-      const int pi = 8 * cb[0] - 2 + e % 12, pj = 8 * cb[1] - 2 + (e / 12) % 12, pk = 8 * cb[2] - 2 + e / 144;
-#pragma unroll 1
-      for (int vi = 0; vi < 2; ++vi) {
-        const int v = vi == 0 ? 0 : 4;
-        const QTerms q = qterms(P + v * NCELL, pi, pj, pk);
-#pragma unroll
-        for (int sub = 0; sub < 8; ++sub) {
-          const int a = sub & 1, b = (sub >> 1) & 1, c = (sub >> 2) & 1;
-          const int fi = 2 * (pi - 8 * cb[0]) + a, fj = 2 * (pj - 8 * cb[1]) + b, fk = 2 * (pk - 8 * cb[2]) + c;
-          const bool ghost = (fi < 0 && gl[0]) || (fi >= NB && gh[0]) || (fj < 0 && gl[1]) || (fj >= NB && gh[1]) ||
-                             (fk < 0 && gl[2]) || (fk >= NB && gh[2]);
-          if (ghost) continue;
-          const double pr = predict_from(q, a ? -1.0 : 1.0, b ? -1.0 : 1.0, c ? -1.0 : 1.0);
-          const double uf = U[v * NCELL + sidx(fi, fj, fk)];
-          const double r = fabs(uf - pr) / fabs(uf);
-          m = fmax(m, r);
-        }
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double x = sh[0];
-      for (int q = 1; q < (int)(blockDim.x >> 5); ++q) x = fmax(x, sh[q]);
-      delta_node[node] = x;
-    }
-    __syncthreads();
-  }
-}
-
+// ---------------------------------------------------------------- MR details (mr.cuh) and tags
 __global__ void k_tags(Topo t, Phys p, const double* __restrict__ delta_node, int allow_refine,
                        int8_t* __restrict__ tags, double* __restrict__ delta_leaf) {
   const int nleaves = t.cnt[CNT_NLEAVES];
@@ -470,8 +338,11 @@ __global__ void k_tags(Topo t, Phys p, const double* __restrict__ delta_node, in
 
 void launch_delta_tags(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node,
                        int allow_refine, int8_t* tags, double* delta_leaf, int n_leaves_cap, cudaStream_t st) {
-  k_delta<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, delta_node);
-  ++g_kernel_launches;
+  if (p.precision == 1) launch_delta_f32(t, p, pool, cur, delta_node, st);
+  else {
+    k_delta_t<double><<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, delta_node);
+    ++g_kernel_launches;
+  }
   k_tags<<<(n_leaves_cap + 255) / 256, 256, 0, st>>>(t, p, delta_node, allow_refine, tags, delta_leaf);
   ++g_kernel_launches;
 }
@@ -490,12 +361,12 @@ __global__ void __launch_bounds__(256) k_refine_fill(Topo t, Pool pool, int cur,
     for (int e = threadIdx.x; e < 12 * 12 * 12 * NV; e += blockDim.x) {
       const int v = e / 1728, r = e % 1728;
       const int pi = 8 * cb[0] - 2 + r % 12, pj = 8 * cb[1] - 2 + (r / 12) % 12, pk = 8 * cb[2] - 2 + r / 144;
-      const QTerms q = qterms(P + v * NCELL, pi, pj, pk);
+      const QT<double> q = qterms_t<double>(P + v * NCELL, pi, pj, pk);
 #pragma unroll
       for (int sub = 0; sub < 8; ++sub) {
         const int a = sub & 1, b = (sub >> 1) & 1, c = (sub >> 2) & 1;
         const int fi = 2 * (pi - 8 * cb[0]) + a, fj = 2 * (pj - 8 * cb[1]) + b, fk = 2 * (pk - 8 * cb[2]) + c;
-        U[v * NCELL + sidx(fi, fj, fk)] = predict_from(q, a ? -1.0 : 1.0, b ? -1.0 : 1.0, c ? -1.0 : 1.0);
+        U[v * NCELL + sidx(fi, fj, fk)] = predict_t<double>(q, a ? -1.0 : 1.0, b ? -1.0 : 1.0, c ? -1.0 : 1.0);
       }
     }
   }

@@ -38,6 +38,7 @@ struct Phys {
   int n_inst;
   int recon;
   int has_grav;
+  int precision;           // 0 FP64, 1 FP32 bulk (MRB_FP64 / MRB_FP32_ACC64)
   const int32_t* lmax;     // device [n_inst]
 };
 
@@ -74,6 +75,11 @@ void launch_refine_fill(const Topo& t, const Pool& pool, int cur, const int32_t*
 void launch_nbr(const Topo& t, const Phys& p, int32_t* nbr_out, int nnodes_cap, cudaStream_t st);
 void launch_sums(const Topo& t, const Phys& p, const Pool& pool, int cur, double* partial, double* out,
                  int nleaves_cap, cudaStream_t st);
+// mixed-precision variants (kern_f32.cu)
+void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st);
+void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, cudaStream_t st);
+void launch_cfl_speeds_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax,
+                           int* status, cudaStream_t st);
 int sm_count();
 // kernel launches issued by this process (host-side counter, bumped by every launch_* wrapper)
 extern long long g_kernel_launches;

@@ -1,9 +1,8 @@
 // Device physics of the block-based MR Euler method (arXiv:2012.04385):
 // stiffened-gas EOS and Euler fluxes (Eq. Euler, Eq. StiffenedGas), the Roe
 // eigensystem, WENO5-JS / linear 5th-order reconstruction in characteristic
-// variables with the Roe / local Lax-Friedrichs switch per field (Sec. 2.2),
-// and the 5th-order conservative prediction of Eq. (Prediction) with the
-// appendix Q-terms.
+// variables with the Roe / local Lax-Friedrichs switch per field (Sec. 2.2).
+// The prediction of Eq. (Prediction) lives in mr.cuh.
 //
 // Every formula is written in one fixed evaluation order.  The FP64 kernels are
 // compiled without FMA contraction (-fmad=false), so each double result is the
@@ -206,99 +205,6 @@ __device__ __forceinline__ void face_flux(const R U6[6][5], int d, R g, R B, boo
   Fout[1 + a1] = Fh[2];
   Fout[1 + a2] = Fh[3];
   Fout[4] = Fh[4];
-}
-
-// ---------------------------------------------------------------- prediction
-// Eq. (Prediction) with the appendix Q-terms: c0 = -22/128, c1 = 3/128,
-// c_pq = c_p c_q, c_rpq = c_r c_p c_q (index 0 for an offset of one parent
-// cell, 1 for two); Q_z read with u_{i,j,k+2}.  The child half below the
-// parent centre along an axis takes +Q, the upper half -Q.
-struct QTerms {
-  double u, Qx, Qy, Qz, Qxy, Qxz, Qyz, Qxyz;
-};
-
-__device__ __forceinline__ double qcoef(int off) { return off == 1 ? (-22.0 / 128.0) : (3.0 / 128.0); }
-
-// P points at a parent's stored array of one variable; (i, j, k) the parent cell
-__device__ __forceinline__ double pat(const double* P, int i, int j, int k) { return P[sidx(i, j, k)]; }
-
-__device__ __forceinline__ double mix2(const double* P, int i, int j, int k, int A, int Bx, int p, int q) {
-  int o1[3] = {0, 0, 0}, o2[3] = {0, 0, 0}, o3[3] = {0, 0, 0}, o4[3] = {0, 0, 0};
-  o1[A] = p; o1[Bx] = q;      // (+p, +q)
-  o2[A] = -p; o2[Bx] = -q;    // (-p, -q)
-  o3[A] = -p; o3[Bx] = q;     // (-p, +q)
-  o4[A] = p; o4[Bx] = -q;     // (+p, -q)
-  return (pat(P, i + o1[0], j + o1[1], k + o1[2]) + pat(P, i + o2[0], j + o2[1], k + o2[2])) -
-         (pat(P, i + o3[0], j + o3[1], k + o3[2]) + pat(P, i + o4[0], j + o4[1], k + o4[2]));
-}
-
-__device__ __forceinline__ double mix3(const double* P, int i, int j, int k, int p, int q, int r) {
-  const int sg[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, -1, 1}, {-1, 1, -1}};
-  double acc = 0.0;
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    double term = pat(P, i + sg[t][0] * p, j + sg[t][1] * q, k + sg[t][2] * r) -
-                  pat(P, i - sg[t][0] * p, j - sg[t][1] * q, k - sg[t][2] * r);
-    acc = (t == 0) ? term : acc + term;
-  }
-  return acc;
-}
-
-__device__ __forceinline__ QTerms qterms(const double* P, int i, int j, int k) {
-  const double C0 = -22.0 / 128.0, C1 = 3.0 / 128.0;
-  QTerms t;
-  t.u = pat(P, i, j, k);
-  t.Qx = C0 * (pat(P, i + 1, j, k) - pat(P, i - 1, j, k)) + C1 * (pat(P, i + 2, j, k) - pat(P, i - 2, j, k));
-  t.Qy = C0 * (pat(P, i, j + 1, k) - pat(P, i, j - 1, k)) + C1 * (pat(P, i, j + 2, k) - pat(P, i, j - 2, k));
-  t.Qz = C0 * (pat(P, i, j, k + 1) - pat(P, i, j, k - 1)) + C1 * (pat(P, i, j, k + 2) - pat(P, i, j, k - 2));
-  const int pq[4][2] = {{1, 1}, {2, 2}, {1, 2}, {2, 1}};
-  double qxy = 0.0, qxz = 0.0, qyz = 0.0;
-#pragma unroll
-  for (int t2 = 0; t2 < 4; ++t2) {
-    int p = pq[t2][0], q = pq[t2][1];
-    double cc = qcoef(p) * qcoef(q);
-    double a = cc * mix2(P, i, j, k, 0, 1, p, q);
-    double b = cc * mix2(P, i, j, k, 0, 2, p, q);
-    double c = cc * mix2(P, i, j, k, 1, 2, p, q);
-    qxy = (t2 == 0) ? a : qxy + a;
-    qxz = (t2 == 0) ? b : qxz + b;
-    qyz = (t2 == 0) ? c : qyz + c;
-  }
-  t.Qxy = qxy;
-  t.Qxz = qxz;
-  t.Qyz = qyz;
-  const int pqr[8][3] = {{1, 1, 1}, {2, 2, 2}, {1, 1, 2}, {2, 2, 1}, {1, 2, 2}, {2, 1, 1}, {1, 2, 1}, {2, 1, 2}};
-  double qxyz = 0.0;
-#pragma unroll
-  for (int t3 = 0; t3 < 8; ++t3) {
-    int p = pqr[t3][0], q = pqr[t3][1], r = pqr[t3][2];
-    double cc = qcoef(p) * qcoef(q) * qcoef(r);
-    double a = cc * mix3(P, i, j, k, p, q, r);
-    qxyz = (t3 == 0) ? a : qxyz + a;
-  }
-  t.Qxyz = qxyz;
-  return t;
-}
-
-__device__ __forceinline__ double predict_from(const QTerms& t, double sx, double sy, double sz) {
-  return t.u + sx * t.Qx + sy * t.Qy + sz * t.Qz + (sx * sy) * t.Qxy + (sx * sz) * t.Qxz + (sy * sz) * t.Qyz +
-         (sx * sy * sz) * t.Qxyz;
-}
-
-__device__ __forceinline__ int floordiv2(int i) { return (i >= 0) ? (i >> 1) : -((-i + 1) >> 1); }
-
-// fine stored cell (i, j, k) of child `ch` predicted from its parent's array P
-__device__ __forceinline__ double predict_cell(const double* P, int ch, int i, int j, int k) {
-  int f[3] = {i, j, k}, p[3];
-  double s[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    int h = floordiv2(f[d]);
-    p[d] = 8 * ((ch >> d) & 1) + h;
-    s[d] = (f[d] - 2 * h == 0) ? 1.0 : -1.0;
-  }
-  QTerms t = qterms(P, p[0], p[1], p[2]);
-  return predict_from(t, s[0], s[1], s[2]);
 }
 
 }  // namespace mrb

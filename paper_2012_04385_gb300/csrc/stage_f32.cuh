@@ -1,0 +1,341 @@
+// Mixed-precision fused stage kernel (MRB_FP32_ACC64): characteristic WENO5-JS
+// with the Roe / local Lax-Friedrichs switch (Sec. 2.2 of arXiv:2012.04385) in
+// FP32, flux differences accumulated per cell in FP32, and the TVD-RK3 update
+// of the FP64 state in FP64.
+//
+// Work item = (leaf, z-slab of 16 x 16 x 4 cells); a CTA of 256 threads loops
+// over items.  For each direction the stencil region of the slab (the slab
+// plus 3 cells on both sides along that direction) is converted once from the
+// FP64 stage buffer into FP32 primitive records in shared memory; then one
+// thread per face computes the face flux from six records, writes it to
+// shared memory (and, on the block boundary, to the block's face buffers), and
+// each thread adds the flux differences of the four cells of its (i, j)
+// column.  Reciprocals and square roots use the fast hardware approximations;
+// the WENO weights need one reciprocal: omega_k = d_k P_k / sum_j d_j P_j with
+// P_k the product of the other two (eps + beta)^2.
+#pragma once
+
+#include "convert.cuh"
+#include "kernels.cuh"
+
+namespace mrb {
+
+constexpr int SF_TZ = 4;
+constexpr int SF_NSLAB = NB / SF_TZ;
+constexpr int SF_THREADS = 256;
+constexpr int SF_REG = NB * NB * (SF_TZ + 6);            // largest stencil region (z): 2560 cells
+constexpr int SF_FMAX = NB * NB * (SF_TZ + 1);           // largest face count (z): 1280
+constexpr int SF_NREC = 7;                                // rho, u, v, w, p, E, c
+constexpr size_t SF_SMEM = sizeof(float) * (SF_NREC * SF_REG + NV * SF_FMAX);
+
+__device__ __constant__ static const double kSfA[3] = {0.0, 0.75, 1.0 / 3.0};
+__device__ __constant__ static const double kSfB[3] = {1.0, 0.25, 2.0 / 3.0};
+
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+
+// WENO5-JS with a single reciprocal
+__device__ __forceinline__ float weno5f(float a, float b, float c, float d, float e) {
+  const float eps = 1e-6f;
+  float t1 = fmaf(-2.f, b, a) + c, t2 = fmaf(3.f, c, fmaf(-4.f, b, a));
+  float s0 = eps + fmaf(13.f / 12.f * t1, t1, 0.25f * t2 * t2);
+  t1 = fmaf(-2.f, c, b) + d;
+  t2 = b - d;
+  float s1 = eps + fmaf(13.f / 12.f * t1, t1, 0.25f * t2 * t2);
+  t1 = fmaf(-2.f, d, c) + e;
+  t2 = fmaf(-4.f, d, 3.f * c) + e;
+  float s2 = eps + fmaf(13.f / 12.f * t1, t1, 0.25f * t2 * t2);
+  s0 *= s0;
+  s1 *= s1;
+  s2 *= s2;
+  const float w0 = 0.1f * (s1 * s2), w1 = 0.6f * (s0 * s2), w2 = 0.3f * (s0 * s1);
+  const float q0 = fmaf(11.f, c, fmaf(-7.f, b, 2.f * a));
+  const float q1 = fmaf(2.f, d, fmaf(5.f, c, -b));
+  const float q2 = fmaf(-1.f, e, fmaf(5.f, d, 2.f * c));
+  return fmaf(w0, q0, fmaf(w1, q1, w2 * q2)) * frcp(6.f * (w0 + w1 + w2));
+}
+
+__device__ __forceinline__ float linear5f(float a, float b, float c, float d, float e) {
+  // (2a - 13b + 47c + 27d - 3e) / 60
+  return fmaf(2.f / 60.f, a, fmaf(-13.f / 60.f, b, fmaf(47.f / 60.f, c, fmaf(27.f / 60.f, d, (-3.f / 60.f) * e))));
+}
+
+template <bool LIN>
+__device__ __forceinline__ float rec5(float a, float b, float c, float d, float e) {
+  return LIN ? linear5f(a, b, c, d, e) : weno5f(a, b, c, d, e);
+}
+
+// Face flux between stencil cells 2 and 3 (cells at S index c0 + m*st, m = 0..5)
+// along D, from the FP32 records; result in the lab frame.
+template <int D, bool LIN>
+__device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, float gm1, float F[5]) {
+  constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
+  float Ur[6][5], Fr[6][5];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const int c = c0 + m * st;
+    const float r = S[c], un = S[(1 + A0) * SF_REG + c], u1 = S[(1 + A1) * SF_REG + c], u2 = S[(1 + A2) * SF_REG + c];
+    const float p = S[4 * SF_REG + c], E = S[5 * SF_REG + c];
+    const float mn = r * un;
+    Ur[m][0] = r;
+    Ur[m][1] = mn;
+    Ur[m][2] = r * u1;
+    Ur[m][3] = r * u2;
+    Ur[m][4] = E;
+    Fr[m][0] = mn;
+    Fr[m][1] = fmaf(mn, un, p);
+    Fr[m][2] = mn * u1;
+    Fr[m][3] = mn * u2;
+    Fr[m][4] = un * (E + p);
+  }
+  const int cl = c0 + 2 * st, cr = c0 + 3 * st;
+  const float rL = S[cl], rR = S[cr];
+  const float unL = S[(1 + A0) * SF_REG + cl], unR = S[(1 + A0) * SF_REG + cr];
+  const float cL = S[6 * SF_REG + cl], cR = S[6 * SF_REG + cr];
+  // Roe average: sqrt(rho) weights, H = (E + p) / rho
+  const float rsL = rsqrtf(rL), rsR = rsqrtf(rR);
+  const float sL = rL * rsL, sR = rR * rsR;
+  const float iden = frcp(sL + sR);
+  const float un = fmaf(sL, unL, sR * unR) * iden;
+  const float ut1 = fmaf(sL, S[(1 + A1) * SF_REG + cl], sR * S[(1 + A1) * SF_REG + cr]) * iden;
+  const float ut2 = fmaf(sL, S[(1 + A2) * SF_REG + cl], sR * S[(1 + A2) * SF_REG + cr]) * iden;
+  const float H = fmaf(Ur[2][4] + S[4 * SF_REG + cl], rsL, (Ur[3][4] + S[4 * SF_REG + cr]) * rsR) * iden;
+  const float q2 = fmaf(un, un, fmaf(ut1, ut1, ut2 * ut2));
+  const float c2 = gm1 * fmaf(-0.5f, q2, H);
+  const float ic = rsqrtf(c2);
+  const float c = c2 * ic;
+  const float b1 = gm1 * ic * ic;
+  const float b2 = 0.5f * b1 * q2;
+  const float hb1 = 0.5f * b1;
+  float Fh0 = 0.f, Fh1 = 0.f, Fh2 = 0.f, Fh3 = 0.f, Fh4 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    float G[6], V[6];
+    float lL, lR, lt;
+    if (k == 0 || k == 4) {
+      const float sg = (k == 0) ? 1.f : -1.f;
+      const float l0 = fmaf(0.5f * sg * un, ic, 0.5f * b2), l1 = fmaf(-hb1, un, -0.5f * sg * ic);
+      const float l2 = -hb1 * ut1, l3 = -hb1 * ut2, l4 = hb1;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        V[m] = fmaf(l0, Ur[m][0], fmaf(l1, Ur[m][1], fmaf(l2, Ur[m][2], fmaf(l3, Ur[m][3], l4 * Ur[m][4]))));
+        G[m] = fmaf(l0, Fr[m][0], fmaf(l1, Fr[m][1], fmaf(l2, Fr[m][2], fmaf(l3, Fr[m][3], l4 * Fr[m][4]))));
+      }
+      lL = fmaf(-sg, cL, unL);
+      lR = fmaf(-sg, cR, unR);
+      lt = fmaf(-sg, c, un);
+    } else if (k == 1) {
+      const float l0 = 1.f - b2, l1 = b1 * un, l2 = b1 * ut1, l3 = b1 * ut2, l4 = -b1;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        V[m] = fmaf(l0, Ur[m][0], fmaf(l1, Ur[m][1], fmaf(l2, Ur[m][2], fmaf(l3, Ur[m][3], l4 * Ur[m][4]))));
+        G[m] = fmaf(l0, Fr[m][0], fmaf(l1, Fr[m][1], fmaf(l2, Fr[m][2], fmaf(l3, Fr[m][3], l4 * Fr[m][4]))));
+      }
+      lL = unL;
+      lR = unR;
+      lt = un;
+    } else {
+      const float ut = (k == 2) ? ut1 : ut2;
+      const int j = (k == 2) ? 2 : 3;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        V[m] = fmaf(-ut, Ur[m][0], Ur[m][j]);
+        G[m] = fmaf(-ut, Fr[m][0], Fr[m][j]);
+      }
+      lL = unL;
+      lR = unR;
+      lt = un;
+    }
+    float gh;
+    if (lL > 0.f && lR > 0.f && lt > 0.f) {
+      gh = rec5<LIN>(G[0], G[1], G[2], G[3], G[4]);
+    } else if (lL < 0.f && lR < 0.f && lt < 0.f) {
+      gh = rec5<LIN>(G[5], G[4], G[3], G[2], G[1]);
+    } else {
+      const float ha = 0.5f * fmaxf(fabsf(lL), fabsf(lR));
+      float fp[6], fm[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        fp[m] = fmaf(0.5f, G[m], ha * V[m]);
+        fm[m] = fmaf(0.5f, G[m], -ha * V[m]);
+      }
+      gh = rec5<LIN>(fp[0], fp[1], fp[2], fp[3], fp[4]) + rec5<LIN>(fm[5], fm[4], fm[3], fm[2], fm[1]);
+    }
+    // F_hat = R g_hat, columns r0 = (1, u-c, ut1, ut2, H-uc), r1 = (1, u, ut1, ut2, q2/2),
+    // r2 = (0, 0, 1, 0, ut1), r3 = (0, 0, 0, 1, ut2), r4 = (1, u+c, ut1, ut2, H+uc)
+    if (k == 0 || k == 4) {
+      const float sg = (k == 0) ? -1.f : 1.f;
+      Fh0 += gh;
+      Fh1 = fmaf(fmaf(sg, c, un), gh, Fh1);
+      Fh2 = fmaf(ut1, gh, Fh2);
+      Fh3 = fmaf(ut2, gh, Fh3);
+      Fh4 = fmaf(fmaf(sg * un, c, H), gh, Fh4);
+    } else if (k == 1) {
+      Fh0 += gh;
+      Fh1 = fmaf(un, gh, Fh1);
+      Fh2 = fmaf(ut1, gh, Fh2);
+      Fh3 = fmaf(ut2, gh, Fh3);
+      Fh4 = fmaf(0.5f * q2, gh, Fh4);
+    } else if (k == 2) {
+      Fh2 += gh;
+      Fh4 = fmaf(ut1, gh, Fh4);
+    } else {
+      Fh3 += gh;
+      Fh4 = fmaf(ut2, gh, Fh4);
+    }
+  }
+  F[0] = Fh0;
+  F[1 + A0] = Fh1;
+  F[1 + A1] = Fh2;
+  F[1 + A2] = Fh3;
+  F[4] = Fh4;
+}
+
+// Stencil region of direction D for the slab at z0 -> FP32 records in S.
+template <int D>
+__device__ __forceinline__ void load_region_f32(const double* __restrict__ u, float* __restrict__ S, int z0, float g,
+                                                float B, float gm1) {
+  constexpr int n = (D == 2) ? SF_REG : 22 * 16 * SF_TZ;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    int x, y, z;
+    if (D == 0) { x = idx % 22 - 3; y = (idx / 22) % 16; z = z0 + idx / 352; }
+    else if (D == 1) { x = idx % 16; y = (idx / 16) % 22 - 3; z = z0 + idx / 352; }
+    else { x = idx % 16; y = (idx / 16) % 16; z = z0 - 3 + idx / 256; }
+    const int s = sidx(x, y, z);
+    const float r = d2f_fast(u[s]), mx = d2f_fast(u[NCELL + s]), my = d2f_fast(u[2 * NCELL + s]);
+    const float mz = d2f_fast(u[3 * NCELL + s]), E = d2f_fast(u[4 * NCELL + s]);
+    const float ir = frcp(r);
+    const float vx = mx * ir, vy = my * ir, vz = mz * ir;
+    const float q2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+    const float p = fmaf(gm1, fmaf(-0.5f * r, q2, E), -g * B);
+    S[idx] = r;
+    S[SF_REG + idx] = vx;
+    S[2 * SF_REG + idx] = vy;
+    S[3 * SF_REG + idx] = vz;
+    S[4 * SF_REG + idx] = p;
+    S[5 * SF_REG + idx] = E;
+    S[6 * SF_REG + idx] = sqrtf(g * (p + B) * ir);
+  }
+}
+
+template <int D, bool LIN>
+__device__ __forceinline__ void sweep_f32(const double* __restrict__ u, double* __restrict__ fb, float* __restrict__ S,
+                                          float* __restrict__ Fs, int z0, float g, float B, float gm1,
+                                          float (&acc)[SF_TZ][NV]) {
+  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+  load_region_f32<D>(u, S, z0, g, B, gm1);
+  __syncthreads();
+  constexpr int nf = (D == 2) ? NB * NB * (SF_TZ + 1) : 17 * 16 * SF_TZ;
+  constexpr int st = (D == 0) ? 1 : (D == 1 ? 16 : 256);
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+    int fa, c0, ta, tb;
+    if (D == 0) {
+      fa = f % 17;
+      const int r = f / 17;                 // row = kz * 16 + j
+      c0 = r * 22 + fa;                     // cell x = fa - 3 at record index fa
+      ta = r % 16;
+      tb = z0 + r / 16;
+    } else if (D == 1) {
+      const int i = f % 16, r = f / 16;     // r = kz * 17 + fa
+      fa = r % 17;
+      const int kz = r / 17;
+      c0 = (kz * 22 + fa) * 16 + i;
+      ta = i;
+      tb = z0 + kz;
+    } else {
+      const int i = f % 16, j = (f / 16) % 16;
+      fa = f / 256;
+      c0 = (fa * 16 + j) * 16 + i;
+      ta = i;
+      tb = j;
+    }
+    float F[5];
+    face_flux_f32<D, LIN>(S, c0, st, gm1, F);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Fs[v * SF_FMAX + f] = F[v];
+    const int gface = (D == 2) ? z0 + fa : fa;
+    if (gface == 0 || gface == NB) {
+      const int side = 2 * D + (gface == NB ? 1 : 0);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) fb[((side * NV + v) * NB + tb) * NB + ta] = f2d_fast(F[v]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int kz = 0; kz < SF_TZ; ++kz) {
+    int lo, hi;
+    if (D == 0) { lo = (kz * 16 + tj) * 17 + ti; hi = lo + 1; }
+    else if (D == 1) { lo = (kz * 17 + tj) * 16 + ti; hi = lo + 16; }
+    else { lo = (kz * 16 + tj) * 16 + ti; hi = lo + 256; }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const float diff = Fs[v * SF_FMAX + lo] - Fs[v * SF_FMAX + hi];
+      acc[kz][v] = (D == 0) ? diff : acc[kz][v] + diff;
+    }
+  }
+  __syncthreads();
+}
+
+template <bool LIN>
+__global__ void __launch_bounds__(SF_THREADS, 2)
+    k_stage_f32(Topo t, Phys p, Pool pool, int cur, int stage, const double* __restrict__ dt,
+                double* __restrict__ rhs_out) {
+  extern __shared__ __align__(16) float sf_smem[];
+  float* S = sf_smem;
+  float* Fs = sf_smem + SF_NREC * SF_REG;
+  const int nitems = t.cnt[CNT_NLEAVES] * SF_NSLAB;
+  const double* __restrict__ src = pool.buf[cur];
+  double* __restrict__ dst = pool.buf[cur ^ 1];
+  const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
+  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int li = w / SF_NSLAB, z0 = (w % SF_NSLAB) * SF_TZ;
+    const int node = t.leaves[li];
+    const int slot = t.slot[node];
+    const double* __restrict__ u = src + (size_t)slot * SLOT_U;
+    double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
+    float acc[SF_TZ][NV];
+    sweep_f32<0, LIN>(u, fb, S, Fs, z0, g, B, gm1, acc);
+    sweep_f32<1, LIN>(u, fb, S, Fs, z0, g, B, gm1, acc);
+    sweep_f32<2, LIN>(u, fb, S, Fs, z0, g, B, gm1, acc);
+    const double dx = ldexp(p.dx0, -t.level[node]);
+    const double idx_ = 1.0 / dx;
+    const double h = dt ? dt[t.inst[node]] : 0.0;
+    const double hdx = h * idx_;
+#pragma unroll
+    for (int kz = 0; kz < SF_TZ; ++kz) {
+      const int k = z0 + kz;
+      const int s = sidx(ti, tj, k), ii = iidx(ti, tj, k);
+      double S4[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      if (p.has_grav) {
+        const double rho = u[s], mx = u[NCELL + s], my = u[2 * NCELL + s], mz = u[3 * NCELL + s];
+        S4[1] = rho * p.grav[0];
+        S4[2] = rho * p.grav[1];
+        S4[3] = rho * p.grav[2];
+        S4[4] = fma(mx, p.grav[0], fma(my, p.grav[1], mz * p.grav[2]));
+      }
+      if (rhs_out) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) rhs_out[((size_t)li * NV + v) * NINT + ii] = fma(f2d_fast(acc[kz][v]), idx_, S4[v]);
+      } else {
+        double* __restrict__ unb = pool.un + (size_t)slot * SLOT_N;
+        double* __restrict__ o = dst + (size_t)slot * SLOT_U;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const double us = u[v * NCELL + s];
+          double tt = fma(f2d_fast(acc[kz][v]), hdx, us);
+          if (p.has_grav) tt = fma(h, S4[v], tt);
+          double out;
+          if (stage == 0) {
+            unb[v * NINT + ii] = us;
+            out = tt;
+          } else {
+            out = fma(kSfA[stage], unb[v * NINT + ii], kSfB[stage] * tt);
+          }
+          o[v * NCELL + s] = out;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace mrb

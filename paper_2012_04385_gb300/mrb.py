@@ -89,6 +89,7 @@ def lib():
                 "mrb_profile": (ci, [vp, i32]),
                 "mrb_profile_read": (ci, [vp, vp, vp, vp]),
                 "mrb_block_sums_noalloc": (ci, [vp, i64, vp, ctypes.c_double, vp, vp]),
+                "mrb_measure_peaks": (ci, [vp, i32]),
                 "mrb_status": (ci, [vp]),
                 "mrb_sync": (ci, [vp]),
                 "mrb_destroy": (ci, [vp]),
@@ -132,6 +133,16 @@ def _ptr(t) -> int:
     if isinstance(t, np.ndarray):
         return t.ctypes.data
     return t.data_ptr()
+
+
+def measure_peaks() -> dict:
+    """FP32/FP64 FMA, conversion and rsqrt throughputs of the current GPU."""
+    out = np.zeros(8)
+    rc = lib().mrb_measure_peaks(out.ctypes.data, 8)
+    if rc != MRB_OK:
+        raise MrbError(rc, "mrb_measure_peaks failed")
+    keys = ["fp32_tflops", "fp64_tflops", "d2f_tps", "f2d_tps", "rsqrt_tps", "sm_count", "sm_clock_mhz"]
+    return {k: float(v) for k, v in zip(keys, out)}
 
 
 def pool_bytes(cfg: RunConfig, n_slots: int) -> int:
