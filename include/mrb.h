@@ -98,8 +98,10 @@ typedef struct mrb_ctx mrb_ctx;
 
 /* Bytes of block pool needed for `n_slots` blocks (leaves and internal nodes
  * together).  Per block: two stage buffers with halo (2 x 5 x 24^3 doubles),
- * the u^n buffer of the RK step (5 x 16^3) and six face-flux buffers
- * (6 x 5 x 16^2), 256-byte aligned.  Returns 0 for a bad config. */
+ * the u^n buffer of the RK step (5 x 16^3), six face-flux buffers
+ * (6 x 5 x 16^2) and the learned selector's decision bits of the current
+ * step (432 words), each region 256-byte aligned.  Returns 0 for a bad
+ * config. */
 size_t mrb_pool_bytes(const mrb_config* cfg, int64_t n_slots);
 
 /* Create a context: checks the config, builds the level-0 topology of every
@@ -201,6 +203,59 @@ int mrb_sums(mrb_ctx* ctx, double* sums_dev);
  * the id, or 0 where no same-level block exists, or 1 beyond a non-periodic
  * boundary (ids always have a headbit, so 0 and 1 are never ids). */
 int mrb_neighbors(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, uint64_t* nbr_host);
+
+/* ---- learned reconstruction selector (MRB_RECON_LEARNED) -----------------
+ * Not in the paper: a 15 -> 32 -> 32 -> 1 perceptron with GELU (tanh form)
+ * reads, per face, the characteristic fluxes g_m = L_k F(U_m) and variables
+ * v_m = L_k U_m of fields k = 0 (u-c), 1 (entropy) and 4 (u+c) of the face's
+ * Roe eigensystem over the six stencil cells m = i-2 .. i+3 -- per field the
+ * five consecutive variations d = s (|g_{m+1} - g_m| + alpha_k |v_{m+1} - v_m|)
+ * (alpha_k the field's local Lax-Friedrichs speed, s the sign of the flux
+ * difference, of the variable difference where that is zero) compressed as
+ * sign(d) log10(1 + 1e6 |d|) / 8 -- and
+ * predicts whether WENO5-JS is needed (logit >= mlp_tau) or the linear
+ * 5th-order upwind reconstruction suffices (logit < mlp_tau) for those three
+ * fields; the shear fields always use WENO5-JS.
+ * Parameters: MRB_MLP_NPARAM floats (FP32 master copy, device) laid out
+ * W1[32][15], b1[32], W2[32][32], b2[32], w3[32], b3; the kernels round
+ * the weights to BF16 and run the layers on the tensor cores with FP32
+ * accumulation.  cfg.mlp_weights points at them; the learned path applies
+ * to MRB_FP32_ACC64 contexts. */
+#define MRB_MLP_NPARAM 1601
+#define MRB_MLP_WORK_FLOATS (512 * (MRB_MLP_NPARAM + 1))
+
+/* Training data from the context's current state: every `stride`-th face of
+ * every leaf (face id = leaf index * 13056 + direction * 4352 + position in
+ * the block's face order, x then y then z faces, index f + 17 (t1 + 16 t2))
+ * gives its features feats_dev [n][16] (15 + a zero pad), its label
+ * labels_dev [n] (1 when, for field 0, 1 or 4 and any reconstruction the
+ * face performs, |WENO5 - linear5| > max(tau_lab x the largest |input|,
+ * 1e-6)) and, when
+ * where_dev is not null, its face id.  n = min(cap, ceil(faces / stride)) is
+ * returned in *n_out.  Halos must be filled.  FP32 arithmetic. */
+int mrb_face_samples(mrb_ctx* ctx, float tau_lab, int64_t stride, float* feats_dev, uint8_t* labels_dev,
+                     int64_t* where_dev, int64_t cap, int64_t* n_out);
+
+/* Faces evaluated by the selector and faces it sent to the linear scheme
+ * since the last reset (reset = 1 clears after reading).  Synchronises. */
+int mrb_learned_stats(mrb_ctx* ctx, int64_t* linear_faces, int64_t* evaluated_faces, int32_t reset);
+
+/* Selector logits of n samples (feats_dev [n][16]) on the tensor cores, into
+ * logits_dev [n]; asynchronous on `stream`.  No context needed. */
+int mrb_mlp_logits(const float* params_dev, const float* feats_dev, int64_t n, float* logits_dev, void* stream);
+
+/* One training step of the selector on n samples: forward and backward with
+ * BF16-rounded inputs, weights and hidden activations and FP32 accumulation,
+ * loss = mean over samples of the binary cross-entropy with logits weighted
+ * by pos_weight on label 1, gradient reduced in a fixed order, then (lr > 0)
+ * one Adam step (beta 0.9, 0.999, eps 1e-8; t_step counts from 1) on the FP32
+ * parameters and moments (device, MRB_MLP_NPARAM each).  work_dev: device
+ * scratch of MRB_MLP_WORK_FLOATS floats.  loss_dev (device float, nullable)
+ * receives the loss, grad_dev (device [MRB_MLP_NPARAM], nullable) the
+ * gradient.  Asynchronous on `stream`. */
+int mrb_mlp_train_step(float* params_dev, float* adam_m_dev, float* adam_v_dev, int32_t t_step, const float* feats_dev,
+                       const uint8_t* labels_dev, int64_t n, float pos_weight, float lr, float* work_dev,
+                       float* loss_dev, float* grad_dev, void* stream);
 
 /* Profiling.  mrb_profile(ctx, 1) starts recording CUDA events around every
  * launch of the fused stage kernel (the dominant kernel, on cfg.stream, also

@@ -96,6 +96,7 @@ def lib():
                 "orc_roe_eigen": (None, [vp, vp, i32, dbl, dbl, vp, vp, vp]),
                 "orc_face_flux": (None, [vp, i32, dbl, dbl, i32, vp]),
                 "orc_predict_block": (None, [vp, i32, vp]),
+                "orc_face_features": (None, [vp, i32, dbl, dbl, dbl, vp, vp]),
                 "orc_average_block": (None, [vp, vp]),
                 "orc_threads": (i32, []),
             }
@@ -278,6 +279,16 @@ def face_flux(U6, d: int, gamma: float = 1.4, B: float = 0.0, mode: int = 0) -> 
     F = np.zeros(5)
     lib().orc_face_flux(_p(U6), d, gamma, B, mode, _p(F))
     return F
+
+
+def face_features(U6, d: int, gamma: float = 1.4, B: float = 0.0, tau_lab: float = 1e-3):
+    """Selector features [15] and label of one face (U6: six lab-frame cells)."""
+    U6 = np.ascontiguousarray(U6, dtype=np.float64)
+    assert U6.shape == (6, 5)
+    f = np.zeros(15)
+    lab = np.zeros(1, dtype=np.int32)
+    lib().orc_face_features(_p(U6), d, gamma, B, tau_lab, _p(f), _p(lab))
+    return f, int(lab[0])
 
 
 def predict_block(parent: np.ndarray, child: int) -> np.ndarray:

@@ -358,6 +358,102 @@ void face_flux(const double U6[6][5], int d, double g, double B, int mode, doubl
   unrotate(Fr_hat, d, Fout);
 }
 
+// ------------------------------------------------------------ selector features
+// Learned reconstruction selector (not in the paper; a reading of the
+// selector the benchmark adds).  Features of the face between cells 2 and 3
+// of U6: for the characteristic fields k = 0 (u-c), 1 (entropy), 4 (u+c),
+// with g_m = L_k F(U_m), v_m = L_k U_m over the six stencil cells m = 0..5
+// (i-2 .. i+3) and alpha_k = max(|lam_k(U_i)|, |lam_k(U_{i+1})|) (the LLF
+// speed of the field), the five consecutive variations
+// d = s (|g_{m+1} - g_m| + alpha_k |v_{m+1} - v_m|), s the sign of the flux
+// difference (of the variable difference where the flux difference is zero),
+// compressed as sign(d) log10(1 + 1e6 |d|) / 8 (absolute units, like WENO's
+// epsilon).  The selector decides for these three fields; the shear fields
+// keep WENO5.  Label: 1 when, for field 0, 1 or 4 and any reconstruction the
+// face performs (one for Roe upwinding, two for the LLF split),
+// |WENO5 - linear5| exceeds both tau_lab times the largest |input| of that
+// reconstruction and the absolute floor 1e-6 (below which a difference is
+// rounding noise of O(1) fluxes in FP32).
+inline bool selected_field(int k) { return k == 0 || k == 1 || k == 4; }
+
+double compress_diff(double d) {
+  double a = std::log10(1.0 + 1e6 * std::fabs(d)) / 8.0;
+  return d < 0.0 ? -a : a;
+}
+
+void face_features(const double U6[6][5], int d, double g, double B, double tau_lab, double feats[15], int* label) {
+  Prim q[6];
+  double Ur[6][5], Fr[6][5];
+  for (int m = 0; m < 6; ++m) {
+    q[m] = prim_of(U6[m], g, B);
+    rotate(U6[m], d, Ur[m]);
+    flux_rot(Ur[m], q[m], d, Fr[m]);
+  }
+  Eigen e = roe_eigen(q[2], q[3], d, g);
+  const int ks[3] = {0, 1, 4};
+  for (int t = 0; t < 3; ++t) {
+    int k = ks[t];
+    double gk[6], vk[6];
+    for (int m = 0; m < 6; ++m) {
+      double sg = e.Lm[k][0] * Fr[m][0], sv = e.Lm[k][0] * Ur[m][0];
+      for (int j = 1; j < 5; ++j) {
+        sg = sg + e.Lm[k][j] * Fr[m][j];
+        sv = sv + e.Lm[k][j] * Ur[m][j];
+      }
+      gk[m] = sg;
+      vk[m] = sv;
+    }
+    double unL0 = q[2].vel[d], unR0 = q[3].vel[d];
+    double lL = (k == 0) ? unL0 - q[2].c : (k == 4 ? unL0 + q[2].c : unL0);
+    double lR = (k == 0) ? unR0 - q[3].c : (k == 4 ? unR0 + q[3].c : unR0);
+    double alpha = std::max(std::fabs(lL), std::fabs(lR));
+    for (int m = 0; m < 5; ++m) {
+      double dg = gk[m + 1] - gk[m], dv = vk[m + 1] - vk[m];
+      double sgn = (dg != 0.0) ? (dg < 0.0 ? -1.0 : 1.0) : (dv < 0.0 ? -1.0 : 1.0);
+      feats[5 * t + m] = compress_diff(sgn * (std::fabs(dg) + alpha * std::fabs(dv)));
+    }
+  }
+  double unL = q[2].vel[d], unR = q[3].vel[d];
+  double lamL[5] = {unL - q[2].c, unL, unL, unL, unL + q[2].c};
+  double lamR[5] = {unR - q[3].c, unR, unR, unR, unR + q[3].c};
+  int lab = 0;
+  auto check = [&](const double f[5]) {
+    double sc = 0.0;
+    for (int m = 0; m < 5; ++m) sc = std::max(sc, std::fabs(f[m]));
+    double dw = std::fabs(weno5(f[0], f[1], f[2], f[3], f[4]) - linear5(f[0], f[1], f[2], f[3], f[4]));
+    if (dw > std::max(tau_lab * sc, 1e-6)) lab = 1;
+  };
+  for (int k = 0; k < 5; ++k) {
+    if (!selected_field(k)) continue;
+    double G[6], V[6];
+    for (int m = 0; m < 6; ++m) {
+      double sv = e.Lm[k][0] * Ur[m][0], sg = e.Lm[k][0] * Fr[m][0];
+      for (int j = 1; j < 5; ++j) {
+        sv = sv + e.Lm[k][j] * Ur[m][j];
+        sg = sg + e.Lm[k][j] * Fr[m][j];
+      }
+      V[m] = sv;
+      G[m] = sg;
+    }
+    double lL = lamL[k], lR = lamR[k], lt = e.lam[k];
+    if (lL > 0.0 && lR > 0.0 && lt > 0.0) {
+      double f[5] = {G[0], G[1], G[2], G[3], G[4]};
+      check(f);
+    } else if (lL < 0.0 && lR < 0.0 && lt < 0.0) {
+      double f[5] = {G[5], G[4], G[3], G[2], G[1]};
+      check(f);
+    } else {
+      double alpha = std::max(std::fabs(lL), std::fabs(lR));
+      double fp[5], fm[5];
+      for (int m = 0; m < 5; ++m) fp[m] = 0.5 * (G[m] + alpha * V[m]);
+      for (int m = 0; m < 5; ++m) fm[m] = 0.5 * (G[5 - m] - alpha * V[5 - m]);
+      check(fp);
+      check(fm);
+    }
+  }
+  *label = lab;
+}
+
 // ------------------------------------------------------------ MR operators
 // Prediction, Eq. (Prediction) with the Q-terms of the appendix.  c0 = -22/128,
 // c1 = 3/128, c_pq = c_p c_q, c_rpq = c_r c_p c_q, where index 0 belongs to an
@@ -1191,6 +1287,17 @@ void orc_face_flux(const double* U6, int32_t d, double g, double B, int32_t mode
   for (int m = 0; m < 6; ++m)
     for (int v = 0; v < 5; ++v) U[m][v] = U6[m * 5 + v];
   face_flux(U, d, g, B, mode, F);
+}
+
+// Selector features [15] and label of one face (six lab-frame cells [6][5]).
+void orc_face_features(const double* U6, int32_t d, double g, double B, double tau_lab, double* feats,
+                       int32_t* label) {
+  double U[6][5];
+  for (int m = 0; m < 6; ++m)
+    for (int v = 0; v < 5; ++v) U[m][v] = U6[m * 5 + v];
+  int lab = 0;
+  face_features(U, d, g, B, tau_lab, feats, &lab);
+  *label = lab;
 }
 
 // Child `ch` (bit 0 x, bit 1 y, bit 2 z) predicted over its whole stored range

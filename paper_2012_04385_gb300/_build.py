@@ -27,6 +27,7 @@ UNITS = {
     "kern_f32.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "noalloc.cu": ["-fmad=false"],
     "peaks.cu": ["-fmad=true"],
+    "learned.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
 }
 
 

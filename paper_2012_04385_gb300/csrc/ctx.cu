@@ -75,6 +75,7 @@ struct mrb_ctx {
   unsigned long long* d_smax = nullptr;
   int8_t* d_tags = nullptr;
   int* d_status = nullptr;
+  unsigned long long* d_lin = nullptr;
   std::vector<void*> allocs;
 
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -393,7 +394,7 @@ int check_config(const mrb_config* cfg) {
   return MRB_OK;
 }
 
-constexpr size_t slot_doubles() { return 2 * (size_t)SLOT_U + SLOT_N + SLOT_F; }
+constexpr size_t slot_doubles() { return 2 * (size_t)SLOT_U + SLOT_N + SLOT_F + SLOT_SEL / 2; }
 
 }  // namespace
 
@@ -402,7 +403,7 @@ extern "C" {
 size_t mrb_pool_bytes(const mrb_config* cfg, int64_t n_slots) {
   if (check_config(cfg) != MRB_OK || n_slots <= 0) return 0;
   const size_t n = (size_t)n_slots;
-  return align256(n * SLOT_U * 8) * 2 + align256(n * SLOT_N * 8) + align256(n * SLOT_F * 8);
+  return align256(n * SLOT_U * 8) * 2 + align256(n * SLOT_N * 8) + align256(n * SLOT_F * 8) + align256(n * SLOT_SEL * 4);
 }
 
 int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ctx** out) {
@@ -439,6 +440,8 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     c->P.un = (double*)q;
     q += align256(n * SLOT_N * 8);
     c->P.face = (double*)q;
+    q += align256(n * SLOT_F * 8);
+    c->P.sel = (uint32_t*)q;
     Phys& p = c->phys;
     p.gamma = cfg->gamma;
     p.B = cfg->B;
@@ -454,6 +457,8 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     p.n_inst = cfg->n_instances;
     p.recon = cfg->recon;
     p.precision = cfg->precision;
+    p.mlp = (const float*)cfg->mlp_weights;
+    p.mlp_tau = (float)cfg->mlp_tau;
     c->max_lmax = 0;
     for (int i = 0; i < cfg->n_instances; ++i) c->max_lmax = std::max(c->max_lmax, (int)cfg->lmax[i]);
     c->d_keys = c->dalloc<uint64_t>(n);
@@ -475,7 +480,10 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     c->d_partial = c->dalloc<double>(5 * n);
     c->d_tags = c->dalloc<int8_t>(n);
     c->d_status = c->dalloc<int>(1);
+    c->d_lin = c->dalloc<unsigned long long>(2);
+    p.lin_count = c->d_lin;
     p.lmax = c->d_lmax;
+    CK(cudaMemsetAsync(c->d_lin, 0, 2 * sizeof(unsigned long long), c->st));
     CK(cudaMemcpyAsync(c->d_lmax, cfg->lmax, sizeof(int32_t) * cfg->n_instances, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
     CK(cudaMemsetAsync(c->d_cnt, 0, sizeof(int32_t) * CNT_SIZE, c->st));
@@ -656,6 +664,29 @@ int mrb_step(mrb_ctx* c, int32_t nsteps, double* dt_hist_dev) {
         }
       }
     }
+  });
+}
+
+int mrb_face_samples(mrb_ctx* c, float tau_lab, int64_t stride, float* feats_dev, uint8_t* labels_dev,
+                     int64_t* where_dev, int64_t cap, int64_t* n_out) {
+  return guarded(c, [&] {
+    if (stride < 1 || cap < 0 || (cap > 0 && (!feats_dev || !labels_dev))) throw Err(MRB_EINVAL, "bad arguments");
+    const int64_t faces = (int64_t)c->n_leaves() * 3 * 17 * 256;
+    const int64_t n = std::min<int64_t>(cap, (faces + stride - 1) / stride);
+    if (n > 0) launch_face_samples(c->topo(), c->phys, c->P, c->cur, tau_lab, stride, feats_dev, labels_dev, where_dev, n,
+                                   c->st);
+    if (n_out) *n_out = n;
+  });
+}
+
+int mrb_learned_stats(mrb_ctx* c, int64_t* linear_faces, int64_t* evaluated_faces, int32_t reset) {
+  return guarded(c, [&] {
+    unsigned long long h[2] = {0, 0};
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemcpy(h, c->d_lin, sizeof(h), cudaMemcpyDeviceToHost));
+    if (linear_faces) *linear_faces = (int64_t)h[0];
+    if (evaluated_faces) *evaluated_faces = (int64_t)h[1];
+    if (reset) CK(cudaMemset(c->d_lin, 0, sizeof(h)));
   });
 }
 

@@ -7,24 +7,26 @@
 
 namespace mrb {
 
-template <bool LIN>
+template <int MODE>
 static void launch_stage_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
                              double* rhs_out, cudaStream_t st) {
+  const size_t smem = (MODE == 1) ? SF_SMEM_LEARNED : SF_SMEM;
   static int grid = 0;
   if (grid == 0) {
-    cudaFuncSetAttribute(k_stage_f32<LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SF_SMEM);
+    cudaFuncSetAttribute(k_stage_f32<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_f32<LIN>, SF_THREADS, SF_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_f32<MODE>, SF_THREADS, smem);
     grid = sm_count() * (per_sm < 1 ? 1 : per_sm);
   }
-  k_stage_f32<LIN><<<grid, SF_THREADS, SF_SMEM, st>>>(t, p, pool, cur, stage, dt, rhs_out);
+  k_stage_f32<MODE><<<grid, SF_THREADS, smem, st>>>(t, p, pool, cur, stage, dt, rhs_out);
   ++g_kernel_launches;
 }
 
 void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
                        double* rhs_out, cudaStream_t st) {
-  if (p.recon == 2) launch_stage_f32<true>(t, p, pool, cur, stage, dt, rhs_out, st);
-  else launch_stage_f32<false>(t, p, pool, cur, stage, dt, rhs_out, st);
+  if (p.recon == 2) launch_stage_f32<2>(t, p, pool, cur, stage, dt, rhs_out, st);
+  else if (p.recon == 1 && p.mlp) launch_stage_f32<1>(t, p, pool, cur, stage, dt, rhs_out, st);
+  else launch_stage_f32<0>(t, p, pool, cur, stage, dt, rhs_out, st);
 }
 
 void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st) {

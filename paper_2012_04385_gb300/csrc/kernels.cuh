@@ -39,6 +39,9 @@ struct Phys {
   int recon;
   int has_grav;
   int precision;           // 0 FP64, 1 FP32 bulk (MRB_FP64 / MRB_FP32_ACC64)
+  float mlp_tau;           // learned selector: linear reconstruction when logit < mlp_tau
+  const float* mlp;        // learned selector parameters (device, FP32), or null
+  unsigned long long* lin_count;   // [0] faces sent to linear, [1] faces evaluated
   const int32_t* lmax;     // device [n_inst]
 };
 
@@ -46,6 +49,7 @@ struct Pool {
   double* buf[2];          // stage buffers, [slot][5][24^3]
   double* un;              // u^n, [slot][5][16^3]
   double* face;            // face fluxes, [slot][6][5][16][16]
+  uint32_t* sel;           // learned selector decisions of the current step, [slot][SLOT_SEL]
 };
 
 __device__ __forceinline__ double ldexp_(double x, int e) { return ldexp(x, e); }
@@ -80,6 +84,8 @@ void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int c
 void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, cudaStream_t st);
 void launch_cfl_speeds_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax,
                            int* status, cudaStream_t st);
+void launch_face_samples(const Topo& t, const Phys& p, const Pool& pool, int cur, float tau_lab, int64_t stride,
+                         float* feats, uint8_t* labels, int64_t* where, int64_t cap, cudaStream_t st);
 int sm_count();
 // kernel launches issued by this process (host-side counter, bumped by every launch_* wrapper)
 extern long long g_kernel_launches;

@@ -17,6 +17,7 @@
 
 #include "convert.cuh"
 #include "kernels.cuh"
+#include "learned.cuh"
 
 namespace mrb {
 
@@ -27,6 +28,9 @@ constexpr int SF_REG = NB * NB * (SF_TZ + 6);            // largest stencil regi
 constexpr int SF_FMAX = NB * NB * (SF_TZ + 1);           // largest face count (z): 1280
 constexpr int SF_NREC = 7;                                // rho, u, v, w, p, E, c
 constexpr size_t SF_SMEM = sizeof(float) * (SF_NREC * SF_REG + NV * SF_FMAX);
+// learned selector scratch: B fragments, per-warp feature rows and logits
+constexpr size_t SF_SMEM_LEARNED = SF_SMEM + sizeof(uint32_t) * (FRAG_N + (SF_THREADS / 32) * 32 * 9) +
+                                   sizeof(float) * SF_THREADS;
 
 __device__ __constant__ static const double kSfA[3] = {0.0, 0.75, 1.0 / 3.0};
 __device__ __constant__ static const double kSfB[3] = {1.0, 0.25, 2.0 / 3.0};
@@ -64,92 +68,139 @@ __device__ __forceinline__ float rec5(float a, float b, float c, float d, float 
   return LIN ? linear5f(a, b, c, d, e) : weno5f(a, b, c, d, e);
 }
 
-// Face flux between stencil cells 2 and 3 (cells at S index c0 + m*st, m = 0..5)
-// along D, from the FP32 records; result in the lab frame.
-template <int D, bool LIN>
-__device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, float gm1, float F[5]) {
+// Roe average of the face between the records at cl and cr (rotated frame of
+// direction D) and the cell eigenvalue ingredients of the two face cells.
+struct RoeF {
+  float un, ut1, ut2, H, q2, c, ic, b1, b2, hb1, unL, unR, cL, cR;
+};
+
+template <int D>
+__device__ __forceinline__ RoeF roe_f32(const float* __restrict__ S, int cl, int cr, float gm1) {
   constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
-  float Ur[6][5], Fr[6][5];
-#pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    const int c = c0 + m * st;
-    const float r = S[c], un = S[(1 + A0) * SF_REG + c], u1 = S[(1 + A1) * SF_REG + c], u2 = S[(1 + A2) * SF_REG + c];
-    const float p = S[4 * SF_REG + c], E = S[5 * SF_REG + c];
-    const float mn = r * un;
-    Ur[m][0] = r;
-    Ur[m][1] = mn;
-    Ur[m][2] = r * u1;
-    Ur[m][3] = r * u2;
-    Ur[m][4] = E;
-    Fr[m][0] = mn;
-    Fr[m][1] = fmaf(mn, un, p);
-    Fr[m][2] = mn * u1;
-    Fr[m][3] = mn * u2;
-    Fr[m][4] = un * (E + p);
-  }
-  const int cl = c0 + 2 * st, cr = c0 + 3 * st;
+  RoeF e;
   const float rL = S[cl], rR = S[cr];
-  const float unL = S[(1 + A0) * SF_REG + cl], unR = S[(1 + A0) * SF_REG + cr];
-  const float cL = S[6 * SF_REG + cl], cR = S[6 * SF_REG + cr];
-  // Roe average: sqrt(rho) weights, H = (E + p) / rho
+  e.unL = S[(1 + A0) * SF_REG + cl];
+  e.unR = S[(1 + A0) * SF_REG + cr];
+  e.cL = S[6 * SF_REG + cl];
+  e.cR = S[6 * SF_REG + cr];
+  // sqrt(rho) weights, H = (E + p) / rho
   const float rsL = rsqrtf(rL), rsR = rsqrtf(rR);
   const float sL = rL * rsL, sR = rR * rsR;
   const float iden = frcp(sL + sR);
-  const float un = fmaf(sL, unL, sR * unR) * iden;
-  const float ut1 = fmaf(sL, S[(1 + A1) * SF_REG + cl], sR * S[(1 + A1) * SF_REG + cr]) * iden;
-  const float ut2 = fmaf(sL, S[(1 + A2) * SF_REG + cl], sR * S[(1 + A2) * SF_REG + cr]) * iden;
-  const float H = fmaf(Ur[2][4] + S[4 * SF_REG + cl], rsL, (Ur[3][4] + S[4 * SF_REG + cr]) * rsR) * iden;
-  const float q2 = fmaf(un, un, fmaf(ut1, ut1, ut2 * ut2));
-  const float c2 = gm1 * fmaf(-0.5f, q2, H);
-  const float ic = rsqrtf(c2);
-  const float c = c2 * ic;
-  const float b1 = gm1 * ic * ic;
-  const float b2 = 0.5f * b1 * q2;
-  const float hb1 = 0.5f * b1;
+  e.un = fmaf(sL, e.unL, sR * e.unR) * iden;
+  e.ut1 = fmaf(sL, S[(1 + A1) * SF_REG + cl], sR * S[(1 + A1) * SF_REG + cr]) * iden;
+  e.ut2 = fmaf(sL, S[(1 + A2) * SF_REG + cl], sR * S[(1 + A2) * SF_REG + cr]) * iden;
+  e.H = fmaf(S[5 * SF_REG + cl] + S[4 * SF_REG + cl], rsL, (S[5 * SF_REG + cr] + S[4 * SF_REG + cr]) * rsR) * iden;
+  e.q2 = fmaf(e.un, e.un, fmaf(e.ut1, e.ut1, e.ut2 * e.ut2));
+  const float c2 = gm1 * fmaf(-0.5f, e.q2, e.H);
+  e.ic = rsqrtf(c2);
+  e.c = c2 * e.ic;
+  e.b1 = gm1 * e.ic * e.ic;
+  e.b2 = 0.5f * e.b1 * e.q2;
+  e.hb1 = 0.5f * e.b1;
+  return e;
+}
+
+// Left eigenvector k (rotated frame): rows 0 and 4 the acoustic fields, 1 the
+// entropy field, 2 and 3 the shear fields.
+__device__ __forceinline__ void lrow_f32(const RoeF& e, int k, float l[5]) {
+  if (k == 0 || k == 4) {
+    const float sg = (k == 0) ? 1.f : -1.f;
+    l[0] = fmaf(0.5f * sg * e.un, e.ic, 0.5f * e.b2);
+    l[1] = fmaf(-e.hb1, e.un, -0.5f * sg * e.ic);
+    l[2] = -e.hb1 * e.ut1;
+    l[3] = -e.hb1 * e.ut2;
+    l[4] = e.hb1;
+  } else if (k == 1) {
+    l[0] = 1.f - e.b2;
+    l[1] = e.b1 * e.un;
+    l[2] = e.b1 * e.ut1;
+    l[3] = e.b1 * e.ut2;
+    l[4] = -e.b1;
+  } else {
+    l[0] = -((k == 2) ? e.ut1 : e.ut2);
+    l[1] = 0.f;
+    l[2] = (k == 2) ? 1.f : 0.f;
+    l[3] = (k == 3) ? 1.f : 0.f;
+    l[4] = 0.f;
+  }
+}
+
+// Rotated conserved state and physical flux of the record at c.
+template <int D>
+__device__ __forceinline__ void cell_uf(const float* __restrict__ S, int c, float U[5], float F[5]) {
+  constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
+  const float r = S[c], un = S[(1 + A0) * SF_REG + c], u1 = S[(1 + A1) * SF_REG + c], u2 = S[(1 + A2) * SF_REG + c];
+  const float p = S[4 * SF_REG + c], E = S[5 * SF_REG + c];
+  const float mn = r * un;
+  U[0] = r;
+  U[1] = mn;
+  U[2] = r * u1;
+  U[3] = r * u2;
+  U[4] = E;
+  F[0] = mn;
+  F[1] = fmaf(mn, un, p);
+  F[2] = mn * u1;
+  F[3] = mn * u2;
+  F[4] = un * (E + p);
+}
+
+__device__ __forceinline__ float rec5_rt(bool lin, float a, float b, float c, float d, float e) {
+  return lin ? linear5f(a, b, c, d, e) : weno5f(a, b, c, d, e);
+}
+
+// Face flux between stencil cells 2 and 3 (cells at S index c0 + m*st, m = 0..5)
+// along D, from the FP32 records; result in the lab frame.  MODE 0: WENO5,
+// 2: linear, 1: per-face choice `lin` for fields 0, 1, 4 (learned selector;
+// the shear fields keep WENO5).
+template <int D, int MODE>
+__device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, float gm1, bool lin,
+                                              float F[5]) {
+  constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
+  float Ur[6][5], Fr[6][5];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) cell_uf<D>(S, c0 + m * st, Ur[m], Fr[m]);
+  const RoeF e = roe_f32<D>(S, c0 + 2 * st, c0 + 3 * st, gm1);
   float Fh0 = 0.f, Fh1 = 0.f, Fh2 = 0.f, Fh3 = 0.f, Fh4 = 0.f;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
+    // the selector decides for the acoustic and entropy fields; shear fields keep WENO5
+    const bool use_lin = (MODE == 2) || (MODE == 1 && lin && (k == 0 || k == 1 || k == 4));
     float G[6], V[6];
-    float lL, lR, lt;
-    if (k == 0 || k == 4) {
-      const float sg = (k == 0) ? 1.f : -1.f;
-      const float l0 = fmaf(0.5f * sg * un, ic, 0.5f * b2), l1 = fmaf(-hb1, un, -0.5f * sg * ic);
-      const float l2 = -hb1 * ut1, l3 = -hb1 * ut2, l4 = hb1;
-#pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        V[m] = fmaf(l0, Ur[m][0], fmaf(l1, Ur[m][1], fmaf(l2, Ur[m][2], fmaf(l3, Ur[m][3], l4 * Ur[m][4]))));
-        G[m] = fmaf(l0, Fr[m][0], fmaf(l1, Fr[m][1], fmaf(l2, Fr[m][2], fmaf(l3, Fr[m][3], l4 * Fr[m][4]))));
-      }
-      lL = fmaf(-sg, cL, unL);
-      lR = fmaf(-sg, cR, unR);
-      lt = fmaf(-sg, c, un);
-    } else if (k == 1) {
-      const float l0 = 1.f - b2, l1 = b1 * un, l2 = b1 * ut1, l3 = b1 * ut2, l4 = -b1;
-#pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        V[m] = fmaf(l0, Ur[m][0], fmaf(l1, Ur[m][1], fmaf(l2, Ur[m][2], fmaf(l3, Ur[m][3], l4 * Ur[m][4]))));
-        G[m] = fmaf(l0, Fr[m][0], fmaf(l1, Fr[m][1], fmaf(l2, Fr[m][2], fmaf(l3, Fr[m][3], l4 * Fr[m][4]))));
-      }
-      lL = unL;
-      lR = unR;
-      lt = un;
-    } else {
-      const float ut = (k == 2) ? ut1 : ut2;
+    float l[5];
+    lrow_f32(e, k, l);
+    if (k == 2 || k == 3) {
       const int j = (k == 2) ? 2 : 3;
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
-        V[m] = fmaf(-ut, Ur[m][0], Ur[m][j]);
-        G[m] = fmaf(-ut, Fr[m][0], Fr[m][j]);
+        V[m] = fmaf(l[0], Ur[m][0], Ur[m][j]);
+        G[m] = fmaf(l[0], Fr[m][0], Fr[m][j]);
       }
-      lL = unL;
-      lR = unR;
-      lt = un;
+    } else {
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        V[m] = fmaf(l[0], Ur[m][0], fmaf(l[1], Ur[m][1], fmaf(l[2], Ur[m][2], fmaf(l[3], Ur[m][3], l[4] * Ur[m][4]))));
+        G[m] = fmaf(l[0], Fr[m][0], fmaf(l[1], Fr[m][1], fmaf(l[2], Fr[m][2], fmaf(l[3], Fr[m][3], l[4] * Fr[m][4]))));
+      }
+    }
+    float lL, lR, lt;
+    if (k == 0 || k == 4) {
+      const float sg = (k == 0) ? 1.f : -1.f;
+      lL = fmaf(-sg, e.cL, e.unL);
+      lR = fmaf(-sg, e.cR, e.unR);
+      lt = fmaf(-sg, e.c, e.un);
+    } else {
+      lL = e.unL;
+      lR = e.unR;
+      lt = e.un;
     }
     float gh;
     if (lL > 0.f && lR > 0.f && lt > 0.f) {
-      gh = rec5<LIN>(G[0], G[1], G[2], G[3], G[4]);
+      gh = (MODE == 1) ? rec5_rt(use_lin, G[0], G[1], G[2], G[3], G[4])
+                       : (use_lin ? linear5f(G[0], G[1], G[2], G[3], G[4]) : weno5f(G[0], G[1], G[2], G[3], G[4]));
     } else if (lL < 0.f && lR < 0.f && lt < 0.f) {
-      gh = rec5<LIN>(G[5], G[4], G[3], G[2], G[1]);
+      gh = (MODE == 1) ? rec5_rt(use_lin, G[5], G[4], G[3], G[2], G[1])
+                       : (use_lin ? linear5f(G[5], G[4], G[3], G[2], G[1]) : weno5f(G[5], G[4], G[3], G[2], G[1]));
     } else {
       const float ha = 0.5f * fmaxf(fabsf(lL), fabsf(lR));
       float fp[6], fm[6];
@@ -158,29 +209,34 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
         fp[m] = fmaf(0.5f, G[m], ha * V[m]);
         fm[m] = fmaf(0.5f, G[m], -ha * V[m]);
       }
-      gh = rec5<LIN>(fp[0], fp[1], fp[2], fp[3], fp[4]) + rec5<LIN>(fm[5], fm[4], fm[3], fm[2], fm[1]);
+      if (MODE == 1)
+        gh = rec5_rt(use_lin, fp[0], fp[1], fp[2], fp[3], fp[4]) + rec5_rt(use_lin, fm[5], fm[4], fm[3], fm[2], fm[1]);
+      else if (use_lin)
+        gh = linear5f(fp[0], fp[1], fp[2], fp[3], fp[4]) + linear5f(fm[5], fm[4], fm[3], fm[2], fm[1]);
+      else
+        gh = weno5f(fp[0], fp[1], fp[2], fp[3], fp[4]) + weno5f(fm[5], fm[4], fm[3], fm[2], fm[1]);
     }
     // F_hat = R g_hat, columns r0 = (1, u-c, ut1, ut2, H-uc), r1 = (1, u, ut1, ut2, q2/2),
     // r2 = (0, 0, 1, 0, ut1), r3 = (0, 0, 0, 1, ut2), r4 = (1, u+c, ut1, ut2, H+uc)
     if (k == 0 || k == 4) {
       const float sg = (k == 0) ? -1.f : 1.f;
       Fh0 += gh;
-      Fh1 = fmaf(fmaf(sg, c, un), gh, Fh1);
-      Fh2 = fmaf(ut1, gh, Fh2);
-      Fh3 = fmaf(ut2, gh, Fh3);
-      Fh4 = fmaf(fmaf(sg * un, c, H), gh, Fh4);
+      Fh1 = fmaf(fmaf(sg, e.c, e.un), gh, Fh1);
+      Fh2 = fmaf(e.ut1, gh, Fh2);
+      Fh3 = fmaf(e.ut2, gh, Fh3);
+      Fh4 = fmaf(fmaf(sg * e.un, e.c, e.H), gh, Fh4);
     } else if (k == 1) {
       Fh0 += gh;
-      Fh1 = fmaf(un, gh, Fh1);
-      Fh2 = fmaf(ut1, gh, Fh2);
-      Fh3 = fmaf(ut2, gh, Fh3);
-      Fh4 = fmaf(0.5f * q2, gh, Fh4);
+      Fh1 = fmaf(e.un, gh, Fh1);
+      Fh2 = fmaf(e.ut1, gh, Fh2);
+      Fh3 = fmaf(e.ut2, gh, Fh3);
+      Fh4 = fmaf(0.5f * e.q2, gh, Fh4);
     } else if (k == 2) {
       Fh2 += gh;
-      Fh4 = fmaf(ut1, gh, Fh4);
+      Fh4 = fmaf(e.ut1, gh, Fh4);
     } else {
       Fh3 += gh;
-      Fh4 = fmaf(ut2, gh, Fh4);
+      Fh4 = fmaf(e.ut2, gh, Fh4);
     }
   }
   F[0] = Fh0;
@@ -188,6 +244,41 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
   F[1 + A1] = Fh2;
   F[1 + A2] = Fh3;
   F[4] = Fh4;
+}
+
+// Selector features of the face between records c0+2st and c0+3st: for the
+// characteristic fields k = 0, 1, 4, the compressed consecutive variations
+// s (|dg| + alpha_k |dv|) of the characteristic fluxes g = L_k F(U_m) and
+// variables v = L_k U_m over the six stencil cells (alpha_k the field's LLF
+// speed, s the sign of dg, of dv where dg is zero).
+template <int D>
+__device__ __forceinline__ void face_features_f32(const float* __restrict__ S, int c0, int st, const RoeF& e,
+                                                  float f[15]) {
+  float l[3][5], alpha[3];
+  lrow_f32(e, 0, l[0]);
+  lrow_f32(e, 1, l[1]);
+  lrow_f32(e, 4, l[2]);
+  alpha[0] = fmaxf(fabsf(e.unL - e.cL), fabsf(e.unR - e.cR));
+  alpha[1] = fmaxf(fabsf(e.unL), fabsf(e.unR));
+  alpha[2] = fmaxf(fabsf(e.unL + e.cL), fabsf(e.unR + e.cR));
+  float pg[3], pv[3];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    float U[5], F[5];
+    cell_uf<D>(S, c0 + m * st, U, F);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float gq = fmaf(l[q][0], F[0], fmaf(l[q][1], F[1], fmaf(l[q][2], F[2], fmaf(l[q][3], F[3], l[q][4] * F[4]))));
+      const float vq = fmaf(l[q][0], U[0], fmaf(l[q][1], U[1], fmaf(l[q][2], U[2], fmaf(l[q][3], U[3], l[q][4] * U[4]))));
+      if (m > 0) {
+        const float dg = gq - pg[q], dv = vq - pv[q];
+        const float mag = fmaf(alpha[q], fabsf(dv), fabsf(dg));
+        f[5 * q + m - 1] = compress_diff((dg != 0.f) ? copysignf(mag, dg) : copysignf(mag, dv));
+      }
+      pg[q] = gq;
+      pv[q] = vq;
+    }
+  }
 }
 
 // Stencil region of direction D for the slab at z0 -> FP32 records in S.
@@ -217,16 +308,45 @@ __device__ __forceinline__ void load_region_f32(const double* __restrict__ u, fl
   }
 }
 
-template <int D, bool LIN>
+// Learned-selector state of a CTA (MODE 1 only).
+struct LearnedCtx {
+  const float* P;            // FP32 parameters (biases read from here)
+  const uint32_t* frag;      // BF16 B fragments in shared memory
+  uint32_t* rows;            // per-warp feature rows
+  float* logit;              // per-warp logits
+  float tau;                 // linear when logit < tau
+  unsigned long long* count; // [0] faces sent to linear, [1] faces evaluated (nullable)
+  uint32_t* bits;            // this block's decision words (SLOT_SEL)
+  bool evaluate;             // stage 0: run the MLP and store; later stages: reuse
+  float z0;                  // the network's logit for all-zero features
+};
+
+// True when the six stencil records are identical, in which case every
+// selector feature is exactly zero.
+__device__ __forceinline__ bool stencil_flat(const float* __restrict__ S, int c0, int st) {
+  bool flat = true;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float a = S[q * SF_REG + c0];
+#pragma unroll
+    for (int m = 1; m < 6; ++m) flat = flat && (S[q * SF_REG + c0 + m * st] == a);
+  }
+  return flat;
+}
+
+template <int D, int MODE>
 __device__ __forceinline__ void sweep_f32(const double* __restrict__ u, double* __restrict__ fb, float* __restrict__ S,
                                           float* __restrict__ Fs, int z0, float g, float B, float gm1,
-                                          float (&acc)[SF_TZ][NV]) {
+                                          float (&acc)[SF_TZ][NV], const LearnedCtx& L) {
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   load_region_f32<D>(u, S, z0, g, B, gm1);
   __syncthreads();
   constexpr int nf = (D == 2) ? NB * NB * (SF_TZ + 1) : 17 * 16 * SF_TZ;
   constexpr int st = (D == 0) ? 1 : (D == 1 ? 16 : 256);
-  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+  const int nfr = (MODE == 1) ? ((nf + blockDim.x - 1) / blockDim.x) * blockDim.x : nf;
+  for (int f0 = threadIdx.x; f0 < nfr; f0 += blockDim.x) {
+    const bool act = f0 < nf;
+    const int f = act ? f0 : 0;
     int fa, c0, ta, tb;
     if (D == 0) {
       fa = f % 17;
@@ -248,8 +368,45 @@ __device__ __forceinline__ void sweep_f32(const double* __restrict__ u, double* 
       ta = i;
       tb = j;
     }
+    bool lin = false;
+    if (MODE == 1) {
+      // decision word of this warp's 32 consecutive faces
+      constexpr int doff = (D == 0) ? 0 : (D == 1 ? 34 : 68);
+      uint32_t* word = L.bits + (z0 / SF_TZ) * 108 + doff + (f0 >> 5);
+      if (L.evaluate) {
+        // flat stencils have all-zero features, whose logit z0 is known; the
+        // warp runs the tensor-core MLP only when one of its faces is not flat
+        const bool flat = !act || stencil_flat(S, c0, st);
+        float z = L.z0;
+        if (!__all_sync(0xffffffffu, flat)) {
+          float fe[15];
+          if (flat) {
+#pragma unroll
+            for (int q = 0; q < 15; ++q) fe[q] = 0.f;
+          } else {
+            const RoeF e = roe_f32<D>(S, c0 + 2 * st, c0 + 3 * st, gm1);
+            face_features_f32<D>(S, c0, st, e, fe);
+          }
+          const int wid = threadIdx.x >> 5;
+          mlp_put_row(L.rows + wid * 32 * 9, fe);
+          z = mlp_warp_logit(L.P, L.frag, L.rows + wid * 32 * 9, L.logit + wid * 32);
+        }
+        lin = act && (z < L.tau);
+        const unsigned bl = __ballot_sync(0xffffffffu, lin), ba = __ballot_sync(0xffffffffu, act);
+        if ((threadIdx.x & 31) == 0) {
+          *word = bl;
+          if (L.count) {
+            atomicAdd(&L.count[0], (unsigned long long)__popc(bl));
+            atomicAdd(&L.count[1], (unsigned long long)__popc(ba));
+          }
+        }
+      } else {
+        lin = act && ((*word >> (threadIdx.x & 31)) & 1u);
+      }
+    }
+    if (!act) continue;
     float F[5];
-    face_flux_f32<D, LIN>(S, c0, st, gm1, F);
+    face_flux_f32<D, MODE>(S, c0, st, gm1, lin, F);
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fs[v * SF_FMAX + f] = F[v];
     const int gface = (D == 2) ? z0 + fa : fa;
@@ -275,7 +432,7 @@ __device__ __forceinline__ void sweep_f32(const double* __restrict__ u, double* 
   __syncthreads();
 }
 
-template <bool LIN>
+template <int MODE>
 __global__ void __launch_bounds__(SF_THREADS, 2)
     k_stage_f32(Topo t, Phys p, Pool pool, int cur, int stage, const double* __restrict__ dt,
                 double* __restrict__ rhs_out) {
@@ -287,16 +444,39 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
   double* __restrict__ dst = pool.buf[cur ^ 1];
   const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+  LearnedCtx L{nullptr, nullptr, nullptr, nullptr, 0.f, nullptr, nullptr, stage == 0, 0.f};
+  if (MODE == 1) {
+    uint32_t* frag = reinterpret_cast<uint32_t*>(Fs + NV * SF_FMAX);
+    L.P = p.mlp;
+    L.frag = frag;
+    L.rows = frag + FRAG_N;
+    L.logit = reinterpret_cast<float*>(L.rows + (SF_THREADS / 32) * 32 * 9);
+    L.tau = p.mlp_tau;
+    L.count = p.lin_count;
+    mlp_stage_fragments(p.mlp, frag);
+    __syncthreads();
+    // logit of all-zero features (same value in every lane)
+    if (threadIdx.x < 32) {
+      const float zero[15] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      mlp_put_row(L.rows, zero);
+      const float z = mlp_warp_logit(L.P, L.frag, L.rows, L.logit);
+      if (threadIdx.x == 0) L.logit[SF_THREADS - 1] = z;
+    }
+    __syncthreads();
+    L.z0 = L.logit[SF_THREADS - 1];
+    __syncthreads();
+  }
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int li = w / SF_NSLAB, z0 = (w % SF_NSLAB) * SF_TZ;
     const int node = t.leaves[li];
     const int slot = t.slot[node];
     const double* __restrict__ u = src + (size_t)slot * SLOT_U;
     double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
+    if (MODE == 1) L.bits = pool.sel + (size_t)slot * SLOT_SEL;
     float acc[SF_TZ][NV];
-    sweep_f32<0, LIN>(u, fb, S, Fs, z0, g, B, gm1, acc);
-    sweep_f32<1, LIN>(u, fb, S, Fs, z0, g, B, gm1, acc);
-    sweep_f32<2, LIN>(u, fb, S, Fs, z0, g, B, gm1, acc);
+    sweep_f32<0, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L);
+    sweep_f32<1, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L);
+    sweep_f32<2, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L);
     const double dx = ldexp(p.dx0, -t.level[node]);
     const double idx_ = 1.0 / dx;
     const double h = dt ? dt[t.inst[node]] : 0.0;

@@ -90,6 +90,11 @@ def lib():
                 "mrb_profile_read": (ci, [vp, vp, vp, vp]),
                 "mrb_block_sums_noalloc": (ci, [vp, i64, vp, ctypes.c_double, vp, vp]),
                 "mrb_measure_peaks": (ci, [vp, i32]),
+                "mrb_face_samples": (ci, [vp, ctypes.c_float, i64, vp, vp, vp, i64, vp]),
+                "mrb_learned_stats": (ci, [vp, vp, vp, i32]),
+                "mrb_mlp_logits": (ci, [vp, vp, i64, vp, vp]),
+                "mrb_mlp_train_step": (ci, [vp, vp, vp, i32, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp, vp, vp,
+                                            vp]),
                 "mrb_status": (ci, [vp]),
                 "mrb_sync": (ci, [vp]),
                 "mrb_destroy": (ci, [vp]),
@@ -145,6 +150,48 @@ def measure_peaks() -> dict:
     return {k: float(v) for k, v in zip(keys, out)}
 
 
+MLP_NPARAM = 1601
+MLP_WORK_FLOATS = 512 * (MLP_NPARAM + 1)
+
+
+def mlp_logits(params, feats, stream=None):
+    """Selector logits (tensor cores) of feats [n][16] (float32, device)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    n = feats.shape[0]
+    out = torch.empty(max(n, 1), dtype=torch.float32, device=feats.device)
+    rc = lib().mrb_mlp_logits(params.data_ptr(), feats.data_ptr(), n, out.data_ptr(), st.cuda_stream)
+    if rc != MRB_OK:
+        raise MrbError(rc, "mrb_mlp_logits failed")
+    return out[:n]
+
+
+class MlpTrainer:
+    """Adam state and scratch for mrb_mlp_train_step."""
+
+    def __init__(self, params, device="cuda"):
+        import torch
+        self.torch = torch
+        self.params = params
+        self.m = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=device)
+        self.v = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=device)
+        self.work = torch.empty(MLP_WORK_FLOATS, dtype=torch.float32, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.t = 0
+
+    def step(self, feats, labels, pos_weight=1.0, lr=1e-3, grad=None):
+        st = self.torch.cuda.current_stream()
+        if lr > 0:
+            self.t += 1
+        rc = lib().mrb_mlp_train_step(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), max(self.t, 1),
+                                      feats.data_ptr(), labels.data_ptr(), feats.shape[0], float(pos_weight),
+                                      float(lr), self.work.data_ptr(), self.loss.data_ptr(),
+                                      grad.data_ptr() if grad is not None else None, st.cuda_stream)
+        if rc != MRB_OK:
+            raise MrbError(rc, "mrb_mlp_train_step failed")
+        return self.loss
+
+
 def pool_bytes(cfg: RunConfig, n_slots: int) -> int:
     c = make_config(cfg)
     return int(lib().mrb_pool_bytes(ctypes.byref(c), int(n_slots)))
@@ -153,13 +200,16 @@ def pool_bytes(cfg: RunConfig, n_slots: int) -> int:
 class Context:
     """An mrb context plus the torch-allocated block pool it lives in."""
 
-    def __init__(self, cfg: RunConfig, n_slots: int, stream=None, device="cuda"):
+    def __init__(self, cfg: RunConfig, n_slots: int, stream=None, device="cuda", mlp_params=None):
         import torch
 
         self.cfg = cfg
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._c = make_config(cfg, self.stream.cuda_stream)
+        self.mlp_params = mlp_params
+        if mlp_params is not None:
+            self._c.mlp_weights = mlp_params.data_ptr()
         nbytes = int(lib().mrb_pool_bytes(ctypes.byref(self._c), int(n_slots)))
         if nbytes == 0:
             raise MrbError(MRB_EINVAL, "invalid configuration")
@@ -312,6 +362,24 @@ class Context:
         n_k = ctypes.c_int64()
         self._rc(lib().mrb_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n_rhs), ctypes.byref(n_k)))
         return float(ms.value), int(n_rhs.value), int(n_k.value)
+
+    def face_samples(self, tau_lab=1e-3, stride=1, cap=None, with_where=False):
+        torch = self.torch
+        faces = self.n_leaves() * 3 * 17 * 256
+        n = (faces + stride - 1) // stride if cap is None else min(cap, (faces + stride - 1) // stride)
+        feats = torch.empty((max(n, 1), 16), dtype=torch.float32, device=self.pool.device)
+        labels = torch.empty(max(n, 1), dtype=torch.uint8, device=self.pool.device)
+        where = torch.empty(max(n, 1), dtype=torch.int64, device=self.pool.device) if with_where else None
+        cnt = ctypes.c_int64()
+        self._rc(lib().mrb_face_samples(self._h, float(tau_lab), int(stride), feats.data_ptr(), labels.data_ptr(),
+                                        where.data_ptr() if where is not None else None, n, ctypes.byref(cnt)))
+        k = int(cnt.value)
+        return feats[:k], labels[:k], (where[:k] if where is not None else None)
+
+    def learned_stats(self, reset=True):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._rc(lib().mrb_learned_stats(self._h, ctypes.byref(a), ctypes.byref(b), int(reset)))
+        return int(a.value), int(b.value)
 
     def status(self) -> int:
         return int(lib().mrb_status(self._h))

@@ -39,7 +39,7 @@ def test_pool_bytes_and_config_checks():
     cfg = I.sod_config()
     b1 = mrb.pool_bytes(cfg, 1)
     b8 = mrb.pool_bytes(cfg, 8)
-    per_slot = (2 * 5 * 24 ** 3 + 5 * 16 ** 3 + 6 * 5 * 256) * 8
+    per_slot = (2 * 5 * 24 ** 3 + 5 * 16 ** 3 + 6 * 5 * 256) * 8 + 432 * 4
     assert b8 >= 8 * per_slot and b8 < 8 * per_slot + 4 * 256
     assert b1 > 0
     bad = I.sod_config(bc=(1, 0, 1, 1, 1, 1))          # periodic on one side only

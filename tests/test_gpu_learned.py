@@ -1,0 +1,132 @@
+"""GPU checks of the learned reconstruction selector against the oracle.
+
+Features and labels of sampled faces against the oracle's FP64 definition,
+gradients of the training kernels against the FP64 reference (same BF16
+roundings), tensor-core logits against the reference forward, one Adam step,
+training progress, and the learned path's accuracy against plain WENO5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_2012_04385_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2012_04385_gb300 import learned, mrb  # noqa: E402
+
+
+def _face_cells(U, li, fid_in_leaf):
+    """Six lab-frame cells [6][5] of a face from a stored block array U [n][5][24][24][24]."""
+    D, canon = fid_in_leaf // 4352, fid_in_leaf % 4352
+    if D == 0:
+        fx, y, z = canon % 17, (canon // 17) % 16, canon // 272
+        cells = [(fx - 3 + m, y, z) for m in range(6)]
+    elif D == 1:
+        x, fy, z = canon % 16, (canon // 16) % 17, canon // 272
+        cells = [(x, fy - 3 + m, z) for m in range(6)]
+    else:
+        x, y, fz = canon % 16, (canon // 16) % 16, canon // 256
+        cells = [(x, y, fz - 3 + m) for m in range(6)]
+    return D, np.array([U[li, :, k + 4, j + 4, i + 4] for (i, j, k) in cells])
+
+
+@pytest.mark.parametrize("ic_name", ["smooth", "rough"])
+def test_features_and_labels_vs_oracle(ic_name):
+    cfg = I.periodic_config(base=(2, 1, 1), precision=I.FP32_ACC64)
+    g = mrb.Context(cfg, 4)
+    k, geo = g.list_blocks()
+    prim = I.ic_random_smooth(cfg, geo) if ic_name == "smooth" else \
+        I.random_states(len(k), seed=3, rho=(1.0, 1.5), p=(1.0, 1.5), vmax=0.3)
+    g.set_state(k, prim)
+    g.fill_halos()
+    f, lab, where = g.face_samples(tau_lab=1e-3, stride=11, with_where=True)
+    f, lab, where = f.cpu().numpy(), lab.cpu().numpy(), where.cpu().numpy()
+    U = g.get_state(k, with_halo=True).cpu().numpy()
+    agree, n = 0, len(where)
+    maxerr = 0.0
+    for s in range(n):
+        li, fid = divmod(int(where[s]), 13056)
+        D, U6 = _face_cells(U, li, fid)
+        fo, lo = oracle.face_features(U6, D, tau_lab=1e-3)
+        maxerr = max(maxerr, np.abs(f[s, :15] - fo).max())
+        agree += int(lo == lab[s])
+    print(ic_name, "samples", n, "max feature error", maxerr, "label agreement", agree / n, "positives", lab.mean())
+    assert maxerr < 1e-2
+    assert agree / n >= 0.97
+
+
+def _rand_batch(n, seed):
+    rng = np.random.default_rng(seed)
+    X = np.zeros((n, 16), np.float32)
+    X[:, :15] = rng.uniform(-1, 1, (n, 15))
+    y = (rng.uniform(size=n) < 0.35).astype(np.uint8)
+    return X, y
+
+
+def test_training_gradient_vs_oracle():
+    X, y = _rand_batch(3000, 1)
+    p0 = learned.init_params(5) + np.random.default_rng(2).normal(0, 0.05, 1601).astype(np.float32)
+    P = torch.from_numpy(p0.copy()).cuda()
+    tr = mrb.MlpTrainer(P)
+    grad = torch.zeros(1601, dtype=torch.float32, device="cuda")
+    loss = tr.step(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), pos_weight=3.0, lr=0.0, grad=grad)
+    gg = grad.cpu().numpy().astype(np.float64)
+    lr_, gr = omlp.loss_and_grad(p0.astype(np.float64), X[:, :15].astype(np.float64), y, pos_weight=3.0, rounded=True)
+    assert abs(float(loss.item()) - lr_) <= 1e-4 * abs(lr_)
+    o = 0
+    for name, shape in omlp.SIZES:
+        m = int(np.prod(shape))
+        a, b = gg[o:o + m], gr[o:o + m]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+        print(name, "rel", rel, "cos", cos)
+        assert rel <= 1e-2 and cos >= 0.999, name
+        o += m
+    # one Adam step matches the reference update given the same gradient
+    P2 = torch.from_numpy(p0.copy()).cuda()
+    tr2 = mrb.MlpTrainer(P2)
+    tr2.step(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), pos_weight=3.0, lr=1e-2)
+    ref, _, _ = omlp.adam(p0.astype(np.float64), gg, np.zeros(1601), np.zeros(1601), 1, lr=1e-2)
+    assert np.abs(P2.cpu().numpy() - ref).max() < 1e-5
+
+
+def test_tensor_core_logits_vs_oracle_forward():
+    X, _ = _rand_batch(1000, 4)
+    p0 = learned.init_params(7)
+    z = mrb.mlp_logits(torch.from_numpy(p0).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    zr, _ = omlp.forward(p0.astype(np.float64), X[:, :15].astype(np.float64), rounded=True)
+    err = np.abs(z - zr)
+    print("logit max abs err", err.max(), "scale", np.abs(zr).max())
+    assert (err <= 2e-2 + 2e-2 * np.abs(zr)).all()
+
+
+def test_training_lowers_loss_and_learned_path_accuracy():
+    data = learned.generate(sod_steps=8, explosion_steps=6, every=3, stride=5, explosion_lmax=2)
+    params, tau, rep = learned.train(data, epochs=6, batch=8192)
+    print(rep)
+    assert rep["losses"][-1] < rep["losses"][0]
+    assert rep["holdout_missed_positives"] <= 0.01
+    # learned FP32 path vs plain WENO5 FP32 path on the Sod tube
+    res = {}
+    for recon in (I.RECON_WENO, I.RECON_LEARNED):
+        cfg = I.sod_config(precision=I.FP32_ACC64, recon=recon, mlp_tau=tau)
+        g = mrb.Context(cfg, 8, mlp_params=params if recon == I.RECON_LEARNED else None)
+        k, geo = g.list_blocks()
+        g.set_state(k, I.ic_sod(cfg, geo))
+        g.learned_stats(reset=True)
+        g.step(20)
+        res[recon] = g.get_state(k).cpu().numpy()
+        if recon == I.RECON_LEARNED:
+            lin, tot = g.learned_stats()
+            print("faces sent to linear:", lin, "of", tot)
+            assert tot > 0 and 0 < lin < tot
+    a, b = res[I.RECON_LEARNED][:, 0], res[I.RECON_WENO][:, 0]
+    l1 = np.abs(a - b).sum() / np.abs(b).sum()
+    print("learned vs WENO L1 density difference:", l1)
+    assert l1 <= 1e-4
