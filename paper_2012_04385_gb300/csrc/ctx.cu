@@ -189,8 +189,8 @@ struct mrb_ctx {
   }
 
   // ---- the steps
-  void fill_halos() {
-    for (int l = 0; l <= max_lmax; ++l) launch_fill_level(topo(), phys, P, cur, l, st);
+  void fill_halos(int leaf_faces_only = 0) {
+    for (int l = 0; l <= max_lmax; ++l) launch_fill_level(topo(), phys, P, cur, l, st, leaf_faces_only);
   }
   void stage(int s, const double* dt) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -217,8 +217,11 @@ struct mrb_ctx {
   }
   void step_stages() {
     launch_cfl(topo(), phys, P, cur, d_smax, d_dt, d_status, st);
+    // the mixed-precision stage kernel reads face neighbours directly, so the
+    // stage fill of leaves is limited to predicted and boundary face regions
+    const int partial = (cfg.precision == MRB_FP32_ACC64) ? 1 : 0;
     for (int s = 0; s < 3; ++s) {
-      fill_halos();
+      fill_halos(partial);
       stage(s, d_dt);
       project();
     }
@@ -328,7 +331,7 @@ struct mrb_ctx {
         pairs.push_back((int32_t)find(pr.second));
       }
       upload_list(pairs);
-      launch_refine_fill(topo(), P, cur, d_list, (int)newpairs.size(), st);
+      launch_refine_fill(topo(), phys, P, cur, d_list, (int)newpairs.size(), st);
       check_launch();
     }
     return n_leaves();

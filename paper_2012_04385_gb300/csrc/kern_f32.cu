@@ -29,9 +29,11 @@ void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, 
   else launch_stage_f32<0>(t, p, pool, cur, stage, dt, rhs_out, st);
 }
 
-void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st) {
-  k_fill_level_t<float><<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, level);
-  ++g_kernel_launches;
+void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st,
+                           int leaf_faces_only) {
+  k_fill_regions_t<float><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, level, leaf_faces_only);
+  k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, level);
+  g_kernel_launches += 2;
 }
 
 void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, cudaStream_t st) {

@@ -94,13 +94,15 @@ void launch_get_state(const Topo& t, const Pool& pool, int cur, const int32_t* n
 }
 
 // ---------------------------------------------------------------- halo fill (mr.cuh)
-void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st) {
+void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st,
+                       int leaf_faces_only) {
   if (p.precision == 1) {
-    launch_fill_level_f32(t, p, pool, cur, level, st);
+    launch_fill_level_f32(t, p, pool, cur, level, st, leaf_faces_only);
     return;
   }
-  k_fill_level_t<double><<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, level);
-  ++g_kernel_launches;
+  k_fill_regions_t<double><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, level, 0);
+  k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, level);
+  g_kernel_launches += 2;
 }
 
 // ---------------------------------------------------------------- RHS + RK (FP64)
@@ -203,35 +205,9 @@ void launch_jump(const Topo& t, const Phys& p, const Pool& pool, int target, int
   ++g_kernel_launches;
 }
 
-// ---------------------------------------------------------------- averaging
-__global__ void k_project_level(Topo t, Pool pool, int buf, int level) {
-  const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
-  double* B = pool.buf[buf];
-  for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
-    const int node = t.lvl_nodes[w];
-    const int c0 = t.child0[node];
-    if (c0 < 0) continue;
-    double* P = B + (size_t)t.slot[node] * SLOT_U;
-    for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
-      const int I = e % 16, J = (e / 16) % 16, K = e / 256;
-      const int o = (I / 8) | ((J / 8) << 1) | ((K / 8) << 2);
-      const double* C = B + (size_t)t.slot[c0 + o] * SLOT_U;
-      const int fi = 2 * (I - 8 * (I / 8)), fj = 2 * (J - 8 * (J / 8)), fk = 2 * (K - 8 * (K / 8));
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const double* u = C + v * NCELL;
-        double c0v = u[sidx(fi, fj, fk)], c1v = u[sidx(fi + 1, fj, fk)];
-        double c2v = u[sidx(fi, fj + 1, fk)], c3v = u[sidx(fi + 1, fj + 1, fk)];
-        double c4v = u[sidx(fi, fj, fk + 1)], c5v = u[sidx(fi + 1, fj, fk + 1)];
-        double c6v = u[sidx(fi, fj + 1, fk + 1)], c7v = u[sidx(fi + 1, fj + 1, fk + 1)];
-        P[v * NCELL + sidx(I, J, K)] = 0.125 * (((c0v + c1v) + (c2v + c3v)) + ((c4v + c5v) + (c6v + c7v)));
-      }
-    }
-  }
-}
-
+// ---------------------------------------------------------------- averaging (mr.cuh)
 void launch_project_level(const Topo& t, const Pool& pool, int buf, int level, cudaStream_t st) {
-  k_project_level<<<sm_count() * 4, 256, 0, st>>>(t, pool, buf, level);
+  k_project_octants<<<sm_count() * 8, 256, 0, st>>>(t, pool, buf, level);
   ++g_kernel_launches;
 }
 
@@ -347,34 +323,12 @@ void launch_delta_tags(const Topo& t, const Phys& p, const Pool& pool, int cur, 
   ++g_kernel_launches;
 }
 
-// ---------------------------------------------------------------- refinement
-// New child: every stored cell predicted from the parent (Eq. Prediction).
-__global__ void __launch_bounds__(256) k_refine_fill(Topo t, Pool pool, int cur, const int32_t* __restrict__ pairs,
-                                                     int n) {
-  double* B = pool.buf[cur];
-  for (int w = blockIdx.x; w < n; w += gridDim.x) {
-    const int child = pairs[2 * w], par = pairs[2 * w + 1];
-    double* U = B + (size_t)t.slot[child] * SLOT_U;
-    const double* P = B + (size_t)t.slot[par] * SLOT_U;
-    const int ch = (int)(t.keys[child] & 7ull);
-    const int cb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
-    for (int e = threadIdx.x; e < 12 * 12 * 12 * NV; e += blockDim.x) {
-      const int v = e / 1728, r = e % 1728;
-      const int pi = 8 * cb[0] - 2 + r % 12, pj = 8 * cb[1] - 2 + (r / 12) % 12, pk = 8 * cb[2] - 2 + r / 144;
-      const QT<double> q = qterms_t<double>(P + v * NCELL, pi, pj, pk);
-#pragma unroll
-      for (int sub = 0; sub < 8; ++sub) {
-        const int a = sub & 1, b = (sub >> 1) & 1, c = (sub >> 2) & 1;
-        const int fi = 2 * (pi - 8 * cb[0]) + a, fj = 2 * (pj - 8 * cb[1]) + b, fk = 2 * (pk - 8 * cb[2]) + c;
-        U[v * NCELL + sidx(fi, fj, fk)] = predict_t<double>(q, a ? -1.0 : 1.0, b ? -1.0 : 1.0, c ? -1.0 : 1.0);
-      }
-    }
-  }
-}
-
-void launch_refine_fill(const Topo& t, const Pool& pool, int cur, const int32_t* pairs, int n, cudaStream_t st) {
+// ---------------------------------------------------------------- refinement (mr.cuh)
+void launch_refine_fill(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* pairs, int n,
+                        cudaStream_t st) {
   if (n <= 0) return;
-  k_refine_fill<<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, pairs, n);
+  if (p.precision == 1) k_refine_fill_t<float><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, pairs, n);
+  else k_refine_fill_t<double><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, pairs, n);
   ++g_kernel_launches;
 }
 

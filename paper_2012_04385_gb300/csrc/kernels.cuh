@@ -62,7 +62,8 @@ void launch_set_cons(const Topo& t, const Pool& pool, int cur, const int32_t* no
                      cudaStream_t st);
 void launch_get_state(const Topo& t, const Pool& pool, int cur, const int32_t* nodes, int n, double* out,
                       int with_halo, cudaStream_t st);
-void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st);
+void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st,
+                       int leaf_faces_only = 0);
 void launch_rhs_rk_f64(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
                        double* rhs_out, cudaStream_t st);
 void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
@@ -75,12 +76,14 @@ void launch_cfl(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigne
                 int* status, cudaStream_t st);
 void launch_delta_tags(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node,
                        int allow_refine, int8_t* tags, double* delta_leaf, int n_leaves_cap, cudaStream_t st);
-void launch_refine_fill(const Topo& t, const Pool& pool, int cur, const int32_t* pairs, int n, cudaStream_t st);
+void launch_refine_fill(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* pairs, int n,
+                        cudaStream_t st);
 void launch_nbr(const Topo& t, const Phys& p, int32_t* nbr_out, int nnodes_cap, cudaStream_t st);
 void launch_sums(const Topo& t, const Phys& p, const Pool& pool, int cur, double* partial, double* out,
                  int nleaves_cap, cudaStream_t st);
 // mixed-precision variants (kern_f32.cu)
-void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st);
+void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st,
+                           int leaf_faces_only);
 void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, cudaStream_t st);
 void launch_cfl_speeds_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax,
                            int* status, cudaStream_t st);

@@ -97,64 +97,81 @@ template <class R> __device__ __forceinline__ R predict_t(const QT<R>& t, R sx, 
 
 __device__ __forceinline__ int sgn_region(int rel) { return rel < 0 ? -1 : (rel >= 8 ? 1 : 0); }
 
-// ---------------------------------------------------------------- halo fill
-// One CTA per node of `level`: copy regions from same-level neighbours,
-// predicted regions from the parent (per parent cell), then the boundary
-// passes x-, x+, y-, y+, z-, z+ on the node's own cells.
+// ---------------------------------------------------------------- halo fill by region
+// Sec. 3 (Fig. MrCommunicationMesh): a halo region facing a same-level node
+// is a copy of its internal cells, one facing no same-level node is predicted
+// from the node's parent (one parent cell, eight fine cells, per step).  One
+// work item per (node, halo region) on a persistent grid; k_fill_bc then
+// applies the boundary conditions.  With leaf_faces_only, leaves get only
+// their predicted face regions (the mixed-precision stage kernel reads face
+// neighbours' cells directly); internal nodes, whose halos feed their
+// children's predictions, are filled completely.
+__device__ __forceinline__ int region_extent(int s) { return s == 0 ? NB : HW; }
+__device__ __forceinline__ int region_start(int s) { return s < 0 ? -HW : (s == 0 ? 0 : NB); }
+
 template <class R>
-__global__ void __launch_bounds__(256) k_fill_level_t(Topo t, Phys p, Pool pool, int cur, int level) {
+__global__ void __launch_bounds__(256) k_fill_regions_t(Topo t, Pool pool, int cur, int level, int leaf_faces_only) {
   const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
   double* buf = pool.buf[cur];
-  __shared__ int kind[27];
-  __shared__ int src_slot[27];
-  __shared__ int any_pred;
-  for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
-    const int node = t.lvl_nodes[w];
-    double* u = buf + (size_t)t.slot[node] * SLOT_U;
+  const int nitems = (end - beg) * 26;
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int node = t.lvl_nodes[beg + w / 26];
+    const int r = w % 26 < 13 ? w % 26 : w % 26 + 1;      // skip the centre
+    const int sx = r % 3 - 1, sy = (r / 3) % 3 - 1, sz = r / 9 - 1;
+    const bool face = (sx != 0) + (sy != 0) + (sz != 0) == 1;
+    const bool partial = leaf_faces_only && t.child0[node] < 0;
+    if (partial && !face) continue;
+    const int nb = t.nbr[(size_t)node * 27 + r];
     const int par = t.parent[node];
-    const double* P = (par >= 0) ? buf + (size_t)t.slot[par] * SLOT_U : nullptr;
-    const int ch = (int)(t.keys[node] & 7ull);
-    __syncthreads();
-    if (threadIdx.x == 0) any_pred = 0;
-    __syncthreads();
-    if (threadIdx.x < 27) {
-      const int nb = t.nbr[(size_t)node * 27 + threadIdx.x];
-      const int kd = (threadIdx.x == 13) ? 0 : ((nb >= 0) ? 1 : ((nb == -1 && P != nullptr) ? 2 : 0));
-      kind[threadIdx.x] = kd;
-      src_slot[threadIdx.x] = (nb >= 0) ? t.slot[nb] : -1;
-      if (kd == 2) atomicOr(&any_pred, 1);
-    }
-    __syncthreads();
-    // copies
-    for (int idx = threadIdx.x; idx < NCELL; idx += blockDim.x) {
-      const int i = idx % NS - HW, j = (idx / NS) % NS - HW, k = idx / (NS * NS) - HW;
-      const int sx = i < 0 ? -1 : (i >= NB ? 1 : 0), sy = j < 0 ? -1 : (j >= NB ? 1 : 0),
-                sz = k < 0 ? -1 : (k >= NB ? 1 : 0);
-      const int r = (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
-      if (kind[r] != 1) continue;
-      const double* s = buf + (size_t)src_slot[r] * SLOT_U;
-      const int off = idx - NB * (sx + NS * sy + NS * NS * sz);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) u[v * NCELL + idx] = s[v * NCELL + off];
-    }
-    // predictions, one parent cell (eight fine cells) per step
-    if (any_pred) {
+    double* u = buf + (size_t)t.slot[node] * SLOT_U;
+    if (nb >= 0) {
+      if (partial) continue;                              // read directly by the stage kernel
+      const double* src = buf + (size_t)t.slot[nb] * SLOT_U;
+      const int ex = region_extent(sx), ey = region_extent(sy), ez = region_extent(sz);
+      const int x0 = region_start(sx), y0 = region_start(sy), z0 = region_start(sz);
+      const int n = ex * ey * ez;
+      for (int e = threadIdx.x; e < n * NV; e += blockDim.x) {
+        const int v = e / n, c = e % n;
+        const int i = x0 + c % ex, j = y0 + (c / ex) % ey, k = z0 + c / (ex * ey);
+        u[v * NCELL + sidx(i, j, k)] = src[v * NCELL + sidx(i - NB * sx, j - NB * sy, k - NB * sz)];
+      }
+    } else if (nb == -1 && par >= 0) {
+      const double* P = buf + (size_t)t.slot[par] * SLOT_U;
+      const int ch = (int)(t.keys[node] & 7ull);
       const int cb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
-      for (int e = threadIdx.x; e < 12 * 12 * 12 * NV; e += blockDim.x) {
-        const int v = e / 1728, q = e % 1728;
-        const int rx = q % 12 - 2, ry = (q / 12) % 12 - 2, rz = q / 144 - 2;   // parent cell relative to the child
-        const int r = (sgn_region(rz) + 1) * 9 + (sgn_region(ry) + 1) * 3 + (sgn_region(rx) + 1);
-        if (kind[r] != 2) continue;
+      // parent cells covering the region, relative to the child's origin
+      const int px = sx < 0 ? 2 : (sx == 0 ? 8 : 2), py = sy < 0 ? 2 : (sy == 0 ? 8 : 2), pz = sz < 0 ? 2 : (sz == 0 ? 8 : 2);
+      const int qx0 = sx < 0 ? -2 : (sx == 0 ? 0 : 8), qy0 = sy < 0 ? -2 : (sy == 0 ? 0 : 8), qz0 = sz < 0 ? -2 : (sz == 0 ? 0 : 8);
+      const int n = px * py * pz;
+      for (int e = threadIdx.x; e < n * NV; e += blockDim.x) {
+        const int v = e / n, c = e % n;
+        const int rx = qx0 + c % px, ry = qy0 + (c / px) % py, rz = qz0 + c / (px * py);
         const QT<R> qt = qterms_t<R>(P + v * NCELL, 8 * cb[0] + rx, 8 * cb[1] + ry, 8 * cb[2] + rz);
 #pragma unroll
         for (int sub = 0; sub < 8; ++sub) {
-          const int a = sub & 1, b = (sub >> 1) & 1, c = (sub >> 2) & 1;
-          const R val = predict_t<R>(qt, a ? R(-1) : R(1), b ? R(-1) : R(1), c ? R(-1) : R(1));
-          u[v * NCELL + sidx(2 * rx + a, 2 * ry + b, 2 * rz + c)] = from_r<R>(val);
+          const int a = sub & 1, b = (sub >> 1) & 1, cc = (sub >> 2) & 1;
+          const R val = predict_t<R>(qt, a ? R(-1) : R(1), b ? R(-1) : R(1), cc ? R(-1) : R(1));
+          u[v * NCELL + sidx(2 * rx + a, 2 * ry + b, 2 * rz + cc)] = from_r<R>(val);
         }
       }
     }
-    __syncthreads();
+  }
+}
+
+// Boundary passes x-, x+, y-, y+, z-, z+ of the nodes of `level` on the
+// domain boundary (after their copies and predictions).
+static __global__ void __launch_bounds__(256) k_fill_bc(Topo t, Phys p, Pool pool, int cur, int level) {
+  const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
+  double* buf = pool.buf[cur];
+  for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
+    const int node = t.lvl_nodes[w];
+    bool any = false;
+    for (int d = 0; d < 3; ++d) {
+      const int nl = p.nb[d] << level, Xd = t.X[(size_t)node * 3 + d];
+      any = any || (Xd == 0 && p.bc[2 * d] != 1) || (Xd == nl - 1 && p.bc[2 * d + 1] != 1);
+    }
+    if (!any) continue;
+    double* u = buf + (size_t)t.slot[node] * SLOT_U;
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
 #pragma unroll 1
@@ -165,20 +182,14 @@ __global__ void __launch_bounds__(256) k_fill_level_t(Topo t, Phys p, Pool pool,
         const int Xd = t.X[(size_t)node * 3 + d];
         if (side == 0 && Xd != 0) continue;
         if (side == 1 && Xd != nl - 1) continue;
-        // ghost slab: 4 cells deep along d, the full stored extent across
         for (int e = threadIdx.x; e < HW * NS * NS; e += blockDim.x) {
           const int g0 = e % HW, a1 = (e / HW) % NS - HW, a2 = e / (HW * NS) - HW;
           const int a = (side == 0) ? (-1 - g0) : (NB + g0);
-          int c[3], sc[3];
-          c[d] = a;
-          c[(d + 1) % 3] = a1;
-          c[(d + 2) % 3] = a2;
-          sc[0] = c[0];
-          sc[1] = c[1];
-          sc[2] = c[2];
-          if (bc == 0) sc[d] = (side == 0) ? 0 : NB - 1;
-          else sc[d] = (side == 0) ? (-1 - a) : (2 * NB - 1 - a);
-          const int di = sidx(c[0], c[1], c[2]), si = sidx(sc[0], sc[1], sc[2]);
+          const int sa = (bc == 0) ? ((side == 0) ? 0 : NB - 1) : ((side == 0) ? (-1 - a) : (2 * NB - 1 - a));
+          int di, si;
+          if (d == 0) { di = sidx(a, a1, a2); si = sidx(sa, a1, a2); }
+          else if (d == 1) { di = sidx(a2, a, a1); si = sidx(a2, sa, a1); }
+          else { di = sidx(a1, a2, a); si = sidx(a1, a2, sa); }
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             double val = u[v * NCELL + si];
@@ -249,6 +260,78 @@ __global__ void __launch_bounds__(256) k_delta_t(Topo t, Phys p, Pool pool, int 
       delta_node[node] = x;
     }
     __syncthreads();
+  }
+}
+
+}  // namespace mrb
+
+namespace mrb {
+
+// New child: every stored cell predicted from the parent (Eq. Prediction).
+// R = double evaluates the prediction in FP64; R = float evaluates the Q-term
+// corrections in FP32 and adds them to the FP64 parent value, so that the
+// children's mean stays the parent value up to FP64 rounding (the eight
+// corrections of a parent cell are sign-symmetric and cancel exactly).
+template <class R>
+__global__ void __launch_bounds__(256) k_refine_fill_t(Topo t, Pool pool, int cur, const int32_t* __restrict__ pairs,
+                                                      int n) {
+  double* B = pool.buf[cur];
+  const int nitems = n * 8;
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int child = pairs[2 * (w / 8)], par = pairs[2 * (w / 8) + 1];
+    const int zq = w % 8;                                      // 8 chunks of the 12 x 12 x 12 parent cells
+    double* U = B + (size_t)t.slot[child] * SLOT_U;
+    const double* P = B + (size_t)t.slot[par] * SLOT_U;
+    const int ch = (int)(t.keys[child] & 7ull);
+    const int cb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+    for (int e = threadIdx.x; e < 216 * NV; e += blockDim.x) {
+      const int v = e / 216, r = e % 216 + zq * 216;
+      const int pi = 8 * cb[0] - 2 + r % 12, pj = 8 * cb[1] - 2 + (r / 12) % 12, pk = 8 * cb[2] - 2 + r / 144;
+      const QT<R> q = qterms_t<R>(P + v * NCELL, pi, pj, pk);
+      const double base = P[v * NCELL + sidx(pi, pj, pk)];
+#pragma unroll
+      for (int sub = 0; sub < 8; ++sub) {
+        const int a = sub & 1, b = (sub >> 1) & 1, c = (sub >> 2) & 1;
+        const int fi = 2 * (pi - 8 * cb[0]) + a, fj = 2 * (pj - 8 * cb[1]) + b, fk = 2 * (pk - 8 * cb[2]) + c;
+        double val;
+        if (sizeof(R) == sizeof(double)) {
+          val = from_r<R>(predict_t<R>(q, a ? R(-1) : R(1), b ? R(-1) : R(1), c ? R(-1) : R(1)));
+        } else {
+          QT<R> q0 = q;
+          q0.u = R(0);
+          val = base + from_r<R>(predict_t<R>(q0, a ? R(-1) : R(1), b ? R(-1) : R(1), c ? R(-1) : R(1)));
+        }
+        U[v * NCELL + sidx(fi, fj, fk)] = val;
+      }
+    }
+  }
+}
+
+// Averaging, Eq. (Averaging), levels fine to coarse; one work item per
+// (internal node, octant): the octant's 512 parent cells come from one child.
+static __global__ void __launch_bounds__(256) k_project_octants(Topo t, Pool pool, int buf, int level) {
+  const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
+  double* B = pool.buf[buf];
+  const int nitems = (end - beg) * 8;
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int node = t.lvl_nodes[beg + w / 8];
+    const int c0 = t.child0[node];
+    if (c0 < 0) continue;
+    const int o = w % 8;
+    double* Pp = B + (size_t)t.slot[node] * SLOT_U;
+    const double* C = B + (size_t)t.slot[c0 + o] * SLOT_U;
+    const int ox = 8 * (o & 1), oy = 8 * ((o >> 1) & 1), oz = 8 * ((o >> 2) & 1);
+    for (int e = threadIdx.x; e < 512 * NV; e += blockDim.x) {
+      const int v = e / 512, c = e % 512;
+      const int I = c % 8, J = (c / 8) % 8, K = c / 64;
+      const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
+      const double* u = C + v * NCELL;
+      const double c0v = u[sidx(fi, fj, fk)], c1v = u[sidx(fi + 1, fj, fk)];
+      const double c2v = u[sidx(fi, fj + 1, fk)], c3v = u[sidx(fi + 1, fj + 1, fk)];
+      const double c4v = u[sidx(fi, fj, fk + 1)], c5v = u[sidx(fi + 1, fj, fk + 1)];
+      const double c6v = u[sidx(fi, fj + 1, fk + 1)], c7v = u[sidx(fi + 1, fj + 1, fk + 1)];
+      Pp[v * NCELL + sidx(ox + I, oy + J, oz + K)] = 0.125 * (((c0v + c1v) + (c2v + c3v)) + ((c4v + c5v) + (c6v + c7v)));
+    }
   }
 }
 

@@ -282,18 +282,33 @@ __device__ __forceinline__ void face_features_f32(const float* __restrict__ S, i
 }
 
 // Stencil region of direction D for the slab at z0 -> FP32 records in S.
+// Cells beyond the block along D come from the same-level face neighbour's
+// internal cells when it exists (ulo/uhi, else null: the block's own halo,
+// filled by prediction or the boundary condition).
 template <int D>
 __device__ __forceinline__ void load_region_f32(const double* __restrict__ u, float* __restrict__ S, int z0, float g,
-                                                float B, float gm1) {
+                                                float B, float gm1, const double* __restrict__ ulo = nullptr,
+                                                const double* __restrict__ uhi = nullptr) {
   constexpr int n = (D == 2) ? SF_REG : 22 * 16 * SF_TZ;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     int x, y, z;
     if (D == 0) { x = idx % 22 - 3; y = (idx / 22) % 16; z = z0 + idx / 352; }
     else if (D == 1) { x = idx % 16; y = (idx / 16) % 22 - 3; z = z0 + idx / 352; }
     else { x = idx % 16; y = (idx / 16) % 16; z = z0 - 3 + idx / 256; }
-    const int s = sidx(x, y, z);
-    const float r = d2f_fast(u[s]), mx = d2f_fast(u[NCELL + s]), my = d2f_fast(u[2 * NCELL + s]);
-    const float mz = d2f_fast(u[3 * NCELL + s]), E = d2f_fast(u[4 * NCELL + s]);
+    const int a = (D == 0) ? x : (D == 1 ? y : z);
+    const double* src = u;
+    int s;
+    if (a < 0 && ulo) {
+      src = ulo;
+      s = (D == 0) ? sidx(x + NB, y, z) : (D == 1 ? sidx(x, y + NB, z) : sidx(x, y, z + NB));
+    } else if (a >= NB && uhi) {
+      src = uhi;
+      s = (D == 0) ? sidx(x - NB, y, z) : (D == 1 ? sidx(x, y - NB, z) : sidx(x, y, z - NB));
+    } else {
+      s = sidx(x, y, z);
+    }
+    const float r = d2f_fast(src[s]), mx = d2f_fast(src[NCELL + s]), my = d2f_fast(src[2 * NCELL + s]);
+    const float mz = d2f_fast(src[3 * NCELL + s]), E = d2f_fast(src[4 * NCELL + s]);
     const float ir = frcp(r);
     const float vx = mx * ir, vy = my * ir, vz = mz * ir;
     const float q2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
@@ -337,9 +352,17 @@ __device__ __forceinline__ bool stencil_flat(const float* __restrict__ S, int c0
 template <int D, int MODE>
 __device__ __forceinline__ void sweep_f32(const double* __restrict__ u, double* __restrict__ fb, float* __restrict__ S,
                                           float* __restrict__ Fs, int z0, float g, float B, float gm1,
-                                          float (&acc)[SF_TZ][NV], const LearnedCtx& L) {
+                                          float (&acc)[SF_TZ][NV], const LearnedCtx& L, const Topo& t,
+                                          const double* __restrict__ buf, int node) {
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
-  load_region_f32<D>(u, S, z0, g, B, gm1);
+  {
+    // same-level face neighbours along D read directly
+    constexpr int rlo = (D == 0) ? 12 : (D == 1 ? 10 : 4), rhi = (D == 0) ? 14 : (D == 1 ? 16 : 22);
+    const int nlo = t.nbr[(size_t)node * 27 + rlo], nhi = t.nbr[(size_t)node * 27 + rhi];
+    const double* ulo = (nlo >= 0) ? buf + (size_t)t.slot[nlo] * SLOT_U : nullptr;
+    const double* uhi = (nhi >= 0) ? buf + (size_t)t.slot[nhi] * SLOT_U : nullptr;
+    load_region_f32<D>(u, S, z0, g, B, gm1, ulo, uhi);
+  }
   __syncthreads();
   constexpr int nf = (D == 2) ? NB * NB * (SF_TZ + 1) : 17 * 16 * SF_TZ;
   constexpr int st = (D == 0) ? 1 : (D == 1 ? 16 : 256);
@@ -474,9 +497,9 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
     if (MODE == 1) L.bits = pool.sel + (size_t)slot * SLOT_SEL;
     float acc[SF_TZ][NV];
-    sweep_f32<0, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L);
-    sweep_f32<1, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L);
-    sweep_f32<2, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L);
+    sweep_f32<0, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+    sweep_f32<1, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+    sweep_f32<2, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
     const double dx = ldexp(p.dx0, -t.level[node]);
     const double idx_ = 1.0 / dx;
     const double h = dt ? dt[t.inst[node]] : 0.0;
