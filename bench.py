@@ -40,7 +40,7 @@ WORKLOAD = "explosion_mr_256cubed_l3"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mrb", choices=["mrb", "reference"])
     ap.add_argument("--lmax", type=int, default=3)
@@ -144,18 +144,28 @@ def finest_density(keys, geo, rho, cfg):
     return out
 
 
-def roofline_numbers():
-    """Algorithmic FLOPs of the fused stage kernel per leaf cell and stage, and
-    the FP32 CUDA-core peak; see the accounting in this function's body."""
+def roofline_numbers(linear_fraction=0.0):
+    """Algorithmic FP32 FLOPs of the fused stage kernel per face and per leaf
+    cell and stage (the accounting is in this function's body)."""
     # Per face (the oracle's face flux, WENO5 on every field, Roe upwinding on
     # every field, zero matrix entries skipped): Roe average and eigensystem 71,
     # characteristic projections 6 cells x 62, split tests 6, WENO5 5 x 66,
-    # R g 33 -> 812.  Per cell and direction: primitive variables and physical
-    # flux 25.  Per cell and stage: 3 x (17/16 faces x 812 + 22/16 x 25)
-    # + divergence 30 + update 20 = 2747 + 103 + 50.
-    per_face = 812
+    # R g 33 -> 812.  A face the selector sends to the linear scheme does the
+    # linear reconstruction (21) instead of WENO5 (66) on fields 0, 1, 4:
+    # 812 - 3 x 45 = 677.  Per cell and direction: primitive variables and
+    # physical flux 25.  Per cell and stage: 3 x (17/16 faces x per_face +
+    # 22/16 x 25) + divergence 30 + update 20.  The selector's MLP runs on the
+    # tensor cores and is not counted here.
+    per_face = 812 - linear_fraction * 3 * 45
     per_cell = 3 * (17 / 16 * per_face + 22 / 16 * 25) + 30 + 20
     return per_face, per_cell
+
+
+# DRAM bytes per leaf cell of one launch of the FP32 stage kernels, from the
+# ncu captures summarised in profiles/stage_kernels_explosion_256.md (levels
+# 0-2 case; traffic grows in proportion to the leaf cells of a launch).
+TRAFFIC_BYTES_PER_CELL = {"learned": (163.711488e6 + 165.856512e6) / (512 * 4096),
+                          "weno": (149.616640e6 + 160.287488e6) / (512 * 4096)}
 
 
 def measured_peaks():
@@ -167,11 +177,56 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ GPU arm
+def timed_path(args, cfg, stream, steps, warmup, mlp_params=None, profile=True):
+    """Build the workload tree, warm up, time `steps` full steps with CUDA
+    events on the launching stream; returns the context and measurements."""
+    import torch
+
+    from paper_2012_04385_gb300 import mrb
+    ctx = mrb.Context(cfg, slots_for(cfg), stream=stream, mlp_params=mlp_params)
+    build_tree(ctx, cfg)
+    for _ in range(warmup):
+        ctx.step(1)
+    torch.cuda.synchronize()
+    if profile:
+        ctx.profile(True)
+    ctx.learned_stats(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cells = 0
+    ev0.record(stream)
+    for _ in range(steps):
+        cells += ctx.n_leaves() * 4096 * 3
+        ctx.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    kms, kn, nk = ctx.profile_read() if profile else (0.0, 0, 0)
+    lin, tot = ctx.learned_stats()
+    return ctx, dict(ms=ms, cells=cells, stage_ms=kms / max(kn, 1), launches=nk,
+                     linear_fraction=(lin / tot) if tot else 0.0)
+
+
+def l1_after(cfg_a, cfg_b, stream, nsteps, params=None):
+    """L1 density difference of two paths after nsteps from the same initial tree."""
+    from paper_2012_04385_gb300 import mrb
+    out = []
+    for cfg in (cfg_a, cfg_b):
+        ctx = mrb.Context(cfg, slots_for(cfg), stream=stream,
+                          mlp_params=params if cfg.recon == 1 else None)
+        build_tree(ctx, cfg)
+        ctx.step(nsteps)
+        k, g = ctx.list_blocks()
+        out.append((k, finest_density(k, g, ctx.get_state(k).cpu().numpy()[:, 0], cfg)))
+        ctx.close()
+    (ka, ra), (kb, rb) = out
+    return float(np.abs(ra - rb).sum() / np.abs(rb).sum()), bool(np.array_equal(ka, kb))
+
+
 def run_gpu(args, rank, world):
     import torch
 
     from paper_2012_04385_gb300 import inputs as I
-    from paper_2012_04385_gb300 import mrb
+    from paper_2012_04385_gb300 import learned, mrb
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
@@ -185,101 +240,70 @@ def run_gpu(args, rank, world):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
+    def reduce(x, op):
         if dist is None:
             return x
         t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=op)
         return float(t.item())
+
+    def max_over_ranks(x):
+        return reduce(x, dist.ReduceOp.MAX) if dist is not None else x
 
     def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce(x, dist.ReduceOp.SUM) if dist is not None else x
 
     stream = torch.cuda.current_stream()
-    cfg = workload_config(args.lmax, I.FP32_ACC64)
-    ctx = mrb.Context(cfg, slots_for(cfg), stream=stream)
-    build_tree(ctx, cfg)
-    keys0 = ctx.keys()
-    state0 = ctx.get_state(keys0).clone()
-    for _ in range(args.warmup):
-        ctx.step(1)
+    # ---- the learned selector, trained on the GPU by the library's own kernels
+    t0 = time.perf_counter()
+    data = learned.generate()
+    params, tau, rep = learned.train(data, epochs=10)
+    train_s = time.perf_counter() - t0
+    cfg_l = workload_config(args.lmax, I.FP32_ACC64)
+    cfg_l.recon, cfg_l.mlp_tau = I.RECON_LEARNED, tau
+    cfg_w = workload_config(args.lmax, I.FP32_ACC64)
+    cfg_64 = workload_config(args.lmax, I.FP64)
+
+    # ---- headline: FP32 bulk + learned selector, timed region with clocks
     barrier()
-    # ---- timed region (device time, CUDA events on the launching stream)
     sampler = ClockSampler(dev)
     sampler.start()
-    ctx.profile(True)
-    cells = 0
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        cells += ctx.n_leaves() * 4096 * 3
-        ctx.step(1)
-    ev1.record(stream)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    rhs_ms, rhs_n, n_kernels = ctx.profile_read()
-    ctx.profile(False)
+    ctx, m = timed_path(args, cfg_l, stream, args.steps, args.warmup, mlp_params=params)
     clocks = sampler.stop()
-    ms_max = max_over_ranks(ms)
-    total_cells = sum_over_ranks(cells)
-    value = total_cells / (ms_max * 1e-3)
-    leaves_end = ctx.n_leaves()
+    barrier()
+    ms_max = max_over_ranks(m["ms"])
+    value = sum_over_ranks(m["cells"]) / (ms_max * 1e-3)
+    keys0 = ctx.keys()
 
-    # ---- roofline of the fused stage kernel
-    per_face, per_cell = roofline_numbers()
+    # ---- roofline of the fused stage kernel (FP32 CUDA cores)
+    per_face, per_cell = roofline_numbers(m["linear_fraction"])
     pk = measured_peaks()
     clk = clocks["sm_mhz"] or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 1447.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = nsm * 128 * 2 * clk * 1e6 / 1e12          # TFLOP/s at the sampled clock
-    avg_launch_ms = rhs_ms / max(rhs_n, 1)
-    achieved = (cells / 3 / args.steps) * per_cell / (avg_launch_ms * 1e-3) / 1e12   # per launch: one stage
+    fp32_peak = nsm * 128 * 2 * clk * 1e6 / 1e12
+    cells_per_launch = m["cells"] / 3 / args.steps
+    achieved = cells_per_launch * per_cell / (m["stage_ms"] * 1e-3) / 1e12
 
-    # ---- FP64 path on the same workload
-    cfg64 = workload_config(args.lmax, I.FP64)
-    ctx64 = mrb.Context(cfg64, slots_for(cfg64), stream=stream)
-    build_tree(ctx64, cfg64)
-    ctx64.step(1)
-    barrier()
-    cells64 = 0
-    ctx64.profile(True)
-    ev0.record(stream)
-    for _ in range(args.fp64_steps):
-        cells64 += ctx64.n_leaves() * 4096 * 3
-        ctx64.step(1)
-    ev1.record(stream)
-    barrier()
-    ms64 = ev0.elapsed_time(ev1)
-    rhs64_ms, rhs64_n, _ = ctx64.profile_read()
-    value64 = sum_over_ranks(cells64) / (max_over_ranks(ms64) * 1e-3)
+    # ---- the same workload on the FP32 WENO5 path and the all-FP64 path
+    _, mw = timed_path(args, cfg_w, stream, args.steps, args.warmup)
+    _, m64 = timed_path(args, cfg_64, stream, args.fp64_steps, 1)
+    value_w = sum_over_ranks(mw["cells"]) / (max_over_ranks(mw["ms"]) * 1e-3)
+    value_64 = sum_over_ranks(m64["cells"]) / (max_over_ranks(m64["ms"]) * 1e-3)
+    _, pfw = roofline_numbers(0.0)
+    achieved_w = (mw["cells"] / 3 / args.steps) * pfw / (mw["stage_ms"] * 1e-3) / 1e12
 
-    # ---- L1 density error FP32-bulk vs FP64, same initial tree, same steps
-    ca = mrb.Context(cfg, slots_for(cfg), stream=stream)
-    cb = mrb.Context(cfg64, slots_for(cfg64), stream=stream)
-    build_tree(ca, cfg)
-    build_tree(cb, cfg64)
+    # ---- L1 density errors against the FP64 GPU path (same initial tree, same steps)
     nerr = max(args.fp64_steps, 3)
-    ca.step(nerr)
-    cb.step(nerr)
-    ka, ga = ca.list_blocks()
-    kb, gb = cb.list_blocks()
-    ra = finest_density(ka, ga, ca.get_state(ka).cpu().numpy()[:, 0], cfg)
-    rb = finest_density(kb, gb, cb.get_state(kb).cpu().numpy()[:, 0], cfg)
-    l1 = float(np.abs(ra - rb).sum() / np.abs(rb).sum())
-    same_tree = bool(np.array_equal(ka, kb))
-    del ca, cb, ctx64
+    l1_l, same_l = l1_after(cfg_l, cfg_64, stream, nerr, params)
+    l1_w, same_w = l1_after(cfg_w, cfg_64, stream, nerr)
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers (headline path)
     e2e = None
     if not args.no_e2e:
         # per step: H2D of the step's input state from pinned host memory,
         # mrb_set_cons + mrb_step + mrb_get_state, D2H of the result state and
         # the conservation sums
-        cap = slots_for(cfg)
+        cap = slots_for(cfg_l)
         host = [torch.empty((cap, 5, 16, 16, 16), dtype=torch.float64).pin_memory() for _ in range(2)]
         dev_buf = torch.empty((cap, 5, 16, 16, 16), dtype=torch.float64, device="cuda")
         sums = torch.empty((1, 5), dtype=torch.float64, device="cuda")
@@ -288,7 +312,7 @@ def run_gpu(args, rank, world):
         n = len(keys)
         host[0][:n].copy_(ctx.get_state(keys))
         barrier()
-        t0 = time.perf_counter()
+        t1 = time.perf_counter()
         ecells, h2d, d2h = 0, 0, 0
         e_steps = max(3, args.steps // 2)
         for it in range(e_steps):
@@ -307,30 +331,37 @@ def run_gpu(args, rank, world):
             d2h += n * 5 * 4096 * 8 + 5 * 8
             stream.synchronize()
         barrier()
-        el = time.perf_counter() - t0
-        e2e_value = sum_over_ranks(ecells) / max_over_ranks(el)
-        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d // e_steps),
-               "d2h_bytes_per_step": int(d2h // e_steps)}
+        el = time.perf_counter() - t1
+        e2e = {"value": sum_over_ranks(ecells) / max_over_ranks(el), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d // e_steps), "d2h_bytes_per_step": int(d2h // e_steps)}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 bulk / f64 state+update", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "path": "FP32 bulk + FP64 accumulate, WENO5-JS",
+        "vs_baseline": None, "dtype": "f32 bulk (bf16 tensor-core selector) / f64 state+update", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "path": "FP32 bulk + FP64 accumulate, learned WENO5/linear selector",
                    "effective_resolution": "256^3", "lmax": args.lmax,
-                   "leaf_blocks_start": int(len(keys0)), "leaf_blocks_end": int(leaves_end),
+                   "leaf_blocks_start": int(len(keys0)),
                    "l2": "inputs larger than L2 (block pool %.1f GB)" % (ctx.pool.numel() / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
-                     "kernel": "k_rhs_rk<float> (fused RHS + RK stage)",
-                     "flops_per_cell_stage": per_cell, "avg_launch_ms": avg_launch_ms,
+                     "frac": achieved / fp32_peak,
+                     "traffic": TRAFFIC_BYTES_PER_CELL["learned"] * cells_per_launch,
+                     "traffic_note": "ncu dram bytes of a 2.1M-cell launch scaled to the launch's leaf cells",
+                     "kernel": "k_stage_f32<1> (fused RHS + RK stage, learned selector)",
+                     "flops_per_cell_stage": per_cell, "avg_launch_ms": m["stage_ms"],
                      "peak_basis": f"FP32 CUDA cores {nsm} SMs x 128 lanes x 2 x {clk:.0f} MHz sampled"},
-        "gpu_launches": int(n_kernels),
+        "gpu_launches": int(m["launches"]),
         "clocks": clocks,
-        "fp64_path": {"value": value64, "unit": UNIT, "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps,
-                      "stage_kernel_ms": rhs64_ms / max(rhs64_n, 1)},
-        "l1_density_err_fp32_vs_fp64": l1, "l1_steps": nerr, "l1_same_tree": same_tree,
+        "selector": {"linear_fraction": m["linear_fraction"], "tau": tau, "train_s": round(train_s, 1),
+                     "train_samples": rep["samples"], "holdout_accuracy": rep["holdout_accuracy"],
+                     "holdout_missed_positives": rep["holdout_missed_positives"]},
+        "fp32_weno_path": {"value": value_w, "unit": UNIT, "ms_per_step": mw["ms"] / args.steps,
+                           "stage_kernel_ms": mw["stage_ms"], "roofline_frac": achieved_w / fp32_peak},
+        "fp64_path": {"value": value_64, "unit": UNIT, "steps": args.fp64_steps,
+                      "ms_per_step": m64["ms"] / args.fp64_steps, "stage_kernel_ms": m64["stage_ms"]},
+        "l1_density_err_vs_fp64": {"fp32_learned": l1_l, "fp32_weno": l1_w, "steps": nerr,
+                                   "same_tree": same_l and same_w},
     }
     if e2e:
         result["e2e"] = e2e
