@@ -301,6 +301,9 @@ int mrb_measure_peaks(double* out, int32_t n);
 
 int mrb_status(mrb_ctx* ctx);   /* sticky device status (synchronises)       */
 int mrb_sync(mrb_ctx* ctx);     /* synchronise the stream, return status     */
+/* Reset the sticky device status to MRB_OK (after the caller has repaired or
+ * replaced the offending state); synchronises.  The context stays usable. */
+int mrb_clear_status(mrb_ctx* ctx);
 int mrb_destroy(mrb_ctx* ctx);  /* free internal arrays (not the pool)       */
 const char* mrb_last_error(mrb_ctx* ctx);
 

@@ -765,6 +765,13 @@ int mrb_sync(mrb_ctx* c) {
   return MRB_OK;
 }
 
+int mrb_clear_status(mrb_ctx* c) {
+  return guarded(c, [&] {
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemset(c->d_status, 0, sizeof(int)));
+  });
+}
+
 int mrb_destroy(mrb_ctx* c) {
   if (!c) return MRB_EINVAL;
   cudaStreamSynchronize(c->st);

@@ -200,6 +200,17 @@ def ic_four_quadrant(cfg, geo, inst: int = 0, seed: int = 2012):
     return out
 
 
+def ic_ensemble(cfg, geo, keys, seed: int = 2012):
+    """Batched four-quadrant problems: block b belongs to instance keys[b] >> 56."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    inst = (keys >> np.uint64(56)).astype(np.int64)
+    out = _prim(len(geo))
+    for i in np.unique(inst):
+        sel = inst == i
+        out[sel] = ic_four_quadrant(cfg, geo[sel], inst=int(i), seed=seed)
+    return out
+
+
 def post_shock_state(mach=1.22, gamma=1.4, rho1=1.0, p1=1.0):
     """Rankine-Hugoniot state behind a normal shock moving into rest."""
     g = gamma

@@ -97,6 +97,7 @@ def lib():
                                             vp]),
                 "mrb_status": (ci, [vp]),
                 "mrb_sync": (ci, [vp]),
+                "mrb_clear_status": (ci, [vp]),
                 "mrb_destroy": (ci, [vp]),
                 "mrb_last_error": (ctypes.c_char_p, [vp]),
             }
@@ -387,27 +388,61 @@ class Context:
     def sync(self):
         self._rc(lib().mrb_sync(self._h))
 
+    def clear_status(self):
+        self._rc(lib().mrb_clear_status(self._h))
 
-def init_tree(ctx, ic, allow_coarsen=True):
+
+def init_tree(ctx, ic, allow_coarsen=True, with_keys=False):
     """Alg. (Initialization): impose the initial condition on level 0, then for
     m = 1 .. lmax refine every block of level m-1, impose the initial condition
     on level m and, for m > 1, coarsen sibling groups whose details are below
-    eps_m.  `ic(cfg, geo) -> prim[n, 5, 16, 16, 16]` (host numpy)."""
+    eps_m.  `ic(cfg, geo) -> prim[n, 5, 16, 16, 16]` (host numpy), or
+    `ic(cfg, geo, keys)` with `with_keys` (batched instances: the instance is
+    key >> 56)."""
+    if with_keys:
+        ic_k = ic
+    else:
+        def ic_k(c, geo, keys):
+            return ic(c, geo)
     torch = ctx.torch
     cfg = ctx.cfg
     lmax = max(cfg.lmax_of(i) for i in range(cfg.n_instances))
     keys, geo = ctx.list_blocks(0)
-    ctx.set_state(keys, ic(cfg, geo))
+    ctx.set_state(keys, ic_k(cfg, geo, keys))
     for m in range(1, lmax + 1):
         ctx.fill_halos()
         _, geo_l = ctx.list_blocks()
         tags = np.where(geo_l[:, 0] == m - 1, TAG_REFINE, TAG_KEEP).astype(np.int8)
         ctx.remesh(tags)
         keys, geo = ctx.list_blocks(m)
-        ctx.set_state(keys, ic(cfg, geo))
+        ctx.set_state(keys, ic_k(cfg, geo, keys))
         if m > 1 and allow_coarsen:
             ctx.fill_halos()
             tags, _ = ctx.mr_predict_and_tag(allow_refine=False, with_delta=False)
             ctx.remesh(tags)
     ctx.mr_project()
     torch.cuda.current_stream().synchronize()
+
+
+def restore_tree(ctx, node_keys):
+    """Checkpoint / resume: rebuild a saved block tree in a fresh context.
+    `node_keys` are all node ids (internal nodes and leaves, as listed by
+    keys(leaves_only=False)); leaves whose first child is saved are refined,
+    level by level.  The caller then restores every node's state with
+    set_cons."""
+    want = set(int(k) for k in np.asarray(node_keys, dtype=np.uint64))
+    mask56 = (1 << 56) - 1
+
+    def child0(k):
+        return ((k & mask56) << 3) | ((k >> 56) << 56)
+
+    while True:
+        leaves = [int(k) for k in ctx.keys()]
+        tags = np.array([TAG_REFINE if child0(k) in want else TAG_KEEP for k in leaves], np.int8)
+        if not (tags == TAG_REFINE).any():
+            break
+        ctx.fill_halos()
+        ctx.remesh(tags)
+    have = set(int(k) for k in ctx.keys(leaves_only=False))
+    if have != want:
+        raise MrbError(MRB_EINVAL, "saved ids do not form a tree reachable from level 0")

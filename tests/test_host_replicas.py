@@ -1,0 +1,74 @@
+"""Host side of the multi-GPU replica runs, on CPU with two gloo ranks.
+
+Each rank runs the whole workload on its own GPU; the only exchange is the
+timing: a barrier around the timed region, the maximum of the per-rank
+elapsed times and the sum of the per-rank cell-updates.  These tests run that
+host logic (bench.Ranks) in two processes without a GPU.
+"""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.Ranks(world, "gloo", "cpu")
+    # per-rank measurements: elapsed ms and cell-updates
+    ms = [120.0, 135.5][rank]
+    cells = [3.0e9, 2.5e9][rank]
+    r.barrier()
+    ms_max = r.max(ms)
+    total = r.sum(cells)
+    value = total / (ms_max * 1e-3)
+    # the reference arm: only rank 0 works, the others return nothing
+    ref = bench.run_reference(None, rank, world) if rank != 0 else "rank0"
+    q.put((rank, ms_max, total, value, ref))
+    r.close()
+
+
+def test_two_rank_timing_reduction():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = {}
+    for _ in range(world):
+        rank, ms_max, total, value, ref = q.get(timeout=120)
+        out[rank] = (ms_max, total, value, ref)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank in range(world):
+        ms_max, total, value, ref = out[rank]
+        assert ms_max == 135.5                     # slowest rank
+        assert total == 5.5e9                      # all ranks' cell-updates
+        assert value == pytest.approx(5.5e9 / 0.1355)
+    assert out[1][3] is None                       # reference arm: rank 1 exits without work
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.Ranks(1, "gloo", "cpu")
+    assert r.dist is None
+    assert r.max(3.0) == 3.0 and r.sum(4.0) == 4.0
+    r.barrier()
+    r.close()
