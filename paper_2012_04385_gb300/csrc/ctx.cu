@@ -81,6 +81,7 @@ struct mrb_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t cap_st = nullptr;     // private stream for capture (the caller's may be the legacy stream)
   bool graph_dirty = true;
+  bool detail_filled = false;        // leaves' halos hold rho and E only (fill before the details)
   long long graph_kernels[2] = {0, 0};
   int capturing = -1;                // graph parity being captured, or -1
   cudaEvent_t gev[2][3][2] = {};     // events around the stage kernel inside each graph
@@ -189,8 +190,8 @@ struct mrb_ctx {
   }
 
   // ---- the steps
-  void fill_halos(int leaf_faces_only = 0) {
-    for (int l = 0; l <= max_lmax; ++l) launch_fill_level(topo(), phys, P, cur, l, st, leaf_faces_only);
+  void fill_halos(int mode = FILL_FULL) {
+    for (int l = 0; l <= max_lmax; ++l) launch_fill_level(topo(), phys, P, cur, l, st, mode);
   }
   void stage(int s, const double* dt) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -219,9 +220,9 @@ struct mrb_ctx {
     launch_cfl(topo(), phys, P, cur, d_smax, d_dt, d_status, st);
     // the mixed-precision stage kernel reads face neighbours directly, so the
     // stage fill of leaves is limited to predicted and boundary face regions
-    const int partial = (cfg.precision == MRB_FP32_ACC64) ? 1 : 0;
+    const int mode = (cfg.precision == MRB_FP32_ACC64) ? FILL_STAGE : FILL_FULL;
     for (int s = 0; s < 3; ++s) {
-      fill_halos(partial);
+      fill_halos(mode);
       stage(s, d_dt);
       project();
     }
@@ -270,6 +271,8 @@ struct mrb_ctx {
 
   int64_t remesh(const int8_t* tags_dev) {
     const int nl = n_leaves();
+    const bool detail_fill = detail_filled;
+    detail_filled = false;
     std::vector<int8_t> tags((size_t)nl);
     if (nl) CK(cudaMemcpyAsync(tags.data(), tags_dev, nl, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -290,6 +293,15 @@ struct mrb_ctx {
     if ((int64_t)refine.size() * 8 > (int64_t)free_slots.size() + 8 * (int64_t)coarse_parents.size())
       throw Err(MRB_ECAPACITY, "block pool exhausted by refinement");
     if (refine.empty() && coarse_parents.empty()) return nl;
+    if (detail_fill && !refine.empty()) {
+      // the halos of leaves were filled for the details only (rho, E): complete
+      // those of the blocks about to be refined, whose children are predicted
+      // over their whole stored range
+      upload_list(refine);
+      launch_fill_list(topo(), phys, P, cur, d_list, (int)refine.size(), st);
+      check_launch();
+    }
+
     // coarsening frees slots first (ascending key order), refinement then takes them
     std::vector<char> removed(nodes.size(), 0);
     for (uint64_t pk : coarse_parents) {
@@ -652,7 +664,8 @@ int mrb_step(mrb_ctx* c, int32_t nsteps, double* dt_hist_dev) {
         CK(cudaMemcpyAsync(dt_hist_dev + (size_t)s * c->cfg.n_instances, c->d_dt, sizeof(double) * c->cfg.n_instances,
                            cudaMemcpyDeviceToDevice, c->st));
       if (mr) {
-        c->fill_halos();
+        c->fill_halos(FILL_DETAIL);
+        c->detail_filled = true;
         launch_delta_tags(c->topo(), c->phys, c->P, c->cur, c->d_delta_node, 1, c->d_tags, nullptr, c->n_leaves(),
                           c->st);
         c->remesh(c->d_tags);

@@ -30,9 +30,18 @@ void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, 
 }
 
 void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st,
-                           int leaf_faces_only) {
-  k_fill_regions_t<float><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, level, leaf_faces_only);
-  k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, level);
+                           int mode) {
+  const NodeSet ns{level, nullptr, 0};
+  k_fill_regions_t<float><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, ns, mode);
+  k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, mode);
+  g_kernel_launches += 2;
+}
+
+void launch_fill_list_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* list, int n,
+                          cudaStream_t st) {
+  const NodeSet ns{0, list, n};
+  k_fill_regions_t<float><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, ns, FILL_FULL);
+  k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, FILL_FULL);
   g_kernel_launches += 2;
 }
 

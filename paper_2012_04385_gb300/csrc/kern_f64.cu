@@ -95,13 +95,29 @@ void launch_get_state(const Topo& t, const Pool& pool, int cur, const int32_t* n
 
 // ---------------------------------------------------------------- halo fill (mr.cuh)
 void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st,
-                       int leaf_faces_only) {
+                       int mode) {
   if (p.precision == 1) {
-    launch_fill_level_f32(t, p, pool, cur, level, st, leaf_faces_only);
+    launch_fill_level_f32(t, p, pool, cur, level, st, mode);
     return;
   }
-  k_fill_regions_t<double><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, level, 0);
-  k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, level);
+  // the FP64 stage kernel reads every halo region: no stage-partial fill
+  const NodeSet ns{level, nullptr, 0};
+  const int m = (mode == FILL_STAGE) ? FILL_FULL : mode;
+  k_fill_regions_t<double><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, ns, m);
+  k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, m);
+  g_kernel_launches += 2;
+}
+
+void launch_fill_list(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* list, int n,
+                      cudaStream_t st) {
+  if (n <= 0) return;
+  if (p.precision == 1) {
+    launch_fill_list_f32(t, p, pool, cur, list, n, st);
+    return;
+  }
+  const NodeSet ns{0, list, n};
+  k_fill_regions_t<double><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, ns, FILL_FULL);
+  k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, FILL_FULL);
   g_kernel_launches += 2;
 }
 

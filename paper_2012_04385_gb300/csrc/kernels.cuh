@@ -15,6 +15,13 @@ constexpr int CNT_SIZE = CNT_LVL + MAXL + 2;
 
 enum : int { ST_OK = 0, ST_NONPHYS = 6 };
 
+// Halo fill modes, for leaves (internal nodes are always filled completely):
+//   FILL_FULL       every region, every variable;
+//   FILL_STAGE      only the predicted face regions (the mixed-precision stage
+//                   kernel reads same-level face neighbours' cells directly);
+//   FILL_DETAIL     every region, rho and E only (the detail norm's inputs).
+enum : int { FILL_FULL = 0, FILL_STAGE = 1, FILL_DETAIL = 2 };
+
 // Node arrays, in ascending id order (instance, level, Morton).
 struct Topo {
   const uint64_t* keys;
@@ -63,7 +70,10 @@ void launch_set_cons(const Topo& t, const Pool& pool, int cur, const int32_t* no
 void launch_get_state(const Topo& t, const Pool& pool, int cur, const int32_t* nodes, int n, double* out,
                       int with_halo, cudaStream_t st);
 void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st,
-                       int leaf_faces_only = 0);
+                       int mode = 0);
+// every halo region of the listed nodes (device list of n node indices), all variables
+void launch_fill_list(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* list, int n,
+                      cudaStream_t st);
 void launch_rhs_rk_f64(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
                        double* rhs_out, cudaStream_t st);
 void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
@@ -83,7 +93,9 @@ void launch_sums(const Topo& t, const Phys& p, const Pool& pool, int cur, double
                  int nleaves_cap, cudaStream_t st);
 // mixed-precision variants (kern_f32.cu)
 void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st,
-                           int leaf_faces_only);
+                           int mode);
+void launch_fill_list_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* list, int n,
+                          cudaStream_t st);
 void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, cudaStream_t st);
 void launch_cfl_speeds_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax,
                            int* status, cudaStream_t st);

@@ -13,12 +13,11 @@ namespace mrb {
 // Label: 1 when any reconstruction of fields 0, 1, 4 the face performs
 // differs between WENO5 and the linear scheme by more than both tau_lab times
 // its largest |input| and the absolute floor 1e-6.
-template <int D>
 __device__ __forceinline__ int face_label_f32(const float* __restrict__ S, int c0, int st, const RoeF& e,
                                               float tau_lab) {
   float Ur[6][5], Fr[6][5];
 #pragma unroll
-  for (int m = 0; m < 6; ++m) cell_uf<D>(S, c0 + m * st, Ur[m], Fr[m]);
+  for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, Ur[m], Fr[m]);
   int lab = 0;
   auto check = [&](float a, float b, float c, float d, float ee) {
     const float sc = fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fmaxf(fabsf(c), fabsf(d)), fabsf(ee)));
@@ -69,42 +68,30 @@ constexpr int FACES_PER_LEAF = 3 * 17 * 256;   // 13056
 // Every stride-th face (global id = leaf * 13056 + direction * 4352 + index in
 // the block's canonical face order) -> features [n][16], labels [n] and the
 // face id.  Work items are (leaf, z-slab) as in the stage kernel.
-template <int D>
-__device__ __forceinline__ void sample_dir(const double* __restrict__ u, float* __restrict__ S, int li, int z0,
+__device__ __forceinline__ void sample_dir(int D, const double* __restrict__ u, float* __restrict__ S, int li, int z0,
                                            float g, float B, float gm1, float tau_lab, int64_t stride,
                                            float* __restrict__ feats, uint8_t* __restrict__ labels,
                                            int64_t* __restrict__ where, int64_t cap) {
-  load_region_f32<D>(u, S, z0, g, B, gm1);
+  load_region_f32(D, u, S, z0, g, B, gm1);
   __syncthreads();
-  constexpr int nf = (D == 2) ? NB * NB * (SF_TZ + 1) : 17 * 16 * SF_TZ;
-  constexpr int st = (D == 0) ? 1 : (D == 1 ? 16 : 256);
+  const int nf = region_faces(D);
+  const int st = region_stride(D);
   for (int f = threadIdx.x; f < nf; f += blockDim.x) {
-    int c0, canon;
-    if (D == 0) {
-      const int fa = f % 17, r = f / 17;
-      c0 = r * 22 + fa;
-      canon = z0 * 16 * 17 + f;
-    } else if (D == 1) {
-      const int i = f % 16, r = f / 16, fa = r % 17, kz = r / 17;
-      c0 = (kz * 22 + fa) * 16 + i;
-      canon = z0 * 17 * 16 + f;
-    } else {
-      const int i = f % 16, j = (f / 16) % 16, fa = f / 256;
-      if (fa == SF_TZ && z0 + SF_TZ != NB) continue;   // the next slab owns this face plane
-      c0 = (fa * 16 + j) * 16 + i;
-      canon = z0 * 256 + f;
-    }
+    int fa, c0, ta, tb;
+    face_of(D, f, z0, fa, c0, ta, tb);
+    if (D == 2 && fa == SF_TZ && z0 + SF_TZ != NB) continue;   // the next slab owns this face plane
+    const int canon = (D == 0) ? z0 * 16 * 17 + f : (D == 1 ? z0 * 17 * 16 + f : z0 * 256 + f);
     const int64_t id = (int64_t)li * FACES_PER_LEAF + D * 4352 + canon;
     if (id % stride) continue;
     const int64_t o = id / stride;
     if (o >= cap) continue;
-    const RoeF e = roe_f32<D>(S, c0 + 2 * st, c0 + 3 * st, gm1);
+    const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1);
     float fe[15];
-    face_features_f32<D>(S, c0, st, e, fe);
+    face_features_f32(S, c0, st, e, fe);
 #pragma unroll
     for (int q = 0; q < 15; ++q) feats[o * 16 + q] = fe[q];
     feats[o * 16 + 15] = 0.f;
-    labels[o] = (uint8_t)face_label_f32<D>(S, c0, st, e, tau_lab);
+    labels[o] = (uint8_t)face_label_f32(S, c0, st, e, tau_lab);
     if (where) where[o] = id;
   }
   __syncthreads();
@@ -120,9 +107,9 @@ __global__ void __launch_bounds__(SF_THREADS) k_face_samples(Topo t, Phys p, Poo
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int li = w / SF_NSLAB, z0 = (w % SF_NSLAB) * SF_TZ;
     const double* u = pool.buf[cur] + (size_t)t.slot[t.leaves[li]] * SLOT_U;
-    sample_dir<0>(u, smp_smem, li, z0, g, B, gm1, tau_lab, stride, feats, labels, where, cap);
-    sample_dir<1>(u, smp_smem, li, z0, g, B, gm1, tau_lab, stride, feats, labels, where, cap);
-    sample_dir<2>(u, smp_smem, li, z0, g, B, gm1, tau_lab, stride, feats, labels, where, cap);
+#pragma unroll 1
+    for (int D = 0; D < 3; ++D)
+      sample_dir(D, u, smp_smem, li, z0, g, B, gm1, tau_lab, stride, feats, labels, where, cap);
   }
 }
 

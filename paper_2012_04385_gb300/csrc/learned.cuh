@@ -9,7 +9,9 @@
 // 32 x 16 @ 16 x 32 -> 32 x 32 @ 32 x 32 -> 32 x 32 @ 32 x 8 chain of
 // mma.sync.m16n8k16 (BF16 operands, FP32 accumulation).  Biases enter as the
 // accumulator's initial value; the FP32 result fragments of one layer are
-// packed to BF16 and reused directly as the A fragments of the next layer.
+// packed to BF16, passed through the GELU in packed BF16 arithmetic
+// (tanh.approx.bf16x2), and reused directly as the A fragments of the next
+// layer.
 //
 // Parameters (FP32 master copy, MRB_MLP_NPARAM = 1601 floats): W1[32][15],
 // b1[32], W2[32][32], b2[32], w3[32], b3.  The kernels round the weights to
@@ -46,15 +48,19 @@ __device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__device__ __forceinline__ float tanh_approx(float x) {
-  float y;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ float gelu_fast(float z) {
-  const float t = tanh_approx(GELU_K0 * fmaf(GELU_K1 * z, z * z, z));
-  return 0.5f * z * (1.f + t);
+// GELU (tanh form) of two pre-activations in packed BF16 arithmetic; the
+// result is the packed BF16 A operand of the next layer.
+__device__ __forceinline__ uint32_t gelu2_bf16(float z0, float z1) {
+  const __nv_bfloat162 z = __floats2bfloat162_rn(z0, z1);
+  const __nv_bfloat162 k0 = __float2bfloat162_rn(GELU_K0), k01 = __float2bfloat162_rn(GELU_K0 * GELU_K1);
+  const __nv_bfloat162 half = __float2bfloat162_rn(0.5f);
+  const __nv_bfloat162 z2 = __hmul2(z, z);
+  const __nv_bfloat162 arg = __hmul2(__hfma2(z2, k01, k0), z);   // k0 (z + k1 z^3)
+  uint32_t th;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(*reinterpret_cast<const uint32_t*>(&arg)));
+  const __nv_bfloat162 hz = __hmul2(z, half);
+  const __nv_bfloat162 out = __hfma2(*reinterpret_cast<const __nv_bfloat162*>(&th), hz, hz);
+  return *reinterpret_cast<const uint32_t*>(&out);
 }
 
 // Weight element B(k, n) of layer L as the B operand (k = input, n = output).
@@ -89,7 +95,7 @@ __device__ __forceinline__ float mlp_warp_logit(const float* __restrict__ P, con
                                                 uint32_t* rows, float* logit_sh) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   __syncwarp();
-#pragma unroll
+#pragma unroll 1
   for (int mt = 0; mt < 2; ++mt) {
     uint32_t a[4];
     a[0] = rows[(16 * mt + g) * 9 + t];
@@ -108,10 +114,10 @@ __device__ __forceinline__ float mlp_warp_logit(const float* __restrict__ P, con
     uint32_t a2[2][4];
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
-      a2[ks][0] = pack_bf16(gelu_fast(c1[2 * ks][0]), gelu_fast(c1[2 * ks][1]));
-      a2[ks][1] = pack_bf16(gelu_fast(c1[2 * ks][2]), gelu_fast(c1[2 * ks][3]));
-      a2[ks][2] = pack_bf16(gelu_fast(c1[2 * ks + 1][0]), gelu_fast(c1[2 * ks + 1][1]));
-      a2[ks][3] = pack_bf16(gelu_fast(c1[2 * ks + 1][2]), gelu_fast(c1[2 * ks + 1][3]));
+      a2[ks][0] = gelu2_bf16(c1[2 * ks][0], c1[2 * ks][1]);
+      a2[ks][1] = gelu2_bf16(c1[2 * ks][2], c1[2 * ks][3]);
+      a2[ks][2] = gelu2_bf16(c1[2 * ks + 1][0], c1[2 * ks + 1][1]);
+      a2[ks][3] = gelu2_bf16(c1[2 * ks + 1][2], c1[2 * ks + 1][3]);
     }
     // layer 2
     float c2[4][4];
@@ -129,10 +135,10 @@ __device__ __forceinline__ float mlp_warp_logit(const float* __restrict__ P, con
     uint32_t a3[2][4];
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
-      a3[ks][0] = pack_bf16(gelu_fast(c2[2 * ks][0]), gelu_fast(c2[2 * ks][1]));
-      a3[ks][1] = pack_bf16(gelu_fast(c2[2 * ks][2]), gelu_fast(c2[2 * ks][3]));
-      a3[ks][2] = pack_bf16(gelu_fast(c2[2 * ks + 1][0]), gelu_fast(c2[2 * ks + 1][1]));
-      a3[ks][3] = pack_bf16(gelu_fast(c2[2 * ks + 1][2]), gelu_fast(c2[2 * ks + 1][3]));
+      a3[ks][0] = gelu2_bf16(c2[2 * ks][0], c2[2 * ks][1]);
+      a3[ks][1] = gelu2_bf16(c2[2 * ks][2], c2[2 * ks][3]);
+      a3[ks][2] = gelu2_bf16(c2[2 * ks + 1][0], c2[2 * ks + 1][1]);
+      a3[ks][3] = gelu2_bf16(c2[2 * ks + 1][2], c2[2 * ks + 1][3]);
     }
     // layer 3 (output column 0)
     const float b3 = P[OFF_B3];

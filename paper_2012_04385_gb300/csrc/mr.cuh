@@ -101,25 +101,57 @@ __device__ __forceinline__ int sgn_region(int rel) { return rel < 0 ? -1 : (rel 
 // Sec. 3 (Fig. MrCommunicationMesh): a halo region facing a same-level node
 // is a copy of its internal cells, one facing no same-level node is predicted
 // from the node's parent (one parent cell, eight fine cells, per step).  One
-// work item per (node, halo region) on a persistent grid; k_fill_bc then
-// applies the boundary conditions.  With leaf_faces_only, leaves get only
-// their predicted face regions (the mixed-precision stage kernel reads face
-// neighbours' cells directly); internal nodes, whose halos feed their
-// children's predictions, are filled completely.
-__device__ __forceinline__ int region_extent(int s) { return s == 0 ? NB : HW; }
+// warp per (node, halo region) on a persistent grid; k_fill_bc then applies
+// the boundary conditions.  The nodes are those of one level, or a list.
+// Internal nodes, whose halos feed their children's predictions, are always
+// filled completely; leaves according to the fill mode (FILL_* in kernels.cuh).
+
+struct NodeSet {
+  int level;                // nodes of this level, when list is null
+  const int32_t* list;      // else these nodes
+  int n;
+};
+
+__device__ __forceinline__ void nodeset_range(const Topo& t, const NodeSet& ns, int& beg, int& cnt) {
+  if (ns.list) {
+    beg = 0;
+    cnt = ns.n;
+  } else {
+    beg = t.cnt[CNT_LVL + ns.level];
+    cnt = t.cnt[CNT_LVL + ns.level + 1] - beg;
+  }
+}
+__device__ __forceinline__ int nodeset_node(const Topo& t, const NodeSet& ns, int beg, int i) {
+  return ns.list ? ns.list[i] : t.lvl_nodes[beg + i];
+}
+
+// Variable q of the fill: all five, or rho (q = 0) and E (q = 1) only.
+__device__ __forceinline__ int fill_var(bool detail_only, int q) { return detail_only ? 4 * q : q; }
+
 __device__ __forceinline__ int region_start(int s) { return s < 0 ? -HW : (s == 0 ? 0 : NB); }
 
+__device__ __forceinline__ int region_log2(int s) { return s == 0 ? 4 : 2; }   // extents 16 or 4
+
+// One warp per (node, halo region).  Extents are powers of two, so the element
+// index splits with shifts; copies move 16-byte pairs of doubles (every
+// region row starts on a 32-byte boundary of the 24^3 array).
 template <class R>
-__global__ void __launch_bounds__(256) k_fill_regions_t(Topo t, Pool pool, int cur, int level, int leaf_faces_only) {
-  const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
+__global__ void __launch_bounds__(256) k_fill_regions_t(Topo t, Pool pool, int cur, NodeSet ns, int mode) {
+  int beg, cnt;
+  nodeset_range(t, ns, beg, cnt);
   double* buf = pool.buf[cur];
-  const int nitems = (end - beg) * 26;
-  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-    const int node = t.lvl_nodes[beg + w / 26];
+  const int nitems = cnt * 26;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < nitems; w += gridDim.x * wpb) {
+    const int node = nodeset_node(t, ns, beg, w / 26);
     const int r = w % 26 < 13 ? w % 26 : w % 26 + 1;      // skip the centre
     const int sx = r % 3 - 1, sy = (r / 3) % 3 - 1, sz = r / 9 - 1;
     const bool face = (sx != 0) + (sy != 0) + (sz != 0) == 1;
-    const bool partial = leaf_faces_only && t.child0[node] < 0;
+    const bool leaf = t.child0[node] < 0;
+    const bool partial = mode == FILL_STAGE && leaf;
+    const bool detail_only = mode == FILL_DETAIL && leaf;
+    const int nvar = detail_only ? 2 : NV;
     if (partial && !face) continue;
     const int nb = t.nbr[(size_t)node * 27 + r];
     const int par = t.parent[node];
@@ -127,25 +159,39 @@ __global__ void __launch_bounds__(256) k_fill_regions_t(Topo t, Pool pool, int c
     if (nb >= 0) {
       if (partial) continue;                              // read directly by the stage kernel
       const double* src = buf + (size_t)t.slot[nb] * SLOT_U;
-      const int ex = region_extent(sx), ey = region_extent(sy), ez = region_extent(sz);
+      const int lx = region_log2(sx) - 1, ly = region_log2(sy), lz = region_log2(sz);   // x in pairs
       const int x0 = region_start(sx), y0 = region_start(sy), z0 = region_start(sz);
-      const int n = ex * ey * ez;
-      for (int e = threadIdx.x; e < n * NV; e += blockDim.x) {
-        const int v = e / n, c = e % n;
-        const int i = x0 + c % ex, j = y0 + (c / ex) % ey, k = z0 + c / (ex * ey);
-        u[v * NCELL + sidx(i, j, k)] = src[v * NCELL + sidx(i - NB * sx, j - NB * sy, k - NB * sz)];
+      const int lxy = lx + ly, ln = lxy + lz;
+      const int soff = -NB * (sx + NS * (sy + NS * sz));
+      const int ne = nvar << ln;               // a multiple of 32
+      // four 16-byte loads in flight per lane before their stores
+      for (int e0 = lane; e0 < ne; e0 += 128) {
+        double2 val[4];
+        int dst[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = e0 + 32 * q;
+          const int v = fill_var(detail_only, e >> ln), c = e & ((1 << ln) - 1);
+          const int i = x0 + 2 * (c & ((1 << lx) - 1)), j = y0 + ((c >> lx) & ((1 << ly) - 1)), k = z0 + (c >> lxy);
+          dst[q] = v * NCELL + sidx(i, j, k);
+          if (e < ne) val[q] = *reinterpret_cast<const double2*>(src + dst[q] + soff);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (e0 + 32 * q < ne) *reinterpret_cast<double2*>(u + dst[q]) = val[q];
       }
     } else if (nb == -1 && par >= 0) {
       const double* P = buf + (size_t)t.slot[par] * SLOT_U;
       const int ch = (int)(t.keys[node] & 7ull);
       const int cb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
-      // parent cells covering the region, relative to the child's origin
-      const int px = sx < 0 ? 2 : (sx == 0 ? 8 : 2), py = sy < 0 ? 2 : (sy == 0 ? 8 : 2), pz = sz < 0 ? 2 : (sz == 0 ? 8 : 2);
+      // parent cells covering the region, relative to the child's origin:
+      // 8 (interior range) or 2 (halo range) per axis
+      const int lx = sx == 0 ? 3 : 1, ly = sy == 0 ? 3 : 1, lz = sz == 0 ? 3 : 1;
       const int qx0 = sx < 0 ? -2 : (sx == 0 ? 0 : 8), qy0 = sy < 0 ? -2 : (sy == 0 ? 0 : 8), qz0 = sz < 0 ? -2 : (sz == 0 ? 0 : 8);
-      const int n = px * py * pz;
-      for (int e = threadIdx.x; e < n * NV; e += blockDim.x) {
-        const int v = e / n, c = e % n;
-        const int rx = qx0 + c % px, ry = qy0 + (c / px) % py, rz = qz0 + c / (px * py);
+      const int lxy = lx + ly, ln = lxy + lz;
+      for (int e = lane; e < (nvar << ln); e += 32) {
+        const int v = fill_var(detail_only, e >> ln), c = e & ((1 << ln) - 1);
+        const int rx = qx0 + (c & ((1 << lx) - 1)), ry = qy0 + ((c >> lx) & ((1 << ly) - 1)), rz = qz0 + (c >> lxy);
         const QT<R> qt = qterms_t<R>(P + v * NCELL, 8 * cb[0] + rx, 8 * cb[1] + ry, 8 * cb[2] + rz);
 #pragma unroll
         for (int sub = 0; sub < 8; ++sub) {
@@ -158,47 +204,83 @@ __global__ void __launch_bounds__(256) k_fill_regions_t(Topo t, Pool pool, int c
   }
 }
 
-// Boundary passes x-, x+, y-, y+, z-, z+ of the nodes of `level` on the
-// domain boundary (after their copies and predictions).
-static __global__ void __launch_bounds__(256) k_fill_bc(Topo t, Phys p, Pool pool, int cur, int level) {
-  const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
+// Boundary conditions of the nodes of `level` on the domain boundary (after
+// their copies and predictions).  The oracle applies the x, y and z passes in
+// turn; their composition maps each ghost cell to one source cell, every
+// coordinate beyond a non-periodic side being mapped back into the block
+// (zero gradient: the nearest internal cell; any other condition: the mirror
+// cell, with the normal momentum negated under symmetry).  So one warp per
+// (node, side) fills the side's 4 x 24 x 24 slab from source cells that this
+// kernel never writes; cells in two slabs get the same value twice.
+__device__ __forceinline__ int bc_map(int x, int blo, int bhi, int& flip, int bit) {
+  if (x < 0 && blo >= 0) {
+    flip ^= (blo == 2) ? bit : 0;
+    return blo == 0 ? 0 : -1 - x;
+  }
+  if (x >= NB && bhi >= 0) {
+    flip ^= (bhi == 2) ? bit : 0;
+    return bhi == 0 ? NB - 1 : 2 * NB - 1 - x;
+  }
+  return x;
+}
+
+static __global__ void __launch_bounds__(256) k_fill_bc(Topo t, Phys p, Pool pool, int cur, NodeSet ns, int mode) {
+  int beg, cnt;
+  nodeset_range(t, ns, beg, cnt);
   double* buf = pool.buf[cur];
-  for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
-    const int node = t.lvl_nodes[w];
-    bool any = false;
-    for (int d = 0; d < 3; ++d) {
-      const int nl = p.nb[d] << level, Xd = t.X[(size_t)node * 3 + d];
-      any = any || (Xd == 0 && p.bc[2 * d] != 1) || (Xd == nl - 1 && p.bc[2 * d + 1] != 1);
+  const int nitems = cnt * 6;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < nitems; w += gridDim.x * wpb) {
+    const int node = nodeset_node(t, ns, beg, w / 6);
+    const int side = w % 6, d = side >> 1;
+    const int level = t.level[node];
+    const bool detail_only = mode == FILL_DETAIL && t.child0[node] < 0;
+    int blo[3], bhi[3];   // condition of each boundary side of this node, -1 if none (or periodic)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int nl = p.nb[q] << level, Xq = t.X[(size_t)node * 3 + q];
+      blo[q] = (Xq == 0 && p.bc[2 * q] != 1) ? p.bc[2 * q] : -1;
+      bhi[q] = (Xq == nl - 1 && p.bc[2 * q + 1] != 1) ? p.bc[2 * q + 1] : -1;
     }
-    if (!any) continue;
+    const int bself = (side & 1) ? (d == 0 ? bhi[0] : (d == 1 ? bhi[1] : bhi[2]))
+                                 : (d == 0 ? blo[0] : (d == 1 ? blo[1] : blo[2]));
+    if (bself < 0) continue;
     double* u = buf + (size_t)t.slot[node] * SLOT_U;
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-#pragma unroll 1
-      for (int side = 0; side < 2; ++side) {
-        const int bc = p.bc[2 * d + side];
-        if (bc == 1) continue;
-        const int nl = p.nb[d] << level;
-        const int Xd = t.X[(size_t)node * 3 + d];
-        if (side == 0 && Xd != 0) continue;
-        if (side == 1 && Xd != nl - 1) continue;
-        for (int e = threadIdx.x; e < HW * NS * NS; e += blockDim.x) {
-          const int g0 = e % HW, a1 = (e / HW) % NS - HW, a2 = e / (HW * NS) - HW;
-          const int a = (side == 0) ? (-1 - g0) : (NB + g0);
-          const int sa = (bc == 0) ? ((side == 0) ? 0 : NB - 1) : ((side == 0) ? (-1 - a) : (2 * NB - 1 - a));
-          int di, si;
-          if (d == 0) { di = sidx(a, a1, a2); si = sidx(sa, a1, a2); }
-          else if (d == 1) { di = sidx(a2, a, a1); si = sidx(a2, sa, a1); }
-          else { di = sidx(a1, a2, a); si = sidx(a1, a2, sa); }
+    constexpr int n = HW * NS * NS;           // 2304 = 72 x 32
+    for (int e0 = lane; e0 < n; e0 += 4 * 32) {
+      double val[4][NV];
+      int di[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + 32 * q;
+        const int g0 = e % HW, a1 = (e / HW) % NS - HW, a2 = e / (HW * NS) - HW;
+        const int a = (side & 1) ? NB + g0 : -1 - g0;
+        const int x = (d == 0) ? a : (d == 1 ? a2 : a1);
+        const int y = (d == 0) ? a1 : (d == 1 ? a : a2);
+        const int z = (d == 0) ? a2 : (d == 1 ? a1 : a);
+        int flip = 0;
+        const int sx = bc_map(x, blo[0], bhi[0], flip, 1);
+        const int sy = bc_map(y, blo[1], bhi[1], flip, 2);
+        const int sz = bc_map(z, blo[2], bhi[2], flip, 4);
+        di[q] = sidx(x, y, z);
+        const int si = sidx(sx, sy, sz);
+        if (e < n) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            double val = u[v * NCELL + si];
-            if (bc == 2 && v == 1 + d) val = -val;
-            u[v * NCELL + di] = val;
+            if (detail_only && v >= 1 && v <= 3) continue;
+            const double s = u[v * NCELL + si];
+            val[q][v] = (v >= 1 && v <= 3 && ((flip >> (v - 1)) & 1)) ? -s : s;
           }
         }
-        __syncthreads();
       }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (e0 + 32 * q < n) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            if (!(detail_only && v >= 1 && v <= 3)) u[v * NCELL + di[q]] = val[q][v];
+        }
     }
   }
 }

@@ -4,15 +4,19 @@
 // of the FP64 state in FP64.
 //
 // Work item = (leaf, z-slab of 16 x 16 x 4 cells); a CTA of 256 threads loops
-// over items.  For each direction the stencil region of the slab (the slab
-// plus 3 cells on both sides along that direction) is converted once from the
-// FP64 stage buffer into FP32 primitive records in shared memory; then one
-// thread per face computes the face flux from six records, writes it to
-// shared memory (and, on the block boundary, to the block's face buffers), and
-// each thread adds the flux differences of the four cells of its (i, j)
-// column.  Reciprocals and square roots use the fast hardware approximations;
-// the WENO weights need one reciprocal: omega_k = d_k P_k / sum_j d_j P_j with
-// P_k the product of the other two (eps + beta)^2.
+// over items.  For each direction D (a run-time loop in the learned-selector
+// variant, whose face code would not fit the instruction cache three times;
+// unrolled with constant D otherwise) the stencil region of the slab -- the slab plus
+// 3 cells on both sides along D -- is converted once from the FP64 stage buffer
+// into FP32 primitive records in shared memory, with the velocity rotated into
+// the direction's frame (normal, tangential 1, tangential 2).  One thread per
+// face then computes the face flux from six records, writes it to shared
+// memory (and, on the block boundary, to the block's face buffers), and each
+// thread adds the flux differences of the four cells of its (i, j) column.
+// Reciprocals and square roots use the fast hardware approximations; WENO5
+// works on the consecutive differences of its five values and needs one
+// reciprocal: omega_k = d_k P_k / sum_j d_j P_j with P_k the product of the
+// other two (eps + beta)^2.
 #pragma once
 
 #include "convert.cuh"
@@ -26,7 +30,7 @@ constexpr int SF_NSLAB = NB / SF_TZ;
 constexpr int SF_THREADS = 256;
 constexpr int SF_REG = NB * NB * (SF_TZ + 6);            // largest stencil region (z): 2560 cells
 constexpr int SF_FMAX = NB * NB * (SF_TZ + 1);           // largest face count (z): 1280
-constexpr int SF_NREC = 7;                                // rho, u, v, w, p, E, c
+constexpr int SF_NREC = 7;                                // rho, u_n, u_t1, u_t2, p, E, c
 constexpr size_t SF_SMEM = sizeof(float) * (SF_NREC * SF_REG + NV * SF_FMAX);
 // learned selector scratch: B fragments, per-warp feature rows and logits
 constexpr size_t SF_SMEM_LEARNED = SF_SMEM + sizeof(uint32_t) * (FRAG_N + (SF_THREADS / 32) * 32 * 9) +
@@ -37,25 +41,31 @@ __device__ __constant__ static const double kSfB[3] = {1.0, 0.25, 2.0 / 3.0};
 
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 
-// WENO5-JS with a single reciprocal
+// Three-way select by direction (D = 0, 1, 2).
+__device__ __forceinline__ float sel3(int D, float a, float b, float c) { return D == 0 ? a : (D == 1 ? b : c); }
+__device__ __forceinline__ int sel3i(int D, int a, int b, int c) { return D == 0 ? a : (D == 1 ? b : c); }
+
+// WENO5-JS on the differences da = a-b, db = b-c, dc = c-d, dd = d-e; the
+// smoothness indicators are scaled by 12 (beta' = 13 t1^2 + 3 t2^2) together
+// with eps' = 12 eps, which leaves the weights unchanged, and the candidate
+// stencils are written as c + (linear combination of differences) / 6.
 __device__ __forceinline__ float weno5f(float a, float b, float c, float d, float e) {
-  const float eps = 1e-6f;
-  float t1 = fmaf(-2.f, b, a) + c, t2 = fmaf(3.f, c, fmaf(-4.f, b, a));
-  float s0 = eps + fmaf(13.f / 12.f * t1, t1, 0.25f * t2 * t2);
-  t1 = fmaf(-2.f, c, b) + d;
-  t2 = b - d;
-  float s1 = eps + fmaf(13.f / 12.f * t1, t1, 0.25f * t2 * t2);
-  t1 = fmaf(-2.f, d, c) + e;
-  t2 = fmaf(-4.f, d, 3.f * c) + e;
-  float s2 = eps + fmaf(13.f / 12.f * t1, t1, 0.25f * t2 * t2);
+  const float da = a - b, db = b - c, dc = c - d, dd = d - e;
+  const float eps12 = 12e-6f;
+  float t1 = da - db, t2 = fmaf(-3.f, db, da);
+  float s0 = fmaf(13.f * t1, t1, fmaf(3.f * t2, t2, eps12));
+  t1 = db - dc;
+  t2 = db + dc;
+  float s1 = fmaf(13.f * t1, t1, fmaf(3.f * t2, t2, eps12));
+  t1 = dc - dd;
+  t2 = fmaf(3.f, dc, -dd);
+  float s2 = fmaf(13.f * t1, t1, fmaf(3.f * t2, t2, eps12));
   s0 *= s0;
   s1 *= s1;
   s2 *= s2;
   const float w0 = 0.1f * (s1 * s2), w1 = 0.6f * (s0 * s2), w2 = 0.3f * (s0 * s1);
-  const float q0 = fmaf(11.f, c, fmaf(-7.f, b, 2.f * a));
-  const float q1 = fmaf(2.f, d, fmaf(5.f, c, -b));
-  const float q2 = fmaf(-1.f, e, fmaf(5.f, d, 2.f * c));
-  return fmaf(w0, q0, fmaf(w1, q1, w2 * q2)) * frcp(6.f * (w0 + w1 + w2));
+  const float e0 = fmaf(2.f, da, -5.f * db), e1 = fmaf(-2.f, dc, -db), e2 = fmaf(-4.f, dc, dd);
+  return fmaf(fmaf(w0, e0, fmaf(w1, e1, w2 * e2)), frcp(6.f * (w0 + w1 + w2)), c);
 }
 
 __device__ __forceinline__ float linear5f(float a, float b, float c, float d, float e) {
@@ -63,24 +73,17 @@ __device__ __forceinline__ float linear5f(float a, float b, float c, float d, fl
   return fmaf(2.f / 60.f, a, fmaf(-13.f / 60.f, b, fmaf(47.f / 60.f, c, fmaf(27.f / 60.f, d, (-3.f / 60.f) * e))));
 }
 
-template <bool LIN>
-__device__ __forceinline__ float rec5(float a, float b, float c, float d, float e) {
-  return LIN ? linear5f(a, b, c, d, e) : weno5f(a, b, c, d, e);
-}
-
-// Roe average of the face between the records at cl and cr (rotated frame of
-// direction D) and the cell eigenvalue ingredients of the two face cells.
+// Roe average of the face between the records at cl and cr (direction frame)
+// and the cell eigenvalue ingredients of the two face cells.
 struct RoeF {
   float un, ut1, ut2, H, q2, c, ic, b1, b2, hb1, unL, unR, cL, cR;
 };
 
-template <int D>
 __device__ __forceinline__ RoeF roe_f32(const float* __restrict__ S, int cl, int cr, float gm1) {
-  constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
   RoeF e;
   const float rL = S[cl], rR = S[cr];
-  e.unL = S[(1 + A0) * SF_REG + cl];
-  e.unR = S[(1 + A0) * SF_REG + cr];
+  e.unL = S[SF_REG + cl];
+  e.unR = S[SF_REG + cr];
   e.cL = S[6 * SF_REG + cl];
   e.cR = S[6 * SF_REG + cr];
   // sqrt(rho) weights, H = (E + p) / rho
@@ -88,8 +91,8 @@ __device__ __forceinline__ RoeF roe_f32(const float* __restrict__ S, int cl, int
   const float sL = rL * rsL, sR = rR * rsR;
   const float iden = frcp(sL + sR);
   e.un = fmaf(sL, e.unL, sR * e.unR) * iden;
-  e.ut1 = fmaf(sL, S[(1 + A1) * SF_REG + cl], sR * S[(1 + A1) * SF_REG + cr]) * iden;
-  e.ut2 = fmaf(sL, S[(1 + A2) * SF_REG + cl], sR * S[(1 + A2) * SF_REG + cr]) * iden;
+  e.ut1 = fmaf(sL, S[2 * SF_REG + cl], sR * S[2 * SF_REG + cr]) * iden;
+  e.ut2 = fmaf(sL, S[3 * SF_REG + cl], sR * S[3 * SF_REG + cr]) * iden;
   e.H = fmaf(S[5 * SF_REG + cl] + S[4 * SF_REG + cl], rsL, (S[5 * SF_REG + cr] + S[4 * SF_REG + cr]) * rsR) * iden;
   e.q2 = fmaf(e.un, e.un, fmaf(e.ut1, e.ut1, e.ut2 * e.ut2));
   const float c2 = gm1 * fmaf(-0.5f, e.q2, e.H);
@@ -126,11 +129,10 @@ __device__ __forceinline__ void lrow_f32(const RoeF& e, int k, float l[5]) {
   }
 }
 
-// Rotated conserved state and physical flux of the record at c.
-template <int D>
+// Conserved state and physical flux of the record at c in the direction frame
+// (index 1 normal, 2 and 3 tangential).
 __device__ __forceinline__ void cell_uf(const float* __restrict__ S, int c, float U[5], float F[5]) {
-  constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
-  const float r = S[c], un = S[(1 + A0) * SF_REG + c], u1 = S[(1 + A1) * SF_REG + c], u2 = S[(1 + A2) * SF_REG + c];
+  const float r = S[c], un = S[SF_REG + c], u1 = S[2 * SF_REG + c], u2 = S[3 * SF_REG + c];
   const float p = S[4 * SF_REG + c], E = S[5 * SF_REG + c];
   const float mn = r * un;
   U[0] = r;
@@ -145,43 +147,41 @@ __device__ __forceinline__ void cell_uf(const float* __restrict__ S, int c, floa
   F[4] = un * (E + p);
 }
 
-__device__ __forceinline__ float rec5_rt(bool lin, float a, float b, float c, float d, float e) {
+template <int MODE>
+__device__ __forceinline__ float rec5(bool lin, float a, float b, float c, float d, float e) {
+  if (MODE == 2) return linear5f(a, b, c, d, e);
+  if (MODE == 0) return weno5f(a, b, c, d, e);
   return lin ? linear5f(a, b, c, d, e) : weno5f(a, b, c, d, e);
 }
 
 // Face flux between stencil cells 2 and 3 (cells at S index c0 + m*st, m = 0..5)
-// along D, from the FP32 records; result in the lab frame.  MODE 0: WENO5,
+// from the FP32 records; result in the direction frame.  MODE 0: WENO5,
 // 2: linear, 1: per-face choice `lin` for fields 0, 1, 4 (learned selector;
-// the shear fields keep WENO5).
-template <int D, int MODE>
+// the shear fields keep WENO5).  In MODE 1 one reconstruction site per field
+// serves both upwind cases and, run twice, the two halves of the LLF split.
+template <int MODE>
 __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, float gm1, bool lin,
                                               float F[5]) {
-  constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
   float Ur[6][5], Fr[6][5];
 #pragma unroll
-  for (int m = 0; m < 6; ++m) cell_uf<D>(S, c0 + m * st, Ur[m], Fr[m]);
-  const RoeF e = roe_f32<D>(S, c0 + 2 * st, c0 + 3 * st, gm1);
+  for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, Ur[m], Fr[m]);
+  const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1);
   float Fh0 = 0.f, Fh1 = 0.f, Fh2 = 0.f, Fh3 = 0.f, Fh4 = 0.f;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     // the selector decides for the acoustic and entropy fields; shear fields keep WENO5
-    const bool use_lin = (MODE == 2) || (MODE == 1 && lin && (k == 0 || k == 1 || k == 4));
-    float G[6], V[6];
+    const bool use_lin = (MODE == 1) && lin && (k == 0 || k == 1 || k == 4);
+    float G[6];
     float l[5];
     lrow_f32(e, k, l);
     if (k == 2 || k == 3) {
       const int j = (k == 2) ? 2 : 3;
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        V[m] = fmaf(l[0], Ur[m][0], Ur[m][j]);
-        G[m] = fmaf(l[0], Fr[m][0], Fr[m][j]);
-      }
+      for (int m = 0; m < 6; ++m) G[m] = fmaf(l[0], Fr[m][0], Fr[m][j]);
     } else {
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        V[m] = fmaf(l[0], Ur[m][0], fmaf(l[1], Ur[m][1], fmaf(l[2], Ur[m][2], fmaf(l[3], Ur[m][3], l[4] * Ur[m][4]))));
+      for (int m = 0; m < 6; ++m)
         G[m] = fmaf(l[0], Fr[m][0], fmaf(l[1], Fr[m][1], fmaf(l[2], Fr[m][2], fmaf(l[3], Fr[m][3], l[4] * Fr[m][4]))));
-      }
     }
     float lL, lR, lt;
     if (k == 0 || k == 4) {
@@ -194,13 +194,47 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
       lR = e.unR;
       lt = e.un;
     }
+    const bool pos = lL > 0.f && lR > 0.f && lt > 0.f;
+    const bool llf = !pos && !(lL < 0.f && lR < 0.f && lt < 0.f);
+    // upwind: W+ of G (pos) or W- of G; LLF: W+ of (G + a V)/2 and W- of (G - a V)/2
+    float V[6];
+    if (llf) {
+      if (k == 2 || k == 3) {
+        const int j = (k == 2) ? 2 : 3;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) V[m] = fmaf(l[0], Ur[m][0], Ur[m][j]);
+      } else {
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+          V[m] = fmaf(l[0], Ur[m][0], fmaf(l[1], Ur[m][1], fmaf(l[2], Ur[m][2], fmaf(l[3], Ur[m][3], l[4] * Ur[m][4]))));
+      }
+    }
     float gh;
-    if (lL > 0.f && lR > 0.f && lt > 0.f) {
-      gh = (MODE == 1) ? rec5_rt(use_lin, G[0], G[1], G[2], G[3], G[4])
-                       : (use_lin ? linear5f(G[0], G[1], G[2], G[3], G[4]) : weno5f(G[0], G[1], G[2], G[3], G[4]));
-    } else if (lL < 0.f && lR < 0.f && lt < 0.f) {
-      gh = (MODE == 1) ? rec5_rt(use_lin, G[5], G[4], G[3], G[2], G[1])
-                       : (use_lin ? linear5f(G[5], G[4], G[3], G[2], G[1]) : weno5f(G[5], G[4], G[3], G[2], G[1]));
+    if (MODE == 1) {
+      // one reconstruction site (the kernel's code size matters more than its schedule)
+      float in[6];
+      const float ha = llf ? 0.5f * fmaxf(fabsf(lL), fabsf(lR)) : 0.f;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        in[m] = llf ? 0.5f * G[m] : G[m];
+        if (llf) G[m] = ha * V[m];                // G now holds a V / 2
+      }
+      gh = 0.f;
+      bool fwd = pos || llf;
+#pragma unroll 1
+      for (int pass = 0; pass < (llf ? 2 : 1); ++pass) {
+        // pass 0: W+ (fwd) or W- of the upwind values; pass 1 (LLF only): W- of (G - a V)/2
+        float x[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) x[m] = llf ? (pass == 0 ? in[m] + G[m] : in[m] - G[m]) : in[m];
+        gh += rec5<MODE>(use_lin, fwd ? x[0] : x[5], fwd ? x[1] : x[4], fwd ? x[2] : x[3], fwd ? x[3] : x[2],
+                         fwd ? x[4] : x[1]);
+        fwd = false;
+      }
+    } else if (pos) {
+      gh = rec5<MODE>(false, G[0], G[1], G[2], G[3], G[4]);
+    } else if (!llf) {
+      gh = rec5<MODE>(false, G[5], G[4], G[3], G[2], G[1]);
     } else {
       const float ha = 0.5f * fmaxf(fabsf(lL), fabsf(lR));
       float fp[6], fm[6];
@@ -209,12 +243,7 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
         fp[m] = fmaf(0.5f, G[m], ha * V[m]);
         fm[m] = fmaf(0.5f, G[m], -ha * V[m]);
       }
-      if (MODE == 1)
-        gh = rec5_rt(use_lin, fp[0], fp[1], fp[2], fp[3], fp[4]) + rec5_rt(use_lin, fm[5], fm[4], fm[3], fm[2], fm[1]);
-      else if (use_lin)
-        gh = linear5f(fp[0], fp[1], fp[2], fp[3], fp[4]) + linear5f(fm[5], fm[4], fm[3], fm[2], fm[1]);
-      else
-        gh = weno5f(fp[0], fp[1], fp[2], fp[3], fp[4]) + weno5f(fm[5], fm[4], fm[3], fm[2], fm[1]);
+      gh = rec5<MODE>(false, fp[0], fp[1], fp[2], fp[3], fp[4]) + rec5<MODE>(false, fm[5], fm[4], fm[3], fm[2], fm[1]);
     }
     // F_hat = R g_hat, columns r0 = (1, u-c, ut1, ut2, H-uc), r1 = (1, u, ut1, ut2, q2/2),
     // r2 = (0, 0, 1, 0, ut1), r3 = (0, 0, 0, 1, ut2), r4 = (1, u+c, ut1, ut2, H+uc)
@@ -240,9 +269,9 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
     }
   }
   F[0] = Fh0;
-  F[1 + A0] = Fh1;
-  F[1 + A1] = Fh2;
-  F[1 + A2] = Fh3;
+  F[1] = Fh1;
+  F[2] = Fh2;
+  F[3] = Fh3;
   F[4] = Fh4;
 }
 
@@ -251,7 +280,6 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
 // s (|dg| + alpha_k |dv|) of the characteristic fluxes g = L_k F(U_m) and
 // variables v = L_k U_m over the six stencil cells (alpha_k the field's LLF
 // speed, s the sign of dg, of dv where dg is zero).
-template <int D>
 __device__ __forceinline__ void face_features_f32(const float* __restrict__ S, int c0, int st, const RoeF& e,
                                                   float f[15]) {
   float l[3][5], alpha[3];
@@ -265,7 +293,7 @@ __device__ __forceinline__ void face_features_f32(const float* __restrict__ S, i
 #pragma unroll
   for (int m = 0; m < 6; ++m) {
     float U[5], F[5];
-    cell_uf<D>(S, c0 + m * st, U, F);
+    cell_uf(S, c0 + m * st, U, F);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const float gq = fmaf(l[q][0], F[0], fmaf(l[q][1], F[1], fmaf(l[q][2], F[2], fmaf(l[q][3], F[3], l[q][4] * F[4]))));
@@ -281,31 +309,34 @@ __device__ __forceinline__ void face_features_f32(const float* __restrict__ S, i
   }
 }
 
-// Stencil region of direction D for the slab at z0 -> FP32 records in S.
-// Cells beyond the block along D come from the same-level face neighbour's
-// internal cells when it exists (ulo/uhi, else null: the block's own halo,
-// filled by prediction or the boundary condition).
-template <int D>
-__device__ __forceinline__ void load_region_f32(const double* __restrict__ u, float* __restrict__ S, int z0, float g,
-                                                float B, float gm1, const double* __restrict__ ulo = nullptr,
+// Number of region records and faces of direction D for one slab.
+__device__ __forceinline__ int region_cells(int D) { return D == 2 ? SF_REG : 22 * 16 * SF_TZ; }
+__device__ __forceinline__ int region_faces(int D) { return D == 2 ? NB * NB * (SF_TZ + 1) : 17 * 16 * SF_TZ; }
+__device__ __forceinline__ int region_stride(int D) { return sel3i(D, 1, 16, 256); }
+
+// Stencil region of direction D for the slab at z0 -> FP32 records in S, the
+// velocity in the direction frame.  Cells beyond the block along D come from
+// the same-level face neighbour's internal cells when it exists (ulo/uhi,
+// else null: the block's own halo, filled by prediction or the boundary
+// condition).
+__device__ __forceinline__ void load_region_f32(int D, const double* __restrict__ u, float* __restrict__ S, int z0,
+                                                float g, float B, float gm1, const double* __restrict__ ulo = nullptr,
                                                 const double* __restrict__ uhi = nullptr) {
-  constexpr int n = (D == 2) ? SF_REG : 22 * 16 * SF_TZ;
+  const int n = region_cells(D);
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     int x, y, z;
     if (D == 0) { x = idx % 22 - 3; y = (idx / 22) % 16; z = z0 + idx / 352; }
     else if (D == 1) { x = idx % 16; y = (idx / 16) % 22 - 3; z = z0 + idx / 352; }
     else { x = idx % 16; y = (idx / 16) % 16; z = z0 - 3 + idx / 256; }
-    const int a = (D == 0) ? x : (D == 1 ? y : z);
+    const int a = sel3i(D, x, y, z);
     const double* src = u;
-    int s;
+    int s = sidx(x, y, z);
     if (a < 0 && ulo) {
       src = ulo;
-      s = (D == 0) ? sidx(x + NB, y, z) : (D == 1 ? sidx(x, y + NB, z) : sidx(x, y, z + NB));
+      s += sel3i(D, NB, NB * NS, NB * NS * NS);
     } else if (a >= NB && uhi) {
       src = uhi;
-      s = (D == 0) ? sidx(x - NB, y, z) : (D == 1 ? sidx(x, y - NB, z) : sidx(x, y, z - NB));
-    } else {
-      s = sidx(x, y, z);
+      s -= sel3i(D, NB, NB * NS, NB * NS * NS);
     }
     const float r = d2f_fast(src[s]), mx = d2f_fast(src[NCELL + s]), my = d2f_fast(src[2 * NCELL + s]);
     const float mz = d2f_fast(src[3 * NCELL + s]), E = d2f_fast(src[4 * NCELL + s]);
@@ -314,12 +345,37 @@ __device__ __forceinline__ void load_region_f32(const double* __restrict__ u, fl
     const float q2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
     const float p = fmaf(gm1, fmaf(-0.5f * r, q2, E), -g * B);
     S[idx] = r;
-    S[SF_REG + idx] = vx;
-    S[2 * SF_REG + idx] = vy;
-    S[3 * SF_REG + idx] = vz;
+    S[SF_REG + idx] = sel3(D, vx, vy, vz);
+    S[2 * SF_REG + idx] = sel3(D, vy, vz, vx);
+    S[3 * SF_REG + idx] = sel3(D, vz, vx, vy);
     S[4 * SF_REG + idx] = p;
     S[5 * SF_REG + idx] = E;
     S[6 * SF_REG + idx] = sqrtf(g * (p + B) * ir);
+  }
+}
+
+// Face f of direction D in the slab: first stencil record c0 and the face's
+// position (fa along D; ta, tb the block-face coordinates of a boundary face).
+__device__ __forceinline__ void face_of(int D, int f, int z0, int& fa, int& c0, int& ta, int& tb) {
+  if (D == 0) {
+    fa = f % 17;
+    const int r = f / 17;                 // row = kz * 16 + j
+    c0 = r * 22 + fa;                     // cell x = fa - 3 at record index fa
+    ta = r % 16;
+    tb = z0 + r / 16;
+  } else if (D == 1) {
+    const int i = f % 16, r = f / 16;     // r = kz * 17 + fa
+    fa = r % 17;
+    const int kz = r / 17;
+    c0 = (kz * 22 + fa) * 16 + i;
+    ta = i;
+    tb = z0 + kz;
+  } else {
+    const int i = f % 16, j = (f / 16) % 16;
+    fa = f / 256;
+    c0 = (fa * 16 + j) * 16 + i;
+    ta = i;
+    tb = j;
   }
 }
 
@@ -349,53 +405,41 @@ __device__ __forceinline__ bool stencil_flat(const float* __restrict__ S, int c0
   return flat;
 }
 
-template <int D, int MODE>
-__device__ __forceinline__ void sweep_f32(const double* __restrict__ u, double* __restrict__ fb, float* __restrict__ S,
-                                          float* __restrict__ Fs, int z0, float g, float B, float gm1,
-                                          float (&acc)[SF_TZ][NV], const LearnedCtx& L, const Topo& t,
+// Direction-frame flux components (normal, tangential 1, tangential 2) of
+// direction D -> lab components x, y, z.
+__device__ __forceinline__ void to_lab(int D, float n, float t1, float t2, float& x, float& y, float& z) {
+  x = sel3(D, n, t2, t1);
+  y = sel3(D, t1, n, t2);
+  z = sel3(D, t2, t1, n);
+}
+
+template <int MODE>
+__device__ __forceinline__ void sweep_f32(int D, const double* __restrict__ u, double* __restrict__ fb,
+                                          float* __restrict__ S, float* __restrict__ Fs, int z0, float g, float B,
+                                          float gm1, float (&acc)[SF_TZ][NV], const LearnedCtx& L, const Topo& t,
                                           const double* __restrict__ buf, int node) {
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   {
     // same-level face neighbours along D read directly
-    constexpr int rlo = (D == 0) ? 12 : (D == 1 ? 10 : 4), rhi = (D == 0) ? 14 : (D == 1 ? 16 : 22);
+    const int rlo = sel3i(D, 12, 10, 4), rhi = sel3i(D, 14, 16, 22);
     const int nlo = t.nbr[(size_t)node * 27 + rlo], nhi = t.nbr[(size_t)node * 27 + rhi];
     const double* ulo = (nlo >= 0) ? buf + (size_t)t.slot[nlo] * SLOT_U : nullptr;
     const double* uhi = (nhi >= 0) ? buf + (size_t)t.slot[nhi] * SLOT_U : nullptr;
-    load_region_f32<D>(u, S, z0, g, B, gm1, ulo, uhi);
+    load_region_f32(D, u, S, z0, g, B, gm1, ulo, uhi);
   }
   __syncthreads();
-  constexpr int nf = (D == 2) ? NB * NB * (SF_TZ + 1) : 17 * 16 * SF_TZ;
-  constexpr int st = (D == 0) ? 1 : (D == 1 ? 16 : 256);
+  const int nf = region_faces(D);
+  const int st = region_stride(D);
   const int nfr = (MODE == 1) ? ((nf + blockDim.x - 1) / blockDim.x) * blockDim.x : nf;
   for (int f0 = threadIdx.x; f0 < nfr; f0 += blockDim.x) {
     const bool act = f0 < nf;
     const int f = act ? f0 : 0;
     int fa, c0, ta, tb;
-    if (D == 0) {
-      fa = f % 17;
-      const int r = f / 17;                 // row = kz * 16 + j
-      c0 = r * 22 + fa;                     // cell x = fa - 3 at record index fa
-      ta = r % 16;
-      tb = z0 + r / 16;
-    } else if (D == 1) {
-      const int i = f % 16, r = f / 16;     // r = kz * 17 + fa
-      fa = r % 17;
-      const int kz = r / 17;
-      c0 = (kz * 22 + fa) * 16 + i;
-      ta = i;
-      tb = z0 + kz;
-    } else {
-      const int i = f % 16, j = (f / 16) % 16;
-      fa = f / 256;
-      c0 = (fa * 16 + j) * 16 + i;
-      ta = i;
-      tb = j;
-    }
+    face_of(D, f, z0, fa, c0, ta, tb);
     bool lin = false;
     if (MODE == 1) {
       // decision word of this warp's 32 consecutive faces
-      constexpr int doff = (D == 0) ? 0 : (D == 1 ? 34 : 68);
-      uint32_t* word = L.bits + (z0 / SF_TZ) * 108 + doff + (f0 >> 5);
+      uint32_t* word = L.bits + (z0 / SF_TZ) * 108 + D * 34 + (f0 >> 5);
       if (L.evaluate) {
         // flat stencils have all-zero features, whose logit z0 is known; the
         // warp runs the tensor-core MLP only when one of its faces is not flat
@@ -407,8 +451,8 @@ __device__ __forceinline__ void sweep_f32(const double* __restrict__ u, double* 
 #pragma unroll
             for (int q = 0; q < 15; ++q) fe[q] = 0.f;
           } else {
-            const RoeF e = roe_f32<D>(S, c0 + 2 * st, c0 + 3 * st, gm1);
-            face_features_f32<D>(S, c0, st, e, fe);
+            const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1);
+            face_features_f32(S, c0, st, e, fe);
           }
           const int wid = threadIdx.x >> 5;
           mlp_put_row(L.rows + wid * 32 * 9, fe);
@@ -429,14 +473,18 @@ __device__ __forceinline__ void sweep_f32(const double* __restrict__ u, double* 
     }
     if (!act) continue;
     float F[5];
-    face_flux_f32<D, MODE>(S, c0, st, gm1, lin, F);
+    face_flux_f32<MODE>(S, c0, st, gm1, lin, F);
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fs[v * SF_FMAX + f] = F[v];
     const int gface = (D == 2) ? z0 + fa : fa;
     if (gface == 0 || gface == NB) {
       const int side = 2 * D + (gface == NB ? 1 : 0);
+      float Fl[5];
+      Fl[0] = F[0];
+      Fl[4] = F[4];
+      to_lab(D, F[1], F[2], F[3], Fl[1], Fl[2], Fl[3]);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) fb[((side * NV + v) * NB + tb) * NB + ta] = f2d_fast(F[v]);
+      for (int v = 0; v < 5; ++v) fb[((side * NV + v) * NB + tb) * NB + ta] = f2d_fast(Fl[v]);
     }
   }
   __syncthreads();
@@ -446,11 +494,16 @@ __device__ __forceinline__ void sweep_f32(const double* __restrict__ u, double* 
     if (D == 0) { lo = (kz * 16 + tj) * 17 + ti; hi = lo + 1; }
     else if (D == 1) { lo = (kz * 17 + tj) * 16 + ti; hi = lo + 16; }
     else { lo = (kz * 16 + tj) * 16 + ti; hi = lo + 256; }
+    float d[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const float diff = Fs[v * SF_FMAX + lo] - Fs[v * SF_FMAX + hi];
-      acc[kz][v] = (D == 0) ? diff : acc[kz][v] + diff;
-    }
+    for (int v = 0; v < 5; ++v) d[v] = Fs[v * SF_FMAX + lo] - Fs[v * SF_FMAX + hi];
+    float dx, dy, dz;
+    to_lab(D, d[1], d[2], d[3], dx, dy, dz);
+    d[1] = dx;
+    d[2] = dy;
+    d[3] = dz;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[kz][v] = (D == 0) ? d[v] : acc[kz][v] + d[v];
   }
   __syncthreads();
 }
@@ -497,13 +550,23 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
     if (MODE == 1) L.bits = pool.sel + (size_t)slot * SLOT_SEL;
     float acc[SF_TZ][NV];
-    sweep_f32<0, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
-    sweep_f32<1, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
-    sweep_f32<2, MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+    if (MODE == 1) {
+      // the selector's code is large: one copy of the sweep, direction at run time
+#pragma unroll 1
+      for (int D = 0; D < 3; ++D) sweep_f32<MODE>(D, u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+    } else {
+      // direction-specialised copies (constant strides and index arithmetic)
+      sweep_f32<MODE>(0, u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+      sweep_f32<MODE>(1, u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+      sweep_f32<MODE>(2, u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+    }
     const double dx = ldexp(p.dx0, -t.level[node]);
     const double idx_ = 1.0 / dx;
     const double h = dt ? dt[t.inst[node]] : 0.0;
     const double hdx = h * idx_;
+    // the stage increment b_s dt / dx (sum of flux differences) is formed in
+    // FP32 and accumulated into the FP64 state
+    const float hf = d2f_fast(hdx), bhf = d2f_fast(kSfB[stage] * hdx);
 #pragma unroll
     for (int kz = 0; kz < SF_TZ; ++kz) {
       const int k = z0 + kz;
@@ -525,14 +588,15 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           const double us = u[v * NCELL + s];
-          double tt = fma(f2d_fast(acc[kz][v]), hdx, us);
-          if (p.has_grav) tt = fma(h, S4[v], tt);
           double out;
           if (stage == 0) {
             unb[v * NINT + ii] = us;
-            out = tt;
+            out = us + f2d_fast(acc[kz][v] * hf);
+            if (p.has_grav) out = fma(h, S4[v], out);
           } else {
-            out = fma(kSfA[stage], unb[v * NINT + ii], kSfB[stage] * tt);
+            double inc = f2d_fast(acc[kz][v] * bhf);
+            if (p.has_grav) inc = fma(kSfB[stage] * h, S4[v], inc);
+            out = fma(kSfA[stage], unb[v * NINT + ii], fma(kSfB[stage], us, inc));
           }
           o[v * NCELL + s] = out;
         }
