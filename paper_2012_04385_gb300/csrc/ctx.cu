@@ -65,11 +65,11 @@ struct mrb_ctx {
 
   std::vector<HNode> nodes;          // sorted by key
   std::vector<int32_t> free_slots;   // stack, back = next
-  std::vector<int32_t> h_parent, h_child0, h_leaves, h_lvl_nodes, h_cnt;
+  std::vector<int32_t> h_parent, h_child0, h_leaves, h_lvl_nodes, h_bc_items, h_cnt;
 
   uint64_t* d_keys = nullptr;
   int32_t *d_slot = nullptr, *d_level = nullptr, *d_inst = nullptr, *d_X = nullptr, *d_parent = nullptr,
-          *d_child0 = nullptr, *d_nbr = nullptr, *d_leaves = nullptr, *d_lvl_nodes = nullptr, *d_cnt = nullptr,
+          *d_child0 = nullptr, *d_nbr = nullptr, *d_leaves = nullptr, *d_lvl_nodes = nullptr, *d_bc_items = nullptr, *d_cnt = nullptr,
           *d_lmax = nullptr, *d_list = nullptr;
   double *d_dt = nullptr, *d_delta_node = nullptr, *d_partial = nullptr;
   unsigned long long* d_smax = nullptr;
@@ -103,6 +103,7 @@ struct mrb_ctx {
     t.nbr = d_nbr;
     t.leaves = d_leaves;
     t.lvl_nodes = d_lvl_nodes;
+    t.bc_items = d_bc_items;
     t.cnt = d_cnt;
     return t;
   }
@@ -146,6 +147,20 @@ struct mrb_ctx {
         if (nodes[i].level == l) h_lvl_nodes.push_back(i);
     }
     h_cnt[CNT_LVL + MAXL + 1] = (int)h_lvl_nodes.size();
+    // boundary-condition work: the non-periodic domain-boundary sides of each node
+    h_bc_items.clear();
+    for (int l = 0; l <= MAXL; ++l) {
+      h_cnt[CNT_BC + l] = (int)h_bc_items.size();
+      for (int q = h_cnt[CNT_LVL + l]; q < h_cnt[CNT_LVL + l + 1]; ++q) {
+        const int i = h_lvl_nodes[q];
+        for (int d = 0; d < 3; ++d) {
+          const int nl = cfg.base_blocks[d] << l;
+          if (nodes[i].X[d] == 0 && cfg.bc[2 * d] != MRB_BC_PERIODIC) h_bc_items.push_back(8 * i + 2 * d);
+          if (nodes[i].X[d] == nl - 1 && cfg.bc[2 * d + 1] != MRB_BC_PERIODIC) h_bc_items.push_back(8 * i + 2 * d + 1);
+        }
+      }
+    }
+    h_cnt[CNT_BC + MAXL + 1] = (int)h_bc_items.size();
     std::vector<uint64_t> k(n);
     std::vector<int32_t> s(n), lv(n), in(n), X(3 * (size_t)n);
     for (int i = 0; i < n; ++i) {
@@ -165,6 +180,9 @@ struct mrb_ctx {
     CK(cudaMemcpyAsync(d_leaves, h_leaves.data(), sizeof(int32_t) * h_leaves.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_lvl_nodes, h_lvl_nodes.data(), sizeof(int32_t) * h_lvl_nodes.size(), cudaMemcpyHostToDevice,
                        st));
+    if (!h_bc_items.empty())
+      CK(cudaMemcpyAsync(d_bc_items, h_bc_items.data(), sizeof(int32_t) * h_bc_items.size(), cudaMemcpyHostToDevice,
+                         st));
     CK(cudaMemcpyAsync(d_cnt, h_cnt.data(), sizeof(int32_t) * CNT_SIZE, cudaMemcpyHostToDevice, st));
     launch_nbr(topo(), phys, d_nbr, n, st);
     CK(cudaGetLastError());
@@ -486,6 +504,7 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     c->d_nbr = c->dalloc<int32_t>(27 * n);
     c->d_leaves = c->dalloc<int32_t>(n);
     c->d_lvl_nodes = c->dalloc<int32_t>(n);
+    c->d_bc_items = c->dalloc<int32_t>(6 * n);
     c->d_cnt = c->dalloc<int32_t>(CNT_SIZE);
     c->d_lmax = c->dalloc<int32_t>(cfg->n_instances);
     c->d_list = c->dalloc<int32_t>(2 * n);

@@ -33,16 +33,18 @@ void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int c
                            int mode) {
   const NodeSet ns{level, nullptr, 0};
   k_fill_regions_t<float><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, ns, mode);
+  k_fill_predict_t<float><<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, ns, mode);
   k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, mode);
-  g_kernel_launches += 2;
+  g_kernel_launches += 3;
 }
 
 void launch_fill_list_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* list, int n,
                           cudaStream_t st) {
   const NodeSet ns{0, list, n};
   k_fill_regions_t<float><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, ns, FILL_FULL);
+  k_fill_predict_t<float><<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, ns, FILL_FULL);
   k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, FILL_FULL);
-  g_kernel_launches += 2;
+  g_kernel_launches += 3;
 }
 
 void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, cudaStream_t st) {

@@ -104,8 +104,9 @@ void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, 
   const NodeSet ns{level, nullptr, 0};
   const int m = (mode == FILL_STAGE) ? FILL_FULL : mode;
   k_fill_regions_t<double><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, ns, m);
+  k_fill_predict_t<double><<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, ns, m);
   k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, m);
-  g_kernel_launches += 2;
+  g_kernel_launches += 3;
 }
 
 void launch_fill_list(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* list, int n,
@@ -117,8 +118,9 @@ void launch_fill_list(const Topo& t, const Phys& p, const Pool& pool, int cur, c
   }
   const NodeSet ns{0, list, n};
   k_fill_regions_t<double><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, ns, FILL_FULL);
+  k_fill_predict_t<double><<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, ns, FILL_FULL);
   k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, FILL_FULL);
-  g_kernel_launches += 2;
+  g_kernel_launches += 3;
 }
 
 // ---------------------------------------------------------------- RHS + RK (FP64)

@@ -11,7 +11,8 @@ namespace mrb {
 
 constexpr int MAXL = 11;              // deepest level
 constexpr int CNT_NNODES = 0, CNT_NLEAVES = 1, CNT_LVL = 2;   // lvl offsets at CNT_LVL + l, l = 0..MAXL+1
-constexpr int CNT_SIZE = CNT_LVL + MAXL + 2;
+constexpr int CNT_BC = CNT_LVL + MAXL + 2;                     // bc item offsets at CNT_BC + l, l = 0..MAXL+1
+constexpr int CNT_SIZE = CNT_BC + MAXL + 2;
 
 enum : int { ST_OK = 0, ST_NONPHYS = 6 };
 
@@ -34,6 +35,7 @@ struct Topo {
   const int32_t* nbr;      // [n][27] same-level neighbour node, -1 none, -2 beyond the boundary
   const int32_t* leaves;   // leaf node indices, ascending id
   const int32_t* lvl_nodes;// node indices grouped by level
+  const int32_t* bc_items; // 8 * node + side of every non-periodic domain-boundary side, grouped by level
   const int32_t* cnt;      // counts, see CNT_*
 };
 

@@ -25,42 +25,55 @@ template <> __device__ __forceinline__ float to_r<float>(double x) { return d2f_
 template <class R> __device__ __forceinline__ double from_r(R x) { return double(x); }
 template <> __device__ __forceinline__ double from_r<float>(float x) { return f2d_fast(x); }
 
-template <class R> __device__ __forceinline__ R pld(const double* P, int i, int j, int k) {
-  return to_r<R>(P[sidx(i, j, k)]);
-}
+// Parent values for the Q-terms: the stored FP64 array, converted to R on
+// load, or a box of R values staged in shared memory (origin i0, j0, k0 in
+// stored coordinates, row length nx, plane size nxy).  Both give the same R
+// value for a cell, so the Q-terms do not depend on where they are read.
+template <class R> struct GAcc {
+  const double* P;
+  __device__ __forceinline__ R operator()(int i, int j, int k) const { return to_r<R>(P[sidx(i, j, k)]); }
+};
+template <class R> struct SAcc {
+  const R* s;
+  int i0, j0, k0, nx, nxy;
+  __device__ __forceinline__ R operator()(int i, int j, int k) const {
+    return s[(k - k0) * nxy + (j - j0) * nx + (i - i0)];
+  }
+};
 
 template <class R> __device__ __forceinline__ R qc(int off) { return off == 1 ? R(-22.0 / 128.0) : R(3.0 / 128.0); }
 
-template <class R>
-__device__ __forceinline__ R mix2t(const double* P, int i, int j, int k, int A, int Bx, int p, int q) {
+template <class R, class A>
+__device__ __forceinline__ R mix2t(const A& P, int i, int j, int k, int Ax, int Bx, int p, int q) {
   int o1[3] = {0, 0, 0}, o2[3] = {0, 0, 0}, o3[3] = {0, 0, 0}, o4[3] = {0, 0, 0};
-  o1[A] = p; o1[Bx] = q;
-  o2[A] = -p; o2[Bx] = -q;
-  o3[A] = -p; o3[Bx] = q;
-  o4[A] = p; o4[Bx] = -q;
-  return (pld<R>(P, i + o1[0], j + o1[1], k + o1[2]) + pld<R>(P, i + o2[0], j + o2[1], k + o2[2])) -
-         (pld<R>(P, i + o3[0], j + o3[1], k + o3[2]) + pld<R>(P, i + o4[0], j + o4[1], k + o4[2]));
+  o1[Ax] = p; o1[Bx] = q;
+  o2[Ax] = -p; o2[Bx] = -q;
+  o3[Ax] = -p; o3[Bx] = q;
+  o4[Ax] = p; o4[Bx] = -q;
+  return (P(i + o1[0], j + o1[1], k + o1[2]) + P(i + o2[0], j + o2[1], k + o2[2])) -
+         (P(i + o3[0], j + o3[1], k + o3[2]) + P(i + o4[0], j + o4[1], k + o4[2]));
 }
 
-template <class R> __device__ __forceinline__ R mix3t(const double* P, int i, int j, int k, int p, int q, int r) {
+template <class R, class A> __device__ __forceinline__ R mix3t(const A& P, int i, int j, int k, int p, int q, int r) {
   const int sg[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, -1, 1}, {-1, 1, -1}};
   R acc = R(0);
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    R term = pld<R>(P, i + sg[t][0] * p, j + sg[t][1] * q, k + sg[t][2] * r) -
-             pld<R>(P, i - sg[t][0] * p, j - sg[t][1] * q, k - sg[t][2] * r);
+    R term = P(i + sg[t][0] * p, j + sg[t][1] * q, k + sg[t][2] * r) - P(i - sg[t][0] * p, j - sg[t][1] * q, k - sg[t][2] * r);
     acc = (t == 0) ? term : acc + term;
   }
   return acc;
 }
 
-template <class R> __device__ __forceinline__ QT<R> qterms_t(const double* P, int i, int j, int k) {
+// Q-terms of parent cell (i, j, k) (Eq. Prediction with the appendix
+// coefficients c0 = -22/128, c1 = 3/128).
+template <class R, class A> __device__ __forceinline__ QT<R> qterms_t(const A& P, int i, int j, int k) {
   const R C0 = R(-22.0 / 128.0), C1 = R(3.0 / 128.0);
   QT<R> t;
-  t.u = pld<R>(P, i, j, k);
-  t.Qx = C0 * (pld<R>(P, i + 1, j, k) - pld<R>(P, i - 1, j, k)) + C1 * (pld<R>(P, i + 2, j, k) - pld<R>(P, i - 2, j, k));
-  t.Qy = C0 * (pld<R>(P, i, j + 1, k) - pld<R>(P, i, j - 1, k)) + C1 * (pld<R>(P, i, j + 2, k) - pld<R>(P, i, j - 2, k));
-  t.Qz = C0 * (pld<R>(P, i, j, k + 1) - pld<R>(P, i, j, k - 1)) + C1 * (pld<R>(P, i, j, k + 2) - pld<R>(P, i, j, k - 2));
+  t.u = P(i, j, k);
+  t.Qx = C0 * (P(i + 1, j, k) - P(i - 1, j, k)) + C1 * (P(i + 2, j, k) - P(i - 2, j, k));
+  t.Qy = C0 * (P(i, j + 1, k) - P(i, j - 1, k)) + C1 * (P(i, j + 2, k) - P(i, j - 2, k));
+  t.Qz = C0 * (P(i, j, k + 1) - P(i, j, k - 1)) + C1 * (P(i, j, k + 2) - P(i, j, k - 2));
   const int pq[4][2] = {{1, 1}, {2, 2}, {1, 2}, {2, 1}};
   R qxy = R(0), qxz = R(0), qyz = R(0);
 #pragma unroll
@@ -88,6 +101,18 @@ template <class R> __device__ __forceinline__ QT<R> qterms_t(const double* P, in
   }
   t.Qxyz = qxyz;
   return t;
+}
+
+// Stage the parent values of the box [i0, i0+nx) x [j0, j0+ny) x [k0, k0+nz)
+// (stored coordinates) of variable v into shared memory as R; all threads.
+template <class R>
+__device__ __forceinline__ void stage_box(R* __restrict__ s, const double* __restrict__ P, int i0, int j0, int k0,
+                                          int nx, int ny, int nz) {
+  const int n = nx * ny * nz;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
+    s[e] = to_r<R>(P[sidx(i0 + i, j0 + j, k0 + k)]);
+  }
 }
 
 template <class R> __device__ __forceinline__ R predict_t(const QT<R>& t, R sx, R sy, R sz) {
@@ -154,7 +179,6 @@ __global__ void __launch_bounds__(256) k_fill_regions_t(Topo t, Pool pool, int c
     const int nvar = detail_only ? 2 : NV;
     if (partial && !face) continue;
     const int nb = t.nbr[(size_t)node * 27 + r];
-    const int par = t.parent[node];
     double* u = buf + (size_t)t.slot[node] * SLOT_U;
     if (nb >= 0) {
       if (partial) continue;                              // read directly by the stage kernel
@@ -180,19 +204,70 @@ __global__ void __launch_bounds__(256) k_fill_regions_t(Topo t, Pool pool, int c
         for (int q = 0; q < 4; ++q)
           if (e0 + 32 * q < ne) *reinterpret_cast<double2*>(u + dst[q]) = val[q];
       }
-    } else if (nb == -1 && par >= 0) {
-      const double* P = buf + (size_t)t.slot[par] * SLOT_U;
-      const int ch = (int)(t.keys[node] & 7ull);
-      const int cb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
-      // parent cells covering the region, relative to the child's origin:
-      // 8 (interior range) or 2 (halo range) per axis
+    }
+  }
+}
+
+// Predicted halo regions (no same-level node on that side, the node has a
+// parent): one CTA per node, one region after the other; the parent cells
+// of the region and their +-2 stencil (6 or 12 per axis) are staged in shared
+// memory as R for the variables filled, then every thread evaluates the
+// Q-terms of parent cells and writes their eight fine cells.
+template <class R>
+__global__ void __launch_bounds__(256) k_fill_predict_t(Topo t, Pool pool, int cur, NodeSet ns, int mode) {
+  __shared__ R box[NV * 864];
+  __shared__ unsigned rmask;
+  int beg, cnt;
+  nodeset_range(t, ns, beg, cnt);
+  double* buf = pool.buf[cur];
+  for (int w = blockIdx.x; w < cnt; w += gridDim.x) {
+    const int node = nodeset_node(t, ns, beg, w);
+    const int par = t.parent[node];
+    if (par < 0) continue;                                   // level 0: no prediction
+    const bool leaf = t.child0[node] < 0;
+    const bool partial = mode == FILL_STAGE && leaf;
+    const bool detail_only = mode == FILL_DETAIL && leaf;
+    const int nvar = detail_only ? 2 : NV;
+    if (threadIdx.x < 32) {
+      bool want = false;
+      const int r = threadIdx.x;
+      if (r < 27 && r != 13) {
+        const int sx = r % 3 - 1, sy = (r / 3) % 3 - 1, sz = r / 9 - 1;
+        const bool face = (sx != 0) + (sy != 0) + (sz != 0) == 1;
+        want = t.nbr[(size_t)node * 27 + r] == -1 && (!partial || face);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, want);
+      if (threadIdx.x == 0) rmask = m;
+    }
+    __syncthreads();
+    unsigned m = rmask;
+    __syncthreads();
+    if (!m) continue;
+    double* u = buf + (size_t)t.slot[node] * SLOT_U;
+    const double* P = buf + (size_t)t.slot[par] * SLOT_U;
+    const int ch = (int)(t.keys[node] & 7ull);
+    const int cb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+    while (m) {
+      const int r = __ffs(m) - 1;
+      m &= m - 1;
+      const int sx = r % 3 - 1, sy = (r / 3) % 3 - 1, sz = r / 9 - 1;
+      // parent cells of the region relative to the child's origin: [q0, q0 + n)
       const int lx = sx == 0 ? 3 : 1, ly = sy == 0 ? 3 : 1, lz = sz == 0 ? 3 : 1;
       const int qx0 = sx < 0 ? -2 : (sx == 0 ? 0 : 8), qy0 = sy < 0 ? -2 : (sy == 0 ? 0 : 8), qz0 = sz < 0 ? -2 : (sz == 0 ? 0 : 8);
+      // staged box: those parent cells +-2, in the parent's stored coordinates
+      const int bx0 = 8 * cb[0] + qx0 - 2, by0 = 8 * cb[1] + qy0 - 2, bz0 = 8 * cb[2] + qz0 - 2;
+      const int nx = (1 << lx) + 4, ny = (1 << ly) + 4, nz = (1 << lz) + 4;
+      const int nb = nx * ny * nz;
+      for (int q = 0; q < nvar; ++q)
+        stage_box<R>(box + q * nb, P + fill_var(detail_only, q) * NCELL, bx0, by0, bz0, nx, ny, nz);
+      __syncthreads();
       const int lxy = lx + ly, ln = lxy + lz;
-      for (int e = lane; e < (nvar << ln); e += 32) {
-        const int v = fill_var(detail_only, e >> ln), c = e & ((1 << ln) - 1);
+      for (int e = threadIdx.x; e < (nvar << ln); e += blockDim.x) {
+        const int q = e >> ln, c = e & ((1 << ln) - 1);
+        const int v = fill_var(detail_only, q);
         const int rx = qx0 + (c & ((1 << lx) - 1)), ry = qy0 + ((c >> lx) & ((1 << ly) - 1)), rz = qz0 + (c >> lxy);
-        const QT<R> qt = qterms_t<R>(P + v * NCELL, 8 * cb[0] + rx, 8 * cb[1] + ry, 8 * cb[2] + rz);
+        const SAcc<R> A{box + q * nb, bx0, by0, bz0, nx, nx * ny};
+        const QT<R> qt = qterms_t<R>(A, 8 * cb[0] + rx, 8 * cb[1] + ry, 8 * cb[2] + rz);
 #pragma unroll
         for (int sub = 0; sub < 8; ++sub) {
           const int a = sub & 1, b = (sub >> 1) & 1, cc = (sub >> 2) & 1;
@@ -200,6 +275,7 @@ __global__ void __launch_bounds__(256) k_fill_regions_t(Topo t, Pool pool, int c
           u[v * NCELL + sidx(2 * rx + a, 2 * ry + b, 2 * rz + cc)] = from_r<R>(val);
         }
       }
+      __syncthreads();
     }
   }
 }
@@ -210,8 +286,9 @@ __global__ void __launch_bounds__(256) k_fill_regions_t(Topo t, Pool pool, int c
 // coordinate beyond a non-periodic side being mapped back into the block
 // (zero gradient: the nearest internal cell; any other condition: the mirror
 // cell, with the normal momentum negated under symmetry).  So one warp per
-// (node, side) fills the side's 4 x 24 x 24 slab from source cells that this
-// kernel never writes; cells in two slabs get the same value twice.
+// (node, side) item fills the side's 4 x 24 x 24 slab from source cells that this
+// kernel never writes; cells in two slabs get the same value twice.  Work
+// items are (node, side, chunk of 256 slab cells), one warp each.
 __device__ __forceinline__ int bc_map(int x, int blo, int bhi, int& flip, int bit) {
   if (x < 0 && blo >= 0) {
     flip ^= (blo == 2) ? bit : 0;
@@ -225,15 +302,31 @@ __device__ __forceinline__ int bc_map(int x, int blo, int bhi, int& flip, int bi
 }
 
 static __global__ void __launch_bounds__(256) k_fill_bc(Topo t, Phys p, Pool pool, int cur, NodeSet ns, int mode) {
+  // sides: the level's boundary items, or every side of the listed nodes
   int beg, cnt;
-  nodeset_range(t, ns, beg, cnt);
+  if (ns.list) {
+    beg = 0;
+    cnt = 6 * ns.n;
+  } else {
+    beg = t.cnt[CNT_BC + ns.level];
+    cnt = t.cnt[CNT_BC + ns.level + 1] - beg;
+  }
   double* buf = pool.buf[cur];
-  const int nitems = cnt * 6;
+  constexpr int NCHUNK = 9;                  // 2304 slab cells = 9 chunks of 256
+  const int nitems = cnt * NCHUNK;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < nitems; w += gridDim.x * wpb) {
-    const int node = nodeset_node(t, ns, beg, w / 6);
-    const int side = w % 6, d = side >> 1;
+    int node, side;
+    if (ns.list) {
+      node = ns.list[w / (6 * NCHUNK)];
+      side = (w / NCHUNK) % 6;
+    } else {
+      const int it = t.bc_items[beg + w / NCHUNK];
+      node = it >> 3;
+      side = it & 7;
+    }
+    const int d = side >> 1, chunk = w % NCHUNK;
     const int level = t.level[node];
     const bool detail_only = mode == FILL_DETAIL && t.child0[node] < 0;
     int blo[3], bhi[3];   // condition of each boundary side of this node, -1 if none (or periodic)
@@ -248,7 +341,7 @@ static __global__ void __launch_bounds__(256) k_fill_bc(Topo t, Phys p, Pool poo
     if (bself < 0) continue;
     double* u = buf + (size_t)t.slot[node] * SLOT_U;
     constexpr int n = HW * NS * NS;           // 2304 = 72 x 32
-    for (int e0 = lane; e0 < n; e0 += 4 * 32) {
+    for (int e0 = chunk * 256 + lane; e0 < (chunk + 1) * 256; e0 += 4 * 32) {
       double val[4][NV];
       int di[4];
 #pragma unroll
@@ -291,6 +384,7 @@ static __global__ void __launch_bounds__(256) k_fill_bc(Topo t, Phys p, Pool poo
 template <class R>
 __global__ void __launch_bounds__(256) k_delta_t(Topo t, Phys p, Pool pool, int cur, double* __restrict__ delta_node) {
   __shared__ double sh[8];
+  __shared__ R box[4096];           // the parent's cells 8 cb - 4 .. 8 cb + 11 per axis, one variable
   const int nleaves = t.cnt[CNT_NLEAVES];
   const double* B = pool.buf[cur];
   for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
@@ -313,24 +407,30 @@ __global__ void __launch_bounds__(256) k_delta_t(Topo t, Phys p, Pool pool, int 
       gl[d] = (Xd == 0) && (p.bc[2 * d] != 1);
       gh[d] = (Xd == nl - 1) && (p.bc[2 * d + 1] != 1);
     }
+    const int bx0 = 8 * cb[0] - 4, by0 = 8 * cb[1] - 4, bz0 = 8 * cb[2] - 4;
     R m = R(0);
-    for (int e = threadIdx.x; e < 2 * 1728; e += blockDim.x) {
-      const int vi = e / 1728, q = e % 1728;
+    for (int vi = 0; vi < 2; ++vi) {
       const int v = vi == 0 ? 0 : 4;
-      const int rx = q % 12 - 2, ry = (q / 12) % 12 - 2, rz = q / 144 - 2;
-      // all eight fine cells of this parent cell share the ghost status
-      const bool ghost = (rx < 0 && gl[0]) || (rx >= 8 && gh[0]) || (ry < 0 && gl[1]) || (ry >= 8 && gh[1]) ||
-                         (rz < 0 && gl[2]) || (rz >= 8 && gh[2]);
-      if (ghost) continue;
-      const QT<R> qt = qterms_t<R>(P + v * NCELL, 8 * cb[0] + rx, 8 * cb[1] + ry, 8 * cb[2] + rz);
+      stage_box<R>(box, P + v * NCELL, bx0, by0, bz0, 16, 16, 16);
+      __syncthreads();
+      const SAcc<R> A{box, bx0, by0, bz0, 16, 256};
+      for (int q = threadIdx.x; q < 1728; q += blockDim.x) {
+        const int rx = q % 12 - 2, ry = (q / 12) % 12 - 2, rz = q / 144 - 2;
+        // all eight fine cells of this parent cell share the ghost status
+        const bool ghost = (rx < 0 && gl[0]) || (rx >= 8 && gh[0]) || (ry < 0 && gl[1]) || (ry >= 8 && gh[1]) ||
+                           (rz < 0 && gl[2]) || (rz >= 8 && gh[2]);
+        if (ghost) continue;
+        const QT<R> qt = qterms_t<R>(A, 8 * cb[0] + rx, 8 * cb[1] + ry, 8 * cb[2] + rz);
 #pragma unroll
-      for (int sub = 0; sub < 8; ++sub) {
-        const int a = sub & 1, b = (sub >> 1) & 1, c = (sub >> 2) & 1;
-        const R pr = predict_t<R>(qt, a ? R(-1) : R(1), b ? R(-1) : R(1), c ? R(-1) : R(1));
-        const R uf = to_r<R>(U[v * NCELL + sidx(2 * rx + a, 2 * ry + b, 2 * rz + c)]);
-        const R r = (uf - pr) / uf;
-        m = (r < R(0) ? -r : r) > m ? (r < R(0) ? -r : r) : m;
+        for (int sub = 0; sub < 8; ++sub) {
+          const int a = sub & 1, b = (sub >> 1) & 1, c = (sub >> 2) & 1;
+          const R pr = predict_t<R>(qt, a ? R(-1) : R(1), b ? R(-1) : R(1), c ? R(-1) : R(1));
+          const R uf = to_r<R>(U[v * NCELL + sidx(2 * rx + a, 2 * ry + b, 2 * rz + c)]);
+          const R r = (uf - pr) / uf;
+          m = (r < R(0) ? -r : r) > m ? (r < R(0) ? -r : r) : m;
+        }
       }
+      __syncthreads();
     }
     double md = from_r<R>(m);
     for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
@@ -357,20 +457,24 @@ namespace mrb {
 template <class R>
 __global__ void __launch_bounds__(256) k_refine_fill_t(Topo t, Pool pool, int cur, const int32_t* __restrict__ pairs,
                                                       int n) {
+  __shared__ R box[4096];           // the parent's cells 8 cb - 4 .. 8 cb + 11 per axis, one variable
   double* B = pool.buf[cur];
-  const int nitems = n * 8;
+  const int nitems = n * NV;
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-    const int child = pairs[2 * (w / 8)], par = pairs[2 * (w / 8) + 1];
-    const int zq = w % 8;                                      // 8 chunks of the 12 x 12 x 12 parent cells
-    double* U = B + (size_t)t.slot[child] * SLOT_U;
-    const double* P = B + (size_t)t.slot[par] * SLOT_U;
+    const int child = pairs[2 * (w / NV)], par = pairs[2 * (w / NV) + 1];
+    const int v = w % NV;
+    double* U = B + (size_t)t.slot[child] * SLOT_U + v * NCELL;
+    const double* P = B + (size_t)t.slot[par] * SLOT_U + v * NCELL;
     const int ch = (int)(t.keys[child] & 7ull);
     const int cb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
-    for (int e = threadIdx.x; e < 216 * NV; e += blockDim.x) {
-      const int v = e / 216, r = e % 216 + zq * 216;
+    const int bx0 = 8 * cb[0] - 4, by0 = 8 * cb[1] - 4, bz0 = 8 * cb[2] - 4;
+    stage_box<R>(box, P, bx0, by0, bz0, 16, 16, 16);
+    __syncthreads();
+    const SAcc<R> A{box, bx0, by0, bz0, 16, 256};
+    for (int r = threadIdx.x; r < 1728; r += blockDim.x) {
       const int pi = 8 * cb[0] - 2 + r % 12, pj = 8 * cb[1] - 2 + (r / 12) % 12, pk = 8 * cb[2] - 2 + r / 144;
-      const QT<R> q = qterms_t<R>(P + v * NCELL, pi, pj, pk);
-      const double base = P[v * NCELL + sidx(pi, pj, pk)];
+      const QT<R> q = qterms_t<R>(A, pi, pj, pk);
+      const double base = P[sidx(pi, pj, pk)];
 #pragma unroll
       for (int sub = 0; sub < 8; ++sub) {
         const int a = sub & 1, b = (sub >> 1) & 1, c = (sub >> 2) & 1;
@@ -383,9 +487,10 @@ __global__ void __launch_bounds__(256) k_refine_fill_t(Topo t, Pool pool, int cu
           q0.u = R(0);
           val = base + from_r<R>(predict_t<R>(q0, a ? R(-1) : R(1), b ? R(-1) : R(1), c ? R(-1) : R(1)));
         }
-        U[v * NCELL + sidx(fi, fj, fk)] = val;
+        U[sidx(fi, fj, fk)] = val;
       }
     }
+    __syncthreads();
   }
 }
 
@@ -408,11 +513,13 @@ static __global__ void __launch_bounds__(256) k_project_octants(Topo t, Pool poo
       const int I = c % 8, J = (c / 8) % 8, K = c / 64;
       const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
       const double* u = C + v * NCELL;
-      const double c0v = u[sidx(fi, fj, fk)], c1v = u[sidx(fi + 1, fj, fk)];
-      const double c2v = u[sidx(fi, fj + 1, fk)], c3v = u[sidx(fi + 1, fj + 1, fk)];
-      const double c4v = u[sidx(fi, fj, fk + 1)], c5v = u[sidx(fi + 1, fj, fk + 1)];
-      const double c6v = u[sidx(fi, fj + 1, fk + 1)], c7v = u[sidx(fi + 1, fj + 1, fk + 1)];
-      Pp[v * NCELL + sidx(ox + I, oy + J, oz + K)] = 0.125 * (((c0v + c1v) + (c2v + c3v)) + ((c4v + c5v) + (c6v + c7v)));
+      // fi is even: each x-pair of children is one aligned 16-byte load
+      const double2 a01 = *reinterpret_cast<const double2*>(u + sidx(fi, fj, fk));
+      const double2 a23 = *reinterpret_cast<const double2*>(u + sidx(fi, fj + 1, fk));
+      const double2 a45 = *reinterpret_cast<const double2*>(u + sidx(fi, fj, fk + 1));
+      const double2 a67 = *reinterpret_cast<const double2*>(u + sidx(fi, fj + 1, fk + 1));
+      Pp[v * NCELL + sidx(ox + I, oy + J, oz + K)] =
+          0.125 * (((a01.x + a01.y) + (a23.x + a23.y)) + ((a45.x + a45.y) + (a67.x + a67.y)));
     }
   }
 }

@@ -166,23 +166,31 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
 #pragma unroll
   for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, Ur[m], Fr[m]);
   const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1);
+  // characteristic fluxes of all fields, sharing the terms of the rows:
+  // l0 F = A + B, l4 F = A - B, l1 F = F0 - 2A, l2 F = F2 - ut1 F0, l3 F = F3 - ut2 F0
+  float Gall[5][6];
+  {
+    const float hb2 = 0.5f * e.b2, hic = 0.5f * e.ic;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      const float Sm = fmaf(e.un, Fr[m][1], fmaf(e.ut1, Fr[m][2], e.ut2 * Fr[m][3]));
+      const float A = fmaf(hb2, Fr[m][0], e.hb1 * (Fr[m][4] - Sm));
+      const float Bm = hic * fmaf(e.un, Fr[m][0], -Fr[m][1]);
+      Gall[0][m] = A + Bm;
+      Gall[4][m] = A - Bm;
+      Gall[1][m] = fmaf(-2.f, A, Fr[m][0]);
+      Gall[2][m] = fmaf(-e.ut1, Fr[m][0], Fr[m][2]);
+      Gall[3][m] = fmaf(-e.ut2, Fr[m][0], Fr[m][3]);
+    }
+  }
   float Fh0 = 0.f, Fh1 = 0.f, Fh2 = 0.f, Fh3 = 0.f, Fh4 = 0.f;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     // the selector decides for the acoustic and entropy fields; shear fields keep WENO5
     const bool use_lin = (MODE == 1) && lin && (k == 0 || k == 1 || k == 4);
     float G[6];
-    float l[5];
-    lrow_f32(e, k, l);
-    if (k == 2 || k == 3) {
-      const int j = (k == 2) ? 2 : 3;
 #pragma unroll
-      for (int m = 0; m < 6; ++m) G[m] = fmaf(l[0], Fr[m][0], Fr[m][j]);
-    } else {
-#pragma unroll
-      for (int m = 0; m < 6; ++m)
-        G[m] = fmaf(l[0], Fr[m][0], fmaf(l[1], Fr[m][1], fmaf(l[2], Fr[m][2], fmaf(l[3], Fr[m][3], l[4] * Fr[m][4]))));
-    }
+    for (int m = 0; m < 6; ++m) G[m] = Gall[k][m];
     float lL, lR, lt;
     if (k == 0 || k == 4) {
       const float sg = (k == 0) ? 1.f : -1.f;
@@ -199,6 +207,8 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
     // upwind: W+ of G (pos) or W- of G; LLF: W+ of (G + a V)/2 and W- of (G - a V)/2
     float V[6];
     if (llf) {
+      float l[5];
+      lrow_f32(e, k, l);
       if (k == 2 || k == 3) {
         const int j = (k == 2) ? 2 : 3;
 #pragma unroll
