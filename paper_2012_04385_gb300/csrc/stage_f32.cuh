@@ -4,9 +4,7 @@
 // of the FP64 state in FP64.
 //
 // Work item = (leaf, z-slab of 16 x 16 x 4 cells); a CTA of 256 threads loops
-// over items.  For each direction D (a run-time loop in the learned-selector
-// variant, whose face code would not fit the instruction cache three times;
-// unrolled with constant D otherwise) the stencil region of the slab -- the slab plus
+// over items.  For each direction D the stencil region of the slab -- the slab plus
 // 3 cells on both sides along D -- is converted once from the FP64 stage buffer
 // into FP32 primitive records in shared memory, with the velocity rotated into
 // the direction's frame (normal, tangential 1, tangential 2).  One thread per
@@ -147,47 +145,73 @@ __device__ __forceinline__ void cell_uf(const float* __restrict__ S, int c, floa
   F[4] = un * (E + p);
 }
 
+// Kernel variants: MODE 0 WENO5, 2 linear, 1 learned selector at stage 0
+// (WENO5 fluxes; the selector is evaluated on the same faces and its
+// decisions stored), 3 learned selector at stages 1 and 2 (the stored
+// decision of each face picks linear or WENO5 for fields 0, 1, 4).
 template <int MODE>
 __device__ __forceinline__ float rec5(bool lin, float a, float b, float c, float d, float e) {
   if (MODE == 2) return linear5f(a, b, c, d, e);
-  if (MODE == 0) return weno5f(a, b, c, d, e);
+  if (MODE != 3) return weno5f(a, b, c, d, e);
   return lin ? linear5f(a, b, c, d, e) : weno5f(a, b, c, d, e);
 }
 
+// Selector features from the characteristic fluxes g and variables v of
+// fields 0, 1, 4 over the six stencil cells: the compressed consecutive
+// variations s (|dg| + alpha_k |dv|) (alpha_k the field's LLF speed, s the
+// sign of dg, of dv where dg is zero).
+__device__ __forceinline__ void features_gv(const float (&g)[3][6], const float (&v)[3][6], const RoeF& e,
+                                            float f[15]) {
+  float alpha[3];
+  alpha[0] = fmaxf(fabsf(e.unL - e.cL), fabsf(e.unR - e.cR));
+  alpha[1] = fmaxf(fabsf(e.unL), fabsf(e.unR));
+  alpha[2] = fmaxf(fabsf(e.unL + e.cL), fabsf(e.unR + e.cR));
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int m = 1; m < 6; ++m) {
+      const float dg = g[q][m] - g[q][m - 1], dv = v[q][m] - v[q][m - 1];
+      const float mag = fmaf(alpha[q], fabsf(dv), fabsf(dg));
+      f[5 * q + m - 1] = compress_diff((dg != 0.f) ? copysignf(mag, dg) : copysignf(mag, dv));
+    }
+}
+
+// Characteristic values of fields 0, 1, 4 of a conserved (or flux) vector X,
+// sharing the terms of the left eigenvector rows: l0 X = A + B, l4 X = A - B,
+// l1 X = X0 - 2A with A = b2/2 X0 + b1/2 (X4 - un X1 - ut1 X2 - ut2 X3) and
+// B = (un X0 - X1) / (2c).
+__device__ __forceinline__ void char014(const float X[5], const RoeF& e, float& x0, float& x1, float& x4) {
+  const float Sm = fmaf(e.un, X[1], fmaf(e.ut1, X[2], e.ut2 * X[3]));
+  const float A = fmaf(0.5f * e.b2, X[0], e.hb1 * (X[4] - Sm));
+  const float Bm = (0.5f * e.ic) * fmaf(e.un, X[0], -X[1]);
+  x0 = A + Bm;
+  x4 = A - Bm;
+  x1 = fmaf(-2.f, A, X[0]);
+}
+
 // Face flux between stencil cells 2 and 3 (cells at S index c0 + m*st, m = 0..5)
-// from the FP32 records; result in the direction frame.  MODE 0: WENO5,
-// 2: linear, 1: per-face choice `lin` for fields 0, 1, 4 (learned selector;
-// the shear fields keep WENO5).  In MODE 1 one reconstruction site per field
-// serves both upwind cases and, run twice, the two halves of the LLF split.
-template <int MODE>
+// from the FP32 records; result in the direction frame.  With FEAT the
+// selector features of the face are returned as well.
+template <int MODE, bool FEAT>
 __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, float gm1, bool lin,
-                                              float F[5]) {
+                                              float F[5], float* feat = nullptr) {
   float Ur[6][5], Fr[6][5];
 #pragma unroll
   for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, Ur[m], Fr[m]);
   const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1);
-  // characteristic fluxes of all fields, sharing the terms of the rows:
-  // l0 F = A + B, l4 F = A - B, l1 F = F0 - 2A, l2 F = F2 - ut1 F0, l3 F = F3 - ut2 F0
+  // characteristic fluxes of all fields (l2 F = F2 - ut1 F0, l3 F = F3 - ut2 F0)
   float Gall[5][6];
-  {
-    const float hb2 = 0.5f * e.b2, hic = 0.5f * e.ic;
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
-      const float Sm = fmaf(e.un, Fr[m][1], fmaf(e.ut1, Fr[m][2], e.ut2 * Fr[m][3]));
-      const float A = fmaf(hb2, Fr[m][0], e.hb1 * (Fr[m][4] - Sm));
-      const float Bm = hic * fmaf(e.un, Fr[m][0], -Fr[m][1]);
-      Gall[0][m] = A + Bm;
-      Gall[4][m] = A - Bm;
-      Gall[1][m] = fmaf(-2.f, A, Fr[m][0]);
-      Gall[2][m] = fmaf(-e.ut1, Fr[m][0], Fr[m][2]);
-      Gall[3][m] = fmaf(-e.ut2, Fr[m][0], Fr[m][3]);
-    }
+  for (int m = 0; m < 6; ++m) {
+    char014(Fr[m], e, Gall[0][m], Gall[1][m], Gall[4][m]);
+    Gall[2][m] = fmaf(-e.ut1, Fr[m][0], Fr[m][2]);
+    Gall[3][m] = fmaf(-e.ut2, Fr[m][0], Fr[m][3]);
   }
   float Fh0 = 0.f, Fh1 = 0.f, Fh2 = 0.f, Fh3 = 0.f, Fh4 = 0.f;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     // the selector decides for the acoustic and entropy fields; shear fields keep WENO5
-    const bool use_lin = (MODE == 1) && lin && (k == 0 || k == 1 || k == 4);
+    const bool use_lin = (MODE == 3) && lin && (k == 0 || k == 1 || k == 4);
     float G[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) G[m] = Gall[k][m];
@@ -205,9 +229,13 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
     const bool pos = lL > 0.f && lR > 0.f && lt > 0.f;
     const bool llf = !pos && !(lL < 0.f && lR < 0.f && lt < 0.f);
     // upwind: W+ of G (pos) or W- of G; LLF: W+ of (G + a V)/2 and W- of (G - a V)/2
-    float V[6];
-    if (llf) {
-      float l[5];
+    float gh;
+    if (pos) {
+      gh = rec5<MODE>(use_lin, G[0], G[1], G[2], G[3], G[4]);
+    } else if (!llf) {
+      gh = rec5<MODE>(use_lin, G[5], G[4], G[3], G[2], G[1]);
+    } else {
+      float l[5], V[6];
       lrow_f32(e, k, l);
       if (k == 2 || k == 3) {
         const int j = (k == 2) ? 2 : 3;
@@ -218,34 +246,6 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
         for (int m = 0; m < 6; ++m)
           V[m] = fmaf(l[0], Ur[m][0], fmaf(l[1], Ur[m][1], fmaf(l[2], Ur[m][2], fmaf(l[3], Ur[m][3], l[4] * Ur[m][4]))));
       }
-    }
-    float gh;
-    if (MODE == 1) {
-      // one reconstruction site (the kernel's code size matters more than its schedule)
-      float in[6];
-      const float ha = llf ? 0.5f * fmaxf(fabsf(lL), fabsf(lR)) : 0.f;
-#pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        in[m] = llf ? 0.5f * G[m] : G[m];
-        if (llf) G[m] = ha * V[m];                // G now holds a V / 2
-      }
-      gh = 0.f;
-      bool fwd = pos || llf;
-#pragma unroll 1
-      for (int pass = 0; pass < (llf ? 2 : 1); ++pass) {
-        // pass 0: W+ (fwd) or W- of the upwind values; pass 1 (LLF only): W- of (G - a V)/2
-        float x[6];
-#pragma unroll
-        for (int m = 0; m < 6; ++m) x[m] = llf ? (pass == 0 ? in[m] + G[m] : in[m] - G[m]) : in[m];
-        gh += rec5<MODE>(use_lin, fwd ? x[0] : x[5], fwd ? x[1] : x[4], fwd ? x[2] : x[3], fwd ? x[3] : x[2],
-                         fwd ? x[4] : x[1]);
-        fwd = false;
-      }
-    } else if (pos) {
-      gh = rec5<MODE>(false, G[0], G[1], G[2], G[3], G[4]);
-    } else if (!llf) {
-      gh = rec5<MODE>(false, G[5], G[4], G[3], G[2], G[1]);
-    } else {
       const float ha = 0.5f * fmaxf(fabsf(lL), fabsf(lR));
       float fp[6], fm[6];
 #pragma unroll
@@ -253,7 +253,7 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
         fp[m] = fmaf(0.5f, G[m], ha * V[m]);
         fm[m] = fmaf(0.5f, G[m], -ha * V[m]);
       }
-      gh = rec5<MODE>(false, fp[0], fp[1], fp[2], fp[3], fp[4]) + rec5<MODE>(false, fm[5], fm[4], fm[3], fm[2], fm[1]);
+      gh = rec5<MODE>(use_lin, fp[0], fp[1], fp[2], fp[3], fp[4]) + rec5<MODE>(use_lin, fm[5], fm[4], fm[3], fm[2], fm[1]);
     }
     // F_hat = R g_hat, columns r0 = (1, u-c, ut1, ut2, H-uc), r1 = (1, u, ut1, ut2, q2/2),
     // r2 = (0, 0, 1, 0, ut1), r3 = (0, 0, 0, 1, ut2), r4 = (1, u+c, ut1, ut2, H+uc)
@@ -278,6 +278,17 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
       Fh4 = fmaf(e.ut2, gh, Fh4);
     }
   }
+  if (FEAT) {
+    float g[3][6], v[3][6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      g[0][m] = Gall[0][m];
+      g[1][m] = Gall[1][m];
+      g[2][m] = Gall[4][m];
+      char014(Ur[m], e, v[0][m], v[1][m], v[2][m]);
+    }
+    features_gv(g, v, e, feat);
+  }
   F[0] = Fh0;
   F[1] = Fh1;
   F[2] = Fh2;
@@ -285,38 +296,19 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
   F[4] = Fh4;
 }
 
-// Selector features of the face between records c0+2st and c0+3st: for the
-// characteristic fields k = 0, 1, 4, the compressed consecutive variations
-// s (|dg| + alpha_k |dv|) of the characteristic fluxes g = L_k F(U_m) and
-// variables v = L_k U_m over the six stencil cells (alpha_k the field's LLF
-// speed, s the sign of dg, of dv where dg is zero).
+// Selector features of the face between records c0+2st and c0+3st (the
+// same arithmetic as the stage-0 kernel's).
 __device__ __forceinline__ void face_features_f32(const float* __restrict__ S, int c0, int st, const RoeF& e,
                                                   float f[15]) {
-  float l[3][5], alpha[3];
-  lrow_f32(e, 0, l[0]);
-  lrow_f32(e, 1, l[1]);
-  lrow_f32(e, 4, l[2]);
-  alpha[0] = fmaxf(fabsf(e.unL - e.cL), fabsf(e.unR - e.cR));
-  alpha[1] = fmaxf(fabsf(e.unL), fabsf(e.unR));
-  alpha[2] = fmaxf(fabsf(e.unL + e.cL), fabsf(e.unR + e.cR));
-  float pg[3], pv[3];
+  float g[3][6], v[3][6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) {
     float U[5], F[5];
     cell_uf(S, c0 + m * st, U, F);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float gq = fmaf(l[q][0], F[0], fmaf(l[q][1], F[1], fmaf(l[q][2], F[2], fmaf(l[q][3], F[3], l[q][4] * F[4]))));
-      const float vq = fmaf(l[q][0], U[0], fmaf(l[q][1], U[1], fmaf(l[q][2], U[2], fmaf(l[q][3], U[3], l[q][4] * U[4]))));
-      if (m > 0) {
-        const float dg = gq - pg[q], dv = vq - pv[q];
-        const float mag = fmaf(alpha[q], fabsf(dv), fabsf(dg));
-        f[5 * q + m - 1] = compress_diff((dg != 0.f) ? copysignf(mag, dg) : copysignf(mag, dv));
-      }
-      pg[q] = gq;
-      pv[q] = vq;
-    }
+    char014(F, e, g[0][m], g[1][m], g[2][m]);
+    char014(U, e, v[0][m], v[1][m], v[2][m]);
   }
+  features_gv(g, v, e, f);
 }
 
 // Number of region records and faces of direction D for one slab.
@@ -389,7 +381,7 @@ __device__ __forceinline__ void face_of(int D, int f, int z0, int& fa, int& c0, 
   }
 }
 
-// Learned-selector state of a CTA (MODE 1 only).
+// Learned-selector state of a CTA (MODES 1 and 3).
 struct LearnedCtx {
   const float* P;            // FP32 parameters (biases read from here)
   const uint32_t* frag;      // BF16 B fragments in shared memory
@@ -398,7 +390,6 @@ struct LearnedCtx {
   float tau;                 // linear when logit < tau
   unsigned long long* count; // [0] faces sent to linear, [1] faces evaluated (nullable)
   uint32_t* bits;            // this block's decision words (SLOT_SEL)
-  bool evaluate;             // stage 0: run the MLP and store; later stages: reuse
   float z0;                  // the network's logit for all-zero features
 };
 
@@ -446,44 +437,40 @@ __device__ __forceinline__ void sweep_f32(int D, const double* __restrict__ u, d
     const int f = act ? f0 : 0;
     int fa, c0, ta, tb;
     face_of(D, f, z0, fa, c0, ta, tb);
-    bool lin = false;
-    if (MODE == 1) {
-      // decision word of this warp's 32 consecutive faces
-      uint32_t* word = L.bits + (z0 / SF_TZ) * 108 + D * 34 + (f0 >> 5);
-      if (L.evaluate) {
-        // flat stencils have all-zero features, whose logit z0 is known; the
-        // warp runs the tensor-core MLP only when one of its faces is not flat
-        const bool flat = !act || stencil_flat(S, c0, st);
-        float z = L.z0;
-        if (!__all_sync(0xffffffffu, flat)) {
-          float fe[15];
-          if (flat) {
-#pragma unroll
-            for (int q = 0; q < 15; ++q) fe[q] = 0.f;
-          } else {
-            const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1);
-            face_features_f32(S, c0, st, e, fe);
-          }
-          const int wid = threadIdx.x >> 5;
-          mlp_put_row(L.rows + wid * 32 * 9, fe);
-          z = mlp_warp_logit(L.P, L.frag, L.rows + wid * 32 * 9, L.logit + wid * 32);
-        }
-        lin = act && (z < L.tau);
-        const unsigned bl = __ballot_sync(0xffffffffu, lin), ba = __ballot_sync(0xffffffffu, act);
-        if ((threadIdx.x & 31) == 0) {
-          *word = bl;
-          if (L.count) {
-            atomicAdd(&L.count[0], (unsigned long long)__popc(bl));
-            atomicAdd(&L.count[1], (unsigned long long)__popc(ba));
-          }
-        }
-      } else {
-        lin = act && ((*word >> (threadIdx.x & 31)) & 1u);
-      }
-    }
-    if (!act) continue;
+    // decision word of this warp's 32 consecutive faces
+    uint32_t* word = (MODE == 1 || MODE == 3) ? L.bits + (z0 / SF_TZ) * 108 + D * 34 + (f0 >> 5) : nullptr;
+    const bool lin = (MODE == 3) && ((*word >> (threadIdx.x & 31)) & 1u);
     float F[5];
-    face_flux_f32<MODE>(S, c0, st, gm1, lin, F);
+    if (MODE == 1) {
+      // WENO5 fluxes and the selector's features of the same faces; flat
+      // stencils have all-zero features, whose logit z0 is known, so the warp
+      // runs the tensor-core MLP only when one of its faces is not flat
+      float fe[15];
+      const bool flat = !act || stencil_flat(S, c0, st);
+      if (act) face_flux_f32<MODE, true>(S, c0, st, gm1, false, F, fe);
+      float z = L.z0;
+      if (!__all_sync(0xffffffffu, flat)) {
+        if (flat) {
+#pragma unroll
+          for (int q = 0; q < 15; ++q) fe[q] = 0.f;
+        }
+        const int wid = threadIdx.x >> 5;
+        mlp_put_row(L.rows + wid * 32 * 9, fe);
+        z = mlp_warp_logit(L.P, L.frag, L.rows + wid * 32 * 9, L.logit + wid * 32);
+      }
+      const bool dl = act && (z < L.tau);
+      const unsigned bl = __ballot_sync(0xffffffffu, dl), ba = __ballot_sync(0xffffffffu, act);
+      if ((threadIdx.x & 31) == 0) {
+        *word = bl;
+        if (L.count) {
+          atomicAdd(&L.count[0], (unsigned long long)__popc(bl));
+          atomicAdd(&L.count[1], (unsigned long long)__popc(ba));
+        }
+      }
+      if (!act) continue;
+    } else {
+      face_flux_f32<MODE, false>(S, c0, st, gm1, lin, F);
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fs[v * SF_FMAX + f] = F[v];
     const int gface = (D == 2) ? z0 + fa : fa;
@@ -530,7 +517,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
   double* __restrict__ dst = pool.buf[cur ^ 1];
   const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
-  LearnedCtx L{nullptr, nullptr, nullptr, nullptr, 0.f, nullptr, nullptr, stage == 0, 0.f};
+  LearnedCtx L{nullptr, nullptr, nullptr, nullptr, 0.f, nullptr, nullptr, 0.f};
   if (MODE == 1) {
     uint32_t* frag = reinterpret_cast<uint32_t*>(Fs + NV * SF_FMAX);
     L.P = p.mlp;
@@ -558,10 +545,11 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     const int slot = t.slot[node];
     const double* __restrict__ u = src + (size_t)slot * SLOT_U;
     double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
-    if (MODE == 1) L.bits = pool.sel + (size_t)slot * SLOT_SEL;
+    if (MODE == 1 || MODE == 3) L.bits = pool.sel + (size_t)slot * SLOT_SEL;
     float acc[SF_TZ][NV];
     if (MODE == 1) {
-      // the selector's code is large: one copy of the sweep, direction at run time
+      // with the selector inlined, one copy of the sweep (direction at run
+      // time) keeps the kernel within the instruction cache
 #pragma unroll 1
       for (int D = 0; D < 3; ++D) sweep_f32<MODE>(D, u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
     } else {
