@@ -146,7 +146,9 @@ def finest_density(keys, geo, rho, cfg):
 
 def roofline_numbers(linear_fraction=0.0):
     """Algorithmic FP32 FLOPs of the fused stage kernel per face and per leaf
-    cell and stage (the accounting is in this function's body)."""
+    cell and stage (the accounting is in this function's body).
+    `linear_fraction` is the share of faces that take the linear scheme,
+    averaged over the stages timed."""
     # Per face (the oracle's face flux, WENO5 on every field, Roe upwinding on
     # every field, zero matrix entries skipped): Roe average and eigensystem 71,
     # characteristic projections 6 cells x 62, split tests 6, WENO5 5 x 66,
@@ -161,11 +163,11 @@ def roofline_numbers(linear_fraction=0.0):
     return per_face, per_cell
 
 
-# DRAM bytes per leaf cell of one launch of the FP32 stage kernels, from the
-# ncu captures summarised in profiles/stage_kernels_explosion_256.md (levels
-# 0-2 case; traffic grows in proportion to the leaf cells of a launch).
-TRAFFIC_BYTES_PER_CELL = {"learned": (163.711488e6 + 165.856512e6) / (512 * 4096),
-                          "weno": (149.616640e6 + 160.287488e6) / (512 * 4096)}
+# DRAM bytes per leaf cell of one launch of the stage kernels, from the ncu
+# capture summarised in profiles/stage_kernels_explosion_256.md (levels 0-2
+# explosion; traffic grows in proportion to the leaf cells of a launch).
+# Learned path: the mean over its stage-0 and stage-1/2 variants (1 + 2 launches).
+TRAFFIC_BYTES_PER_CELL = {"learned": None, "weno": None}
 
 
 def measured_peaks():
@@ -296,7 +298,8 @@ def run_gpu(args, rank, world):
     keys0 = ctx.keys()
 
     # ---- roofline of the fused stage kernel (FP32 CUDA cores)
-    per_face, per_cell = roofline_numbers(m["linear_fraction"])
+    # stage 0 evaluates the selector with WENO5 fluxes; stages 1 and 2 use its decisions
+    per_face, per_cell = roofline_numbers(m["linear_fraction"] * 2 / 3)
     pk = measured_peaks()
     clk = clocks["sm_mhz"] or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 1447.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -366,9 +369,10 @@ def run_gpu(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak,
-                     "traffic": TRAFFIC_BYTES_PER_CELL["learned"] * cells_per_launch,
+                     "traffic": (TRAFFIC_BYTES_PER_CELL["learned"] * cells_per_launch
+                                 if TRAFFIC_BYTES_PER_CELL["learned"] else None),
                      "traffic_note": "ncu dram bytes of a 2.1M-cell launch scaled to the launch's leaf cells",
-                     "kernel": "k_stage_f32<1> (fused RHS + RK stage, learned selector)",
+                     "kernel": "k_stage_f32<1> (stage 0, selector evaluated) + k_stage_f32<3> (stages 1, 2): fused RHS + RK stage",
                      "flops_per_cell_stage": per_cell, "avg_launch_ms": m["stage_ms"],
                      "peak_basis": f"FP32 CUDA cores {nsm} SMs x 128 lanes x 2 x {clk:.0f} MHz sampled"},
         "gpu_launches": int(m["launches"]),

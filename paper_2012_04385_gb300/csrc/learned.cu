@@ -13,11 +13,11 @@ namespace mrb {
 // Label: 1 when any reconstruction of fields 0, 1, 4 the face performs
 // differs between WENO5 and the linear scheme by more than both tau_lab times
 // its largest |input| and the absolute floor 1e-6.
-__device__ __forceinline__ int face_label_f32(const float* __restrict__ S, int c0, int st, const RoeF& e,
+__device__ __forceinline__ int face_label_f32(const float* __restrict__ S, int c0, int st, Rot R, const RoeF& e,
                                               float tau_lab) {
   float Ur[6][5], Fr[6][5];
 #pragma unroll
-  for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, Ur[m], Fr[m]);
+  for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, R, Ur[m], Fr[m]);
   int lab = 0;
   auto check = [&](float a, float b, float c, float d, float ee) {
     const float sc = fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fmaxf(fabsf(c), fabsf(d)), fabsf(ee)));
@@ -85,13 +85,14 @@ __device__ __forceinline__ void sample_dir(int D, const double* __restrict__ u, 
     if (id % stride) continue;
     const int64_t o = id / stride;
     if (o >= cap) continue;
-    const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1);
+    const Rot R = rot_of(D);
+    const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1, g, B, R);
     float fe[15];
-    face_features_f32(S, c0, st, e, fe);
+    face_features_f32(S, c0, st, R, e, fe);
 #pragma unroll
     for (int q = 0; q < 15; ++q) feats[o * 16 + q] = fe[q];
     feats[o * 16 + 15] = 0.f;
-    labels[o] = (uint8_t)face_label_f32(S, c0, st, e, tau_lab);
+    labels[o] = (uint8_t)face_label_f32(S, c0, st, R, e, tau_lab);
     if (where) where[o] = id;
   }
   __syncthreads();

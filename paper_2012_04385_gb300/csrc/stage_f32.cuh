@@ -4,13 +4,16 @@
 // of the FP64 state in FP64.
 //
 // Work item = (leaf, z-slab of 16 x 16 x 4 cells); a CTA of 256 threads loops
-// over items.  For each direction D the stencil region of the slab -- the slab plus
-// 3 cells on both sides along D -- is converted once from the FP64 stage buffer
-// into FP32 primitive records in shared memory, with the velocity rotated into
-// the direction's frame (normal, tangential 1, tangential 2).  One thread per
-// face then computes the face flux from six records, writes it to shared
-// memory (and, on the block boundary, to the block's face buffers), and each
-// thread adds the flux differences of the four cells of its (i, j) column.
+// over items.  The FP64 stage buffer is converted into FP32 primitive records
+// (rho, vx, vy, vz, p, E) in shared memory: for the x and y directions one
+// region holds the slab with 3 cells on each side in x and in y (the slab's
+// own cells are converted once for both), for z the slab with 3 planes
+// below and above.  One thread per face then computes the face flux from six
+// records (velocity read in the direction's frame: normal, tangential 1,
+// tangential 2), writes it to shared memory (and, on the block boundary, to
+// the block's face buffers), and each thread adds the flux differences of the
+// four cells of its (i, j) column.  The x and y faces form one loop of
+// 2 x 1088 faces (34 warps each, so every warp has one direction).
 // Reciprocals and square roots use the fast hardware approximations; WENO5
 // works on the consecutive differences of its five values and needs one
 // reciprocal: omega_k = d_k P_k / sum_j d_j P_j with P_k the product of the
@@ -26,12 +29,17 @@ namespace mrb {
 constexpr int SF_TZ = 4;
 constexpr int SF_NSLAB = NB / SF_TZ;
 constexpr int SF_THREADS = 256;
-constexpr int SF_REG = NB * NB * (SF_TZ + 6);            // largest stencil region (z): 2560 cells
-constexpr int SF_FMAX = NB * NB * (SF_TZ + 1);           // largest face count (z): 1280
-constexpr int SF_NREC = 7;                                // rho, u_n, u_t1, u_t2, p, E, c
+constexpr int SF_REG = NB * NB * (SF_TZ + 6);            // record slots: the z region, 2560 cells
+constexpr int SF_XY = 22 * 22 * SF_TZ;                   // x-y region (corners unused): 1936 slots
+constexpr int SF_NFX = 17 * 16 * SF_TZ;                  // x (and y) faces of a slab: 1088
+constexpr int SF_NFZ = NB * NB * (SF_TZ + 1);            // z faces of a slab: 1280
+constexpr int SF_FMAX = 2 * SF_NFX;                      // face-flux slots: the x-y loop, 2176
+constexpr int SF_NREC = 6;                                // rho, vx, vy, vz, p, E
 constexpr size_t SF_SMEM = sizeof(float) * (SF_NREC * SF_REG + NV * SF_FMAX);
-// learned selector scratch: B fragments, per-warp feature rows and logits
-constexpr size_t SF_SMEM_LEARNED = SF_SMEM + sizeof(uint32_t) * (FRAG_N + (SF_THREADS / 32) * 32 * 9) +
+// learned selector at stage 0 (one direction at a time, face-flux rows of
+// SF_NFZ): records, face fluxes, B fragments, per-warp feature rows and logits
+constexpr size_t SF_SMEM_LEARNED = sizeof(float) * (SF_NREC * SF_REG + NV * SF_NFZ) +
+                                   sizeof(uint32_t) * (FRAG_N + (SF_THREADS / 32) * 32 * 9) +
                                    sizeof(float) * SF_THREADS;
 
 __device__ __constant__ static const double kSfA[3] = {0.0, 0.75, 1.0 / 3.0};
@@ -71,27 +79,38 @@ __device__ __forceinline__ float linear5f(float a, float b, float c, float d, fl
   return fmaf(2.f / 60.f, a, fmaf(-13.f / 60.f, b, fmaf(47.f / 60.f, c, fmaf(27.f / 60.f, d, (-3.f / 60.f) * e))));
 }
 
+// Record offsets of the velocity components in the direction frame of D:
+// normal, tangential 1, tangential 2 (x: vx, vy, vz; y: vy, vz, vx; z: vz, vx, vy).
+struct Rot {
+  int n, t1, t2;
+};
+__device__ __forceinline__ Rot rot_of(int D) {
+  return Rot{(1 + D) * SF_REG, (1 + (D + 1) % 3) * SF_REG, (1 + (D + 2) % 3) * SF_REG};
+}
+
 // Roe average of the face between the records at cl and cr (direction frame)
 // and the cell eigenvalue ingredients of the two face cells.
 struct RoeF {
   float un, ut1, ut2, H, q2, c, ic, b1, b2, hb1, unL, unR, cL, cR;
 };
 
-__device__ __forceinline__ RoeF roe_f32(const float* __restrict__ S, int cl, int cr, float gm1) {
+__device__ __forceinline__ RoeF roe_f32(const float* __restrict__ S, int cl, int cr, float gm1, float g, float B,
+                                        Rot R) {
   RoeF e;
   const float rL = S[cl], rR = S[cr];
-  e.unL = S[SF_REG + cl];
-  e.unR = S[SF_REG + cr];
-  e.cL = S[6 * SF_REG + cl];
-  e.cR = S[6 * SF_REG + cr];
-  // sqrt(rho) weights, H = (E + p) / rho
+  const float pL = S[4 * SF_REG + cl], pR = S[4 * SF_REG + cr];
+  e.unL = S[R.n + cl];
+  e.unR = S[R.n + cr];
+  // sqrt(rho) weights, H = (E + p) / rho, c = sqrt(gamma (p + B) / rho)
   const float rsL = rsqrtf(rL), rsR = rsqrtf(rR);
+  e.cL = sqrtf(g * (pL + B)) * rsL;
+  e.cR = sqrtf(g * (pR + B)) * rsR;
   const float sL = rL * rsL, sR = rR * rsR;
   const float iden = frcp(sL + sR);
   e.un = fmaf(sL, e.unL, sR * e.unR) * iden;
-  e.ut1 = fmaf(sL, S[2 * SF_REG + cl], sR * S[2 * SF_REG + cr]) * iden;
-  e.ut2 = fmaf(sL, S[3 * SF_REG + cl], sR * S[3 * SF_REG + cr]) * iden;
-  e.H = fmaf(S[5 * SF_REG + cl] + S[4 * SF_REG + cl], rsL, (S[5 * SF_REG + cr] + S[4 * SF_REG + cr]) * rsR) * iden;
+  e.ut1 = fmaf(sL, S[R.t1 + cl], sR * S[R.t1 + cr]) * iden;
+  e.ut2 = fmaf(sL, S[R.t2 + cl], sR * S[R.t2 + cr]) * iden;
+  e.H = fmaf(S[5 * SF_REG + cl] + pL, rsL, (S[5 * SF_REG + cr] + pR) * rsR) * iden;
   e.q2 = fmaf(e.un, e.un, fmaf(e.ut1, e.ut1, e.ut2 * e.ut2));
   const float c2 = gm1 * fmaf(-0.5f, e.q2, e.H);
   e.ic = rsqrtf(c2);
@@ -129,8 +148,8 @@ __device__ __forceinline__ void lrow_f32(const RoeF& e, int k, float l[5]) {
 
 // Conserved state and physical flux of the record at c in the direction frame
 // (index 1 normal, 2 and 3 tangential).
-__device__ __forceinline__ void cell_uf(const float* __restrict__ S, int c, float U[5], float F[5]) {
-  const float r = S[c], un = S[SF_REG + c], u1 = S[2 * SF_REG + c], u2 = S[3 * SF_REG + c];
+__device__ __forceinline__ void cell_uf(const float* __restrict__ S, int c, Rot R, float U[5], float F[5]) {
+  const float r = S[c], un = S[R.n + c], u1 = S[R.t1 + c], u2 = S[R.t2 + c];
   const float p = S[4 * SF_REG + c], E = S[5 * SF_REG + c];
   const float mn = r * un;
   U[0] = r;
@@ -193,12 +212,12 @@ __device__ __forceinline__ void char014(const float X[5], const RoeF& e, float& 
 // from the FP32 records; result in the direction frame.  With FEAT the
 // selector features of the face are returned as well.
 template <int MODE, bool FEAT>
-__device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, float gm1, bool lin,
-                                              float F[5], float* feat = nullptr) {
+__device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, Rot R, float gm1, float g,
+                                              float B, bool lin, float F[5], float* feat = nullptr) {
   float Ur[6][5], Fr[6][5];
 #pragma unroll
-  for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, Ur[m], Fr[m]);
-  const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1);
+  for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, R, Ur[m], Fr[m]);
+  const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1, g, B, R);
   // characteristic fluxes of all fields (l2 F = F2 - ut1 F0, l3 F = F3 - ut2 F0)
   float Gall[5][6];
 #pragma unroll
@@ -298,29 +317,45 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
 
 // Selector features of the face between records c0+2st and c0+3st (the
 // same arithmetic as the stage-0 kernel's).
-__device__ __forceinline__ void face_features_f32(const float* __restrict__ S, int c0, int st, const RoeF& e,
+__device__ __forceinline__ void face_features_f32(const float* __restrict__ S, int c0, int st, Rot R, const RoeF& e,
                                                   float f[15]) {
   float g[3][6], v[3][6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) {
     float U[5], F[5];
-    cell_uf(S, c0 + m * st, U, F);
+    cell_uf(S, c0 + m * st, R, U, F);
     char014(F, e, g[0][m], g[1][m], g[2][m]);
     char014(U, e, v[0][m], v[1][m], v[2][m]);
   }
   features_gv(g, v, e, f);
 }
 
-// Number of region records and faces of direction D for one slab.
+// Number of region records and faces of direction D for one slab (the
+// per-direction regions of the stage-0 selector variant and of the samples).
 __device__ __forceinline__ int region_cells(int D) { return D == 2 ? SF_REG : 22 * 16 * SF_TZ; }
-__device__ __forceinline__ int region_faces(int D) { return D == 2 ? NB * NB * (SF_TZ + 1) : 17 * 16 * SF_TZ; }
+__device__ __forceinline__ int region_faces(int D) { return D == 2 ? SF_NFZ : SF_NFX; }
 __device__ __forceinline__ int region_stride(int D) { return sel3i(D, 1, 16, 256); }
 
-// Stencil region of direction D for the slab at z0 -> FP32 records in S, the
-// velocity in the direction frame.  Cells beyond the block along D come from
-// the same-level face neighbour's internal cells when it exists (ulo/uhi,
-// else null: the block's own halo, filled by prediction or the boundary
-// condition).
+// One FP32 primitive record from the FP64 conserved state at s.
+__device__ __forceinline__ void put_record(const double* __restrict__ src, int s, float* __restrict__ S, int idx,
+                                           float g, float B, float gm1) {
+  const float r = d2f_fast(src[s]), mx = d2f_fast(src[NCELL + s]), my = d2f_fast(src[2 * NCELL + s]);
+  const float mz = d2f_fast(src[3 * NCELL + s]), E = d2f_fast(src[4 * NCELL + s]);
+  const float ir = frcp(r);
+  const float vx = mx * ir, vy = my * ir, vz = mz * ir;
+  const float q2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+  S[idx] = r;
+  S[SF_REG + idx] = vx;
+  S[2 * SF_REG + idx] = vy;
+  S[3 * SF_REG + idx] = vz;
+  S[4 * SF_REG + idx] = fmaf(gm1, fmaf(-0.5f * r, q2, E), -g * B);
+  S[5 * SF_REG + idx] = E;
+}
+
+// Stencil region of direction D for the slab at z0 -> records in S.  Cells
+// beyond the block along D come from the same-level face neighbour's internal
+// cells when it exists (ulo/uhi, else null: the block's own halo, filled by
+// prediction or the boundary condition).
 __device__ __forceinline__ void load_region_f32(int D, const double* __restrict__ u, float* __restrict__ S, int z0,
                                                 float g, float B, float gm1, const double* __restrict__ ulo = nullptr,
                                                 const double* __restrict__ uhi = nullptr) {
@@ -340,24 +375,35 @@ __device__ __forceinline__ void load_region_f32(int D, const double* __restrict_
       src = uhi;
       s -= sel3i(D, NB, NB * NS, NB * NS * NS);
     }
-    const float r = d2f_fast(src[s]), mx = d2f_fast(src[NCELL + s]), my = d2f_fast(src[2 * NCELL + s]);
-    const float mz = d2f_fast(src[3 * NCELL + s]), E = d2f_fast(src[4 * NCELL + s]);
-    const float ir = frcp(r);
-    const float vx = mx * ir, vy = my * ir, vz = mz * ir;
-    const float q2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
-    const float p = fmaf(gm1, fmaf(-0.5f * r, q2, E), -g * B);
-    S[idx] = r;
-    S[SF_REG + idx] = sel3(D, vx, vy, vz);
-    S[2 * SF_REG + idx] = sel3(D, vy, vz, vx);
-    S[3 * SF_REG + idx] = sel3(D, vz, vx, vy);
-    S[4 * SF_REG + idx] = p;
-    S[5 * SF_REG + idx] = E;
-    S[6 * SF_REG + idx] = sqrtf(g * (p + B) * ir);
+    put_record(src, s, S, idx, g, B, gm1);
   }
 }
 
-// Face f of direction D in the slab: first stencil record c0 and the face's
-// position (fa along D; ta, tb the block-face coordinates of a boundary face).
+// The x-y region of the slab at z0: slot ((kz * 22) + y + 3) * 22 + x + 3 for
+// x, y in [-3, 19) except the corners (outside the block in both x and y).
+__device__ __forceinline__ int xy_slot(int x, int y, int kz) { return (kz * 22 + y + 3) * 22 + x + 3; }
+
+__device__ __forceinline__ void load_xy_f32(const double* __restrict__ u, float* __restrict__ S, int z0, float g,
+                                            float B, float gm1, const double* __restrict__ uxl,
+                                            const double* __restrict__ uxh, const double* __restrict__ uyl,
+                                            const double* __restrict__ uyh) {
+  for (int idx = threadIdx.x; idx < SF_XY; idx += blockDim.x) {
+    const int x = idx % 22 - 3, y = (idx / 22) % 22 - 3, z = z0 + idx / 484;
+    const bool ox = x < 0 || x >= NB, oy = y < 0 || y >= NB;
+    if (ox && oy) continue;
+    const double* src = u;
+    int s = sidx(x, y, z);
+    if (x < 0 && uxl) { src = uxl; s += NB; }
+    else if (x >= NB && uxh) { src = uxh; s -= NB; }
+    else if (y < 0 && uyl) { src = uyl; s += NB * NS; }
+    else if (y >= NB && uyh) { src = uyh; s -= NB * NS; }
+    put_record(src, s, S, idx, g, B, gm1);
+  }
+}
+
+// Face f of direction D in the slab (per-direction regions): first stencil
+// record c0 and the face's position (fa along D; ta, tb the block-face
+// coordinates of a boundary face).
 __device__ __forceinline__ void face_of(int D, int f, int z0, int& fa, int& c0, int& ta, int& tb) {
   if (D == 0) {
     fa = f % 17;
@@ -414,6 +460,43 @@ __device__ __forceinline__ void to_lab(int D, float n, float t1, float t2, float
   z = sel3(D, t2, t1, n);
 }
 
+// Store face f's flux (direction frame of D) into the flux slots (row length
+// fstr per variable), and into
+// the block's face buffer (lab frame, FP64) when the face is on the block
+// boundary (gface 0 or 16 along D).
+__device__ __forceinline__ void store_face(int D, const float F[5], float* __restrict__ Fs, int fstr, int f, int gface,
+                                           int ta, int tb, double* __restrict__ fb) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Fs[v * fstr + f] = F[v];
+  if (gface == 0 || gface == NB) {
+    const int side = 2 * D + (gface == NB ? 1 : 0);
+    float Fl[5];
+    Fl[0] = F[0];
+    Fl[4] = F[4];
+    to_lab(D, F[1], F[2], F[3], Fl[1], Fl[2], Fl[3]);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fb[((side * NV + v) * NB + tb) * NB + ta] = f2d_fast(Fl[v]);
+  }
+}
+
+// acc[kz][.] += flux difference of direction D at column (ti, tj); lo, hi the
+// slots of the cell's lower and upper faces.
+__device__ __forceinline__ void add_diff(int D, const float* __restrict__ Fs, int fstr, int lo, int hi,
+                                         float (&a)[NV]) {
+  float d[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) d[v] = Fs[v * fstr + lo] - Fs[v * fstr + hi];
+  float dx, dy, dz;
+  to_lab(D, d[1], d[2], d[3], dx, dy, dz);
+  a[0] += d[0];
+  a[1] += dx;
+  a[2] += dy;
+  a[3] += dz;
+  a[4] += d[4];
+}
+
+// Per-direction sweep (the stage-0 selector variant, MODE 1): region of D,
+// faces with WENO5 fluxes and the selector's decisions, flux differences.
 template <int MODE>
 __device__ __forceinline__ void sweep_f32(int D, const double* __restrict__ u, double* __restrict__ fb,
                                           float* __restrict__ S, float* __restrict__ Fs, int z0, float g, float B,
@@ -431,58 +514,42 @@ __device__ __forceinline__ void sweep_f32(int D, const double* __restrict__ u, d
   __syncthreads();
   const int nf = region_faces(D);
   const int st = region_stride(D);
-  const int nfr = (MODE == 1) ? ((nf + blockDim.x - 1) / blockDim.x) * blockDim.x : nf;
+  const Rot R = rot_of(D);
+  const int nfr = ((nf + blockDim.x - 1) / blockDim.x) * blockDim.x;
   for (int f0 = threadIdx.x; f0 < nfr; f0 += blockDim.x) {
     const bool act = f0 < nf;
     const int f = act ? f0 : 0;
     int fa, c0, ta, tb;
     face_of(D, f, z0, fa, c0, ta, tb);
     // decision word of this warp's 32 consecutive faces
-    uint32_t* word = (MODE == 1 || MODE == 3) ? L.bits + (z0 / SF_TZ) * 108 + D * 34 + (f0 >> 5) : nullptr;
-    const bool lin = (MODE == 3) && ((*word >> (threadIdx.x & 31)) & 1u);
-    float F[5];
-    if (MODE == 1) {
-      // WENO5 fluxes and the selector's features of the same faces; flat
-      // stencils have all-zero features, whose logit z0 is known, so the warp
-      // runs the tensor-core MLP only when one of its faces is not flat
-      float fe[15];
-      const bool flat = !act || stencil_flat(S, c0, st);
-      if (act) face_flux_f32<MODE, true>(S, c0, st, gm1, false, F, fe);
-      float z = L.z0;
-      if (!__all_sync(0xffffffffu, flat)) {
-        if (flat) {
+    uint32_t* word = L.bits + (z0 / SF_TZ) * 108 + D * 34 + (f0 >> 5);
+    // WENO5 fluxes and the selector's features of the same faces; flat
+    // stencils have all-zero features, whose logit z0 is known, so the warp
+    // runs the tensor-core MLP only when one of its faces is not flat
+    float F[5], fe[15];
+    const bool flat = !act || stencil_flat(S, c0, st);
+    if (act) face_flux_f32<MODE, true>(S, c0, st, R, gm1, g, B, false, F, fe);
+    float z = L.z0;
+    if (!__all_sync(0xffffffffu, flat)) {
+      if (flat) {
 #pragma unroll
-          for (int q = 0; q < 15; ++q) fe[q] = 0.f;
-        }
-        const int wid = threadIdx.x >> 5;
-        mlp_put_row(L.rows + wid * 32 * 9, fe);
-        z = mlp_warp_logit(L.P, L.frag, L.rows + wid * 32 * 9, L.logit + wid * 32);
+        for (int q = 0; q < 15; ++q) fe[q] = 0.f;
       }
-      const bool dl = act && (z < L.tau);
-      const unsigned bl = __ballot_sync(0xffffffffu, dl), ba = __ballot_sync(0xffffffffu, act);
-      if ((threadIdx.x & 31) == 0) {
-        *word = bl;
-        if (L.count) {
-          atomicAdd(&L.count[0], (unsigned long long)__popc(bl));
-          atomicAdd(&L.count[1], (unsigned long long)__popc(ba));
-        }
+      const int wid = threadIdx.x >> 5;
+      mlp_put_row(L.rows + wid * 32 * 9, fe);
+      z = mlp_warp_logit(L.P, L.frag, L.rows + wid * 32 * 9, L.logit + wid * 32);
+    }
+    const bool dl = act && (z < L.tau);
+    const unsigned bl = __ballot_sync(0xffffffffu, dl), ba = __ballot_sync(0xffffffffu, act);
+    if ((threadIdx.x & 31) == 0) {
+      *word = bl;
+      if (L.count) {
+        atomicAdd(&L.count[0], (unsigned long long)__popc(bl));
+        atomicAdd(&L.count[1], (unsigned long long)__popc(ba));
       }
-      if (!act) continue;
-    } else {
-      face_flux_f32<MODE, false>(S, c0, st, gm1, lin, F);
     }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) Fs[v * SF_FMAX + f] = F[v];
-    const int gface = (D == 2) ? z0 + fa : fa;
-    if (gface == 0 || gface == NB) {
-      const int side = 2 * D + (gface == NB ? 1 : 0);
-      float Fl[5];
-      Fl[0] = F[0];
-      Fl[4] = F[4];
-      to_lab(D, F[1], F[2], F[3], Fl[1], Fl[2], Fl[3]);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) fb[((side * NV + v) * NB + tb) * NB + ta] = f2d_fast(Fl[v]);
-    }
+    if (!act) continue;
+    store_face(D, F, Fs, SF_NFZ, f, (D == 2) ? z0 + fa : fa, ta, tb, fb);
   }
   __syncthreads();
 #pragma unroll
@@ -491,16 +558,86 @@ __device__ __forceinline__ void sweep_f32(int D, const double* __restrict__ u, d
     if (D == 0) { lo = (kz * 16 + tj) * 17 + ti; hi = lo + 1; }
     else if (D == 1) { lo = (kz * 17 + tj) * 16 + ti; hi = lo + 16; }
     else { lo = (kz * 16 + tj) * 16 + ti; hi = lo + 256; }
-    float d[5];
+    add_diff(D, Fs, SF_NFZ, lo, hi, acc[kz]);
+  }
+  __syncthreads();
+}
+
+// x and y directions of the slab together (MODES 0, 2, 3): one region, one
+// loop over the 1088 x faces followed by the 1088 y faces.
+template <int MODE>
+__device__ __forceinline__ void sweep_xy(const double* __restrict__ u, double* __restrict__ fb, float* __restrict__ S,
+                                         float* __restrict__ Fs, int z0, float g, float B, float gm1,
+                                         float (&acc)[SF_TZ][NV], const LearnedCtx& L, const Topo& t,
+                                         const double* __restrict__ buf, int node) {
+  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+  {
+    const int n0 = t.nbr[(size_t)node * 27 + 12], n1 = t.nbr[(size_t)node * 27 + 14];
+    const int n2 = t.nbr[(size_t)node * 27 + 10], n3 = t.nbr[(size_t)node * 27 + 16];
+    const double* uxl = (n0 >= 0) ? buf + (size_t)t.slot[n0] * SLOT_U : nullptr;
+    const double* uxh = (n1 >= 0) ? buf + (size_t)t.slot[n1] * SLOT_U : nullptr;
+    const double* uyl = (n2 >= 0) ? buf + (size_t)t.slot[n2] * SLOT_U : nullptr;
+    const double* uyh = (n3 >= 0) ? buf + (size_t)t.slot[n3] * SLOT_U : nullptr;
+    load_xy_f32(u, S, z0, g, B, gm1, uxl, uxh, uyl, uyh);
+  }
+  __syncthreads();
+  for (int f = threadIdx.x; f < 2 * SF_NFX; f += blockDim.x) {
+    float F[5];
+    if (f < SF_NFX) {                     // x face: warp-uniform (1088 = 34 warps)
+      const int fa = f % 17, r = f / 17;  // r = kz * 16 + j
+      const int c0 = xy_slot(fa - 3, r % 16, r / 16);
+      const bool lin = (MODE == 3) && ((L.bits[(z0 / SF_TZ) * 108 + (f >> 5)] >> (threadIdx.x & 31)) & 1u);
+      face_flux_f32<MODE, false>(S, c0, 1, rot_of(0), gm1, g, B, lin, F);
+      store_face(0, F, Fs, SF_FMAX, f, fa, r % 16, z0 + r / 16, fb);
+    } else {                              // y face
+      const int fy = f - SF_NFX;
+      const int i = fy % 16, r = fy / 16; // r = kz * 17 + fa
+      const int fa = r % 17, kz = r / 17;
+      const int c0 = xy_slot(i, fa - 3, kz);
+      const bool lin = (MODE == 3) && ((L.bits[(z0 / SF_TZ) * 108 + 34 + (fy >> 5)] >> (threadIdx.x & 31)) & 1u);
+      face_flux_f32<MODE, false>(S, c0, 22, rot_of(1), gm1, g, B, lin, F);
+      store_face(1, F, Fs, SF_FMAX, f, fa, i, z0 + kz, fb);
+    }
+  }
+  __syncthreads();
 #pragma unroll
-    for (int v = 0; v < 5; ++v) d[v] = Fs[v * SF_FMAX + lo] - Fs[v * SF_FMAX + hi];
-    float dx, dy, dz;
-    to_lab(D, d[1], d[2], d[3], dx, dy, dz);
-    d[1] = dx;
-    d[2] = dy;
-    d[3] = dz;
+  for (int kz = 0; kz < SF_TZ; ++kz) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[kz][v] = (D == 0) ? d[v] : acc[kz][v] + d[v];
+    for (int v = 0; v < NV; ++v) acc[kz][v] = 0.f;
+    const int lx = (kz * 16 + tj) * 17 + ti, ly = SF_NFX + (kz * 17 + tj) * 16 + ti;
+    add_diff(0, Fs, SF_FMAX, lx, lx + 1, acc[kz]);
+    add_diff(1, Fs, SF_FMAX, ly, ly + 16, acc[kz]);
+  }
+  __syncthreads();
+}
+
+// z direction of the slab (MODES 0, 2, 3).
+template <int MODE>
+__device__ __forceinline__ void sweep_z(const double* __restrict__ u, double* __restrict__ fb, float* __restrict__ S,
+                                        float* __restrict__ Fs, int z0, float g, float B, float gm1,
+                                        float (&acc)[SF_TZ][NV], const LearnedCtx& L, const Topo& t,
+                                        const double* __restrict__ buf, int node) {
+  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+  {
+    const int nlo = t.nbr[(size_t)node * 27 + 4], nhi = t.nbr[(size_t)node * 27 + 22];
+    const double* ulo = (nlo >= 0) ? buf + (size_t)t.slot[nlo] * SLOT_U : nullptr;
+    const double* uhi = (nhi >= 0) ? buf + (size_t)t.slot[nhi] * SLOT_U : nullptr;
+    load_region_f32(2, u, S, z0, g, B, gm1, ulo, uhi);
+  }
+  __syncthreads();
+  for (int f = threadIdx.x; f < SF_NFZ; f += blockDim.x) {
+    const int i = f % 16, j = (f / 16) % 16, fa = f / 256;
+    const int c0 = (fa * 16 + j) * 16 + i;
+    const bool lin = (MODE == 3) && ((L.bits[(z0 / SF_TZ) * 108 + 68 + (f >> 5)] >> (threadIdx.x & 31)) & 1u);
+    float F[5];
+    face_flux_f32<MODE, false>(S, c0, 256, rot_of(2), gm1, g, B, lin, F);
+    store_face(2, F, Fs, SF_FMAX, f, z0 + fa, i, j, fb);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int kz = 0; kz < SF_TZ; ++kz) {
+    const int lo = (kz * 16 + tj) * 16 + ti;
+    add_diff(2, Fs, SF_FMAX, lo, lo + 256, acc[kz]);
   }
   __syncthreads();
 }
@@ -519,7 +656,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   LearnedCtx L{nullptr, nullptr, nullptr, nullptr, 0.f, nullptr, nullptr, 0.f};
   if (MODE == 1) {
-    uint32_t* frag = reinterpret_cast<uint32_t*>(Fs + NV * SF_FMAX);
+    uint32_t* frag = reinterpret_cast<uint32_t*>(Fs + NV * SF_NFZ);   // after one direction's face fluxes
     L.P = p.mlp;
     L.frag = frag;
     L.rows = frag + FRAG_N;
@@ -550,13 +687,15 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     if (MODE == 1) {
       // with the selector inlined, one copy of the sweep (direction at run
       // time) keeps the kernel within the instruction cache
+#pragma unroll
+      for (int kz = 0; kz < SF_TZ; ++kz)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[kz][v] = 0.f;
 #pragma unroll 1
       for (int D = 0; D < 3; ++D) sweep_f32<MODE>(D, u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
     } else {
-      // direction-specialised copies (constant strides and index arithmetic)
-      sweep_f32<MODE>(0, u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
-      sweep_f32<MODE>(1, u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
-      sweep_f32<MODE>(2, u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+      sweep_xy<MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+      sweep_z<MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
     }
     const double dx = ldexp(p.dx0, -t.level[node]);
     const double idx_ = 1.0 / dx;
