@@ -167,7 +167,7 @@ def roofline_numbers(linear_fraction=0.0):
 # capture summarised in profiles/stage_kernels_explosion_256.md (levels 0-2
 # explosion; traffic grows in proportion to the leaf cells of a launch).
 # Learned path: the mean over its stage-0 and stage-1/2 variants (1 + 2 launches).
-TRAFFIC_BYTES_PER_CELL = {"learned": None, "weno": None}
+TRAFFIC_BYTES_PER_CELL = {"learned": (148.0 + 154.9 + 155.1) / 3, "weno": (146.6 + 154.0 + 154.0) / 3}
 
 
 def measured_peaks():
@@ -371,7 +371,7 @@ def run_gpu(args, rank, world):
                      "frac": achieved / fp32_peak,
                      "traffic": (TRAFFIC_BYTES_PER_CELL["learned"] * cells_per_launch
                                  if TRAFFIC_BYTES_PER_CELL["learned"] else None),
-                     "traffic_note": "ncu dram bytes of a 2.1M-cell launch scaled to the launch's leaf cells",
+                     "traffic_note": "ncu dram bytes per leaf cell of 2.1M-cell launches (stage 0, 1, 2 mean) x the launch's leaf cells",
                      "kernel": "k_stage_f32<1> (stage 0, selector evaluated) + k_stage_f32<3> (stages 1, 2): fused RHS + RK stage",
                      "flops_per_cell_stage": per_cell, "avg_launch_ms": m["stage_ms"],
                      "peak_basis": f"FP32 CUDA cores {nsm} SMs x 128 lanes x 2 x {clk:.0f} MHz sampled"},

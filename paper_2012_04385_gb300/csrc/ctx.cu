@@ -69,7 +69,7 @@ struct mrb_ctx {
 
   uint64_t* d_keys = nullptr;
   int32_t *d_slot = nullptr, *d_level = nullptr, *d_inst = nullptr, *d_X = nullptr, *d_parent = nullptr,
-          *d_child0 = nullptr, *d_nbr = nullptr, *d_leaves = nullptr, *d_lvl_nodes = nullptr, *d_bc_items = nullptr, *d_cnt = nullptr,
+          *d_child0 = nullptr, *d_nbr = nullptr, *d_leaves = nullptr, *d_lvl_nodes = nullptr, *d_bc_items = nullptr, *d_jump = nullptr, *d_cnt = nullptr,
           *d_lmax = nullptr, *d_list = nullptr;
   double *d_dt = nullptr, *d_delta_node = nullptr, *d_partial = nullptr;
   unsigned long long* d_smax = nullptr;
@@ -82,6 +82,9 @@ struct mrb_ctx {
   cudaStream_t cap_st = nullptr;     // private stream for capture (the caller's may be the legacy stream)
   bool graph_dirty = true;
   bool detail_filled = false;        // leaves' halos hold rho and E only (fill before the details)
+  char* h_stage = nullptr;           // pinned staging of the topology uploads
+  int32_t* h_list = nullptr;         // pinned staging of work lists
+  cudaEvent_t stage_ev = nullptr, list_ev = nullptr;
   long long graph_kernels[2] = {0, 0};
   int capturing = -1;                // graph parity being captured, or -1
   cudaEvent_t gev[2][3][2] = {};     // events around the stage kernel inside each graph
@@ -104,6 +107,7 @@ struct mrb_ctx {
     t.leaves = d_leaves;
     t.lvl_nodes = d_lvl_nodes;
     t.bc_items = d_bc_items;
+    t.jump = d_jump;
     t.cnt = d_cnt;
     return t;
   }
@@ -129,11 +133,29 @@ struct mrb_ctx {
     h_parent.assign(n, -1);
     h_child0.assign(n, -1);
     h_leaves.clear();
-    for (int i = 0; i < n; ++i) {
-      const HNode& a = nodes[i];
-      const uint64_t inst = a.key >> 56;
-      if (a.level > 0) h_parent[i] = (int32_t)find((((a.key & MASK56) >> 3)) | (inst << 56));
-      h_child0[i] = (int32_t)find((((a.key & MASK56) << 3)) | (inst << 56));
+    // Parents by a merge: ids are sorted (instance, then level through the
+    // headbit, then Morton order), and along each (instance, level) run the
+    // parent ids (id >> 3) do not decrease.  The first child of a parent in
+    // id order is its child 0 (siblings come in complete groups of eight).
+    {
+      int64_t q = 0;
+      int run_inst = -1, run_level = -1;
+      for (int i = 0; i < n; ++i) {
+        const HNode& a = nodes[i];
+        if (a.level == 0) continue;
+        const uint64_t pk = ((a.key & MASK56) >> 3) | ((a.key >> 56) << 56);
+        if (a.inst != run_inst || a.level != run_level) {
+          q = std::lower_bound(nodes.begin(), nodes.end(), pk,
+                               [](const HNode& b, uint64_t k) { return b.key < k; }) - nodes.begin();
+          run_inst = a.inst;
+          run_level = a.level;
+        }
+        while (q < n && nodes[q].key < pk) ++q;
+        if (q < n && nodes[q].key == pk) {
+          h_parent[i] = (int32_t)q;
+          if (h_child0[q] < 0) h_child0[q] = i;
+        }
+      }
     }
     for (int i = 0; i < n; ++i)
       if (h_child0[i] < 0) h_leaves.push_back(i);
@@ -161,33 +183,45 @@ struct mrb_ctx {
       }
     }
     h_cnt[CNT_BC + MAXL + 1] = (int)h_bc_items.size();
-    std::vector<uint64_t> k(n);
-    std::vector<int32_t> s(n), lv(n), in(n), X(3 * (size_t)n);
-    for (int i = 0; i < n; ++i) {
-      k[i] = nodes[i].key;
-      s[i] = nodes[i].slot;
-      lv[i] = nodes[i].level;
-      in[i] = nodes[i].inst;
-      for (int d = 0; d < 3; ++d) X[3 * (size_t)i + d] = nodes[i].X[d];
+    h_cnt[CNT_JUMP] = 0;     // counted on the device after the neighbour table
+    // one pinned staging area for every array (asynchronous copies); the
+    // previous rebuild's copies have long finished when it is rewritten
+    if (stage_ev) CK(cudaEventSynchronize(stage_ev));
+    char* q = h_stage;
+    auto put = [&](void* dev, const void* src, size_t bytes) {
+      if (bytes == 0) return;
+      std::memcpy(q, src, bytes);
+      CK(cudaMemcpyAsync(dev, q, bytes, cudaMemcpyHostToDevice, st));
+      q += (bytes + 15) & ~(size_t)15;
+    };
+    {
+      uint64_t* k = reinterpret_cast<uint64_t*>(q);
+      for (int i = 0; i < n; ++i) k[i] = nodes[i].key;
+      CK(cudaMemcpyAsync(d_keys, k, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st));
+      q += (sizeof(uint64_t) * n + 15) & ~(size_t)15;
+      int32_t* a = reinterpret_cast<int32_t*>(q);
+      for (int i = 0; i < n; ++i) {
+        a[i] = nodes[i].slot;
+        a[n + i] = nodes[i].level;
+        a[2 * n + i] = nodes[i].inst;
+        for (int d = 0; d < 3; ++d) a[3 * n + 3 * i + d] = nodes[i].X[d];
+      }
+      CK(cudaMemcpyAsync(d_slot, a, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_level, a + n, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_inst, a + 2 * n, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_X, a + 3 * n, sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, st));
+      q += (sizeof(int32_t) * 6 * n + 15) & ~(size_t)15;
     }
-    CK(cudaMemcpyAsync(d_keys, k.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_slot, s.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_level, lv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_inst, in.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_X, X.data(), sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_parent, h_parent.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_child0, h_child0.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_leaves, h_leaves.data(), sizeof(int32_t) * h_leaves.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_lvl_nodes, h_lvl_nodes.data(), sizeof(int32_t) * h_lvl_nodes.size(), cudaMemcpyHostToDevice,
-                       st));
-    if (!h_bc_items.empty())
-      CK(cudaMemcpyAsync(d_bc_items, h_bc_items.data(), sizeof(int32_t) * h_bc_items.size(), cudaMemcpyHostToDevice,
-                         st));
-    CK(cudaMemcpyAsync(d_cnt, h_cnt.data(), sizeof(int32_t) * CNT_SIZE, cudaMemcpyHostToDevice, st));
+    put(d_parent, h_parent.data(), sizeof(int32_t) * n);
+    put(d_child0, h_child0.data(), sizeof(int32_t) * n);
+    put(d_leaves, h_leaves.data(), sizeof(int32_t) * h_leaves.size());
+    put(d_lvl_nodes, h_lvl_nodes.data(), sizeof(int32_t) * h_lvl_nodes.size());
+    put(d_bc_items, h_bc_items.data(), sizeof(int32_t) * h_bc_items.size());
+    put(d_cnt, h_cnt.data(), sizeof(int32_t) * CNT_SIZE);
     launch_nbr(topo(), phys, d_nbr, n, st);
+    launch_jump_list(topo(), d_jump, d_cnt, (int)h_leaves.size(), st);
     CK(cudaGetLastError());
-    // the host vectors above are pageable: the copies are staged before return
-    CK(cudaStreamSynchronize(st));
+    CK(cudaEventRecord(stage_ev, st));
   }
 
   void check_launch() { CK(cudaGetLastError()); }
@@ -204,8 +238,13 @@ struct mrb_ctx {
 
   void upload_list(const std::vector<int32_t>& v) {
     if ((int64_t)v.size() > 2 * nslots) throw Err(MRB_ECAPACITY, "list longer than the pool");
-    CK(cudaMemcpyAsync(d_list, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice, st));
+    // pinned staging; wait until the device has read the previous list
+    if (list_ev) CK(cudaEventSynchronize(list_ev));
+    if (!v.empty()) std::memcpy(h_list, v.data(), sizeof(int32_t) * v.size());
+    CK(cudaMemcpyAsync(d_list, h_list, sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice, st));
   }
+  // after the kernels that read d_list have been launched
+  void list_used() { CK(cudaEventRecord(list_ev, st)); }
 
   // ---- the steps
   void fill_halos(int mode = FILL_FULL) {
@@ -317,6 +356,7 @@ struct mrb_ctx {
       // over their whole stored range
       upload_list(refine);
       launch_fill_list(topo(), phys, P, cur, d_list, (int)refine.size(), st);
+      list_used();
       check_launch();
     }
 
@@ -362,6 +402,7 @@ struct mrb_ctx {
       }
       upload_list(pairs);
       launch_refine_fill(topo(), phys, P, cur, d_list, (int)newpairs.size(), st);
+      list_used();
       check_launch();
     }
     return n_leaves();
@@ -381,6 +422,15 @@ struct mrb_ctx {
     }
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
+    if (stage_ev) cudaEventSynchronize(stage_ev);
+    if (list_ev) cudaEventSynchronize(list_ev);
+    if (stage_ev) cudaEventDestroy(stage_ev);
+    if (list_ev) cudaEventDestroy(list_ev);
+    if (h_stage) cudaFreeHost(h_stage);
+    if (h_list) cudaFreeHost(h_list);
+    stage_ev = list_ev = nullptr;
+    h_stage = nullptr;
+    h_list = nullptr;
   }
 };
 
@@ -505,6 +555,7 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     c->d_leaves = c->dalloc<int32_t>(n);
     c->d_lvl_nodes = c->dalloc<int32_t>(n);
     c->d_bc_items = c->dalloc<int32_t>(6 * n);
+    c->d_jump = c->dalloc<int32_t>(n);
     c->d_cnt = c->dalloc<int32_t>(CNT_SIZE);
     c->d_lmax = c->dalloc<int32_t>(cfg->n_instances);
     c->d_list = c->dalloc<int32_t>(2 * n);
@@ -515,6 +566,13 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     c->d_tags = c->dalloc<int8_t>(n);
     c->d_status = c->dalloc<int>(1);
     c->d_lin = c->dalloc<unsigned long long>(2);
+    // pinned staging of the topology uploads (keys, six int arrays of n, parent,
+    // child0, leaves, level lists, boundary items of 6 n, counts) and of work lists
+    if (cudaMallocHost((void**)&c->h_stage, 80 * n + 4 * CNT_SIZE + 256) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_list, sizeof(int32_t) * 2 * n) != cudaSuccess)
+      throw Err(MRB_ENOMEM, "pinned host staging");
+    CK(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->list_ev, cudaEventDisableTiming));
     p.lin_count = c->d_lin;
     p.lmax = c->d_lmax;
     CK(cudaMemsetAsync(c->d_lin, 0, 2 * sizeof(unsigned long long), c->st));
@@ -596,6 +654,7 @@ int mrb_set_state(mrb_ctx* c, const uint64_t* keys_host, int64_t n, const double
     std::vector<int32_t> v = c->nodes_of(keys_host, n);
     c->upload_list(v);
     launch_set_state(c->topo(), c->phys, c->P, c->cur, c->d_list, (int)n, prim_dev, c->st);
+    c->list_used();
   });
 }
 
@@ -605,6 +664,7 @@ int mrb_set_cons(mrb_ctx* c, const uint64_t* keys_host, int64_t n, const double*
     std::vector<int32_t> v = c->nodes_of(keys_host, n);
     c->upload_list(v);
     launch_set_cons(c->topo(), c->P, c->cur, c->d_list, (int)n, cons_dev, c->st);
+    c->list_used();
   });
 }
 
@@ -614,6 +674,7 @@ int mrb_get_state(mrb_ctx* c, const uint64_t* keys_host, int64_t n, double* cons
     std::vector<int32_t> v = c->nodes_of(keys_host, n);
     c->upload_list(v);
     launch_get_state(c->topo(), c->P, c->cur, c->d_list, (int)n, cons_dev, with_halo ? 1 : 0, c->st);
+    c->list_used();
   });
 }
 

@@ -173,8 +173,9 @@ void launch_face_avg_level(const Topo& t, const Pool& pool, int level, cudaStrea
 // inspection form), sides x-, x+, y-, y+, z-, z+ in order.
 __global__ void k_jump(Topo t, Phys p, Pool pool, int target, int stage, const double* __restrict__ dt,
                        double* __restrict__ rhs_out) {
-  const int nleaves = t.cnt[CNT_NLEAVES];
-  for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
+  const int nitems = t.cnt[CNT_JUMP];
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int li = t.jump[w] >> 6, mask = t.jump[w] & 63;
     const int node = t.leaves[li];
     const double* Fc_all = pool.face + (size_t)t.slot[node] * SLOT_F;
     const double dx = ldexp(p.dx0, -t.level[node]);
@@ -187,8 +188,8 @@ __global__ void k_jump(Topo t, Phys p, Pool pool, int target, int stage, const d
       int sv[3] = {0, 0, 0};
       sv[d] = hi ? 1 : -1;
       const int r = (sv[2] + 1) * 9 + (sv[1] + 1) * 3 + (sv[0] + 1);
+      if (!((mask >> s) & 1)) continue;      // the side's neighbour is not refined
       const int nb = t.nbr[(size_t)node * 27 + r];
-      if (nb < 0 || t.child0[nb] < 0) continue;
       const double* Ff_all = pool.face + (size_t)t.slot[nb] * SLOT_F;
       const int so = s ^ 1;
       const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
@@ -399,6 +400,27 @@ __global__ void k_nbr(Topo t, Phys p, int32_t* __restrict__ nbr_out) {
     }
     nbr_out[e] = found;
   }
+}
+
+__global__ void k_jump_list(Topo t, int32_t* __restrict__ jump, int32_t* __restrict__ cnt) {
+  const int nleaves = t.cnt[CNT_NLEAVES];
+  for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < nleaves; li += gridDim.x * blockDim.x) {
+    const int node = t.leaves[li];
+    int mask = 0;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      const int d = s / 2, hi = s & 1;
+      const int r = 13 + (hi ? 1 : -1) * (d == 0 ? 1 : (d == 1 ? 3 : 9));
+      const int nb = t.nbr[(size_t)node * 27 + r];
+      if (nb >= 0 && t.child0[nb] >= 0) mask |= 1 << s;
+    }
+    if (mask) jump[atomicAdd(&cnt[CNT_JUMP], 1)] = 64 * li + mask;
+  }
+}
+
+void launch_jump_list(const Topo& t, int32_t* jump, int32_t* cnt, int n_leaves_cap, cudaStream_t st) {
+  k_jump_list<<<(n_leaves_cap + 255) / 256 + 1, 256, 0, st>>>(t, jump, cnt);
+  ++g_kernel_launches;
 }
 
 void launch_nbr(const Topo& t, const Phys& p, int32_t* nbr_out, int nnodes_cap, cudaStream_t st) {

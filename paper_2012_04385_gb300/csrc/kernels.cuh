@@ -12,7 +12,8 @@ namespace mrb {
 constexpr int MAXL = 11;              // deepest level
 constexpr int CNT_NNODES = 0, CNT_NLEAVES = 1, CNT_LVL = 2;   // lvl offsets at CNT_LVL + l, l = 0..MAXL+1
 constexpr int CNT_BC = CNT_LVL + MAXL + 2;                     // bc item offsets at CNT_BC + l, l = 0..MAXL+1
-constexpr int CNT_SIZE = CNT_BC + MAXL + 2;
+constexpr int CNT_JUMP = CNT_BC + MAXL + 2;                    // number of jump items
+constexpr int CNT_SIZE = CNT_JUMP + 1;
 
 enum : int { ST_OK = 0, ST_NONPHYS = 6 };
 
@@ -36,6 +37,7 @@ struct Topo {
   const int32_t* leaves;   // leaf node indices, ascending id
   const int32_t* lvl_nodes;// node indices grouped by level
   const int32_t* bc_items; // 8 * node + side of every non-periodic domain-boundary side, grouped by level
+  const int32_t* jump;     // 64 * leaf index + mask of the sides whose same-level neighbour is refined
   const int32_t* cnt;      // counts, see CNT_*
 };
 
@@ -90,6 +92,10 @@ void launch_delta_tags(const Topo& t, const Phys& p, const Pool& pool, int cur, 
                        int allow_refine, int8_t* tags, double* delta_leaf, int n_leaves_cap, cudaStream_t st);
 void launch_refine_fill(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* pairs, int n,
                         cudaStream_t st);
+// Leaves with resolution jumps (a same-level face neighbour that is refined):
+// jump[] = 64 * leaf index + side mask, counted into cnt[CNT_JUMP] (item
+// order unspecified; every item is independent).
+void launch_jump_list(const Topo& t, int32_t* jump, int32_t* cnt, int n_leaves_cap, cudaStream_t st);
 void launch_nbr(const Topo& t, const Phys& p, int32_t* nbr_out, int nnodes_cap, cudaStream_t st);
 void launch_sums(const Topo& t, const Phys& p, const Pool& pool, int cur, double* partial, double* out,
                  int nleaves_cap, cudaStream_t st);

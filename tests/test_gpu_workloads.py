@@ -1,0 +1,131 @@
+"""The paper-shaped workloads on the GPU against the oracle: the shock-bubble
+interaction and the Rayleigh-Taylor layer (gravity source, symmetry walls) on
+small trees, the MR explosion at its full size (levels 0..3, 256^3
+effective) in the launch configuration the benchmark times, and free-stream
+preservation on every GPU path across resolution jumps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2012_04385_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2012_04385_gb300 import learned, mrb  # noqa: E402
+
+
+def oracle_init_tree(o, cfg, ic):
+    """Alg. (Initialization) on the oracle (same sequence as mrb.init_tree)."""
+    lmax = max(cfg.lmax_of(i) for i in range(cfg.n_instances))
+    o.set_state(o.keys(), ic(cfg, o.geometry()))
+    for m in range(1, lmax + 1):
+        o.fill_halos()
+        geo = o.geometry()
+        o.remesh((geo[:, 0] == m - 1).astype(np.int8))
+        o.set_state(o.keys(level=m), ic(cfg, o.geometry(level=m)))
+        if m > 1:
+            o.fill_halos()
+            t, _ = o.predict_and_tag(allow_refine=False)
+            o.remesh(t)
+    o.project()
+
+
+def slots(cfg):
+    base = int(np.prod(cfg.base_blocks)) * cfg.n_instances
+    return int(sum(base * 8 ** l for l in range(max(cfg.lmax_of(i) for i in range(cfg.n_instances)) + 1)))
+
+
+def run_pair(cfg, ic, nsteps):
+    o = oracle.Oracle(cfg)
+    oracle_init_tree(o, cfg, ic)
+    g = mrb.Context(cfg, slots(cfg))
+    mrb.init_tree(g, ic)
+    assert np.array_equal(o.keys(leaves_only=False), g.keys(leaves_only=False))
+    dts_o = o.step(nsteps)
+    dts_g = torch.empty((nsteps, cfg.n_instances), dtype=torch.float64, device="cuda")
+    g.step(nsteps, dts_g)
+    return o, g, dts_o, dts_g.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", ["shock_bubble", "rayleigh_taylor"])
+def test_paper_workloads_fp64_bit_exact(name):
+    if name == "shock_bubble":
+        cfg, ic, n = I.shock_bubble_config(lmax=2), I.ic_shock_bubble, 3
+    else:
+        cfg, ic, n = I.rt_config(lmax=1), I.ic_rt, 3
+    o, g, dts_o, dts_g = run_pair(cfg, ic, n)
+    assert np.array_equal(dts_g, dts_o)
+    assert np.array_equal(o.keys(leaves_only=False), g.keys(leaves_only=False))
+    k = o.keys()
+    ref, got = o.get_state(k), g.get_state(k).cpu().numpy()
+    print(name, "leaves", len(k), "values not bit-identical:", np.count_nonzero(got != ref))
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.slow
+def test_full_size_explosion_one_step_vs_oracle():
+    """The benchmark's workload (levels 0..3, initial tree about 2500 leaves):
+    one full step of the FP64 GPU path is bit-identical to the oracle's, and
+    the FP32 bulk path is within 1e-5 L1 density of it."""
+    cfg = I.explosion_config(lmax=3)
+    o, g, dts_o, dts_g = run_pair(cfg, I.ic_explosion, 1)
+    assert np.array_equal(dts_g, dts_o)
+    assert np.array_equal(o.keys(leaves_only=False), g.keys(leaves_only=False))
+    k = o.keys()
+    ref = o.get_state(k)
+    assert np.array_equal(g.get_state(k).cpu().numpy(), ref)
+    g32 = mrb.Context(I.explosion_config(lmax=3, precision=I.FP32_ACC64), slots(cfg))
+    mrb.init_tree(g32, I.ic_explosion)
+    g32.step(1)
+    assert np.array_equal(g32.keys(leaves_only=False), o.keys(leaves_only=False))
+    got = g32.get_state(k).cpu().numpy()
+    l1 = np.abs(got[:, 0] - ref[:, 0]).sum() / np.abs(ref[:, 0]).sum()
+    print("full size, FP32 bulk L1 density vs oracle after one step:", l1)
+    assert l1 < 1e-5
+
+
+@pytest.fixture(scope="module")
+def selector():
+    data = learned.generate(sod_steps=6, explosion_steps=4, every=3, stride=9, explosion_lmax=2)
+    params, tau, _ = learned.train(data, epochs=3, batch=8192)
+    return params, tau
+
+
+@pytest.mark.parametrize("path", ["fp64", "fp32_weno", "fp32_linear", "fp32_learned"])
+def test_free_stream_preserved(path, selector):
+    """A uniform state on a tree with resolution jumps: the RHS is bitwise
+    zero (identical face fluxes cancel; prediction of a constant is exact), so
+    after 4 steps every cell still holds one and the same value, within the
+    rounding of the TVD-RK3 convex combinations (2 ulp per step) of the
+    initial one."""
+    kw = dict(precision=I.FP64) if path == "fp64" else dict(precision=I.FP32_ACC64)
+    if path == "fp32_linear":
+        kw["recon"] = I.RECON_LINEAR
+    if path == "fp32_learned":
+        kw["recon"], kw["mlp_tau"] = I.RECON_LEARNED, selector[1]
+    cfg = I.periodic_config(base=(2, 2, 2), lmax=2, **kw)
+    g = mrb.Context(cfg, 8 * 73, mlp_params=selector[0] if path == "fp32_learned" else None)
+    k, geo = g.list_blocks()
+    g.set_state(k, I.ic_uniform(cfg, geo))
+    g.fill_halos()
+    mask = (geo[:, 1] == 0).astype(np.int8)           # refine half of the blocks: jumps
+    g.remesh(mask)
+    k, geo = g.list_blocks()
+    g.set_state(k, I.ic_uniform(cfg, geo))
+    g.mr_project()
+    g.fill_halos()
+    assert np.count_nonzero(g.compute_rhs().cpu().numpy()) == 0, path
+    u0 = g.get_state(k).cpu().numpy()
+    g.step(4)
+    assert np.array_equal(g.keys(), k)
+    u1 = g.get_state(k).cpu().numpy()
+    for v in range(5):
+        vals = np.unique(u1[:, v])
+        assert vals.size == 1, (path, v)
+        ref = u0[0, v, 0, 0, 0]
+        assert abs(vals[0] - ref) <= 2 * 4 * np.spacing(abs(ref)) + 1e-300, (path, v)
