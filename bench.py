@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    # wrap the headline path's timed steps in cudaProfilerStart/Stop (for
+    # ncu --profile-from-start off)
+    ap.add_argument("--profile-range", action="store_true")
     return ap.parse_args()
 
 
@@ -219,7 +222,7 @@ class Ranks:
 
 
 # ------------------------------------------------------------------ GPU arm
-def timed_path(args, cfg, stream, steps, warmup, mlp_params=None, profile=True):
+def timed_path(args, cfg, stream, steps, warmup, mlp_params=None, profile=True, profiler_range=False):
     """Build the workload tree, warm up, time `steps` full steps with CUDA
     events on the launching stream; returns the context and measurements."""
     import torch
@@ -235,12 +238,16 @@ def timed_path(args, cfg, stream, steps, warmup, mlp_params=None, profile=True):
     ctx.learned_stats(reset=True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     cells = 0
+    if profiler_range:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     for _ in range(steps):
         cells += ctx.n_leaves() * 4096 * 3
         ctx.step(1)
     ev1.record(stream)
     torch.cuda.synchronize()
+    if profiler_range:
+        torch.cuda.profiler.stop()
     ms = ev0.elapsed_time(ev1)
     kms, kn, nk = ctx.profile_read() if profile else (0.0, 0, 0)
     lin, tot = ctx.learned_stats()
@@ -290,7 +297,8 @@ def run_gpu(args, rank, world):
     barrier()
     sampler = ClockSampler(dev)
     sampler.start()
-    ctx, m = timed_path(args, cfg_l, stream, args.steps, args.warmup, mlp_params=params)
+    ctx, m = timed_path(args, cfg_l, stream, args.steps, args.warmup, mlp_params=params,
+                        profiler_range=args.profile_range)
     clocks = sampler.stop()
     barrier()
     ms_max = max_over_ranks(m["ms"])

@@ -120,7 +120,6 @@ template <class R> __device__ __forceinline__ R predict_t(const QT<R>& t, R sx, 
          (sx * sy * sz) * t.Qxyz;
 }
 
-__device__ __forceinline__ int sgn_region(int rel) { return rel < 0 ? -1 : (rel >= 8 ? 1 : 0); }
 
 // ---------------------------------------------------------------- halo fill by region
 // Sec. 3 (Fig. MrCommunicationMesh): a halo region facing a same-level node
@@ -505,21 +504,34 @@ static __global__ void __launch_bounds__(256) k_project_octants(Topo t, Pool poo
     const int c0 = t.child0[node];
     if (c0 < 0) continue;
     const int o = w % 8;
-    double* Pp = B + (size_t)t.slot[node] * SLOT_U;
-    const double* C = B + (size_t)t.slot[c0 + o] * SLOT_U;
+    double* __restrict__ Pp = B + (size_t)t.slot[node] * SLOT_U;
+    const double* __restrict__ C = B + (size_t)t.slot[c0 + o] * SLOT_U;
     const int ox = 8 * (o & 1), oy = 8 * ((o >> 1) & 1), oz = 8 * ((o >> 2) & 1);
-    for (int e = threadIdx.x; e < 512 * NV; e += blockDim.x) {
-      const int v = e / 512, c = e % 512;
-      const int I = c % 8, J = (c / 8) % 8, K = c / 64;
-      const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
-      const double* u = C + v * NCELL;
-      // fi is even: each x-pair of children is one aligned 16-byte load
-      const double2 a01 = *reinterpret_cast<const double2*>(u + sidx(fi, fj, fk));
-      const double2 a23 = *reinterpret_cast<const double2*>(u + sidx(fi, fj + 1, fk));
-      const double2 a45 = *reinterpret_cast<const double2*>(u + sidx(fi, fj, fk + 1));
-      const double2 a67 = *reinterpret_cast<const double2*>(u + sidx(fi, fj + 1, fk + 1));
-      Pp[v * NCELL + sidx(ox + I, oy + J, oz + K)] =
-          0.125 * (((a01.x + a01.y) + (a23.x + a23.y)) + ((a45.x + a45.y) + (a67.x + a67.y)));
+    // two parent cells per iteration, their eight 16-byte child loads in flight together
+    for (int e0 = threadIdx.x; e0 < 512 * NV; e0 += 2 * blockDim.x) {
+      double2 a[2][4];
+      int dst[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int e = e0 + q * blockDim.x;
+        const int v = e / 512, c = e % 512;
+        const int I = c % 8, J = (c / 8) % 8, K = c / 64;
+        const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
+        dst[q] = v * NCELL + sidx(ox + I, oy + J, oz + K);
+        // fi is even: each x-pair of children is one aligned 16-byte load
+        const double* u = C + v * NCELL;
+        if (e < 512 * NV) {
+          a[q][0] = *reinterpret_cast<const double2*>(u + sidx(fi, fj, fk));
+          a[q][1] = *reinterpret_cast<const double2*>(u + sidx(fi, fj + 1, fk));
+          a[q][2] = *reinterpret_cast<const double2*>(u + sidx(fi, fj, fk + 1));
+          a[q][3] = *reinterpret_cast<const double2*>(u + sidx(fi, fj + 1, fk + 1));
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (e0 + q * blockDim.x < 512 * NV)
+          Pp[dst[q]] = 0.125 * (((a[q][0].x + a[q][0].y) + (a[q][1].x + a[q][1].y)) +
+                                ((a[q][2].x + a[q][2].y) + (a[q][3].x + a[q][3].y)));
     }
   }
 }

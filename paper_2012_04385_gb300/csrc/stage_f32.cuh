@@ -437,6 +437,7 @@ struct LearnedCtx {
   unsigned long long* count; // [0] faces sent to linear, [1] faces evaluated (nullable)
   uint32_t* bits;            // this block's decision words (SLOT_SEL)
   float z0;                  // the network's logit for all-zero features
+  const uint32_t* selw;      // MODE 3: the slab's 108 decision words, staged in shared memory
 };
 
 // True when the six stencil records are identical, in which case every
@@ -586,7 +587,7 @@ __device__ __forceinline__ void sweep_xy(const double* __restrict__ u, double* _
     if (f < SF_NFX) {                     // x face: warp-uniform (1088 = 34 warps)
       const int fa = f % 17, r = f / 17;  // r = kz * 16 + j
       const int c0 = xy_slot(fa - 3, r % 16, r / 16);
-      const bool lin = (MODE == 3) && ((L.bits[(z0 / SF_TZ) * 108 + (f >> 5)] >> (threadIdx.x & 31)) & 1u);
+      const bool lin = (MODE == 3) && ((L.selw[f >> 5] >> (threadIdx.x & 31)) & 1u);
       face_flux_f32<MODE, false>(S, c0, 1, rot_of(0), gm1, g, B, lin, F);
       store_face(0, F, Fs, SF_FMAX, f, fa, r % 16, z0 + r / 16, fb);
     } else {                              // y face
@@ -594,7 +595,7 @@ __device__ __forceinline__ void sweep_xy(const double* __restrict__ u, double* _
       const int i = fy % 16, r = fy / 16; // r = kz * 17 + fa
       const int fa = r % 17, kz = r / 17;
       const int c0 = xy_slot(i, fa - 3, kz);
-      const bool lin = (MODE == 3) && ((L.bits[(z0 / SF_TZ) * 108 + 34 + (fy >> 5)] >> (threadIdx.x & 31)) & 1u);
+      const bool lin = (MODE == 3) && ((L.selw[34 + (fy >> 5)] >> (threadIdx.x & 31)) & 1u);
       face_flux_f32<MODE, false>(S, c0, 22, rot_of(1), gm1, g, B, lin, F);
       store_face(1, F, Fs, SF_FMAX, f, fa, i, z0 + kz, fb);
     }
@@ -628,7 +629,7 @@ __device__ __forceinline__ void sweep_z(const double* __restrict__ u, double* __
   for (int f = threadIdx.x; f < SF_NFZ; f += blockDim.x) {
     const int i = f % 16, j = (f / 16) % 16, fa = f / 256;
     const int c0 = (fa * 16 + j) * 16 + i;
-    const bool lin = (MODE == 3) && ((L.bits[(z0 / SF_TZ) * 108 + 68 + (f >> 5)] >> (threadIdx.x & 31)) & 1u);
+    const bool lin = (MODE == 3) && ((L.selw[68 + (f >> 5)] >> (threadIdx.x & 31)) & 1u);
     float F[5];
     face_flux_f32<MODE, false>(S, c0, 256, rot_of(2), gm1, g, B, lin, F);
     store_face(2, F, Fs, SF_FMAX, f, z0 + fa, i, j, fb);
@@ -654,7 +655,8 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
   double* __restrict__ dst = pool.buf[cur ^ 1];
   const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
-  LearnedCtx L{nullptr, nullptr, nullptr, nullptr, 0.f, nullptr, nullptr, 0.f};
+  __shared__ uint32_t sel_sh[108];
+  LearnedCtx L{nullptr, nullptr, nullptr, nullptr, 0.f, nullptr, nullptr, 0.f, sel_sh};
   if (MODE == 1) {
     uint32_t* frag = reinterpret_cast<uint32_t*>(Fs + NV * SF_NFZ);   // after one direction's face fluxes
     L.P = p.mlp;
@@ -683,6 +685,8 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     const double* __restrict__ u = src + (size_t)slot * SLOT_U;
     double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
     if (MODE == 1 || MODE == 3) L.bits = pool.sel + (size_t)slot * SLOT_SEL;
+    // the slab's decision words (read before the first barrier of the sweep)
+    if (MODE == 3 && threadIdx.x < 108) sel_sh[threadIdx.x] = L.bits[(z0 / SF_TZ) * 108 + threadIdx.x];
     float acc[SF_TZ][NV];
     if (MODE == 1) {
       // with the selector inlined, one copy of the sweep (direction at run
