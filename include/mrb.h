@@ -215,7 +215,12 @@ int mrb_neighbors(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, uint64_t* 
  * sign(d) log10(1 + 1e6 |d|) / 8 -- and
  * predicts whether WENO5-JS is needed (logit >= mlp_tau) or the linear
  * 5th-order upwind reconstruction suffices (logit < mlp_tau) for those three
- * fields; the shear fields always use WENO5-JS.
+ * fields; the shear fields always use WENO5-JS.  The selector runs at
+ * stage 0 of each step (mrb_rk_stage with stage 0, and mrb_compute_rhs), on
+ * the faces whose WENO5 fluxes that stage computes, and stores one decision
+ * bit per face in the block pool; stages 1 and 2 apply the stored decisions
+ * (a stage 1 or 2 not preceded by a stage 0 since the last remesh reads
+ * decisions that belong to no state: call the stages in order).
  * Parameters: MRB_MLP_NPARAM floats (FP32 master copy, device) laid out
  * W1[32][15], b1[32], W2[32][32], b2[32], w3[32], b3; the kernels round
  * the weights to BF16 and run the layers on the tensor cores with FP32

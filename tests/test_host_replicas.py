@@ -3,7 +3,8 @@
 Each rank runs the whole workload on its own GPU; the only exchange is the
 timing: a barrier around the timed region, the maximum of the per-rank
 elapsed times and the sum of the per-rank cell-updates.  These tests run that
-host logic (bench.Ranks) in two processes without a GPU.
+host logic (bench.Ranks) in two processes without a GPU, and check the JSON
+contract of the benchmark's reference arm (the oracle on the host cores).
 """
 import os
 import socket
@@ -72,3 +73,18 @@ def test_single_rank_needs_no_process_group():
     assert r.max(3.0) == 3.0 and r.sum(4.0) == 4.0
     r.barrier()
     r.close()
+
+
+def test_reference_arm_json_contract():
+    """bench.py --impl reference: the oracle on the host cores, same metric and
+    unit as the GPU arm, with the cpu_baseline and e2e objects (small case)."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    args = argparse.Namespace(lmax=1, steps=1, warmup=1)
+    res = bench.run_reference(args, 0, 1)
+    assert res["impl"] == "reference" and res["metric"] == bench.METRIC and res["unit"] == bench.UNIT
+    assert res["value"] > 0 and res["higher_is_better"] is True
+    cb = res["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == res["value"] and cb["sample"]
+    assert res["e2e"] == {"value": res["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
