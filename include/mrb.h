@@ -65,6 +65,11 @@ extern "C" {
 #define MRB_RECON_WENO5 0     /* WENO5-JS everywhere                                 */
 #define MRB_RECON_LEARNED 1   /* per-face MLP chooses linear 5th order or WENO5-JS   */
 #define MRB_RECON_LINEAR5 2   /* linear 5th-order upwind everywhere (tests)          */
+#define MRB_RECON_TENO5 3     /* TENO5 everywhere (Fu, Hu & Adams 2016): the WENO5   */
+                              /* stencils kept or dropped by a sharp cutoff C_T =    */
+                              /* 1e-5 on gamma_k = (1 + tau5/(beta_k + eps))^6,      */
+                              /* tau5 = |beta0 - beta2|; kept ones combined with the */
+                              /* linear weights renormalised                         */
 
 /* refinement tags, one int8 per leaf in leaf order */
 #define MRB_TAG_KEEP 0
@@ -81,7 +86,8 @@ typedef struct mrb_config {
   int32_t bc[6];                   /* MRB_BC_* per side; periodic must be set on both sides*/
   int32_t precision;               /* MRB_FP64 | MRB_FP32_ACC64                            */
   int32_t recon;                   /* MRB_RECON_*                                          */
-  int32_t pad0;
+  int32_t rk_stages;               /* Runge-Kutta stages per step: 3 (TVD-RK3, also    */
+                                   /* when 0) or 2 (TVD-RK2)                           */
   int32_t pad1;
   double domain_lo[3];             /* lower corner of the domain                           */
   double dx0;                      /* level-0 cell size (block edge = 16 dx0)              */
@@ -150,11 +156,14 @@ int mrb_fill_halos(mrb_ctx* ctx);
  * stepping uses the fused mrb_rk_stage.  Halos must be filled. */
 int mrb_compute_rhs(mrb_ctx* ctx, double* rhs_dev);
 
-/* One TVD-RK3 stage (stage = 0, 1, 2) on every leaf, fused with the
- * right-hand side: u1 = un + dt L(un), u2 = 3/4 un + 1/4 (u1 + dt L(u1)),
- * u3 = 1/3 un + 2/3 (u2 + dt L(u2)), followed by the jump flux correction of
- * coarse cells next to finer leaves (Sec. 4, Alg. ComputeLoop).  dt_dev:
- * device [n_instances] time steps (from mrb_cfl_dt).  Halos must be filled. */
+/* One Runge-Kutta stage (stage = 0 .. rk_stages - 1) on every leaf, fused
+ * with the right-hand side, in Shu-Osher form.  TVD-RK3: u1 = un + dt L(un),
+ * u2 = 3/4 un + 1/4 (u1 + dt L(u1)), u3 = 1/3 un + 2/3 (u2 + dt L(u2));
+ * TVD-RK2 (the paper's standard second-order Runge-Kutta, Sec. 5): u1 = un +
+ * dt L(un), u2 = 1/2 un + 1/2 (u1 + dt L(u1)).  Followed by the jump flux
+ * correction of coarse cells next to finer leaves (Sec. 4, Alg. ComputeLoop).
+ * dt_dev: device [n_instances] time steps (from mrb_cfl_dt).  Halos must be
+ * filled. */
 int mrb_rk_stage(mrb_ctx* ctx, int32_t stage, const double* dt_dev);
 
 /* Time step of Eq. (Cfl) per instance: dt = CFL dx_lmax /
@@ -300,8 +309,9 @@ int mrb_block_sums_noalloc(const double* blocks_dev, int64_t n_blocks, const int
  * every SM): out[0] FP32 FMA TFLOP/s, out[1] FP64 FMA TFLOP/s, out[2]
  * double->float and out[3] float->double conversions (10^12 per s), out[4]
  * reciprocal square roots (10^12 per s), out[5] SM count, out[6] SM clock
- * (MHz) the device reports.  n >= 7.  Synchronises the device; allocates 64
- * bytes of scratch. */
+ * (MHz) the device reports; with n >= 8, out[7] packed FP32 FMA
+ * (fma.rn.f32x2, two FP32 FMAs per lane and instruction) TFLOP/s.  n >= 7.
+ * Synchronises the device; allocates 64 bytes of scratch. */
 int mrb_measure_peaks(double* out, int32_t n);
 
 int mrb_status(mrb_ctx* ctx);   /* sticky device status (synchronises)       */

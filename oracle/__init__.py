@@ -49,6 +49,8 @@ class OrcConfig(ctypes.Structure):
         ("bc", ctypes.c_int32 * 6),
         ("recon", ctypes.c_int32),
         ("n_threads", ctypes.c_int32),
+        ("rk_stages", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
         ("domain_lo", ctypes.c_double * 3),
         ("dx0", ctypes.c_double),
         ("gamma", ctypes.c_double),
@@ -92,6 +94,7 @@ def lib():
                 "orc_key_level": (i32, [u64]),
                 "orc_weno5": (dbl, [vp]),
                 "orc_linear5": (dbl, [vp]),
+                "orc_teno5": (dbl, [vp]),
                 "orc_flux": (None, [vp, i32, dbl, dbl, vp]),
                 "orc_roe_eigen": (None, [vp, vp, i32, dbl, dbl, vp, vp, vp]),
                 "orc_face_flux": (None, [vp, i32, dbl, dbl, i32, vp]),
@@ -122,6 +125,7 @@ def make_config(cfg, n_threads: int = 0) -> OrcConfig:
         c.bc[s] = int(cfg.bc[s])
     c.recon = int(cfg.recon)
     c.n_threads = int(n_threads)
+    c.rk_stages = int(getattr(cfg, "rk_stages", 3))
     c.dx0 = float(cfg.dx0)
     c.gamma = float(cfg.gamma)
     c.B = float(cfg.B)
@@ -256,6 +260,11 @@ def weno5(f) -> float:
 def linear5(f) -> float:
     f = np.ascontiguousarray(f, dtype=np.float64)
     return float(lib().orc_linear5(_p(f)))
+
+
+def teno5(f) -> float:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return float(lib().orc_teno5(_p(f)))
 
 
 def flux(U, d: int, gamma: float = 1.4, B: float = 0.0) -> np.ndarray:

@@ -50,7 +50,7 @@ constexpr int NSHADOW = 7;                   // shadow levels of the 64-bit id (
 constexpr uint64_t MASK56 = (1ull << 56) - 1;
 
 constexpr int BC_ZERO_GRADIENT = 0, BC_PERIODIC = 1, BC_SYMMETRY = 2;
-constexpr int RECON_WENO = 0, RECON_LINEAR = 2;
+constexpr int RECON_WENO = 0, RECON_LINEAR = 2, RECON_TENO = 3;
 constexpr int8_t TAG_KEEP = 0, TAG_REFINE = 1, TAG_COARSEN = -1;
 
 inline int sidx(int i, int j, int k) { return ((k + HW) * NS + (j + HW)) * NS + (i + HW); }
@@ -68,8 +68,10 @@ struct orc_config {
   int32_t base_blocks[3];
   int32_t lmax[256];
   int32_t bc[6];          // x-, x+, y-, y+, z-, z+
-  int32_t recon;          // 0 = WENO5-JS, 2 = linear 5th-order upwind everywhere
+  int32_t recon;          // 0 = WENO5-JS, 2 = linear 5th-order upwind everywhere, 3 = TENO5
   int32_t n_threads;      // 0 = OpenMP default
+  int32_t rk_stages;      // 3 = TVD-RK3 (default when 0), 2 = TVD-RK2
+  int32_t pad;
   double domain_lo[3];
   double dx0;             // level-0 cell size
   double gamma, B, cfl;
@@ -296,8 +298,43 @@ double linear5(double a, double b, double c, double d, double e) {
   return (0.1 * q0 + 0.6 * q1) + 0.3 * q2;
 }
 
+// TENO5 (Fu, Hu & Adams 2016, one of the reconstructions the paper's modular
+// framework offers, Sec. 2.2): the WENO5 candidate stencils and smoothness
+// indicators; each stencil is kept or dropped by a sharp cutoff on its
+// relative smoothness chi_k = gamma_k / sum gamma, gamma_k = (C + tau5 /
+// (beta_k + eps))^q with tau5 = |beta0 - beta2|, C = 1, q = 6, eps = 1e-40,
+// cutoff C_T = 1e-5; the kept stencils are combined with the linear weights,
+// renormalised.
+double teno5(double a, double b, double c, double d, double e) {
+  const double eps = 1e-40, CT = 1e-5;
+  double t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;
+  double beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  t1 = (b - 2.0 * c) + d;
+  t2 = b - d;
+  double beta1 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  t1 = (c - 2.0 * d) + e;
+  t2 = (3.0 * c - 4.0 * d) + e;
+  double beta2 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  const double tau = std::fabs(beta0 - beta2);
+  double r0 = 1.0 + tau / (beta0 + eps), r1 = 1.0 + tau / (beta1 + eps), r2 = 1.0 + tau / (beta2 + eps);
+  r0 = r0 * r0 * r0;
+  r1 = r1 * r1 * r1;
+  r2 = r2 * r2 * r2;
+  const double g0 = r0 * r0, g1 = r1 * r1, g2 = r2 * r2;
+  const double sum = (g0 + g1) + g2;
+  const double w0 = (g0 / sum < CT) ? 0.0 : 0.1;
+  const double w1 = (g1 / sum < CT) ? 0.0 : 0.6;
+  const double w2 = (g2 / sum < CT) ? 0.0 : 0.3;
+  double q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
+  double q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
+  double q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
+  return ((w0 * q0 + w1 * q1) + w2 * q2) / ((w0 + w1) + w2);
+}
+
 inline double recon5(int mode, double a, double b, double c, double d, double e) {
-  return (mode == RECON_LINEAR) ? linear5(a, b, c, d, e) : weno5(a, b, c, d, e);
+  if (mode == RECON_LINEAR) return linear5(a, b, c, d, e);
+  if (mode == RECON_TENO) return teno5(a, b, c, d, e);
+  return weno5(a, b, c, d, e);
 }
 
 // Numerical flux at the face between cells 2 and 3 of a six-cell stencil
@@ -830,8 +867,16 @@ void jump_correct(Ctx& C, bool target_L, double bs, const double* dt) {
 // ------------------------------------------------------------ time integration
 // TVD-RK3 in Shu-Osher form: u1 = un + dt L(un); u2 = 3/4 un + 1/4 (u1 + dt L(u1));
 // u3 = 1/3 un + 2/3 (u2 + dt L(u2)); evaluated as t = u + dt L, out = a un + b t.
-const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
-const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
+// TVD-RK2 (the paper's standard second-order Runge-Kutta, Sec. 5, in the same
+// form): u1 = un + dt L(un); u2 = 1/2 un + 1/2 (u1 + dt L(u1)).
+const double RK_A3[3] = {0.0, 0.75, 1.0 / 3.0};
+const double RK_B3[3] = {1.0, 0.25, 2.0 / 3.0};
+const double RK_A2[2] = {0.0, 0.5};
+const double RK_B2[2] = {1.0, 0.5};
+
+inline int rk_stages(const Ctx& C) { return C.c.rk_stages == 2 ? 2 : 3; }
+inline double rk_a(const Ctx& C, int s) { return rk_stages(C) == 2 ? RK_A2[s] : RK_A3[s]; }
+inline double rk_b(const Ctx& C, int s) { return rk_stages(C) == 2 ? RK_B2[s] : RK_B3[s]; }
 
 void rk_update(Ctx& C, int s, const double* dt) {
   std::vector<Node*> v = nodes_at(C, -1, true);
@@ -847,7 +892,7 @@ void rk_update(Ctx& C, int s, const double* dt) {
             size_t ii = (size_t)var * NINT + iidx(i, j, k);
             if (s == 0) n.un[ii] = n.u[si];
             double tt = n.u[si] + h * n.L[ii];
-            n.u[si] = (s == 0) ? tt : (RK_A[s] * n.un[ii] + RK_B[s] * tt);
+            n.u[si] = (s == 0) ? tt : (rk_a(C, s) * n.un[ii] + rk_b(C, s) * tt);
           }
   }
 }
@@ -1057,7 +1102,7 @@ void stage(Ctx& C, int s, const double* dt) {
   compute_L_all(C);
   average_faces(C);
   rk_update(C, s, dt);
-  jump_correct(C, false, RK_B[s], dt);
+  jump_correct(C, false, rk_b(C, s), dt);
   project(C);
 }
 
@@ -1207,13 +1252,13 @@ void orc_compute_rhs(void* h, double* L) {
   }
 }
 
-// One TVD-RK3 stage on the leaves: L, update, jump correction (halos must be filled).
+// One Runge-Kutta stage on the leaves: L, update, jump correction (halos must be filled).
 void orc_rk_stage(void* h, int32_t s, const double* dt) {
   Ctx& C = *(Ctx*)h;
   compute_L_all(C);
   average_faces(C);
   rk_update(C, s, dt);
-  jump_correct(C, false, RK_B[s], dt);
+  jump_correct(C, false, rk_b(C, s), dt);
 }
 
 void orc_project(void* h) { project(*(Ctx*)h); }
@@ -1224,7 +1269,7 @@ void orc_predict_and_tag(void* h, int32_t allow_refine, int8_t* tags, double* de
 int64_t orc_remesh(void* h, const int8_t* tags) { return remesh(*(Ctx*)h, tags); }
 void orc_sums(void* h, double* out) { sums(*(Ctx*)h, out); }
 
-// nsteps full steps: CFL, three stages, then (with MR) analysis and remesh.
+// nsteps full steps: CFL, the Runge-Kutta stages, then (with MR) analysis and remesh.
 // dt_hist (nullable) receives [nsteps][n_instances].
 void orc_step(void* h, int32_t nsteps, double* dt_hist) {
   Ctx& C = *(Ctx*)h;
@@ -1232,7 +1277,7 @@ void orc_step(void* h, int32_t nsteps, double* dt_hist) {
   for (int st = 0; st < nsteps; ++st) {
     cfl_dt(C, dt.data());
     if (dt_hist) std::memcpy(dt_hist + (size_t)st * C.c.n_instances, dt.data(), sizeof(double) * C.c.n_instances);
-    for (int s = 0; s < 3; ++s) stage(C, s, dt.data());
+    for (int s = 0; s < rk_stages(C); ++s) stage(C, s, dt.data());
     if (any_mr(C)) {
       fill_halos(C);
       std::vector<int8_t> tags((size_t)orc_list(h, -1, 1, nullptr, 0));
@@ -1258,6 +1303,7 @@ int32_t orc_key_level(uint64_t key) { return key_level(key); }
 // ---- pure functions exported for the pins
 double orc_weno5(const double* f) { return weno5(f[0], f[1], f[2], f[3], f[4]); }
 double orc_linear5(const double* f) { return linear5(f[0], f[1], f[2], f[3], f[4]); }
+double orc_teno5(const double* f) { return teno5(f[0], f[1], f[2], f[3], f[4]); }
 
 void orc_flux(const double* U, int32_t d, double g, double B, double* F) {
   Prim q = prim_of(U, g, B);

@@ -278,7 +278,7 @@ struct mrb_ctx {
     // the mixed-precision stage kernel reads face neighbours directly, so the
     // stage fill of leaves is limited to predicted and boundary face regions
     const int mode = (cfg.precision == MRB_FP32_ACC64) ? FILL_STAGE : FILL_FULL;
-    for (int s = 0; s < 3; ++s) {
+    for (int s = 0; s < phys.rk; ++s) {
       fill_halos(mode);
       stage(s, d_dt);
       project();
@@ -472,7 +472,8 @@ int check_config(const mrb_config* cfg) {
   for (int s = 0; s < 6; ++s)
     if (cfg->bc[s] < 0 || cfg->bc[s] > 2) return MRB_EINVAL;
   if (cfg->precision != MRB_FP64 && cfg->precision != MRB_FP32_ACC64) return MRB_EINVAL;
-  if (cfg->recon < 0 || cfg->recon > 2) return MRB_EINVAL;
+  if (cfg->recon < 0 || cfg->recon > 3) return MRB_EINVAL;
+  if (cfg->rk_stages != 0 && cfg->rk_stages != 2 && cfg->rk_stages != 3) return MRB_EINVAL;
   if (!(cfg->dx0 > 0) || !(cfg->gamma > 1.0) || !(cfg->cfl > 0)) return MRB_EINVAL;
   return MRB_OK;
 }
@@ -540,6 +541,7 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     p.n_inst = cfg->n_instances;
     p.recon = cfg->recon;
     p.precision = cfg->precision;
+    p.rk = (cfg->rk_stages == 2) ? 2 : 3;
     p.mlp = (const float*)cfg->mlp_weights;
     p.mlp_tau = (float)cfg->mlp_tau;
     c->max_lmax = 0;
@@ -694,7 +696,7 @@ int mrb_compute_rhs(mrb_ctx* c, double* rhs_dev) {
 
 int mrb_rk_stage(mrb_ctx* c, int32_t stage, const double* dt_dev) {
   return guarded(c, [&] {
-    if (stage < 0 || stage > 2 || !dt_dev) throw Err(MRB_EINVAL, "bad stage or dt");
+    if (stage < 0 || stage >= c->phys.rk || !dt_dev) throw Err(MRB_EINVAL, "bad stage or dt");
     c->stage(stage, dt_dev);
   });
 }
@@ -739,7 +741,7 @@ int mrb_step(mrb_ctx* c, int32_t nsteps, double* dt_hist_dev) {
       const int g = c->cur;
       CK(cudaGraphLaunch(c->graph[g], c->st));
       g_kernel_launches += c->graph_kernels[g];
-      c->cur ^= 1;   // three stages flip the stage buffer three times
+      if (c->phys.rk & 1) c->cur ^= 1;   // every stage flips the stage buffer
       if (dt_hist_dev)
         CK(cudaMemcpyAsync(dt_hist_dev + (size_t)s * c->cfg.n_instances, c->d_dt, sizeof(double) * c->cfg.n_instances,
                            cudaMemcpyDeviceToDevice, c->st));
@@ -752,7 +754,7 @@ int mrb_step(mrb_ctx* c, int32_t nsteps, double* dt_hist_dev) {
       }
       if (c->prof) {
         CK(cudaStreamSynchronize(c->st));
-        for (int q = 0; q < 3; ++q) {
+        for (int q = 0; q < c->phys.rk; ++q) {
           float ms = 0.f;
           CK(cudaEventElapsedTime(&ms, c->gev[g][q][0], c->gev[g][q][1]));
           c->prof_ms += ms;

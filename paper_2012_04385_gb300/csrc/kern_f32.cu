@@ -25,6 +25,7 @@ static void launch_stage_f32(const Topo& t, const Phys& p, const Pool& pool, int
 void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
                        double* rhs_out, cudaStream_t st) {
   if (p.recon == 2) launch_stage_f32<2>(t, p, pool, cur, stage, dt, rhs_out, st);
+  else if (p.recon == 3) launch_stage_f32<4>(t, p, pool, cur, stage, dt, rhs_out, st);
   else if (p.recon == 1 && p.mlp) {
     // the selector is evaluated on the stage-0 state; stages 1 and 2 use its decisions
     if (stage == 0 || rhs_out) launch_stage_f32<1>(t, p, pool, cur, stage, dt, rhs_out, st);

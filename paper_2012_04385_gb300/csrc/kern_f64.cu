@@ -180,7 +180,7 @@ __global__ void k_jump(Topo t, Phys p, Pool pool, int target, int stage, const d
     const double* Fc_all = pool.face + (size_t)t.slot[node] * SLOT_F;
     const double dx = ldexp(p.dx0, -t.level[node]);
     const double h = dt ? dt[t.inst[node]] : 0.0;
-    const double bs = kRkB[stage];
+    const double bs = kRkB[rk_row(p)][stage];
     double* U = pool.buf[target] + (size_t)t.slot[node] * SLOT_U;
 #pragma unroll 1
     for (int s = 0; s < 6; ++s) {

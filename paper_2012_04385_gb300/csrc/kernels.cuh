@@ -50,11 +50,18 @@ struct Phys {
   int recon;
   int has_grav;
   int precision;           // 0 FP64, 1 FP32 bulk (MRB_FP64 / MRB_FP32_ACC64)
+  int rk;                  // Runge-Kutta stages per step: 3 (TVD-RK3) or 2 (TVD-RK2)
   float mlp_tau;           // learned selector: linear reconstruction when logit < mlp_tau
   const float* mlp;        // learned selector parameters (device, FP32), or null
   unsigned long long* lin_count;   // [0] faces sent to linear, [1] faces evaluated
   const int32_t* lmax;     // device [n_inst]
 };
+
+// Shu-Osher coefficients of stage s: out = a u^n + b (u + dt L); row 0 TVD-RK3,
+// row 1 TVD-RK2.
+__device__ __constant__ static const double kRkA[2][3] = {{0.0, 0.75, 1.0 / 3.0}, {0.0, 0.5, 0.0}};
+__device__ __constant__ static const double kRkB[2][3] = {{1.0, 0.25, 2.0 / 3.0}, {1.0, 0.5, 0.0}};
+__device__ __forceinline__ int rk_row(const Phys& p) { return p.rk == 2 ? 1 : 0; }
 
 struct Pool {
   double* buf[2];          // stage buffers, [slot][5][24^3]

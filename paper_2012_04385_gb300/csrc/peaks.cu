@@ -22,6 +22,32 @@ __global__ void __launch_bounds__(PK_THREADS) k_pk_ffma(float* out, float a, flo
   if (x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7 == 1234.5f) out[0] = x0;
 }
 
+// packed FP32 FMA (two lanes of FP32 per instruction, fma.rn.f32x2)
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long x, unsigned long long a,
+                                                    unsigned long long b) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(x), "l"(a), "l"(b));
+  return r;
+}
+
+__global__ void __launch_bounds__(PK_THREADS) k_pk_ffma2(float* out, float a, float b) {
+  const unsigned long long A = ((unsigned long long)__float_as_uint(a) << 32) | __float_as_uint(a);
+  const unsigned long long Bv = ((unsigned long long)__float_as_uint(b) << 32) | __float_as_uint(b);
+  unsigned long long x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    x[q] = ((unsigned long long)__float_as_uint(threadIdx.x + q + 0.5f) << 32) | __float_as_uint(threadIdx.x + q + 0.25f);
+#pragma unroll 4
+  for (int i = 0; i < PK_ITERS; ++i) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = ffma2(x[q], A, Bv);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += __uint_as_float((unsigned)x[q]) + __uint_as_float((unsigned)(x[q] >> 32));
+  if (s == 1234.5f) out[0] = s;
+}
+
 __global__ void __launch_bounds__(PK_THREADS) k_pk_dfma(double* out, double a, double b) {
   double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
 #pragma unroll 4
@@ -85,7 +111,8 @@ __global__ void __launch_bounds__(PK_THREADS) k_pk_mufu(float* out, float a) {
 // out[0] FP32 FMA TFLOP/s (2 flops per FMA), out[1] FP64 FMA TFLOP/s,
 // out[2] double->float conversions (10^12/s), out[3] float->double conversions
 // (10^12/s), out[4] reciprocal square roots (10^12/s), out[5] SM count,
-// out[6] SM clock (MHz) reported by the device.  Synchronises the device.
+// out[6] SM clock (MHz) reported by the device, and with n >= 8 out[7] packed
+// FP32 FMA (fma.rn.f32x2) TFLOP/s.  Synchronises the device.
 extern "C" int mrb_measure_peaks(double* out, int32_t n) {
   using namespace mrb;
   if (!out || n < 7) return MRB_EINVAL;
@@ -118,6 +145,10 @@ extern "C" int mrb_measure_peaks(double* out, int32_t n) {
   out[3] = threads * (PK_ITERS / 8) * 4 / t / 1e12;
   t = timed([&] { k_pk_mufu<<<grid, PK_THREADS>>>((float*)scratch, 1.0f); });
   out[4] = threads * (PK_ITERS / 4) * 4 / t / 1e12;
+  if (n >= 8) {
+    t = timed([&] { k_pk_ffma2<<<grid, PK_THREADS>>>((float*)scratch, 0.999f, 0.001f); });
+    out[7] = threads * PK_ITERS * 8 * 4 / t / 1e12;
+  }
   int dev = 0, clk = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);

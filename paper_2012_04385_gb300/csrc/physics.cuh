@@ -91,8 +91,41 @@ template <class R> __device__ __forceinline__ R linear5(R a, R b, R c, R d, R e)
   return (R(0.1) * q0 + R(0.6) * q1) + R(0.3) * q2;
 }
 
-template <class R> __device__ __forceinline__ R recon5(bool lin, R a, R b, R c, R d, R e) {
-  return lin ? linear5<R>(a, b, c, d, e) : weno5<R>(a, b, c, d, e);
+// TENO5 (Fu, Hu & Adams 2016): the WENO5 stencils kept or dropped by a sharp
+// cutoff C_T = 1e-5 on chi_k = gamma_k / sum gamma, gamma_k = (1 + tau5 /
+// (beta_k + eps))^6, tau5 = |beta0 - beta2|, eps = 1e-40; the kept stencils
+// combined with the linear weights, renormalised.
+template <class R> __device__ __forceinline__ R teno5(R a, R b, R c, R d, R e) {
+  const R eps = R(1e-40), CT = R(1e-5);
+  R t1 = (a - R(2.0) * b) + c, t2 = (a - R(4.0) * b) + R(3.0) * c;
+  R beta0 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+  t1 = (b - R(2.0) * c) + d;
+  t2 = b - d;
+  R beta1 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+  t1 = (c - R(2.0) * d) + e;
+  t2 = (R(3.0) * c - R(4.0) * d) + e;
+  R beta2 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+  const R tau = fabs(beta0 - beta2);
+  R r0 = R(1.0) + tau / (beta0 + eps), r1 = R(1.0) + tau / (beta1 + eps), r2 = R(1.0) + tau / (beta2 + eps);
+  r0 = r0 * r0 * r0;
+  r1 = r1 * r1 * r1;
+  r2 = r2 * r2 * r2;
+  const R g0 = r0 * r0, g1 = r1 * r1, g2 = r2 * r2;
+  const R sum = (g0 + g1) + g2;
+  const R w0 = (g0 / sum < CT) ? R(0.0) : R(0.1);
+  const R w1 = (g1 / sum < CT) ? R(0.0) : R(0.6);
+  const R w2 = (g2 / sum < CT) ? R(0.0) : R(0.3);
+  R q0 = ((R(2.0) * a - R(7.0) * b) + R(11.0) * c) / R(6.0);
+  R q1 = ((-b + R(5.0) * c) + R(2.0) * d) / R(6.0);
+  R q2 = ((R(2.0) * c + R(5.0) * d) - e) / R(6.0);
+  return ((w0 * q0 + w1 * q1) + w2 * q2) / ((w0 + w1) + w2);
+}
+
+// Reconstruction by mode: 0 WENO5-JS, 2 linear, 3 TENO5.
+template <class R> __device__ __forceinline__ R recon5(int mode, R a, R b, R c, R d, R e) {
+  if (mode == 2) return linear5<R>(a, b, c, d, e);
+  if (mode == 3) return teno5<R>(a, b, c, d, e);
+  return weno5<R>(a, b, c, d, e);
 }
 
 // ---------------------------------------------------------------- face flux
@@ -104,7 +137,7 @@ template <class R> __device__ __forceinline__ R recon5(bool lin, R a, R b, R c, 
 // when lam_k of both face cells and the Roe lam_k share a strict sign,
 // otherwise split with alpha = max(|lam_k(U_i)|, |lam_k(U_i+1)|); F = R g.
 template <class R>
-__device__ __forceinline__ void face_flux(const R U6[6][5], int d, R g, R B, bool lin, R Fout[5]) {
+__device__ __forceinline__ void face_flux(const R U6[6][5], int d, R g, R B, int lin, R Fout[5]) {
   const int a0 = rot_axis(d, 0), a1 = rot_axis(d, 1), a2 = rot_axis(d, 2);
   R Ur[6][5], Fr[6][5];
   R unL, cL, unR, cR;

@@ -20,14 +20,12 @@ constexpr int RHS_NSLAB = NB / RHS_TZ;
 constexpr int RHS_FMAX = NB * NB * (RHS_TZ + 1);   // >= 17 * 16 * RHS_TZ
 constexpr int RHS_THREADS = 256;
 
-__device__ __constant__ static const double kRkA[3] = {0.0, 0.75, 1.0 / 3.0};
-__device__ __constant__ static const double kRkB[3] = {1.0, 0.25, 2.0 / 3.0};
 
 // Faces of one direction D of the slab starting at z0: fluxes into Fs, boundary
 // faces into the face buffers, then the flux differences into acc.
 template <class R, int D>
 __device__ __forceinline__ void rhs_dir(const double* __restrict__ u, double* __restrict__ fb, R* Fs, int z0, R g,
-                                        R B, bool lin, double (&acc)[RHS_TZ][NV]) {
+                                        R B, int lin, double (&acc)[RHS_TZ][NV]) {
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   constexpr int nf = (D == 2) ? NB * NB * (RHS_TZ + 1) : (NB + 1) * NB * RHS_TZ;
   constexpr int stride = (D == 0) ? 1 : (D == 1 ? NS : NS * NS);
@@ -99,7 +97,7 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs_rk(Topo t, Phys p, Pool poo
   const double* __restrict__ src = pool.buf[cur];
   double* __restrict__ dst = pool.buf[cur ^ 1];
   const R g = R(p.gamma), B = R(p.B);
-  const bool lin = (p.recon == 2);
+  const int lin = p.recon;   // reconstruction mode: 0 WENO5, 2 linear, 3 TENO5
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int li = w / RHS_NSLAB, z0 = (w % RHS_NSLAB) * RHS_TZ;
@@ -145,7 +143,7 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs_rk(Topo t, Phys p, Pool poo
             un = unb[v * NINT + ii];
           }
           const double tt = us + h * L[v];
-          o[v * NCELL + s] = (stage == 0) ? tt : (kRkA[stage] * un + kRkB[stage] * tt);
+          o[v * NCELL + s] = (stage == 0) ? tt : (kRkA[rk_row(p)][stage] * un + kRkB[rk_row(p)][stage] * tt);
         }
       }
     }

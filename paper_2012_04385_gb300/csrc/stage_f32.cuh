@@ -42,8 +42,6 @@ constexpr size_t SF_SMEM_LEARNED = sizeof(float) * (SF_NREC * SF_REG + NV * SF_N
                                    sizeof(uint32_t) * (FRAG_N + (SF_THREADS / 32) * 32 * 9) +
                                    sizeof(float) * SF_THREADS;
 
-__device__ __constant__ static const double kSfA[3] = {0.0, 0.75, 1.0 / 3.0};
-__device__ __constant__ static const double kSfB[3] = {1.0, 0.25, 2.0 / 3.0};
 
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 
@@ -70,6 +68,39 @@ __device__ __forceinline__ float weno5f(float a, float b, float c, float d, floa
   s1 *= s1;
   s2 *= s2;
   const float w0 = 0.1f * (s1 * s2), w1 = 0.6f * (s0 * s2), w2 = 0.3f * (s0 * s1);
+  const float e0 = fmaf(2.f, da, -5.f * db), e1 = fmaf(-2.f, dc, -db), e2 = fmaf(-4.f, dc, dd);
+  return fmaf(fmaf(w0, e0, fmaf(w1, e1, w2 * e2)), frcp(6.f * (w0 + w1 + w2)), c);
+}
+
+// TENO5 (Fu, Hu & Adams 2016) on the differences, with the smoothness
+// indicators scaled by 12 as in weno5f: stencil k is kept when gamma_k >=
+// C_T sum gamma, gamma_k = (1 + tau5 / (beta_k + eps))^6, tau5 = |beta0 -
+// beta2|, C_T = 1e-5; the comparison uses gamma_k / max gamma (no overflow)
+// and eps = 1e-30 (a normal FP32 number).  Kept stencils take the linear
+// weights, renormalised.
+__device__ __forceinline__ float teno5f(float a, float b, float c, float d, float e) {
+  const float da = a - b, db = b - c, dc = c - d, dd = d - e;
+  const float eps = 1e-30f;
+  float t1 = da - db, t2 = fmaf(-3.f, db, da);
+  const float s0 = fmaf(13.f * t1, t1, 3.f * t2 * t2);
+  t1 = db - dc;
+  t2 = db + dc;
+  const float s1 = fmaf(13.f * t1, t1, 3.f * t2 * t2);
+  t1 = dc - dd;
+  t2 = fmaf(3.f, dc, -dd);
+  const float s2 = fmaf(13.f * t1, t1, 3.f * t2 * t2);
+  const float tau = fabsf(s0 - s2);
+  const float r0 = fmaf(tau, frcp(s0 + eps), 1.f), r1 = fmaf(tau, frcp(s1 + eps), 1.f), r2 = fmaf(tau, frcp(s2 + eps), 1.f);
+  const float inv = frcp(fmaxf(r0, fmaxf(r1, r2)));
+  float g0 = r0 * inv, g1 = r1 * inv, g2 = r2 * inv;
+  g0 = g0 * g0 * g0;
+  g1 = g1 * g1 * g1;
+  g2 = g2 * g2 * g2;
+  g0 *= g0;
+  g1 *= g1;
+  g2 *= g2;
+  const float lim = 1e-5f * (g0 + g1 + g2);
+  const float w0 = (g0 < lim) ? 0.f : 0.1f, w1 = (g1 < lim) ? 0.f : 0.6f, w2 = (g2 < lim) ? 0.f : 0.3f;
   const float e0 = fmaf(2.f, da, -5.f * db), e1 = fmaf(-2.f, dc, -db), e2 = fmaf(-4.f, dc, dd);
   return fmaf(fmaf(w0, e0, fmaf(w1, e1, w2 * e2)), frcp(6.f * (w0 + w1 + w2)), c);
 }
@@ -164,13 +195,14 @@ __device__ __forceinline__ void cell_uf(const float* __restrict__ S, int c, Rot 
   F[4] = un * (E + p);
 }
 
-// Kernel variants: MODE 0 WENO5, 2 linear, 1 learned selector at stage 0
+// Kernel variants: MODE 0 WENO5, 2 linear, 4 TENO5, 1 learned selector at stage 0
 // (WENO5 fluxes; the selector is evaluated on the same faces and its
 // decisions stored), 3 learned selector at stages 1 and 2 (the stored
 // decision of each face picks linear or WENO5 for fields 0, 1, 4).
 template <int MODE>
 __device__ __forceinline__ float rec5(bool lin, float a, float b, float c, float d, float e) {
   if (MODE == 2) return linear5f(a, b, c, d, e);
+  if (MODE == 4) return teno5f(a, b, c, d, e);
   if (MODE != 3) return weno5f(a, b, c, d, e);
   return lin ? linear5f(a, b, c, d, e) : weno5f(a, b, c, d, e);
 }
@@ -707,7 +739,8 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     const double hdx = h * idx_;
     // the stage increment b_s dt / dx (sum of flux differences) is formed in
     // FP32 and accumulated into the FP64 state
-    const float hf = d2f_fast(hdx), bhf = d2f_fast(kSfB[stage] * hdx);
+    const double ka = kRkA[rk_row(p)][stage], kb = kRkB[rk_row(p)][stage];
+    const float hf = d2f_fast(hdx), bhf = d2f_fast(kb * hdx);
 #pragma unroll
     for (int kz = 0; kz < SF_TZ; ++kz) {
       const int k = z0 + kz;
@@ -736,8 +769,8 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
             if (p.has_grav) out = fma(h, S4[v], out);
           } else {
             double inc = f2d_fast(acc[kz][v] * bhf);
-            if (p.has_grav) inc = fma(kSfB[stage] * h, S4[v], inc);
-            out = fma(kSfA[stage], unb[v * NINT + ii], fma(kSfB[stage], us, inc));
+            if (p.has_grav) inc = fma(kb * h, S4[v], inc);
+            out = fma(ka, unb[v * NINT + ii], fma(kb, us, inc));
           }
           o[v * NCELL + s] = out;
         }

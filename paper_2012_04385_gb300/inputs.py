@@ -23,7 +23,7 @@ import numpy as np
 NB = 16
 BC_ZERO_GRADIENT, BC_PERIODIC, BC_SYMMETRY = 0, 1, 2
 FP64, FP32_ACC64 = 0, 1
-RECON_WENO, RECON_LEARNED, RECON_LINEAR = 0, 1, 2
+RECON_WENO, RECON_LEARNED, RECON_LINEAR, RECON_TENO = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
@@ -41,6 +41,7 @@ class RunConfig:
     eps: float = 1e-3
     precision: int = FP64
     recon: int = RECON_WENO
+    rk_stages: int = 3          # 3: TVD-RK3, 2: TVD-RK2
     mlp_tau: float = 0.0
     name: str = "custom"
 

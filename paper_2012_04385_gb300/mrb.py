@@ -40,7 +40,7 @@ class MrbConfig(ctypes.Structure):
         ("bc", ctypes.c_int32 * 6),
         ("precision", ctypes.c_int32),
         ("recon", ctypes.c_int32),
-        ("pad0", ctypes.c_int32),
+        ("rk_stages", ctypes.c_int32),
         ("pad1", ctypes.c_int32),
         ("domain_lo", ctypes.c_double * 3),
         ("dx0", ctypes.c_double),
@@ -122,6 +122,7 @@ def make_config(cfg: RunConfig, stream_ptr: int = 0) -> MrbConfig:
         c.bc[s] = int(cfg.bc[s])
     c.precision = int(cfg.precision)
     c.recon = int(cfg.recon)
+    c.rk_stages = int(getattr(cfg, "rk_stages", 3))
     c.dx0 = float(cfg.dx0)
     c.gamma = float(cfg.gamma)
     c.B = float(cfg.B)
@@ -142,12 +143,12 @@ def _ptr(t) -> int:
 
 
 def measure_peaks() -> dict:
-    """FP32/FP64 FMA, conversion and rsqrt throughputs of the current GPU."""
+    """FP32 (scalar and packed x2) and FP64 FMA, conversion and rsqrt throughputs of the current GPU."""
     out = np.zeros(8)
     rc = lib().mrb_measure_peaks(out.ctypes.data, 8)
     if rc != MRB_OK:
         raise MrbError(rc, "mrb_measure_peaks failed")
-    keys = ["fp32_tflops", "fp64_tflops", "d2f_tps", "f2d_tps", "rsqrt_tps", "sm_count", "sm_clock_mhz"]
+    keys = ["fp32_tflops", "fp64_tflops", "d2f_tps", "f2d_tps", "rsqrt_tps", "sm_count", "sm_clock_mhz", "fp32x2_tflops"]
     return {k: float(v) for k, v in zip(keys, out)}
 
 

@@ -139,7 +139,7 @@ def test_project_bit_exact():
 
 
 # ------------------------------------------------------------------ RHS, stages, CFL
-@pytest.mark.parametrize("recon", [I.RECON_WENO, I.RECON_LINEAR])
+@pytest.mark.parametrize("recon", [I.RECON_WENO, I.RECON_LINEAR, I.RECON_TENO])
 def test_compute_rhs_random_states_with_jumps(recon):
     cfg = I.explosion_config(lmax=3, recon=recon)
     o, g = make_pair(cfg, rnd(4, mild=True), (ALL, SOME, lambda geo: (geo[:, 0] == 2) & (geo[:, 1] % 2 == 0)))
@@ -296,6 +296,75 @@ def test_fp32_bulk_path_error_vs_oracle():
     l1 = np.abs(got[:, 0] - ref[:, 0]).sum() / np.abs(ref[:, 0]).sum()
     print("fp32 bulk L1 density error vs FP64 oracle:", l1)
     assert l1 < 1e-5
+
+
+def test_rk2_bit_exact_sod_and_mr():
+    """TVD-RK2 (rk_stages = 2): 20 Sod steps and 3 MR explosion steps
+    (remeshing, resolution jumps) bit-identical to the oracle; the FP32 bulk
+    path within 1e-5 L1 density on Sod."""
+    cfg = I.sod_config(rk_stages=2)
+    o = oracle.Oracle(cfg)
+    k, geo = o.keys(), o.geometry()
+    o.set_state(k, I.ic_sod(cfg, geo))
+    o.step(20)
+    ref = o.get_state(k)
+    for prec in (I.FP64, I.FP32_ACC64):
+        c = I.sod_config(rk_stages=2, precision=prec)
+        g = mrb.Context(c, 8)
+        g.set_state(k, I.ic_sod(c, geo))
+        g.step(20)
+        got = g.get_state(k).cpu().numpy()
+        if prec == I.FP64:
+            assert np.array_equal(got, ref)
+        else:
+            l1 = np.abs(got[:, 0] - ref[:, 0]).sum() / np.abs(ref[:, 0]).sum()
+            print("RK2 FP32 bulk L1 density vs FP64 oracle:", l1)
+            assert l1 < 1e-5
+    cfg = I.explosion_config(lmax=2, rk_stages=2)
+    o = oracle.Oracle(cfg)
+    g = mrb.Context(cfg, 8 * 80)
+    mrb.init_tree(g, lambda c, geo: I.ic_explosion(c, geo))
+    o.set_state(o.keys(), I.ic_explosion(cfg, o.geometry()))
+    for m in range(1, 3):
+        o.fill_halos()
+        geo = o.geometry()
+        o.remesh((geo[:, 0] == m - 1).astype(np.int8))
+        o.set_state(o.keys(level=m), I.ic_explosion(cfg, o.geometry(level=m)))
+        if m > 1:
+            o.fill_halos()
+            t, _ = o.predict_and_tag(allow_refine=False)
+            o.remesh(t)
+    o.project()
+    o.step(3)
+    g.step(3)
+    assert np.array_equal(o.keys(leaves_only=False), g.keys(leaves_only=False))
+    k = o.keys()
+    assert np.array_equal(g.get_state(k).cpu().numpy(), o.get_state(k))
+
+
+def test_teno5_sod_fp64_bit_exact_and_fp32():
+    """TENO5 on the Sod tube, 20 steps: FP64 GPU bit-identical to the oracle,
+    FP32 bulk within 1e-5 L1 density (the FP32 cutoff decisions may differ
+    from FP64 only at faces whose smoothness ratio sits at the threshold)."""
+    cfg = I.sod_config(recon=I.RECON_TENO)
+    o = oracle.Oracle(cfg)
+    k = o.keys()
+    geo = o.geometry()
+    o.set_state(k, I.ic_sod(cfg, geo))
+    o.step(20)
+    ref = o.get_state(k)
+    for prec in (I.FP64, I.FP32_ACC64):
+        c = I.sod_config(recon=I.RECON_TENO, precision=prec)
+        g = mrb.Context(c, 8)
+        g.set_state(k, I.ic_sod(c, geo))
+        g.step(20)
+        got = g.get_state(k).cpu().numpy()
+        if prec == I.FP64:
+            assert np.array_equal(got, ref)
+        else:
+            l1 = np.abs(got[:, 0] - ref[:, 0]).sum() / np.abs(ref[:, 0]).sum()
+            print("TENO5 FP32 bulk L1 density vs FP64 oracle:", l1)
+            assert l1 < 1e-5
 
 
 @pytest.mark.parametrize("recon", [I.RECON_WENO, I.RECON_LINEAR])

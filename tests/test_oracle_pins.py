@@ -90,6 +90,35 @@ def test_weno_mirror_and_discontinuity():
     assert oracle.linear5(f) < -0.1          # (2 - 13) / 60
 
 
+# ------------------------------------------------------------------ TENO5
+def test_teno5_cutoff_keeps_the_smooth_side_exactly():
+    """At a step, the stencils that cross it are cut off and the one-sided
+    stencil reproduces the smooth side's value exactly (no oscillation)."""
+    assert oracle.teno5([1.0, 1.0, 1.0, 0.0, 0.0]) == 1.0     # only stencil 0 kept: q0 = 1
+    assert oracle.teno5([0.0, 0.0, 1.0, 1.0, 1.0]) == 1.0     # only stencil 2 kept: q2 = 1
+    assert oracle.teno5([2.0, 2.0, 2.0, 7.0, 7.0]) == 2.0
+    # WENO5 only approaches these values
+    assert 0 < abs(oracle.weno5([1.0, 1.0, 1.0, 0.0, 0.0]) - 1.0) < 1e-2
+
+
+def test_teno5_is_the_linear_scheme_on_smooth_data():
+    """On resolved smooth data away from critical points (|f'| >= 1 across
+    the stencil) every stencil is kept, so TENO5 equals the linear 5th-order
+    scheme, which is exact on quartics (unlike WENO5-JS).  Near an extremum
+    the cutoff may drop a stencil; that is TENO's design, not tested here."""
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        c = rng.uniform(-2, 2, 5)
+        c[1] = rng.choice([-1.0, 1.0]) * rng.uniform(2.0, 4.0)    # f'(0) well away from 0
+        h = rng.uniform(0.005, 0.02)
+        edges = (np.arange(6) - 2.5) * h
+        f = cell_avgs_poly(c, edges)
+        exact = poly_at(c, 0.5 * h)
+        scale = max(1.0, np.abs(f).max())
+        assert abs(oracle.teno5(f) - oracle.linear5(f)) <= 1e-14 * scale
+        assert abs(oracle.teno5(f) - exact) <= 1e-13 * scale
+
+
 # ------------------------------------------------------------------ eigensystem
 def _rand_cons(rng, g=1.4):
     rho = rng.uniform(0.1, 3)
@@ -324,15 +353,16 @@ def test_sod_exact_solution_and_transverse_momentum():
     assert errs[1] < errs[0] * 0.8 and errs[2] < errs[1] * 0.8, errs
 
 
-@pytest.mark.parametrize("axis", [0, 1, 2])
-def test_fifth_order_convergence_density_wave(axis):
-    """Smooth advected density wave, exact cell averages; observed L1 order."""
+@pytest.mark.parametrize("axis,recon", [(0, I.RECON_WENO), (1, I.RECON_WENO), (2, I.RECON_WENO), (0, I.RECON_TENO)])
+def test_fifth_order_convergence_density_wave(axis, recon):
+    """Smooth advected density wave, exact cell averages; observed L1 order
+    (WENO5-JS along each axis, TENO5 along x)."""
     errs = []
     t_end = 0.05
     for n in (32, 64, 128):
         base = [1, 1, 1]
         base[axis] = n // 16
-        cfg = I.periodic_config(base=tuple(base))
+        cfg = I.periodic_config(base=tuple(base), recon=recon)
         cfg.dx0 = 1.0 / n
         o = oracle.Oracle(cfg)
         o.set_state(o.keys(), I.ic_density_wave(cfg, o.geometry(), axis=axis))
@@ -344,6 +374,33 @@ def test_fifth_order_convergence_density_wave(axis):
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     print("density wave axis", axis, "L1 errors", errs, "orders", orders)
     assert min(orders) >= 4.7, (errs, orders)
+
+
+def test_rk2_is_second_order_in_time():
+    """TVD-RK2 (the paper's second-order Runge-Kutta): with the grid fixed
+    (64 cells, 5th-order space) and dt halved twice, the error of the
+    advected density wave falls by 4 each time; TVD-RK3 at the largest dt is
+    already far below RK2's error at the smallest."""
+    def run(nst, dt, n=64, t_end=0.2):
+        cfg = I.periodic_config(base=(n // 16, 1, 1), rk_stages=nst)
+        cfg.dx0 = 1.0 / n
+        o = oracle.Oracle(cfg)
+        o.set_state(o.keys(), I.ic_density_wave(cfg, o.geometry(), axis=0))
+        t = 0.0
+        while t < t_end - 1e-14:
+            h = min(dt, t_end - t)
+            for s in range(nst):
+                o.fill_halos()
+                o.rk_stage(s, np.full(1, h))
+                o.project()
+            t += h
+        ex = I.ic_density_wave(cfg, o.geometry(), axis=0, t=t_end)[:, 0]
+        return np.abs(o.get_state()[:, 0] - ex).mean()
+    e2 = [run(2, dt) for dt in (0.008, 0.004, 0.002)]
+    orders = [math.log2(e2[i] / e2[i + 1]) for i in range(2)]
+    print("RK2 errors", e2, "orders", orders)
+    assert all(1.9 <= q <= 2.1 for q in orders)
+    assert run(3, 0.008) < e2[2] / 2
 
 
 def test_tags_uniform_state_collapses_to_level1():
