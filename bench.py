@@ -37,6 +37,12 @@ UNIT = "cell-updates/s"
 WORKLOAD = "explosion_mr_256cubed_l3"
 
 
+# FP32-path variants timed beside the headline: (name, reconstruction, flux scheme)
+VARIANTS = [("weno5_roe", 0, 0), ("linear5_roe", 2, 0), ("teno5_roe", 3, 0), ("wenoao53_roe", 4, 0),
+            ("weno5_llf", 0, 1), ("teno5_llf", 3, 1), ("weno5_hllc", 0, 2), ("teno5_hllc", 3, 2),
+            ("wenoao53_hllc", 4, 2)]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -47,6 +53,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip timing the reconstruction/flux variants of the FP32 path")
     # wrap the headline path's timed steps in cudaProfilerStart/Stop (for
     # ncu --profile-from-start off)
     ap.add_argument("--profile-range", action="store_true")
@@ -323,6 +331,19 @@ def run_gpu(args, rank, world):
     _, pfw = roofline_numbers(0.0)
     achieved_w = (mw["cells"] / 3 / args.steps) * pfw / (mw["stage_ms"] * 1e-3) / 1e12
 
+    # ---- reconstruction / flux variants of the FP32 path on the same workload
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        vsteps = max(3, min(args.steps, 10))
+        for name, rec, fl in VARIANTS:
+            cfg_v = workload_config(args.lmax, I.FP32_ACC64)
+            cfg_v.recon, cfg_v.flux = rec, fl
+            _, mv = timed_path(args, cfg_v, stream, vsteps, 2)
+            variants[name] = {"value": sum_over_ranks(mv["cells"]) / (max_over_ranks(mv["ms"]) * 1e-3),
+                              "ms_per_step": mv["ms"] / vsteps, "stage_kernel_ms": mv["stage_ms"],
+                              "steps": vsteps}
+
     # ---- L1 density errors against the FP64 GPU path (same initial tree, same steps)
     nerr = max(args.fp64_steps, 3)
     l1_l, same_l = l1_after(cfg_l, cfg_64, stream, nerr, params)
@@ -395,6 +416,8 @@ def run_gpu(args, rank, world):
         "l1_density_err_vs_fp64": {"fp32_learned": l1_l, "fp32_weno": l1_w, "steps": nerr,
                                    "same_tree": same_l and same_w},
     }
+    if variants:
+        result["fp32_variants"] = variants
     if e2e:
         result["e2e"] = e2e
     if rank == 0 and not args.no_cpu_baseline:

@@ -70,6 +70,23 @@ extern "C" {
                               /* 1e-5 on gamma_k = (1 + tau5/(beta_k + eps))^6,      */
                               /* tau5 = |beta0 - beta2|; kept ones combined with the */
                               /* linear weights renormalised                         */
+#define MRB_RECON_WENOAO53 4  /* WENO-AO(5,3) everywhere (Balsara, Garain & Shu     */
+                              /* 2016): the quartic over all five cells blended with */
+                              /* the three parabolas, linear weights from gamma_hi = */
+                              /* gamma_lo = 0.85, WENO-Z type nonlinear weights      */
+                              /* gamma_k (1 + (tau/(beta_k + 1e-12))^2)              */
+
+/* flux scheme at a face (Sec. 2.2 lists Roe, LLF and HLLC); the learned
+   selector requires MRB_FLUX_ROE */
+#define MRB_FLUX_ROE 0   /* per characteristic field: Roe upwinding where the two   */
+                         /* face cells' and the Roe eigenvalue share a strict sign, */
+                         /* else the local Lax-Friedrichs split                     */
+#define MRB_FLUX_LLF 1   /* the local Lax-Friedrichs split on every field, alpha_k  */
+                         /* = max |lam_k| of the two cells sharing the face         */
+#define MRB_FLUX_HLLC 2  /* characteristic variables reconstructed to the face from */
+                         /* both sides, mapped back to two states, HLLC (Einfeldt   */
+                         /* outer speeds); an inadmissible state (rho <= 0 or       */
+                         /* p + B <= 0) falls back to the two face cells' states    */
 
 /* refinement tags, one int8 per leaf in leaf order */
 #define MRB_TAG_KEEP 0
@@ -88,7 +105,7 @@ typedef struct mrb_config {
   int32_t recon;                   /* MRB_RECON_*                                          */
   int32_t rk_stages;               /* Runge-Kutta stages per step: 3 (TVD-RK3, also    */
                                    /* when 0) or 2 (TVD-RK2)                           */
-  int32_t pad1;
+  int32_t flux;                    /* MRB_FLUX_*                                           */
   double domain_lo[3];             /* lower corner of the domain                           */
   double dx0;                      /* level-0 cell size (block edge = 16 dx0)              */
   double gamma, B;                 /* stiffened-gas EOS, Eq. (StiffenedGas)                */

@@ -50,7 +50,7 @@ class OrcConfig(ctypes.Structure):
         ("recon", ctypes.c_int32),
         ("n_threads", ctypes.c_int32),
         ("rk_stages", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("flux", ctypes.c_int32),
         ("domain_lo", ctypes.c_double * 3),
         ("dx0", ctypes.c_double),
         ("gamma", ctypes.c_double),
@@ -95,9 +95,11 @@ def lib():
                 "orc_weno5": (dbl, [vp]),
                 "orc_linear5": (dbl, [vp]),
                 "orc_teno5": (dbl, [vp]),
+                "orc_wenoao53": (dbl, [vp]),
+                "orc_hllc": (None, [vp, vp, i32, dbl, dbl, vp]),
                 "orc_flux": (None, [vp, i32, dbl, dbl, vp]),
                 "orc_roe_eigen": (None, [vp, vp, i32, dbl, dbl, vp, vp, vp]),
-                "orc_face_flux": (None, [vp, i32, dbl, dbl, i32, vp]),
+                "orc_face_flux": (None, [vp, i32, dbl, dbl, i32, i32, vp]),
                 "orc_predict_block": (None, [vp, i32, vp]),
                 "orc_face_features": (None, [vp, i32, dbl, dbl, dbl, vp, vp]),
                 "orc_average_block": (None, [vp, vp]),
@@ -126,6 +128,7 @@ def make_config(cfg, n_threads: int = 0) -> OrcConfig:
     c.recon = int(cfg.recon)
     c.n_threads = int(n_threads)
     c.rk_stages = int(getattr(cfg, "rk_stages", 3))
+    c.flux = int(getattr(cfg, "flux", 0))
     c.dx0 = float(cfg.dx0)
     c.gamma = float(cfg.gamma)
     c.B = float(cfg.B)
@@ -267,6 +270,20 @@ def teno5(f) -> float:
     return float(lib().orc_teno5(_p(f)))
 
 
+def wenoao53(f) -> float:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return float(lib().orc_wenoao53(_p(f)))
+
+
+def hllc(UL, UR, d: int, gamma: float = 1.4, B: float = 0.0) -> np.ndarray:
+    """HLLC flux between two lab-frame conserved states along axis d."""
+    UL = np.ascontiguousarray(UL, dtype=np.float64)
+    UR = np.ascontiguousarray(UR, dtype=np.float64)
+    F = np.zeros(5)
+    lib().orc_hllc(_p(UL), _p(UR), d, gamma, B, _p(F))
+    return F
+
+
 def flux(U, d: int, gamma: float = 1.4, B: float = 0.0) -> np.ndarray:
     U = np.ascontiguousarray(U, dtype=np.float64)
     F = np.zeros(5)
@@ -282,11 +299,11 @@ def roe_eigen(UL, UR, d: int = 0, gamma: float = 1.4, B: float = 0.0):
     return Lm, Rm, lam
 
 
-def face_flux(U6, d: int, gamma: float = 1.4, B: float = 0.0, mode: int = 0) -> np.ndarray:
+def face_flux(U6, d: int, gamma: float = 1.4, B: float = 0.0, mode: int = 0, flux: int = 0) -> np.ndarray:
     U6 = np.ascontiguousarray(U6, dtype=np.float64)
     assert U6.shape == (6, 5)
     F = np.zeros(5)
-    lib().orc_face_flux(_p(U6), d, gamma, B, mode, _p(F))
+    lib().orc_face_flux(_p(U6), d, gamma, B, mode, flux, _p(F))
     return F
 
 

@@ -50,7 +50,8 @@ constexpr int NSHADOW = 7;                   // shadow levels of the 64-bit id (
 constexpr uint64_t MASK56 = (1ull << 56) - 1;
 
 constexpr int BC_ZERO_GRADIENT = 0, BC_PERIODIC = 1, BC_SYMMETRY = 2;
-constexpr int RECON_WENO = 0, RECON_LINEAR = 2, RECON_TENO = 3;
+constexpr int RECON_WENO = 0, RECON_LINEAR = 2, RECON_TENO = 3, RECON_WENOAO = 4;
+constexpr int FLUX_ROE = 0, FLUX_LLF = 1, FLUX_HLLC = 2;
 constexpr int8_t TAG_KEEP = 0, TAG_REFINE = 1, TAG_COARSEN = -1;
 
 inline int sidx(int i, int j, int k) { return ((k + HW) * NS + (j + HW)) * NS + (i + HW); }
@@ -68,10 +69,10 @@ struct orc_config {
   int32_t base_blocks[3];
   int32_t lmax[256];
   int32_t bc[6];          // x-, x+, y-, y+, z-, z+
-  int32_t recon;          // 0 = WENO5-JS, 2 = linear 5th-order upwind everywhere, 3 = TENO5
+  int32_t recon;          // 0 = WENO5-JS, 2 = linear 5th-order upwind everywhere, 3 = TENO5, 4 = WENO-AO(5,3)
   int32_t n_threads;      // 0 = OpenMP default
   int32_t rk_stages;      // 3 = TVD-RK3 (default when 0), 2 = TVD-RK2
-  int32_t pad;
+  int32_t flux;           // 0 = Roe with per-field LLF fallback, 1 = LLF on every field, 2 = HLLC
   double domain_lo[3];
   double dx0;             // level-0 cell size
   double gamma, B, cfl;
@@ -331,20 +332,119 @@ double teno5(double a, double b, double c, double d, double e) {
   return ((w0 * q0 + w1 * q1) + w2 * q2) / ((w0 + w1) + w2);
 }
 
+// WENO-AO(5,3) (Balsara, Garain & Shu 2016, one of the stencils Sec. 2.2
+// lists): the quartic through all five cell averages is blended with the three
+// parabolas of WENO5.  Smoothness of the parabolas as in WENO5-JS; of the
+// quartic, the sum over derivative orders 1..4 of the integral of the squared
+// derivative over the middle cell, written with the Legendre coefficients of
+// the quartic on that cell.  Linear weights from gamma_hi = gamma_lo = 0.85:
+// quartic gamma_hi, middle parabola (1 - gamma_hi) gamma_lo, outer parabolas
+// (1 - gamma_hi)(1 - gamma_lo)/2 each.  Nonlinear weights of WENO-Z type,
+// gamma_k (1 + (tau / (beta_k + eps))^2), tau the mean of |beta_5 - beta_k|,
+// eps = 1e-12, normalised.  Value at the right face of the middle cell:
+// (w_5 / gamma_5)(q_5 - sum gamma_k q_k) + sum w_k q_k over the parabolas k.
+double wenoao53(double a, double b, double c, double d, double e) {
+  const double eps = 1e-12;
+  const double ghi = 0.85, glo = 0.85;
+  double t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;
+  double beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  t1 = (b - 2.0 * c) + d;
+  t2 = b - d;
+  double beta1 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  t1 = (c - 2.0 * d) + e;
+  t2 = (3.0 * c - 4.0 * d) + e;
+  double beta2 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  // Legendre coefficients of the quartic on the middle cell (a..e = u_{i-2..i+2})
+  double u1 = (((11.0 * a - 82.0 * b) + 82.0 * d) - 11.0 * e) / 120.0;
+  double u2 = ((((-3.0 * a + 40.0 * b) - 74.0 * c) + 40.0 * d) - 3.0 * e) / 56.0;
+  double u3 = (((-a + 2.0 * b) - 2.0 * d) + e) / 12.0;
+  double u4 = ((((a - 4.0 * b) + 6.0 * c) - 4.0 * d) + e) / 24.0;
+  double s1 = u1 + u3 / 10.0, s2 = u2 + (123.0 / 455.0) * u4;
+  double beta5 = (((s1 * s1 + (13.0 / 3.0) * (s2 * s2)) + (781.0 / 20.0) * (u3 * u3)) + (1421461.0 / 2275.0) * (u4 * u4));
+  const double g5 = ghi, g1 = (1.0 - ghi) * glo, g0 = 0.5 * ((1.0 - ghi) * (1.0 - glo)), g2 = g0;
+  double tau = ((std::fabs(beta5 - beta0) + std::fabs(beta5 - beta1)) + std::fabs(beta5 - beta2)) / 3.0;
+  double r5 = tau / (beta5 + eps), r0 = tau / (beta0 + eps), r1 = tau / (beta1 + eps), r2 = tau / (beta2 + eps);
+  double w5 = g5 * (1.0 + r5 * r5), w0 = g0 * (1.0 + r0 * r0), w1 = g1 * (1.0 + r1 * r1), w2 = g2 * (1.0 + r2 * r2);
+  double sum = ((w5 + w0) + w1) + w2;
+  w5 = w5 / sum;
+  w0 = w0 / sum;
+  w1 = w1 / sum;
+  w2 = w2 / sum;
+  double q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
+  double q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
+  double q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
+  double q5 = ((((2.0 * a - 13.0 * b) + 47.0 * c) + 27.0 * d) - 3.0 * e) / 60.0;
+  return (w5 / g5) * (((q5 - g0 * q0) - g1 * q1) - g2 * q2) + ((w0 * q0 + w1 * q1) + w2 * q2);
+}
+
 inline double recon5(int mode, double a, double b, double c, double d, double e) {
   if (mode == RECON_LINEAR) return linear5(a, b, c, d, e);
   if (mode == RECON_TENO) return teno5(a, b, c, d, e);
+  if (mode == RECON_WENOAO) return wenoao53(a, b, c, d, e);
   return weno5(a, b, c, d, e);
+}
+
+// HLLC approximate Riemann solver (Toro, Spruce & Speares 1994; Sec. 2.2 lists
+// it beside Roe and LLF) on rotated-frame states UL, UR (normal momentum in
+// slot 1).  Outer signal speeds after Einfeldt: S_L = min(u_L - c_L, u~ - c~),
+// S_R = max(u_R + c_R, u~ + c~), ~ the Roe average of UL and UR.  Contact speed
+// S* from the momentum balance over both outer waves.  The flux is F_L, F*_L,
+// F*_R or F_R by where x/t = 0 falls among S_L <= S* <= S_R, with
+// F*_K = F_K + S_K (U*_K - U_K) and U*_K = rho_K (S_K - u_K) / (S_K - S*) times
+// (1, S*, v_K, w_K, E_K / rho_K + (S* - u_K)(S* + p_K / (rho_K (S_K - u_K)))).
+void hllc_rot(const double UL[5], const double UR[5], double g, double B, double F[5]) {
+  Prim a = prim_of(UL, g, B), b = prim_of(UR, g, B);
+  double FL[5], FR[5];
+  flux_rot(UL, a, 0, FL);
+  flux_rot(UR, b, 0, FR);
+  Eigen e = roe_eigen(a, b, 0, g);
+  double uL = a.vel[0], uR = b.vel[0];
+  double SL = std::min(uL - a.c, e.lam[0]);
+  double SR = std::max(uR + b.c, e.lam[4]);
+  double mL = a.rho * (SL - uL), mR = b.rho * (SR - uR);
+  double Ss = (((b.p - a.p) + uL * mL) - uR * mR) / (mL - mR);
+  if (SL >= 0.0) {
+    for (int j = 0; j < 5; ++j) F[j] = FL[j];
+  } else if (SR <= 0.0) {
+    for (int j = 0; j < 5; ++j) F[j] = FR[j];
+  } else {
+    const bool left = Ss >= 0.0;
+    const Prim& q = left ? a : b;
+    const double* U = left ? UL : UR;
+    const double* FK = left ? FL : FR;
+    double SK = left ? SL : SR, mK = left ? mL : mR;
+    double fac = mK / (SK - Ss);
+    double Us[5];
+    Us[0] = fac;
+    Us[1] = fac * Ss;
+    Us[2] = fac * q.vel[1];
+    Us[3] = fac * q.vel[2];
+    Us[4] = fac * (U[4] / q.rho + (Ss - q.vel[0]) * (Ss + q.p / mK));
+    for (int j = 0; j < 5; ++j) F[j] = FK[j] + SK * (Us[j] - U[j]);
+  }
+}
+
+// Reconstructed face state admissible for HLLC: positive density and p + B > 0.
+bool admissible(const double U[5], double g, double B) {
+  if (!(U[0] > 0.0)) return false;
+  double q2 = ((U[1] * U[1] + U[2] * U[2]) + U[3] * U[3]) / U[0];
+  double p = (g - 1.0) * (U[4] - 0.5 * q2) - g * B;
+  return p + B > 0.0;
 }
 
 // Numerical flux at the face between cells 2 and 3 of a six-cell stencil
 // (cells i-2 .. i+3), along direction d, returned in the lab frame.
 // Characteristic-wise reconstruction: v = L U, g = L F(U) with the Roe
-// matrices of the face; per field k, Roe upwinding when the cell eigenvalues on
-// both sides and the Roe eigenvalue share a strict sign, else the local
-// Lax-Friedrichs split with alpha = max(|lam_k(U_i)|, |lam_k(U_{i+1})|) from
-// the two cells sharing the face (Sec. 2.2); F = R g_hat.
-void face_flux(const double U6[6][5], int d, double g, double B, int mode, double Fout[5]) {
+// matrices of the face.  flux = FLUX_ROE: per field k, Roe upwinding when the
+// cell eigenvalues on both sides and the Roe eigenvalue share a strict sign,
+// else the local Lax-Friedrichs split with alpha = max(|lam_k(U_i)|,
+// |lam_k(U_{i+1})|) from the two cells sharing the face (Sec. 2.2); F = R g_hat.
+// flux = FLUX_LLF: that split on every field.  flux = FLUX_HLLC: the
+// characteristic variables are reconstructed to the face from the left
+// (cells i-2..i+2) and from the right (cells i+3..i-1), mapped back with R to
+// the states U_L, U_R, and HLLC gives the flux; where either state is not
+// admissible the face falls back to the cell states U_i, U_{i+1}.
+void face_flux(const double U6[6][5], int d, double g, double B, int mode, int flux, double Fout[5]) {
   Prim q[6];
   double Ur[6][5], Fr[6][5];
   for (int m = 0; m < 6; ++m) {
@@ -365,6 +465,31 @@ void face_flux(const double U6[6][5], int d, double g, double B, int mode, doubl
       v[k][m] = sv;
       gc[k][m] = sg;
     }
+  if (flux == FLUX_HLLC) {
+    double vL[5], vR[5], UL[5], UR[5], Fh[5];
+    for (int k = 0; k < 5; ++k) {
+      vL[k] = recon5(mode, v[k][0], v[k][1], v[k][2], v[k][3], v[k][4]);
+      vR[k] = recon5(mode, v[k][5], v[k][4], v[k][3], v[k][2], v[k][1]);
+    }
+    for (int j = 0; j < 5; ++j) {
+      double sl = e.Rm[j][0] * vL[0], sr = e.Rm[j][0] * vR[0];
+      for (int k = 1; k < 5; ++k) {
+        sl = sl + e.Rm[j][k] * vL[k];
+        sr = sr + e.Rm[j][k] * vR[k];
+      }
+      UL[j] = sl;
+      UR[j] = sr;
+    }
+    if (!admissible(UL, g, B) || !admissible(UR, g, B)) {
+      for (int j = 0; j < 5; ++j) {
+        UL[j] = Ur[2][j];
+        UR[j] = Ur[3][j];
+      }
+    }
+    hllc_rot(UL, UR, g, B, Fh);
+    unrotate(Fh, d, Fout);
+    return;
+  }
   double unL = q[2].vel[d], unR = q[3].vel[d];
   double lamL[5] = {unL - q[2].c, unL, unL, unL, unL + q[2].c};
   double lamR[5] = {unR - q[3].c, unR, unR, unR, unR + q[3].c};
@@ -372,9 +497,9 @@ void face_flux(const double U6[6][5], int d, double g, double B, int mode, doubl
   for (int k = 0; k < 5; ++k) {
     double lL = lamL[k], lR = lamR[k], lt = e.lam[k];
     const double* G = gc[k];
-    if (lL > 0.0 && lR > 0.0 && lt > 0.0) {
+    if (flux == FLUX_ROE && lL > 0.0 && lR > 0.0 && lt > 0.0) {
       gh[k] = recon5(mode, G[0], G[1], G[2], G[3], G[4]);
-    } else if (lL < 0.0 && lR < 0.0 && lt < 0.0) {
+    } else if (flux == FLUX_ROE && lL < 0.0 && lR < 0.0 && lt < 0.0) {
       gh[k] = recon5(mode, G[5], G[4], G[3], G[2], G[1]);
     } else {
       double alpha = std::max(std::fabs(lL), std::fabs(lR));
@@ -739,7 +864,7 @@ void leaf_rhs(const Ctx& C, Node& n) {
             for (int v = 0; v < NV; ++v) U6[m][v] = n.u[(size_t)v * NCELL + sidx(c[0], c[1], c[2])];
           }
           double Fo[5];
-          face_flux(U6, d, g, B, C.c.recon, Fo);
+          face_flux(U6, d, g, B, C.c.recon, C.c.flux, Fo);
           for (int v = 0; v < NV; ++v) F[fidx(d, v, f, a, b)] = Fo[v];
         }
   }
@@ -1304,6 +1429,7 @@ int32_t orc_key_level(uint64_t key) { return key_level(key); }
 double orc_weno5(const double* f) { return weno5(f[0], f[1], f[2], f[3], f[4]); }
 double orc_linear5(const double* f) { return linear5(f[0], f[1], f[2], f[3], f[4]); }
 double orc_teno5(const double* f) { return teno5(f[0], f[1], f[2], f[3], f[4]); }
+double orc_wenoao53(const double* f) { return wenoao53(f[0], f[1], f[2], f[3], f[4]); }
 
 void orc_flux(const double* U, int32_t d, double g, double B, double* F) {
   Prim q = prim_of(U, g, B);
@@ -1328,11 +1454,20 @@ void orc_roe_eigen(const double* UL, const double* UR, int32_t d, double g, doub
   }
 }
 
-void orc_face_flux(const double* U6, int32_t d, double g, double B, int32_t mode, double* F) {
+void orc_face_flux(const double* U6, int32_t d, double g, double B, int32_t mode, int32_t flux, double* F) {
   double U[6][5];
   for (int m = 0; m < 6; ++m)
     for (int v = 0; v < 5; ++v) U[m][v] = U6[m * 5 + v];
-  face_flux(U, d, g, B, mode, F);
+  face_flux(U, d, g, B, mode, flux, F);
+}
+
+// HLLC flux between two lab-frame states along d (lab frame out).
+void orc_hllc(const double* UL, const double* UR, int32_t d, double g, double B, double* F) {
+  double a[5], b[5], Fr[5];
+  rotate(UL, d, a);
+  rotate(UR, d, b);
+  hllc_rot(a, b, g, B, Fr);
+  unrotate(Fr, d, F);
 }
 
 // Selector features [15] and label of one face (six lab-frame cells [6][5]).

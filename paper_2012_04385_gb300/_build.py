@@ -25,6 +25,8 @@ UNITS = {
     "ctx.cu": [],
     "kern_f64.cu": ["-fmad=false"],
     "kern_f32.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "kern_f32_llf.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "kern_f32_hllc.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "noalloc.cu": ["-fmad=false"],
     "peaks.cu": ["-fmad=true"],
     "learned.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],

@@ -472,7 +472,9 @@ int check_config(const mrb_config* cfg) {
   for (int s = 0; s < 6; ++s)
     if (cfg->bc[s] < 0 || cfg->bc[s] > 2) return MRB_EINVAL;
   if (cfg->precision != MRB_FP64 && cfg->precision != MRB_FP32_ACC64) return MRB_EINVAL;
-  if (cfg->recon < 0 || cfg->recon > 3) return MRB_EINVAL;
+  if (cfg->recon < 0 || cfg->recon > 4) return MRB_EINVAL;
+  if (cfg->flux < 0 || cfg->flux > 2) return MRB_EINVAL;
+  if (cfg->recon == MRB_RECON_LEARNED && cfg->flux != MRB_FLUX_ROE) return MRB_EINVAL;
   if (cfg->rk_stages != 0 && cfg->rk_stages != 2 && cfg->rk_stages != 3) return MRB_EINVAL;
   if (!(cfg->dx0 > 0) || !(cfg->gamma > 1.0) || !(cfg->cfl > 0)) return MRB_EINVAL;
   return MRB_OK;
@@ -542,6 +544,7 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     p.recon = cfg->recon;
     p.precision = cfg->precision;
     p.rk = (cfg->rk_stages == 2) ? 2 : 3;
+    p.flux = cfg->flux;
     p.mlp = (const float*)cfg->mlp_weights;
     p.mlp_tau = (float)cfg->mlp_tau;
     c->max_lmax = 0;

@@ -7,25 +7,13 @@
 
 namespace mrb {
 
-template <int MODE>
-static void launch_stage_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
-                             double* rhs_out, cudaStream_t st) {
-  const size_t smem = (MODE == 1) ? SF_SMEM_LEARNED : SF_SMEM;
-  static int grid = 0;
-  if (grid == 0) {
-    cudaFuncSetAttribute(k_stage_f32<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_f32<MODE>, SF_THREADS, smem);
-    grid = sm_count() * (per_sm < 1 ? 1 : per_sm);
-  }
-  k_stage_f32<MODE><<<grid, SF_THREADS, smem, st>>>(t, p, pool, cur, stage, dt, rhs_out);
-  ++g_kernel_launches;
-}
-
 void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
                        double* rhs_out, cudaStream_t st) {
-  if (p.recon == 2) launch_stage_f32<2>(t, p, pool, cur, stage, dt, rhs_out, st);
+  if (p.flux == 1) launch_rhs_rk_f32_llf(t, p, pool, cur, stage, dt, rhs_out, st);
+  else if (p.flux == 2) launch_rhs_rk_f32_hllc(t, p, pool, cur, stage, dt, rhs_out, st);
+  else if (p.recon == 2) launch_stage_f32<2>(t, p, pool, cur, stage, dt, rhs_out, st);
   else if (p.recon == 3) launch_stage_f32<4>(t, p, pool, cur, stage, dt, rhs_out, st);
+  else if (p.recon == 4) launch_stage_f32<5>(t, p, pool, cur, stage, dt, rhs_out, st);
   else if (p.recon == 1 && p.mlp) {
     // the selector is evaluated on the stage-0 state; stages 1 and 2 use its decisions
     if (stage == 0 || rhs_out) launch_stage_f32<1>(t, p, pool, cur, stage, dt, rhs_out, st);

@@ -51,6 +51,7 @@ struct Phys {
   int has_grav;
   int precision;           // 0 FP64, 1 FP32 bulk (MRB_FP64 / MRB_FP32_ACC64)
   int rk;                  // Runge-Kutta stages per step: 3 (TVD-RK3) or 2 (TVD-RK2)
+  int flux;                // MRB_FLUX_*: Roe with LLF fallback, LLF, HLLC
   float mlp_tau;           // learned selector: linear reconstruction when logit < mlp_tau
   const float* mlp;        // learned selector parameters (device, FP32), or null
   unsigned long long* lin_count;   // [0] faces sent to linear, [1] faces evaluated
@@ -89,6 +90,12 @@ void launch_rhs_rk_f64(const Topo& t, const Phys& p, const Pool& pool, int cur, 
                        double* rhs_out, cudaStream_t st);
 void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
                        double* rhs_out, cudaStream_t st);
+// FP32 stage kernels of the flux variants (separate translation units):
+// LLF on every field, and HLLC, each with every non-learned reconstruction.
+void launch_rhs_rk_f32_llf(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
+                           double* rhs_out, cudaStream_t st);
+void launch_rhs_rk_f32_hllc(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
+                            double* rhs_out, cudaStream_t st);
 void launch_face_avg_level(const Topo& t, const Pool& pool, int level, cudaStream_t st);
 void launch_jump(const Topo& t, const Phys& p, const Pool& pool, int target, int stage, const double* dt,
                  double* rhs_out, cudaStream_t st);

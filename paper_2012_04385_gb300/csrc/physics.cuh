@@ -121,11 +121,119 @@ template <class R> __device__ __forceinline__ R teno5(R a, R b, R c, R d, R e) {
   return ((w0 * q0 + w1 * q1) + w2 * q2) / ((w0 + w1) + w2);
 }
 
-// Reconstruction by mode: 0 WENO5-JS, 2 linear, 3 TENO5.
+// WENO-AO(5,3) (Balsara, Garain & Shu 2016): the quartic through the five
+// cell averages blended with WENO5's three parabolas.  Linear weights from
+// gamma_hi = gamma_lo = 0.85 (quartic gamma_hi, middle parabola (1 - gamma_hi)
+// gamma_lo, outer parabolas half the rest each); the quartic's smoothness from
+// its Legendre coefficients on the middle cell; WENO-Z type weights gamma_k (1
+// + (tau / (beta_k + eps))^2), tau the mean of |beta_5 - beta_k|, eps = 1e-12.
+template <class R> __device__ __forceinline__ R wenoao53(R a, R b, R c, R d, R e) {
+  const R eps = R(1e-12);
+  const R ghi = R(0.85), glo = R(0.85);
+  R t1 = (a - R(2.0) * b) + c, t2 = (a - R(4.0) * b) + R(3.0) * c;
+  R beta0 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+  t1 = (b - R(2.0) * c) + d;
+  t2 = b - d;
+  R beta1 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+  t1 = (c - R(2.0) * d) + e;
+  t2 = (R(3.0) * c - R(4.0) * d) + e;
+  R beta2 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+  R u1 = (((R(11.0) * a - R(82.0) * b) + R(82.0) * d) - R(11.0) * e) / R(120.0);
+  R u2 = ((((R(-3.0) * a + R(40.0) * b) - R(74.0) * c) + R(40.0) * d) - R(3.0) * e) / R(56.0);
+  R u3 = (((-a + R(2.0) * b) - R(2.0) * d) + e) / R(12.0);
+  R u4 = ((((a - R(4.0) * b) + R(6.0) * c) - R(4.0) * d) + e) / R(24.0);
+  R s1 = u1 + u3 / R(10.0), s2 = u2 + R(123.0 / 455.0) * u4;
+  R beta5 = (((s1 * s1 + R(13.0 / 3.0) * (s2 * s2)) + R(781.0 / 20.0) * (u3 * u3)) + R(1421461.0 / 2275.0) * (u4 * u4));
+  const R g5 = ghi, g1 = (R(1.0) - ghi) * glo, g0 = R(0.5) * ((R(1.0) - ghi) * (R(1.0) - glo)), g2 = g0;
+  R tau = ((fabs(beta5 - beta0) + fabs(beta5 - beta1)) + fabs(beta5 - beta2)) / R(3.0);
+  R r5 = tau / (beta5 + eps), r0 = tau / (beta0 + eps), r1 = tau / (beta1 + eps), r2 = tau / (beta2 + eps);
+  R w5 = g5 * (R(1.0) + r5 * r5), w0 = g0 * (R(1.0) + r0 * r0), w1 = g1 * (R(1.0) + r1 * r1), w2 = g2 * (R(1.0) + r2 * r2);
+  R sum = ((w5 + w0) + w1) + w2;
+  w5 = w5 / sum;
+  w0 = w0 / sum;
+  w1 = w1 / sum;
+  w2 = w2 / sum;
+  R q0 = ((R(2.0) * a - R(7.0) * b) + R(11.0) * c) / R(6.0);
+  R q1 = ((-b + R(5.0) * c) + R(2.0) * d) / R(6.0);
+  R q2 = ((R(2.0) * c + R(5.0) * d) - e) / R(6.0);
+  R q5 = ((((R(2.0) * a - R(13.0) * b) + R(47.0) * c) + R(27.0) * d) - R(3.0) * e) / R(60.0);
+  return (w5 / g5) * (((q5 - g0 * q0) - g1 * q1) - g2 * q2) + ((w0 * q0 + w1 * q1) + w2 * q2);
+}
+
+// Reconstruction by mode: 0 WENO5-JS, 2 linear, 3 TENO5, 4 WENO-AO(5,3).
 template <class R> __device__ __forceinline__ R recon5(int mode, R a, R b, R c, R d, R e) {
   if (mode == 2) return linear5<R>(a, b, c, d, e);
   if (mode == 3) return teno5<R>(a, b, c, d, e);
+  if (mode == 4) return wenoao53<R>(a, b, c, d, e);
   return weno5<R>(a, b, c, d, e);
+}
+
+// Flux schemes: Roe with the per-field LLF fallback, LLF on every field, HLLC.
+constexpr int FLUX_ROE = 0, FLUX_LLF = 1, FLUX_HLLC = 2;
+
+// HLLC (Toro, Spruce & Speares 1994) between rotated-frame states UL, UR
+// (normal momentum in slot 1): Einfeldt's outer speeds S_L = min(u_L - c_L,
+// u~ - c~), S_R = max(u_R + c_R, u~ + c~) from the Roe average of UL and UR;
+// contact speed S* from the momentum balance over the outer waves; flux F_L,
+// F*_L, F*_R or F_R by the position of x/t = 0, F*_K = F_K + S_K (U*_K - U_K).
+template <class R> __device__ __forceinline__ void hllc_rot(const R UL[5], const R UR[5], R g, R B, R F[5]) {
+  const Prim<R> a = prim_of<R>(UL, g, B), b = prim_of<R>(UR, g, B);
+  R FL[5], FR[5];
+  FL[0] = UL[1];
+  FL[1] = UL[1] * a.vel[0] + a.p;
+  FL[2] = UL[1] * a.vel[1];
+  FL[3] = UL[1] * a.vel[2];
+  FL[4] = a.vel[0] * (UL[4] + a.p);
+  FR[0] = UR[1];
+  FR[1] = UR[1] * b.vel[0] + b.p;
+  FR[2] = UR[1] * b.vel[1];
+  FR[3] = UR[1] * b.vel[2];
+  FR[4] = b.vel[0] * (UR[4] + b.p);
+  const R sL = rsqrt_<R>(a.rho), sR = rsqrt_<R>(b.rho);
+  const R den = sL + sR;
+  const R un = (sL * a.vel[0] + sR * b.vel[0]) / den;
+  const R ut1 = (sL * a.vel[1] + sR * b.vel[1]) / den;
+  const R ut2 = (sL * a.vel[2] + sR * b.vel[2]) / den;
+  const R HL = (a.E + a.p) / a.rho, HR = (b.E + b.p) / b.rho;
+  const R H = (sL * HL + sR * HR) / den;
+  const R q2 = (un * un + ut1 * ut1) + ut2 * ut2;
+  const R c = rsqrt_<R>((g - R(1.0)) * (H - R(0.5) * q2));
+  const R uL = a.vel[0], uR = b.vel[0];
+  const R l0 = un - c, l4 = un + c, xL = uL - a.c, xR = uR + b.c;
+  const R SL = (l0 < xL) ? l0 : xL;
+  const R SR = (xR < l4) ? l4 : xR;
+  const R mL = a.rho * (SL - uL), mR = b.rho * (SR - uR);
+  const R Ss = (((b.p - a.p) + uL * mL) - uR * mR) / (mL - mR);
+  if (SL >= R(0.0)) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) F[j] = FL[j];
+  } else if (SR <= R(0.0)) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) F[j] = FR[j];
+  } else {
+    const bool left = Ss >= R(0.0);
+    const Prim<R>& q = left ? a : b;
+    const R* U = left ? UL : UR;
+    const R* FK = left ? FL : FR;
+    const R SK = left ? SL : SR, mK = left ? mL : mR;
+    const R fac = mK / (SK - Ss);
+    R Us[5];
+    Us[0] = fac;
+    Us[1] = fac * Ss;
+    Us[2] = fac * q.vel[1];
+    Us[3] = fac * q.vel[2];
+    Us[4] = fac * (U[4] / q.rho + (Ss - q.vel[0]) * (Ss + q.p / mK));
+#pragma unroll
+    for (int j = 0; j < 5; ++j) F[j] = FK[j] + SK * (Us[j] - U[j]);
+  }
+}
+
+// A reconstructed face state usable by HLLC: rho > 0 and p + B > 0.
+template <class R> __device__ __forceinline__ bool admissible(const R U[5], R g, R B) {
+  if (!(U[0] > R(0.0))) return false;
+  const R q2 = ((U[1] * U[1] + U[2] * U[2]) + U[3] * U[3]) / U[0];
+  const R p = (g - R(1.0)) * (U[4] - R(0.5) * q2) - g * B;
+  return p + B > R(0.0);
 }
 
 // ---------------------------------------------------------------- face flux
@@ -135,9 +243,13 @@ template <class R> __device__ __forceinline__ R recon5(int mode, R a, R b, R c, 
 // and the eigensystem of the face project the six cells to characteristic
 // variables v = L U and fluxes g = L F(U); per field k the flux is upwinded
 // when lam_k of both face cells and the Roe lam_k share a strict sign,
-// otherwise split with alpha = max(|lam_k(U_i)|, |lam_k(U_i+1)|); F = R g.
+// otherwise split with alpha = max(|lam_k(U_i)|, |lam_k(U_i+1)|); F = R g
+// (flux = FLUX_ROE).  FLUX_LLF splits every field.  FLUX_HLLC reconstructs v
+// to the face from both sides, maps the two states back with R and applies
+// HLLC; an inadmissible state sends the face back to the cell states U_i,
+// U_i+1.
 template <class R>
-__device__ __forceinline__ void face_flux(const R U6[6][5], int d, R g, R B, int lin, R Fout[5]) {
+__device__ __forceinline__ void face_flux(const R U6[6][5], int d, R g, R B, int lin, int flux, R Fout[5]) {
   const int a0 = rot_axis(d, 0), a1 = rot_axis(d, 1), a2 = rot_axis(d, 2);
   R Ur[6][5], Fr[6][5];
   R unL, cL, unR, cR;
@@ -177,7 +289,7 @@ __device__ __forceinline__ void face_flux(const R U6[6][5], int d, R g, R B, int
   R ic = R(1.0) / c;
   R b1 = (g - R(1.0)) / c2;
   R b2 = R(0.5) * b1 * q2;
-  R Fh[5];
+  R Fh[5], UL[5], UR[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     R l[5], r[5];
@@ -212,14 +324,24 @@ __device__ __forceinline__ void face_flux(const R U6[6][5], int d, R g, R B, int
       v[m] = sv;
       G[m] = sg;
     }
+    if (flux == FLUX_HLLC) {
+      const R vl = recon5<R>(lin, v[0], v[1], v[2], v[3], v[4]);
+      const R vr = recon5<R>(lin, v[5], v[4], v[3], v[2], v[1]);
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        UL[j] = (k == 0) ? r[j] * vl : UL[j] + r[j] * vl;
+        UR[j] = (k == 0) ? r[j] * vr : UR[j] + r[j] * vr;
+      }
+      continue;
+    }
     R lL, lR, lt;
     if (k == 0) { lL = unL - cL; lR = unR - cR; lt = un - c; }
     else if (k == 4) { lL = unL + cL; lR = unR + cR; lt = un + c; }
     else { lL = unL; lR = unR; lt = un; }
     R gh;
-    if (lL > R(0.0) && lR > R(0.0) && lt > R(0.0)) {
+    if (flux == FLUX_ROE && lL > R(0.0) && lR > R(0.0) && lt > R(0.0)) {
       gh = recon5<R>(lin, G[0], G[1], G[2], G[3], G[4]);
-    } else if (lL < R(0.0) && lR < R(0.0) && lt < R(0.0)) {
+    } else if (flux == FLUX_ROE && lL < R(0.0) && lR < R(0.0) && lt < R(0.0)) {
       gh = recon5<R>(lin, G[5], G[4], G[3], G[2], G[1]);
     } else {
       R alpha = rmax<R>(rabs<R>(lL), rabs<R>(lR));
@@ -233,6 +355,16 @@ __device__ __forceinline__ void face_flux(const R U6[6][5], int d, R g, R B, int
     }
 #pragma unroll
     for (int j = 0; j < 5; ++j) Fh[j] = (k == 0) ? r[j] * gh : Fh[j] + r[j] * gh;
+  }
+  if (flux == FLUX_HLLC) {
+    if (!admissible<R>(UL, g, B) || !admissible<R>(UR, g, B)) {
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        UL[j] = Ur[2][j];
+        UR[j] = Ur[3][j];
+      }
+    }
+    hllc_rot<R>(UL, UR, g, B, Fh);
   }
   Fout[0] = Fh[0];
   Fout[1 + a0] = Fh[1];

@@ -105,6 +105,48 @@ __device__ __forceinline__ float teno5f(float a, float b, float c, float d, floa
   return fmaf(fmaf(w0, e0, fmaf(w1, e1, w2 * e2)), frcp(6.f * (w0 + w1 + w2)), c);
 }
 
+// WENO-AO(5,3) (Balsara, Garain & Shu 2016) on the differences, smoothness
+// indicators (the parabolas' and the quartic's) scaled by 12 with eps' = 12
+// eps, eps = 1e-12; linear weights from gamma_hi = gamma_lo = 0.85; weights
+// gamma_k (1 + r_k^2), r_k = tau / (beta_k + eps), evaluated as gamma_k (1/M^2
+// + (r_k/M)^2) with M = max(1, max r_k) (no overflow; same normalised weights).
+// The value is c + [(w5/g5)(e5/60 - sum g_k e_k/6) + sum w_k e_k/6] / sum w,
+// e_k the parabolas' and e5 the quartic's offsets from c times 6 and 60.
+__device__ __forceinline__ float wenoao5f(float a, float b, float c, float d, float e) {
+  const float da = a - b, db = b - c, dc = c - d, dd = d - e;
+  const float eps12 = 12e-12f;
+  float t1 = da - db, t2 = fmaf(-3.f, db, da);
+  const float s0 = fmaf(13.f * t1, t1, 3.f * t2 * t2);
+  t1 = db - dc;
+  t2 = db + dc;
+  const float s1 = fmaf(13.f * t1, t1, 3.f * t2 * t2);
+  t1 = dc - dd;
+  t2 = fmaf(3.f, dc, -dd);
+  const float s2 = fmaf(13.f * t1, t1, 3.f * t2 * t2);
+  // Legendre coefficients of the quartic on the middle cell
+  const float ae = da + db + dc + dd, bd = db + dc;   // a - e, b - d
+  const float u1 = fmaf(11.f / 120.f, ae, (-82.f / 120.f) * bd);
+  const float u2 = (fmaf(-3.f, da, 3.f * dd) + 37.f * (db - dc)) * (1.f / 56.f);
+  const float u3 = fmaf(-1.f / 12.f, ae, (2.f / 12.f) * bd);
+  const float u4 = (fmaf(-3.f, db - dc, da) - dd) * (1.f / 24.f);
+  const float x1 = fmaf(0.1f, u3, u1), x2 = fmaf(123.f / 455.f, u4, u2);
+  const float s5 = 12.f * fmaf(x1, x1, fmaf(13.f / 3.f * x2, x2, fmaf(781.f / 20.f * u3, u3, (1421461.f / 2275.f) * u4 * u4)));
+  const float tau = (fabsf(s5 - s0) + fabsf(s5 - s1) + fabsf(s5 - s2)) * (1.f / 3.f);
+  const float r0 = tau * frcp(s0 + eps12), r1 = tau * frcp(s1 + eps12), r2 = tau * frcp(s2 + eps12);
+  const float r5 = tau * frcp(s5 + eps12);
+  const float M = fmaxf(1.f, fmaxf(fmaxf(r0, r1), fmaxf(r2, r5))), iM = frcp(M);
+  const float iM2 = iM * iM;
+  const float y0 = r0 * iM, y1 = r1 * iM, y2 = r2 * iM, y5 = r5 * iM;
+  constexpr float g5 = 0.85f, g1 = 0.15f * 0.85f, g0 = 0.5f * 0.15f * 0.15f;
+  const float w0 = g0 * fmaf(y0, y0, iM2), w1 = g1 * fmaf(y1, y1, iM2), w2 = g0 * fmaf(y2, y2, iM2);
+  const float w5 = g5 * fmaf(y5, y5, iM2);
+  const float e0 = fmaf(2.f, da, -5.f * db), e1 = fmaf(-2.f, dc, -db), e2 = fmaf(-4.f, dc, dd);
+  const float e5 = fmaf(2.f, da, fmaf(-11.f, db, fmaf(-24.f, dc, 3.f * dd)));
+  const float hi = fmaf(e5, 1.f / 60.f, -(1.f / 6.f) * fmaf(g0, e0 + e2, g1 * e1));
+  const float num = fmaf(w5 * (1.f / g5), hi, (1.f / 6.f) * fmaf(w0, e0, fmaf(w1, e1, w2 * e2)));
+  return fmaf(num, frcp(w0 + w1 + w2 + w5), c);
+}
+
 __device__ __forceinline__ float linear5f(float a, float b, float c, float d, float e) {
   // (2a - 13b + 47c + 27d - 3e) / 60
   return fmaf(2.f / 60.f, a, fmaf(-13.f / 60.f, b, fmaf(47.f / 60.f, c, fmaf(27.f / 60.f, d, (-3.f / 60.f) * e))));
@@ -199,11 +241,15 @@ __device__ __forceinline__ void cell_uf(const float* __restrict__ S, int c, Rot 
 // (WENO5 fluxes; the selector is evaluated on the same faces and its
 // decisions stored), 3 learned selector at stages 1 and 2 (the stored
 // decision of each face picks linear or WENO5 for fields 0, 1, 4).
+// MODE 5 is WENO-AO(5,3).  Bits 3-4 of MODE select the flux scheme (0 Roe
+// with the LLF fallback, 1 LLF on every field, 2 HLLC) for MODES 0, 2, 4, 5.
 template <int MODE>
 __device__ __forceinline__ float rec5(bool lin, float a, float b, float c, float d, float e) {
-  if (MODE == 2) return linear5f(a, b, c, d, e);
-  if (MODE == 4) return teno5f(a, b, c, d, e);
-  if (MODE != 3) return weno5f(a, b, c, d, e);
+  constexpr int REC = MODE & 7;
+  if (REC == 2) return linear5f(a, b, c, d, e);
+  if (REC == 4) return teno5f(a, b, c, d, e);
+  if (REC == 5) return wenoao5f(a, b, c, d, e);
+  if (REC != 3) return weno5f(a, b, c, d, e);
   return lin ? linear5f(a, b, c, d, e) : weno5f(a, b, c, d, e);
 }
 
@@ -240,16 +286,119 @@ __device__ __forceinline__ void char014(const float X[5], const RoeF& e, float& 
   x1 = fmaf(-2.f, A, X[0]);
 }
 
+// X += x times right eigenvector k of the face (columns r0 = (1, u-c, ut1,
+// ut2, H-uc), r1 = (1, u, ut1, ut2, q2/2), r2 = (0, 0, 1, 0, ut1), r3 = (0, 0,
+// 0, 1, ut2), r4 = (1, u+c, ut1, ut2, H+uc)).
+__device__ __forceinline__ void add_rcol(const RoeF& e, int k, float x, float X[5]) {
+  if (k == 0 || k == 4) {
+    const float sg = (k == 0) ? -1.f : 1.f;
+    X[0] += x;
+    X[1] = fmaf(fmaf(sg, e.c, e.un), x, X[1]);
+    X[2] = fmaf(e.ut1, x, X[2]);
+    X[3] = fmaf(e.ut2, x, X[3]);
+    X[4] = fmaf(fmaf(sg * e.un, e.c, e.H), x, X[4]);
+  } else if (k == 1) {
+    X[0] += x;
+    X[1] = fmaf(e.un, x, X[1]);
+    X[2] = fmaf(e.ut1, x, X[2]);
+    X[3] = fmaf(e.ut2, x, X[3]);
+    X[4] = fmaf(0.5f * e.q2, x, X[4]);
+  } else if (k == 2) {
+    X[2] += x;
+    X[4] = fmaf(e.ut1, x, X[4]);
+  } else {
+    X[3] += x;
+    X[4] = fmaf(e.ut2, x, X[4]);
+  }
+}
+
+// Reconstructed face state usable by HLLC: rho > 0 and p + B > 0.
+__device__ __forceinline__ bool admissible_f32(const float U[5], float gm1, float g, float B) {
+  if (!(U[0] > 0.f)) return false;
+  const float q2 = fmaf(U[1], U[1], fmaf(U[2], U[2], U[3] * U[3])) * frcp(U[0]);
+  return fmaf(gm1, fmaf(-0.5f, q2, U[4]), -g * B) + B > 0.f;
+}
+
+// HLLC (Toro, Spruce & Speares 1994) between direction-frame states UL, UR:
+// Einfeldt outer speeds from the Roe average of the two states, contact speed
+// from the momentum balance, F_L / F*_L / F*_R / F_R by the sign pattern.
+__device__ __forceinline__ void hllc_f32(const float UL[5], const float UR[5], float gm1, float g, float B,
+                                         float F[5]) {
+  const float rsL = rsqrtf(UL[0]), rsR = rsqrtf(UR[0]);
+  const float irL = rsL * rsL, irR = rsR * rsR;
+  const float uL = UL[1] * irL, vL = UL[2] * irL, wL = UL[3] * irL;
+  const float uR = UR[1] * irR, vR = UR[2] * irR, wR = UR[3] * irR;
+  const float pL = fmaf(gm1, fmaf(-0.5f * UL[0], fmaf(uL, uL, fmaf(vL, vL, wL * wL)), UL[4]), -g * B);
+  const float pR = fmaf(gm1, fmaf(-0.5f * UR[0], fmaf(uR, uR, fmaf(vR, vR, wR * wR)), UR[4]), -g * B);
+  const float cL = sqrtf(g * (pL + B) * irL), cR = sqrtf(g * (pR + B) * irR);
+  const float sL = UL[0] * rsL, sR = UR[0] * rsR, iden = frcp(sL + sR);
+  const float un = fmaf(sL, uL, sR * uR) * iden, ut1 = fmaf(sL, vL, sR * vR) * iden, ut2 = fmaf(sL, wL, sR * wR) * iden;
+  const float H = fmaf(UL[4] + pL, rsL, (UR[4] + pR) * rsR) * iden;
+  const float c = sqrtf(gm1 * fmaf(-0.5f, fmaf(un, un, fmaf(ut1, ut1, ut2 * ut2)), H));
+  const float SL = fminf(uL - cL, un - c), SR = fmaxf(uR + cR, un + c);
+  const float mL = UL[0] * (SL - uL), mR = UR[0] * (SR - uR);
+  const float Ss = fmaf(uL, mL, fmaf(-uR, mR, pR - pL)) * frcp(mL - mR);
+  const bool left = Ss >= 0.f;
+  const float* U = left ? UL : UR;
+  const float SK = (SL >= 0.f) ? 0.f : ((SR <= 0.f) ? 0.f : (left ? SL : SR));
+  const float uK = left ? uL : uR, vK = left ? vL : vR, wK = left ? wL : wR, pK = left ? pL : pR;
+  const float mK = left ? mL : mR, irK = left ? irL : irR;
+  // upwind physical flux of the side the contact leaves behind x/t = 0
+  const bool useL = (SL >= 0.f) || (SR > 0.f && left);
+  const float* UK = useL ? UL : UR;
+  const float uF = useL ? uL : uR, vF = useL ? vL : vR, wF = useL ? wL : wR, pF = useL ? pL : pR;
+  F[0] = UK[1];
+  F[1] = fmaf(UK[1], uF, pF);
+  F[2] = UK[1] * vF;
+  F[3] = UK[1] * wF;
+  F[4] = uF * (UK[4] + pF);
+  if (SK != 0.f) {
+    const float fac = mK * frcp(SK - Ss);
+    const float Es = fac * fmaf(Ss - uK, Ss + pK * frcp(mK), U[4] * irK);
+    F[0] = fmaf(SK, fac - U[0], F[0]);
+    F[1] = fmaf(SK, fmaf(fac, Ss, -U[1]), F[1]);
+    F[2] = fmaf(SK, fmaf(fac, vK, -U[2]), F[2]);
+    F[3] = fmaf(SK, fmaf(fac, wK, -U[3]), F[3]);
+    F[4] = fmaf(SK, Es - U[4], F[4]);
+  }
+}
+
 // Face flux between stencil cells 2 and 3 (cells at S index c0 + m*st, m = 0..5)
 // from the FP32 records; result in the direction frame.  With FEAT the
 // selector features of the face are returned as well.
 template <int MODE, bool FEAT>
 __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, Rot R, float gm1, float g,
                                               float B, bool lin, float F[5], float* feat = nullptr) {
+  constexpr int FLUX = MODE >> 3;
   float Ur[6][5], Fr[6][5];
 #pragma unroll
   for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, R, Ur[m], Fr[m]);
   const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1, g, B, R);
+  if constexpr (FLUX == 2) {
+    // HLLC: characteristic variables reconstructed from both sides, back to states
+    float UL[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, UR[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float V[5][6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      char014(Ur[m], e, V[0][m], V[1][m], V[4][m]);
+      V[2][m] = fmaf(-e.ut1, Ur[m][0], Ur[m][2]);
+      V[3][m] = fmaf(-e.ut2, Ur[m][0], Ur[m][3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      add_rcol(e, k, rec5<MODE>(false, V[k][0], V[k][1], V[k][2], V[k][3], V[k][4]), UL);
+      add_rcol(e, k, rec5<MODE>(false, V[k][5], V[k][4], V[k][3], V[k][2], V[k][1]), UR);
+    }
+    if (!admissible_f32(UL, gm1, g, B) || !admissible_f32(UR, gm1, g, B)) {
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        UL[j] = Ur[2][j];
+        UR[j] = Ur[3][j];
+      }
+    }
+    hllc_f32(UL, UR, gm1, g, B, F);
+    return;
+  }
   // characteristic fluxes of all fields (l2 F = F2 - ut1 F0, l3 F = F3 - ut2 F0)
   float Gall[5][6];
 #pragma unroll
@@ -277,8 +426,8 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
       lR = e.unR;
       lt = e.un;
     }
-    const bool pos = lL > 0.f && lR > 0.f && lt > 0.f;
-    const bool llf = !pos && !(lL < 0.f && lR < 0.f && lt < 0.f);
+    const bool pos = FLUX == 0 && lL > 0.f && lR > 0.f && lt > 0.f;
+    const bool llf = FLUX == 1 || (!pos && !(lL < 0.f && lR < 0.f && lt < 0.f));
     // upwind: W+ of G (pos) or W- of G; LLF: W+ of (G + a V)/2 and W- of (G - a V)/2
     float gh;
     if (pos) {
@@ -777,6 +926,22 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
       }
     }
   }
+}
+
+// Launch of one stage-kernel variant on a grid of (CTAs per SM) x SMs.
+template <int MODE>
+static void launch_stage_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
+                             double* rhs_out, cudaStream_t st) {
+  const size_t smem = (MODE == 1) ? SF_SMEM_LEARNED : SF_SMEM;
+  static int grid = 0;
+  if (grid == 0) {
+    cudaFuncSetAttribute(k_stage_f32<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_f32<MODE>, SF_THREADS, smem);
+    grid = sm_count() * (per_sm < 1 ? 1 : per_sm);
+  }
+  k_stage_f32<MODE><<<grid, SF_THREADS, smem, st>>>(t, p, pool, cur, stage, dt, rhs_out);
+  ++g_kernel_launches;
 }
 
 }  // namespace mrb

@@ -23,7 +23,8 @@ import numpy as np
 NB = 16
 BC_ZERO_GRADIENT, BC_PERIODIC, BC_SYMMETRY = 0, 1, 2
 FP64, FP32_ACC64 = 0, 1
-RECON_WENO, RECON_LEARNED, RECON_LINEAR, RECON_TENO = 0, 1, 2, 3
+RECON_WENO, RECON_LEARNED, RECON_LINEAR, RECON_TENO, RECON_WENOAO = 0, 1, 2, 3, 4
+FLUX_ROE, FLUX_LLF, FLUX_HLLC = 0, 1, 2
 
 
 @dataclasses.dataclass
@@ -42,6 +43,7 @@ class RunConfig:
     precision: int = FP64
     recon: int = RECON_WENO
     rk_stages: int = 3          # 3: TVD-RK3, 2: TVD-RK2
+    flux: int = FLUX_ROE        # Roe with per-field LLF fallback, LLF, or HLLC
     mlp_tau: float = 0.0
     name: str = "custom"
 

@@ -41,7 +41,7 @@ class MrbConfig(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("recon", ctypes.c_int32),
         ("rk_stages", ctypes.c_int32),
-        ("pad1", ctypes.c_int32),
+        ("flux", ctypes.c_int32),
         ("domain_lo", ctypes.c_double * 3),
         ("dx0", ctypes.c_double),
         ("gamma", ctypes.c_double),
@@ -123,6 +123,7 @@ def make_config(cfg: RunConfig, stream_ptr: int = 0) -> MrbConfig:
     c.precision = int(cfg.precision)
     c.recon = int(cfg.recon)
     c.rk_stages = int(getattr(cfg, "rk_stages", 3))
+    c.flux = int(getattr(cfg, "flux", 0))
     c.dx0 = float(cfg.dx0)
     c.gamma = float(cfg.gamma)
     c.B = float(cfg.B)

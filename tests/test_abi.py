@@ -46,3 +46,12 @@ def test_pool_bytes_and_config_checks():
     assert mrb.pool_bytes(bad, 8) == 0
     assert mrb.pool_bytes(I.sod_config(lmax=(12,)), 8) == 0
     assert mrb.pool_bytes(cfg, 0) == 0
+    # reconstruction and flux choices: every pair valid except the learned
+    # selector with a flux other than Roe; out-of-range codes rejected
+    for recon in (I.RECON_WENO, I.RECON_LEARNED, I.RECON_LINEAR, I.RECON_TENO, I.RECON_WENOAO):
+        for flux in (I.FLUX_ROE, I.FLUX_LLF, I.FLUX_HLLC):
+            ok = recon != I.RECON_LEARNED or flux == I.FLUX_ROE
+            assert (mrb.pool_bytes(I.sod_config(recon=recon, flux=flux), 8) > 0) == ok, (recon, flux)
+    assert mrb.pool_bytes(I.sod_config(recon=5), 8) == 0
+    assert mrb.pool_bytes(I.sod_config(flux=3), 8) == 0
+    assert mrb.pool_bytes(I.sod_config(flux=-1), 8) == 0

@@ -139,9 +139,16 @@ def test_project_bit_exact():
 
 
 # ------------------------------------------------------------------ RHS, stages, CFL
-@pytest.mark.parametrize("recon", [I.RECON_WENO, I.RECON_LINEAR, I.RECON_TENO])
-def test_compute_rhs_random_states_with_jumps(recon):
-    cfg = I.explosion_config(lmax=3, recon=recon)
+# (reconstruction, flux scheme) pairs: every reconstruction with the Roe flux,
+# LLF and HLLC with two reconstructions each
+VARIANTS = [(I.RECON_WENO, I.FLUX_ROE), (I.RECON_LINEAR, I.FLUX_ROE), (I.RECON_TENO, I.FLUX_ROE),
+            (I.RECON_WENOAO, I.FLUX_ROE), (I.RECON_WENO, I.FLUX_LLF), (I.RECON_WENOAO, I.FLUX_LLF),
+            (I.RECON_WENO, I.FLUX_HLLC), (I.RECON_TENO, I.FLUX_HLLC)]
+
+
+@pytest.mark.parametrize("recon,flux", VARIANTS)
+def test_compute_rhs_random_states_with_jumps(recon, flux):
+    cfg = I.explosion_config(lmax=3, recon=recon, flux=flux)
     o, g = make_pair(cfg, rnd(4, mild=True), (ALL, SOME, lambda geo: (geo[:, 0] == 2) & (geo[:, 1] % 2 == 0)))
     o.fill_halos()
     g.fill_halos()
@@ -217,9 +224,10 @@ def test_tags_and_deltas_bit_exact():
     assert np.array_equal(g.get_state(k, with_halo=True).cpu().numpy(), o.get_state(k, with_halo=True))
 
 
-def test_explosion_mr_steps():
+@pytest.mark.parametrize("flux", [I.FLUX_ROE, I.FLUX_HLLC])
+def test_explosion_mr_steps(flux):
     """Spherical explosion with MR (levels 0..2): 4 full steps with remeshing."""
-    cfg = I.explosion_config(lmax=2)
+    cfg = I.explosion_config(lmax=2, flux=flux)
     o = oracle.Oracle(cfg)
     g = mrb.Context(cfg, 8 * 80)
     # Alg. (Initialization) on both sides
@@ -342,11 +350,15 @@ def test_rk2_bit_exact_sod_and_mr():
     assert np.array_equal(g.get_state(k).cpu().numpy(), o.get_state(k))
 
 
-def test_teno5_sod_fp64_bit_exact_and_fp32():
-    """TENO5 on the Sod tube, 20 steps: FP64 GPU bit-identical to the oracle,
-    FP32 bulk within 1e-5 L1 density (the FP32 cutoff decisions may differ
-    from FP64 only at faces whose smoothness ratio sits at the threshold)."""
-    cfg = I.sod_config(recon=I.RECON_TENO)
+@pytest.mark.parametrize("recon,flux", [(I.RECON_TENO, I.FLUX_ROE), (I.RECON_WENOAO, I.FLUX_ROE),
+                                        (I.RECON_WENO, I.FLUX_LLF), (I.RECON_WENO, I.FLUX_HLLC),
+                                        (I.RECON_WENOAO, I.FLUX_HLLC)])
+def test_variant_sod_fp64_bit_exact_and_fp32(recon, flux):
+    """Reconstruction and flux variants on the Sod tube, 20 steps: FP64 GPU
+    bit-identical to the oracle, FP32 bulk within 1e-5 L1 density (FP32
+    decisions, such as TENO5's cutoff or HLLC's wave pattern, may differ from
+    FP64 only at faces that sit at a threshold)."""
+    cfg = I.sod_config(recon=recon, flux=flux)
     o = oracle.Oracle(cfg)
     k = o.keys()
     geo = o.geometry()
@@ -354,7 +366,7 @@ def test_teno5_sod_fp64_bit_exact_and_fp32():
     o.step(20)
     ref = o.get_state(k)
     for prec in (I.FP64, I.FP32_ACC64):
-        c = I.sod_config(recon=I.RECON_TENO, precision=prec)
+        c = I.sod_config(recon=recon, flux=flux, precision=prec)
         g = mrb.Context(c, 8)
         g.set_state(k, I.ic_sod(c, geo))
         g.step(20)
@@ -363,17 +375,20 @@ def test_teno5_sod_fp64_bit_exact_and_fp32():
             assert np.array_equal(got, ref)
         else:
             l1 = np.abs(got[:, 0] - ref[:, 0]).sum() / np.abs(ref[:, 0]).sum()
-            print("TENO5 FP32 bulk L1 density vs FP64 oracle:", l1)
+            print(f"recon {recon} flux {flux}: FP32 bulk L1 density vs FP64 oracle:", l1)
             assert l1 < 1e-5
 
 
-@pytest.mark.parametrize("recon", [I.RECON_WENO, I.RECON_LINEAR])
-def test_fp32_bulk_rhs_vs_oracle(recon):
+@pytest.mark.parametrize("recon,flux", [(I.RECON_WENO, I.FLUX_ROE), (I.RECON_LINEAR, I.FLUX_ROE),
+                                        (I.RECON_TENO, I.FLUX_ROE), (I.RECON_WENOAO, I.FLUX_ROE),
+                                        (I.RECON_TENO, I.FLUX_LLF), (I.RECON_WENO, I.FLUX_HLLC),
+                                        (I.RECON_WENOAO, I.FLUX_HLLC)])
+def test_fp32_bulk_rhs_vs_oracle(recon, flux):
     """FP32 reconstruction and fluxes against the FP64 oracle on a tree with
     jumps: per value within 2e-5 of the variable's largest |L| (FP32 rounding
     of O(1) states amplified by the 1/dx of the divergence)."""
-    cfg64 = I.explosion_config(lmax=2, recon=recon)
-    cfg32 = I.explosion_config(lmax=2, recon=recon, precision=I.FP32_ACC64)
+    cfg64 = I.explosion_config(lmax=2, recon=recon, flux=flux)
+    cfg32 = I.explosion_config(lmax=2, recon=recon, flux=flux, precision=I.FP32_ACC64)
     ic = rnd(7, mild=True)
     o = oracle.Oracle(cfg64)
     g = mrb.Context(cfg32, 8 * 80)
@@ -395,5 +410,13 @@ def test_fp32_bulk_rhs_vs_oracle(recon):
     got = g.compute_rhs().cpu().numpy()
     scale = np.abs(ref).max(axis=(0, 2, 3, 4), keepdims=True)
     err = np.abs(got - ref) / scale
-    print("fp32 rhs max error relative to max|L| per variable:", err.max())
-    assert err.max() < 2e-5
+    print("fp32 rhs max error relative to max|L| per variable:", err.max(),
+          "values beyond 2e-5:", np.count_nonzero(err >= 2e-5), "of", err.size)
+    if recon == I.RECON_TENO:
+        # TENO5's cutoff is a discrete decision taken in FP32 here and in FP64
+        # by the oracle; on independent random cells a few faces sit at the
+        # threshold and flip.  Every other value stays within the bound.
+        assert np.count_nonzero(err >= 2e-5) <= 1e-3 * err.size
+        assert np.median(err) < 1e-7
+    else:
+        assert err.max() < 2e-5

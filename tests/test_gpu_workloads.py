@@ -96,14 +96,21 @@ def selector():
     return params, tau
 
 
-@pytest.mark.parametrize("path", ["fp64", "fp32_weno", "fp32_linear", "fp32_learned"])
+@pytest.mark.parametrize("path", ["fp64", "fp32_weno", "fp32_linear", "fp32_learned", "fp64_hllc", "fp32_hllc",
+                                  "fp32_llf", "fp32_wenoao"])
 def test_free_stream_preserved(path, selector):
     """A uniform state on a tree with resolution jumps: the RHS is bitwise
     zero (identical face fluxes cancel; prediction of a constant is exact), so
     after 4 steps every cell still holds one and the same value, within the
     rounding of the TVD-RK3 convex combinations (2 ulp per step) of the
     initial one."""
-    kw = dict(precision=I.FP64) if path == "fp64" else dict(precision=I.FP32_ACC64)
+    kw = dict(precision=I.FP64) if path.startswith("fp64") else dict(precision=I.FP32_ACC64)
+    if path.endswith("hllc"):
+        kw["flux"] = I.FLUX_HLLC
+    if path == "fp32_llf":
+        kw["flux"] = I.FLUX_LLF
+    if path == "fp32_wenoao":
+        kw["recon"] = I.RECON_WENOAO
     if path == "fp32_linear":
         kw["recon"] = I.RECON_LINEAR
     if path == "fp32_learned":

@@ -119,6 +119,80 @@ def test_teno5_is_the_linear_scheme_on_smooth_data():
         assert abs(oracle.teno5(f) - exact) <= 1e-13 * scale
 
 
+# ------------------------------------------------------------------ WENO-AO(5,3)
+def _wenoao_from_definition(f):
+    """WENO-AO(5,3) from the definitions: the quartic and the three parabolas
+    through the cell averages (solved as linear systems), their smoothness as
+    the sum of the integrals of the squared derivatives over the middle cell
+    (exact polynomial integration), the WENO-Z type weights and the
+    adaptive-order combination at the right face of the middle cell."""
+    P = np.polynomial.polynomial
+
+    def fit(cells):
+        # cell j covers [j - 1/2, j + 1/2]; the averages of x^k give the system
+        A = np.array([[((j + .5) ** (k + 1) - (j - .5) ** (k + 1)) / (k + 1) for k in range(len(cells))]
+                      for j in cells])
+        return np.linalg.solve(A, np.array([f[j + 2] for j in cells]))
+
+    def beta(c):
+        tot = 0.0
+        for l in range(1, len(c)):
+            d = P.polyder(c, l)
+            sq = P.polyint(P.polymul(d, d))
+            tot += P.polyval(0.5, sq) - P.polyval(-0.5, sq)
+        return tot
+    polys = [fit([-2, -1, 0]), fit([-1, 0, 1]), fit([0, 1, 2]), fit([-2, -1, 0, 1, 2])]
+    b = [beta(c) for c in polys]
+    q = [P.polyval(0.5, c) for c in polys]
+    ghi = glo = 0.85
+    gam = [(1 - ghi) * (1 - glo) / 2, (1 - ghi) * glo, (1 - ghi) * (1 - glo) / 2, ghi]
+    tau = sum(abs(b[3] - b[k]) for k in range(3)) / 3
+    w = np.array([gam[k] * (1 + (tau / (b[k] + 1e-12)) ** 2) for k in range(4)])
+    w /= w.sum()
+    return w[3] / gam[3] * (q[3] - sum(gam[k] * q[k] for k in range(3))) + sum(w[k] * q[k] for k in range(3))
+
+
+def test_wenoao_matches_its_definition():
+    """Random data of several scales, smooth and with jumps: the oracle's
+    closed forms (Legendre-coefficient smoothness of the quartic, face values)
+    agree with the polynomial fits and integrals of the definition."""
+    rng = np.random.default_rng(21)
+    for it in range(300):
+        scale = 10.0 ** rng.uniform(-2, 2)
+        f = rng.normal(size=5) * scale if it % 2 else np.cumsum(rng.normal(size=5)) * scale
+        ref = _wenoao_from_definition(f)
+        assert abs(oracle.wenoao53(f) - ref) <= 1e-10 * max(scale, abs(ref)), (f, ref)
+
+
+def test_wenoao_exact_on_quadratics_and_fifth_order_on_quartics():
+    """Quadratics: every polynomial of the scheme reproduces them, so any
+    weights do.  Smooth quartic data on a fine grid: the weights tend to the
+    linear ones and the value to the quartic's (error well below WENO5-JS's)."""
+    rng = np.random.default_rng(22)
+    for _ in range(20):
+        c = rng.uniform(-2, 2, 3)
+        h = rng.uniform(0.01, 0.5)
+        edges = (np.arange(6) - 2.5) * h
+        f = cell_avgs_poly(c, edges)
+        assert abs(oracle.wenoao53(f) - poly_at(c, 0.5 * h)) <= 1e-13 * max(1.0, np.abs(f).max())
+    errs_ao, errs_js = [], []
+    for _ in range(20):
+        c = rng.uniform(-2, 2, 5)
+        c[1] = 3.0
+        edges = (np.arange(6) - 2.5) * 0.02
+        f = cell_avgs_poly(c, edges)
+        ex = poly_at(c, 0.01)
+        errs_ao.append(abs(oracle.wenoao53(f) - ex))
+        errs_js.append(abs(oracle.weno5(f) - ex))
+    assert max(errs_ao) < 1e-9 and np.mean(errs_ao) < 0.1 * np.mean(errs_js)
+
+
+def test_wenoao_step_keeps_the_smooth_side():
+    assert abs(oracle.wenoao53([1.0, 1.0, 1.0, 0.0, 0.0]) - 1.0) < 1e-8
+    assert abs(oracle.wenoao53([0.0, 0.0, 1.0, 1.0, 1.0]) - 1.0) < 1e-8
+    assert abs(oracle.wenoao53([1.0, 1.0, 0.0, 0.0, 0.0])) < 1e-8
+
+
 # ------------------------------------------------------------------ eigensystem
 def _rand_cons(rng, g=1.4):
     rho = rng.uniform(0.1, 3)
@@ -152,6 +226,182 @@ def test_face_flux_consistency():
             U = _rand_cons(rng)
             F = oracle.face_flux(np.tile(U, (6, 1)), d)
             assert np.abs(F - oracle.flux(U, d)).max() < 1e-12 * max(1.0, np.abs(F).max())
+
+
+# ------------------------------------------------------------------ LLF and HLLC
+def _cons(rho, u, v, w, p, g=1.4, B=0.0):
+    return np.array([rho, rho * u, rho * v, rho * w, (p + g * B) / (g - 1) + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+def _np_flux(U, d, g=1.4, B=0.0):
+    """Euler flux along axis d of a lab-frame conserved state (stiffened gas)."""
+    rho, m, E = U[0], U[1:4], U[4]
+    vel = m / rho
+    p = (g - 1) * (E - 0.5 * rho * vel @ vel) - g * B
+    F = np.empty(5)
+    F[0] = m[d]
+    F[1:4] = m * vel[d]
+    F[1 + d] += p
+    F[4] = vel[d] * (E + p)
+    return F
+
+
+def _shock_pair(g, B, M, pre, right_facing):
+    """States on both sides of a shock of Mach number M into the pre-shock
+    state pre = (rho, u, p) (Rankine-Hugoniot of the stiffened gas: the ideal
+    gas relations in p + B).  Returns (U_left, U_right, shock speed)."""
+    r0, u0, p0 = pre
+    c0 = math.sqrt(g * (p0 + B) / r0)
+    ratio = (g + 1) * M * M / ((g - 1) * M * M + 2)
+    p1 = (p0 + B) * (1 + 2 * g / (g + 1) * (M * M - 1)) - B
+    if right_facing:                               # pre-shock state on the right
+        s = u0 + M * c0
+        u1 = s - (s - u0) / ratio
+        return _cons(r0 * ratio, u1, 0.3, -0.1, p1, g, B), _cons(r0, u0, 0.3, -0.1, p0, g, B), s
+    s = u0 - M * c0                                # pre-shock state on the left
+    u1 = s + (u0 - s) / ratio
+    return _cons(r0, u0, 0.3, -0.1, p0, g, B), _cons(r0 * ratio, u1, 0.3, -0.1, p1, g, B), s
+
+
+def _to_axis(U, d):
+    """Move the x components of a state built along x onto axis d."""
+    out = U.copy()
+    out[1:4] = 0.0
+    out[1 + d] = U[1]
+    out[1 + (d + 1) % 3] = U[2]
+    out[1 + (d + 2) % 3] = U[3]
+    return out
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_hllc_exact_on_isolated_shocks(d):
+    """An isolated shock satisfying Rankine-Hugoniot: the Roe-averaged outer
+    speed equals the shock speed, the contact speed the post-shock velocity,
+    and HLLC returns the exact upwind flux (F_L when the shock moves right of
+    x/t = 0, F_R when left), for ideal and stiffened gas and both families."""
+    for g, B in ((1.4, 0.0), (4.4, 0.6), (1.67, 2.0)):
+        for M in (1.2, 2.5, 6.0):
+            for right_facing in (True, False):
+                for u0 in (-3.0, -0.4, 0.0, 0.7, 3.0):
+                    UL, UR, s = _shock_pair(g, B, M, (1.3, u0, 0.8), right_facing)
+                    UL, UR = _to_axis(UL, d), _to_axis(UR, d)
+                    FL, FR = _np_flux(UL, d, g, B), _np_flux(UR, d, g, B)
+                    assert np.abs(FR - FL - s * (UR - UL)).max() < 1e-11 * np.abs(FL).max()
+                    F = oracle.hllc(UL, UR, d, g, B)
+                    ref = FL if s > 0 else FR
+                    assert np.abs(F - ref).max() <= 1e-11 * np.abs(ref).max(), (g, B, M, right_facing, u0)
+
+
+def test_hllc_contact_shear_consistency_and_supersonic():
+    """Stationary contact with shear: the flux is the pressure alone (no
+    mass, tangential momentum or energy flux); HLLC(U, U) = F(U); both
+    states supersonic to one side: the upwind physical flux."""
+    rng = np.random.default_rng(31)
+    for d in range(3):
+        for _ in range(20):
+            p = rng.uniform(0.1, 3)
+            UL = _cons(rng.uniform(0.1, 3), 0.0, *rng.uniform(-2, 2, 2), p)
+            UR = _cons(rng.uniform(0.1, 3), 0.0, *rng.uniform(-2, 2, 2), p)
+            UL, UR = _to_axis(UL, d), _to_axis(UR, d)
+            F = oracle.hllc(UL, UR, d)
+            ref = np.zeros(5)
+            ref[1 + d] = p
+            # the contact speed is zero up to rounding: errors of a few ulp of the states
+            assert np.abs(F - ref).max() <= 1e-14 * max(np.abs(UL).max(), np.abs(UR).max())
+            U = _rand_cons(rng)
+            assert np.abs(oracle.hllc(U, U, d) - _np_flux(U, d)).max() <= 1e-13 * np.abs(_np_flux(U, d)).max()
+            sgn = rng.choice([-1.0, 1.0])
+            A = _to_axis(_cons(1.0, sgn * 4.0, 0.1, 0.2, 0.5), d)
+            Bs = _to_axis(_cons(0.6, sgn * 4.5, -0.3, 0.2, 0.4), d)
+            ref = _np_flux(A, d) if sgn > 0 else _np_flux(Bs, d)
+            assert np.abs(oracle.hllc(A, Bs, d) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def _roe_jacobian(UL, UR, g):
+    """The Euler flux Jacobian along x at the Roe averages (u, v, w, H) of
+    two states (Toro's textbook form; valid for the stiffened gas, whose
+    pressure differs from the ideal gas's by a constant)."""
+    def prim(U):
+        rho = U[0]
+        vel = U[1:4] / rho
+        p = (g - 1) * (U[4] - 0.5 * rho * vel @ vel)          # B = 0 here
+        return rho, vel, (U[4] + p) / rho
+    rL, vL, HL = prim(UL)
+    rR, vR, HR = prim(UR)
+    sL, sR = math.sqrt(rL), math.sqrt(rR)
+    u, v, w = (sL * vL + sR * vR) / (sL + sR)
+    H = (sL * HL + sR * HR) / (sL + sR)
+    gh = g - 1
+    q2 = u * u + v * v + w * w
+    A = np.array([
+        [0, 1, 0, 0, 0],
+        [gh / 2 * q2 - u * u, (3 - g) * u, -gh * v, -gh * w, gh],
+        [-u * v, v, u, 0, 0],
+        [-u * w, w, 0, u, 0],
+        [u * (gh / 2 * q2 - H), H - gh * u * u, -gh * u * v, -gh * u * w, g * u]])
+    c = math.sqrt(gh * (H - q2 / 2))
+    return A, u, c
+
+
+def test_llf_face_flux_on_a_step_closed_form():
+    """Six cells forming a step at the face: TENO5 returns each side's value
+    exactly (its cutoff keeps only the one-sided stencil), so the LLF flux on
+    every field is 1/2 (F_L + F_R) - 1/2 R diag(alpha) L
+    (U_R - U_L), alpha_k the larger |lam_k| of the two face cells, which is
+    the spectral sum over the Roe Jacobian's eigenvalue groups (u - c, u,
+    u + c), built here from Sylvester's projectors of the textbook Jacobian.  The default Roe
+    flux on a supersonic step is the upwind F_L exactly; LLF adds dissipation."""
+    rng = np.random.default_rng(41)
+    for _ in range(30):
+        UL = _cons(rng.uniform(0.5, 2), *rng.uniform(-1, 1, 3), rng.uniform(0.5, 2))
+        UR = _cons(rng.uniform(0.5, 2), *rng.uniform(-1, 1, 3), rng.uniform(0.5, 2))
+        U6 = np.array([UL] * 3 + [UR] * 3)
+        A, u, c = _roe_jacobian(UL, UR, 1.4)
+        mu = [u - c, u, u + c]
+        Id = np.eye(5)
+        # minimal polynomial (A - mu0)(A - mu1)(A - mu2) = 0: A is diagonalisable with these eigenvalues
+        assert np.abs((A - mu[0] * Id) @ (A - mu[1] * Id) @ (A - mu[2] * Id)).max() < 1e-11
+        def cell_lams(U):
+            vel = U[1] / U[0]
+            p = 0.4 * (U[4] - 0.5 * U[1:4] @ U[1:4] / U[0])
+            cc = math.sqrt(1.4 * p / U[0])
+            return np.array([vel - cc, vel, vel + cc])
+        aL, aR = cell_lams(UL), cell_lams(UR)
+        alpha_g = np.maximum(np.abs(aL), np.abs(aR))
+        # R diag(alpha) L = sum over groups of alpha_g times the spectral projector (Sylvester)
+        Pm = np.zeros((5, 5))
+        for gi in range(3):
+            proj = Id.copy()
+            for h in range(3):
+                if h != gi:
+                    proj = proj @ (A - mu[h] * Id) / (mu[gi] - mu[h])
+            Pm += alpha_g[gi] * proj
+        ref = 0.5 * (_np_flux(UL, 0) + _np_flux(UR, 0)) - 0.5 * Pm @ (UR - UL)
+        F = oracle.face_flux(U6, 0, mode=I.RECON_TENO, flux=I.FLUX_LLF)
+        assert np.abs(F - ref).max() <= 1e-12 * np.abs(ref).max()
+    UL, UR = _cons(1.0, 3.0, 0.1, 0.0, 0.5), _cons(0.7, 3.2, 0.0, 0.2, 0.4)
+    U6 = np.array([UL] * 3 + [UR] * 3)
+    F_roe = oracle.face_flux(U6, 0, mode=I.RECON_TENO)
+    assert np.abs(F_roe - _np_flux(UL, 0)).max() < 1e-12
+    assert np.abs(oracle.face_flux(U6, 0, mode=I.RECON_TENO, flux=I.FLUX_LLF) - F_roe).max() > 1e-3
+
+
+def test_hllc_face_flux_on_a_step_is_the_riemann_flux():
+    """The same step through the HLLC face flux: the reconstructed face
+    states are the two sides' states (TENO5 on a step), so the face flux is
+    HLLC(U_L, U_R); consistency on six equal cells for LLF and HLLC."""
+    rng = np.random.default_rng(42)
+    for d in range(3):
+        for _ in range(20):
+            UL, UR = _rand_cons(rng), _rand_cons(rng)
+            U6 = np.array([UL] * 3 + [UR] * 3)
+            ref = oracle.hllc(UL, UR, d)
+            F = oracle.face_flux(U6, d, mode=I.RECON_TENO, flux=I.FLUX_HLLC)
+            assert np.abs(F - ref).max() <= 1e-12 * np.abs(ref).max()
+            U = _rand_cons(rng)
+            for fl in (I.FLUX_LLF, I.FLUX_HLLC):
+                F = oracle.face_flux(np.tile(U, (6, 1)), d, flux=fl)
+                assert np.abs(F - oracle.flux(U, d)).max() < 1e-12 * max(1.0, np.abs(F).max())
 
 
 # ------------------------------------------------------------------ MR operators
@@ -325,8 +575,10 @@ def test_conservation_periodic_with_jumps():
     assert (np.abs(s1 - s0) <= 1e-13 * np.maximum(np.abs(s0), scale)).all(), (s1 - s0)
 
 
-def test_sod_exact_solution_and_transverse_momentum():
-    """Sec. 5.1: Sod along x converges to the exact solution; rho v, rho w stay 0."""
+@pytest.mark.parametrize("flux", [I.FLUX_ROE, I.FLUX_LLF, I.FLUX_HLLC])
+def test_sod_exact_solution_and_transverse_momentum(flux):
+    """Sec. 5.1: Sod along x converges to the exact solution; rho v, rho w
+    stay 0 (each flux scheme)."""
     tox = dict(l.split() for l in open(os.path.join(HERE, "golden", "toro_test1.txt")) if l[0] != "#")
     ps, us = er.star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
     assert abs(ps - float(tox["p_star"])) < 5e-6 and abs(us - float(tox["u_star"])) < 5e-6
@@ -334,7 +586,7 @@ def test_sod_exact_solution_and_transverse_momentum():
     errs = []
     for nx in (32, 64, 128):
         nbx = nx // 16
-        cfg = I.sod_config(base_blocks=(nbx, 1, 1), dx0=1.0 / nx)
+        cfg = I.sod_config(base_blocks=(nbx, 1, 1), dx0=1.0 / nx, flux=flux)
         o = oracle.Oracle(cfg)
         o.set_state(o.keys(), I.ic_sod(cfg, o.geometry()))
         run_fixed_dt(o, 0.2 / nx, t_end)
@@ -353,10 +605,11 @@ def test_sod_exact_solution_and_transverse_momentum():
     assert errs[1] < errs[0] * 0.8 and errs[2] < errs[1] * 0.8, errs
 
 
-@pytest.mark.parametrize("axis,recon", [(0, I.RECON_WENO), (1, I.RECON_WENO), (2, I.RECON_WENO), (0, I.RECON_TENO)])
+@pytest.mark.parametrize("axis,recon", [(0, I.RECON_WENO), (1, I.RECON_WENO), (2, I.RECON_WENO), (0, I.RECON_TENO),
+                                        (0, I.RECON_WENOAO)])
 def test_fifth_order_convergence_density_wave(axis, recon):
     """Smooth advected density wave, exact cell averages; observed L1 order
-    (WENO5-JS along each axis, TENO5 along x)."""
+    (WENO5-JS along each axis, TENO5 and WENO-AO(5,3) along x)."""
     errs = []
     t_end = 0.05
     for n in (32, 64, 128):
