@@ -267,7 +267,10 @@ def ic_rt(cfg, geo, seed: int = 2012, rho_heavy=3.0, rho_light=1.0, p_interface=
     for g = (0, 0, -1) with p = 10 at z = 1."""
     X, Y, Z, _ = cell_centres(cfg, geo)
     width = 2.0 * cfg.dx0 * 0.5 ** cfg.lmax_of(0)
-    zi = rt_interface(seed, X[:, 0], Y[:, 0])[:, None]          # [n, 1, 16, 16] -> broadcast over z
+    # interface height per distinct (x, y) column (blocks stacked in z share columns)
+    xy = np.stack([X[:, 0].ravel(), Y[:, 0].ravel()], axis=1)
+    cols, inv = np.unique(xy, axis=0, return_inverse=True)
+    zi = rt_interface(seed, cols[:, 0], cols[:, 1])[inv.ravel()].reshape(X[:, 0].shape)[:, None]
     s = 0.5 * (1.0 + np.tanh((Z - zi) / width))
     rho = rho_light + (rho_heavy - rho_light) * s
     g = -cfg.gravity[2]

@@ -231,9 +231,12 @@ class Context:
             raise MrbError(rc, msg.decode() if msg else "")
 
     def close(self):
+        """Destroy the context and drop its block pool (the memory returns to
+        torch's allocator once no other reference holds it)."""
         if getattr(self, "_h", None):
             lib().mrb_destroy(self._h)
             self._h = None
+            self.pool = None
 
     def __del__(self):
         try:
