@@ -112,6 +112,12 @@ typedef struct mrb_config {
   double cfl;                      /* CFL number k of Eq. (Cfl)                            */
   double gravity[3];               /* body force in S(U) of Eq. (Euler); zero = none       */
   double eps;                      /* detail threshold at l_max (Eq. UserEpsilon applied)  */
+  double mu;                       /* dynamic viscosity of the Navier-Stokes terms (Sec.   */
+                                   /* 2.1; Stokes' hypothesis, no heat conduction); 0 =    */
+                                   /* Euler.  Viscous face fluxes from second-order compact*/
+                                   /* gradients; the time step also obeys k dx^2 /         */
+                                   /* (6 max(mu/rho)).  With MRB_FP32_ACC64 it requires     */
+                                   /* MRB_RECON_WENO5 and MRB_FLUX_ROE (else EINVAL)        */
   const void* mlp_weights;         /* device, learned selector weights (see mrb_mlp_*)     */
   double mlp_tau;                  /* logit threshold of the learned selector              */
   void* stream;                    /* cudaStream_t for all work                            */

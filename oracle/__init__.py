@@ -58,6 +58,7 @@ class OrcConfig(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("gravity", ctypes.c_double * 3),
         ("eps", ctypes.c_double),
+        ("mu", ctypes.c_double),
     ]
 
 
@@ -134,6 +135,7 @@ def make_config(cfg, n_threads: int = 0) -> OrcConfig:
     c.B = float(cfg.B)
     c.cfl = float(cfg.cfl)
     c.eps = float(cfg.eps)
+    c.mu = float(getattr(cfg, "mu", 0.0))
     return c
 
 

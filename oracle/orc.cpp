@@ -82,6 +82,7 @@ struct orc_config {
   double gamma, B, cfl;
   double gravity[3];
   double eps;             // threshold at l_max (Eq. UserEpsilon already applied)
+  double mu;              // dynamic viscosity of the Navier-Stokes terms; 0 = Euler
 };
 
 }  // extern "C"
@@ -846,6 +847,58 @@ void fill_halos(Ctx& C) {
 // Sec. 2.2: dimension-by-dimension face fluxes; L = -sum_d (F_{+1/2} - F_{-1/2})/dx
 // evaluated as ((Fx_lo - Fx_hi) + (Fy_lo - Fy_hi) + (Fz_lo - Fz_hi)) / dx, plus the
 // gravity source S = (0, rho g, m . g) of Eq. (Euler) when gravity is set.
+// Viscous flux of the Navier-Stokes equations (Sec. 2.1 names them beside
+// Eq. Euler; Stokes' hypothesis, constant dynamic viscosity mu, no heat
+// conduction) at the face between the stored cells cL and cL + e_d of node n,
+// lab frame: (0, tau_xd, tau_yd, tau_zd, u . tau_d) with
+// tau_ij = mu (du_i/dx_j + du_j/dx_i) - 2/3 mu (div u) delta_ij.  Second-order
+// compact face gradients: the normal derivative from the two face cells, a
+// tangential derivative as the mean of the two face cells' central
+// differences; the face velocity is the mean of the two face cells'.
+void viscous_flux(const Node& n, int d, const int cL[3], double mu, double dx, double Fv[5]) {
+  auto vel = [&](const int c[3], double w[3]) {
+    int s = sidx(c[0], c[1], c[2]);
+    double rho = n.u[s];
+    w[0] = n.u[NCELL + s] / rho;
+    w[1] = n.u[2 * NCELL + s] / rho;
+    w[2] = n.u[3 * NCELL + s] / rho;
+  };
+  int cR[3] = {cL[0], cL[1], cL[2]};
+  cR[d] += 1;
+  double uL[3], uR[3];
+  vel(cL, uL);
+  vel(cR, uR);
+  double G[3][3];   // G[i][j] = du_i / dx_j at the face
+  for (int i = 0; i < 3; ++i) G[i][d] = (uR[i] - uL[i]) / dx;
+  for (int j = 0; j < 3; ++j) {
+    if (j == d) continue;
+    int lp[3] = {cL[0], cL[1], cL[2]}, lm[3] = {cL[0], cL[1], cL[2]};
+    int rp[3] = {cR[0], cR[1], cR[2]}, rm[3] = {cR[0], cR[1], cR[2]};
+    lp[j] += 1;
+    lm[j] -= 1;
+    rp[j] += 1;
+    rm[j] -= 1;
+    double a[3], b[3], c[3], e[3];
+    vel(lp, a);
+    vel(lm, b);
+    vel(rp, c);
+    vel(rm, e);
+    for (int i = 0; i < 3; ++i) G[i][j] = ((a[i] - b[i]) + (c[i] - e[i])) / (4.0 * dx);
+  }
+  double div = (G[0][0] + G[1][1]) + G[2][2];
+  double ub[3], tau[3];
+  for (int i = 0; i < 3; ++i) {
+    ub[i] = 0.5 * (uL[i] + uR[i]);
+    tau[i] = mu * (G[i][d] + G[d][i]);
+  }
+  tau[d] = tau[d] - ((2.0 / 3.0) * mu) * div;
+  Fv[0] = 0.0;
+  Fv[1] = tau[0];
+  Fv[2] = tau[1];
+  Fv[3] = tau[2];
+  Fv[4] = (ub[0] * tau[0] + ub[1] * tau[1]) + ub[2] * tau[2];
+}
+
 void leaf_rhs(const Ctx& C, Node& n) {
   double g = C.c.gamma, B = C.c.B;
   double dx = dx_of(C, n.level);
@@ -869,6 +922,16 @@ void leaf_rhs(const Ctx& C, Node& n) {
           }
           double Fo[5];
           face_flux(U6, d, g, B, C.c.recon, C.c.flux, Fo);
+          if (C.c.mu > 0.0) {
+            // Navier-Stokes: the face flux is F(U) - F_v(U, grad u)
+            int cl[3];
+            cl[d] = f - 1;
+            cl[(d == 0) ? 1 : 0] = a;
+            cl[(d == 2) ? 1 : 2] = b;
+            double Fv[5];
+            viscous_flux(n, d, cl, C.c.mu, dx, Fv);
+            for (int v = 0; v < NV; ++v) Fo[v] = Fo[v] - Fv[v];
+          }
           for (int v = 0; v < NV; ++v) F[fidx(d, v, f, a, b)] = Fo[v];
         }
   }
@@ -1061,9 +1124,12 @@ void project(Ctx& C) {
 
 // Eq. (Cfl): dt = CFL dx_lmax / ( max|u|+c + max|v|+c + max|w|+c ), each maximum
 // over all leaf internal cells of the instance, summed in x, y, z order.
+// Eq. (Cfl), extended for the viscous terms by the explicit diffusion limit
+// of the second-order Laplacian in 3D: dt_v = k dx^2 / (6 max(mu / rho)); the
+// step is the smaller of the two.
 void cfl_dt(Ctx& C, double* dt) {
   int ni = C.c.n_instances;
-  std::vector<double> sm((size_t)ni * 3, 0.0);
+  std::vector<double> sm((size_t)ni * 3, 0.0), ir((size_t)ni, 0.0);
   for (auto& kv : C.nodes) {
     Node& n = kv.second;
     if (!n.leaf) continue;
@@ -1074,11 +1140,13 @@ void cfl_dt(Ctx& C, double* dt) {
           for (int v = 0; v < NV; ++v) U[v] = n.u[(size_t)v * NCELL + sidx(i, j, k)];
           Prim q = prim_of(U, C.c.gamma, C.c.B);
           for (int d = 0; d < 3; ++d) sm[(size_t)n.inst * 3 + d] = std::max(sm[(size_t)n.inst * 3 + d], std::fabs(q.vel[d]) + q.c);
+          ir[n.inst] = std::max(ir[n.inst], 1.0 / q.rho);
         }
   }
   for (int i = 0; i < ni; ++i) {
     double dxl = dx_of(C, C.c.lmax[i]);
     dt[i] = C.c.cfl * dxl / ((sm[(size_t)i * 3] + sm[(size_t)i * 3 + 1]) + sm[(size_t)i * 3 + 2]);
+    if (C.c.mu > 0.0) dt[i] = std::min(dt[i], (C.c.cfl * (dxl * dxl)) / ((6.0 * C.c.mu) * ir[i]));
   }
 }
 

@@ -7,6 +7,7 @@
 // device arrays after every change; all kernels read it (and its counts) from
 // device memory, so the captured stage graph stays valid across remeshes.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <exception>
@@ -276,8 +277,9 @@ struct mrb_ctx {
   void step_stages() {
     launch_cfl(topo(), phys, P, cur, d_smax, d_dt, d_status, st);
     // the mixed-precision stage kernel reads face neighbours directly, so the
-    // stage fill of leaves is limited to predicted and boundary face regions
-    const int mode = (cfg.precision == MRB_FP32_ACC64) ? FILL_STAGE : FILL_FULL;
+    // stage fill of leaves is limited to predicted and boundary face regions;
+    // the viscous gradients read edge halo cells, which need the full fill
+    const int mode = (cfg.precision == MRB_FP32_ACC64 && !(cfg.mu > 0.0)) ? FILL_STAGE : FILL_FULL;
     for (int s = 0; s < phys.rk; ++s) {
       fill_halos(mode);
       stage(s, d_dt);
@@ -475,6 +477,11 @@ int check_config(const mrb_config* cfg) {
   if (cfg->recon < 0 || cfg->recon > 4) return MRB_EINVAL;
   if (cfg->flux < 0 || cfg->flux > 2) return MRB_EINVAL;
   if (cfg->recon == MRB_RECON_LEARNED && cfg->flux != MRB_FLUX_ROE) return MRB_EINVAL;
+  if (!(cfg->mu >= 0.0) || !std::isfinite(cfg->mu)) return MRB_EINVAL;
+  // the mixed-precision viscous kernel exists for WENO5-JS with the Roe flux
+  if (cfg->mu > 0.0 && cfg->precision == MRB_FP32_ACC64 &&
+      (cfg->recon != MRB_RECON_WENO5 || cfg->flux != MRB_FLUX_ROE))
+    return MRB_EINVAL;
   if (cfg->rk_stages != 0 && cfg->rk_stages != 2 && cfg->rk_stages != 3) return MRB_EINVAL;
   if (!(cfg->dx0 > 0) || !(cfg->gamma > 1.0) || !(cfg->cfl > 0)) return MRB_EINVAL;
   return MRB_OK;
@@ -534,6 +541,7 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     p.cfl = cfg->cfl;
     p.dx0 = cfg->dx0;
     p.eps = cfg->eps;
+    p.mu = cfg->mu;
     for (int d = 0; d < 3; ++d) {
       p.grav[d] = cfg->gravity[d];
       p.nb[d] = cfg->base_blocks[d];
@@ -565,7 +573,7 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     c->d_lmax = c->dalloc<int32_t>(cfg->n_instances);
     c->d_list = c->dalloc<int32_t>(2 * n);
     c->d_dt = c->dalloc<double>(cfg->n_instances);
-    c->d_smax = c->dalloc<unsigned long long>(3 * (size_t)cfg->n_instances);
+    c->d_smax = c->dalloc<unsigned long long>(4 * (size_t)cfg->n_instances);
     c->d_delta_node = c->dalloc<double>(n);
     c->d_partial = c->dalloc<double>(5 * n);
     c->d_tags = c->dalloc<int8_t>(n);

@@ -9,7 +9,8 @@ namespace mrb {
 
 void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
                        double* rhs_out, cudaStream_t st) {
-  if (p.flux == 1) launch_rhs_rk_f32_llf(t, p, pool, cur, stage, dt, rhs_out, st);
+  if (p.mu > 0.0) launch_stage_f32<32>(t, p, pool, cur, stage, dt, rhs_out, st);   // WENO5, Roe, viscous
+  else if (p.flux == 1) launch_rhs_rk_f32_llf(t, p, pool, cur, stage, dt, rhs_out, st);
   else if (p.flux == 2) launch_rhs_rk_f32_hllc(t, p, pool, cur, stage, dt, rhs_out, st);
   else if (p.recon == 2) launch_stage_f32<2>(t, p, pool, cur, stage, dt, rhs_out, st);
   else if (p.recon == 3) launch_stage_f32<4>(t, p, pool, cur, stage, dt, rhs_out, st);
@@ -44,17 +45,18 @@ void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, d
   ++g_kernel_launches;
 }
 
-// Per-instance maxima of |u_d| + c over the leaves' internal cells: speeds in
-// FP32, maxima (exact) and the time step of Eq. (Cfl) in FP64.
+// Per-instance maxima of |u_d| + c (and of 1/rho, for the viscous limit) over
+// the leaves' internal cells: speeds in FP32, maxima (exact) and the time step
+// of Eq. (Cfl) in FP64.
 __global__ void __launch_bounds__(256) k_cfl_f32(Topo t, Phys p, Pool pool, int cur,
                                                  unsigned long long* __restrict__ smax, int* __restrict__ status) {
-  __shared__ float sh[3][8];
+  __shared__ float sh[4][8];
   const int nleaves = t.cnt[CNT_NLEAVES];
   const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
   for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
     const int node = t.leaves[li];
     const double* U = pool.buf[cur] + (size_t)t.slot[node] * SLOT_U;
-    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;   // max |u_d| + c, max 1/rho
     bool bad = false;
     for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
       const int s = sidx(e % 16, (e / 16) % 16, e / 256);
@@ -68,23 +70,26 @@ __global__ void __launch_bounds__(256) k_cfl_f32(Topo t, Phys p, Pool pool, int 
       m0 = fmaxf(m0, fabsf(vx) + c);
       m1 = fmaxf(m1, fabsf(vy) + c);
       m2 = fmaxf(m2, fabsf(vz) + c);
+      m3 = fmaxf(m3, ir);
     }
     if (bad) atomicExch(status, (int)ST_NONPHYS);
     for (int o = 16; o > 0; o >>= 1) {
       m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
       m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
       m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+      m3 = fmaxf(m3, __shfl_xor_sync(0xffffffffu, m3, o));
     }
     if ((threadIdx.x & 31) == 0) {
       sh[0][threadIdx.x >> 5] = m0;
       sh[1][threadIdx.x >> 5] = m1;
       sh[2][threadIdx.x >> 5] = m2;
+      sh[3][threadIdx.x >> 5] = m3;
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
+    if (threadIdx.x < 4) {
       float x = sh[threadIdx.x][0];
       for (int q = 1; q < 8; ++q) x = fmaxf(x, sh[threadIdx.x][q]);
-      atomicMax(&smax[t.inst[node] * 3 + threadIdx.x], (unsigned long long)__double_as_longlong(f2d_fast(x)));
+      atomicMax(&smax[t.inst[node] * 4 + threadIdx.x], (unsigned long long)__double_as_longlong(f2d_fast(x)));
     }
     __syncthreads();
   }

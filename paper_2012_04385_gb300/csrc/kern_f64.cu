@@ -231,16 +231,18 @@ void launch_project_level(const Topo& t, const Pool& pool, int buf, int level, c
 }
 
 // ---------------------------------------------------------------- CFL
-__device__ __forceinline__ void block_max3(double v[3], double* sh) {
-  // sh: [3][8] for 256 threads
-  for (int q = 0; q < 3; ++q)
+// Block-wide maxima of N values per thread (sh: [N][8] for 256 threads); the
+// result is valid in the first warp.
+template <int N>
+__device__ __forceinline__ void block_max(double v[N], double* sh) {
+  for (int q = 0; q < N; ++q)
     for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0)
-    for (int q = 0; q < 3; ++q) sh[q * 8 + wid] = v[q];
+    for (int q = 0; q < N; ++q) sh[q * 8 + wid] = v[q];
   __syncthreads();
   if (threadIdx.x < 32) {
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < N; ++q) {
       double x = (lane < 8) ? sh[q * 8 + lane] : 0.0;
       for (int o = 4; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
       v[q] = x;
@@ -251,12 +253,12 @@ __device__ __forceinline__ void block_max3(double v[3], double* sh) {
 
 __global__ void __launch_bounds__(256) k_cfl(Topo t, Phys p, Pool pool, int cur,
                                              unsigned long long* __restrict__ smax, int* __restrict__ status) {
-  __shared__ double sh[24];
+  __shared__ double sh[32];
   const int nleaves = t.cnt[CNT_NLEAVES];
   for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
     const int node = t.leaves[li];
     const double* U = pool.buf[cur] + (size_t)t.slot[node] * SLOT_U;
-    double m[3] = {0.0, 0.0, 0.0};
+    double m[4] = {0.0, 0.0, 0.0, 0.0};   // max |u_d| + c per direction, max 1/rho
     bool bad = false;
     for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
       const int s = sidx(e % 16, (e / 16) % 16, e / 256);
@@ -267,12 +269,13 @@ __global__ void __launch_bounds__(256) k_cfl(Topo t, Phys p, Pool pool, int cur,
       if (!(q.rho > 0.0) || !(q.p + p.B > 0.0)) bad = true;
 #pragma unroll
       for (int d = 0; d < 3; ++d) m[d] = fmax(m[d], fabs(q.vel[d]) + q.c);
+      if (p.mu > 0.0) m[3] = fmax(m[3], 1.0 / q.rho);
     }
     if (bad) atomicExch(status, (int)ST_NONPHYS);
-    block_max3(m, sh);
+    block_max<4>(m, sh);
     if (threadIdx.x == 0) {
       const int inst = t.inst[node];
-      for (int d = 0; d < 3; ++d) atomicMax(&smax[inst * 3 + d], (unsigned long long)__double_as_longlong(m[d]));
+      for (int d = 0; d < 4; ++d) atomicMax(&smax[inst * 4 + d], (unsigned long long)__double_as_longlong(m[d]));
     }
   }
 }
@@ -280,16 +283,23 @@ __global__ void __launch_bounds__(256) k_cfl(Topo t, Phys p, Pool pool, int cur,
 __global__ void k_cfl_finish(Phys p, const unsigned long long* __restrict__ smax, double* __restrict__ dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.n_inst) return;
-  const double s0 = __longlong_as_double((long long)smax[i * 3]);
-  const double s1 = __longlong_as_double((long long)smax[i * 3 + 1]);
-  const double s2 = __longlong_as_double((long long)smax[i * 3 + 2]);
+  const double s0 = __longlong_as_double((long long)smax[i * 4]);
+  const double s1 = __longlong_as_double((long long)smax[i * 4 + 1]);
+  const double s2 = __longlong_as_double((long long)smax[i * 4 + 2]);
   const double dxl = ldexp(p.dx0, -p.lmax[i]);
-  dt[i] = p.cfl * dxl / ((s0 + s1) + s2);
+  double h = p.cfl * dxl / ((s0 + s1) + s2);
+  if (p.mu > 0.0) {
+    // explicit diffusion limit of the viscous terms: k dx^2 / (6 max(mu / rho))
+    const double mr = __longlong_as_double((long long)smax[i * 4 + 3]);
+    const double hv = (p.cfl * (dxl * dxl)) / ((6.0 * p.mu) * mr);
+    h = (hv < h) ? hv : h;
+  }
+  dt[i] = h;
 }
 
 void launch_cfl(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax, double* dt,
                 int* status, cudaStream_t st) {
-  cudaMemsetAsync(smax, 0, sizeof(unsigned long long) * 3 * p.n_inst, st);
+  cudaMemsetAsync(smax, 0, sizeof(unsigned long long) * 4 * p.n_inst, st);
   if (p.precision == 1) launch_cfl_speeds_f32(t, p, pool, cur, smax, status, st);
   else {
     k_cfl<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, smax, status);

@@ -43,6 +43,7 @@ struct Topo {
 
 struct Phys {
   double gamma, B, cfl, dx0, eps;
+  double mu;               // dynamic viscosity of the Navier-Stokes terms; 0 = Euler
   double grav[3];
   int bc[6];
   int nb[3];

@@ -236,6 +236,57 @@ template <class R> __device__ __forceinline__ bool admissible(const R U[5], R g,
   return p + B > R(0.0);
 }
 
+// ---------------------------------------------------------------- viscous flux
+// Navier-Stokes viscous flux (Stokes' hypothesis, constant mu, no heat
+// conduction) at the face between the stored cells sL and sL + step_d of a
+// block (FP64 state with halos), lab frame: (0, tau_xd, tau_yd, tau_zd,
+// u . tau_d), tau_ij = mu (du_i/dx_j + du_j/dx_i) - 2/3 mu (div u) delta_ij.
+// Second-order compact face gradients: normal derivative from the two face
+// cells, tangential derivative as the mean of their central differences;
+// face velocity the mean of the two cells'.
+__device__ __forceinline__ void cell_vel(const double* __restrict__ u, int s, double w[3]) {
+  const double rho = u[s];
+  w[0] = u[NCELL + s] / rho;
+  w[1] = u[2 * NCELL + s] / rho;
+  w[2] = u[3 * NCELL + s] / rho;
+}
+
+__device__ __forceinline__ void viscous_flux(const double* __restrict__ u, int d, int sL, double mu, double dx,
+                                             double Fv[5]) {
+  const int step[3] = {1, NS, NS * NS};
+  const int sR = sL + step[d];
+  double uL[3], uR[3];
+  cell_vel(u, sL, uL);
+  cell_vel(u, sR, uR);
+  double G[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) G[i][d] = (uR[i] - uL[i]) / dx;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (j == d) continue;
+    double a[3], b[3], c[3], e[3];
+    cell_vel(u, sL + step[j], a);
+    cell_vel(u, sL - step[j], b);
+    cell_vel(u, sR + step[j], c);
+    cell_vel(u, sR - step[j], e);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) G[i][j] = ((a[i] - b[i]) + (c[i] - e[i])) / (4.0 * dx);
+  }
+  const double div = (G[0][0] + G[1][1]) + G[2][2];
+  double ub[3], tau[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    ub[i] = 0.5 * (uL[i] + uR[i]);
+    tau[i] = mu * (G[i][d] + G[d][i]);
+  }
+  tau[d] = tau[d] - ((2.0 / 3.0) * mu) * div;
+  Fv[0] = 0.0;
+  Fv[1] = tau[0];
+  Fv[2] = tau[1];
+  Fv[3] = tau[2];
+  Fv[4] = (ub[0] * tau[0] + ub[1] * tau[1]) + ub[2] * tau[2];
+}
+
 // ---------------------------------------------------------------- face flux
 // Numerical flux at the face between cells 2 and 3 of U6 (cells i-2 .. i+3
 // along d, lab-frame conserved states), returned in the lab frame.  Rotated

@@ -25,7 +25,8 @@ constexpr int RHS_THREADS = 256;
 // faces into the face buffers, then the flux differences into acc.
 template <class R, int D>
 __device__ __forceinline__ void rhs_dir(const double* __restrict__ u, double* __restrict__ fb, R* Fs, int z0, R g,
-                                        R B, int lin, int flux, double (&acc)[RHS_TZ][NV]) {
+                                        R B, int lin, int flux, double mu, double dx,
+                                        double (&acc)[RHS_TZ][NV]) {
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   constexpr int nf = (D == 2) ? NB * NB * (RHS_TZ + 1) : (NB + 1) * NB * RHS_TZ;
   constexpr int stride = (D == 0) ? 1 : (D == 1 ? NS : NS * NS);
@@ -58,6 +59,13 @@ __device__ __forceinline__ void rhs_dir(const double* __restrict__ u, double* __
       for (int v = 0; v < 5; ++v) U6[m][v] = R(u[v * NCELL + base + m * stride]);
     R F[5];
     face_flux<R>(U6, D, g, B, lin, flux, F);
+    if (mu > 0.0) {
+      // Navier-Stokes: F(U) - F_v at the face between stencil cells 2 and 3
+      double Fv[5];
+      viscous_flux(u, D, base + 2 * stride, mu, dx, Fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) F[v] = R(double(F[v]) - Fv[v]);
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fs[v * RHS_FMAX + f] = F[v];
     const int gface = (D == 2) ? z0 + fa : fa;
@@ -107,9 +115,10 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs_rk(Topo t, Phys p, Pool poo
     const double* __restrict__ u = src + (size_t)slot * SLOT_U;
     double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
     double acc[RHS_TZ][NV];
-    rhs_dir<R, 0>(u, fb, Fs, z0, g, B, lin, flux, acc);
-    rhs_dir<R, 1>(u, fb, Fs, z0, g, B, lin, flux, acc);
-    rhs_dir<R, 2>(u, fb, Fs, z0, g, B, lin, flux, acc);
+    const double dxn = ldexp(p.dx0, -t.level[node]);
+    rhs_dir<R, 0>(u, fb, Fs, z0, g, B, lin, flux, p.mu, dxn, acc);
+    rhs_dir<R, 1>(u, fb, Fs, z0, g, B, lin, flux, p.mu, dxn, acc);
+    rhs_dir<R, 2>(u, fb, Fs, z0, g, B, lin, flux, p.mu, dxn, acc);
     const int inst = t.inst[node];
     const double dx = ldexp(p.dx0, -t.level[node]);
     const double h = dt ? dt[inst] : 0.0;

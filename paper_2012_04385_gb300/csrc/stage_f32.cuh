@@ -242,7 +242,8 @@ __device__ __forceinline__ void cell_uf(const float* __restrict__ S, int c, Rot 
 // decisions stored), 3 learned selector at stages 1 and 2 (the stored
 // decision of each face picks linear or WENO5 for fields 0, 1, 4).
 // MODE 5 is WENO-AO(5,3).  Bits 3-4 of MODE select the flux scheme (0 Roe
-// with the LLF fallback, 1 LLF on every field, 2 HLLC) for MODES 0, 2, 4, 5.
+// with the LLF fallback, 1 LLF on every field, 2 HLLC) for MODES 0, 2, 4, 5;
+// bit 5 adds the viscous (Navier-Stokes) face fluxes.
 template <int MODE>
 __device__ __forceinline__ float rec5(bool lin, float a, float b, float c, float d, float e) {
   constexpr int REC = MODE & 7;
@@ -369,7 +370,7 @@ __device__ __forceinline__ void hllc_f32(const float UL[5], const float UR[5], f
 template <int MODE, bool FEAT>
 __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, Rot R, float gm1, float g,
                                               float B, bool lin, float F[5], float* feat = nullptr) {
-  constexpr int FLUX = MODE >> 3;
+  constexpr int FLUX = (MODE >> 3) & 3;
   float Ur[6][5], Fr[6][5];
 #pragma unroll
   for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, R, Ur[m], Fr[m]);
@@ -496,6 +497,55 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
   F[4] = Fh4;
 }
 
+// Velocity of the stored cell s of a block's FP64 state, in FP32.
+__device__ __forceinline__ void cell_vel_f32(const double* __restrict__ u, int s, float w[3]) {
+  const float ir = frcp(d2f_fast(u[s]));
+  w[0] = d2f_fast(u[NCELL + s]) * ir;
+  w[1] = d2f_fast(u[2 * NCELL + s]) * ir;
+  w[2] = d2f_fast(u[3 * NCELL + s]) * ir;
+}
+
+// F -= the viscous flux at the face between stored cells sL and sL + step_D
+// of the block (FP64 state with halos, arithmetic in FP32), F in the
+// direction frame of D: second-order compact gradients (normal derivative
+// from the two face cells, tangential ones as the mean of their central
+// differences), tau = mu (grad u + grad u^T) - 2/3 mu (div u) I, energy flux
+// u_face . tau_D.
+template <int D>
+__device__ __forceinline__ void sub_viscous_f32(const double* __restrict__ u, int sL, float mu, float idx,
+                                                float F[5]) {
+  constexpr int step[3] = {1, NS, NS * NS};
+  const int sR = sL + step[D];
+  float uL[3], uR[3];
+  cell_vel_f32(u, sL, uL);
+  cell_vel_f32(u, sR, uR);
+  float G[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) G[i][D] = (uR[i] - uL[i]) * idx;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (j == D) continue;
+    float a[3], b[3], c[3], e[3];
+    cell_vel_f32(u, sL + step[j], a);
+    cell_vel_f32(u, sL - step[j], b);
+    cell_vel_f32(u, sR + step[j], c);
+    cell_vel_f32(u, sR - step[j], e);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) G[i][j] = ((a[i] - b[i]) + (c[i] - e[i])) * (0.25f * idx);
+  }
+  const float div = G[0][0] + G[1][1] + G[2][2];
+  float tau[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) tau[i] = mu * (G[i][D] + G[D][i]);
+  tau[D] = fmaf(-2.f / 3.f * mu, div, tau[D]);
+  const float E = fmaf(0.5f * (uL[0] + uR[0]), tau[0],
+                       fmaf(0.5f * (uL[1] + uR[1]), tau[1], 0.5f * (uL[2] + uR[2]) * tau[2]));
+  F[1] -= tau[D];
+  F[2] -= tau[(D + 1) % 3];
+  F[3] -= tau[(D + 2) % 3];
+  F[4] -= E;
+}
+
 // Selector features of the face between records c0+2st and c0+3st (the
 // same arithmetic as the stage-0 kernel's).
 __device__ __forceinline__ void face_features_f32(const float* __restrict__ S, int c0, int st, Rot R, const RoeF& e,
@@ -608,7 +658,8 @@ __device__ __forceinline__ void face_of(int D, int f, int z0, int& fa, int& c0, 
   }
 }
 
-// Learned-selector state of a CTA (MODES 1 and 3).
+// Per-CTA state of the learned selector (MODES 1 and 3) and of the viscous
+// variants (MODE bit 5).
 struct LearnedCtx {
   const float* P;            // FP32 parameters (biases read from here)
   const uint32_t* frag;      // BF16 B fragments in shared memory
@@ -619,6 +670,7 @@ struct LearnedCtx {
   uint32_t* bits;            // this block's decision words (SLOT_SEL)
   float z0;                  // the network's logit for all-zero features
   const uint32_t* selw;      // MODE 3: the slab's 108 decision words, staged in shared memory
+  float mu, idx;             // viscous variants: dynamic viscosity and 1 / dx of the block
 };
 
 // True when the six stencil records are identical, in which case every
@@ -770,6 +822,7 @@ __device__ __forceinline__ void sweep_xy(const double* __restrict__ u, double* _
       const int c0 = xy_slot(fa - 3, r % 16, r / 16);
       const bool lin = (MODE == 3) && ((L.selw[f >> 5] >> (threadIdx.x & 31)) & 1u);
       face_flux_f32<MODE, false>(S, c0, 1, rot_of(0), gm1, g, B, lin, F);
+      if (MODE & 32) sub_viscous_f32<0>(u, sidx(fa - 1, r % 16, z0 + r / 16), L.mu, L.idx, F);
       store_face(0, F, Fs, SF_FMAX, f, fa, r % 16, z0 + r / 16, fb);
     } else {                              // y face
       const int fy = f - SF_NFX;
@@ -778,6 +831,7 @@ __device__ __forceinline__ void sweep_xy(const double* __restrict__ u, double* _
       const int c0 = xy_slot(i, fa - 3, kz);
       const bool lin = (MODE == 3) && ((L.selw[34 + (fy >> 5)] >> (threadIdx.x & 31)) & 1u);
       face_flux_f32<MODE, false>(S, c0, 22, rot_of(1), gm1, g, B, lin, F);
+      if (MODE & 32) sub_viscous_f32<1>(u, sidx(i, fa - 1, z0 + kz), L.mu, L.idx, F);
       store_face(1, F, Fs, SF_FMAX, f, fa, i, z0 + kz, fb);
     }
   }
@@ -813,6 +867,7 @@ __device__ __forceinline__ void sweep_z(const double* __restrict__ u, double* __
     const bool lin = (MODE == 3) && ((L.selw[68 + (f >> 5)] >> (threadIdx.x & 31)) & 1u);
     float F[5];
     face_flux_f32<MODE, false>(S, c0, 256, rot_of(2), gm1, g, B, lin, F);
+    if (MODE & 32) sub_viscous_f32<2>(u, sidx(i, j, z0 + fa - 1), L.mu, L.idx, F);
     store_face(2, F, Fs, SF_FMAX, f, z0 + fa, i, j, fb);
   }
   __syncthreads();
@@ -837,7 +892,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
   const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   __shared__ uint32_t sel_sh[108];
-  LearnedCtx L{nullptr, nullptr, nullptr, nullptr, 0.f, nullptr, nullptr, 0.f, sel_sh};
+  LearnedCtx L{nullptr, nullptr, nullptr, nullptr, 0.f, nullptr, nullptr, 0.f, sel_sh, (float)p.mu, 0.f};
   if (MODE == 1) {
     uint32_t* frag = reinterpret_cast<uint32_t*>(Fs + NV * SF_NFZ);   // after one direction's face fluxes
     L.P = p.mlp;
@@ -866,6 +921,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     const double* __restrict__ u = src + (size_t)slot * SLOT_U;
     double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
     if (MODE == 1 || MODE == 3) L.bits = pool.sel + (size_t)slot * SLOT_SEL;
+    if (MODE & 32) L.idx = d2f_fast(ldexp(1.0 / p.dx0, t.level[node]));
     // the slab's decision words (read before the first barrier of the sweep)
     if (MODE == 3 && threadIdx.x < 108) sel_sh[threadIdx.x] = L.bits[(z0 / SF_TZ) * 108 + threadIdx.x];
     float acc[SF_TZ][NV];

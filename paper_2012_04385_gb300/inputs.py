@@ -44,6 +44,7 @@ class RunConfig:
     recon: int = RECON_WENO
     rk_stages: int = 3          # 3: TVD-RK3, 2: TVD-RK2
     flux: int = FLUX_ROE        # Roe with per-field LLF fallback, LLF, or HLLC
+    mu: float = 0.0             # dynamic viscosity (Navier-Stokes terms); 0 = Euler
     mlp_tau: float = 0.0
     name: str = "custom"
 
@@ -92,6 +93,68 @@ def rt_config(lmax: int = 5, **kw) -> RunConfig:
                   gravity=(0.0, 0.0, -1.0), eps=1e-3,
                   bc=(BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_SYMMETRY, BC_SYMMETRY))
     return dataclasses.replace(c, **kw)
+
+
+# Fluid properties of the viscous single-mode Rayleigh-Taylor growth-rate study
+# by Atwood number: rho_heavy, rho_light, mu (the table of the RTI section).
+RTI_FLUIDS = {0.5: (1.5, 0.5, 0.1), 0.998: (99.9, 0.1, 0.5)}
+
+
+def rti_growth_config(k: float, atwood: float = 0.5, lmax: int = 2, **kw) -> RunConfig:
+    """Viscous single-mode Rayleigh-Taylor set-up of the growth-rate study:
+    the short side (x) spans one wavelength 2 pi / k between symmetry walls,
+    the long side (z, gravity -1) ten wavelengths between walls, one block in y
+    (periodic, the flow is y-invariant); 16 cells per wavelength at level 0,
+    so lmax = 2 gives 64 (the paper's lmax = 3 gives 128)."""
+    lam = 2.0 * math.pi / k
+    c = RunConfig(name=f"rti_k{k:g}_at{atwood:g}_l{lmax}", base_blocks=(1, 1, 10), lmax=(lmax,), dx0=lam / 16.0,
+                  gravity=(0.0, 0.0, -1.0), mu=RTI_FLUIDS[atwood][2], eps=1e-3,
+                  bc=(BC_SYMMETRY, BC_SYMMETRY, BC_PERIODIC, BC_PERIODIC, BC_SYMMETRY, BC_SYMMETRY))
+    return dataclasses.replace(c, **kw)
+
+
+def ic_rti_single_mode(cfg, geo, k: float, atwood: float = 0.5, p_interface: float | None = None):
+    """Heavy over light fluid, interface z = 5 lambda + (0.05 / k) cos(k x)
+    with a tanh edge two finest cells wide, at rest, hydrostatic pressure of
+    the unperturbed layers (p at the interface chosen so that the top stays at
+    p >= 10: low Mach number)."""
+    rho_h, rho_l, _ = RTI_FLUIDS[atwood]
+    lam = 2.0 * math.pi / k
+    z0, g = 5.0 * lam, -cfg.gravity[2]
+    if p_interface is None:
+        p_interface = 10.0 + rho_h * g * 5.0 * lam
+    X, _, Z, _ = cell_centres(cfg, geo)
+    width = 2.0 * cfg.dx0 * 0.5 ** cfg.lmax_of(0)
+    zi = z0 + (0.05 / k) * np.cos(k * X)
+    s = 0.5 * (1.0 + np.tanh((Z - zi) / width))
+    out = _prim(len(geo))
+    out[:, 0] = rho_l + (rho_h - rho_l) * s
+    out[:, 4] = np.where(Z < z0, p_interface + rho_l * g * (z0 - Z), p_interface - rho_h * g * (Z - z0))
+    return out
+
+
+def rti_growth_rate_theory(k: float, atwood: float = 0.5, g: float = 1.0) -> float:
+    """Growth rate n > 0 of the viscous single-mode RTI in the linear regime,
+    equal dynamic viscosities, no surface tension: the root of
+    -{g k / n^2 (a_l - a_h) + 1}(a_h q_l + a_l q_h - k) - 4 k a_l a_h = 0,
+    q_i = sqrt(k^2 + n / nu_i), a_i = rho_i / (rho_l + rho_h) (Eq.
+    SinglePhaseGrowth), found by bisection."""
+    rho_h, rho_l, mu = RTI_FLUIDS[atwood]
+    ah, al = rho_h / (rho_h + rho_l), rho_l / (rho_h + rho_l)
+    nuh, nul = mu / rho_h, mu / rho_l
+
+    def f(n):
+        ql, qh = math.sqrt(k * k + n / nul), math.sqrt(k * k + n / nuh)
+        return -(g * k / (n * n) * (al - ah) + 1.0) * (ah * ql + al * qh - k) - 4.0 * k * al * ah
+    lo, hi = 1e-9, math.sqrt(g * k)            # the inviscid rate sqrt(At g k) bounds it from above
+    assert f(lo) * f(hi) < 0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(lo) * f(mid) <= 0:
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
 
 
 def periodic_config(base=(2, 2, 2), lmax=0, **kw) -> RunConfig:

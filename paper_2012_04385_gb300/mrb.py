@@ -49,6 +49,7 @@ class MrbConfig(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("gravity", ctypes.c_double * 3),
         ("eps", ctypes.c_double),
+        ("mu", ctypes.c_double),
         ("mlp_weights", ctypes.c_void_p),
         ("mlp_tau", ctypes.c_double),
         ("stream", ctypes.c_void_p),
@@ -129,6 +130,7 @@ def make_config(cfg: RunConfig, stream_ptr: int = 0) -> MrbConfig:
     c.B = float(cfg.B)
     c.cfl = float(cfg.cfl)
     c.eps = float(cfg.eps)
+    c.mu = float(getattr(cfg, "mu", 0.0))
     c.mlp_weights = None
     c.mlp_tau = float(cfg.mlp_tau)
     c.stream = stream_ptr or None

@@ -420,3 +420,59 @@ def test_fp32_bulk_rhs_vs_oracle(recon, flux):
         assert np.median(err) < 1e-7
     else:
         assert err.max() < 2e-5
+
+
+# ------------------------------------------------------------------ viscous terms
+def test_viscous_rhs_time_step_and_steps():
+    """Navier-Stokes terms (mu > 0), FP64: the right-hand side on a tree with
+    jumps of one and two levels, the time step with the viscous limit active
+    (smaller than the convective one) and 3 MR explosion steps with remeshing,
+    against the oracle; the FP32 bulk path's right-hand side within 2e-5 of
+    each variable's largest |L|."""
+    plans = (ALL, SOME, lambda geo: (geo[:, 0] == 2) & (geo[:, 1] % 2 == 0))
+    cfg = I.explosion_config(lmax=3, mu=0.02)
+    o, g = make_pair(cfg, rnd(4, mild=True), plans)
+    o.fill_halos()
+    g.fill_halos()
+    ref = o.compute_rhs()
+    close(g.compute_rhs().cpu().numpy(), ref, what="viscous rhs")
+    dt_o = o.cfl_dt()
+    close(g.cfl_dt().cpu().numpy(), dt_o, what="viscous dt")
+    o0, _ = make_pair(I.explosion_config(lmax=3), rnd(4, mild=True), plans)
+    assert (dt_o < 0.5 * o0.cfl_dt()).all()               # the viscous limit decides
+    # FP32 bulk right-hand side with the viscous terms
+    g32 = mrb.Context(I.explosion_config(lmax=3, mu=0.02, precision=I.FP32_ACC64), g.n_slots)
+    mrb.restore_tree(g32, o.keys(leaves_only=False))
+    kl = o.keys()
+    g32.set_cons(kl, torch.from_numpy(o.get_state(kl)).cuda())
+    g32.mr_project()
+    g32.fill_halos()
+    got = g32.compute_rhs().cpu().numpy()
+    scale = np.abs(ref).max(axis=(0, 2, 3, 4), keepdims=True)
+    err = np.abs(got - ref) / scale
+    print("viscous fp32 rhs max error relative to max|L| per variable:", err.max())
+    assert err.max() < 2e-5
+    # full steps with remeshing
+    cfg = I.explosion_config(lmax=2, mu=0.002)
+    o = oracle.Oracle(cfg)
+    g = mrb.Context(cfg, 8 * 80)
+    mrb.init_tree(g, lambda c, geo: I.ic_explosion(c, geo))
+    o.set_state(o.keys(), I.ic_explosion(cfg, o.geometry()))
+    for m in range(1, 3):
+        o.fill_halos()
+        geo = o.geometry()
+        o.remesh((geo[:, 0] == m - 1).astype(np.int8))
+        o.set_state(o.keys(level=m), I.ic_explosion(cfg, o.geometry(level=m)))
+        if m > 1:
+            o.fill_halos()
+            t, _ = o.predict_and_tag(allow_refine=False)
+            o.remesh(t)
+    o.project()
+    assert np.array_equal(o.keys(leaves_only=False), g.keys(leaves_only=False))
+    dts_o = o.step(3)
+    dts_g = torch.empty((3, 1), dtype=torch.float64, device="cuda")
+    g.step(3, dts_g)
+    assert np.array_equal(o.keys(leaves_only=False), g.keys(leaves_only=False))
+    k = o.keys()
+    close(g.get_state(k).cpu().numpy(), o.get_state(k), what="viscous explosion MR 3 steps")
+    close(dts_g.cpu().numpy(), dts_o, what="viscous dt history")

@@ -1,9 +1,12 @@
 """The paper-shaped workloads on the GPU against the oracle: the shock-bubble
 interaction and the Rayleigh-Taylor layer (gravity source, symmetry walls) on
 small trees, the MR explosion at its full size (levels 0..3, 256^3
-effective) in the launch configuration the benchmark times, and free-stream
-preservation on every GPU path across resolution jumps.
+effective) in the launch configuration the benchmark times, free-stream
+preservation on every GPU path across resolution jumps, and the viscous
+single-mode Rayleigh-Taylor growth rate against the linear theory.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -97,7 +100,7 @@ def selector():
 
 
 @pytest.mark.parametrize("path", ["fp64", "fp32_weno", "fp32_linear", "fp32_learned", "fp64_hllc", "fp32_hllc",
-                                  "fp32_llf", "fp32_wenoao"])
+                                  "fp32_llf", "fp32_wenoao", "fp64_viscous", "fp32_viscous"])
 def test_free_stream_preserved(path, selector):
     """A uniform state on a tree with resolution jumps: the RHS is bitwise
     zero (identical face fluxes cancel; prediction of a constant is exact), so
@@ -111,6 +114,8 @@ def test_free_stream_preserved(path, selector):
         kw["flux"] = I.FLUX_LLF
     if path == "fp32_wenoao":
         kw["recon"] = I.RECON_WENOAO
+    if path.endswith("viscous"):
+        kw["mu"] = 0.01
     if path == "fp32_linear":
         kw["recon"] = I.RECON_LINEAR
     if path == "fp32_learned":
@@ -136,3 +141,65 @@ def test_free_stream_preserved(path, selector):
         assert vals.size == 1, (path, v)
         ref = u0[0, v, 0, 0, 0]
         assert abs(vals[0] - ref) <= 2 * 4 * np.spacing(abs(ref)) + 1e-300, (path, v)
+
+
+def _centreline_interface(g, cfg, k, mid):
+    """Height of the interface (the crossing of the mid density) on the
+    vertical centreline x = lambda / 2, from the leaves that hold it (cell
+    values weighted linearly around x = lambda / 2, averaged over y)."""
+    lam = 2.0 * math.pi / k
+    keys, geo = g.list_blocks()
+    dxs = cfg.dx0 * 0.5 ** geo[:, 0]
+    x0 = geo[:, 1] * 16 * dxs
+    sel = (x0 <= lam / 2) & (x0 + 16 * dxs >= lam / 2)
+    U = g.get_state(keys[sel]).cpu().numpy()
+    zs, rs = [], []
+    for b, (lvl, X, _, Z) in enumerate(geo[sel]):
+        dx = cfg.dx0 * 0.5 ** lvl
+        xc = (X * 16 + np.arange(16) + 0.5) * dx
+        w = np.maximum(0.0, 1.0 - np.abs(xc - lam / 2) / dx)
+        if w.sum() == 0:
+            continue
+        zs.append((Z * 16 + np.arange(16) + 0.5) * dx)
+        rs.append(((U[b, 0] * w).sum(axis=2) / w.sum()).mean(axis=1))
+    z, r = np.concatenate(zs), np.concatenate(rs)
+    o = np.argsort(z, kind="stable")
+    z, r = z[o], r[o]
+    i = np.where((r[:-1] - mid) * (r[1:] - mid) <= 0)[0]
+    j = i[np.argmin(np.abs(z[i] - 5.0 * lam))]
+    return z[j] + (mid - r[j]) * (z[j + 1] - z[j]) / (r[j + 1] - r[j])
+
+
+@pytest.mark.parametrize("k", [2.0, 5.0])
+def test_viscous_rti_growth_rate_vs_linear_theory(k):
+    """Sec. 5's viscous Rayleigh-Taylor growth-rate study (At = 0.5, mu = 0.1,
+    g = 1, equal dynamic viscosities): a single mode of wavenumber k on a
+    lambda x 10 lambda column (64 cells per wavelength at the finest level),
+    FP32 bulk path with the viscous terms and gravity.  The interface
+    displacement d(t) on the centreline grows as exp(n t); n is fitted on
+    2 <= d / d(0) <= 6 (still linear: k d <= 0.3) and must match the root of
+    Eq. (SinglePhaseGrowth) within 5%."""
+    cfg = I.rti_growth_config(k, precision=I.FP32_ACC64)
+    lam = 2.0 * math.pi / k
+    rho_h, rho_l, _ = I.RTI_FLUIDS[0.5]
+    mid = 0.5 * (rho_h + rho_l)
+    g = mrb.Context(cfg, 6000)
+    mrb.init_tree(g, lambda c, geo: I.ic_rti_single_mode(c, geo, k))
+    d0 = 5.0 * lam - _centreline_interface(g, cfg, k, mid)
+    assert abs(d0 - 0.05 / k) < 0.1 * 0.05 / k
+    n_th = I.rti_growth_rate_theory(k)
+    dts = torch.empty((50, 1), dtype=torch.float64, device="cuda")
+    t, ts, ds = 0.0, [0.0], [d0]
+    while ds[-1] / d0 < 7.0 and t < 15.0 / n_th:
+        g.step(50, dts)
+        t += float(dts.sum())
+        ts.append(t)
+        ds.append(5.0 * lam - _centreline_interface(g, cfg, k, mid))
+    assert g.status() == mrb.MRB_OK
+    ts, ratio = np.array(ts), np.array(ds) / d0
+    w = (ratio >= 2.0) & (ratio <= 6.0)
+    assert w.sum() >= 5
+    n_fit = np.polyfit(ts[w], np.log(ratio[w]), 1)[0]
+    print(f"k = {k}: growth rate {n_fit:.4f}, linear theory {n_th:.4f}, relative {(n_fit - n_th) / n_th:+.3f}, "
+          f"t = {t:.2f}, {g.n_leaves()} leaves")
+    assert abs(n_fit - n_th) <= 0.05 * n_th

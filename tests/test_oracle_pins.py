@@ -556,8 +556,12 @@ def test_free_stream_with_jumps():
         assert abs(vals[0] - ref) <= 2 * 3 * np.spacing(abs(ref)) + 1e-300
 
 
-def test_conservation_periodic_with_jumps():
-    cfg = I.periodic_config(base=(2, 2, 2), lmax=2, eps=1e-4)
+@pytest.mark.parametrize("mu", [0.0, 0.02])
+def test_conservation_periodic_with_jumps(mu):
+    """Periodic domain with resolution jumps: mass, momentum and energy are
+    conserved to round-off over 6 steps with remeshing (Euler, and with the
+    viscous terms, whose boundary-face fluxes enter the jump correction)."""
+    cfg = I.periodic_config(base=(2, 2, 2), lmax=2, eps=1e-4, mu=mu)
     o = oracle.Oracle(cfg)
     o.set_state(o.keys(), I.ic_random_smooth(cfg, o.geometry()))
     o.fill_halos()
@@ -749,3 +753,86 @@ def test_tags_refine_at_discontinuity_and_valid_octree():
         m = k & ((1 << 56) - 1)
         if oracle.key_level(k) > 0:
             assert (k >> 56 << 56) | (m >> 3) in allk
+
+
+# ------------------------------------------------------------------ viscous terms
+def _linear_velocity_state(cfg, geo, A, u0, rho=1.3, p=2.0):
+    X, Y, Z, _ = I.cell_centres(cfg, geo)
+    out = np.zeros((len(geo), 5, 16, 16, 16))
+    out[:, 0] = rho
+    for i in range(3):
+        out[:, 1 + i] = u0[i] + A[i, 0] * X + A[i, 1] * Y + A[i, 2] * Z
+    out[:, 4] = p
+    return out
+
+
+def test_viscous_terms_on_a_linear_velocity_field():
+    """u = u0 + A x with uniform rho and p: every face gradient of the compact
+    stencils is exact, the stress tau = mu (A + A^T - 2/3 tr(A) I) is uniform,
+    so the viscous part of the right-hand side is zero in the momenta and
+    tau : A (the dissipation) in the energy.  Checked on the cells whose
+    viscous stencils stay inside the domain, as L(mu) - L(0)."""
+    A = np.array([[0.11, -0.07, 0.05], [0.03, -0.04, 0.09], [-0.08, 0.02, 0.06]])
+    u0 = np.array([0.2, -0.1, 0.15])
+    mu = 0.03
+    Ls = []
+    for m in (0.0, mu):
+        cfg = I.explosion_config(lmax=0, mu=m)
+        o = oracle.Oracle(cfg)
+        o.set_state(o.keys(), _linear_velocity_state(cfg, o.geometry(), A, u0))
+        o.fill_halos()
+        Ls.append(o.compute_rhs())
+    geo = o.geometry()
+    dL = Ls[1] - Ls[0]
+    tau = mu * (A + A.T) - (2.0 / 3.0) * mu * np.trace(A) * np.eye(3)
+    diss = float((tau * A).sum())
+    # cells at least 2 cells from the domain boundary (32^3 cells over 2^3 blocks)
+    idx = np.arange(16)
+    inner = []
+    for b, (_, X, Y, Z) in enumerate(geo):
+        gx, gy, gz = X * 16 + idx, Y * 16 + idx, Z * 16 + idx
+        mx = (gx >= 2) & (gx <= 29)
+        my = (gy >= 2) & (gy <= 29)
+        mz = (gz >= 2) & (gz <= 29)
+        inner.append(mz[:, None, None] & my[None, :, None] & mx[None, None, :])
+    inner = np.array(inner)
+    for v in range(1, 4):
+        assert np.abs(dL[:, v][inner]).max() < 1e-12, v
+    assert np.abs(dL[:, 4][inner] - diss).max() < 1e-12 * max(1.0, abs(diss)) + 1e-13
+    assert abs(diss) > 1e-4
+
+
+def test_viscous_shear_wave_decay_is_second_order():
+    """A transverse velocity wave v = U sin(2 pi x) in a uniform gas at rest
+    decays as exp(-nu k^2 t) (the momentum equation reduces to the diffusion
+    equation; the inviscid fluxes vanish identically).  The observed decay of
+    the wave's discrete Fourier coefficient approaches the exact one at second
+    order (the compact viscous gradients); the scheme under-damps."""
+    nu, U, T = 0.05, 0.01, 0.1
+    k = 2.0 * math.pi
+    errs = []
+    for n in (16, 32):
+        cfg = I.periodic_config(base=(n // 16, 1, 1), mu=nu)
+        cfg.dx0 = 1.0 / n
+        o = oracle.Oracle(cfg)
+        geo = o.geometry()
+        X, Y, Z, dx = I.cell_centres(cfg, geo)
+        h = dx[:, None, None, None]
+        prim = np.zeros((len(geo), 5, 16, 16, 16))
+        prim[:, 0] = 1.0
+        prim[:, 2] = U * (np.cos(k * (X - 0.5 * h)) - np.cos(k * (X + 0.5 * h))) / (k * h)   # cell averages
+        prim[:, 4] = 1.0
+        o.set_state(o.keys(), prim)
+
+        def coeff():
+            Ust = o.get_state()
+            return float((Ust[:, 2] * np.sin(k * X)).sum())
+        c0 = coeff()
+        run_fixed_dt(o, 0.2 * (1.0 / n) ** 2 / nu, T)
+        ratio = coeff() / c0
+        exact = math.exp(-nu * k * k * T)
+        errs.append(math.log(ratio) - math.log(exact))
+    print("shear wave: log-decay errors", errs)
+    assert errs[0] > 0 and errs[1] > 0                 # under-damped
+    assert 3.5 <= errs[0] / errs[1] <= 4.5             # second order
+    assert errs[1] < 1e-3
