@@ -133,30 +133,6 @@ def ic_rti_single_mode(cfg, geo, k: float, atwood: float = 0.5, p_interface: flo
     return out
 
 
-def rti_growth_rate_theory(k: float, atwood: float = 0.5, g: float = 1.0) -> float:
-    """Growth rate n > 0 of the viscous single-mode RTI in the linear regime,
-    equal dynamic viscosities, no surface tension: the root of
-    -{g k / n^2 (a_l - a_h) + 1}(a_h q_l + a_l q_h - k) - 4 k a_l a_h = 0,
-    q_i = sqrt(k^2 + n / nu_i), a_i = rho_i / (rho_l + rho_h) (Eq.
-    SinglePhaseGrowth), found by bisection."""
-    rho_h, rho_l, mu = RTI_FLUIDS[atwood]
-    ah, al = rho_h / (rho_h + rho_l), rho_l / (rho_h + rho_l)
-    nuh, nul = mu / rho_h, mu / rho_l
-
-    def f(n):
-        ql, qh = math.sqrt(k * k + n / nul), math.sqrt(k * k + n / nuh)
-        return -(g * k / (n * n) * (al - ah) + 1.0) * (ah * ql + al * qh - k) - 4.0 * k * al * ah
-    lo, hi = 1e-9, math.sqrt(g * k)            # the inviscid rate sqrt(At g k) bounds it from above
-    assert f(lo) * f(hi) < 0
-    for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        if f(lo) * f(mid) <= 0:
-            hi = mid
-        else:
-            lo = mid
-    return 0.5 * (lo + hi)
-
-
 def periodic_config(base=(2, 2, 2), lmax=0, **kw) -> RunConfig:
     c = RunConfig(name="periodic", base_blocks=tuple(base), lmax=(lmax,), dx0=1.0 / (16 * max(base)),
                   bc=(BC_PERIODIC,) * 6)

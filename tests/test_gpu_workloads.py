@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from paper_2012_04385_gb300 import inputs as I
+from rti_theory import growth_rate
 
 pytestmark = pytest.mark.gpu
 
@@ -187,7 +188,7 @@ def test_viscous_rti_growth_rate_vs_linear_theory(k):
     mrb.init_tree(g, lambda c, geo: I.ic_rti_single_mode(c, geo, k))
     d0 = 5.0 * lam - _centreline_interface(g, cfg, k, mid)
     assert abs(d0 - 0.05 / k) < 0.1 * 0.05 / k
-    n_th = I.rti_growth_rate_theory(k)
+    n_th = growth_rate(k, rho_h, rho_l, I.RTI_FLUIDS[0.5][2])
     dts = torch.empty((50, 1), dtype=torch.float64, device="cuda")
     t, ts, ds = 0.0, [0.0], [d0]
     while ds[-1] / d0 < 7.0 and t < 15.0 / n_th:

@@ -836,3 +836,18 @@ def test_viscous_shear_wave_decay_is_second_order():
     assert errs[0] > 0 and errs[1] > 0                 # under-damped
     assert 3.5 <= errs[0] / errs[1] <= 4.5             # second order
     assert errs[1] < 1e-3
+
+
+def test_rti_linear_theory_limits():
+    """The growth-rate relation used by the GPU RTI test: as mu -> 0 it tends
+    to the inviscid rate sqrt(At g k); viscosity lowers it, more so at large
+    k; the returned root satisfies the relation."""
+    import sys
+    sys.path.insert(0, HERE)
+    from rti_theory import growth_rate
+    for k in (1.0, 5.0, 20.0):
+        n0 = growth_rate(k, 1.5, 0.5, 1e-9)
+        assert abs(n0 - math.sqrt(0.5 * k)) < 1e-3 * math.sqrt(0.5 * k)
+    n = [growth_rate(k, 1.5, 0.5, 0.1) for k in (1.0, 2.0, 5.0, 10.0, 20.0)]
+    assert all(a < math.sqrt(0.5 * k) for a, k in zip(n, (1.0, 2.0, 5.0, 10.0, 20.0)))
+    assert n[1] > n[2] > n[3] > n[4]                  # damped at short wavelengths
