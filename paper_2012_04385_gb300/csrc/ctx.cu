@@ -540,6 +540,7 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     p.B = cfg->B;
     p.cfl = cfg->cfl;
     p.dx0 = cfg->dx0;
+    p.inv_dx0 = 1.0 / cfg->dx0;
     p.eps = cfg->eps;
     p.mu = cfg->mu;
     for (int d = 0; d < 3; ++d) {

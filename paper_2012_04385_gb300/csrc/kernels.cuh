@@ -44,6 +44,7 @@ struct Topo {
 struct Phys {
   double gamma, B, cfl, dx0, eps;
   double mu;               // dynamic viscosity of the Navier-Stokes terms; 0 = Euler
+  double inv_dx0;          // 1 / dx0 (1 / dx of level l is its exact 2^l multiple)
   double grav[3];
   int bc[6];
   int nb[3];

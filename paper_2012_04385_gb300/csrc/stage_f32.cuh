@@ -918,6 +918,15 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     const int li = w / SF_NSLAB, z0 = (w % SF_NSLAB) * SF_TZ;
     const int node = t.leaves[li];
     const int slot = t.slot[node];
+    // the update's per-block scalars, loaded here so that their latency is
+    // hidden behind the sweeps (after them in the register-bound selector
+    // variant)
+    int lvl = 0;
+    double h = 0.0;
+    if (MODE != 1) {
+      lvl = t.level[node];
+      h = dt ? dt[t.inst[node]] : 0.0;
+    }
     const double* __restrict__ u = src + (size_t)slot * SLOT_U;
     double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
     if (MODE == 1 || MODE == 3) L.bits = pool.sel + (size_t)slot * SLOT_SEL;
@@ -938,46 +947,66 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
       sweep_xy<MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
       sweep_z<MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
     }
-    const double dx = ldexp(p.dx0, -t.level[node]);
-    const double idx_ = 1.0 / dx;
-    const double h = dt ? dt[t.inst[node]] : 0.0;
+    if (MODE == 1) {
+      lvl = t.level[node];
+      h = dt ? dt[t.inst[node]] : 0.0;
+    }
+    // 1 / dx = 2^level / dx0 (exact power-of-two scaling, no division)
+    const double idx_ = ldexp(p.inv_dx0, lvl);
     const double hdx = h * idx_;
     // the stage increment b_s dt / dx (sum of flux differences) is formed in
     // FP32 and accumulated into the FP64 state
     const double ka = kRkA[rk_row(p)][stage], kb = kRkB[rk_row(p)][stage];
     const float hf = d2f_fast(hdx), bhf = d2f_fast(kb * hdx);
+    // the thread's four cells in groups of KC: every FP64 operand of a group is
+    // loaded before its first store, so those loads are in flight together
+    // (groups of one cell in the register-bound selector variant)
+    constexpr int KC = (MODE == 1) ? 1 : SF_TZ;
 #pragma unroll
-    for (int kz = 0; kz < SF_TZ; ++kz) {
-      const int k = z0 + kz;
-      const int s = sidx(ti, tj, k), ii = iidx(ti, tj, k);
-      double S4[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      if (p.has_grav) {
-        const double rho = u[s], mx = u[NCELL + s], my = u[2 * NCELL + s], mz = u[3 * NCELL + s];
-        S4[1] = rho * p.grav[0];
-        S4[2] = rho * p.grav[1];
-        S4[3] = rho * p.grav[2];
-        S4[4] = fma(mx, p.grav[0], fma(my, p.grav[1], mz * p.grav[2]));
+    for (int k0 = 0; k0 < SF_TZ; k0 += KC) {
+      double us[KC][NV], un[KC][NV];
+#pragma unroll
+      for (int c = 0; c < KC; ++c) {
+        const int s = sidx(ti, tj, z0 + k0 + c), ii = iidx(ti, tj, z0 + k0 + c);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          us[c][v] = u[v * NCELL + s];
+          un[c][v] = (stage != 0 && !rhs_out) ? pool.un[(size_t)slot * SLOT_N + v * NINT + ii] : 0.0;
+        }
       }
-      if (rhs_out) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) rhs_out[((size_t)li * NV + v) * NINT + ii] = fma(f2d_fast(acc[kz][v]), idx_, S4[v]);
-      } else {
-        double* __restrict__ unb = pool.un + (size_t)slot * SLOT_N;
-        double* __restrict__ o = dst + (size_t)slot * SLOT_U;
+      for (int c = 0; c < KC; ++c) {
+        const int kz = k0 + c, k = z0 + kz;
+        const int s = sidx(ti, tj, k), ii = iidx(ti, tj, k);
+        double S4[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        if (p.has_grav) {
+          const double rho = us[c][0], mx = us[c][1], my = us[c][2], mz = us[c][3];
+          S4[1] = rho * p.grav[0];
+          S4[2] = rho * p.grav[1];
+          S4[3] = rho * p.grav[2];
+          S4[4] = fma(mx, p.grav[0], fma(my, p.grav[1], mz * p.grav[2]));
+        }
+        if (rhs_out) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const double us = u[v * NCELL + s];
-          double out;
-          if (stage == 0) {
-            unb[v * NINT + ii] = us;
-            out = us + f2d_fast(acc[kz][v] * hf);
-            if (p.has_grav) out = fma(h, S4[v], out);
-          } else {
-            double inc = f2d_fast(acc[kz][v] * bhf);
-            if (p.has_grav) inc = fma(kb * h, S4[v], inc);
-            out = fma(ka, unb[v * NINT + ii], fma(kb, us, inc));
+          for (int v = 0; v < 5; ++v)
+            rhs_out[((size_t)li * NV + v) * NINT + ii] = fma(f2d_fast(acc[kz][v]), idx_, S4[v]);
+        } else {
+          double* __restrict__ unb = pool.un + (size_t)slot * SLOT_N;
+          double* __restrict__ o = dst + (size_t)slot * SLOT_U;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            double out;
+            if (stage == 0) {
+              unb[v * NINT + ii] = us[c][v];
+              out = us[c][v] + f2d_fast(acc[kz][v] * hf);
+              if (p.has_grav) out = fma(h, S4[v], out);
+            } else {
+              double inc = f2d_fast(acc[kz][v] * bhf);
+              if (p.has_grav) inc = fma(kb * h, S4[v], inc);
+              out = fma(ka, un[c][v], fma(kb, us[c][v], inc));
+            }
+            o[v * NCELL + s] = out;
           }
-          o[v * NCELL + s] = out;
         }
       }
     }
