@@ -178,7 +178,7 @@ def roofline_numbers(linear_fraction=0.0):
 # capture summarised in profiles/stage_kernels_explosion_256.md (levels 0-2
 # explosion; traffic grows in proportion to the leaf cells of a launch).
 # Learned path: the mean over its stage-0 and stage-1/2 variants (1 + 2 launches).
-TRAFFIC_BYTES_PER_CELL = {"learned": (148.0 + 154.9 + 155.1) / 3, "weno": (146.6 + 154.0 + 154.0) / 3}
+TRAFFIC_BYTES_PER_CELL = {"learned": (148.2 + 155.0 + 155.1) / 3, "weno": (146.6 + 154.0 + 154.3) / 3}
 
 
 def measured_peaks():
