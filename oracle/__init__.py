@@ -22,7 +22,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "orc.cpp")
-_LIB = os.path.join(_HERE, "liborc.so")
+# ORC_LIB names an already built oracle library to load instead (the tests
+# that plant mistakes in copies of orc.cpp use it); nothing is compiled then.
+_LIB = os.environ.get("ORC_LIB") or os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -30,8 +32,16 @@ NB, HW, NS, NV = 16, 4, 24, 5
 TAG_KEEP, TAG_REFINE, TAG_COARSEN = 0, 1, -1
 
 
+def compile_to(src: str, out: str) -> None:
+    """Compile an oracle source file into a shared library at `out`."""
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", src, "-o", out],
+                   check=True)
+
+
 def build(force: bool = False) -> str:
     """Compile orc.cpp into liborc.so (gcc, -ffp-contract=off, OpenMP)."""
+    if os.environ.get("ORC_LIB"):
+        return _LIB
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",

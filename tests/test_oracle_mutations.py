@@ -1,0 +1,71 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake
+in a copy of oracle/orc.cpp (a sign, a coefficient, a transposed index, a
+dropped condition), builds it into a separate library and runs the pin that
+should fail against it (in a subprocess, through ORC_LIB).  The unmodified
+oracle passes the same pins in test_oracle_pins.py.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "orc.cpp")
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+# id: (text in orc.cpp, its mistaken replacement, the pin that must fail)
+MUTATIONS = {
+    "roe_left_eigenvector_sign": ("0.5 * (b2 + un * ic), 0.5 * (-b1 * un - ic)",
+                                  "0.5 * (b2 - un * ic), 0.5 * (-b1 * un - ic)",
+                                  "test_eigensystem_inverse_and_roe_property"),
+    "hllc_star_energy_sign": ("(Ss - q.vel[0]) * (Ss + q.p / mK)", "(Ss - q.vel[0]) * (Ss - q.p / mK)",
+                              "test_hllc_exact_on_isolated_shocks"),
+    "hllc_contact_speed": ("(((b.p - a.p) + uL * mL) - uR * mR)", "(((b.p - a.p) + uL * mL) + uR * mR)",
+                           "test_hllc_exact_on_isolated_shocks"),
+    "llf_not_everywhere": ("if (flux == FLUX_ROE && lL > 0.0 && lR > 0.0 && lt > 0.0) {",
+                           "if (lL > 0.0 && lR > 0.0 && lt > 0.0) {",
+                           "test_llf_face_flux_on_a_step_closed_form"),
+    "wenoao_quartic_smoothness": ("(781.0 / 20.0) * (u3 * u3)", "(781.0 / 30.0) * (u3 * u3)",
+                                  "test_wenoao_matches_its_definition"),
+    "wenoao_weight_exponent": ("double w5 = g5 * (1.0 + r5 * r5)", "double w5 = g5 * (1.0 + r5)",
+                               "test_wenoao_matches_its_definition"),
+    "viscous_stress_not_symmetrised": ("tau[i] = mu * (G[i][d] + G[d][i]);", "tau[i] = mu * (G[i][d] + G[i][d]);",
+                                       "test_viscous_terms_on_a_linear_velocity_field"),
+    "viscous_bulk_term_sign": ("tau[d] = tau[d] - ((2.0 / 3.0) * mu) * div;",
+                               "tau[d] = tau[d] + ((2.0 / 3.0) * mu) * div;",
+                               "test_viscous_terms_on_a_linear_velocity_field"),
+    "prediction_coefficient": ("const double C0 = -22.0 / 128.0, C1 = 3.0 / 128.0;",
+                               "const double C0 = -22.0 / 128.0, C1 = -3.0 / 128.0;",
+                               "test_prediction_reproduces_quartics"),
+    "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
+                    "test_rk2_is_second_order_in_time"),
+}
+
+
+@pytest.fixture(scope="module")
+def mutants(tmp_path_factory):
+    src = open(SRC).read()
+    d = tmp_path_factory.mktemp("mutants")
+    jobs = {}
+    for mid, (old, new, _) in MUTATIONS.items():
+        assert src.count(old) == 1, mid
+        p = os.path.join(d, mid + ".cpp")
+        open(p, "w").write(src.replace(old, new))
+        jobs[mid] = (p, os.path.join(d, mid + ".so"))
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        list(ex.map(lambda j: oracle.compile_to(*j), jobs.values()))
+    return {mid: so for mid, (_, so) in jobs.items()}
+
+
+@pytest.mark.parametrize("mid", sorted(MUTATIONS))
+def test_pin_catches_planted_mistake(mutants, mid):
+    pin = MUTATIONS[mid][2]
+    env = dict(os.environ, ORC_LIB=mutants[mid], OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", f"{PINS}::{pin}"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, (mid, pin, r.stdout[-2000:])
+    assert "failed" in r.stdout, (mid, r.stdout[-2000:])
