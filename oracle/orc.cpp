@@ -21,13 +21,14 @@
 // density wave, L.R = I and the Roe property of the eigensystem, WENO5/linear
 // special cases, A(P(u)) = u and quartic reproduction of P, the Morton
 // neighbour example of Fig. (NeighborLookup) and brute force in all 26
-// directions, tag invariants, TENO5 cutoff and smooth-data cases, WENO-AO(5,3)
+// directions, tag invariants, the Roe/LLF per-field switch in closed form on a
+// transonic step, TENO5 cutoff and smooth-data cases, WENO-AO(5,3)
 // against its definition (polynomial fits, exact integrals), HLLC exact on
 // isolated shocks and stationary contacts, the LLF step flux in closed form,
 // the Sod solution for each flux scheme, second order in time of TVD-RK2.
-// Parity unpinned: the Roe/LLF per-field switch
-// and the detail norm are readings (the paper names them without a formula);
-// they are pinned only indirectly (free-stream, conservation, Sod, convergence).
+// Parity unpinned: the detail norm is a reading (the paper names only the
+// l-infinity norm); it is pinned only indirectly (tag invariants, Sod,
+// conservation with remeshing).
 
 #include <algorithm>
 #include <cmath>

@@ -29,6 +29,9 @@ MUTATIONS = {
     "llf_not_everywhere": ("if (flux == FLUX_ROE && lL > 0.0 && lR > 0.0 && lt > 0.0) {",
                            "if (lL > 0.0 && lR > 0.0 && lt > 0.0) {",
                            "test_llf_face_flux_on_a_step_closed_form"),
+    "llf_speed_from_roe_average": ("      double alpha = std::max(std::fabs(lL), std::fabs(lR));\n      double fp[6], fm[6];",
+                                   "      double alpha = std::fabs(lt);\n      double fp[6], fm[6];",
+                                   "test_roe_llf_switch_on_a_transonic_step_closed_form"),
     "wenoao_quartic_smoothness": ("(781.0 / 20.0) * (u3 * u3)", "(781.0 / 30.0) * (u3 * u3)",
                                   "test_wenoao_matches_its_definition"),
     "wenoao_weight_exponent": ("double w5 = g5 * (1.0 + r5 * r5)", "double w5 = g5 * (1.0 + r5)",

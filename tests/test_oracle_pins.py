@@ -386,6 +386,38 @@ def test_llf_face_flux_on_a_step_closed_form():
     assert np.abs(oracle.face_flux(U6, 0, mode=I.RECON_TENO, flux=I.FLUX_LLF) - F_roe).max() > 1e-3
 
 
+def test_roe_llf_switch_on_a_transonic_step_closed_form():
+    """The per-field switch (the reading of Sec. 2.2's Roe / LLF pair) on a
+    step whose u - c field changes sign across the face while u and u + c
+    are positive on both sides: fields 1-4 are upwinded from the left and the
+    u - c field alone takes the LLF split, so with exact one-sided
+    reconstruction (TENO5 on a step) the face flux is
+    (I - P0) F_L + P0 [(F_L + F_R)/2 - alpha0/2 (U_R - U_L)], P0 the spectral
+    projector of the Roe Jacobian on its u - c eigenvalue (Sylvester) and
+    alpha0 the larger |u - c| of the two face cells."""
+    def lam0(U):
+        vel = U[1] / U[0]
+        p = 0.4 * (U[4] - 0.5 * U[1:4] @ U[1:4] / U[0])
+        return vel - math.sqrt(1.4 * p / U[0])
+    for UL, UR in ((_cons(1.0, 0.5, 0.1, -0.2, 1.0), _cons(0.5, 2.0, 0.0, 0.1, 0.3)),
+                   (_cons(1.2, 0.3, -0.3, 0.0, 1.5), _cons(0.4, 1.8, 0.2, 0.2, 0.25))):
+        assert lam0(UL) < 0 < lam0(UR)
+        A, u, c = _roe_jacobian(UL, UR, 1.4)
+        assert u > 0
+        Id = np.eye(5)
+        mu = [u - c, u, u + c]
+        P0 = (A - mu[1] * Id) @ (A - mu[2] * Id) / ((mu[0] - mu[1]) * (mu[0] - mu[2]))
+        a0 = max(abs(lam0(UL)), abs(lam0(UR)))
+        FL, FR = _np_flux(UL, 0), _np_flux(UR, 0)
+        ref = (Id - P0) @ FL + P0 @ (0.5 * (FL + FR) - 0.5 * a0 * (UR - UL))
+        F = oracle.face_flux(np.array([UL] * 3 + [UR] * 3), 0, mode=I.RECON_TENO)
+        assert np.abs(F - ref).max() <= 1e-12 * np.abs(ref).max()
+        # neither plain upwinding nor the split on every field gives it
+        assert np.abs(F - FL).max() > 1e-3
+        assert np.abs(F - oracle.face_flux(np.array([UL] * 3 + [UR] * 3), 0, mode=I.RECON_TENO,
+                                           flux=I.FLUX_LLF)).max() > 1e-3
+
+
 def test_hllc_face_flux_on_a_step_is_the_riemann_flux():
     """The same step through the HLLC face flux: the reconstructed face
     states are the two sides' states (TENO5 on a step), so the face flux is
