@@ -1191,6 +1191,14 @@ double block_delta(Ctx& C, Node& n) {
 // Tags (Eq. (Thresholding)): REFINE if delta > eps_l and l < lmax; a sibling
 // group is COARSENED if all eight are leaves at level >= 2 (no node on level 1
 // is ever coarsened, Sec. 4) with delta < eps_l; equality keeps the block.
+// Tags of the leaves (Eq. Thresholding with Eq. LevelWiseEpsilon): REFINE a
+// leaf whose detail exceeds its level's threshold (below l_max); COARSEN a
+// complete group of eight leaf siblings at level >= 2 whose details are all
+// below their threshold.  In the analysis between time steps (allow_refine) a
+// group is kept while its parent's own detail exceeds the parent's threshold:
+// the parent would be refined again at once (its children, just predicted
+// from it, have no details), so coarsening them would make the tree
+// alternate between two states from step to step.
 void predict_and_tag(Ctx& C, int allow_refine, int8_t* tags, double* deltas) {
   std::vector<Node*> leaves = nodes_at(C, -1, true);
   std::vector<double> dl(leaves.size(), 0.0);
@@ -1199,6 +1207,17 @@ void predict_and_tag(Ctx& C, int allow_refine, int8_t* tags, double* deltas) {
     if (leaves[t]->level >= 1) dl[t] = block_delta(C, *leaves[t]);
   std::map<uint64_t, size_t> pos;
   for (size_t t = 0; t < leaves.size(); ++t) pos[leaves[t]->key] = t;
+  // details of the parents of complete leaf groups at level >= 2
+  std::map<uint64_t, double> dpar;
+  if (allow_refine) {
+    std::vector<Node*> par;
+    for (Node* n : leaves)
+      if (n->level >= 2 && (n->key & 7ull) == 0) par.push_back(parent_of(C, *n));
+    std::vector<double> dp(par.size(), 0.0);
+#pragma omp parallel for schedule(dynamic)
+    for (long t = 0; t < (long)par.size(); ++t) dp[t] = block_delta(C, *par[t]);
+    for (size_t t = 0; t < par.size(); ++t) dpar[par[t]->key] = dp[t];
+  }
   for (size_t t = 0; t < leaves.size(); ++t) {
     Node& n = *leaves[t];
     int8_t tag = TAG_KEEP;
@@ -1216,6 +1235,10 @@ void predict_and_tag(Ctx& C, int allow_refine, int8_t* tags, double* deltas) {
           auto it = pos.find(sk);
           if (it == pos.end()) { all = false; break; }
           if (!(dl[it->second] < el)) all = false;
+        }
+        if (all && allow_refine) {
+          double ep = std::ldexp(C.c.eps, -3 * (lmx - (n.level - 1)));
+          if (dpar[pk | (inst << 56)] > ep) all = false;
         }
         if (all) tag = TAG_COARSEN;
       }

@@ -40,8 +40,9 @@ void launch_fill_list_f32(const Topo& t, const Phys& p, const Pool& pool, int cu
   g_kernel_launches += 3;
 }
 
-void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, cudaStream_t st) {
-  k_delta_t<float><<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, delta_node);
+void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, int all_nodes,
+                      cudaStream_t st) {
+  k_delta_t<float><<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, delta_node, all_nodes);
   ++g_kernel_launches;
 }
 

@@ -333,6 +333,9 @@ __global__ void k_tags(Topo t, Phys p, const double* __restrict__ delta_node, in
             break;
           }
         }
+        // between time steps a group stays while its parent's own detail asks
+        // for it (the parent would be refined again at once)
+        if (all && allow_refine && delta_node[t.parent[node]] > ldexp(p.eps, -3 * (lmx - (lvl - 1)))) all = false;
         if (all) tag = -1;
       }
     }
@@ -343,9 +346,9 @@ __global__ void k_tags(Topo t, Phys p, const double* __restrict__ delta_node, in
 
 void launch_delta_tags(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node,
                        int allow_refine, int8_t* tags, double* delta_leaf, int n_leaves_cap, cudaStream_t st) {
-  if (p.precision == 1) launch_delta_f32(t, p, pool, cur, delta_node, st);
+  if (p.precision == 1) launch_delta_f32(t, p, pool, cur, delta_node, allow_refine, st);
   else {
-    k_delta_t<double><<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, delta_node);
+    k_delta_t<double><<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, delta_node, allow_refine);
     ++g_kernel_launches;
   }
   k_tags<<<(n_leaves_cap + 255) / 256, 256, 0, st>>>(t, p, delta_node, allow_refine, tags, delta_leaf);

@@ -378,16 +378,19 @@ static __global__ void __launch_bounds__(256) k_fill_bc(Topo t, Phys p, Pool poo
 }
 
 // ---------------------------------------------------------------- details
-// delta of a leaf at level >= 1: max over its stored cells that are not ghost
-// cells and over rho, E of |u - P(u_parent)| / |u|.
+// delta of a node at level >= 1: max over its stored cells that are not ghost
+// cells and over rho, E of |u - P(u_parent)| / |u|.  Every leaf, and with
+// `all_nodes` every node (the tags then also read the details of the parents
+// of leaf groups).
 template <class R>
-__global__ void __launch_bounds__(256) k_delta_t(Topo t, Phys p, Pool pool, int cur, double* __restrict__ delta_node) {
+__global__ void __launch_bounds__(256) k_delta_t(Topo t, Phys p, Pool pool, int cur, double* __restrict__ delta_node,
+                                                 int all_nodes) {
   __shared__ double sh[8];
   __shared__ R box[4096];           // the parent's cells 8 cb - 4 .. 8 cb + 11 per axis, one variable
-  const int nleaves = t.cnt[CNT_NLEAVES];
+  const int nitems = all_nodes ? t.cnt[CNT_NNODES] : t.cnt[CNT_NLEAVES];
   const double* B = pool.buf[cur];
-  for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
-    const int node = t.leaves[li];
+  for (int li = blockIdx.x; li < nitems; li += gridDim.x) {
+    const int node = all_nodes ? li : t.leaves[li];
     const int lvl = t.level[node];
     if (lvl == 0) {
       if (threadIdx.x == 0) delta_node[node] = 0.0;

@@ -32,6 +32,9 @@ MUTATIONS = {
     "llf_speed_from_roe_average": ("      double alpha = std::max(std::fabs(lL), std::fabs(lR));\n      double fp[6], fm[6];",
                                    "      double alpha = std::fabs(lt);\n      double fp[6], fm[6];",
                                    "test_roe_llf_switch_on_a_transonic_step_closed_form"),
+    "coarsen_ignores_parent_detail": ("          if (dpar[pk | (inst << 56)] > ep) all = false;",
+                                      "          if (dpar[pk | (inst << 56)] > 1e300 * ep) all = false;",
+                                      "test_refined_groups_are_not_coarsened_right_away"),
     "wenoao_quartic_smoothness": ("(781.0 / 20.0) * (u3 * u3)", "(781.0 / 30.0) * (u3 * u3)",
                                   "test_wenoao_matches_its_definition"),
     "wenoao_weight_exponent": ("double w5 = g5 * (1.0 + r5 * r5)", "double w5 = g5 * (1.0 + r5)",

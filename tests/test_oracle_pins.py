@@ -787,6 +787,38 @@ def test_tags_refine_at_discontinuity_and_valid_octree():
             assert (k >> 56 << 56) | (m >> 3) in allk
 
 
+def test_refined_groups_are_not_coarsened_right_away():
+    """Blocks refined by the analysis between steps get children predicted
+    from them, which have no details of their own; while the parent's detail
+    still exceeds its threshold the next analysis keeps them (no
+    refine/coarsen alternation from step to step).  Without a time step in
+    between, no group made by the first analysis is tagged for coarsening by
+    the second."""
+    cfg = I.explosion_config(lmax=2, dx0=1.0 / 32.0)
+    o = oracle.Oracle(cfg)
+    o.set_state(o.keys(), I.ic_explosion(cfg, o.geometry(), r0=0.25))
+    for m in range(1, cfg.lmax_of(0) + 1):
+        o.fill_halos()
+        g = o.geometry()
+        o.remesh((g[:, 0] == m - 1).astype(np.int8))
+        o.set_state(o.keys(), I.ic_explosion(cfg, o.geometry(), r0=0.25))
+        if m > 1:
+            o.fill_halos()
+            tags, _ = o.predict_and_tag(allow_refine=False)
+            o.remesh(tags)
+    o.project()
+    before = set(int(k) for k in o.keys())
+    o.fill_halos()
+    t1, _ = o.predict_and_tag(allow_refine=True)
+    assert (t1 == 1).any()
+    o.remesh(t1)
+    made = [i for i, k in enumerate(o.keys()) if int(k) not in before]
+    assert len(made) >= 8
+    o.fill_halos()
+    t2, _ = o.predict_and_tag(allow_refine=True)
+    assert not (t2[made] == -1).any()
+
+
 # ------------------------------------------------------------------ viscous terms
 def _linear_velocity_state(cfg, geo, A, u0, rho=1.3, p=2.0):
     X, Y, Z, _ = I.cell_centres(cfg, geo)
