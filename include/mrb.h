@@ -204,9 +204,12 @@ int mrb_mr_project(mrb_ctx* ctx);
  * delta = max over cells and over rho, E of |d| / |u|, threshold
  * eps_l = 2^(-3 (lmax - l)) eps.  Tags (device, [n_leaves] int8, leaf order):
  * REFINE if delta > eps_l and l < lmax (only when allow_refine), COARSEN for
- * a complete group of eight sibling leaves at level >= 2 all below eps_l,
- * else KEEP.  delta_dev (device, [n_leaves], nullable) receives delta.
- * Halos and the projection must be current. */
+ * a complete group of eight sibling leaves at level >= 2 all below eps_l
+ * (with allow_refine, only if the group's parent, at level l-1, does not have
+ * delta > eps_(l-1) itself: such a parent would be refined again at once, so
+ * the tree would alternate from step to step), else KEEP.  delta_dev
+ * (device, [n_leaves], nullable) receives delta.  Halos and the projection
+ * must be current. */
 int mrb_mr_predict_and_tag(mrb_ctx* ctx, int32_t allow_refine, int8_t* tags_dev, double* delta_dev);
 
 /* Apply tags (device, [n_leaves] int8, leaf order; as from
