@@ -155,21 +155,32 @@ def finest_density(keys, geo, rho, cfg):
     return out
 
 
-def roofline_numbers(linear_fraction=0.0):
+# FLOPs of the face flux by part, as the oracle's face flux performs them
+# (zero entries of the eigenvectors and loop-invariant constants skipped).
+FLOP_ROE = 71                  # Roe average and eigensystem
+FLOP_PROJ_G = 6 * 31           # g = L F(U) of the six cells: 9 per acoustic / entropy field, 2 per shear field
+FLOP_TESTS = 6                 # eigenvalue sign tests
+FLOP_RG = 33                   # F = R g_hat
+FLOP_WENO, FLOP_LIN = 66, 21   # one WENO5-JS / linear 5th-order reconstruction
+FLOP_V = (54, 54, 12, 12, 54)  # v = l_k U of the six cells, needed only by a split field k
+FLOP_SPLIT = 34                # alpha (3), the split halves of the six cells (30), the sum (1)
+
+
+def roofline_numbers(linear_fraction=0.0, split=None):
     """Algorithmic FP32 FLOPs of the fused stage kernel per face and per leaf
-    cell and stage (the accounting is in this function's body).
-    `linear_fraction` is the share of faces that take the linear scheme,
-    averaged over the stages timed."""
-    # Per face (the oracle's face flux, WENO5 on every field, Roe upwinding on
-    # every field, zero matrix entries skipped): Roe average and eigensystem 71,
-    # characteristic projections 6 cells x 62, split tests 6, WENO5 5 x 66,
-    # R g 33 -> 812.  A face the selector sends to the linear scheme does the
-    # linear reconstruction (21) instead of WENO5 (66) on fields 0, 1, 4:
-    # 812 - 3 x 45 = 677.  Per cell and direction: primitive variables and
-    # physical flux 25.  Per cell and stage: 3 x (17/16 faces x per_face +
-    # 22/16 x 25) + divergence 30 + update 20.  The selector's MLP runs on the
-    # tensor cores and is not counted here.
-    per_face = 812 - linear_fraction * 3 * 45
+    cell and stage.  `linear_fraction`: share of faces whose fields 0, 1, 4
+    take the linear scheme (averaged over the stages timed); `split[k]`: share
+    of faces where characteristic field k takes the LLF split (the census of
+    mrb_flux_census), which adds its v projection, the split and a second
+    reconstruction.  Per cell and direction the primitive variables and the
+    physical flux cost 25; per cell and stage: 3 x (17/16 x per_face + 22/16
+    x 25) + divergence 30 + update 20.  The selector's MLP runs on the tensor
+    cores and is not counted."""
+    split = split if split is not None else (0.0,) * 5
+    per_face = FLOP_ROE + FLOP_PROJ_G + FLOP_TESTS + FLOP_RG
+    for k in range(5):
+        rec = FLOP_WENO if k in (2, 3) else (1 - linear_fraction) * FLOP_WENO + linear_fraction * FLOP_LIN
+        per_face += rec + split[k] * (FLOP_V[k] + FLOP_SPLIT + rec)
     per_cell = 3 * (17 / 16 * per_face + 22 / 16 * 25) + 30 + 20
     return per_face, per_cell
 
@@ -230,7 +241,15 @@ class Ranks:
 
 
 # ------------------------------------------------------------------ GPU arm
-def timed_path(args, cfg, stream, steps, warmup, mlp_params=None, profile=True, profiler_range=False):
+def census_fractions(ctx):
+    """Shares of faces where each characteristic field takes the LLF split,
+    on the current state (halos filled first; outside any timed region)."""
+    ctx.fill_halos()
+    c = ctx.flux_census().astype(np.float64)
+    return c[:5] / max(c[5], 1.0)
+
+
+def timed_path(args, cfg, stream, steps, warmup, mlp_params=None, profile=True, profiler_range=False, census=False):
     """Build the workload tree, warm up, time `steps` full steps with CUDA
     events on the launching stream; returns the context and measurements."""
     import torch
@@ -241,6 +260,7 @@ def timed_path(args, cfg, stream, steps, warmup, mlp_params=None, profile=True, 
     for _ in range(warmup):
         ctx.step(1)
     torch.cuda.synchronize()
+    split0 = census_fractions(ctx) if census else None
     if profile:
         ctx.profile(True)
     ctx.learned_stats(reset=True)
@@ -259,8 +279,10 @@ def timed_path(args, cfg, stream, steps, warmup, mlp_params=None, profile=True, 
     ms = ev0.elapsed_time(ev1)
     kms, kn, nk = ctx.profile_read() if profile else (0.0, 0, 0)
     lin, tot = ctx.learned_stats()
+    # the census of the switch at the start and the end of the timed steps
+    split = tuple(0.5 * (split0 + census_fractions(ctx))) if census else None
     return ctx, dict(ms=ms, cells=cells, stage_ms=kms / max(kn, 1), launches=nk,
-                     linear_fraction=(lin / tot) if tot else 0.0)
+                     linear_fraction=(lin / tot) if tot else 0.0, split=split)
 
 
 def l1_after(cfg_a, cfg_b, stream, nsteps, params=None):
@@ -306,7 +328,7 @@ def run_gpu(args, rank, world):
     sampler = ClockSampler(dev)
     sampler.start()
     ctx, m = timed_path(args, cfg_l, stream, args.steps, args.warmup, mlp_params=params,
-                        profiler_range=args.profile_range)
+                        profiler_range=args.profile_range, census=True)
     clocks = sampler.stop()
     barrier()
     ms_max = max_over_ranks(m["ms"])
@@ -315,7 +337,7 @@ def run_gpu(args, rank, world):
 
     # ---- roofline of the fused stage kernel (FP32 CUDA cores)
     # stage 0 evaluates the selector with WENO5 fluxes; stages 1 and 2 use its decisions
-    per_face, per_cell = roofline_numbers(m["linear_fraction"] * 2 / 3)
+    per_face, per_cell = roofline_numbers(m["linear_fraction"] * 2 / 3, m["split"])
     pk = measured_peaks()
     clk = clocks["sm_mhz"] or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 1447.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -324,11 +346,11 @@ def run_gpu(args, rank, world):
     achieved = cells_per_launch * per_cell / (m["stage_ms"] * 1e-3) / 1e12
 
     # ---- the same workload on the FP32 WENO5 path and the all-FP64 path
-    _, mw = timed_path(args, cfg_w, stream, args.steps, args.warmup)
+    _, mw = timed_path(args, cfg_w, stream, args.steps, args.warmup, census=True)
     _, m64 = timed_path(args, cfg_64, stream, args.fp64_steps, 1)
     value_w = sum_over_ranks(mw["cells"]) / (max_over_ranks(mw["ms"]) * 1e-3)
     value_64 = sum_over_ranks(m64["cells"]) / (max_over_ranks(m64["ms"]) * 1e-3)
-    _, pfw = roofline_numbers(0.0)
+    _, pfw = roofline_numbers(0.0, mw["split"])
     achieved_w = (mw["cells"] / 3 / args.steps) * pfw / (mw["stage_ms"] * 1e-3) / 1e12
 
     # ---- reconstruction / flux variants of the FP32 path on the same workload
@@ -402,7 +424,9 @@ def run_gpu(args, rank, world):
                                  if TRAFFIC_BYTES_PER_CELL["learned"] else None),
                      "traffic_note": "ncu dram bytes per leaf cell of 2.1M-cell launches (stage 0, 1, 2 mean) x the launch's leaf cells",
                      "kernel": "k_stage_f32<1> (stage 0, selector evaluated) + k_stage_f32<3> (stages 1, 2): fused RHS + RK stage",
-                     "flops_per_cell_stage": per_cell, "avg_launch_ms": m["stage_ms"],
+                     "flops_per_cell_stage": per_cell, "flops_per_face": per_face,
+                     "llf_split_share_per_field": [round(x, 4) for x in m["split"]],
+                     "avg_launch_ms": m["stage_ms"],
                      "peak_basis": f"FP32 CUDA cores {nsm} SMs x 128 lanes x 2 x {clk:.0f} MHz sampled"},
         "gpu_launches": int(m["launches"]),
         "clocks": clocks,

@@ -233,6 +233,16 @@ int mrb_step(mrb_ctx* ctx, int32_t nsteps, double* dt_hist_dev);
  * into sums_dev (device), in a fixed reduction order. */
 int mrb_sums(mrb_ctx* ctx, double* sums_dev);
 
+/* Census of the Roe / local Lax-Friedrichs switch (Sec. 2.2, the per-field
+ * rule of the MRB_FLUX_ROE scheme) for counting the algorithm's work: over
+ * every face of every leaf (17 x 16 x 16 per direction), counts_host[k]
+ * (host, [6]) receives the number of faces where characteristic field k
+ * (0: u-c, 1: entropy, 2, 3: shear, 4: u+c) takes the LLF split rather than
+ * upwinding, and counts_host[5] the number of faces.  The decisions are
+ * taken in FP64 on the current stage buffer; halos must be filled.
+ * Synchronous. */
+int mrb_flux_census(mrb_ctx* ctx, uint64_t* counts_host);
+
 /* Same-level neighbour ids of the listed blocks in the 26 directions
  * (index (dz+1)*9 + (dy+1)*3 + (dx+1), centre skipped), host [n][27]:
  * the id, or 0 where no same-level block exists, or 1 beyond a non-periodic

@@ -99,6 +99,7 @@ def lib():
                 "orc_predict_and_tag": (None, [vp, i32, vp, vp]),
                 "orc_remesh": (i64, [vp, vp]),
                 "orc_sums": (None, [vp, vp]),
+                "orc_flux_census": (None, [vp, vp]),
                 "orc_step": (None, [vp, i32, vp]),
                 "orc_neighbor": (i32, [vp, u64, i32, i32, i32, vp]),
                 "orc_make_key": (u64, [i32, i32, i64, i64, i64]),
@@ -245,6 +246,13 @@ class Oracle:
     def sums(self) -> np.ndarray:
         out = np.zeros((self.cfg.n_instances, NV))
         lib().orc_sums(self._h, _p(out))
+        return out
+
+    def flux_census(self) -> np.ndarray:
+        """Faces of all leaves where characteristic field k takes the LLF
+        split ([0..4]) and the number of faces ([5]); halos must be filled."""
+        out = np.zeros(6, dtype=np.uint64)
+        lib().orc_flux_census(self._h, _p(out))
         return out
 
     def step(self, nsteps: int = 1) -> np.ndarray:

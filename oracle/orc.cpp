@@ -1298,6 +1298,43 @@ int64_t remesh(Ctx& C, const int8_t* tags) {
   return nl;
 }
 
+// Census of the Roe / LLF switch (used to count the algorithm's work): for
+// every face of every leaf (17 x 16 x 16 per direction), which characteristic
+// fields take the LLF split under the per-field rule of face_flux.
+// counts[k] = faces where field k is split, counts[5] = faces.
+void flux_census(Ctx& C, uint64_t* counts) {
+  for (int k = 0; k < 6; ++k) counts[k] = 0;
+  double g = C.c.gamma, B = C.c.B;
+  for (auto& kv : C.nodes) {
+    const Node& n = kv.second;
+    if (!n.leaf) continue;
+    for (int d = 0; d < 3; ++d)
+      for (int b = 0; b < NB; ++b)
+        for (int a = 0; a < NB; ++a)
+          for (int f = 0; f <= NB; ++f) {
+            double U[2][5];
+            for (int m = 0; m < 2; ++m) {
+              int c[3];
+              c[d] = f - 1 + m;
+              c[(d == 0) ? 1 : 0] = a;
+              c[(d == 2) ? 1 : 2] = b;
+              for (int v = 0; v < NV; ++v) U[m][v] = n.u[(size_t)v * NCELL + sidx(c[0], c[1], c[2])];
+            }
+            Prim qL = prim_of(U[0], g, B), qR = prim_of(U[1], g, B);
+            Eigen e = roe_eigen(qL, qR, d, g);
+            double unL = qL.vel[d], unR = qR.vel[d];
+            double lamL[5] = {unL - qL.c, unL, unL, unL, unL + qL.c};
+            double lamR[5] = {unR - qR.c, unR, unR, unR, unR + qR.c};
+            for (int k = 0; k < 5; ++k) {
+              double lL = lamL[k], lR = lamR[k], lt = e.lam[k];
+              bool up = (lL > 0.0 && lR > 0.0 && lt > 0.0) || (lL < 0.0 && lR < 0.0 && lt < 0.0);
+              if (!up) counts[k] += 1;
+            }
+            counts[5] += 1;
+          }
+  }
+}
+
 // Conservation sums: per instance, sum over leaves (key order) of the cell sum
 // (storage order) times dx^3.
 void sums(Ctx& C, double* out) {
@@ -1489,6 +1526,7 @@ void orc_predict_and_tag(void* h, int32_t allow_refine, int8_t* tags, double* de
 }
 int64_t orc_remesh(void* h, const int8_t* tags) { return remesh(*(Ctx*)h, tags); }
 void orc_sums(void* h, double* out) { sums(*(Ctx*)h, out); }
+void orc_flux_census(void* h, uint64_t* counts) { flux_census(*(Ctx*)h, counts); }
 
 // nsteps full steps: CFL, the Runge-Kutta stages, then (with MR) analysis and remesh.
 // dt_hist (nullable) receives [nsteps][n_instances].

@@ -73,6 +73,7 @@ struct mrb_ctx {
           *d_child0 = nullptr, *d_nbr = nullptr, *d_leaves = nullptr, *d_lvl_nodes = nullptr, *d_bc_items = nullptr, *d_jump = nullptr, *d_cnt = nullptr,
           *d_lmax = nullptr, *d_list = nullptr;
   double *d_dt = nullptr, *d_delta_node = nullptr, *d_partial = nullptr;
+  unsigned long long* d_census = nullptr;   // mrb_flux_census counters (allocated on first use)
   unsigned long long* d_smax = nullptr;
   int8_t* d_tags = nullptr;
   int* d_status = nullptr;
@@ -837,6 +838,16 @@ int mrb_sums(mrb_ctx* c, double* sums_dev) {
   return guarded(c, [&] {
     if (!sums_dev) throw Err(MRB_EINVAL, "null sums");
     launch_sums(c->topo(), c->phys, c->P, c->cur, c->d_partial, sums_dev, c->n_leaves(), c->st);
+  });
+}
+
+int mrb_flux_census(mrb_ctx* c, uint64_t* counts_host) {
+  return guarded(c, [&] {
+    if (!counts_host) throw Err(MRB_EINVAL, "null counts");
+    if (!c->d_census) c->d_census = c->dalloc<unsigned long long>(6);
+    launch_flux_census(c->topo(), c->phys, c->P, c->cur, c->d_census, c->st);
+    CK(cudaMemcpyAsync(counts_host, c->d_census, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
   });
 }
 

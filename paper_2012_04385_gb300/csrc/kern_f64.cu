@@ -355,6 +355,53 @@ void launch_delta_tags(const Topo& t, const Phys& p, const Pool& pool, int cur, 
   ++g_kernel_launches;
 }
 
+// ---------------------------------------------------------------- Roe / LLF census
+// counts[k] += faces (of every leaf, 17 x 16 x 16 per direction) where field k
+// takes the LLF split; counts[5] += faces.  Per-thread counts, warp sums, one
+// atomic per warp and counter.
+__global__ void __launch_bounds__(256) k_flux_census(Topo t, Phys p, Pool pool, int cur,
+                                                     unsigned long long* __restrict__ counts) {
+  const long long nfaces = (long long)t.cnt[CNT_NLEAVES] * 3 * 17 * NFACE;
+  unsigned c[6] = {0, 0, 0, 0, 0, 0};
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < nfaces;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int li = (int)(it / (3 * 17 * NFACE));
+    const int r = (int)(it % (3 * 17 * NFACE));
+    const int d = r / (17 * NFACE), f = (r % (17 * NFACE)) / NFACE, ab = r % NFACE;
+    const int a = ab % NB, b = ab / NB;
+    int cl[3];
+    cl[d] = f - 1;
+    cl[(d == 0) ? 1 : 0] = a;
+    cl[(d == 2) ? 1 : 2] = b;
+    const int step[3] = {1, NS, NS * NS};
+    const int sL = sidx(cl[0], cl[1], cl[2]), sR = sL + step[d];
+    const double* U = pool.buf[cur] + (size_t)t.slot[t.leaves[li]] * SLOT_U;
+    double UL[5], UR[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      UL[v] = U[v * NCELL + sL];
+      UR[v] = U[v * NCELL + sR];
+    }
+    const unsigned m = split_fields(UL, UR, d, p.gamma, p.B);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) c[k] += (m >> k) & 1u;
+    c[5] += 1;
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    unsigned x = c[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&counts[k], (unsigned long long)x);
+  }
+}
+
+void launch_flux_census(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* counts,
+                        cudaStream_t st) {
+  cudaMemsetAsync(counts, 0, 6 * sizeof(unsigned long long), st);
+  k_flux_census<<<sm_count() * 8, 256, 0, st>>>(t, p, pool, cur, counts);
+  ++g_kernel_launches;
+}
+
 // ---------------------------------------------------------------- refinement (mr.cuh)
 void launch_refine_fill(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* pairs, int n,
                         cudaStream_t st) {

@@ -120,6 +120,10 @@ void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int c
                            int mode);
 void launch_fill_list_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* list, int n,
                           cudaStream_t st);
+// Roe / LLF census of every leaf face (FP64 decisions on the stage buffer):
+// counts[k] faces where field k takes the LLF split, counts[5] faces.
+void launch_flux_census(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* counts,
+                        cudaStream_t st);
 void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, int all_nodes,
                       cudaStream_t st);
 void launch_cfl_speeds_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax,

@@ -287,6 +287,35 @@ __device__ __forceinline__ void viscous_flux(const double* __restrict__ u, int d
   Fv[4] = (ub[0] * tau[0] + ub[1] * tau[1]) + ub[2] * tau[2];
 }
 
+// Fields (bit k) that take the LLF split at the face between the lab-frame
+// states UL, UR along d under the Roe / LLF rule of face_flux: the same
+// primitive variables, Roe average and eigenvalue tests.
+__device__ __forceinline__ unsigned split_fields(const double UL[5], const double UR[5], int d, double g, double B) {
+  const int a0 = rot_axis(d, 0), a1 = rot_axis(d, 1), a2 = rot_axis(d, 2);
+  const Prim<double> qL = prim_of<double>(UL, g, B), qR = prim_of<double>(UR, g, B);
+  const double unL = qL.vel[d], cL = qL.c, unR = qR.vel[d], cR = qR.c;
+  const double sL = sqrt(qL.rho), sR = sqrt(qR.rho);
+  const double den = sL + sR;
+  const double un = (sL * qL.vel[a0] + sR * qR.vel[a0]) / den;
+  const double ut1 = (sL * qL.vel[a1] + sR * qR.vel[a1]) / den;
+  const double ut2 = (sL * qL.vel[a2] + sR * qR.vel[a2]) / den;
+  const double HL = (qL.E + qL.p) / qL.rho, HR = (qR.E + qR.p) / qR.rho;
+  const double H = (sL * HL + sR * HR) / den;
+  const double q2 = (un * un + ut1 * ut1) + ut2 * ut2;
+  const double c = sqrt((g - 1.0) * (H - 0.5 * q2));
+  unsigned mask = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    double lL, lR, lt;
+    if (k == 0) { lL = unL - cL; lR = unR - cR; lt = un - c; }
+    else if (k == 4) { lL = unL + cL; lR = unR + cR; lt = un + c; }
+    else { lL = unL; lR = unR; lt = un; }
+    const bool up = (lL > 0.0 && lR > 0.0 && lt > 0.0) || (lL < 0.0 && lR < 0.0 && lt < 0.0);
+    if (!up) mask |= 1u << k;
+  }
+  return mask;
+}
+
 // ---------------------------------------------------------------- face flux
 // Numerical flux at the face between cells 2 and 3 of U6 (cells i-2 .. i+3
 // along d, lab-frame conserved states), returned in the lab frame.  Rotated

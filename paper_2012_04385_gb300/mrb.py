@@ -86,6 +86,7 @@ def lib():
                 "mrb_remesh": (ci, [vp, vp, vp]),
                 "mrb_step": (ci, [vp, i32, vp]),
                 "mrb_sums": (ci, [vp, vp]),
+                "mrb_flux_census": (ci, [vp, vp]),
                 "mrb_neighbors": (ci, [vp, vp, i64, vp]),
                 "mrb_profile": (ci, [vp, i32]),
                 "mrb_profile_read": (ci, [vp, vp, vp, vp]),
@@ -353,6 +354,13 @@ class Context:
         if out is None:
             out = torch.empty((self.cfg.n_instances, NV), dtype=torch.float64, device=self.pool.device)
         self._rc(lib().mrb_sums(self._h, out.data_ptr()))
+        return out
+
+    def flux_census(self) -> np.ndarray:
+        """Faces where each characteristic field takes the LLF split ([0..4])
+        and the number of faces ([5]), over every leaf face (halos filled)."""
+        out = np.zeros(6, dtype=np.uint64)
+        self._rc(lib().mrb_flux_census(self._h, out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
     def neighbors(self, keys):

@@ -165,6 +165,24 @@ def test_compute_rhs_gravity_and_stiffened_gas():
     close(g.compute_rhs().cpu().numpy(), o.compute_rhs(), what="rhs gravity")
 
 
+def test_flux_census_matches_oracle():
+    """The Roe / LLF census (which characteristic fields take the split at
+    every leaf face) on random states with resolution jumps and on the MR
+    explosion: identical counts (integer work, FP64 decisions on both sides)."""
+    cfg = I.explosion_config(lmax=3)
+    o, g = make_pair(cfg, rnd(6, mild=True), (ALL, SOME))
+    o.fill_halos()
+    g.fill_halos()
+    assert np.array_equal(g.flux_census(), o.flux_census())
+    cfg = I.explosion_config(lmax=2)
+    o, g = make_pair(cfg, wrap(I.ic_explosion), (ALL,))
+    o.fill_halos()
+    g.fill_halos()
+    c = g.flux_census()
+    print("explosion census (split faces per field, faces):", c)
+    assert np.array_equal(c, o.flux_census())
+
+
 def test_cfl_bit_exact():
     cfg = I.ensemble_config(n=3)
     o, g = make_pair(cfg, rnd(6), (ALL,))

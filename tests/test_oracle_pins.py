@@ -418,6 +418,27 @@ def test_roe_llf_switch_on_a_transonic_step_closed_form():
                                            flux=I.FLUX_LLF)).max() > 1e-3
 
 
+def test_flux_census_closed_forms():
+    """The census of the Roe / LLF switch on uniform states: gas at rest
+    splits fields 1-3 (u = 0 is not a strict sign) on every face and upwinds
+    the acoustic fields; a uniform supersonic flow along x upwinds every field
+    on the x faces and splits fields 1-3 on the y and z faces."""
+    cfg = I.periodic_config(base=(2, 1, 1))
+    o = oracle.Oracle(cfg)
+    geo = o.geometry()
+    F = 2 * 3 * 17 * 16 * 16
+    prim = I.ic_uniform(cfg, geo, vel=(0.0, 0.0, 0.0))
+    o.set_state(o.keys(), prim)
+    o.fill_halos()
+    c = o.flux_census()
+    assert list(c) == [0, F, F, F, 0, F]
+    prim[:, 1] = 3.0                                   # u = 3 > c = 0.98
+    o.set_state(o.keys(), prim)
+    o.fill_halos()
+    c = o.flux_census()
+    assert list(c) == [0, 2 * F // 3, 2 * F // 3, 2 * F // 3, 0, F]
+
+
 def test_hllc_face_flux_on_a_step_is_the_riemann_flux():
     """The same step through the HLLC face flux: the reconstructed face
     states are the two sides' states (TENO5 on a step), so the face flux is
