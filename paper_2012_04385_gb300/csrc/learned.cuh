@@ -2,8 +2,9 @@
 // (tanh form) that reads the compressed consecutive variations of three
 // characteristic fields over a face's six-cell stencil and predicts whether
 // WENO5-JS is needed or the linear 5th-order reconstruction suffices for the
-// acoustic and entropy fields (the shear fields keep WENO5).  (The paper has no selector; it is the learned
-// component of this GPU design, with WENO5-JS as its fallback and judge.)
+// acoustic and entropy fields (the shear fields keep WENO5).  The paper has no
+// selector; it is the learned component of this GPU design, with WENO5-JS as
+// its fallback and as the reference its labels and error are measured against.
 //
 // Inference runs on the tensor cores: a warp evaluates 32 faces at once as a
 // 32 x 16 @ 16 x 32 -> 32 x 32 @ 32 x 32 -> 32 x 32 @ 32 x 8 chain of
