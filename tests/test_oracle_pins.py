@@ -152,6 +152,57 @@ def _wenoao_from_definition(f):
     return w[3] / gam[3] * (q[3] - sum(gam[k] * q[k] for k in range(3))) + sum(w[k] * q[k] for k in range(3))
 
 
+def _teno5_from_definition(f, CT=1e-5):
+    """TENO5 from the definitions: the three parabolas through the cell
+    averages (linear systems), their smoothness as integrals of the squared
+    derivatives over the middle cell, gamma_k = (1 + tau5 / (beta_k + 1e-40))^6
+    with tau5 = |beta_0 - beta_2|, stencils with gamma_k / sum gamma < CT
+    dropped, the kept ones combined with the linear weights renormalised."""
+    P = np.polynomial.polynomial
+
+    def fit(cells):
+        A = np.array([[((j + .5) ** (k + 1) - (j - .5) ** (k + 1)) / (k + 1) for k in range(3)] for j in cells])
+        return np.linalg.solve(A, np.array([f[j + 2] for j in cells]))
+
+    def beta(c):
+        tot = 0.0
+        for l in (1, 2):
+            d = P.polyder(c, l)
+            sq = P.polyint(P.polymul(d, d))
+            tot += P.polyval(0.5, sq) - P.polyval(-0.5, sq)
+        return tot
+    polys = [fit([-2, -1, 0]), fit([-1, 0, 1]), fit([0, 1, 2])]
+    b = [beta(c) for c in polys]
+    q = [P.polyval(0.5, c) for c in polys]
+    tau = abs(b[0] - b[2])
+    gam = [(1.0 + tau / (bk + 1e-40)) ** 6 for bk in b]
+    chi = [gk / sum(gam) for gk in gam]
+    d = [0.1, 0.6, 0.3]
+    w = [d[k] if chi[k] >= CT else 0.0 for k in range(3)]
+    return sum(w[k] * q[k] for k in range(3)) / sum(w), chi
+
+
+def test_teno5_matches_its_definition():
+    """Random data between smooth and discontinuous, scaled over four
+    decades: the oracle's TENO5 equals the definition computed from
+    polynomial fits, wherever no stencil's share sits within rounding of the
+    cutoff; the set covers kept and dropped stencils with shares on both
+    sides of C_T and far from it."""
+    rng = np.random.default_rng(23)
+    seen_low, seen_mid = False, False
+    for it in range(600):
+        scale = 10.0 ** rng.uniform(-2, 2)
+        x = np.arange(5.0)
+        f = scale * (np.sin(rng.uniform(0.1, 2.5) * x + rng.uniform(0, 6)) + rng.uniform(0, 2) * (x >= rng.integers(1, 5)))
+        ref, chi = _teno5_from_definition(f)
+        if min(abs(np.log10(max(c, 1e-300)) + 5) for c in chi) < 1e-6:
+            continue
+        seen_low |= min(chi) < 1e-5
+        seen_mid |= any(1e-5 < c < 1e-1 for c in chi)
+        assert abs(oracle.teno5(f) - ref) <= 1e-10 * max(scale, abs(ref)), (f, ref, chi)
+    assert seen_low and seen_mid
+
+
 def test_wenoao_matches_its_definition():
     """Random data of several scales, smooth and with jumps: the oracle's
     closed forms (Legendre-coefficient smoothness of the quartic, face values)
