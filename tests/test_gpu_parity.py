@@ -6,6 +6,8 @@ point per cell within 1e-11 relative (|a - b| <= 1e-11 max(|b|, s_v), s_v the
 largest magnitude of variable v); the tests also report how many cells are
 not bit-identical.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -163,6 +165,40 @@ def test_compute_rhs_gravity_and_stiffened_gas():
     o.fill_halos()
     g.fill_halos()
     close(g.compute_rhs().cpu().numpy(), o.compute_rhs(), what="rhs gravity")
+
+
+def test_hllc_fallback_rhs_bit_exact():
+    """Densities that oscillate cell to cell at rest with the linear
+    reconstruction and HLLC: many faces fall back to their cells' states
+    (negative reconstructed density); FP64 right-hand side bit-identical to
+    the oracle, FP32 finite and below 1e-3 (3e-5 of p / dx)."""
+    def ic(cfg, geo, keys):
+        X, Y, Z, dx = I.cell_centres(cfg, geo)
+        i = np.rint(X / dx[:, None, None, None] - 0.5).astype(np.int64)
+        j = np.rint(Y / dx[:, None, None, None] - 0.5).astype(np.int64)
+        out = np.zeros((len(geo), 5, 16, 16, 16))
+        out[:, 0] = np.where((i + 2 * j) % 3 == 1, 1.0, 1e-3)
+        out[:, 4] = 1.0
+        return out
+    for prec in (I.FP64, I.FP32_ACC64):
+        cfg = I.periodic_config(base=(2, 2, 1), recon=I.RECON_LINEAR, flux=I.FLUX_HLLC)
+        o, g = make_pair(cfg, ic, ())
+        g = mrb.Context(dataclasses.replace(cfg, precision=prec), 4)
+        k, geo = g.list_blocks()
+        g.set_state(k, ic(cfg, geo, k))
+        o.fill_halos()
+        g.fill_halos()
+        ref = o.compute_rhs()
+        got = g.compute_rhs().cpu().numpy()
+        assert np.isfinite(got).all()
+        if prec == I.FP64:
+            close(got, ref, what="HLLC fallback rhs")
+            assert np.array_equal(got, ref)
+        else:
+            # the exact right-hand side is zero (uniform pressure at rest); the
+            # FP32 residue stays far below the scale p / dx = 32 of its terms
+            print("FP32 HLLC fallback rhs: max |L|", np.abs(got).max())
+            assert np.abs(got - ref).max() <= 1e-3
 
 
 def test_flux_census_matches_oracle():

@@ -45,6 +45,9 @@ MUTATIONS = {
     "jump_face_mean": ("double val = 0.25 * ((f(0, 0) + f(1, 0)) + (f(0, 1) + f(1, 1)));",
                        "double val = 0.25 * ((f(0, 0) + f(1, 0)) + (f(0, 1) + f(0, 1)));",
                        "test_conservation_periodic_with_jumps"),
+    "hllc_no_fallback": ("    if (!admissible(UL, g, B) || !admissible(UR, g, B)) {\n      for (int j = 0; j < 5; ++j) {\n        UL[j] = Ur[2][j];",
+                         "    if (false) {\n      for (int j = 0; j < 5; ++j) {\n        UL[j] = Ur[2][j];",
+                         "test_hllc_inadmissible_face_state_falls_back_to_the_cells"),
     "wenoao_quartic_smoothness": ("(781.0 / 20.0) * (u3 * u3)", "(781.0 / 30.0) * (u3 * u3)",
                                   "test_wenoao_matches_its_definition"),
     "wenoao_weight_exponent": ("double w5 = g5 * (1.0 + r5 * r5)", "double w5 = g5 * (1.0 + r5)",

@@ -490,6 +490,23 @@ def test_flux_census_closed_forms():
     assert list(c) == [0, 2 * F // 3, 2 * F // 3, 2 * F // 3, 0, F]
 
 
+def test_hllc_inadmissible_face_state_falls_back_to_the_cells():
+    """A density that oscillates cell to cell at constant pressure, at rest:
+    the linear reconstruction of the entropy field gives a negative face
+    density, so the face takes HLLC of its two cells' states, here the
+    pressure alone (without the fallback the sound speed would be NaN)."""
+    eps = 1e-3
+    U6 = np.array([_cons(r, 0.0, 0.0, 0.0, 1.0) for r in (eps, 1.0, eps, eps, 1.0, eps)])
+    assert oracle.linear5([eps, 1.0, eps, eps, 1.0]) < 0
+    for d in range(3):
+        U = np.array([_to_axis(u, d) for u in U6])
+        F = oracle.face_flux(U, d, mode=I.RECON_LINEAR, flux=I.FLUX_HLLC)
+        assert np.array_equal(F, oracle.hllc(U[2], U[3], d))
+        ref = np.zeros(5)
+        ref[1 + d] = 1.0
+        assert np.array_equal(F, ref)
+
+
 def test_hllc_face_flux_on_a_step_is_the_riemann_flux():
     """The same step through the HLLC face flux: the reconstructed face
     states are the two sides' states (TENO5 on a step), so the face flux is
