@@ -65,8 +65,15 @@ MUTATIONS = {
 }
 
 
+def _run_pin(so, pin, threads):
+    env = dict(os.environ, ORC_LIB=so, OMP_NUM_THREADS=str(threads))
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", f"{PINS}::{pin}"],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+
+
 @pytest.fixture(scope="module")
-def mutants(tmp_path_factory):
+def outcomes(tmp_path_factory):
+    """Build every mutant, then run each one's pin, all concurrently."""
     src = open(SRC).read()
     d = tmp_path_factory.mktemp("mutants")
     jobs = {}
@@ -75,16 +82,18 @@ def mutants(tmp_path_factory):
         p = os.path.join(d, mid + ".cpp")
         open(p, "w").write(src.replace(old, new))
         jobs[mid] = (p, os.path.join(d, mid + ".so"))
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+    ncpu = os.cpu_count() or 1
+    with cf.ThreadPoolExecutor(max_workers=min(8, ncpu)) as ex:
         list(ex.map(lambda j: oracle.compile_to(*j), jobs.values()))
-    return {mid: so for mid, (_, so) in jobs.items()}
+    workers = min(len(MUTATIONS), max(1, ncpu // 2))
+    threads = max(1, ncpu // workers)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {mid: ex.submit(_run_pin, jobs[mid][1], MUTATIONS[mid][2], threads) for mid in MUTATIONS}
+        return {mid: f.result() for mid, f in futs.items()}
 
 
 @pytest.mark.parametrize("mid", sorted(MUTATIONS))
-def test_pin_catches_planted_mistake(mutants, mid):
-    pin = MUTATIONS[mid][2]
-    env = dict(os.environ, ORC_LIB=mutants[mid], OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", f"{PINS}::{pin}"],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode == 1, (mid, pin, r.stdout[-2000:])
+def test_pin_catches_planted_mistake(outcomes, mid):
+    r = outcomes[mid]
+    assert r.returncode == 1, (mid, MUTATIONS[mid][2], r.stdout[-2000:])
     assert "failed" in r.stdout, (mid, r.stdout[-2000:])

@@ -736,7 +736,7 @@ def test_fifth_order_convergence_density_wave(axis, recon):
     """Smooth advected density wave, exact cell averages; observed L1 order
     (WENO5-JS along each axis, TENO5 and WENO-AO(5,3) along x)."""
     errs = []
-    t_end = 0.05
+    t_end = 0.02
     for n in (32, 64, 128):
         base = [1, 1, 1]
         base[axis] = n // 16
