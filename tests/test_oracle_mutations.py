@@ -48,6 +48,12 @@ MUTATIONS = {
     "hllc_no_fallback": ("    if (!admissible(UL, g, B) || !admissible(UR, g, B)) {\n      for (int j = 0; j < 5; ++j) {\n        UL[j] = Ur[2][j];",
                          "    if (false) {\n      for (int j = 0; j < 5; ++j) {\n        UL[j] = Ur[2][j];",
                          "test_hllc_inadmissible_face_state_falls_back_to_the_cells"),
+    "detail_relative_to_prediction": ("double r = std::fabs(uf - pr) / std::fabs(uf);",
+                                      "double r = std::fabs(uf - pr) / std::fabs(pr);",
+                                      "test_detail_norm_of_a_single_perturbed_cell"),
+    "detail_without_halo": ("        if (ghost) continue;\n        for (int vi = 0; vi < 2; ++vi) {",
+                            "        if (ghost || sx || sy || sz) continue;\n        for (int vi = 0; vi < 2; ++vi) {",
+                            "test_detail_norm_of_a_single_perturbed_cell"),
     "wenoao_quartic_smoothness": ("(781.0 / 20.0) * (u3 * u3)", "(781.0 / 30.0) * (u3 * u3)",
                                   "test_wenoao_matches_its_definition"),
     "wenoao_weight_exponent": ("double w5 = g5 * (1.0 + r5 * r5)", "double w5 = g5 * (1.0 + r5)",

@@ -876,6 +876,36 @@ def test_tags_refine_at_discontinuity_and_valid_octree():
             assert (k >> 56 << 56) | (m >> 3) in allk
 
 
+def test_detail_norm_of_a_single_perturbed_cell():
+    """The block detail norm on a uniform state, where every prediction is
+    exact, with one interior cell of one leaf perturbed after the
+    projection: relative density e gives delta = e / (1 + e) (|d| / |u| with
+    the leaf's value); a pressure perturbation at rest changes E by the same
+    factor and gives the same delta; the leaves whose halos hold that cell
+    see it too (the norm includes the halo), every other leaf stays at 0."""
+    cfg = I.periodic_config(base=(2, 2, 2), lmax=1)
+    o = oracle.Oracle(cfg)
+    o.set_state(o.keys(), I.ic_uniform(cfg, o.geometry(), vel=(0.0, 0.0, 0.0)))
+    o.fill_halos()
+    o.remesh(np.ones(o.n_leaves(), np.int8))
+    keys, geo = o.keys(), o.geometry()
+    base = I.ic_uniform(cfg, geo, vel=(0.0, 0.0, 0.0))
+    e = 1e-2
+    for var in (0, 4):
+        prim = base.copy()
+        o.set_state(keys, prim)
+        o.project()
+        b = 9                                            # an interior leaf of level 1
+        prim[b, var, 15, 15, 15] *= 1.0 + e              # its corner cell next to three neighbours
+        o.set_state(keys, prim)
+        o.fill_halos()
+        _, delta = o.predict_and_tag(allow_refine=False)
+        assert abs(delta[b] - e / (1.0 + e)) < 1e-13
+        hit = np.flatnonzero(delta)
+        assert b in hit and len(hit) == 8                # the leaf and the seven leaves sharing that corner
+        assert np.allclose(delta[hit], e / (1.0 + e), rtol=0, atol=1e-13)
+
+
 def test_refined_groups_are_not_coarsened_right_away():
     """Blocks refined by the analysis between steps get children predicted
     from them, which have no details of their own; while the parent's detail
