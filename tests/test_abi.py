@@ -55,3 +55,26 @@ def test_pool_bytes_and_config_checks():
     assert mrb.pool_bytes(I.sod_config(recon=5), 8) == 0
     assert mrb.pool_bytes(I.sod_config(flux=3), 8) == 0
     assert mrb.pool_bytes(I.sod_config(flux=-1), 8) == 0
+
+
+def context_functions():
+    """Declared functions whose first parameter is the context."""
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", f)).read(), flags=re.S)
+            names += re.findall(r"\bint\s+(mrb_[a-z0-9_]+)\s*\(\s*mrb_ctx\s*\*", src)
+    return sorted(set(names))
+
+
+def test_every_context_call_rejects_a_null_context():
+    """Each call that takes a context returns MRB_EINVAL for a null one (and
+    leaves a message for mrb_last_error), before touching any device."""
+    L = mrb.lib()
+    names = context_functions()
+    assert len(names) >= 20
+    for n in names:
+        f = getattr(L, n)
+        args = [None if t in (ctypes.c_void_p,) else t(0) for t in f.argtypes]
+        assert f(*args) == mrb.MRB_EINVAL, n
+        assert L.mrb_last_error(None), n
