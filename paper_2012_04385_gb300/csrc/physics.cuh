@@ -1,8 +1,10 @@
 // Device physics of the block-based MR Euler method (arXiv:2012.04385):
 // stiffened-gas EOS and Euler fluxes (Eq. Euler, Eq. StiffenedGas), the Roe
-// eigensystem, WENO5-JS / linear 5th-order reconstruction in characteristic
-// variables with the Roe / local Lax-Friedrichs switch per field (Sec. 2.2).
-// The prediction of Eq. (Prediction) lives in mr.cuh.
+// eigensystem, WENO5-JS / TENO5 / WENO-AO(5,3) / linear 5th-order
+// reconstruction in characteristic variables with the Roe / local
+// Lax-Friedrichs switch per field, the standalone LLF and HLLC fluxes
+// (Sec. 2.2), and the Navier-Stokes viscous flux.  The prediction of
+// Eq. (Prediction) lives in mr.cuh.
 //
 // Every formula is written in one fixed evaluation order.  The FP64 kernels are
 // compiled without FMA contraction (-fmad=false), so each double result is the

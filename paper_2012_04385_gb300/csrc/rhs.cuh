@@ -1,5 +1,7 @@
-// Fused right-hand side + TVD-RK3 stage kernel (Sec. 2.2 and Alg. ComputeLoop of
-// arXiv:2012.04385, with the Shu-Osher third-order Runge-Kutta stages).
+// Fused right-hand side + Runge-Kutta stage kernel of the FP64 path (Sec. 2.2
+// and Alg. ComputeLoop of arXiv:2012.04385, with the Shu-Osher TVD-RK3 or
+// TVD-RK2 stages); every reconstruction, flux scheme and the viscous terms
+// are run-time choices here.
 //
 // One CTA works on one z-slab (16 x 16 x TZ internal cells) of one leaf block
 // at a time, looping over (leaf, slab) items.  For each direction it computes

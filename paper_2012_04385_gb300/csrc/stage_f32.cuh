@@ -1,7 +1,9 @@
 // Mixed-precision fused stage kernel (MRB_FP32_ACC64): characteristic WENO5-JS
 // with the Roe / local Lax-Friedrichs switch (Sec. 2.2 of arXiv:2012.04385) in
-// FP32, flux differences accumulated per cell in FP32, and the TVD-RK3 update
-// of the FP64 state in FP64.
+// FP32, flux differences accumulated per cell in FP32, and the Runge-Kutta
+// stage update of the FP64 state in FP64.  The same kernel template covers the
+// other reconstructions (TENO5, WENO-AO(5,3), linear, the learned selector),
+// the LLF and HLLC flux schemes and the viscous terms (see rec5 and MODE).
 //
 // Work item = (leaf, z-slab of 16 x 16 x 4 cells); a CTA of 256 threads loops
 // over items.  The FP64 stage buffer is converted into FP32 primitive records
