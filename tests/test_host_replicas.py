@@ -88,3 +88,22 @@ def test_reference_arm_json_contract():
     cb = res["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == res["value"] and cb["sample"]
     assert res["e2e"] == {"value": res["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_roofline_flop_accounting():
+    """bench.py's FLOP count per face: all fields upwinded with WENO5 gives
+    the Roe eigensystem, the six g projections, the tests, R g and five WENO5
+    reconstructions; a field that splits adds its v projection, the split and
+    a second reconstruction; linear faces replace WENO5 on fields 0, 1, 4."""
+    sys.path.insert(0, ROOT)
+    import bench
+    base = bench.FLOP_ROE + bench.FLOP_PROJ_G + bench.FLOP_TESTS + bench.FLOP_RG
+    pf, pc = bench.roofline_numbers(0.0)
+    assert pf == base + 5 * bench.FLOP_WENO
+    assert pc == 3 * (17 / 16 * pf + 22 / 16 * 25) + 50
+    pf1, _ = bench.roofline_numbers(0.0, (1.0, 0.0, 0.0, 0.0, 0.0))
+    assert pf1 - pf == bench.FLOP_V[0] + bench.FLOP_SPLIT + bench.FLOP_WENO
+    pf2, _ = bench.roofline_numbers(0.0, (0.0, 0.0, 0.5, 0.0, 0.0))
+    assert pf2 - pf == 0.5 * (bench.FLOP_V[2] + bench.FLOP_SPLIT + bench.FLOP_WENO)
+    pl, _ = bench.roofline_numbers(1.0)
+    assert pf - pl == 3 * (bench.FLOP_WENO - bench.FLOP_LIN)
