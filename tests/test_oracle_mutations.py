@@ -54,6 +54,11 @@ MUTATIONS = {
     "detail_without_halo": ("        if (ghost) continue;\n        for (int vi = 0; vi < 2; ++vi) {",
                             "        if (ghost || sx || sy || sz) continue;\n        for (int vi = 0; vi < 2; ++vi) {",
                             "test_detail_norm_of_a_single_perturbed_cell"),
+    "rk3_weights": ("const double RK_B3[3] = {1.0, 0.25, 2.0 / 3.0};", "const double RK_B3[3] = {1.0, 0.3, 2.0 / 3.0};",
+                    "test_fifth_order_convergence_density_wave[0-0]"),
+    "projection_weight": ("P.u[(size_t)v2 * NCELL + sidx(I, J, K)] = 0.125 * (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7)));",
+                          "P.u[(size_t)v2 * NCELL + sidx(I, J, K)] = 0.125 * (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c6)));",
+                          "test_projection_is_the_mean_of_the_children"),
     "wenoao_quartic_smoothness": ("(781.0 / 20.0) * (u3 * u3)", "(781.0 / 30.0) * (u3 * u3)",
                                   "test_wenoao_matches_its_definition"),
     "wenoao_weight_exponent": ("double w5 = g5 * (1.0 + r5 * r5)", "double w5 = g5 * (1.0 + r5)",

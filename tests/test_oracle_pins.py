@@ -526,6 +526,40 @@ def test_hllc_face_flux_on_a_step_is_the_riemann_flux():
 
 
 # ------------------------------------------------------------------ MR operators
+def test_projection_is_the_mean_of_the_children():
+    """Eq. (Averaging) by brute force: after the projection every parent cell
+    is the mean of the eight child cells that cover it (children in Morton
+    order), on random leaf states two levels deep."""
+    cfg = I.periodic_config(base=(1, 1, 1), lmax=2)
+    o = oracle.Oracle(cfg)
+    o.fill_halos()
+    o.remesh(np.ones(o.n_leaves(), np.int8))
+    o.fill_halos()
+    g = o.geometry()
+    o.remesh((g[:, 1] + g[:, 2] + g[:, 3] == 1).astype(np.int8))
+    k = o.keys()
+    o.set_state(k, I.random_states(len(k), seed=12))
+    o.project()
+    allk = o.keys(leaves_only=False)
+    U = {int(a): b for a, b in zip(allk, o.get_state(allk))}
+    inst_mask = (1 << 56) - 1
+    checked = 0
+    for key in allk:
+        key = int(key)
+        kids = [((key & inst_mask) << 3) | c for c in range(8)]
+        if kids[0] not in U:
+            continue
+        parent = np.zeros((5, 16, 16, 16))
+        for c, kk in enumerate(kids):
+            cx, cy, cz = c & 1, (c >> 1) & 1, (c >> 2) & 1
+            child = U[kk]
+            avg = child.reshape(5, 8, 2, 8, 2, 8, 2).mean(axis=(2, 4, 6))
+            parent[:, 8 * cz:8 * cz + 8, 8 * cy:8 * cy + 8, 8 * cx:8 * cx + 8] = avg
+        assert np.abs(U[key] - parent).max() <= 1e-14 * np.abs(parent).max()
+        checked += 1
+    assert checked >= 2
+
+
 def test_average_of_prediction_is_identity():
     """A(P(u)) = u (Sec. 2.3): within 4 ulp of the parent value per cell."""
     rng = np.random.default_rng(11)
