@@ -59,6 +59,9 @@ MUTATIONS = {
     "projection_weight": ("P.u[(size_t)v2 * NCELL + sidx(I, J, K)] = 0.125 * (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7)));",
                           "P.u[(size_t)v2 * NCELL + sidx(I, J, K)] = 0.125 * (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c6)));",
                           "test_projection_is_the_mean_of_the_children"),
+    "gravity_work_sign": ("n.L[(size_t)4 * NINT + t] = n.L[(size_t)4 * NINT + t] + ((mx * gx + my * gy) + mz * gz);",
+                          "n.L[(size_t)4 * NINT + t] = n.L[(size_t)4 * NINT + t] - ((mx * gx + my * gy) + mz * gz);",
+                          "test_gravity_source_term"),
     "wenoao_quartic_smoothness": ("(781.0 / 20.0) * (u3 * u3)", "(781.0 / 30.0) * (u3 * u3)",
                                   "test_wenoao_matches_its_definition"),
     "wenoao_weight_exponent": ("double w5 = g5 * (1.0 + r5 * r5)", "double w5 = g5 * (1.0 + r5)",

@@ -972,6 +972,28 @@ def test_refined_groups_are_not_coarsened_right_away():
     assert not (t2[made] == -1).any()
 
 
+def test_gravity_source_term():
+    """Eq. (Euler)'s body force: with gravity g the right-hand side gains
+    (0, rho g, m . g) in every cell (momentum density m), and nothing else."""
+    g = np.array([0.3, -0.2, 1.0])
+    Ls = []
+    for grav in ((0.0, 0.0, 0.0), tuple(g)):
+        cfg = I.periodic_config(base=(2, 1, 1), gravity=grav)
+        o = oracle.Oracle(cfg)
+        prim = I.random_states(o.n_leaves(), seed=17, rho=(0.5, 2.0), p=(0.5, 2.0), vmax=0.5)
+        o.set_state(o.keys(), prim)
+        o.fill_halos()
+        Ls.append(o.compute_rhs())
+    U = o.get_state()
+    d = Ls[1] - Ls[0]
+    scale = np.abs(Ls[0]).max()
+    assert np.abs(d[:, 0]).max() <= 1e-13 * scale
+    for i in range(3):
+        assert np.abs(d[:, 1 + i] - U[:, 0] * g[i]).max() <= 1e-13 * scale
+    ref = U[:, 1] * g[0] + U[:, 2] * g[1] + U[:, 3] * g[2]
+    assert np.abs(d[:, 4] - ref).max() <= 1e-13 * scale
+
+
 # ------------------------------------------------------------------ viscous terms
 def _linear_velocity_state(cfg, geo, A, u0, rho=1.3, p=2.0):
     X, Y, Z, _ = I.cell_centres(cfg, geo)
