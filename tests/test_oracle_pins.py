@@ -994,6 +994,28 @@ def test_gravity_source_term():
     assert np.abs(d[:, 4] - ref).max() <= 1e-13 * scale
 
 
+def test_selector_features_and_labels_special_cases():
+    """The selector's inputs and labels (a reading; the paper has no
+    selector): six equal cells give all-zero features and label 0; a step
+    between cells 2 and 3 in a supersonic flow gives nonzero features only
+    at the variation across the face (index 2 of each field's five) and
+    label 1 (WENO5 and the linear scheme differ there); resolved smooth data
+    gives label 0."""
+    U = _cons(1.0, 3.0, 0.2, -0.1, 1.0)
+    f, lab = oracle.face_features(np.tile(U, (6, 1)), 0)
+    assert not f.any() and lab == 0
+    UR = _cons(0.5, 3.5, 0.2, -0.1, 0.6)
+    f, lab = oracle.face_features(np.array([U] * 3 + [UR] * 3), 0)
+    assert lab == 1
+    for q in range(3):
+        row = f[5 * q:5 * q + 5]
+        assert row[2] != 0 and not np.delete(row, 2).any()
+    x = (np.arange(6) - 2.5) * 0.01
+    U6 = np.array([_cons(1.0 + 0.1 * xi + 0.2 * xi * xi, 3.0, 0.2, -0.1, 1.0 + 0.05 * xi) for xi in x])
+    _, lab = oracle.face_features(U6, 0)
+    assert lab == 0
+
+
 # ------------------------------------------------------------------ viscous terms
 def _linear_velocity_state(cfg, geo, A, u0, rho=1.3, p=2.0):
     X, Y, Z, _ = I.cell_centres(cfg, geo)
