@@ -74,6 +74,10 @@ MUTATIONS = {
     "prediction_coefficient": ("const double C0 = -22.0 / 128.0, C1 = 3.0 / 128.0;",
                                "const double C0 = -22.0 / 128.0, C1 = -3.0 / 128.0;",
                                "test_prediction_reproduces_quartics"),
+    "cfl_abs_of_sum": ("std::fabs(q.vel[d]) + q.c);", "std::fabs(q.vel[d] + q.c));",
+                       "test_cfl_time_step_closed_form[0.0]"),
+    "cfl_viscous_factor": ("((6.0 * C.c.mu) * ir[i])", "((2.0 * C.c.mu) * ir[i])",
+                           "test_cfl_time_step_closed_form[0.05]"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }

@@ -994,6 +994,63 @@ def test_gravity_source_term():
     assert np.abs(d[:, 4] - ref).max() <= 1e-13 * scale
 
 
+def _cfl_tree(cfg):
+    """Instance 0: level 0 -> all level 1 -> a few level 2 -> a few level 3;
+    instance 1: all level 1 (below its lmax)."""
+    o = oracle.Oracle(cfg)
+    rest = lambda n: np.concatenate([np.full((n, 1, 16, 16, 16), v) for v in (1.25, 0, 0, 0, 0.8)], axis=1)
+    o.set_state(o.keys(), rest(o.n_leaves()))
+    for step in range(3):
+        k = o.keys().astype(np.int64)
+        g = o.geometry()
+        inst = (k >> 56) & 0xFF
+        sel = [np.ones(len(g), bool), (inst == 0) & (g[:, 1] == 1) & (g[:, 2] <= 1),
+               (inst == 0) & (g[:, 0] == 2) & (g[:, 1] == 2)][step]
+        o.fill_halos()
+        o.remesh(sel.astype(np.int8))
+        o.set_state(o.keys(), rest(o.n_leaves()))
+    return o
+
+
+@pytest.mark.parametrize("mu", [0.0, 1e-4, 0.05])
+def test_cfl_time_step_closed_form(mu):
+    """Eq. (Cfl): dt = k dx_lmax / sum_i max(|v_i| + c), each maximum over all
+    leaf cells of the instance on its own, with dx of the instance's l_max
+    whatever level its fastest cell sits on; stiffened-gas sound speed
+    c^2 = gamma (p + B) / rho.  With the viscous terms the step is also
+    bounded by k dx^2 / (6 max(mu / rho)) (a reading: the explicit limit of
+    the 3D Laplacian).  Every cell has the same c; the fastest x, y and z
+    velocities sit in three different cells on levels 1, 2 and 3, so a
+    per-cell sum, a level-dependent dx or an |v + c| give other steps."""
+    g_, B, k, dx0 = 1.4, 0.3, 0.6, 1.0 / 32.0
+    cfg = I.RunConfig(n_instances=2, base_blocks=(2, 2, 2), lmax=(3, 2), dx0=dx0, gamma=g_, B=B, cfl=k, mu=mu)
+    o = _cfl_tree(cfg)
+    keys, geo = o.keys().astype(np.int64), o.geometry()
+    inst = (keys >> 56) & 0xFF
+    assert sorted(set(geo[inst == 0, 0])) == [1, 2, 3] and set(geo[inst == 1, 0]) == {1}
+    prim = np.concatenate([np.full((len(keys), 1, 16, 16, 16), v) for v in (1.25, 0, 0, 0, 0.8)], axis=1)
+    c0 = math.sqrt(g_ * (0.8 + B) / 1.25)
+
+    def leaf(i, lvl, j=1):
+        return int(np.flatnonzero((inst == i) & (geo[:, 0] == lvl))[j])
+
+    prim[leaf(0, 1), 1, 5, 4, 3] = 2.0          # x velocity, level 1
+    prim[leaf(0, 2), 2, 7, 15, 0] = -1.5        # y velocity, level 2
+    prim[leaf(0, 3), 3, 0, 0, 15] = 1.0         # z velocity, level 3
+    light = prim[leaf(0, 1, 2), :, 9, 9, 9]      # lighter cell at rest, same c
+    light[0], light[4] = 0.5, (0.8 + B) * 0.5 / 1.25 - B
+    prim[leaf(1, 1), 1:4, 2, 2, 2] = (-0.7, 0.4, 0.9)
+    o.set_state(o.keys(), prim)
+    dt = o.cfl_dt()
+    dt_c = [k * (dx0 / 8) / ((2.0 + c0) + (1.5 + c0) + (1.0 + c0)),
+            k * (dx0 / 4) / ((0.7 + c0) + (0.4 + c0) + (0.9 + c0))]
+    exp = dt_c if mu == 0 else [min(dt_c[0], k * (dx0 / 8) ** 2 / (6 * mu / 0.5)),
+                                min(dt_c[1], k * (dx0 / 4) ** 2 / (6 * mu / 1.25))]
+    if mu == 0.05:
+        assert exp[0] < dt_c[0] and exp[1] < dt_c[1]   # the viscous limit decides
+    assert np.allclose(dt, exp, rtol=1e-14, atol=0), (dt, exp)
+
+
 def test_selector_features_and_labels_special_cases():
     """The selector's inputs and labels (a reading; the paper has no
     selector): six equal cells give all-zero features and label 0; a step
