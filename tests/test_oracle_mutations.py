@@ -78,6 +78,12 @@ MUTATIONS = {
                        "test_cfl_time_step_closed_form[0.0]"),
     "cfl_viscous_factor": ("((6.0 * C.c.mu) * ir[i])", "((2.0 * C.c.mu) * ir[i])",
                            "test_cfl_time_step_closed_form[0.05]"),
+    "symmetry_mirror_index": ("else src[d] = (side == 0) ? (-1 - a) : (2 * NB - 1 - a);",
+                              "else src[d] = (side == 0) ? (-a) : (2 * NB - 1 - a);",
+                              "test_symmetry_walls_are_the_mirror_image[0-0]"),
+    "symmetry_flips_x_momentum": ("if (bc == BC_SYMMETRY && v == 1 + d) val = -val;",
+                                  "if (bc == BC_SYMMETRY && v == 1) val = -val;",
+                                  "test_symmetry_walls_are_the_mirror_image[1-2]"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }
