@@ -84,6 +84,9 @@ MUTATIONS = {
     "symmetry_flips_x_momentum": ("if (bc == BC_SYMMETRY && v == 1 + d) val = -val;",
                                   "if (bc == BC_SYMMETRY && v == 1) val = -val;",
                                   "test_symmetry_walls_are_the_mirror_image[1-2]"),
+    "face_average_top_down": ("void average_faces(Ctx& C) {\n  int lm = max_level(C);\n  for (int l = lm - 1; l >= 0; --l) {",
+                              "void average_faces(Ctx& C) {\n  int lm = max_level(C);\n  for (int l = 0; l < lm; ++l) {",
+                              "test_conservation_across_two_level_jumps"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }

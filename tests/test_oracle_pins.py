@@ -734,6 +734,36 @@ def test_conservation_periodic_with_jumps(mu):
     assert (np.abs(s1 - s0) <= 1e-13 * np.maximum(np.abs(s0), scale)).all(), (s1 - s0)
 
 
+def test_conservation_across_two_level_jumps():
+    """Periodic domain where level-1 leaves face level-3 leaves: the coarse
+    face flux is replaced by the mean over the covering level-3 faces, which
+    reaches it through the face buffers of the level-2 and level-1 internal
+    nodes (averaged bottom-up).  Mass, momentum and energy are conserved to
+    round-off over 4 steps on the fixed tree."""
+    cfg = I.periodic_config(base=(2, 2, 2), lmax=3)
+    o = oracle.Oracle(cfg)
+    ic = lambda: o.set_state(o.keys(), I.ic_random_smooth(cfg, o.geometry()))
+    ic()
+    for sel in (lambda g: np.ones(len(g), bool), lambda g: (g[:, 0] == 1) & (g[:, 1] == 1) & (g[:, 2] == 1),
+                lambda g: (g[:, 0] == 2) & (g[:, 1] == 2)):
+        o.fill_halos()
+        g = o.geometry()
+        o.remesh(sel(g).astype(np.int8))
+        ic()
+    o.project()
+    g = o.geometry()
+    assert set(g[:, 0]) == {1, 2, 3}
+    # the level-1 leaf at (0, 1, z) faces level-3 leaves across x
+    assert ((g[:, 0] == 1) & (g[:, 1] == 0) & (g[:, 2] == 1)).any()
+    assert ((g[:, 0] == 3) & (g[:, 1] == 4) & (g[:, 2] // 4 == 1)).any()
+    s0 = o.sums()
+    dt = 0.2 * cfg.dx0 / 8
+    run_fixed_dt(o, dt, 4 * dt)                     # fixed tree: the jumps stay
+    s1 = o.sums()
+    scale = np.abs(o.get_state()).max(axis=(0, 2, 3, 4))
+    assert (np.abs(s1 - s0) <= 1e-13 * np.maximum(np.abs(s0), scale)).all(), (s1 - s0)
+
+
 @pytest.mark.parametrize("flux", [I.FLUX_ROE, I.FLUX_LLF, I.FLUX_HLLC])
 def test_sod_exact_solution_and_transverse_momentum(flux):
     """Sec. 5.1: Sod along x converges to the exact solution; rho v, rho w
