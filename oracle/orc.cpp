@@ -27,7 +27,7 @@
 // isolated shocks and stationary contacts, the LLF step flux in closed form,
 // the Sod solution for each flux scheme, second order in time of TVD-RK2,
 // the CFL time step in closed form, symmetry walls as the mirror image of a
-// doubled periodic box.
+// doubled periodic box, the level thresholds on perturbed cells.
 // The detail norm is a reading (the paper names only the l-infinity norm
 // over the block with its halo); a single perturbed cell on a uniform state
 // pins its parts (the leaf's value as the scale, rho and E, the halo).
@@ -1190,13 +1190,11 @@ double block_delta(Ctx& C, Node& n) {
   return delta;
 }
 
-// Tags (Eq. (Thresholding)): REFINE if delta > eps_l and l < lmax; a sibling
-// group is COARSENED if all eight are leaves at level >= 2 (no node on level 1
-// is ever coarsened, Sec. 4) with delta < eps_l; equality keeps the block.
-// Tags of the leaves (Eq. Thresholding with Eq. LevelWiseEpsilon): REFINE a
-// leaf whose detail exceeds its level's threshold (below l_max); COARSEN a
-// complete group of eight leaf siblings at level >= 2 whose details are all
-// below their threshold.  In the analysis between time steps (allow_refine) a
+// Tags of the leaves (Eq. Thresholding with Eq. LevelWiseEpsilon, D = 3):
+// REFINE a leaf on level l below l_max whose detail exceeds
+// eps_l = 2^{-3 (lmax - l)} eps; COARSEN a complete group of eight leaf
+// siblings at level >= 2 (no node on level 1 is ever coarsened, Sec. 4) whose
+// details are all below eps_l; equality keeps the block.  In the analysis between time steps (allow_refine) a
 // group is kept while its parent's own detail exceeds the parent's threshold:
 // the parent would be refined again at once (its children, just predicted
 // from it, have no details), so coarsening them would make the tree

@@ -87,6 +87,12 @@ MUTATIONS = {
     "face_average_top_down": ("void average_faces(Ctx& C) {\n  int lm = max_level(C);\n  for (int l = lm - 1; l >= 0; --l) {",
                               "void average_faces(Ctx& C) {\n  int lm = max_level(C);\n  for (int l = 0; l < lm; ++l) {",
                               "test_conservation_across_two_level_jumps"),
+    "level_threshold_dimension": ("double el = std::ldexp(C.c.eps, -3 * (lmx - n.level));",
+                                  "double el = std::ldexp(C.c.eps, -2 * (lmx - n.level));",
+                                  "test_level_thresholds_decide_the_tags"),
+    "level_threshold_of_parent": ("double el = std::ldexp(C.c.eps, -3 * (lmx - n.level));",
+                                  "double el = std::ldexp(C.c.eps, -3 * (lmx - (n.level - 1)));",
+                                  "test_level_thresholds_decide_the_tags"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }

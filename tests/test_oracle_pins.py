@@ -970,6 +970,37 @@ def test_detail_norm_of_a_single_perturbed_cell():
         assert np.allclose(delta[hit], e / (1.0 + e), rtol=0, atol=1e-13)
 
 
+def test_level_thresholds_decide_the_tags():
+    """Eq. (Thresholding) with Eq. (LevelWiseEpsilon), D = 3: a leaf on level l
+    is refined when its detail exceeds eps_l = 2^{-3 (lmax - l)} eps.  On a
+    uniform state with one centre cell of a leaf scaled by 1 + r after the
+    projection, that leaf's detail is r / (1 + r) and no halo holds the cell;
+    r is placed between the thresholds of D = 3 and those of D = 2 or of the
+    parent's level, on levels 1 and 2 of a tree with leaves on levels 1-3."""
+    cfg = I.explosion_config(lmax=3, eps=1e-3)
+    o = _jump_tree(cfg, lambda c, g: I.ic_uniform(c, g, vel=(0.0, 0.0, 0.0)))
+    keys, geo = o.keys(), o.geometry()
+    prim = I.ic_uniform(cfg, geo, vel=(0.0, 0.0, 0.0))
+    eps_l = {l: 1e-3 * 2.0 ** (-3 * (3 - l)) for l in (1, 2, 3)}      # 1.5625e-5, 1.25e-4, 1e-3
+    lv = lambda l, j: int(np.flatnonzero(geo[:, 0] == l)[j])
+    # (leaf, r, refined?)
+    cases = [(lv(1, 0), 3e-5, True),     # eps_1 < r < 2^{-2*2} eps (D = 2)
+             (lv(1, 1), 1e-5, False),    # 2^{-3*3} eps (eps of level 0) < r < eps_1
+             (lv(2, 0), 2e-4, True),     # eps_2 < r < 2^{-2} eps (D = 2)
+             (lv(2, 9), 1e-4, False),    # eps_1 < r < eps_2
+             (lv(3, 0), 5e-3, False)]    # above eps_3, but l = lmax
+    for b, r, _ in cases:
+        prim[b, 0, 8, 8, 8] *= 1.0 + r
+    o.set_state(keys, prim)
+    o.fill_halos()
+    tags, delta = o.predict_and_tag()
+    for b, r, refined in cases:
+        assert abs(delta[b] - r / (1.0 + r)) < 1e-15, (b, delta[b], r)
+        assert (tags[b] == oracle.TAG_REFINE) == refined, (b, geo[b, 0], r, tags[b])
+    others = np.setdiff1d(np.arange(len(keys)), [c[0] for c in cases])
+    assert not delta[others].any() and (tags[others] != oracle.TAG_REFINE).all()
+
+
 def test_refined_groups_are_not_coarsened_right_away():
     """Blocks refined by the analysis between steps get children predicted
     from them, which have no details of their own; while the parent's detail
