@@ -27,7 +27,8 @@
 // isolated shocks and stationary contacts, the LLF step flux in closed form,
 // the Sod solution for each flux scheme, second order in time of TVD-RK2,
 // the CFL time step in closed form, symmetry walls as the mirror image of a
-// doubled periodic box, the level thresholds on perturbed cells.
+// doubled periodic box, the level thresholds on perturbed cells, each
+// refined octant and the halo fill at jumps exact on a quartic.
 // The detail norm is a reading (the paper names only the l-infinity norm
 // over the block with its halo); a single perturbed cell on a uniform state
 // pins its parts (the leaf's value as the scale, rho and E, the halo).

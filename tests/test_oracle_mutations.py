@@ -93,6 +93,15 @@ MUTATIONS = {
     "level_threshold_of_parent": ("double el = std::ldexp(C.c.eps, -3 * (lmx - n.level));",
                                   "double el = std::ldexp(C.c.eps, -3 * (lmx - (n.level - 1)));",
                                   "test_level_thresholds_decide_the_tags"),
+    "child_coordinate_bits": ("for (int d = 0; d < 3; ++d) c.X[d] = 2 * P.X[d] + ((ch >> d) & 1);",
+                              "for (int d = 0; d < 3; ++d) c.X[d] = 2 * P.X[d] + ((ch >> (2 - d)) & 1);",
+                              "test_refinement_puts_each_prediction_in_its_octant"),
+    "halo_predicted_from_wrong_octant": ("val = predict_cell(&par->u[(size_t)v * NCELL], ch, i, j, k);",
+                                         "val = predict_cell(&par->u[(size_t)v * NCELL], ch ^ 1, i, j, k);",
+                                         "test_halo_fill_is_exact_on_a_quartic_with_jumps"),
+    "halo_fill_fine_to_coarse": ("  for (int l = 0; l <= lm; ++l) {\n    std::vector<Node*> v = nodes_at(C, l, false);\n#pragma omp parallel for schedule(dynamic)\n    for (long t = 0; t < (long)v.size(); ++t) fill_node(",
+                                 "  for (int l = lm; l >= 0; --l) {\n    std::vector<Node*> v = nodes_at(C, l, false);\n#pragma omp parallel for schedule(dynamic)\n    for (long t = 0; t < (long)v.size(); ++t) fill_node(",
+                                 "test_halo_fill_is_exact_on_a_quartic_with_jumps"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }

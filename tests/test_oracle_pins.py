@@ -560,6 +560,96 @@ def test_projection_is_the_mean_of_the_children():
     assert checked >= 2
 
 
+def _poly_cell_averages(cfg, geo, C, halo=0):
+    """Exact cell averages of the tensor-product polynomial
+    sum_{abc} C[a, b, c] x^a y^b z^c on every cell of the listed blocks
+    (with `halo` cells on each side)."""
+    m = 16 + 2 * halo
+    out = np.zeros((len(geo), m, m, m))
+    for n, (lvl, X, Y, Z) in enumerate(geo):
+        h = cfg.dx0 * 0.5 ** lvl
+        moms = []
+        for X0 in (X, Y, Z):
+            e = (X0 * 16 - halo + np.arange(m + 1)) * h
+            moms.append(np.array([(e[1:] ** (a + 1) - e[:-1] ** (a + 1)) / ((a + 1) * h)
+                                  for a in range(C.shape[0])]))
+        out[n] = np.einsum("abc,ai,bj,ck->kji", C, *moms)
+    return out
+
+
+def test_refinement_puts_each_prediction_in_its_octant():
+    """Refining a block fills child c with the prediction of the parent's
+    octant c (child coordinates 2 X + bit d of c): on a quartic field, the
+    children of the centre block of a 3 x 3 x 3 grid (whose halo is all
+    copies of its neighbours) hold the exact cell averages on the finer grid."""
+    cfg = I.RunConfig(base_blocks=(3, 3, 3), lmax=(1,), dx0=1.0 / 48.0)
+    rng = np.random.default_rng(11)
+    C = rng.uniform(-0.3, 0.3, (5, 5, 5))
+    C[0, 0, 0], C[1, 0, 0], C[0, 1, 0], C[0, 0, 1] = 2.0, 0.7, -0.4, 0.9
+    o = oracle.Oracle(cfg)
+    geo = o.geometry()
+    prim = np.zeros((len(geo), 5, 16, 16, 16))
+    prim[:, 0] = _poly_cell_averages(cfg, geo, C)
+    prim[:, 4] = 1.0
+    o.set_state(o.keys(), prim)
+    o.fill_halos()
+    o.remesh(np.ones(len(geo), np.int8))
+    geo1 = o.geometry()
+    kids = np.flatnonzero(np.all(geo1[:, 1:] // 2 == 1, axis=1))
+    assert len(kids) == 8
+    rho = o.get_state()[kids, 0]
+    exact = _poly_cell_averages(cfg, geo1[kids], C)
+    assert np.abs(rho - exact).max() < 1e-13 * np.abs(exact).max()
+
+
+def test_halo_fill_is_exact_on_a_quartic_with_jumps():
+    """Sec. 3's halo fill on a tree with jumps of one and two levels: regions
+    facing a same-level node are copies, the others are predicted from the
+    node's own parent (levels coarse to fine).  Prediction and projection are
+    exact on a tensor-product quartic, so after the projection every halo
+    cell of every leaf inside the domain holds the exact cell average of the
+    quartic on that leaf's grid, even where the halos held another field
+    before (so a fill that reads a parent's halo before that parent is
+    filled shows)."""
+    cfg = I.RunConfig(base_blocks=(4, 4, 4), lmax=(3,), dx0=1.0 / 64.0)
+    rng = np.random.default_rng(12)
+    C = rng.uniform(-0.3, 0.3, (5, 5, 5))
+    C[0, 0, 0], C[1, 0, 0], C[0, 1, 0], C[0, 0, 1] = 2.0, 0.7, -0.4, 0.9
+    o = oracle.Oracle(cfg)
+
+    def put(Cp):
+        geo = o.geometry()
+        prim = np.zeros((len(geo), 5, 16, 16, 16))
+        prim[:, 0] = _poly_cell_averages(cfg, geo, Cp)
+        prim[:, 4] = 1.0
+        o.set_state(o.keys(), prim)
+
+    other = C.copy()
+    other[1:] = -other[1:]
+    put(other)
+    for sel in (lambda g: (g[:, 0] == 0) & np.all((g[:, 1:] >= 1) & (g[:, 1:] <= 2), axis=1),
+                lambda g: (g[:, 0] == 1) & (g[:, 1] == 3) & (g[:, 2] <= 4),
+                lambda g: (g[:, 0] == 2) & (g[:, 1] == 7)):
+        o.fill_halos()
+        o.remesh(sel(o.geometry()).astype(np.int8))
+        put(other)
+    o.project()
+    o.fill_halos()          # every halo now holds another quartic's values
+    put(C)
+    o.project()
+    o.fill_halos()
+    geo = o.geometry()
+    assert set(geo[:, 0]) == {0, 1, 2, 3}
+    inner = np.all((geo[:, 1:] >> geo[:, :1]) >= 1, axis=1) & np.all((geo[:, 1:] >> geo[:, :1]) <= 2, axis=1)
+    assert set(geo[inner, 0]) == {1, 2, 3}
+    # a level-1 leaf facing level-3 leaves across x (a jump of two levels)
+    assert ((geo[:, 0] == 1) & (geo[:, 1] == 4) & (geo[:, 2] == 2)).any()
+    U = o.get_state(with_halo=True)[inner, 0]
+    exact = _poly_cell_averages(cfg, geo[inner], C, halo=4)
+    assert U.shape == exact.shape
+    assert np.abs(U - exact).max() < 1e-12 * np.abs(exact).max()
+
+
 def test_average_of_prediction_is_identity():
     """A(P(u)) = u (Sec. 2.3): within 4 ulp of the parent value per cell."""
     rng = np.random.default_rng(11)
