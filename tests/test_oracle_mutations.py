@@ -102,6 +102,9 @@ MUTATIONS = {
     "halo_fill_fine_to_coarse": ("  for (int l = 0; l <= lm; ++l) {\n    std::vector<Node*> v = nodes_at(C, l, false);\n#pragma omp parallel for schedule(dynamic)\n    for (long t = 0; t < (long)v.size(); ++t) fill_node(",
                                  "  for (int l = lm; l >= 0; --l) {\n    std::vector<Node*> v = nodes_at(C, l, false);\n#pragma omp parallel for schedule(dynamic)\n    for (long t = 0; t < (long)v.size(); ++t) fill_node(",
                                  "test_halo_fill_is_exact_on_a_quartic_with_jumps"),
+    "sibling_lookup_drops_instance": ("uint64_t sk = ((pk << 3) | (uint64_t)c) | (inst << 56);",
+                                      "uint64_t sk = ((pk << 3) | (uint64_t)c);",
+                                      "test_instances_evolve_independently"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }
