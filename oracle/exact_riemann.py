@@ -7,7 +7,8 @@ Dynamics, ch. 4): the star pressure is the root of
 f(p) = f_L(p) + f_R(p) + (u_R - u_L), each f_K the shock (Rankine-Hugoniot) or
 rarefaction (isentropic) branch, found by Newton iteration; the solution is then
 sampled along x/t.  Pinned itself by the published star values of Toro's test 1
-(tests/golden/toro_test1.txt).
+(tests/golden/toro_test1.txt), and by the integral conservation laws and the
+Rankine-Hugoniot speeds of its sampled solution.
 """
 from __future__ import annotations
 

@@ -894,6 +894,48 @@ def test_conservation_across_two_level_jumps():
     assert (np.abs(s1 - s0) <= 1e-13 * np.maximum(np.abs(s0), scale)).all(), (s1 - s0)
 
 
+@pytest.mark.parametrize("left,right", [
+    ((1.0, 0.0, 1.0), (0.125, 0.0, 0.1)),            # shock, contact, rarefaction
+    ((1.0, -2.0, 0.4), (1.0, 2.0, 0.4)),             # two rarefactions, near vacuum
+    ((1.0, 0.0, 1000.0), (1.0, 0.0, 0.01)),          # strong shock
+    ((5.99924, 19.5975, 460.894), (5.99242, -6.19633, 46.0950)),   # two shocks
+    ((0.5, 1.2, 0.3), (2.0, -0.4, 1.5)),             # shock to the left, shock to the right
+])
+def test_exact_riemann_solution_conserves(left, right):
+    """The sampled exact solution (test infrastructure of the Sod pin) obeys
+    the integral conservation laws: at t = 1 over [a, b] around the waves,
+    the integral of U is -a U_L + b U_R - (F(U_R) - F(U_L)); and for the star
+    values, the Rankine-Hugoniot jump of a shock is satisfied by the wave's
+    own speed.  Independent of how the solver finds p* or samples the fan."""
+    g = 1.4
+
+    def cons(r, u, p):
+        return np.array([r, r * u, p / (g - 1) + 0.5 * r * u * u])
+
+    def flux(r, u, p):
+        E = p / (g - 1) + 0.5 * r * u * u
+        return np.array([r * u, r * u * u + p, u * (E + p)])
+
+    UL, UR = cons(*left), cons(*right)
+    cmax = max(abs(left[1]) + math.sqrt(g * left[2] / left[0]), abs(right[1]) + math.sqrt(g * right[2] / right[0]))
+    a, b = -3.0 * cmax - 5.0, 3.0 * cmax + 5.0
+    n = 400000
+    xi = a + (np.arange(n) + 0.5) * (b - a) / n
+    q = er.sample(left, right, xi, g)
+    U = cons(q[0], q[1], q[2])
+    integral = U.sum(axis=1) * (b - a) / n
+    expect = -a * UL + b * UR - (flux(*right) - flux(*left))
+    scale = np.abs(UL).max() + np.abs(UR).max()
+    assert np.abs(integral - expect).max() < 2e-4 * scale * (b - a), (integral, expect)
+    # every discontinuity in the sample moves at the Rankine-Hugoniot speed
+    jumps = np.flatnonzero(np.abs(np.diff(q[0])) > 1e-3 * q[0].max())
+    for j in jumps:
+        Ua, Ub = U[:, j], U[:, j + 1]
+        Fa, Fb = flux(*q[:, j]), flux(*q[:, j + 1])
+        S = 0.5 * (xi[j] + xi[j + 1])
+        assert np.abs((Fb - Fa) - S * (Ub - Ua)).max() <= 1e-3 * (np.abs(Fb - Fa).max() + np.abs(Ub - Ua).max() + 1e-300)
+
+
 @pytest.mark.parametrize("flux", [I.FLUX_ROE, I.FLUX_LLF, I.FLUX_HLLC])
 def test_sod_exact_solution_and_transverse_momentum(flux):
     """Sec. 5.1: Sod along x converges to the exact solution; rho v, rho w
