@@ -105,6 +105,12 @@ MUTATIONS = {
     "sibling_lookup_drops_instance": ("uint64_t sk = ((pk << 3) | (uint64_t)c) | (inst << 56);",
                                       "uint64_t sk = ((pk << 3) | (uint64_t)c);",
                                       "test_instances_evolve_independently"),
+    "weno5_smoothness_coefficient": ("double weno5(double a, double b, double c, double d, double e) {\n  const double eps = 1e-6;\n  double t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;\n  double beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;",
+                                     "double weno5(double a, double b, double c, double d, double e) {\n  const double eps = 1e-6;\n  double t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;\n  double beta0 = (13.0 / 12.0) * t1 * t1 + 0.5 * t2 * t2;",
+                                     "test_weno5_matches_its_definition"),
+    "weno5_eps": ("double weno5(double a, double b, double c, double d, double e) {\n  const double eps = 1e-6;",
+                  "double weno5(double a, double b, double c, double d, double e) {\n  const double eps = 1e-40;",
+                  "test_weno5_matches_its_definition"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }

@@ -90,6 +90,44 @@ def test_weno_mirror_and_discontinuity():
     assert oracle.linear5(f) < -0.1          # (2 - 13) / 60
 
 
+def _weno5_from_definition(f, eps=1e-6):
+    """WENO5-JS (Jiang & Shu 1996) from its definitions: the three parabolas
+    through the cell averages of cells -2..0, -1..1, 0..2 (linear systems),
+    smoothness beta_k = sum over l = 1, 2 of the integral of (d^l p_k)^2 over
+    the middle cell (unit spacing, exact polynomial integration), weights
+    d_k / (eps + beta_k)^2 with d = (0.1, 0.6, 0.3), value at the right face."""
+    P = np.polynomial.polynomial
+
+    def fit(cells):
+        A = np.array([[((j + .5) ** (k + 1) - (j - .5) ** (k + 1)) / (k + 1) for k in range(3)] for j in cells])
+        return np.linalg.solve(A, np.array([f[j + 2] for j in cells]))
+
+    polys = [fit([-2, -1, 0]), fit([-1, 0, 1]), fit([0, 1, 2])]
+    beta = []
+    for c in polys:
+        tot = 0.0
+        for l in (1, 2):
+            d = P.polyder(c, l)
+            sq = P.polyint(P.polymul(d, d))
+            tot += P.polyval(0.5, sq) - P.polyval(-0.5, sq)
+        beta.append(tot)
+    a = np.array([dk / (eps + bk) ** 2 for dk, bk in zip((0.1, 0.6, 0.3), beta)])
+    return float(sum(ak * P.polyval(0.5, c) for ak, c in zip(a / a.sum(), polys)))
+
+
+def test_weno5_matches_its_definition():
+    """Random smooth-to-discontinuous data over six decades of scale (so the
+    absolute eps = 1e-6 both matters and does not): the oracle's WENO5-JS
+    equals its definition computed from polynomial fits and exact integrals."""
+    rng = np.random.default_rng(29)
+    for _ in range(400):
+        scale = 10.0 ** rng.uniform(-4, 2)
+        x = np.arange(5.0)
+        f = scale * (np.sin(rng.uniform(0.1, 2.5) * x + rng.uniform(0, 6)) + rng.uniform(0, 2) * (x >= rng.integers(1, 5)))
+        ref = _weno5_from_definition(f)
+        assert abs(oracle.weno5(f) - ref) <= 1e-12 * max(scale, abs(ref)), (f, ref)
+
+
 # ------------------------------------------------------------------ TENO5
 def test_teno5_cutoff_keeps_the_smooth_side_exactly():
     """At a step, the stencils that cross it are cut off and the one-sided
