@@ -111,6 +111,15 @@ MUTATIONS = {
     "weno5_eps": ("double weno5(double a, double b, double c, double d, double e) {\n  const double eps = 1e-6;",
                   "double weno5(double a, double b, double c, double d, double e) {\n  const double eps = 1e-40;",
                   "test_weno5_matches_its_definition"),
+    "detail_norm_reads_momentum": ("const int vars[2] = {0, 4};", "const int vars[2] = {0, 1};",
+                                   "test_detail_norm_of_a_single_perturbed_cell"),
+    "viscous_limit_takes_max_rho": ("ir[n.inst] = std::max(ir[n.inst], 1.0 / q.rho);", "ir[n.inst] = std::max(ir[n.inst], q.rho);",
+                                    "test_cfl_time_step_closed_form[0.05]"),
+    "stiffened_pressure_offset": ("q.p = (g - 1.0) * (U[4] - 0.5 * q.rho * q2) - g * B;",
+                                  "q.p = (g - 1.0) * (U[4] - 0.5 * q.rho * q2) - B;",
+                                  "test_cfl_time_step_closed_form[0.0]"),
+    "hllc_left_speed_without_roe": ("double SL = std::min(uL - a.c, e.lam[0]);", "double SL = uL - a.c;",
+                                    "test_hllc_exact_on_isolated_shocks[0]"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }
