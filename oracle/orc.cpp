@@ -19,7 +19,7 @@
 // Pins (tests/test_oracle_*.py): free-stream preservation, conservation on
 // periodic domains, the exact Sod solution, 5th-order convergence on an advected
 // density wave, L.R = I and the Roe property of the eigensystem, WENO5/linear
-// special cases, A(P(u)) = u and quartic reproduction of P, the Morton
+// special cases, WENO5-JS against its definition, A(P(u)) = u and quartic reproduction of P, the Morton
 // neighbour example of Fig. (NeighborLookup) and brute force in all 26
 // directions, tag invariants, the Roe/LLF per-field switch in closed form on a
 // transonic step, TENO5 cutoff and smooth-data cases, WENO-AO(5,3)
@@ -28,7 +28,10 @@
 // the Sod solution for each flux scheme, second order in time of TVD-RK2,
 // the CFL time step in closed form, symmetry walls as the mirror image of a
 // doubled periodic box, the level thresholds on perturbed cells, each
-// refined octant and the halo fill at jumps exact on a quartic.
+// refined octant and the halo fill at jumps exact on a quartic, batched
+// instances bit-identical to each run alone, conservation across two-level
+// jumps, the gravity source term, the projection by brute force, the viscous
+// terms on a linear velocity field and the shear-wave decay.
 // The detail norm is a reading (the paper names only the l-infinity norm
 // over the block with its halo); a single perturbed cell on a uniform state
 // pins its parts (the leaf's value as the scale, rho and E, the halo).
