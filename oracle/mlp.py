@@ -12,7 +12,9 @@ BF16 operands: the GPU rounds inputs, weights and hidden activations to
 bfloat16 and accumulates in FP32.  This reference applies the same roundings
 (round to nearest even on the upper 16 bits) and accumulates in FP64, so that
 GPU and reference differ only by the accumulation precision.  Pinned by
-central finite differences on the unrounded network (tests/test_oracle_mlp.py).
+central finite differences on the unrounded network, and against torch's own
+Linear / GELU(tanh) / BCEWithLogitsLoss layers with autograd, its bfloat16
+conversion and its Adam optimiser (tests/test_oracle_mlp.py).
 
 Parameter vector layout (1601 floats): W1[32][15] (out x in), b1[32],
 W2[32][32], b2[32], w3[32], b3[1].
