@@ -1495,3 +1495,19 @@ def test_symmetry_walls_are_the_mirror_image(lmax, axis):
     err = np.abs(U1 - U2).max(axis=(0, 2, 3, 4))
     assert (err <= 1e-12 * scale).all(), err / scale
     assert np.abs(U1[:, 1 + axis]).max() > 0.1           # a flow through the wall region
+
+
+# ------------------------------------------------------------------ workload inputs
+@pytest.mark.parametrize("mach", [1.22, 2.0, 5.0])
+def test_post_shock_state_satisfies_rankine_hugoniot(mach):
+    """The shock-bubble workload's post-shock state: the jumps of mass,
+    momentum and energy flux across a shock moving at mach * c1 into gas at
+    rest balance the jumps of the conserved variables times that speed."""
+    g = 1.4
+    r2, u2, p2 = I.post_shock_state(mach, g)
+    S = mach * math.sqrt(g)
+    U1, U2 = np.array([1.0, 0.0, 1.0 / (g - 1)]), np.array([r2, r2 * u2, p2 / (g - 1) + 0.5 * r2 * u2 ** 2])
+    F1 = np.array([0.0, 1.0, 0.0])
+    F2 = np.array([r2 * u2, r2 * u2 ** 2 + p2, u2 * (U2[2] + p2)])
+    assert np.allclose(F2 - F1, S * (U2 - U1), rtol=1e-13, atol=1e-13)
+    assert r2 > 1.0 and p2 > 1.0 and 0 < u2 < S
