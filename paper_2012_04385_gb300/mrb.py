@@ -209,6 +209,11 @@ class Context:
     def __init__(self, cfg: RunConfig, n_slots: int, stream=None, device="cuda", mlp_params=None):
         import torch
 
+        # every step runs in the library's CUDA kernels: there is no CPU path
+        if torch.device(device).type != "cuda":
+            raise ValueError(f"the block pool must live in CUDA device memory, not on {device!r}")
+        if not torch.cuda.is_available():
+            raise RuntimeError("mrb needs a CUDA device (sm_103a); it has no CPU fallback")
         self.cfg = cfg
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()

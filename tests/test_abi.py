@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 from paper_2012_04385_gb300 import _build, mrb
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -78,3 +80,17 @@ def test_every_context_call_rejects_a_null_context():
         args = [None if t in (ctypes.c_void_p,) else t(0) for t in f.argtypes]
         assert f(*args) == mrb.MRB_EINVAL, n
         assert L.mrb_last_error(None), n
+
+
+def test_context_refuses_to_run_without_a_cuda_device():
+    """The product path has no CPU fallback: a context on the host, or on a
+    machine without a CUDA device, raises before anything is allocated."""
+    import torch
+
+    from paper_2012_04385_gb300 import inputs as I
+    from paper_2012_04385_gb300 import mrb
+    with pytest.raises(ValueError):
+        mrb.Context(I.sod_config(), 16, device="cpu")
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            mrb.Context(I.sod_config(), 16)
