@@ -94,3 +94,37 @@ def test_context_refuses_to_run_without_a_cuda_device():
     if not torch.cuda.is_available():
         with pytest.raises(RuntimeError, match="no CPU fallback"):
             mrb.Context(I.sod_config(), 16)
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle and the CUDA path are independent: the oracle's C++ includes
+    only standard and OpenMP headers, its Python modules import neither the
+    product package nor its build; the library's sources include only their
+    own headers and CUDA's, and the package's modules never import the
+    oracle.  Only the seeded input generators (inputs.py) serve both."""
+    import ast
+    import glob
+
+    def imports(path):
+        mods = set()
+        for node in ast.walk(ast.parse(open(path).read())):
+            if isinstance(node, ast.Import):
+                mods.update(a.name.split(".")[0] for a in node.names)
+            elif isinstance(node, ast.ImportFrom) and node.module and node.level == 0:
+                mods.add(node.module.split(".")[0])
+        return mods
+
+    for path in glob.glob(os.path.join(ROOT, "oracle", "*.py")):
+        assert "paper_2012_04385_gb300" not in imports(path), path
+    for path in glob.glob(os.path.join(ROOT, "paper_2012_04385_gb300", "*.py")):
+        assert "oracle" not in imports(path), path
+    inc = re.compile(r'^\s*#\s*include\s*[<"]([^>"]+)[>"]', re.M)
+    std = {"algorithm", "cmath", "cstdint", "cstring", "map", "string", "vector", "omp.h"}
+    assert set(inc.findall(open(os.path.join(ROOT, "oracle", "orc.cpp")).read())) <= std
+    csrc = os.path.join(ROOT, "paper_2012_04385_gb300", "csrc")
+    own = {os.path.basename(p) for p in glob.glob(os.path.join(csrc, "*.cuh"))} | {"mrb.h"}
+    system = {"algorithm", "cmath", "cstdint", "cstdio", "cstring", "exception", "mutex", "string", "vector",
+              "cuda_runtime.h", "cuda_bf16.h"}
+    for path in glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")):
+        for h in inc.findall(open(path).read()):
+            assert h in own | system, (path, h)
