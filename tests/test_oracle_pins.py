@@ -1511,3 +1511,41 @@ def test_post_shock_state_satisfies_rankine_hugoniot(mach):
     F2 = np.array([r2 * u2, r2 * u2 ** 2 + p2, u2 * (U2[2] + p2)])
     assert np.allclose(F2 - F1, S * (U2 - U1), rtol=1e-13, atol=1e-13)
     assert r2 > 1.0 and p2 > 1.0 and 0 < u2 < S
+
+
+# ------------------------------------------------------------------ degenerate trees
+@pytest.mark.parametrize("lmax", [0, 1])
+def test_single_periodic_block_is_its_own_neighbour(lmax):
+    """The degenerate periodic domain of one level-0 block, which is its own
+    neighbour on every side, evolves bit for bit like each copy of it in a
+    periodic domain of two identical blocks along x (and at lmax = 1 with
+    every block refined, like each half of the refined pair)."""
+    L = 1.0
+    res = []
+    for nx in (1, 2):
+        cfg = I.RunConfig(base_blocks=(nx, 1, 1), lmax=(lmax,), dx0=L / 16, bc=(I.BC_PERIODIC,) * 6)
+        o = oracle.Oracle(cfg)
+        one = I.RunConfig(base_blocks=(1, 1, 1), lmax=(lmax,), dx0=L / 16, bc=(I.BC_PERIODIC,) * 6)
+
+        def ic():
+            g = o.geometry().copy()
+            g[:, 1] %= 2 ** g[:, 0]                       # the copy in [L, 2L] holds the same state
+            return I.ic_random_smooth(one, g, seed=5)
+
+        o.set_state(o.keys(), ic())
+        if lmax:
+            o.fill_halos()
+            o.remesh(np.ones(o.n_leaves(), np.int8))
+            o.set_state(o.keys(), ic())
+            o.project()
+        dt = 0.1 * cfg.dx0 / 2 ** lmax
+        run_fixed_dt(o, dt, 3 * dt)
+        res.append((o.geometry(), o.get_state()))
+    (g1, U1), (g2, U2) = res
+    half = 2 ** g2[:, 0]
+    for copy in (0, 1):
+        sel = (g2[:, 1] // half) == copy
+        g = g2[sel].copy()
+        g[:, 1] -= copy * half[sel]
+        assert (g == g1).all()
+        assert np.array_equal(U2[sel], U1)
