@@ -839,6 +839,33 @@ def test_free_stream_with_jumps():
         assert abs(vals[0] - ref) <= 2 * 3 * np.spacing(abs(ref)) + 1e-300
 
 
+def test_conservation_across_three_level_jumps():
+    """As above with a level-1 leaf facing level-4 leaves: the averaged fine
+    flux reaches it through three levels of internal nodes' face buffers."""
+    cfg = I.periodic_config(base=(2, 2, 2), lmax=4)
+    o = oracle.Oracle(cfg)
+    ic = lambda: o.set_state(o.keys(), I.ic_random_smooth(cfg, o.geometry()))
+    ic()
+    for sel in (lambda g: np.ones(len(g), bool),
+                lambda g: (g[:, 0] == 1) & (g[:, 1] == 1) & (g[:, 2] == 1) & (g[:, 3] == 1),
+                lambda g: (g[:, 0] == 2) & (g[:, 1] == 2),
+                lambda g: (g[:, 0] == 3) & (g[:, 1] == 4)):
+        o.fill_halos()
+        o.remesh(sel(o.geometry()).astype(np.int8))
+        ic()
+    o.project()
+    g = o.geometry()
+    assert set(g[:, 0]) == {1, 2, 3, 4}
+    assert ((g[:, 0] == 1) & (g[:, 1] == 0) & (g[:, 2] == 1) & (g[:, 3] == 1)).any()
+    assert ((g[:, 0] == 4) & (g[:, 1] == 8) & (g[:, 2] // 8 == 1) & (g[:, 3] // 8 == 1)).any()
+    s0 = o.sums()
+    dt = 0.2 * cfg.dx0 / 16
+    run_fixed_dt(o, dt, 3 * dt)
+    s1 = o.sums()
+    scale = np.abs(o.get_state()).max(axis=(0, 2, 3, 4))
+    assert (np.abs(s1 - s0) <= 1e-13 * np.maximum(np.abs(s0), scale)).all(), (s1 - s0)
+
+
 def _init_tree(o, ic, lmax):
     """Alg. (Init): per level, refine everything below the instance's l_max
     and impose the IC; then coarsen by details and project."""
