@@ -31,7 +31,8 @@
 // refined octant and the halo fill at jumps exact on a quartic, batched
 // instances bit-identical to each run alone, conservation across two-level
 // jumps, the gravity source term, the projection by brute force, the viscous
-// terms on a linear velocity field and the shear-wave decay.
+// terms on a linear velocity field and the shear-wave decay, the right-hand
+// side commuting with rotations and mirrors of the axes.
 // The detail norm is a reading (the paper names only the l-infinity norm
 // over the block with its halo); a single perturbed cell on a uniform state
 // pins its parts (the leaf's value as the scale, rho and E, the halo).
