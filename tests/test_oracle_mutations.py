@@ -122,10 +122,10 @@ MUTATIONS = {
                                     "test_hllc_exact_on_isolated_shocks[0]"),
     "rhs_y_faces_transposed": ("acc = acc + (F[fidx(1, v, j, i, k)] - F[fidx(1, v, j + 1, i, k)]);",
                                "acc = acc + (F[fidx(1, v, j, k, i)] - F[fidx(1, v, j + 1, k, i)]);",
-                               "test_rhs_commutes_with_rotations_and_mirrors[rotate-0-0]"),
+                               "test_rhs_commutes_with_rotations_and_mirrors[rotate-0-0-0.0]"),
     "tangential_momenta_swapped": ("  U[1 + rot_axis(d, 1)] = R[2];\n  U[1 + rot_axis(d, 2)] = R[3];",
                                    "  U[1 + rot_axis(d, 1)] = R[3];\n  U[1 + rot_axis(d, 2)] = R[2];",
-                                   "test_rhs_commutes_with_rotations_and_mirrors[mirror-0-0]"),
+                                   "test_rhs_commutes_with_rotations_and_mirrors[mirror-0-0-0.0]"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }

@@ -1604,16 +1604,17 @@ def _mirror(G):
     return M
 
 
-@pytest.mark.parametrize("recon,flux", [(I.RECON_WENO, I.FLUX_ROE), (I.RECON_TENO, I.FLUX_LLF),
-                                        (I.RECON_WENOAO, I.FLUX_HLLC)])
+@pytest.mark.parametrize("recon,flux,mu", [(I.RECON_WENO, I.FLUX_ROE, 0.0), (I.RECON_TENO, I.FLUX_LLF, 0.0),
+                                           (I.RECON_WENOAO, I.FLUX_HLLC, 0.0), (I.RECON_WENO, I.FLUX_ROE, 0.05)])
 @pytest.mark.parametrize("sym", ["rotate", "mirror"])
-def test_rhs_commutes_with_rotations_and_mirrors(sym, recon, flux):
+def test_rhs_commutes_with_rotations_and_mirrors(sym, recon, flux, mu):
     """The dimension-by-dimension right-hand side treats every axis alike: on
     a periodic cube, cycling the axes (or mirroring x) of a 3D state with all
     velocity components nonzero cycles (or mirrors) its right-hand side, up
     to the rounding of the summation order.  Fixes the rotated frame of each
-    direction (which tangential velocity goes where) and the upwind side."""
-    cfg = I.periodic_config(base=(2, 2, 2), lmax=0, recon=recon, flux=flux, gamma=1.4)
+    direction (which tangential velocity goes where) and the upwind side, and
+    with mu > 0 the viscous stresses' velocity gradients."""
+    cfg = I.periodic_config(base=(2, 2, 2), lmax=0, recon=recon, flux=flux, gamma=1.4, mu=mu)
     T = _rotate if sym == "rotate" else _mirror
     out = []
     for transformed in (False, True):
