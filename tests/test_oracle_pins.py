@@ -1236,6 +1236,12 @@ def test_level_thresholds_decide_the_tags():
         assert (tags[b] == oracle.TAG_REFINE) == refined, (b, geo[b, 0], r, tags[b])
     others = np.setdiff1d(np.arange(len(keys)), [c[0] for c in cases])
     assert not delta[others].any() and (tags[others] != oracle.TAG_REFINE).all()
+    # level 3 holds complete leaf groups: the one with the leaf above eps_3
+    # is kept whole, the uniform ones are coarsened
+    k = keys.astype(np.uint64)
+    sib = (k >> np.uint64(3)) == (k[lv(3, 0)] >> np.uint64(3))
+    assert sib.sum() == 8 and (tags[sib] == oracle.TAG_KEEP).all()
+    assert (tags[(geo[:, 0] == 3) & ~sib] == oracle.TAG_COARSEN).all()
 
 
 def test_refined_groups_are_not_coarsened_right_away():
