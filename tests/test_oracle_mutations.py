@@ -126,6 +126,8 @@ MUTATIONS = {
     "tangential_momenta_swapped": ("  U[1 + rot_axis(d, 1)] = R[2];\n  U[1 + rot_axis(d, 2)] = R[3];",
                                    "  U[1 + rot_axis(d, 1)] = R[3];\n  U[1 + rot_axis(d, 2)] = R[2];",
                                    "test_rhs_commutes_with_rotations_and_mirrors[mirror-0-0-0.0]"),
+    "level1_groups_coarsened": ("} else if (n.level >= 2) {", "} else if (n.level >= 1) {",
+                                "test_tags_uniform_state_collapses_to_level1"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }

@@ -1083,17 +1083,24 @@ def test_rk2_is_second_order_in_time():
 
 
 def test_tags_uniform_state_collapses_to_level1():
+    """No details anywhere: every complete group at level >= 2 coarsens, and
+    no leaf on level 1 is ever tagged for coarsening (D9)."""
     cfg = I.explosion_config(lmax=3)
     o = _jump_tree(cfg, I.ic_uniform)
     o.fill_halos()
     tags, delta = o.predict_and_tag()
     assert (tags != oracle.TAG_REFINE).all()
     assert (delta == 0).all()
+    assert (tags[o.geometry()[:, 0] == 1] == oracle.TAG_KEEP).all()
     o.remesh(tags)
     o.fill_halos()
     tags, _ = o.predict_and_tag()
+    assert (tags[o.geometry()[:, 0] == 1] == oracle.TAG_KEEP).all()
     o.remesh(tags)
     assert set(o.geometry()[:, 0]) == {1}
+    o.fill_halos()
+    tags, _ = o.predict_and_tag()
+    assert (tags == oracle.TAG_KEEP).all()
 
 
 def test_tags_quartic_field_no_refinement():
