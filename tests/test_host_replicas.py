@@ -107,3 +107,21 @@ def test_roofline_flop_accounting():
     assert pf2 - pf == 0.5 * (bench.FLOP_V[2] + bench.FLOP_SPLIT + bench.FLOP_WENO)
     pl, _ = bench.roofline_numbers(1.0)
     assert pf - pl == 3 * (bench.FLOP_WENO - bench.FLOP_LIN)
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    """The driver's launch of the reference arm at N = 2: rank 0 alone runs
+    the oracle and prints one JSON line; rank 1 exits 0 without work."""
+    import json
+    import subprocess
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--lmax", "1"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, OMP_NUM_THREADS="2"))
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    res = json.loads(lines[0])
+    assert res["impl"] == "reference" and res["n_gpus"] == 2 and res["value"] > 0
