@@ -444,7 +444,8 @@ def run_gpu(args, rank, world):
         result["fp32_variants"] = variants
     if e2e:
         result["e2e"] = e2e
-    if rank == 0 and not args.no_cpu_baseline:
+    # the host-core baseline is taken once, by the single rank of an N = 1 run
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args)
     ranks.close()
     return result
