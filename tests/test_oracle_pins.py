@@ -891,9 +891,10 @@ def test_instances_evolve_independently():
     o.set_state(o.keys(), I.ic_ensemble(cfg, o.geometry(), o.keys()))
     _init_tree(o, lambda: I.ic_ensemble(cfg, o.geometry(), o.keys()), cfg.lmax)
     dts = o.step(3)
-    keys, U = o.keys(), o.get_state()
+    keys, U, sums = o.keys(), o.get_state(), o.sums()
     inst = (keys >> np.uint64(56)).astype(np.int64)
     assert set(o.geometry()[inst == 1, 0]) == {1, 2} and np.isfinite(U).all()
+    assert sums.shape == (3, 5)
     mask = np.uint64((1 << 56) - 1)
     for i in range(3):
         ci = dataclasses.replace(cfg, n_instances=1, lmax=(cfg.lmax[i],))
@@ -904,6 +905,7 @@ def test_instances_evolve_independently():
         assert (dti[:, 0] == dts[:, i]).all()
         assert (oi.keys() == (keys[inst == i] & mask)).all()
         assert np.array_equal(oi.get_state(), U[inst == i])
+        assert np.array_equal(oi.sums()[0], sums[i])
 
 
 @pytest.mark.parametrize("mu", [0.0, 0.02])
