@@ -113,9 +113,11 @@ def lib():
                 "orc_roe_eigen": (None, [vp, vp, i32, dbl, dbl, vp, vp, vp]),
                 "orc_face_flux": (None, [vp, i32, dbl, dbl, i32, i32, vp]),
                 "orc_predict_block": (None, [vp, i32, vp]),
-                "orc_face_features": (None, [vp, i32, dbl, dbl, dbl, vp, vp]),
+                "orc_face_features": (None, [vp, i32, dbl, dbl, dbl, vp, vp, vp]),
                 "orc_average_block": (None, [vp, vp]),
                 "orc_threads": (i32, []),
+                "orc_count_row_flops": (None, [vp, i32, dbl, dbl, i32, i32, vp]),
+                "orc_count_recon_flops": (None, [i32, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -327,14 +329,19 @@ def face_flux(U6, d: int, gamma: float = 1.4, B: float = 0.0, mode: int = 0, flu
     return F
 
 
-def face_features(U6, d: int, gamma: float = 1.4, B: float = 0.0, tau_lab: float = 1e-3):
-    """Selector features [15] and label of one face (U6: six lab-frame cells)."""
+def face_features(U6, d: int, gamma: float = 1.4, B: float = 0.0, tau_lab: float = 1e-3, with_aux: bool = False):
+    """Selector features [15] and label of one face (U6: six lab-frame cells).
+    With `with_aux` also the label's decision margin and scales (aux[5]: the
+    largest |WENO5 - linear5| minus its threshold over the label's checks, the
+    largest |input| of those checks, and per selected field the largest
+    |g_m| + alpha |v_m|)."""
     U6 = np.ascontiguousarray(U6, dtype=np.float64)
     assert U6.shape == (6, 5)
     f = np.zeros(15)
     lab = np.zeros(1, dtype=np.int32)
-    lib().orc_face_features(_p(U6), d, gamma, B, tau_lab, _p(f), _p(lab))
-    return f, int(lab[0])
+    aux = np.zeros(5)
+    lib().orc_face_features(_p(U6), d, gamma, B, tau_lab, _p(f), _p(lab), _p(aux))
+    return (f, int(lab[0]), aux) if with_aux else (f, int(lab[0]))
 
 
 def predict_block(parent: np.ndarray, child: int) -> np.ndarray:
@@ -355,3 +362,23 @@ def average_block(children: np.ndarray) -> np.ndarray:
 
 def threads() -> int:
     return int(lib().orc_threads())
+
+
+def count_row_flops(urow: np.ndarray, d: int, gamma: float, B: float, mode: int, flux: int) -> np.ndarray:
+    """Operation count of the 17 face fluxes of one block row along d
+    (urow[22, 5]: conserved lab-frame states of cells -3..18), measured by
+    running the oracle's face flux on its counting number type: [FLOPs,
+    add/sub, mul, div, sqrt] (see the counting section of orc.cpp)."""
+    urow = np.ascontiguousarray(urow, dtype=np.float64)
+    assert urow.shape == (NB + 6, NV)
+    out = np.zeros(5, dtype=np.int64)
+    lib().orc_count_row_flops(_p(urow), int(d), float(gamma), float(B), int(mode), int(flux), _p(out))
+    return out
+
+
+def count_recon_flops(mode: int) -> np.ndarray:
+    """Operation count of one reconstruction of the given mode (same layout)."""
+    out = np.zeros(5, dtype=np.int64)
+    lib().orc_count_recon_flops(int(mode), _p(out))
+    return out
+

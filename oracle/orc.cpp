@@ -43,6 +43,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -185,20 +186,32 @@ bool neighbour(const orc_config& c, uint64_t key, int sx, int sy, int sz, uint64
   return true;
 }
 
+// Elementary functions of the face-flux chain (the counting type at the end of
+// this file has its own).
+inline double osqrt(double x) { return std::sqrt(x); }
+inline double oabs(double x) { return std::fabs(x); }
+inline double omax(double a, double b) { return std::max(a, b); }
+inline double omin(double a, double b) { return std::min(a, b); }
+
 // ------------------------------------------------------------ EOS and fluxes
 // Eq. (Euler) with the stiffened-gas EOS, Eq. (StiffenedGas):
 // p = (gamma-1) rho e - gamma B,  E = rho e + 1/2 rho |v|^2,  c^2 = gamma (p+B)/rho.
-struct Prim { double rho, vel[3], p, c, E; };
+// The face-flux chain below (EOS, fluxes, eigensystem, reconstructions,
+// HLLC, face flux) is written once for a scalar type T: the oracle runs it
+// on double; the operation count of the roofline runs the same code on a
+// counting number type (end of this file).
+template <class T> struct PrimT { T rho, vel[3], p, c, E; };
+using Prim = PrimT<double>;
 
-Prim prim_of(const double U[5], double g, double B) {
-  Prim q;
+template <class T> PrimT<T> prim_of(const T U[5], double g, double B) {
+  PrimT<T> q;
   q.rho = U[0];
   q.vel[0] = U[1] / q.rho;
   q.vel[1] = U[2] / q.rho;
   q.vel[2] = U[3] / q.rho;
-  double q2 = (q.vel[0] * q.vel[0] + q.vel[1] * q.vel[1]) + q.vel[2] * q.vel[2];
+  T q2 = (q.vel[0] * q.vel[0] + q.vel[1] * q.vel[1]) + q.vel[2] * q.vel[2];
   q.p = (g - 1.0) * (U[4] - 0.5 * q.rho * q2) - g * B;
-  q.c = std::sqrt(g * (q.p + B) / q.rho);
+  q.c = osqrt(g * (q.p + B) / q.rho);
   q.E = U[4];
   return q;
 }
@@ -207,7 +220,7 @@ Prim prim_of(const double U[5], double g, double B) {
 // axes in cyclic order, so that one set of x-direction formulas serves all three.
 inline int rot_axis(int d, int j) { return (d + j) % 3; }  // j = 0 normal, 1, 2 tangential
 
-void rotate(const double U[5], int d, double R[5]) {
+template <class T> void rotate(const T U[5], int d, T R[5]) {
   R[0] = U[0];
   R[1] = U[1 + rot_axis(d, 0)];
   R[2] = U[1 + rot_axis(d, 1)];
@@ -215,7 +228,7 @@ void rotate(const double U[5], int d, double R[5]) {
   R[4] = U[4];
 }
 
-void unrotate(const double R[5], int d, double U[5]) {
+template <class T> void unrotate(const T R[5], int d, T U[5]) {
   U[0] = R[0];
   U[1 + rot_axis(d, 0)] = R[1];
   U[1 + rot_axis(d, 1)] = R[2];
@@ -224,10 +237,10 @@ void unrotate(const double R[5], int d, double U[5]) {
 }
 
 // Physical flux along d in the rotated frame: (m_n, m_n u_n + p, m_n u_t1, m_n u_t2, u_n (E + p)).
-void flux_rot(const double Ur[5], const Prim& q, int d, double F[5]) {
-  double un = q.vel[rot_axis(d, 0)];
-  double ut1 = q.vel[rot_axis(d, 1)];
-  double ut2 = q.vel[rot_axis(d, 2)];
+template <class T> void flux_rot(const T Ur[5], const PrimT<T>& q, int d, T F[5]) {
+  T un = q.vel[rot_axis(d, 0)];
+  T ut1 = q.vel[rot_axis(d, 1)];
+  T ut2 = q.vel[rot_axis(d, 2)];
   F[0] = Ur[1];
   F[1] = Ur[1] * un + q.p;
   F[2] = Ur[1] * ut1;
@@ -238,35 +251,36 @@ void flux_rot(const double Ur[5], const Prim& q, int d, double F[5]) {
 // Roe average at a face and its eigensystem in the rotated frame (Roe 1981,
 // named in Sec. 2.2).  Rows of Lm are left eigenvectors, columns of Rm right
 // eigenvectors, lam the eigenvalues (u-c, u, u, u, u+c).
-struct Eigen { double Lm[5][5], Rm[5][5], lam[5]; };
+template <class T> struct EigenT { T Lm[5][5], Rm[5][5], lam[5]; };
+using Eigen = EigenT<double>;
 
-Eigen roe_eigen(const Prim& a, const Prim& b, int d, double g) {
-  double sL = std::sqrt(a.rho), sR = std::sqrt(b.rho);
-  double den = sL + sR;
-  double un = (sL * a.vel[rot_axis(d, 0)] + sR * b.vel[rot_axis(d, 0)]) / den;
-  double ut1 = (sL * a.vel[rot_axis(d, 1)] + sR * b.vel[rot_axis(d, 1)]) / den;
-  double ut2 = (sL * a.vel[rot_axis(d, 2)] + sR * b.vel[rot_axis(d, 2)]) / den;
-  double HL = (a.E + a.p) / a.rho, HR = (b.E + b.p) / b.rho;
-  double H = (sL * HL + sR * HR) / den;
-  double q2 = (un * un + ut1 * ut1) + ut2 * ut2;
-  double c2 = (g - 1.0) * (H - 0.5 * q2);
-  double c = std::sqrt(c2);
-  double ic = 1.0 / c;
-  double b1 = (g - 1.0) / c2;
-  double b2 = 0.5 * b1 * q2;
-  Eigen e;
-  double l0[5] = {0.5 * (b2 + un * ic), 0.5 * (-b1 * un - ic), 0.5 * (-b1 * ut1), 0.5 * (-b1 * ut2), 0.5 * b1};
-  double l1[5] = {1.0 - b2, b1 * un, b1 * ut1, b1 * ut2, -b1};
-  double l2[5] = {-ut1, 0.0, 1.0, 0.0, 0.0};
-  double l3[5] = {-ut2, 0.0, 0.0, 1.0, 0.0};
-  double l4[5] = {0.5 * (b2 - un * ic), 0.5 * (-b1 * un + ic), 0.5 * (-b1 * ut1), 0.5 * (-b1 * ut2), 0.5 * b1};
-  double r0[5] = {1.0, un - c, ut1, ut2, H - un * c};
-  double r1[5] = {1.0, un, ut1, ut2, 0.5 * q2};
-  double r2[5] = {0.0, 0.0, 1.0, 0.0, ut1};
-  double r3[5] = {0.0, 0.0, 0.0, 1.0, ut2};
-  double r4[5] = {1.0, un + c, ut1, ut2, H + un * c};
-  const double* ls[5] = {l0, l1, l2, l3, l4};
-  const double* rs[5] = {r0, r1, r2, r3, r4};
+template <class T> EigenT<T> roe_eigen(const PrimT<T>& a, const PrimT<T>& b, int d, double g) {
+  T sL = osqrt(a.rho), sR = osqrt(b.rho);
+  T den = sL + sR;
+  T un = (sL * a.vel[rot_axis(d, 0)] + sR * b.vel[rot_axis(d, 0)]) / den;
+  T ut1 = (sL * a.vel[rot_axis(d, 1)] + sR * b.vel[rot_axis(d, 1)]) / den;
+  T ut2 = (sL * a.vel[rot_axis(d, 2)] + sR * b.vel[rot_axis(d, 2)]) / den;
+  T HL = (a.E + a.p) / a.rho, HR = (b.E + b.p) / b.rho;
+  T H = (sL * HL + sR * HR) / den;
+  T q2 = (un * un + ut1 * ut1) + ut2 * ut2;
+  T c2 = (g - 1.0) * (H - 0.5 * q2);
+  T c = osqrt(c2);
+  T ic = 1.0 / c;
+  T b1 = (g - 1.0) / c2;
+  T b2 = 0.5 * b1 * q2;
+  EigenT<T> e;
+  T l0[5] = {0.5 * (b2 + un * ic), 0.5 * (-b1 * un - ic), 0.5 * (-b1 * ut1), 0.5 * (-b1 * ut2), 0.5 * b1};
+  T l1[5] = {1.0 - b2, b1 * un, b1 * ut1, b1 * ut2, -b1};
+  T l2[5] = {-ut1, 0.0, 1.0, 0.0, 0.0};
+  T l3[5] = {-ut2, 0.0, 0.0, 1.0, 0.0};
+  T l4[5] = {0.5 * (b2 - un * ic), 0.5 * (-b1 * un + ic), 0.5 * (-b1 * ut1), 0.5 * (-b1 * ut2), 0.5 * b1};
+  T r0[5] = {1.0, un - c, ut1, ut2, H - un * c};
+  T r1[5] = {1.0, un, ut1, ut2, 0.5 * q2};
+  T r2[5] = {0.0, 0.0, 1.0, 0.0, ut1};
+  T r3[5] = {0.0, 0.0, 0.0, 1.0, ut2};
+  T r4[5] = {1.0, un + c, ut1, ut2, H + un * c};
+  const T* ls[5] = {l0, l1, l2, l3, l4};
+  const T* rs[5] = {r0, r1, r2, r3, r4};
   for (int k = 0; k < 5; ++k)
     for (int j = 0; j < 5; ++j) {
       e.Lm[k][j] = ls[k][j];
@@ -283,32 +297,32 @@ Eigen roe_eigen(const Prim& a, const Prim& b, int d, double g) {
 // WENO5-JS (Jiang & Shu 1996, cited in Sec. 2.2) reconstructing the value at
 // the right face of the middle cell of (a, b, c, d, e); epsilon = 1e-6, linear
 // weights (0.1, 0.6, 0.3).
-double weno5(double a, double b, double c, double d, double e) {
+template <class T> T weno5(T a, T b, T c, T d, T e) {
   const double eps = 1e-6;
-  double t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;
-  double beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  T t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;
+  T beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
   t1 = (b - 2.0 * c) + d;
   t2 = b - d;
-  double beta1 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  T beta1 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
   t1 = (c - 2.0 * d) + e;
   t2 = (3.0 * c - 4.0 * d) + e;
-  double beta2 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
-  double a0 = 0.1 / ((eps + beta0) * (eps + beta0));
-  double a1 = 0.6 / ((eps + beta1) * (eps + beta1));
-  double a2 = 0.3 / ((eps + beta2) * (eps + beta2));
-  double sum = (a0 + a1) + a2;
-  double q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
-  double q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
-  double q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
+  T beta2 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  T a0 = 0.1 / ((eps + beta0) * (eps + beta0));
+  T a1 = 0.6 / ((eps + beta1) * (eps + beta1));
+  T a2 = 0.3 / ((eps + beta2) * (eps + beta2));
+  T sum = (a0 + a1) + a2;
+  T q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
+  T q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
+  T q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
   return ((a0 * q0 + a1 * q1) + a2 * q2) / sum;
 }
 
 // The same three candidate stencils combined with the linear weights: the
 // 5th-order upwind reconstruction.
-double linear5(double a, double b, double c, double d, double e) {
-  double q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
-  double q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
-  double q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
+template <class T> T linear5(T a, T b, T c, T d, T e) {
+  T q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
+  T q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
+  T q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
   return (0.1 * q0 + 0.6 * q1) + 0.3 * q2;
 }
 
@@ -319,29 +333,29 @@ double linear5(double a, double b, double c, double d, double e) {
 // (beta_k + eps))^q with tau5 = |beta0 - beta2|, C = 1, q = 6, eps = 1e-40,
 // cutoff C_T = 1e-5; the kept stencils are combined with the linear weights,
 // renormalised.
-double teno5(double a, double b, double c, double d, double e) {
+template <class T> T teno5(T a, T b, T c, T d, T e) {
   const double eps = 1e-40, CT = 1e-5;
-  double t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;
-  double beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  T t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;
+  T beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
   t1 = (b - 2.0 * c) + d;
   t2 = b - d;
-  double beta1 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  T beta1 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
   t1 = (c - 2.0 * d) + e;
   t2 = (3.0 * c - 4.0 * d) + e;
-  double beta2 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
-  const double tau = std::fabs(beta0 - beta2);
-  double r0 = 1.0 + tau / (beta0 + eps), r1 = 1.0 + tau / (beta1 + eps), r2 = 1.0 + tau / (beta2 + eps);
+  T beta2 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  const T tau = oabs(beta0 - beta2);
+  T r0 = 1.0 + tau / (beta0 + eps), r1 = 1.0 + tau / (beta1 + eps), r2 = 1.0 + tau / (beta2 + eps);
   r0 = r0 * r0 * r0;
   r1 = r1 * r1 * r1;
   r2 = r2 * r2 * r2;
-  const double g0 = r0 * r0, g1 = r1 * r1, g2 = r2 * r2;
-  const double sum = (g0 + g1) + g2;
+  const T g0 = r0 * r0, g1 = r1 * r1, g2 = r2 * r2;
+  const T sum = (g0 + g1) + g2;
   const double w0 = (g0 / sum < CT) ? 0.0 : 0.1;
   const double w1 = (g1 / sum < CT) ? 0.0 : 0.6;
   const double w2 = (g2 / sum < CT) ? 0.0 : 0.3;
-  double q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
-  double q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
-  double q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
+  T q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
+  T q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
+  T q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
   return ((w0 * q0 + w1 * q1) + w2 * q2) / ((w0 + w1) + w2);
 }
 
@@ -356,41 +370,41 @@ double teno5(double a, double b, double c, double d, double e) {
 // gamma_k (1 + (tau / (beta_k + eps))^2), tau the mean of |beta_5 - beta_k|,
 // eps = 1e-12, normalised.  Value at the right face of the middle cell:
 // (w_5 / gamma_5)(q_5 - sum gamma_k q_k) + sum w_k q_k over the parabolas k.
-double wenoao53(double a, double b, double c, double d, double e) {
+template <class T> T wenoao53(T a, T b, T c, T d, T e) {
   const double eps = 1e-12;
   const double ghi = 0.85, glo = 0.85;
-  double t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;
-  double beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  T t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;
+  T beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
   t1 = (b - 2.0 * c) + d;
   t2 = b - d;
-  double beta1 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  T beta1 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
   t1 = (c - 2.0 * d) + e;
   t2 = (3.0 * c - 4.0 * d) + e;
-  double beta2 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
+  T beta2 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;
   // Legendre coefficients of the quartic on the middle cell (a..e = u_{i-2..i+2})
-  double u1 = (((11.0 * a - 82.0 * b) + 82.0 * d) - 11.0 * e) / 120.0;
-  double u2 = ((((-3.0 * a + 40.0 * b) - 74.0 * c) + 40.0 * d) - 3.0 * e) / 56.0;
-  double u3 = (((-a + 2.0 * b) - 2.0 * d) + e) / 12.0;
-  double u4 = ((((a - 4.0 * b) + 6.0 * c) - 4.0 * d) + e) / 24.0;
-  double s1 = u1 + u3 / 10.0, s2 = u2 + (123.0 / 455.0) * u4;
-  double beta5 = (((s1 * s1 + (13.0 / 3.0) * (s2 * s2)) + (781.0 / 20.0) * (u3 * u3)) + (1421461.0 / 2275.0) * (u4 * u4));
+  T u1 = (((11.0 * a - 82.0 * b) + 82.0 * d) - 11.0 * e) / 120.0;
+  T u2 = ((((-3.0 * a + 40.0 * b) - 74.0 * c) + 40.0 * d) - 3.0 * e) / 56.0;
+  T u3 = (((-a + 2.0 * b) - 2.0 * d) + e) / 12.0;
+  T u4 = ((((a - 4.0 * b) + 6.0 * c) - 4.0 * d) + e) / 24.0;
+  T s1 = u1 + u3 / 10.0, s2 = u2 + (123.0 / 455.0) * u4;
+  T beta5 = (((s1 * s1 + (13.0 / 3.0) * (s2 * s2)) + (781.0 / 20.0) * (u3 * u3)) + (1421461.0 / 2275.0) * (u4 * u4));
   const double g5 = ghi, g1 = (1.0 - ghi) * glo, g0 = 0.5 * ((1.0 - ghi) * (1.0 - glo)), g2 = g0;
-  double tau = ((std::fabs(beta5 - beta0) + std::fabs(beta5 - beta1)) + std::fabs(beta5 - beta2)) / 3.0;
-  double r5 = tau / (beta5 + eps), r0 = tau / (beta0 + eps), r1 = tau / (beta1 + eps), r2 = tau / (beta2 + eps);
-  double w5 = g5 * (1.0 + r5 * r5), w0 = g0 * (1.0 + r0 * r0), w1 = g1 * (1.0 + r1 * r1), w2 = g2 * (1.0 + r2 * r2);
-  double sum = ((w5 + w0) + w1) + w2;
+  T tau = ((oabs(beta5 - beta0) + oabs(beta5 - beta1)) + oabs(beta5 - beta2)) / 3.0;
+  T r5 = tau / (beta5 + eps), r0 = tau / (beta0 + eps), r1 = tau / (beta1 + eps), r2 = tau / (beta2 + eps);
+  T w5 = g5 * (1.0 + r5 * r5), w0 = g0 * (1.0 + r0 * r0), w1 = g1 * (1.0 + r1 * r1), w2 = g2 * (1.0 + r2 * r2);
+  T sum = ((w5 + w0) + w1) + w2;
   w5 = w5 / sum;
   w0 = w0 / sum;
   w1 = w1 / sum;
   w2 = w2 / sum;
-  double q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
-  double q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
-  double q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
-  double q5 = ((((2.0 * a - 13.0 * b) + 47.0 * c) + 27.0 * d) - 3.0 * e) / 60.0;
+  T q0 = ((2.0 * a - 7.0 * b) + 11.0 * c) / 6.0;
+  T q1 = ((-b + 5.0 * c) + 2.0 * d) / 6.0;
+  T q2 = ((2.0 * c + 5.0 * d) - e) / 6.0;
+  T q5 = ((((2.0 * a - 13.0 * b) + 47.0 * c) + 27.0 * d) - 3.0 * e) / 60.0;
   return (w5 / g5) * (((q5 - g0 * q0) - g1 * q1) - g2 * q2) + ((w0 * q0 + w1 * q1) + w2 * q2);
 }
 
-inline double recon5(int mode, double a, double b, double c, double d, double e) {
+template <class T> inline T recon5(int mode, T a, T b, T c, T d, T e) {
   if (mode == RECON_LINEAR) return linear5(a, b, c, d, e);
   if (mode == RECON_TENO) return teno5(a, b, c, d, e);
   if (mode == RECON_WENOAO) return wenoao53(a, b, c, d, e);
@@ -405,29 +419,29 @@ inline double recon5(int mode, double a, double b, double c, double d, double e)
 // F*_R or F_R by where x/t = 0 falls among S_L <= S* <= S_R, with
 // F*_K = F_K + S_K (U*_K - U_K) and U*_K = rho_K (S_K - u_K) / (S_K - S*) times
 // (1, S*, v_K, w_K, E_K / rho_K + (S* - u_K)(S* + p_K / (rho_K (S_K - u_K)))).
-void hllc_rot(const double UL[5], const double UR[5], double g, double B, double F[5]) {
-  Prim a = prim_of(UL, g, B), b = prim_of(UR, g, B);
-  double FL[5], FR[5];
+template <class T> void hllc_rot(const T UL[5], const T UR[5], double g, double B, T F[5]) {
+  PrimT<T> a = prim_of(UL, g, B), b = prim_of(UR, g, B);
+  T FL[5], FR[5];
   flux_rot(UL, a, 0, FL);
   flux_rot(UR, b, 0, FR);
-  Eigen e = roe_eigen(a, b, 0, g);
-  double uL = a.vel[0], uR = b.vel[0];
-  double SL = std::min(uL - a.c, e.lam[0]);
-  double SR = std::max(uR + b.c, e.lam[4]);
-  double mL = a.rho * (SL - uL), mR = b.rho * (SR - uR);
-  double Ss = (((b.p - a.p) + uL * mL) - uR * mR) / (mL - mR);
+  EigenT<T> e = roe_eigen(a, b, 0, g);
+  T uL = a.vel[0], uR = b.vel[0];
+  T SL = omin(uL - a.c, e.lam[0]);
+  T SR = omax(uR + b.c, e.lam[4]);
+  T mL = a.rho * (SL - uL), mR = b.rho * (SR - uR);
+  T Ss = (((b.p - a.p) + uL * mL) - uR * mR) / (mL - mR);
   if (SL >= 0.0) {
     for (int j = 0; j < 5; ++j) F[j] = FL[j];
   } else if (SR <= 0.0) {
     for (int j = 0; j < 5; ++j) F[j] = FR[j];
   } else {
     const bool left = Ss >= 0.0;
-    const Prim& q = left ? a : b;
-    const double* U = left ? UL : UR;
-    const double* FK = left ? FL : FR;
-    double SK = left ? SL : SR, mK = left ? mL : mR;
-    double fac = mK / (SK - Ss);
-    double Us[5];
+    const PrimT<T>& q = left ? a : b;
+    const T* U = left ? UL : UR;
+    const T* FK = left ? FL : FR;
+    T SK = left ? SL : SR, mK = left ? mL : mR;
+    T fac = mK / (SK - Ss);
+    T Us[5];
     Us[0] = fac;
     Us[1] = fac * Ss;
     Us[2] = fac * q.vel[1];
@@ -438,10 +452,10 @@ void hllc_rot(const double UL[5], const double UR[5], double g, double B, double
 }
 
 // Reconstructed face state admissible for HLLC: positive density and p + B > 0.
-bool admissible(const double U[5], double g, double B) {
+template <class T> bool admissible(const T U[5], double g, double B) {
   if (!(U[0] > 0.0)) return false;
-  double q2 = ((U[1] * U[1] + U[2] * U[2]) + U[3] * U[3]) / U[0];
-  double p = (g - 1.0) * (U[4] - 0.5 * q2) - g * B;
+  T q2 = ((U[1] * U[1] + U[2] * U[2]) + U[3] * U[3]) / U[0];
+  T p = (g - 1.0) * (U[4] - 0.5 * q2) - g * B;
   return p + B > 0.0;
 }
 
@@ -457,20 +471,21 @@ bool admissible(const double U[5], double g, double B) {
 // (cells i-2..i+2) and from the right (cells i+3..i-1), mapped back with R to
 // the states U_L, U_R, and HLLC gives the flux; where either state is not
 // admissible the face falls back to the cell states U_i, U_{i+1}.
-void face_flux(const double U6[6][5], int d, double g, double B, int mode, int flux, double Fout[5]) {
-  Prim q[6];
-  double Ur[6][5], Fr[6][5];
+template <class T>
+void face_flux(const T U6[6][5], int d, double g, double B, int mode, int flux, T Fout[5]) {
+  PrimT<T> q[6];
+  T Ur[6][5], Fr[6][5];
   for (int m = 0; m < 6; ++m) {
     q[m] = prim_of(U6[m], g, B);
     rotate(U6[m], d, Ur[m]);
     flux_rot(Ur[m], q[m], d, Fr[m]);
   }
-  Eigen e = roe_eigen(q[2], q[3], d, g);
-  double v[5][6], gc[5][6];
+  EigenT<T> e = roe_eigen(q[2], q[3], d, g);
+  T v[5][6], gc[5][6];
   for (int k = 0; k < 5; ++k)
     for (int m = 0; m < 6; ++m) {
-      double sv = e.Lm[k][0] * Ur[m][0];
-      double sg = e.Lm[k][0] * Fr[m][0];
+      T sv = e.Lm[k][0] * Ur[m][0];
+      T sg = e.Lm[k][0] * Fr[m][0];
       for (int j = 1; j < 5; ++j) {
         sv = sv + e.Lm[k][j] * Ur[m][j];
         sg = sg + e.Lm[k][j] * Fr[m][j];
@@ -479,13 +494,13 @@ void face_flux(const double U6[6][5], int d, double g, double B, int mode, int f
       gc[k][m] = sg;
     }
   if (flux == FLUX_HLLC) {
-    double vL[5], vR[5], UL[5], UR[5], Fh[5];
+    T vL[5], vR[5], UL[5], UR[5], Fh[5];
     for (int k = 0; k < 5; ++k) {
       vL[k] = recon5(mode, v[k][0], v[k][1], v[k][2], v[k][3], v[k][4]);
       vR[k] = recon5(mode, v[k][5], v[k][4], v[k][3], v[k][2], v[k][1]);
     }
     for (int j = 0; j < 5; ++j) {
-      double sl = e.Rm[j][0] * vL[0], sr = e.Rm[j][0] * vR[0];
+      T sl = e.Rm[j][0] * vL[0], sr = e.Rm[j][0] * vR[0];
       for (int k = 1; k < 5; ++k) {
         sl = sl + e.Rm[j][k] * vL[k];
         sr = sr + e.Rm[j][k] * vR[k];
@@ -503,20 +518,20 @@ void face_flux(const double U6[6][5], int d, double g, double B, int mode, int f
     unrotate(Fh, d, Fout);
     return;
   }
-  double unL = q[2].vel[d], unR = q[3].vel[d];
-  double lamL[5] = {unL - q[2].c, unL, unL, unL, unL + q[2].c};
-  double lamR[5] = {unR - q[3].c, unR, unR, unR, unR + q[3].c};
-  double gh[5];
+  T unL = q[2].vel[d], unR = q[3].vel[d];
+  T lamL[5] = {unL - q[2].c, unL, unL, unL, unL + q[2].c};
+  T lamR[5] = {unR - q[3].c, unR, unR, unR, unR + q[3].c};
+  T gh[5];
   for (int k = 0; k < 5; ++k) {
-    double lL = lamL[k], lR = lamR[k], lt = e.lam[k];
-    const double* G = gc[k];
+    T lL = lamL[k], lR = lamR[k], lt = e.lam[k];
+    const T* G = gc[k];
     if (flux == FLUX_ROE && lL > 0.0 && lR > 0.0 && lt > 0.0) {
       gh[k] = recon5(mode, G[0], G[1], G[2], G[3], G[4]);
     } else if (flux == FLUX_ROE && lL < 0.0 && lR < 0.0 && lt < 0.0) {
       gh[k] = recon5(mode, G[5], G[4], G[3], G[2], G[1]);
     } else {
-      double alpha = std::max(std::fabs(lL), std::fabs(lR));
-      double fp[6], fm[6];
+      T alpha = omax(oabs(lL), oabs(lR));
+      T fp[6], fm[6];
       for (int m = 0; m < 6; ++m) {
         fp[m] = 0.5 * (G[m] + alpha * v[k][m]);
         fm[m] = 0.5 * (G[m] - alpha * v[k][m]);
@@ -524,9 +539,9 @@ void face_flux(const double U6[6][5], int d, double g, double B, int mode, int f
       gh[k] = recon5(mode, fp[0], fp[1], fp[2], fp[3], fp[4]) + recon5(mode, fm[5], fm[4], fm[3], fm[2], fm[1]);
     }
   }
-  double Fr_hat[5];
+  T Fr_hat[5];
   for (int j = 0; j < 5; ++j) {
-    double s = e.Rm[j][0] * gh[0];
+    T s = e.Rm[j][0] * gh[0];
     for (int k = 1; k < 5; ++k) s = s + e.Rm[j][k] * gh[k];
     Fr_hat[j] = s;
   }
@@ -556,7 +571,13 @@ double compress_diff(double d) {
   return d < 0.0 ? -a : a;
 }
 
-void face_features(const double U6[6][5], int d, double g, double B, double tau_lab, double feats[15], int* label) {
+// aux (nullable, 5 values): [0] the largest (|WENO5 - linear5| - threshold)
+// over the label's checks (the label is 1 when it is positive), [1] the largest
+// |input| of those checks, [2..4] per selected field the largest |g_m| +
+// alpha_k |v_m| over the six cells (the size of the values the field's
+// variations are differences of).
+void face_features(const double U6[6][5], int d, double g, double B, double tau_lab, double feats[15], int* label,
+                   double* aux = nullptr) {
   Prim q[6];
   double Ur[6][5], Fr[6][5];
   for (int m = 0; m < 6; ++m) {
@@ -587,16 +608,24 @@ void face_features(const double U6[6][5], int d, double g, double B, double tau_
       double sgn = (dg != 0.0) ? (dg < 0.0 ? -1.0 : 1.0) : (dv < 0.0 ? -1.0 : 1.0);
       feats[5 * t + m] = compress_diff(sgn * (std::fabs(dg) + alpha * std::fabs(dv)));
     }
+    if (aux) {
+      double S = 0.0;
+      for (int m = 0; m < 6; ++m) S = std::max(S, std::fabs(gk[m]) + alpha * std::fabs(vk[m]));
+      aux[2 + t] = S;
+    }
   }
   double unL = q[2].vel[d], unR = q[3].vel[d];
   double lamL[5] = {unL - q[2].c, unL, unL, unL, unL + q[2].c};
   double lamR[5] = {unR - q[3].c, unR, unR, unR, unR + q[3].c};
   int lab = 0;
+  double margin = -INFINITY, scale = 0.0;
   auto check = [&](const double f[5]) {
     double sc = 0.0;
     for (int m = 0; m < 5; ++m) sc = std::max(sc, std::fabs(f[m]));
     double dw = std::fabs(weno5(f[0], f[1], f[2], f[3], f[4]) - linear5(f[0], f[1], f[2], f[3], f[4]));
     if (dw > std::max(tau_lab * sc, 1e-6)) lab = 1;
+    margin = std::max(margin, dw - std::max(tau_lab * sc, 1e-6));
+    scale = std::max(scale, sc);
   };
   for (int k = 0; k < 5; ++k) {
     if (!selected_field(k)) continue;
@@ -627,6 +656,10 @@ void face_features(const double U6[6][5], int d, double g, double B, double tau_
     }
   }
   *label = lab;
+  if (aux) {
+    aux[0] = margin;
+    aux[1] = scale;
+  }
 }
 
 // ------------------------------------------------------------ MR operators
@@ -1375,6 +1408,192 @@ bool any_mr(const Ctx& C) {
   return false;
 }
 
+// ------------------------------------------------------------ operation count
+// Measurement only (the roofline's algorithmic FLOPs), never part of a result.
+// Sym is a counting number type: it carries the double value (so every branch
+// of the face-flux chain is taken as for that value) and a node of an
+// expression graph.  Nodes are hash-consed on (operation, operands), so an
+// expression the chain evaluates twice from the same operands is one node
+// (what common-subexpression elimination keeps once: the primitive variables
+// and physical flux of a cell shared by the faces of a row).  Values built only
+// from literals and from the run constants gamma and B fold to constants; a
+// multiplication by a literal 0 or +-1 and an addition of a literal 0 are no
+// operation (the zero and unit entries of the eigenvectors).  The count is
+// the number of add, subtract, multiply, divide and square-root nodes
+// reachable from the outputs and from the operands of every comparison (the
+// branch decisions: the eigenvalue signs of the Roe/LLF switch, the TENO5
+// cutoff, HLLC's admissibility and wave pattern), so values the chain computes
+// but never uses (the v = L U projections of fields that are upwinded) are not
+// counted.  Negation, absolute value, max/min and comparisons count as no
+// operation.
+enum SymOp : int32_t { S_IN, S_CONST, S_ADD, S_SUB, S_MUL, S_DIV, S_SQRT, S_NEG, S_ABS, S_MAX, S_MIN };
+
+struct SymGraph {
+  struct Rec { int32_t op, a, b; };
+  std::vector<Rec> nodes;
+  std::map<std::tuple<int32_t, int32_t, int32_t, uint64_t>, int32_t> index;
+  int32_t make(int32_t op, int32_t a, int32_t b, uint64_t extra = 0) {
+    if ((op == S_ADD || op == S_MUL) && a > b) std::swap(a, b);
+    auto key = std::make_tuple(op, a, b, extra);
+    auto it = index.find(key);
+    if (it != index.end()) return it->second;
+    nodes.push_back({op, a, b});
+    const int32_t id = (int32_t)nodes.size() - 1;
+    index.emplace(key, id);
+    return id;
+  }
+};
+SymGraph* g_sym = nullptr;
+
+struct Sym {
+  double v;
+  int32_t id;   // -1: a constant
+  Sym() : v(0.0), id(-1) {}
+  Sym(double x) : v(x), id(-1) {}
+  static Sym input(double x, uint64_t serial) {
+    Sym s(x);
+    s.id = g_sym->make(S_IN, -1, -1, serial);
+    return s;
+  }
+  int32_t node() const {
+    if (id >= 0) return id;
+    uint64_t bits;
+    std::memcpy(&bits, &v, 8);
+    return g_sym->make(S_CONST, -1, -1, bits);
+  }
+};
+
+inline Sym sym_node(double v, int32_t op, const Sym& a, const Sym& b) {
+  Sym r(v);
+  r.id = g_sym->make(op, a.node(), b.node());
+  return r;
+}
+inline Sym operator-(const Sym& a) {
+  if (a.id < 0) return Sym(-a.v);
+  Sym r(-a.v);
+  r.id = g_sym->make(S_NEG, a.id, -1);
+  return r;
+}
+inline Sym operator+(const Sym& a, const Sym& b) {
+  if (a.id < 0 && b.id < 0) return Sym(a.v + b.v);
+  if (a.id < 0 && a.v == 0.0) return b;
+  if (b.id < 0 && b.v == 0.0) return a;
+  return sym_node(a.v + b.v, S_ADD, a, b);
+}
+inline Sym operator-(const Sym& a, const Sym& b) {
+  if (a.id < 0 && b.id < 0) return Sym(a.v - b.v);
+  if (b.id < 0 && b.v == 0.0) return a;
+  if (a.id < 0 && a.v == 0.0) return -b;
+  return sym_node(a.v - b.v, S_SUB, a, b);
+}
+inline Sym operator*(const Sym& a, const Sym& b) {
+  if (a.id < 0 && b.id < 0) return Sym(a.v * b.v);
+  if ((a.id < 0 && a.v == 0.0) || (b.id < 0 && b.v == 0.0)) return Sym(0.0);
+  if (a.id < 0 && a.v == 1.0) return b;
+  if (b.id < 0 && b.v == 1.0) return a;
+  if (a.id < 0 && a.v == -1.0) return -b;
+  if (b.id < 0 && b.v == -1.0) return -a;
+  return sym_node(a.v * b.v, S_MUL, a, b);
+}
+inline Sym operator/(const Sym& a, const Sym& b) {
+  if (a.id < 0 && b.id < 0) return Sym(a.v / b.v);
+  if (b.id < 0 && b.v == 1.0) return a;
+  return sym_node(a.v / b.v, S_DIV, a, b);
+}
+inline Sym osqrt(const Sym& a) {
+  if (a.id < 0) return Sym(std::sqrt(a.v));
+  Sym r(std::sqrt(a.v));
+  r.id = g_sym->make(S_SQRT, a.id, -1);
+  return r;
+}
+inline Sym oabs(const Sym& a) {
+  if (a.id < 0) return Sym(std::fabs(a.v));
+  Sym r(std::fabs(a.v));
+  r.id = g_sym->make(S_ABS, a.id, -1);
+  return r;
+}
+inline Sym omax(const Sym& a, const Sym& b) {
+  if (a.id < 0 && b.id < 0) return Sym(std::max(a.v, b.v));
+  return sym_node(std::max(a.v, b.v), S_MAX, a, b);
+}
+inline Sym omin(const Sym& a, const Sym& b) {
+  if (a.id < 0 && b.id < 0) return Sym(std::min(a.v, b.v));
+  return sym_node(std::min(a.v, b.v), S_MIN, a, b);
+}
+// A comparison decides a branch, so the values it compares are needed: their
+// nodes become roots of the count like the outputs.
+std::vector<int32_t>* g_sym_roots = nullptr;
+inline void sym_decides(const Sym& a, const Sym& b) {
+  if (a.id >= 0) g_sym_roots->push_back(a.id);
+  if (b.id >= 0) g_sym_roots->push_back(b.id);
+}
+inline bool operator<(const Sym& a, const Sym& b) { sym_decides(a, b); return a.v < b.v; }
+inline bool operator>(const Sym& a, const Sym& b) { sym_decides(a, b); return a.v > b.v; }
+inline bool operator<=(const Sym& a, const Sym& b) { sym_decides(a, b); return a.v <= b.v; }
+inline bool operator>=(const Sym& a, const Sym& b) { sym_decides(a, b); return a.v >= b.v; }
+
+// Operations reachable from the outputs, by kind: [0] FLOPs (the sum of the
+// next four), [1] add and subtract, [2] multiply, [3] divide, [4] square root.
+void sym_count(const std::vector<int32_t>& outputs, int64_t counts[5]) {
+  std::vector<char> seen(g_sym->nodes.size(), 0);
+  std::vector<int32_t> stack(outputs.begin(), outputs.end());
+  for (int i = 0; i < 5; ++i) counts[i] = 0;
+  while (!stack.empty()) {
+    const int32_t n = stack.back();
+    stack.pop_back();
+    if (n < 0 || seen[n]) continue;
+    seen[n] = 1;
+    const SymGraph::Rec r = g_sym->nodes[n];
+    if (r.op == S_ADD || r.op == S_SUB) counts[1]++;
+    if (r.op == S_MUL) counts[2]++;
+    if (r.op == S_DIV) counts[3]++;
+    if (r.op == S_SQRT) counts[4]++;
+    stack.push_back(r.a);
+    stack.push_back(r.b);
+  }
+  counts[0] = counts[1] + counts[2] + counts[3] + counts[4];
+}
+
+// One row of a block along direction d: the 17 faces between cells -1..16
+// (stencil cells -3..18, i.e. Urow[m] for cell m - 3, conserved variables in
+// the lab frame), each by face_flux exactly as leaf_rhs evaluates it.
+void count_row(const double* Urow, int d, double g, double B, int mode, int flux, int64_t counts[5]) {
+  SymGraph graph;
+  std::vector<int32_t> roots;
+  g_sym = &graph;
+  g_sym_roots = &roots;
+  Sym U[NB + 6][5];
+  for (int m = 0; m < NB + 6; ++m)
+    for (int v = 0; v < NV; ++v) U[m][v] = Sym::input(Urow[m * NV + v], (uint64_t)(m * NV + v));
+  std::vector<int32_t> out;
+  for (int f = 0; f <= NB; ++f) {
+    Sym U6[6][5], Fo[5];
+    for (int m = 0; m < 6; ++m)
+      for (int v = 0; v < NV; ++v) U6[m][v] = U[f + m][v];
+    face_flux(U6, d, g, B, mode, flux, Fo);
+    for (int v = 0; v < NV; ++v) out.push_back(Fo[v].node());
+  }
+  out.insert(out.end(), roots.begin(), roots.end());
+  sym_count(out, counts);
+  g_sym = nullptr;
+  g_sym_roots = nullptr;
+}
+
+// One reconstruction of the given mode on five inputs.
+void count_recon(int mode, int64_t counts[5]) {
+  SymGraph graph;
+  std::vector<int32_t> roots;
+  g_sym = &graph;
+  g_sym_roots = &roots;
+  Sym a[5];
+  for (int m = 0; m < 5; ++m) a[m] = Sym::input(1.0 + 0.1 * m * m, (uint64_t)m);
+  Sym r = recon5(mode, a[0], a[1], a[2], a[3], a[4]);
+  roots.push_back(r.node());
+  sym_count(roots, counts);
+  g_sym = nullptr;
+  g_sym_roots = nullptr;
+}
+
 }  // namespace
 
 // =============================================================== C interface
@@ -1611,12 +1830,12 @@ void orc_hllc(const double* UL, const double* UR, int32_t d, double g, double B,
 
 // Selector features [15] and label of one face (six lab-frame cells [6][5]).
 void orc_face_features(const double* U6, int32_t d, double g, double B, double tau_lab, double* feats,
-                       int32_t* label) {
+                       int32_t* label, double* aux) {
   double U[6][5];
   for (int m = 0; m < 6; ++m)
     for (int v = 0; v < 5; ++v) U[m][v] = U6[m * 5 + v];
   int lab = 0;
-  face_features(U, d, g, B, tau_lab, feats, &lab);
+  face_features(U, d, g, B, tau_lab, feats, &lab, aux);
   *label = lab;
 }
 
@@ -1643,6 +1862,14 @@ void orc_average_block(const double* children, double* parent) {
         parent[iidx(I, J, K)] = 0.125 * (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7)));
       }
 }
+
+// Operation counts of the face flux (measurement of the roofline's algorithmic
+// FLOPs; see count_row): counts[5] = FLOPs, add/sub, mul, div, sqrt.
+void orc_count_row_flops(const double* Urow, int32_t d, double g, double B, int32_t mode, int32_t flux,
+                         int64_t* counts) {
+  count_row(Urow, d, g, B, mode, flux, counts);
+}
+void orc_count_recon_flops(int32_t mode, int64_t* counts) { count_recon(mode, counts); }
 
 int32_t orc_threads(void) {
 #ifdef _OPENMP

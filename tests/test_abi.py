@@ -119,7 +119,7 @@ def test_oracle_and_library_share_no_code():
     for path in glob.glob(os.path.join(ROOT, "paper_2012_04385_gb300", "*.py")):
         assert "oracle" not in imports(path), path
     inc = re.compile(r'^\s*#\s*include\s*[<"]([^>"]+)[>"]', re.M)
-    std = {"algorithm", "cmath", "cstdint", "cstring", "map", "string", "vector", "omp.h"}
+    std = {"algorithm", "cmath", "cstdint", "cstring", "map", "string", "tuple", "vector", "omp.h"}
     assert set(inc.findall(open(os.path.join(ROOT, "oracle", "orc.cpp")).read())) <= std
     csrc = os.path.join(ROOT, "paper_2012_04385_gb300", "csrc")
     own = {os.path.basename(p) for p in glob.glob(os.path.join(csrc, "*.cuh"))} | {"mrb.h"}

@@ -29,14 +29,14 @@ MUTATIONS = {
     "llf_not_everywhere": ("if (flux == FLUX_ROE && lL > 0.0 && lR > 0.0 && lt > 0.0) {",
                            "if (lL > 0.0 && lR > 0.0 && lt > 0.0) {",
                            "test_llf_face_flux_on_a_step_closed_form"),
-    "llf_speed_from_roe_average": ("      double alpha = std::max(std::fabs(lL), std::fabs(lR));\n      double fp[6], fm[6];",
-                                   "      double alpha = std::fabs(lt);\n      double fp[6], fm[6];",
+    "llf_speed_from_roe_average": ("      T alpha = omax(oabs(lL), oabs(lR));\n      T fp[6], fm[6];",
+                                   "      T alpha = oabs(lt);\n      T fp[6], fm[6];",
                                    "test_roe_llf_switch_on_a_transonic_step_closed_form"),
     "coarsen_ignores_parent_detail": ("          if (dpar[pk | (inst << 56)] > ep) all = false;",
                                       "          if (dpar[pk | (inst << 56)] > 1e300 * ep) all = false;",
                                       "test_refined_groups_are_not_coarsened_right_away"),
-    "weno5_linear_weights": ("  double a1 = 0.6 / ((eps + beta1) * (eps + beta1));\n  double a2 = 0.3 / ((eps + beta2) * (eps + beta2));\n  double sum = (a0 + a1) + a2;\n  double q0",
-                             "  double a1 = 0.5 / ((eps + beta1) * (eps + beta1));\n  double a2 = 0.4 / ((eps + beta2) * (eps + beta2));\n  double sum = (a0 + a1) + a2;\n  double q0",
+    "weno5_linear_weights": ("  T a1 = 0.6 / ((eps + beta1) * (eps + beta1));\n  T a2 = 0.3 / ((eps + beta2) * (eps + beta2));\n  T sum = (a0 + a1) + a2;\n  T q0",
+                             "  T a1 = 0.5 / ((eps + beta1) * (eps + beta1));\n  T a2 = 0.4 / ((eps + beta2) * (eps + beta2));\n  T sum = (a0 + a1) + a2;\n  T q0",
                              "test_fifth_order_convergence_density_wave[0-0]"),
     "teno5_cutoff": ("const double eps = 1e-40, CT = 1e-5;", "const double eps = 1e-40, CT = 1e-1;",
                      "test_teno5_matches_its_definition"),
@@ -64,7 +64,7 @@ MUTATIONS = {
                           "test_gravity_source_term"),
     "wenoao_quartic_smoothness": ("(781.0 / 20.0) * (u3 * u3)", "(781.0 / 30.0) * (u3 * u3)",
                                   "test_wenoao_matches_its_definition"),
-    "wenoao_weight_exponent": ("double w5 = g5 * (1.0 + r5 * r5)", "double w5 = g5 * (1.0 + r5)",
+    "wenoao_weight_exponent": ("T w5 = g5 * (1.0 + r5 * r5)", "T w5 = g5 * (1.0 + r5)",
                                "test_wenoao_matches_its_definition"),
     "viscous_stress_not_symmetrised": ("tau[i] = mu * (G[i][d] + G[d][i]);", "tau[i] = mu * (G[i][d] + G[i][d]);",
                                        "test_viscous_terms_on_a_linear_velocity_field"),
@@ -105,11 +105,11 @@ MUTATIONS = {
     "sibling_lookup_drops_instance": ("uint64_t sk = ((pk << 3) | (uint64_t)c) | (inst << 56);",
                                       "uint64_t sk = ((pk << 3) | (uint64_t)c);",
                                       "test_instances_evolve_independently"),
-    "weno5_smoothness_coefficient": ("double weno5(double a, double b, double c, double d, double e) {\n  const double eps = 1e-6;\n  double t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;\n  double beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;",
-                                     "double weno5(double a, double b, double c, double d, double e) {\n  const double eps = 1e-6;\n  double t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;\n  double beta0 = (13.0 / 12.0) * t1 * t1 + 0.5 * t2 * t2;",
+    "weno5_smoothness_coefficient": ("T weno5(T a, T b, T c, T d, T e) {\n  const double eps = 1e-6;\n  T t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;\n  T beta0 = (13.0 / 12.0) * t1 * t1 + 0.25 * t2 * t2;",
+                                     "T weno5(T a, T b, T c, T d, T e) {\n  const double eps = 1e-6;\n  T t1 = (a - 2.0 * b) + c, t2 = (a - 4.0 * b) + 3.0 * c;\n  T beta0 = (13.0 / 12.0) * t1 * t1 + 0.5 * t2 * t2;",
                                      "test_weno5_matches_its_definition"),
-    "weno5_eps": ("double weno5(double a, double b, double c, double d, double e) {\n  const double eps = 1e-6;",
-                  "double weno5(double a, double b, double c, double d, double e) {\n  const double eps = 1e-40;",
+    "weno5_eps": ("T weno5(T a, T b, T c, T d, T e) {\n  const double eps = 1e-6;",
+                  "T weno5(T a, T b, T c, T d, T e) {\n  const double eps = 1e-40;",
                   "test_weno5_matches_its_definition"),
     "detail_norm_reads_momentum": ("const int vars[2] = {0, 4};", "const int vars[2] = {0, 1};",
                                    "test_detail_norm_of_a_single_perturbed_cell"),
@@ -118,7 +118,7 @@ MUTATIONS = {
     "stiffened_pressure_offset": ("q.p = (g - 1.0) * (U[4] - 0.5 * q.rho * q2) - g * B;",
                                   "q.p = (g - 1.0) * (U[4] - 0.5 * q.rho * q2) - B;",
                                   "test_cfl_time_step_closed_form[0.0]"),
-    "hllc_left_speed_without_roe": ("double SL = std::min(uL - a.c, e.lam[0]);", "double SL = uL - a.c;",
+    "hllc_left_speed_without_roe": ("T SL = omin(uL - a.c, e.lam[0]);", "T SL = uL - a.c;",
                                     "test_hllc_exact_on_isolated_shocks[0]"),
     "rhs_y_faces_transposed": ("acc = acc + (F[fidx(1, v, j, i, k)] - F[fidx(1, v, j + 1, i, k)]);",
                                "acc = acc + (F[fidx(1, v, j, k, i)] - F[fidx(1, v, j + 1, k, i)]);",
@@ -128,6 +128,15 @@ MUTATIONS = {
                                    "test_rhs_commutes_with_rotations_and_mirrors[mirror-0-0-0.0]"),
     "level1_groups_coarsened": ("} else if (n.level >= 2) {", "} else if (n.level >= 1) {",
                                 "test_tags_uniform_state_collapses_to_level1"),
+    "feature_alpha_from_roe_average": ("    double alpha = std::max(std::fabs(lL), std::fabs(lR));\n    for (int m = 0; m < 5; ++m) {",
+                                       "    double alpha = std::fabs(e.lam[k]);\n    for (int m = 0; m < 5; ++m) {",
+                                       "test_selector_features_with_the_split_active_match_their_definition[0]"),
+    "feature_without_alpha_term": ("compress_diff(sgn * (std::fabs(dg) + alpha * std::fabs(dv)));",
+                                   "compress_diff(sgn * std::fabs(dg));",
+                                   "test_selector_features_with_the_split_active_match_their_definition[1]"),
+    "feature_compression_constant": ("double a = std::log10(1.0 + 1e6 * std::fabs(d)) / 8.0;",
+                                     "double a = std::log10(1.0 + 1e5 * std::fabs(d)) / 8.0;",
+                                     "test_selector_features_with_the_split_active_match_their_definition[2]"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }

@@ -1386,6 +1386,72 @@ def test_selector_features_and_labels_special_cases():
     assert lab == 0
 
 
+def _features_by_definition(U6, d, g=1.4):
+    """The selector features written out from their definition with numpy:
+    Roe average of cells 2 and 3, right eigenvectors R of the Roe matrix in the
+    direction frame (columns u-c, entropy, two shear, u+c), left eigenvectors
+    as the numerical inverse of R (not the closed form the oracle uses); per
+    field k in (0, 1, 4): g_m = l_k F(U_m), v_m = l_k U_m, alpha_k the larger
+    |eigenvalue k| of the two face cells, five variations d = s (|dg| +
+    alpha_k |dv|), compressed to sign(d) log10(1 + 1e6 |d|) / 8."""
+    perm = [d, (d + 1) % 3, (d + 2) % 3]
+    rho = U6[:, 0]
+    vel = U6[:, 1:4] / rho[:, None]
+    p = (g - 1) * (U6[:, 4] - 0.5 * rho * (vel ** 2).sum(1))
+    c = np.sqrt(g * p / rho)
+    Ur = np.stack([rho, U6[:, 1 + perm[0]], U6[:, 1 + perm[1]], U6[:, 1 + perm[2]], U6[:, 4]], 1)
+    Fr = np.stack([_np_flux(U6[m], d, g)[[0, 1 + perm[0], 1 + perm[1], 1 + perm[2], 4]] for m in range(6)])
+    w = np.sqrt(rho[2:4])
+    vr = vel[:, perm]
+    ut = (w[0] * vr[2] + w[1] * vr[3]) / w.sum()
+    H = (U6[:, 4] + p) / rho
+    Ht = (w[0] * H[2] + w[1] * H[3]) / w.sum()
+    ct = math.sqrt((g - 1) * (Ht - 0.5 * ut @ ut))
+    R = np.array([[1, ut[0] - ct, ut[1], ut[2], Ht - ut[0] * ct],
+                  [1, ut[0], ut[1], ut[2], 0.5 * ut @ ut],
+                  [0, 0, 1, 0, ut[1]],
+                  [0, 0, 0, 1, ut[2]],
+                  [1, ut[0] + ct, ut[1], ut[2], Ht + ut[0] * ct]]).T
+    L = np.linalg.inv(R)
+    lam = lambda m: np.array([vr[m, 0] - c[m], vr[m, 0], vr[m, 0], vr[m, 0], vr[m, 0] + c[m]])
+    out = []
+    for k in (0, 1, 4):
+        gk, vk = Fr @ L[k], Ur @ L[k]
+        alpha = max(abs(lam(2)[k]), abs(lam(3)[k]))
+        dg, dv = np.diff(gk), np.diff(vk)
+        sgn = np.where(dg != 0, np.sign(dg), np.where(dv < 0, -1.0, 1.0))
+        dd = sgn * (np.abs(dg) + alpha * np.abs(dv))
+        out.append(np.sign(dd) * np.log10(1 + 1e6 * np.abs(dd)) / 8)
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_selector_features_with_the_split_active_match_their_definition(d):
+    """A face whose normal velocity changes sign between its two cells (the
+    entropy and shear fields take the LLF split, alpha = max |u|) and whose
+    acoustic fields are upwinded: every one of the 15 features equals its
+    definition evaluated independently (eigenvectors by numerical inversion,
+    the alpha |dv| term, the log compression), along each axis."""
+    vel = [(0.3, 0.1, -0.05), (0.25, 0.12, -0.04), (0.15, 0.08, -0.02), (-0.2, 0.05, 0.03),
+           (-0.35, 0.02, 0.06), (-0.4, 0.0, 0.07)]
+    rho = [1.0, 1.1, 1.3, 0.9, 0.8, 0.85]
+    p = [1.0, 1.05, 1.2, 0.95, 0.9, 0.92]
+    U6 = []
+    for m in range(6):
+        v = [0.0, 0.0, 0.0]
+        for j in range(3):
+            v[(d + j) % 3] = vel[m][j]
+        U6.append(_cons(rho[m], v[0], v[1], v[2], p[m]))
+    U6 = np.array(U6)
+    f, _ = oracle.face_features(U6, d)
+    ref = _features_by_definition(U6, d)
+    # the alpha |dv| term matters here: with alpha = 0 the entropy features differ
+    assert np.abs(f - ref).max() <= 1e-12 * np.abs(ref).max()
+    # sanity of the set-up: the face's u changes sign (split), both acoustic
+    # eigenvalues keep theirs (upwinded)
+    assert vel[2][0] > 0 > vel[3][0]
+
+
 # ------------------------------------------------------------------ viscous terms
 def _linear_velocity_state(cfg, geo, A, u0, rho=1.3, p=2.0):
     X, Y, Z, _ = I.cell_centres(cfg, geo)
