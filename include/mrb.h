@@ -332,11 +332,17 @@ int mrb_profile_read(mrb_ctx* ctx, double* stage_kernel_ms, int64_t* stage_kerne
  *   stream      cudaStream_t (NULL = legacy default stream); asynchronous
  *   sums_dev    device, [5] output: sum over blocks of U dx^3, blocks in the
  *               given order, the same fixed reduction order as mrb_sums
+ * With the blocks in mrb_list_blocks' leaf order the result is bitwise that
+ * of mrb_sums for a single instance; n_blocks = 0 gives zeros.
  * Returns EINVAL for bad arguments, ECAPACITY for n_blocks >
- * MRB_NOALLOC_MAX_BLOCKS (nothing is launched), ECUDA on a CUDA error.  The
- * first call on a device looks up the scratch address with that device
- * current; make it before any stream capture.  All calls share the scratch,
- * which keeps the last call's contents: calls that overlap on the GPU race. */
+ * MRB_NOALLOC_MAX_BLOCKS (nothing is launched), ECUDA on a CUDA error of this
+ * call's own launches (an error pending from an earlier call is left alone).
+ * Every call made outside a stream capture looks up the scratch address with
+ * the calling device current (so a device reset is picked up); a call on a
+ * stream being captured reuses the last address found on that device and
+ * fails with ECUDA if there is none: make one call before any capture.  All
+ * calls share the scratch, which keeps the last call's contents: calls that
+ * overlap on the GPU race. */
 #define MRB_NOALLOC_MAX_BLOCKS 65536
 int mrb_block_sums_noalloc(const double* blocks_dev, int64_t n_blocks, const int32_t* levels_dev, double dx0,
                            void* stream, double* sums_dev);

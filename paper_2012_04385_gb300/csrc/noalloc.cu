@@ -10,13 +10,17 @@
 // Limits and behaviour (also stated in include/mrb.h):
 //  * at most MRB_NOALLOC_MAX_BLOCKS blocks per call (larger n is rejected with
 //    MRB_ECAPACITY before anything is launched);
-//  * the first call on a device looks up the array's device address with that
-//    device current (cudaGetSymbolAddress) and caches it; make that first call
-//    before any stream capture on the device;
+//  * the array's device address is looked up (cudaGetSymbolAddress) with the
+//    calling device current on every call made outside a stream capture, and
+//    cached per device; a call made while its stream is being captured uses
+//    the cached address, so make one call on the device before any capture.
+//    After a device reset the next uncaptured call looks the address up again;
 //  * all calls share the one array, which keeps the last call's contents:
 //    calls that overlap on the GPU (different streams, or different host
 //    threads on one device) race on it;
-//  * no cudaMalloc, cudaFree or allocating library routine is called.
+//  * no cudaMalloc, cudaFree or allocating library routine is called;
+//  * the status reports only this call's own launch errors: an error left
+//    pending by an earlier, unrelated call stays pending for its owner.
 #include <algorithm>
 #include <mutex>
 
@@ -83,21 +87,41 @@ extern "C" int mrb_block_sums_noalloc(const double* blocks_dev, int64_t n_blocks
   if (n_blocks > NOALLOC_MAX_BLOCKS) return MRB_ECAPACITY;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MRB_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MRB_ECUDA;
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
+      if (cap != cudaStreamCaptureStatusNone) return MRB_ECUDA;   // no address known yet: call once uncaptured
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_partial) != cudaSuccess || !p) return MRB_ECUDA;
       g_scratch_ptr[dev] = (double*)p;
     }
     scratch = g_scratch_ptr[dev];
   }
-  cudaStream_t st = (cudaStream_t)stream;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) return MRB_ECUDA;
+  // each launch's own status (cudaLaunchKernel returns it), so that an error
+  // pending from an unrelated earlier call is neither reported nor cleared here
+  const cudaError_t pending = cudaPeekAtLastError();
+  cudaError_t e = cudaSuccess;
   if (n_blocks > 0) {
-    const int grid = (int)std::min<int64_t>(n_blocks, (int64_t)sm_count() * 4);
-    k_noalloc_partial<<<grid, 256, 0, st>>>(blocks_dev, n_blocks, levels_dev, dx0, scratch);
+    const int grid = (int)std::min<int64_t>(n_blocks, (int64_t)nsm * 4);
+    void* a1[] = {(void*)&blocks_dev, (void*)&n_blocks, (void*)&levels_dev, (void*)&dx0, (void*)&scratch};
+    e = cudaLaunchKernel((const void*)k_noalloc_partial, dim3(grid), dim3(256), a1, 0, st);
+    if (e == cudaSuccess) ++g_kernel_launches;
   }
-  k_noalloc_finish<<<1, 32, 0, st>>>(scratch, n_blocks, sums_dev);
-  return cudaGetLastError() == cudaSuccess ? MRB_OK : MRB_ECUDA;
+  if (e == cudaSuccess) {
+    const double* partial = scratch;
+    void* a2[] = {(void*)&partial, (void*)&n_blocks, (void*)&sums_dev};
+    e = cudaLaunchKernel((const void*)k_noalloc_finish, dim3(1), dim3(32), a2, 0, st);
+    if (e == cudaSuccess) ++g_kernel_launches;
+  }
+  if (e != cudaSuccess) {
+    if (pending == cudaSuccess) cudaGetLastError();   // clear our own launch error
+    return MRB_ECUDA;
+  }
+  return MRB_OK;
 }
