@@ -1,9 +1,11 @@
 """GPU checks of the learned reconstruction selector against the oracle.
 
-Features and labels of sampled faces against the oracle's FP64 definition,
-gradients of the training kernels against the FP64 reference (same BF16
-roundings), tensor-core logits against the reference forward, one Adam step,
-training progress, and the learned path's accuracy against plain WENO5.
+Features and labels of sampled faces against the oracle's FP64 definition
+(features within their FP32 bound, labels equal away from the decision
+threshold), gradients of the training kernels against the FP64 reference
+(same BF16 roundings), tensor-core logits against the reference forward, one
+Adam step, training progress, and the learned path's accuracy against plain
+WENO5 and against the FP64 oracle on an MR tree.
 """
 import numpy as np
 import pytest
@@ -36,8 +38,27 @@ def _face_cells(U, li, fid_in_leaf):
     return D, np.array([U[li, :, k + 4, j + 4, i + 4] for (i, j, k) in cells])
 
 
+EPS32 = 2.0 ** -23
+
+
+def feature_bound(fo, S, k=64):
+    """FP32 bound of each selector feature: the variation d = |dg| + alpha |dv|
+    is a difference of FP32 values of size S (the field's largest |g| + alpha
+    |v|), so its error is a few ulp of S; the compression sign(d) log10(1 +
+    1e6 |d|) / 8 turns an error e of d into e 1e6 / (8 ln 10 (1 + 1e6 |d|)).
+    k ulp of S, plus a few ulp of the feature itself."""
+    d = (10.0 ** (8.0 * np.abs(fo)) - 1.0) / 1e6
+    slope = 1e6 / (8.0 * np.log(10.0)) / (1.0 + 1e6 * d)
+    return k * EPS32 * np.repeat(S, 5) * slope + 8 * EPS32
+
+
 @pytest.mark.parametrize("ic_name", ["smooth", "rough"])
 def test_features_and_labels_vs_oracle(ic_name):
+    """Each sampled face's 15 features within their FP32 bound of the
+    oracle's FP64 values, and its label equal to the oracle's wherever the
+    oracle's decision margin |WENO5 - linear5| - threshold is larger than an
+    FP32 budget (64 ulp of the values compared); faces inside the budget may
+    go either way and must be rare."""
     cfg = I.periodic_config(base=(2, 1, 1), precision=I.FP32_ACC64)
     g = mrb.Context(cfg, 4)
     k, geo = g.list_blocks()
@@ -48,17 +69,26 @@ def test_features_and_labels_vs_oracle(ic_name):
     f, lab, where = g.face_samples(tau_lab=1e-3, stride=11, with_where=True)
     f, lab, where = f.cpu().numpy(), lab.cpu().numpy(), where.cpu().numpy()
     U = g.get_state(k, with_halo=True).cpu().numpy()
-    agree, n = 0, len(where)
-    maxerr = 0.0
+    n = len(where)
+    worst, tight, near, mism = 0.0, 0, 0, []
     for s in range(n):
         li, fid = divmod(int(where[s]), 13056)
         D, U6 = _face_cells(U, li, fid)
-        fo, lo = oracle.face_features(U6, D, tau_lab=1e-3)
-        maxerr = max(maxerr, np.abs(f[s, :15] - fo).max())
-        agree += int(lo == lab[s])
-    print(ic_name, "samples", n, "max feature error", maxerr, "label agreement", agree / n, "positives", lab.mean())
-    assert maxerr < 1e-2
-    assert agree / n >= 0.97
+        fo, lo, aux = oracle.face_features(U6, D, tau_lab=1e-3, with_aux=True)
+        b = feature_bound(fo, aux[2:5])
+        err = np.abs(f[s, :15] - fo)
+        worst = max(worst, float((err / b).max()))
+        tight += int((b < 1e-3).sum())
+        budget = 64 * EPS32 * max(aux[1], aux[2:5].max())
+        if abs(aux[0]) <= budget:
+            near += 1
+        elif lo != lab[s]:
+            mism.append((s, lo, int(lab[s]), aux[0], budget))
+    print(ic_name, "samples", n, "worst feature error / bound", worst, "features with bound < 1e-3",
+          tight / (15 * n), "near-threshold faces", near / n, "positives", lab.mean())
+    assert worst <= 1.0
+    assert not mism, mism[:5]
+    assert near <= 0.03 * n
 
 
 def _rand_batch(n, seed):
@@ -106,9 +136,15 @@ def test_tensor_core_logits_vs_oracle_forward():
     assert (err <= 2e-2 + 2e-2 * np.abs(zr)).all()
 
 
-def test_training_lowers_loss_and_learned_path_accuracy():
+@pytest.fixture(scope="module")
+def small_selector():
     data = learned.generate(sod_steps=8, explosion_steps=6, every=3, stride=5, explosion_lmax=2)
     params, tau, rep = learned.train(data, epochs=6, batch=8192)
+    return params, tau, rep
+
+
+def test_training_lowers_loss_and_learned_path_accuracy(small_selector):
+    params, tau, rep = small_selector
     print(rep)
     assert rep["losses"][-1] < rep["losses"][0]
     assert rep["holdout_missed_positives"] <= 0.01
@@ -129,4 +165,44 @@ def test_training_lowers_loss_and_learned_path_accuracy():
     a, b = res[I.RECON_LEARNED][:, 0], res[I.RECON_WENO][:, 0]
     l1 = np.abs(a - b).sum() / np.abs(b).sum()
     print("learned vs WENO L1 density difference:", l1)
+    assert l1 <= 1e-4
+
+
+def test_learned_path_vs_fp64_oracle_on_an_mr_tree(small_selector):
+    """The headline accuracy bar against the judge itself: the FP32 + learned
+    path and the FP64 oracle (WENO5 everywhere) from the same initial MR tree
+    (the explosion on levels 0..2, with resolution jumps) for 5 full steps,
+    remeshing included: the same tree, and the L1 density difference on the
+    finest grid (leaf cells weighted by volume) at most 1e-4."""
+    params, tau, _ = small_selector
+    cfg_g = I.explosion_config(lmax=2, precision=I.FP32_ACC64, recon=I.RECON_LEARNED, mlp_tau=tau)
+    g = mrb.Context(cfg_g, 600, mlp_params=params)
+    mrb.init_tree(g, I.ic_explosion)
+    cfg_o = I.explosion_config(lmax=2)
+    o = oracle.Oracle(cfg_o)
+    o.set_state(o.keys(level=0), I.ic_explosion(cfg_o, o.geometry(level=0)))
+    for m in range(1, 3):
+        o.fill_halos()
+        geo = o.geometry()
+        o.remesh((geo[:, 0] == m - 1).astype(np.int8))
+        o.set_state(o.keys(level=m), I.ic_explosion(cfg_o, o.geometry(level=m)))
+        if m > 1:
+            o.fill_halos()
+            t, _ = o.predict_and_tag(allow_refine=False)
+            o.remesh(t)
+    o.project()
+    assert np.array_equal(g.keys(), o.keys())
+    g.learned_stats(reset=True)
+    g.step(5)
+    o.step(5)
+    lin, tot = g.learned_stats()
+    kg, geo = g.list_blocks()
+    ko = o.keys()
+    assert np.array_equal(kg, ko)
+    rg = g.get_state(kg).cpu().numpy()[:, 0]
+    ro = o.get_state(ko)[:, 0]
+    w = np.ldexp(1.0, -3 * geo[:, 0].astype(np.int64))
+    l1 = (w * np.abs(rg - ro).reshape(len(kg), -1).sum(1)).sum() / (w * np.abs(ro).reshape(len(ko), -1).sum(1)).sum()
+    print(f"learned FP32 vs FP64 oracle after 5 steps: L1 density {l1:.2e}, faces sent to linear {lin / tot:.3f}")
+    assert 0 < lin < tot
     assert l1 <= 1e-4

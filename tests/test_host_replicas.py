@@ -81,7 +81,7 @@ def test_reference_arm_json_contract():
     import argparse
     sys.path.insert(0, ROOT)
     import bench
-    args = argparse.Namespace(lmax=1, steps=1, warmup=1)
+    args = argparse.Namespace(workload=bench.HEADLINE, lmax=1, steps=1, warmup=1)
     res = bench.run_reference(args, 0, 1)
     assert res["impl"] == "reference" and res["metric"] == bench.METRIC and res["unit"] == bench.UNIT
     assert res["value"] > 0 and res["higher_is_better"] is True
@@ -91,22 +91,33 @@ def test_reference_arm_json_contract():
 
 
 def test_roofline_flop_accounting():
-    """bench.py's FLOP count per face: all fields upwinded with WENO5 gives
-    the Roe eigensystem, the six g projections, the tests, R g and five WENO5
-    reconstructions; a field that splits adds its v projection, the split and
-    a second reconstruction; linear faces replace WENO5 on fields 0, 1, 4."""
+    """bench.py's FLOP count, from the oracle's row counts: all fields
+    upwinded gives the all-upwinded row; a split pattern adds its extra in
+    proportion to its share of faces; linear reconstructions of fields 0, 1, 4
+    save the difference of the two reconstructions' counts, once per
+    reconstruction (two for a field that splits); per cell and stage three
+    directions of row / 16 plus the flux differences and the update."""
     sys.path.insert(0, ROOT)
     import bench
-    base = bench.FLOP_ROE + bench.FLOP_PROJ_G + bench.FLOP_TESTS + bench.FLOP_RG
+    t = bench.flop_table()
+    w = {k: v[0] for k, v in t["row"]["weno5"].items()}
+    lin = {k: v[0] for k, v in t["row"]["linear5"].items()}
     pf, pc = bench.roofline_numbers(0.0)
-    assert pf == base + 5 * bench.FLOP_WENO
-    assert pc == 3 * (17 / 16 * pf + 22 / 16 * 25) + 50
-    pf1, _ = bench.roofline_numbers(0.0, (1.0, 0.0, 0.0, 0.0, 0.0))
-    assert pf1 - pf == bench.FLOP_V[0] + bench.FLOP_SPLIT + bench.FLOP_WENO
-    pf2, _ = bench.roofline_numbers(0.0, (0.0, 0.0, 0.5, 0.0, 0.0))
-    assert pf2 - pf == 0.5 * (bench.FLOP_V[2] + bench.FLOP_SPLIT + bench.FLOP_WENO)
+    assert pf == w["all_upwind"] / 17
+    assert pc == 3 * w["all_upwind"] / 16 + 30 + 20
+    pf1, _ = bench.roofline_numbers(0.0, (0.0, 1.0, 1.0, 1.0, 0.0))
+    assert pf1 == w["split_123"] / 17
+    pf2, _ = bench.roofline_numbers(0.0, (0.5, 0.0, 0.0, 0.0, 0.0))
+    assert pf2 == pytest.approx((w["all_upwind"] + 0.5 * (w["split_0"] - w["all_upwind"])) / 17)
+    # all five fields linear in the oracle's own count = WENO5 row minus two
+    # linear fields' worth (the shear fields keep WENO5 in the selector path)
+    save = t["recon"]["weno5"][0] - t["recon"]["linear5"][0]
     pl, _ = bench.roofline_numbers(1.0)
-    assert pf - pl == 3 * (bench.FLOP_WENO - bench.FLOP_LIN)
+    assert pl * 17 == w["all_upwind"] - 17 * 3 * save
+    assert lin["all_upwind"] == w["all_upwind"] - 17 * 5 * save
+    pls, _ = bench.roofline_numbers(1.0, (0.0, 1.0, 1.0, 1.0, 0.0))
+    assert pls * 17 == w["split_123"] - 17 * 4 * save
+    assert lin["split_123"] == w["split_123"] - 17 * 8 * save
 
 
 def test_reference_arm_under_torchrun_prints_one_line():
