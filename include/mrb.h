@@ -129,8 +129,11 @@ typedef struct mrb_ctx mrb_ctx;
  * together).  Per block: two stage buffers with halo (2 x 5 x 24^3 doubles),
  * the u^n buffer of the RK step (5 x 16^3), six face-flux buffers
  * (6 x 5 x 16^2) and the learned selector's decision bits of the current
- * step (432 words), each region 256-byte aligned.  Returns 0 for a bad
- * config. */
+ * step (432 words); with precision MRB_FP32_ACC64 also FP32 primitive
+ * records (rho, u, v, w, p, E) of the internal cells of both stage buffers
+ * (2 x 6 x 16^3 floats), which the mixed-precision stage kernel reads instead
+ * of converting the FP64 state.  Each region 256-byte aligned.  Returns 0 for
+ * a bad config. */
 size_t mrb_pool_bytes(const mrb_config* cfg, int64_t n_slots);
 
 /* Create a context: checks the config, builds the level-0 topology of every
@@ -163,6 +166,14 @@ int mrb_set_cons(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, const doubl
 /* Conserved state of the listed blocks into cons_dev: [n][5][16^3] internal
  * cells (with_halo = 0) or [n][5][24^3] stored cells (with_halo = 1). */
 int mrb_get_state(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, double* cons_dev, int32_t with_halo);
+
+/* FP32 primitive records (rho, u, v, w, p, E) of the internal cells of the
+ * listed blocks, [n][6][16^3] floats into records_dev (device), as the
+ * mixed-precision path keeps them (fresh = 0), or converted afresh from the
+ * FP64 state with the same arithmetic (fresh = 1): the two agree bit for bit
+ * whenever the records are up to date.  EINVAL in an FP64 context or on an
+ * unknown id.  (Inspection of the mixed-precision path's bookkeeping.) */
+int mrb_get_records(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, float* records_dev, int32_t fresh);
 
 /* Halo fill of every node (Sec. 3, Fig. MrCommunicationMesh): a halo region
  * facing a same-level node (brother or cousin) is a copy of its internal
@@ -221,6 +232,18 @@ int mrb_mr_predict_and_tag(mrb_ctx* ctx, int32_t allow_refine, int8_t* tags_dev,
  * Synchronises the stream.  *n_leaves (nullable) receives the leaf count.
  * ECAPACITY when the pool has no free block left (the tree is unchanged). */
 int mrb_remesh(mrb_ctx* ctx, const int8_t* tags_dev, int64_t* n_leaves);
+
+/* Refine every leaf of `level` (Alg. Initialization: "refine all blocks of
+ * level l_(m-1)" before the initial condition is imposed on level m): full
+ * halo fill, then mrb_remesh with REFINE tags on those leaves.  Synchronises;
+ * *n_leaves (nullable) receives the leaf count.  EINVAL for a bad level,
+ * ECAPACITY as mrb_remesh. */
+int mrb_refine_level(mrb_ctx* ctx, int32_t level, int64_t* n_leaves);
+
+/* Refine the listed leaves (keys_host: ids of current leaves; restoring a
+ * saved tree level by level): as mrb_refine_level.  EINVAL when an id is not
+ * a leaf. */
+int mrb_refine_keys(mrb_ctx* ctx, const uint64_t* keys_host, int64_t n, int64_t* n_leaves);
 
 /* nsteps complete steps: dt from Eq. (Cfl), three fused stages each preceded
  * by the halo fill and followed by the averaging, then (when any lmax > 0)
@@ -315,6 +338,30 @@ int mrb_mlp_train_step(float* params_dev, float* adam_m_dev, float* adam_v_dev, 
  * issued since profiling started (graph replays count their kernel nodes).
  * Any pointer may be null. */
 int mrb_profile(mrb_ctx* ctx, int32_t enable);
+
+/* Launch shapes (scheduling only: every choice gives bit-identical results;
+ * the paper has no counterpart -- its blocks are distributed over MPI ranks).
+ * params[MRB_NTUNE]: [0] stage-kernel waves (CTAs = SMs x resident CTAs per SM
+ * x waves, 1..8), [1] stage work-item order (0 strided over the grid, 1 one
+ * contiguous run of (block, z-slab) items per CTA), [2] region-copy halo-fill
+ * CTAs per SM, [3] prediction halo-fill CTAs per SM, [4] averaging CTAs per SM
+ * (1..32 each).  Defaults 1, 0, 8, 4, 8.  Per context; mrb_set_tune returns
+ * EINVAL outside the ranges and re-captures the step graphs at the next
+ * mrb_step. */
+#define MRB_NTUNE 5
+int mrb_get_tune(mrb_ctx* ctx, int32_t* params);
+int mrb_set_tune(mrb_ctx* ctx, const int32_t* params);
+/* Autotuner: times the candidate shapes on the context's current tree (CUDA
+ * events on cfg.stream, `reps` repetitions each, after one warm-up) and keeps
+ * the fastest: stage waves {1, 2, 4} x item order {0, 1}, then fill CTAs per SM
+ * {4, 8, 16} x {2, 4, 8}, then averaging CTAs per SM {4, 8, 16}.  The timed work
+ * leaves the simulation state unchanged: stage 0 (with the learned selector
+ * also stage 1) from the current stage buffer writes only the other buffer and
+ * per-step scratch, the halo fill and the averaging recompute what they wrote
+ * before.  The selector's face counters (mrb_learned_stats) are reset.
+ * times (host, nullable, [6]): default and tuned ms of the stage kernel(s), of
+ * one halo fill and of one averaging pass.  Synchronises. */
+int mrb_autotune(mrb_ctx* ctx, int32_t reps, double* times);
 int mrb_profile_read(mrb_ctx* ctx, double* stage_kernel_ms, int64_t* stage_kernel_launches, int64_t* kernel_launches);
 
 /* Conservation sums for callers that cannot allocate device memory.  (The

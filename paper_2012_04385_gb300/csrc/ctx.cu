@@ -94,6 +94,7 @@ struct mrb_ctx {
   double prof_ms = 0.0;
   long long prof_rhs = 0, prof_base = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend;   // direct launches awaiting their timing
+  Tune tune{1, 8, 4, 8};             // launch shapes of this context (mrb_set_tune / mrb_autotune)
   std::string err;
 
   Topo topo() const {
@@ -270,10 +271,12 @@ struct mrb_ctx {
     if (e1) CK(cudaEventRecordWithFlags(e1, st, flags));
     for (int l = max_lmax - 1; l >= 0; --l) launch_face_avg_level(topo(), P, l, st);
     launch_jump(topo(), phys, P, cur ^ 1, s, dt, nullptr, st);
+    launch_shadow(topo(), phys, P, cur ^ 1, SH_JUMP, nullptr, 0, 0, st);
     cur ^= 1;
   }
   void project() {
     for (int l = max_lmax - 1; l >= 0; --l) launch_project_level(topo(), P, cur, l, st);
+    launch_shadow(topo(), phys, P, cur, SH_INTERNAL, nullptr, 0, 0, st);
   }
   void step_stages() {
     launch_cfl(topo(), phys, P, cur, d_smax, d_dt, d_status, st);
@@ -405,6 +408,7 @@ struct mrb_ctx {
       }
       upload_list(pairs);
       launch_refine_fill(topo(), phys, P, cur, d_list, (int)newpairs.size(), st);
+      launch_shadow(topo(), phys, P, cur, SH_LIST, d_list, (int)newpairs.size(), 2, st);
       list_used();
       check_launch();
     }
@@ -449,6 +453,7 @@ int fail(mrb_ctx* c, int code, const std::string& msg) {
 
 template <class F> int guarded(mrb_ctx* c, F&& f) {
   if (!c) return fail(nullptr, MRB_EINVAL, "null context");
+  g_tune = c->tune;       // this context's launch shapes for the launches below
   try {
     f();
     cudaError_t e = cudaGetLastError();
@@ -497,7 +502,10 @@ extern "C" {
 size_t mrb_pool_bytes(const mrb_config* cfg, int64_t n_slots) {
   if (check_config(cfg) != MRB_OK || n_slots <= 0) return 0;
   const size_t n = (size_t)n_slots;
-  return align256(n * SLOT_U * 8) * 2 + align256(n * SLOT_N * 8) + align256(n * SLOT_F * 8) + align256(n * SLOT_SEL * 4);
+  // the mixed-precision path also keeps FP32 records of both stage buffers' internal cells
+  const size_t sh = (cfg->precision == MRB_FP32_ACC64) ? align256(n * SLOT_SH * 4) * 2 : 0;
+  return align256(n * SLOT_U * 8) * 2 + align256(n * SLOT_N * 8) + align256(n * SLOT_F * 8) + align256(n * SLOT_SEL * 4) +
+         sh;
 }
 
 int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ctx** out) {
@@ -536,6 +544,13 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     c->P.face = (double*)q;
     q += align256(n * SLOT_F * 8);
     c->P.sel = (uint32_t*)q;
+    q += align256(n * SLOT_SEL * 4);
+    c->P.sh[0] = c->P.sh[1] = nullptr;
+    if (cfg->precision == MRB_FP32_ACC64) {
+      c->P.sh[0] = (float*)q;
+      q += align256(n * SLOT_SH * 4);
+      c->P.sh[1] = (float*)q;
+    }
     Phys& p = c->phys;
     p.gamma = cfg->gamma;
     p.B = cfg->B;
@@ -557,6 +572,7 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     p.flux = cfg->flux;
     p.mlp = (const float*)cfg->mlp_weights;
     p.mlp_tau = (float)cfg->mlp_tau;
+    p.blocked = 0;
     c->max_lmax = 0;
     for (int i = 0; i < cfg->n_instances; ++i) c->max_lmax = std::max(c->max_lmax, (int)cfg->lmax[i]);
     c->d_keys = c->dalloc<uint64_t>(n);
@@ -669,6 +685,7 @@ int mrb_set_state(mrb_ctx* c, const uint64_t* keys_host, int64_t n, const double
     std::vector<int32_t> v = c->nodes_of(keys_host, n);
     c->upload_list(v);
     launch_set_state(c->topo(), c->phys, c->P, c->cur, c->d_list, (int)n, prim_dev, c->st);
+    launch_shadow(c->topo(), c->phys, c->P, c->cur, SH_LIST, c->d_list, (int)n, 1, c->st);
     c->list_used();
   });
 }
@@ -679,6 +696,7 @@ int mrb_set_cons(mrb_ctx* c, const uint64_t* keys_host, int64_t n, const double*
     std::vector<int32_t> v = c->nodes_of(keys_host, n);
     c->upload_list(v);
     launch_set_cons(c->topo(), c->P, c->cur, c->d_list, (int)n, cons_dev, c->st);
+    launch_shadow(c->topo(), c->phys, c->P, c->cur, SH_LIST, c->d_list, (int)n, 1, c->st);
     c->list_used();
   });
 }
@@ -689,6 +707,17 @@ int mrb_get_state(mrb_ctx* c, const uint64_t* keys_host, int64_t n, double* cons
     std::vector<int32_t> v = c->nodes_of(keys_host, n);
     c->upload_list(v);
     launch_get_state(c->topo(), c->P, c->cur, c->d_list, (int)n, cons_dev, with_halo ? 1 : 0, c->st);
+    c->list_used();
+  });
+}
+
+int mrb_get_records(mrb_ctx* c, const uint64_t* keys_host, int64_t n, float* records_dev, int32_t fresh) {
+  return guarded(c, [&] {
+    if (!c->P.sh[0]) throw Err(MRB_EINVAL, "no FP32 records in an FP64 context");
+    if (n < 0 || (n > 0 && (!keys_host || !records_dev))) throw Err(MRB_EINVAL, "bad arguments");
+    std::vector<int32_t> v = c->nodes_of(keys_host, n);
+    c->upload_list(v);
+    launch_get_records(c->topo(), c->phys, c->P, c->cur, c->d_list, (int)n, records_dev, fresh ? 1 : 0, c->st);
     c->list_used();
   });
 }
@@ -744,6 +773,45 @@ int mrb_remesh(mrb_ctx* c, const int8_t* tags_dev, int64_t* n_leaves) {
   int st = 0;
   cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   return st ? fail(c, st, "device status set") : MRB_OK;
+}
+
+// Refinement of chosen leaves (Alg. Initialization's "refine all blocks of
+// level m-1", and restoring a saved tree): full halo fill, REFINE tags for the
+// selected leaves, remesh (children predicted from their parent).
+namespace {
+int refine_where(mrb_ctx* c, const std::vector<int8_t>& tags, int64_t* n_leaves) {
+  int rc = guarded(c, [&] {
+    c->fill_halos();
+    c->detail_filled = false;
+    if (!tags.empty()) CK(cudaMemcpyAsync(c->d_tags, tags.data(), tags.size(), cudaMemcpyHostToDevice, c->st));
+    int64_t nl = c->remesh(c->d_tags);
+    if (n_leaves) *n_leaves = nl;
+    CK(cudaStreamSynchronize(c->st));
+  });
+  return rc;
+}
+}  // namespace
+
+int mrb_refine_level(mrb_ctx* c, int32_t level, int64_t* n_leaves) {
+  if (!c) return fail(nullptr, MRB_EINVAL, "null context");
+  if (level < 0 || level > MRB_MAX_LEVEL) return fail(c, MRB_EINVAL, "bad level");
+  std::vector<int8_t> tags((size_t)c->n_leaves());
+  for (int li = 0; li < c->n_leaves(); ++li)
+    tags[li] = (c->nodes[c->h_leaves[li]].level == level) ? (int8_t)MRB_TAG_REFINE : (int8_t)MRB_TAG_KEEP;
+  return refine_where(c, tags, n_leaves);
+}
+
+int mrb_refine_keys(mrb_ctx* c, const uint64_t* keys_host, int64_t n, int64_t* n_leaves) {
+  if (!c) return fail(nullptr, MRB_EINVAL, "null context");
+  if (n < 0 || (n > 0 && !keys_host)) return fail(c, MRB_EINVAL, "bad arguments");
+  std::vector<int8_t> tags((size_t)c->n_leaves(), (int8_t)MRB_TAG_KEEP);
+  for (int64_t b = 0; b < n; ++b) {
+    const int64_t i = c->find(keys_host[b]);
+    const auto it = (i < 0) ? c->h_leaves.end() : std::lower_bound(c->h_leaves.begin(), c->h_leaves.end(), (int32_t)i);
+    if (it == c->h_leaves.end() || *it != i) return fail(c, MRB_EINVAL, "not the id of a leaf");
+    tags[it - c->h_leaves.begin()] = (int8_t)MRB_TAG_REFINE;
+  }
+  return refine_where(c, tags, n_leaves);
 }
 
 int mrb_step(mrb_ctx* c, int32_t nsteps, double* dt_hist_dev) {
@@ -861,6 +929,117 @@ int mrb_neighbors(mrb_ctx* c, const uint64_t* keys_host, int64_t n, uint64_t* nb
       for (int r = 0; r < 27; ++r) {
         const int32_t v = all[(size_t)idx[b] * 27 + r];
         nbr_host[b * 27 + r] = (v >= 0) ? c->nodes[v].key : (v == -1 ? 0ull : 1ull);
+      }
+  });
+}
+
+int mrb_get_tune(mrb_ctx* c, int32_t* params) {
+  return guarded(c, [&] {
+    if (!params) throw Err(MRB_EINVAL, "null params");
+    params[0] = c->tune.stage_waves;
+    params[1] = c->phys.blocked;
+    params[2] = c->tune.fill_copy;
+    params[3] = c->tune.fill_pred;
+    params[4] = c->tune.project;
+  });
+}
+
+namespace {
+bool tune_ok(const int32_t* q) {
+  return q[0] >= 1 && q[0] <= 8 && (q[1] == 0 || q[1] == 1) && q[2] >= 1 && q[2] <= 32 && q[3] >= 1 && q[3] <= 32 &&
+         q[4] >= 1 && q[4] <= 32;
+}
+void apply_tune(mrb_ctx* c, const int32_t* q) {
+  c->tune = Tune{q[0], q[2], q[3], q[4]};
+  c->phys.blocked = q[1];
+  g_tune = c->tune;
+  c->graph_dirty = true;     // the replayed graphs hold launch shapes and kernel arguments
+}
+}  // namespace
+
+int mrb_set_tune(mrb_ctx* c, const int32_t* params) {
+  return guarded(c, [&] {
+    if (!params || !tune_ok(params)) throw Err(MRB_EINVAL, "launch shape out of range");
+    apply_tune(c, params);
+  });
+}
+
+// Scheduling-only search: each candidate is timed with CUDA events on the
+// context's stream over `reps` repetitions of work that leaves the
+// simulation state unchanged -- stage 0 (and, with the learned selector, a
+// stage 1 after it) from the current stage buffer, whose writes go to the
+// other stage buffer and the per-step scratch (u^n, face fluxes, decisions,
+// FP32 records of the other buffer); the halo fill of the current buffer;
+// the averaging (the same averages again).  Coordinate search: stage waves
+// and item order, then fill shapes, then averaging shape.
+int mrb_autotune(mrb_ctx* c, int32_t reps, double* times) {
+  return guarded(c, [&] {
+    if (reps < 1) throw Err(MRB_EINVAL, "reps < 1");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int fmode = (c->cfg.precision == MRB_FP32_ACC64 && !(c->cfg.mu > 0.0)) ? FILL_STAGE : FILL_FULL;
+    launch_cfl(c->topo(), c->phys, c->P, c->cur, c->d_smax, c->d_dt, c->d_status, c->st);
+    auto run = [&](int what) {
+      if (what == 0) {
+        if (c->cfg.precision == MRB_FP32_ACC64) {
+          launch_rhs_rk_f32(c->topo(), c->phys, c->P, c->cur, 0, c->d_dt, nullptr, c->st);
+          if (c->cfg.recon == MRB_RECON_LEARNED && c->cfg.mlp_weights)
+            launch_rhs_rk_f32(c->topo(), c->phys, c->P, c->cur, 1, c->d_dt, nullptr, c->st);
+        } else {
+          launch_rhs_rk_f64(c->topo(), c->phys, c->P, c->cur, 0, c->d_dt, nullptr, c->st);
+        }
+      } else if (what == 1) {
+        c->fill_halos(fmode);
+      } else {
+        c->project();
+      }
+    };
+    auto time_of = [&](int what, const int32_t* q) {
+      apply_tune(c, q);
+      run(what);   // warm-up
+      CK(cudaEventRecord(e0, c->st));
+      for (int r = 0; r < reps; ++r) run(what);
+      CK(cudaEventRecord(e1, c->st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      return (double)ms / reps;
+    };
+    int32_t best[5] = {c->tune.stage_waves, c->phys.blocked, c->tune.fill_copy, c->tune.fill_pred, c->tune.project};
+    const int32_t def[5] = {1, 0, 8, 4, 8};
+    double t_def[3], t_best[3];
+    for (int what = 0; what < 3; ++what) t_def[what] = time_of(what, def);
+    std::copy(def, def + 5, best);
+    t_best[0] = t_def[0];
+    for (int w : {1, 2, 4})
+      for (int b : {0, 1}) {
+        int32_t q[5] = {w, b, best[2], best[3], best[4]};
+        const double tt = time_of(0, q);
+        if (tt < t_best[0]) { t_best[0] = tt; best[0] = w; best[1] = b; }
+      }
+    t_best[1] = t_def[1];
+    for (int fc : {4, 8, 16})
+      for (int fp : {2, 4, 8}) {
+        int32_t q[5] = {best[0], best[1], fc, fp, best[4]};
+        const double tt = time_of(1, q);
+        if (tt < t_best[1]) { t_best[1] = tt; best[2] = fc; best[3] = fp; }
+      }
+    t_best[2] = t_def[2];
+    for (int pr : {4, 8, 16}) {
+      int32_t q[5] = {best[0], best[1], best[2], best[3], pr};
+      const double tt = time_of(2, q);
+      if (tt < t_best[2]) { t_best[2] = tt; best[4] = pr; }
+    }
+    apply_tune(c, best);
+    CK(cudaMemsetAsync(c->d_lin, 0, 2 * sizeof(unsigned long long), c->st));   // the timed launches' selector counts
+    CK(cudaStreamSynchronize(c->st));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (times)
+      for (int what = 0; what < 3; ++what) {
+        times[2 * what] = t_def[what];
+        times[2 * what + 1] = t_best[what];
       }
   });
 }

@@ -25,8 +25,8 @@ void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, 
 void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st,
                            int mode) {
   const NodeSet ns{level, nullptr, 0};
-  k_fill_regions_t<float><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, ns, mode);
-  k_fill_predict_t<float><<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, ns, mode);
+  k_fill_regions_t<float><<<sm_count() * g_tune.fill_copy, 256, 0, st>>>(t, pool, cur, ns, mode);
+  k_fill_predict_t<float><<<sm_count() * g_tune.fill_pred, 256, 0, st>>>(t, pool, cur, ns, mode);
   k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, mode);
   g_kernel_launches += 3;
 }
@@ -38,6 +38,95 @@ void launch_fill_list_f32(const Topo& t, const Phys& p, const Pool& pool, int cu
   k_fill_predict_t<float><<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, ns, FILL_FULL);
   k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, FILL_FULL);
   g_kernel_launches += 3;
+}
+
+// FP32 records of stage buffer b: one CTA per item, the records of the item's
+// internal cells recomputed from the FP64 values (make_record, the same
+// arithmetic as the stage kernel's own conversion).
+__global__ void __launch_bounds__(256) k_shadow(Topo t, Phys p, Pool pool, int b, int mode,
+                                                const int32_t* __restrict__ list, int n, int stride) {
+  const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
+  const int nitems = (mode == SH_INTERNAL) ? t.cnt[CNT_NNODES] : (mode == SH_JUMP ? t.cnt[CNT_JUMP] : n);
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    int node, mask = 0;
+    if (mode == SH_INTERNAL) {
+      node = w;
+      if (t.child0[node] < 0) continue;           // leaves keep the stage kernel's records
+    } else if (mode == SH_JUMP) {
+      node = t.leaves[t.jump[w] >> 6];
+      mask = t.jump[w] & 63;
+    } else {
+      node = list[(size_t)w * stride];
+    }
+    const double* U = pool.buf[b] + (size_t)t.slot[node] * SLOT_U;
+    float* R = pool.sh[b] + (size_t)t.slot[node] * SLOT_SH;
+    if (mode == SH_JUMP) {
+      // the plane of cells next to each side whose neighbour is refined
+      for (int sd = 0; sd < 6; ++sd) {
+        if (!((mask >> sd) & 1)) continue;
+        const int d = sd / 2, hi = sd & 1;
+        const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+        for (int e = threadIdx.x; e < NFACE; e += blockDim.x) {
+          int c[3];
+          c[d] = hi ? NB - 1 : 0;
+          c[t1] = e % 16;
+          c[t2] = e / 16;
+          const int s = sidx(c[0], c[1], c[2]), ii = iidx(c[0], c[1], c[2]);
+          float rec[6];
+          make_record(U[s], U[NCELL + s], U[2 * NCELL + s], U[3 * NCELL + s], U[4 * NCELL + s], g, B, gm1, rec);
+#pragma unroll
+          for (int f = 0; f < 6; ++f) R[f * NINT + ii] = rec[f];
+        }
+      }
+    } else {
+      for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
+        const int s = sidx(e % 16, (e / 16) % 16, e / 256);
+        float rec[6];
+        make_record(U[s], U[NCELL + s], U[2 * NCELL + s], U[3 * NCELL + s], U[4 * NCELL + s], g, B, gm1, rec);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) R[f * NINT + e] = rec[f];
+      }
+    }
+  }
+}
+
+void launch_shadow(const Topo& t, const Phys& p, const Pool& pool, int b, int mode, const int32_t* list, int n,
+                   int stride, cudaStream_t st) {
+  if (!pool.sh[0]) return;
+  k_shadow<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, b, mode, list, n, stride);
+  ++g_kernel_launches;
+}
+
+// Records of the listed nodes' internal cells (kept, or converted afresh).
+__global__ void __launch_bounds__(256) k_get_records(Topo t, Phys p, Pool pool, int cur,
+                                                     const int32_t* __restrict__ nodes, int n, float* __restrict__ out,
+                                                     int fresh) {
+  const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
+  for (int b = blockIdx.x; b < n; b += gridDim.x) {
+    const int slot = t.slot[nodes[b]];
+    const double* U = pool.buf[cur] + (size_t)slot * SLOT_U;
+    const float* R = pool.sh[cur] + (size_t)slot * SLOT_SH;
+    float* o = out + (size_t)b * SLOT_SH;
+    for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
+      if (fresh) {
+        const int s = sidx(e % 16, (e / 16) % 16, e / 256);
+        float rec[6];
+        make_record(U[s], U[NCELL + s], U[2 * NCELL + s], U[3 * NCELL + s], U[4 * NCELL + s], g, B, gm1, rec);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) o[f * NINT + e] = rec[f];
+      } else {
+#pragma unroll
+        for (int f = 0; f < 6; ++f) o[f * NINT + e] = R[f * NINT + e];
+      }
+    }
+  }
+}
+
+void launch_get_records(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* nodes, int n,
+                        float* out, int fresh, cudaStream_t st) {
+  if (n <= 0) return;
+  k_get_records<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, nodes, n, out, fresh);
+  ++g_kernel_launches;
 }
 
 void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, double* delta_node, int all_nodes,

@@ -12,6 +12,8 @@ namespace mrb {
 
 long long g_kernel_launches = 0;
 
+Tune g_tune = {1, 8, 4, 8};
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -103,8 +105,8 @@ void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, 
   // the FP64 stage kernel reads every halo region: no stage-partial fill
   const NodeSet ns{level, nullptr, 0};
   const int m = (mode == FILL_STAGE) ? FILL_FULL : mode;
-  k_fill_regions_t<double><<<sm_count() * 8, 256, 0, st>>>(t, pool, cur, ns, m);
-  k_fill_predict_t<double><<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, ns, m);
+  k_fill_regions_t<double><<<sm_count() * g_tune.fill_copy, 256, 0, st>>>(t, pool, cur, ns, m);
+  k_fill_predict_t<double><<<sm_count() * g_tune.fill_pred, 256, 0, st>>>(t, pool, cur, ns, m);
   k_fill_bc<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur, ns, m);
   g_kernel_launches += 3;
 }
@@ -226,7 +228,7 @@ void launch_jump(const Topo& t, const Phys& p, const Pool& pool, int target, int
 
 // ---------------------------------------------------------------- averaging (mr.cuh)
 void launch_project_level(const Topo& t, const Pool& pool, int buf, int level, cudaStream_t st) {
-  k_project_octants<<<sm_count() * 8, 256, 0, st>>>(t, pool, buf, level);
+  k_project_octants<<<sm_count() * g_tune.project, 256, 0, st>>>(t, pool, buf, level);
   ++g_kernel_launches;
 }
 

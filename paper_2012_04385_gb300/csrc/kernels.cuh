@@ -58,7 +58,30 @@ struct Phys {
   const float* mlp;        // learned selector parameters (device, FP32), or null
   unsigned long long* lin_count;   // [0] faces sent to linear, [1] faces evaluated
   const int32_t* lmax;     // device [n_inst]
+  int blocked;             // stage kernels: 1 = a contiguous run of work items per CTA, 0 = strided by the grid
 };
+
+// Launch shapes of the scheduling-only tunables (mrb_autotune): every choice
+// gives bit-identical results.  Set from the calling context before its
+// launches.
+struct Tune {
+  int stage_waves;         // stage-kernel CTAs = SMs x resident CTAs per SM x stage_waves
+  int fill_copy;           // region-copy fill CTAs per SM
+  int fill_pred;           // prediction fill CTAs per SM
+  int project;             // averaging CTAs per SM
+};
+extern Tune g_tune;
+
+// This CTA's work items: strided by the grid, or one contiguous run.
+struct ItemRange {
+  int first, step, end;
+};
+__device__ __forceinline__ ItemRange item_range(int nitems, int blocked) {
+  if (!blocked) return ItemRange{(int)blockIdx.x, (int)gridDim.x, nitems};
+  const int per = (nitems + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int a = (int)blockIdx.x * per;
+  return ItemRange{a, 1, a + per < nitems ? a + per : nitems};
+}
 
 // Shu-Osher coefficients of stage s: out = a u^n + b (u + dt L); row 0 TVD-RK3,
 // row 1 TVD-RK2.
@@ -71,6 +94,10 @@ struct Pool {
   double* un;              // u^n, [slot][5][16^3]
   double* face;            // face fluxes, [slot][6][5][16][16]
   uint32_t* sel;           // learned selector decisions of the current step, [slot][SLOT_SEL]
+  // FP32 primitive records (rho, vx, vy, vz, p, E) of the internal cells of
+  // buf[b], [slot][6][16^3]; kept by the mixed-precision path only (null
+  // otherwise), rewritten by every kernel that writes internal cells
+  float* sh[2];
 };
 
 __device__ __forceinline__ double ldexp_(double x, int e) { return ldexp(x, e); }
@@ -128,6 +155,16 @@ void launch_delta_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, d
                       cudaStream_t st);
 void launch_cfl_speeds_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, unsigned long long* smax,
                            int* status, cudaStream_t st);
+// FP32 records of stage buffer b from its FP64 internal cells (mixed-precision
+// path): SH_INTERNAL every internal node (after averaging), SH_JUMP the
+// boundary planes that the jump correction changed, SH_LIST the nodes of a
+// device list of n entries (every `stride`-th entry is a node index).
+enum : int { SH_INTERNAL = 0, SH_JUMP = 1, SH_LIST = 2 };
+void launch_shadow(const Topo& t, const Phys& p, const Pool& pool, int b, int mode, const int32_t* list, int n,
+                   int stride, cudaStream_t st);
+// Records of the listed nodes (kept, or converted afresh from the FP64 state).
+void launch_get_records(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* nodes, int n,
+                        float* out, int fresh, cudaStream_t st);
 void launch_face_samples(const Topo& t, const Phys& p, const Pool& pool, int cur, float tau_lab, int64_t stride,
                          float* feats, uint8_t* labels, int64_t* where, int64_t cap, cudaStream_t st);
 int sm_count();

@@ -68,11 +68,11 @@ constexpr int FACES_PER_LEAF = 3 * 17 * 256;   // 13056
 // Every stride-th face (global id = leaf * 13056 + direction * 4352 + index in
 // the block's canonical face order) -> features [n][16], labels [n] and the
 // face id.  Work items are (leaf, z-slab) as in the stage kernel.
-__device__ __forceinline__ void sample_dir(int D, const double* __restrict__ u, float* __restrict__ S, int li, int z0,
+__device__ __forceinline__ void sample_dir(int D, const RegionSrc& RS, float* __restrict__ S, int li, int z0,
                                            float g, float B, float gm1, float tau_lab, int64_t stride,
                                            float* __restrict__ feats, uint8_t* __restrict__ labels,
                                            int64_t* __restrict__ where, int64_t cap) {
-  load_region_f32(D, u, S, z0, g, B, gm1);
+  load_region_f32(D, RS, S, z0, g, B, gm1);
   __syncthreads();
   const int nf = region_faces(D);
   const int st = region_stride(D);
@@ -107,10 +107,17 @@ __global__ void __launch_bounds__(SF_THREADS) k_face_samples(Topo t, Phys p, Poo
   const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int li = w / SF_NSLAB, z0 = (w % SF_NSLAB) * SF_TZ;
-    const double* u = pool.buf[cur] + (size_t)t.slot[t.leaves[li]] * SLOT_U;
+    // the block's own records and stored halo (filled by the caller), no
+    // neighbour reads
+    const int slot = t.slot[t.leaves[li]];
+    RegionSrc RS;
+    RS.u = pool.buf[cur] + (size_t)slot * SLOT_U;
+    RS.sh = pool.sh[cur] ? pool.sh[cur] + (size_t)slot * SLOT_SH : nullptr;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) RS.nsh[q] = nullptr;
 #pragma unroll 1
     for (int D = 0; D < 3; ++D)
-      sample_dir(D, u, smp_smem, li, z0, g, B, gm1, tau_lab, stride, feats, labels, where, cap);
+      sample_dir(D, RS, smp_smem, li, z0, g, B, gm1, tau_lab, stride, feats, labels, where, cap);
   }
 }
 

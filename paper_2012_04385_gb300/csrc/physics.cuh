@@ -28,6 +28,7 @@ constexpr int SLOT_U = NV * NCELL;     // doubles per stage buffer
 constexpr int SLOT_N = NV * NINT;      // doubles per u^n buffer
 constexpr int SLOT_F = 6 * NV * NFACE; // doubles per face-flux set
 constexpr int SLOT_SEL = 4 * (34 + 34 + 40);  // uint32 selector decision bits per block (4 z-slabs x 3 directions)
+constexpr int SLOT_SH = 6 * NINT;      // floats per FP32 record set (mixed-precision path)
 
 __host__ __device__ __forceinline__ int sidx(int i, int j, int k) { return ((k + HW) * NS + (j + HW)) * NS + (i + HW); }
 __host__ __device__ __forceinline__ int iidx(int i, int j, int k) { return (k * NB + j) * NB + i; }

@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs_rk(Topo t, Phys p, Pool poo
   const int lin = p.recon;   // reconstruction mode: 0 WENO5, 2 linear, 3 TENO5, 4 WENO-AO(5,3)
   const int flux = p.flux;   // FLUX_ROE, FLUX_LLF or FLUX_HLLC
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
-  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+  const ItemRange IR = item_range(nitems, p.blocked);
+  for (int w = IR.first; w < IR.end; w += IR.step) {
     const int li = w / RHS_NSLAB, z0 = (w % RHS_NSLAB) * RHS_TZ;
     const int node = t.leaves[li];
     const int slot = t.slot[node];
@@ -174,7 +175,7 @@ void launch_rhs_rk_impl(const Topo& t, const Phys& p, const Pool& pool, int cur,
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rhs_rk<R>, RHS_THREADS, smem);
   if (per_sm < 1) per_sm = 1;
-  const int grid = sm_count() * per_sm;
+  const int grid = sm_count() * per_sm * (g_tune.stage_waves < 1 ? 1 : g_tune.stage_waves);
   k_rhs_rk<R><<<grid, RHS_THREADS, smem, st>>>(t, p, pool, cur, stage, dt, rhs_out);
   ++g_kernel_launches;
 }

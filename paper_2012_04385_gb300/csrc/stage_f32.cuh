@@ -32,7 +32,7 @@ constexpr int SF_TZ = 4;
 constexpr int SF_NSLAB = NB / SF_TZ;
 constexpr int SF_THREADS = 256;
 constexpr int SF_REG = NB * NB * (SF_TZ + 6);            // record slots: the z region, 2560 cells
-constexpr int SF_XY = 22 * 22 * SF_TZ;                   // x-y region (corners unused): 1936 slots
+constexpr int SF_XY = 24 * 22 * SF_TZ;                   // x-y region (corners unused): 2112 slots
 constexpr int SF_NFX = 17 * 16 * SF_TZ;                  // x (and y) faces of a slab: 1088
 constexpr int SF_NFZ = NB * NB * (SF_TZ + 1);            // z faces of a slab: 1280
 constexpr int SF_FMAX = 2 * SF_NFX;                      // face-flux slots: the x-y loop, 2176
@@ -563,75 +563,176 @@ __device__ __forceinline__ void face_features_f32(const float* __restrict__ S, i
   features_gv(g, v, e, f);
 }
 
-// Number of region records and faces of direction D for one slab (the
-// per-direction regions of the stage-0 selector variant and of the samples).
-__device__ __forceinline__ int region_cells(int D) { return D == 2 ? SF_REG : 22 * 16 * SF_TZ; }
+// Region layouts of one slab (records in S, x fastest; rows of the x
+// direction hold 24 slots, x = -4 .. 19, so that every run of four cells
+// starting at a multiple of 4 is one 16-byte chunk in shared memory):
+//   x region (MODE 1, D = 0): slot (kz * 16 + y) * 24 + x + 4, y in [0, 16);
+//   y region (MODE 1, D = 1): slot (kz * 22 + y + 3) * 16 + x, y in [-3, 19);
+//   z region (D = 2):         slot ((z - z0 + 3) * 16 + y) * 16 + x, z in [z0-3, z0+7);
+//   x-y region (MODES 0, 2, 3): slot (kz * 22 + y + 3) * 24 + x + 4, x, y in
+//   [-4, 20) x [-3, 19) except the corners (outside the block in both).
+__device__ __forceinline__ int region_cells(int D) { return D == 2 ? SF_REG : (D == 0 ? 24 * 16 * SF_TZ : 22 * 16 * SF_TZ); }
 __device__ __forceinline__ int region_faces(int D) { return D == 2 ? SF_NFZ : SF_NFX; }
 __device__ __forceinline__ int region_stride(int D) { return sel3i(D, 1, 16, 256); }
+
+// FP32 primitive record (rho, vx, vy, vz, p, E) of FP64 conserved values.
+__device__ __forceinline__ void make_record(double r64, double mx64, double my64, double mz64, double E64, float g,
+                                            float B, float gm1, float rec[6]) {
+  const float r = d2f_fast(r64), mx = d2f_fast(mx64), my = d2f_fast(my64);
+  const float mz = d2f_fast(mz64), E = d2f_fast(E64);
+  const float ir = frcp(r);
+  const float vx = mx * ir, vy = my * ir, vz = mz * ir;
+  const float q2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+  rec[0] = r;
+  rec[1] = vx;
+  rec[2] = vy;
+  rec[3] = vz;
+  rec[4] = fmaf(gm1, fmaf(-0.5f * r, q2, E), -g * B);
+  rec[5] = E;
+}
 
 // One FP32 primitive record from the FP64 conserved state at s.
 __device__ __forceinline__ void put_record(const double* __restrict__ src, int s, float* __restrict__ S, int idx,
                                            float g, float B, float gm1) {
-  const float r = d2f_fast(src[s]), mx = d2f_fast(src[NCELL + s]), my = d2f_fast(src[2 * NCELL + s]);
-  const float mz = d2f_fast(src[3 * NCELL + s]), E = d2f_fast(src[4 * NCELL + s]);
-  const float ir = frcp(r);
-  const float vx = mx * ir, vy = my * ir, vz = mz * ir;
-  const float q2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
-  S[idx] = r;
-  S[SF_REG + idx] = vx;
-  S[2 * SF_REG + idx] = vy;
-  S[3 * SF_REG + idx] = vz;
-  S[4 * SF_REG + idx] = fmaf(gm1, fmaf(-0.5f * r, q2, E), -g * B);
-  S[5 * SF_REG + idx] = E;
+  float rec[6];
+  make_record(src[s], src[NCELL + s], src[2 * NCELL + s], src[3 * NCELL + s], src[4 * NCELL + s], g, B, gm1, rec);
+#pragma unroll
+  for (int f = 0; f < SF_NREC; ++f) S[f * SF_REG + idx] = rec[f];
 }
 
-// Stencil region of direction D for the slab at z0 -> records in S.  Cells
-// beyond the block along D come from the same-level face neighbour's internal
-// cells when it exists (ulo/uhi, else null: the block's own halo, filled by
-// prediction or the boundary condition).
-__device__ __forceinline__ void load_region_f32(int D, const double* __restrict__ u, float* __restrict__ S, int z0,
-                                                float g, float B, float gm1, const double* __restrict__ ulo = nullptr,
-                                                const double* __restrict__ uhi = nullptr) {
-  const int n = region_cells(D);
-  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    int x, y, z;
-    if (D == 0) { x = idx % 22 - 3; y = (idx / 22) % 16; z = z0 + idx / 352; }
-    else if (D == 1) { x = idx % 16; y = (idx / 16) % 22 - 3; z = z0 + idx / 352; }
-    else { x = idx % 16; y = (idx / 16) % 16; z = z0 - 3 + idx / 256; }
-    const int a = sel3i(D, x, y, z);
-    const double* src = u;
-    int s = sidx(x, y, z);
-    if (a < 0 && ulo) {
-      src = ulo;
-      s += sel3i(D, NB, NB * NS, NB * NS * NS);
-    } else if (a >= NB && uhi) {
-      src = uhi;
-      s -= sel3i(D, NB, NB * NS, NB * NS * NS);
+// 16-byte asynchronous copy from global to shared memory (L2 only); both
+// addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Sources of a slab's region: the block's FP64 stage buffer (stored cells,
+// for its predicted and boundary halo regions) and the FP32 records of the
+// internal cells of the block and of its same-level face neighbours (x-, x+,
+// y-, y+, z-, z+; null where there is none, and then the block's own halo
+// is read).  sh is null when the context keeps no records: everything is
+// then converted from the block's own stored cells.
+struct RegionSrc {
+  const double* u;
+  const float* sh;
+  const float* nsh[6];
+};
+
+// Source of the chunk of four cells along x from x0 at (y, z) in block
+// coordinates (x0 a multiple of 4, at most one coordinate outside the block):
+// the FP32 records of the block or of the same-level face neighbour on that
+// side, or null (the block's own stored halo, converted from FP64).
+__device__ __forceinline__ const float* chunk_src(const RegionSrc& R, int x0, int y, int z) {
+  if (!R.sh) return nullptr;
+  int side = -1;
+  if (x0 < 0) side = 0;
+  else if (x0 >= NB) side = 1;
+  else if (y < 0) side = 2;
+  else if (y >= NB) side = 3;
+  else if (z < 0) side = 4;
+  else if (z >= NB) side = 5;
+  if (side < 0) return R.sh + (z * NB + y) * NB + x0;
+  // (selects, not an indexed load: R stays in registers)
+  const float* n = (side == 0) ? R.nsh[0]
+                 : (side == 1) ? R.nsh[1]
+                 : (side == 2) ? R.nsh[2]
+                 : (side == 3) ? R.nsh[3]
+                 : (side == 4) ? R.nsh[4] : R.nsh[5];
+  if (!n) return nullptr;
+  const int d = (side & 1) ? -NB : NB;
+  if (side < 2) x0 += d;
+  else if (side < 4) y += d;
+  else z += d;
+  return n + (z * NB + y) * NB + x0;
+}
+
+// The chunk at (x0, y, z) and the same chunk on the next nk - 1 planes (z + k,
+// same source block) -> slots slot + k * slot_step of S: one 16-byte
+// asynchronous copy per field and plane, or (own halo) four records
+// converted from FP64.
+__device__ __forceinline__ void chunk_planes(const RegionSrc& R, int x0, int y, int z, int nk, float* __restrict__ S,
+                                             int slot, int slot_step, float g, float B, float gm1) {
+  const float* src = chunk_src(R, x0, y, z);
+  for (int k = 0; k < nk; ++k) {
+    if (src) {
+#pragma unroll
+      for (int f = 0; f < SF_NREC; ++f)
+        cp_async16(S + f * SF_REG + slot + k * slot_step, src + f * NINT + k * NB * NB);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) put_record(R.u, sidx(x0 + c, y, z + k), S, slot + k * slot_step + c, g, B, gm1);
     }
-    put_record(src, s, S, idx, g, B, gm1);
   }
 }
 
-// The x-y region of the slab at z0: slot ((kz * 22) + y + 3) * 22 + x + 3 for
-// x, y in [-3, 19) except the corners (outside the block in both x and y).
-__device__ __forceinline__ int xy_slot(int x, int y, int kz) { return (kz * 22 + y + 3) * 22 + x + 3; }
-
-__device__ __forceinline__ void load_xy_f32(const double* __restrict__ u, float* __restrict__ S, int z0, float g,
-                                            float B, float gm1, const double* __restrict__ uxl,
-                                            const double* __restrict__ uxh, const double* __restrict__ uyl,
-                                            const double* __restrict__ uyh) {
-  for (int idx = threadIdx.x; idx < SF_XY; idx += blockDim.x) {
-    const int x = idx % 22 - 3, y = (idx / 22) % 22 - 3, z = z0 + idx / 484;
-    const bool ox = x < 0 || x >= NB, oy = y < 0 || y >= NB;
-    if (ox && oy) continue;
-    const double* src = u;
-    int s = sidx(x, y, z);
-    if (x < 0 && uxl) { src = uxl; s += NB; }
-    else if (x >= NB && uxh) { src = uxh; s -= NB; }
-    else if (y < 0 && uyl) { src = uyl; s += NB * NS; }
-    else if (y >= NB && uyh) { src = uyh; s -= NB * NS; }
-    put_record(src, s, S, idx, g, B, gm1);
+// Stencil region of direction D for the slab at z0 -> records in S (layouts
+// above).  Each thread owns one chunk position of a plane and copies it on
+// a fixed set of planes; every copy has landed when the caller's next
+// barrier is passed.
+__device__ __forceinline__ void load_region_f32(int D, const RegionSrc& R, float* __restrict__ S, int z0, float g,
+                                                float B, float gm1) {
+  const int t = threadIdx.x;
+  if (D == 0) {                 // 96 chunk positions per plane (16 rows of 6), two planes per thread
+    if (t < 192) {
+      const int c = t % 96, kz = t / 96, y = c / 6, q = c % 6;
+      chunk_planes(R, 4 * q - 4, y, z0 + kz, 1, S, (kz * 16 + y) * 24 + 4 * q, 0, g, B, gm1);
+      chunk_planes(R, 4 * q - 4, y, z0 + kz + 2, 1, S, ((kz + 2) * 16 + y) * 24 + 4 * q, 0, g, B, gm1);
+    }
+  } else if (D == 1) {          // 88 chunk positions per plane (22 rows of 4), two planes per thread
+    if (t < 176) {
+      const int c = t % 88, kz = t / 88, r = c / 4, q = c % 4;
+      chunk_planes(R, 4 * q, r - 3, z0 + kz, 1, S, (kz * 22 + r) * 16 + 4 * q, 0, g, B, gm1);
+      chunk_planes(R, 4 * q, r - 3, z0 + kz + 2, 1, S, ((kz + 2) * 22 + r) * 16 + 4 * q, 0, g, B, gm1);
+    }
+  } else {                      // 64 chunk positions per plane, planes t/64, +4, +8 (ten planes)
+    const int c = t % 64, lane = t / 64, y = c / 4, q = c % 4;
+    for (int zz = lane; zz < SF_TZ + 6; zz += 4)
+      chunk_planes(R, 4 * q, y, z0 - 3 + zz, 1, S, (zz * 16 + y) * 16 + 4 * q, 0, g, B, gm1);
   }
+  cp_async_wait_all();
+}
+
+// The x-y region of the slab at z0 (rows of 24 slots, the corners skipped).
+__device__ __forceinline__ int xy_slot(int x, int y, int kz) { return (kz * 22 + y + 3) * 24 + x + 4; }
+
+// 120 chunk positions per plane (16 rows of 6 chunks, 6 rows of 4); threads
+// 0..239 own one position on two of the four planes.
+__device__ __forceinline__ void load_xy_f32(const RegionSrc& R, float* __restrict__ S, int z0, float g, float B,
+                                            float gm1) {
+  const int t = threadIdx.x;
+  if (t < 240) {
+    const int c = t % 120, kz = 2 * (t / 120);
+    int x0, y;
+    if (c < 96) {               // rows y in [0, 16): x = -4 .. 19
+      y = c / 6;
+      x0 = 4 * (c % 6) - 4;
+    } else {                    // rows y in [-3, 0) and [16, 19): x = 0 .. 15
+      const int r = (c - 96) / 4;
+      y = (r < 3) ? r - 3 : r + 13;
+      x0 = 4 * ((c - 96) % 4);
+    }
+    chunk_planes(R, x0, y, z0 + kz, 2, S, xy_slot(x0, y, kz), xy_slot(0, 0, 1) - xy_slot(0, 0, 0), g, B, gm1);
+  }
+  cp_async_wait_all();
+}
+
+// Sources of the block at `slot` with its same-level face neighbours (stage
+// buffer `cur`).
+__device__ __forceinline__ RegionSrc region_src(const Topo& t, const Pool& pool, int cur, int node, int slot) {
+  RegionSrc R;
+  R.u = pool.buf[cur] + (size_t)slot * SLOT_U;
+  R.sh = pool.sh[cur] ? pool.sh[cur] + (size_t)slot * SLOT_SH : nullptr;
+  const int rn[6] = {12, 14, 10, 16, 4, 22};
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int nb = R.sh ? t.nbr[(size_t)node * 27 + rn[q]] : -1;
+    R.nsh[q] = (nb >= 0) ? pool.sh[cur] + (size_t)t.slot[nb] * SLOT_SH : nullptr;
+  }
+  return R;
 }
 
 // Face f of direction D in the slab (per-direction regions): first stencil
@@ -641,7 +742,7 @@ __device__ __forceinline__ void face_of(int D, int f, int z0, int& fa, int& c0, 
   if (D == 0) {
     fa = f % 17;
     const int r = f / 17;                 // row = kz * 16 + j
-    c0 = r * 22 + fa;                     // cell x = fa - 3 at record index fa
+    c0 = r * 24 + fa + 1;                 // cell x = fa - 3 at record index fa + 1
     ta = r % 16;
     tb = z0 + r / 16;
   } else if (D == 1) {
@@ -734,19 +835,13 @@ __device__ __forceinline__ void add_diff(int D, const float* __restrict__ Fs, in
 // Per-direction sweep (the stage-0 selector variant, MODE 1): region of D,
 // faces with WENO5 fluxes and the selector's decisions, flux differences.
 template <int MODE>
-__device__ __forceinline__ void sweep_f32(int D, const double* __restrict__ u, double* __restrict__ fb,
-                                          float* __restrict__ S, float* __restrict__ Fs, int z0, float g, float B,
-                                          float gm1, float (&acc)[SF_TZ][NV], const LearnedCtx& L, const Topo& t,
-                                          const double* __restrict__ buf, int node) {
+__device__ __forceinline__ void sweep_f32(int D, const Topo& t, const Pool& pool, int cur, int node, int slot,
+                                          double* __restrict__ fb, float* __restrict__ S, float* __restrict__ Fs,
+                                          int z0, float g, float B, float gm1, float (&acc)[SF_TZ][NV],
+                                          const LearnedCtx& L) {
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
-  {
-    // same-level face neighbours along D read directly
-    const int rlo = sel3i(D, 12, 10, 4), rhi = sel3i(D, 14, 16, 22);
-    const int nlo = t.nbr[(size_t)node * 27 + rlo], nhi = t.nbr[(size_t)node * 27 + rhi];
-    const double* ulo = (nlo >= 0) ? buf + (size_t)t.slot[nlo] * SLOT_U : nullptr;
-    const double* uhi = (nhi >= 0) ? buf + (size_t)t.slot[nhi] * SLOT_U : nullptr;
-    load_region_f32(D, u, S, z0, g, B, gm1, ulo, uhi);
-  }
+  // same-level face neighbours along D read directly (their records)
+  load_region_f32(D, region_src(t, pool, cur, node, slot), S, z0, g, B, gm1);
   __syncthreads();
   const int nf = region_faces(D);
   const int st = region_stride(D);
@@ -802,20 +897,12 @@ __device__ __forceinline__ void sweep_f32(int D, const double* __restrict__ u, d
 // x and y directions of the slab together (MODES 0, 2, 3): one region, one
 // loop over the 1088 x faces followed by the 1088 y faces.
 template <int MODE>
-__device__ __forceinline__ void sweep_xy(const double* __restrict__ u, double* __restrict__ fb, float* __restrict__ S,
+__device__ __forceinline__ void sweep_xy(const double* __restrict__ u, const Topo& t, const Pool& pool, int cur,
+                                         int node, int slot, double* __restrict__ fb, float* __restrict__ S,
                                          float* __restrict__ Fs, int z0, float g, float B, float gm1,
-                                         float (&acc)[SF_TZ][NV], const LearnedCtx& L, const Topo& t,
-                                         const double* __restrict__ buf, int node) {
+                                         float (&acc)[SF_TZ][NV], const LearnedCtx& L) {
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
-  {
-    const int n0 = t.nbr[(size_t)node * 27 + 12], n1 = t.nbr[(size_t)node * 27 + 14];
-    const int n2 = t.nbr[(size_t)node * 27 + 10], n3 = t.nbr[(size_t)node * 27 + 16];
-    const double* uxl = (n0 >= 0) ? buf + (size_t)t.slot[n0] * SLOT_U : nullptr;
-    const double* uxh = (n1 >= 0) ? buf + (size_t)t.slot[n1] * SLOT_U : nullptr;
-    const double* uyl = (n2 >= 0) ? buf + (size_t)t.slot[n2] * SLOT_U : nullptr;
-    const double* uyh = (n3 >= 0) ? buf + (size_t)t.slot[n3] * SLOT_U : nullptr;
-    load_xy_f32(u, S, z0, g, B, gm1, uxl, uxh, uyl, uyh);
-  }
+  load_xy_f32(region_src(t, pool, cur, node, slot), S, z0, g, B, gm1);
   __syncthreads();
   for (int f = threadIdx.x; f < 2 * SF_NFX; f += blockDim.x) {
     float F[5];
@@ -832,7 +919,7 @@ __device__ __forceinline__ void sweep_xy(const double* __restrict__ u, double* _
       const int fa = r % 17, kz = r / 17;
       const int c0 = xy_slot(i, fa - 3, kz);
       const bool lin = (MODE == 3) && ((L.selw[34 + (fy >> 5)] >> (threadIdx.x & 31)) & 1u);
-      face_flux_f32<MODE, false>(S, c0, 22, rot_of(1), gm1, g, B, lin, F);
+      face_flux_f32<MODE, false>(S, c0, 24, rot_of(1), gm1, g, B, lin, F);
       if (MODE & 32) sub_viscous_f32<1>(u, sidx(i, fa - 1, z0 + kz), L.mu, L.idx, F);
       store_face(1, F, Fs, SF_FMAX, f, fa, i, z0 + kz, fb);
     }
@@ -851,17 +938,12 @@ __device__ __forceinline__ void sweep_xy(const double* __restrict__ u, double* _
 
 // z direction of the slab (MODES 0, 2, 3).
 template <int MODE>
-__device__ __forceinline__ void sweep_z(const double* __restrict__ u, double* __restrict__ fb, float* __restrict__ S,
+__device__ __forceinline__ void sweep_z(const double* __restrict__ u, const Topo& t, const Pool& pool, int cur,
+                                        int node, int slot, double* __restrict__ fb, float* __restrict__ S,
                                         float* __restrict__ Fs, int z0, float g, float B, float gm1,
-                                        float (&acc)[SF_TZ][NV], const LearnedCtx& L, const Topo& t,
-                                        const double* __restrict__ buf, int node) {
+                                        float (&acc)[SF_TZ][NV], const LearnedCtx& L) {
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
-  {
-    const int nlo = t.nbr[(size_t)node * 27 + 4], nhi = t.nbr[(size_t)node * 27 + 22];
-    const double* ulo = (nlo >= 0) ? buf + (size_t)t.slot[nlo] * SLOT_U : nullptr;
-    const double* uhi = (nhi >= 0) ? buf + (size_t)t.slot[nhi] * SLOT_U : nullptr;
-    load_region_f32(2, u, S, z0, g, B, gm1, ulo, uhi);
-  }
+  load_region_f32(2, region_src(t, pool, cur, node, slot), S, z0, g, B, gm1);
   __syncthreads();
   for (int f = threadIdx.x; f < SF_NFZ; f += blockDim.x) {
     const int i = f % 16, j = (f / 16) % 16, fa = f / 256;
@@ -916,7 +998,8 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     L.z0 = L.logit[SF_THREADS - 1];
     __syncthreads();
   }
-  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+  const ItemRange IR = item_range(nitems, p.blocked);
+  for (int w = IR.first; w < IR.end; w += IR.step) {
     const int li = w / SF_NSLAB, z0 = (w % SF_NSLAB) * SF_TZ;
     const int node = t.leaves[li];
     const int slot = t.slot[node];
@@ -944,10 +1027,10 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[kz][v] = 0.f;
 #pragma unroll 1
-      for (int D = 0; D < 3; ++D) sweep_f32<MODE>(D, u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+      for (int D = 0; D < 3; ++D) sweep_f32<MODE>(D, t, pool, cur, node, slot, fb, S, Fs, z0, g, B, gm1, acc, L);
     } else {
-      sweep_xy<MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
-      sweep_z<MODE>(u, fb, S, Fs, z0, g, B, gm1, acc, L, t, src, node);
+      sweep_xy<MODE>(u, t, pool, cur, node, slot, fb, S, Fs, z0, g, B, gm1, acc, L);
+      sweep_z<MODE>(u, t, pool, cur, node, slot, fb, S, Fs, z0, g, B, gm1, acc, L);
     }
     if (MODE == 1) {
       lvl = t.level[node];
@@ -995,6 +1078,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
         } else {
           double* __restrict__ unb = pool.un + (size_t)slot * SLOT_N;
           double* __restrict__ o = dst + (size_t)slot * SLOT_U;
+          double o5[5];
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
             double out;
@@ -1008,6 +1092,15 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
               out = fma(ka, un[c][v], fma(kb, us[c][v], inc));
             }
             o[v * NCELL + s] = out;
+            o5[v] = out;
+          }
+          // the FP32 records of the new state, read by the next stage's regions
+          if (pool.sh[cur ^ 1]) {
+            float rec[6];
+            make_record(o5[0], o5[1], o5[2], o5[3], o5[4], g, B, gm1, rec);
+            float* __restrict__ shw = pool.sh[cur ^ 1] + (size_t)slot * SLOT_SH;
+#pragma unroll
+            for (int f = 0; f < SF_NREC; ++f) shw[f * NINT + ii] = rec[f];
           }
         }
       }
@@ -1020,13 +1113,14 @@ template <int MODE>
 static void launch_stage_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
                              double* rhs_out, cudaStream_t st) {
   const size_t smem = (MODE == 1) ? SF_SMEM_LEARNED : SF_SMEM;
-  static int grid = 0;
-  if (grid == 0) {
+  static int resident = 0;
+  if (resident == 0) {
     cudaFuncSetAttribute(k_stage_f32<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_f32<MODE>, SF_THREADS, smem);
-    grid = sm_count() * (per_sm < 1 ? 1 : per_sm);
+    resident = sm_count() * (per_sm < 1 ? 1 : per_sm);
   }
+  const int grid = resident * (g_tune.stage_waves < 1 ? 1 : g_tune.stage_waves);
   k_stage_f32<MODE><<<grid, SF_THREADS, smem, st>>>(t, p, pool, cur, stage, dt, rhs_out);
   ++g_kernel_launches;
 }

@@ -77,6 +77,7 @@ def lib():
                 "mrb_set_state": (ci, [vp, vp, i64, vp]),
                 "mrb_set_cons": (ci, [vp, vp, i64, vp]),
                 "mrb_get_state": (ci, [vp, vp, i64, vp, i32]),
+                "mrb_get_records": (ci, [vp, vp, i64, vp, i32]),
                 "mrb_fill_halos": (ci, [vp]),
                 "mrb_compute_rhs": (ci, [vp, vp]),
                 "mrb_rk_stage": (ci, [vp, i32, vp]),
@@ -85,10 +86,15 @@ def lib():
                 "mrb_mr_predict_and_tag": (ci, [vp, i32, vp, vp]),
                 "mrb_remesh": (ci, [vp, vp, vp]),
                 "mrb_step": (ci, [vp, i32, vp]),
+                "mrb_refine_level": (ci, [vp, i32, vp]),
+                "mrb_refine_keys": (ci, [vp, vp, i64, vp]),
                 "mrb_sums": (ci, [vp, vp]),
                 "mrb_flux_census": (ci, [vp, vp]),
                 "mrb_neighbors": (ci, [vp, vp, i64, vp]),
                 "mrb_profile": (ci, [vp, i32]),
+                "mrb_get_tune": (ci, [vp, vp]),
+                "mrb_set_tune": (ci, [vp, vp]),
+                "mrb_autotune": (ci, [vp, i32, vp]),
                 "mrb_profile_read": (ci, [vp, vp, vp, vp]),
                 "mrb_block_sums_noalloc": (ci, [vp, i64, vp, ctypes.c_double, vp, vp]),
                 "mrb_measure_peaks": (ci, [vp, i32]),
@@ -308,6 +314,18 @@ class Context:
         self._rc(lib().mrb_get_state(self._h, keys.ctypes.data, len(keys), out.data_ptr(), int(with_halo)))
         return out
 
+    def get_records(self, keys=None, fresh=False):
+        """FP32 primitive records [n][6][16][16][16] of the listed blocks'
+        internal cells (mixed-precision contexts): as kept, or converted
+        afresh from the FP64 state."""
+        torch = self.torch
+        if keys is None:
+            keys = self.keys()
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        out = torch.empty((len(keys), 6, NB, NB, NB), dtype=torch.float32, device=self.pool.device)
+        self._rc(lib().mrb_get_records(self._h, keys.ctypes.data, len(keys), out.data_ptr(), int(fresh)))
+        return out
+
     # ---- steps (same names as the C ABI)
     def fill_halos(self):
         self._rc(lib().mrb_fill_halos(self._h))
@@ -351,6 +369,17 @@ class Context:
         self._rc(lib().mrb_remesh(self._h, tags.data_ptr() if tags.numel() else None, ctypes.byref(n)))
         return int(n.value)
 
+    def refine_level(self, level) -> int:
+        n = ctypes.c_int64()
+        self._rc(lib().mrb_refine_level(self._h, int(level), ctypes.byref(n)))
+        return int(n.value)
+
+    def refine_keys(self, keys) -> int:
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        n = ctypes.c_int64()
+        self._rc(lib().mrb_refine_keys(self._h, keys.ctypes.data, len(keys), ctypes.byref(n)))
+        return int(n.value)
+
     def step(self, nsteps=1, dt_hist=None):
         self._rc(lib().mrb_step(self._h, int(nsteps), dt_hist.data_ptr() if dt_hist is not None else None))
 
@@ -373,6 +402,25 @@ class Context:
         out = np.zeros((len(keys), 27), dtype=np.uint64)
         self._rc(lib().mrb_neighbors(self._h, keys.ctypes.data, len(keys), out.ctypes.data))
         return out
+
+    def get_tune(self):
+        q = np.zeros(5, dtype=np.int32)
+        self._rc(lib().mrb_get_tune(self._h, q.ctypes.data))
+        return [int(x) for x in q]
+
+    def set_tune(self, params):
+        q = np.ascontiguousarray(params, dtype=np.int32)
+        assert q.shape == (5,)
+        self._rc(lib().mrb_set_tune(self._h, q.ctypes.data))
+
+    def autotune(self, reps=3):
+        """Scheduling-only autotuner (mrb_autotune): returns the chosen launch
+        shapes and the default / tuned times (ms) of the stage kernel(s), one
+        halo fill and one averaging pass."""
+        t = np.zeros(6)
+        self._rc(lib().mrb_autotune(self._h, int(reps), t.ctypes.data))
+        return {"params": self.get_tune(), "stage_ms": (t[0], t[1]), "fill_ms": (t[2], t[3]),
+                "project_ms": (t[4], t[5])}
 
     def profile(self, enable=True):
         self._rc(lib().mrb_profile(self._h, int(enable)))
@@ -430,10 +478,7 @@ def init_tree(ctx, ic, allow_coarsen=True, with_keys=False):
     keys, geo = ctx.list_blocks(0)
     ctx.set_state(keys, ic_k(cfg, geo, keys))
     for m in range(1, lmax + 1):
-        ctx.fill_halos()
-        _, geo_l = ctx.list_blocks()
-        tags = np.where(geo_l[:, 0] == m - 1, TAG_REFINE, TAG_KEEP).astype(np.int8)
-        ctx.remesh(tags)
+        ctx.refine_level(m - 1)
         keys, geo = ctx.list_blocks(m)
         ctx.set_state(keys, ic_k(cfg, geo, keys))
         if m > 1 and allow_coarsen:
@@ -458,11 +503,10 @@ def restore_tree(ctx, node_keys):
 
     while True:
         leaves = [int(k) for k in ctx.keys()]
-        tags = np.array([TAG_REFINE if child0(k) in want else TAG_KEEP for k in leaves], np.int8)
-        if not (tags == TAG_REFINE).any():
+        sel = np.array([k for k in leaves if child0(k) in want], dtype=np.uint64)
+        if len(sel) == 0:
             break
-        ctx.fill_halos()
-        ctx.remesh(tags)
+        ctx.refine_keys(sel)
     have = set(int(k) for k in ctx.keys(leaves_only=False))
     if have != want:
         raise MrbError(MRB_EINVAL, "saved ids do not form a tree reachable from level 0")

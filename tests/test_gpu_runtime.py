@@ -134,3 +134,86 @@ def test_nonphysical_state_is_reported_and_cleared():
     g.sync()
     assert g.status() == mrb.MRB_OK
     assert np.isfinite(g.get_state(k).cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("recon", [I.RECON_WENO, I.RECON_LEARNED])
+def test_fp32_records_follow_the_fp64_state(recon):
+    """The mixed-precision path keeps FP32 primitive records of every node's
+    internal cells (leaves and internal nodes, both stage buffers in turn) and
+    its stage kernel reads them instead of converting the FP64 state.  After
+    initialisation, after single stages with resolution jumps (the leaves
+    after the stage update and jump correction, every node after the
+    averaging) and after full steps with remeshing, the kept records equal a
+    fresh conversion of the FP64 state bit for bit."""
+    cfg = I.shock_bubble_config(lmax=2, precision=I.FP32_ACC64, recon=recon)
+    params = None
+    if recon == I.RECON_LEARNED:
+        from paper_2012_04385_gb300 import learned
+        params = torch.from_numpy(learned.init_params(3)).cuda()
+        cfg.mlp_tau = 0.0
+    g = mrb.Context(cfg, 600, mlp_params=params)
+    mrb.init_tree(g, I.ic_shock_bubble)
+
+    def check(what, leaves_only=False):
+        k = g.keys(leaves_only=leaves_only)
+        kept = g.get_records(k).cpu().numpy()
+        fresh = g.get_records(k, fresh=True).cpu().numpy()
+        bad = np.argwhere(kept.view(np.uint32) != fresh.view(np.uint32))
+        assert len(bad) == 0, (what, len(bad), bad[:5])
+
+    check("initial tree")
+    dt = g.cfl_dt()
+    for s in range(3):
+        g.fill_halos()
+        g.rk_stage(s, dt)
+        check(f"stage {s}", leaves_only=True)     # internal nodes are averaged next
+        g.mr_project()
+        check(f"stage {s} averaged")
+    g.step(3)
+    assert g.status() == mrb.MRB_OK
+    check("after 3 steps")
+    g.close()
+
+
+@pytest.mark.parametrize("precision", [I.FP64, I.FP32_ACC64])
+def test_launch_shapes_do_not_change_results(precision):
+    """The autotuner's knobs only schedule work: stage waves, work-item order,
+    fill and averaging grid shapes give bit-identical trees and states after
+    two MR steps (remeshing included); mrb_autotune leaves the state as it
+    found it and the run continues bit for bit like an untuned one."""
+    shapes = [[1, 0, 8, 4, 8], [2, 1, 4, 2, 4], [4, 0, 16, 8, 16], [1, 1, 1, 1, 1]]
+    ref = None
+    for q in shapes:
+        cfg = I.shock_bubble_config(lmax=2, precision=precision)
+        g = mrb.Context(cfg, 600)
+        mrb.init_tree(g, I.ic_shock_bubble)
+        g.set_tune(q)
+        assert g.get_tune() == q
+        g.step(2)
+        assert g.status() == mrb.MRB_OK
+        k = g.keys()
+        st = g.get_state(k).cpu().numpy()
+        if ref is None:
+            ref = (k, st)
+        else:
+            assert np.array_equal(k, ref[0]), q
+            assert np.array_equal(st.view(np.uint64), ref[1].view(np.uint64)), q
+        g.close()
+    with pytest.raises(mrb.MrbError):
+        g = mrb.Context(I.shock_bubble_config(lmax=2, precision=precision), 600)
+        g.set_tune([0, 0, 8, 4, 8])
+    g = mrb.Context(I.shock_bubble_config(lmax=2, precision=precision), 600)
+    mrb.init_tree(g, I.ic_shock_bubble)
+    k0 = g.keys(leaves_only=False)
+    s0 = g.get_state(k0).cpu().numpy()
+    rep = g.autotune(reps=2)
+    print(rep)
+    assert np.array_equal(g.get_state(k0).cpu().numpy().view(np.uint64), s0.view(np.uint64))
+    q = rep["params"]
+    assert 1 <= q[0] <= 8 and q[1] in (0, 1) and all(1 <= x <= 32 for x in q[2:])
+    assert rep["stage_ms"][1] <= rep["stage_ms"][0]
+    g.step(2)
+    k = g.keys()
+    assert np.array_equal(k, ref[0])
+    assert np.array_equal(g.get_state(k).cpu().numpy().view(np.uint64), ref[1].view(np.uint64))
+    g.close()
