@@ -136,3 +136,83 @@ def test_reference_arm_under_torchrun_prints_one_line():
     assert len(lines) == 1, r.stdout
     res = json.loads(lines[0])
     assert res["impl"] == "reference" and res["n_gpus"] == 2 and res["value"] > 0
+
+
+# ------------------------------------------------------------------ ensemble sharding
+def _oracle_ensemble_sums(cfg, ic, steps):
+    """Per-instance conserved totals after `steps` oracle steps of a batched
+    run built by Alg. (Initialization) (ic(cfg, geo, keys))."""
+    import numpy as np
+
+    import oracle
+    o = oracle.Oracle(cfg, n_threads=2)
+    lmax = max(cfg.lmax_of(i) for i in range(cfg.n_instances))
+    o.set_state(o.keys(), ic(cfg, o.geometry(), o.keys()))
+    for m in range(1, lmax + 1):
+        o.fill_halos()
+        geo = o.geometry()
+        o.remesh((geo[:, 0] == m - 1).astype(np.int8))
+        o.set_state(o.keys(level=m), ic(cfg, o.geometry(level=m), o.keys(level=m)))
+        if m > 1:
+            o.fill_halos()
+            t, _ = o.predict_and_tag(allow_refine=False)
+            o.remesh(t)
+    o.project()
+    o.step(steps)
+    return o.sums()
+
+
+def _shard_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    from paper_2012_04385_gb300 import inputs as I
+    from paper_2012_04385_gb300 import shard
+    dist.init_process_group("gloo")
+    cfg = I.ensemble_config(n=5, lmax=(1, 2, 1, 2, 1))
+    mine = shard.instance_shards(cfg, world)[rank]
+    sums = _oracle_ensemble_sums(shard.shard_config(cfg, mine), shard.shard_ic(I.ic_ensemble, mine), 2)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, (mine, sums.tolist()))
+    q.put((rank, gathered))
+    dist.destroy_process_group()
+
+
+def test_ensemble_sharded_by_instance_over_two_ranks():
+    """The batched ensemble splits by instance with no exchange: two gloo
+    ranks each run their instances (the oracle standing in for each rank's
+    GPU), and the gathered per-instance conserved totals after two MR steps
+    equal those of one batched run of the whole ensemble bit for bit.  The
+    partition covers every instance once and balances the effective cells."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    from paper_2012_04385_gb300 import inputs as I
+    from paper_2012_04385_gb300 import shard
+    cfg = I.ensemble_config(n=5, lmax=(1, 2, 1, 2, 1))
+    parts = shard.instance_shards(cfg, 2)
+    assert sorted(sum(parts, [])) == list(range(5))
+    cost = [sum(shard.instance_cost(cfg, i) for i in p) for p in parts]
+    assert max(cost) <= 1.25 * min(cost)
+    assert shard.instance_shards(cfg, 1) == [list(range(5))]
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = {}
+    for _ in range(world):
+        rank, gathered = q.get(timeout=600)
+        out[rank] = gathered
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out[0] == out[1]
+    got = np.zeros((5, 5))
+    for mine, sums in out[0]:
+        got[mine] = np.array(sums)
+    ref = _oracle_ensemble_sums(cfg, I.ic_ensemble, 2)
+    assert np.array_equal(got, ref)
