@@ -69,6 +69,7 @@ class OrcConfig(ctypes.Structure):
         ("gravity", ctypes.c_double * 3),
         ("eps", ctypes.c_double),
         ("mu", ctypes.c_double),
+        ("lts", ctypes.c_int32),
     ]
 
 
@@ -117,6 +118,7 @@ def lib():
                 "orc_average_block": (None, [vp, vp]),
                 "orc_threads": (i32, []),
                 "orc_count_row_flops": (None, [vp, i32, dbl, dbl, i32, i32, vp]),
+                "orc_lts_macro_step": (None, [vp, vp]),
                 "orc_count_recon_flops": (None, [i32, vp]),
             }
             for name, (res, args) in sig.items():
@@ -149,6 +151,7 @@ def make_config(cfg, n_threads: int = 0) -> OrcConfig:
     c.cfl = float(cfg.cfl)
     c.eps = float(cfg.eps)
     c.mu = float(getattr(cfg, "mu", 0.0))
+    c.lts = int(getattr(cfg, "lts", 0))
     return c
 
 
@@ -261,6 +264,13 @@ class Oracle:
         dts = np.zeros((nsteps, self.cfg.n_instances))
         lib().orc_step(self._h, nsteps, _p(dts))
         return dts
+
+    def lts_macro_step(self) -> np.ndarray:
+        """One local-time-stepping macro step (no MR analysis); returns the
+        finest level's time step per instance."""
+        dt = np.zeros(self.cfg.n_instances)
+        lib().orc_lts_macro_step(self._h, _p(dt))
+        return dt
 
     def neighbor(self, key: int, sx: int, sy: int, sz: int):
         out = np.zeros(1, dtype=np.uint64)

@@ -92,6 +92,7 @@ struct orc_config {
   double gravity[3];
   double eps;             // threshold at l_max (Eq. UserEpsilon already applied)
   double mu;              // dynamic viscosity of the Navier-Stokes terms; 0 = Euler
+  int32_t lts;            // 1 = local time stepping per level (all instances with the same l_max)
 };
 
 }  // extern "C"
@@ -107,11 +108,13 @@ struct Node {
   std::vector<double> un;     // [5][16^3] u^n of the current RK step
   std::vector<double> L;      // [5][16^3] right-hand side
   std::vector<double> face;   // [6][5][16][16] boundary-face fluxes
+  std::vector<double> fmac;   // [6][5][16][16] boundary-face fluxes integrated over a macro time step (LTS)
   void alloc() {
     u.assign((size_t)NV * NCELL, 0.0);
     un.assign((size_t)NV * NINT, 0.0);
     L.assign((size_t)NV * NINT, 0.0);
     face.assign((size_t)6 * NV * NFACE, 0.0);
+    fmac.assign((size_t)6 * NV * NFACE, 0.0);
   }
 };
 
@@ -1111,8 +1114,7 @@ inline int rk_stages(const Ctx& C) { return C.c.rk_stages == 2 ? 2 : 3; }
 inline double rk_a(const Ctx& C, int s) { return rk_stages(C) == 2 ? RK_A2[s] : RK_A3[s]; }
 inline double rk_b(const Ctx& C, int s) { return rk_stages(C) == 2 ? RK_B2[s] : RK_B3[s]; }
 
-void rk_update(Ctx& C, int s, const double* dt) {
-  std::vector<Node*> v = nodes_at(C, -1, true);
+void rk_update_nodes(Ctx& C, const std::vector<Node*>& v, int s, const double* dt) {
 #pragma omp parallel for schedule(dynamic)
   for (long t = 0; t < (long)v.size(); ++t) {
     Node& n = *v[t];
@@ -1130,9 +1132,32 @@ void rk_update(Ctx& C, int s, const double* dt) {
   }
 }
 
+void rk_update(Ctx& C, int s, const double* dt) { rk_update_nodes(C, nodes_at(C, -1, true), s, dt); }
+
 // Averaging, Eq. (Averaging): a parent cell is the mean of its eight children,
 // summed pairwise in Morton order ((c0+c1)+(c2+c3))+((c4+c5)+(c6+c7)), levels
 // from fine to coarse.
+void average_children(Ctx& C, Node& P) {
+  uint64_t inst = P.key >> 56;
+  const Node* ch[8];
+  for (int c = 0; c < 8; ++c) ch[c] = find(C, (((P.key & MASK56) << 3) | (uint64_t)c) | (inst << 56));
+  for (int K = 0; K < NB; ++K)
+    for (int J = 0; J < NB; ++J)
+      for (int I = 0; I < NB; ++I) {
+        int o = (I / 8) | ((J / 8) << 1) | ((K / 8) << 2);
+        const Node* c = ch[o];
+        int fi = 2 * (I - 8 * (I / 8)), fj = 2 * (J - 8 * (J / 8)), fk = 2 * (K - 8 * (K / 8));
+        for (int v2 = 0; v2 < NV; ++v2) {
+          const double* u = &c->u[(size_t)v2 * NCELL];
+          double c0 = u[sidx(fi, fj, fk)], c1 = u[sidx(fi + 1, fj, fk)];
+          double c2 = u[sidx(fi, fj + 1, fk)], c3 = u[sidx(fi + 1, fj + 1, fk)];
+          double c4 = u[sidx(fi, fj, fk + 1)], c5 = u[sidx(fi + 1, fj, fk + 1)];
+          double c6 = u[sidx(fi, fj + 1, fk + 1)], c7 = u[sidx(fi + 1, fj + 1, fk + 1)];
+          P.u[(size_t)v2 * NCELL + sidx(I, J, K)] = 0.125 * (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7)));
+        }
+      }
+}
+
 void project(Ctx& C) {
   int lm = max_level(C);
   for (int l = lm - 1; l >= 0; --l) {
@@ -1141,24 +1166,7 @@ void project(Ctx& C) {
     for (long t = 0; t < (long)v.size(); ++t) {
       Node& P = *v[t];
       if (P.leaf) continue;
-      uint64_t inst = P.key >> 56;
-      const Node* ch[8];
-      for (int c = 0; c < 8; ++c) ch[c] = find(C, (((P.key & MASK56) << 3) | (uint64_t)c) | (inst << 56));
-      for (int K = 0; K < NB; ++K)
-        for (int J = 0; J < NB; ++J)
-          for (int I = 0; I < NB; ++I) {
-            int o = (I / 8) | ((J / 8) << 1) | ((K / 8) << 2);
-            const Node* c = ch[o];
-            int fi = 2 * (I - 8 * (I / 8)), fj = 2 * (J - 8 * (J / 8)), fk = 2 * (K - 8 * (K / 8));
-            for (int v2 = 0; v2 < NV; ++v2) {
-              const double* u = &c->u[(size_t)v2 * NCELL];
-              double c0 = u[sidx(fi, fj, fk)], c1 = u[sidx(fi + 1, fj, fk)];
-              double c2 = u[sidx(fi, fj + 1, fk)], c3 = u[sidx(fi + 1, fj + 1, fk)];
-              double c4 = u[sidx(fi, fj, fk + 1)], c5 = u[sidx(fi + 1, fj, fk + 1)];
-              double c6 = u[sidx(fi, fj + 1, fk + 1)], c7 = u[sidx(fi + 1, fj + 1, fk + 1)];
-              P.u[(size_t)v2 * NCELL + sidx(I, J, K)] = 0.125 * (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7)));
-            }
-          }
+      average_children(C, P);
     }
   }
 }
@@ -1399,6 +1407,202 @@ void stage(Ctx& C, int s, const double* dt) {
   average_faces(C);
   rk_update(C, s, dt);
   jump_correct(C, false, rk_b(C, s), dt);
+  project(C);
+}
+
+// ------------------------------------------------------------ local time stepping
+// Reading of Eq. (LtsTimestep) with Alg. (ComputeLoop) and Alg. (Integration)
+// (the paper gives their order but not the data each step acts on; the choices
+// below are this reading's):
+//  * a macro time step starts with Delta t_L from Eq. (Cfl) (L = l_max, the
+//    same for every instance), fixed for the macro step; level l advances in
+//    steps of Delta t_l = 2^(L - l) Delta t_L (Eq. LtsTimestep);
+//  * micro steps r = 0 .. 2^L - 1: every level whose step starts at r (r a
+//    multiple of 2^(L - l)) and that holds leaves takes one full Runge-Kutta
+//    step, coarse levels first;
+//  * a level's step advances all its nodes, leaves and internal nodes alike
+//    (an internal node carries that level's approximation of the finer region
+//    it covers, which its neighbours' stencils and its children's predicted
+//    halos read); each stage fills the halos of all nodes (levels coarse to
+//    fine: a region without a same-level neighbour is predicted from the
+//    parent), with the nodes of coarser levels -- whose current step spans the
+//    stage's time -- interpolated linearly in time between the start (u^n) and
+//    the end of that step; it then computes the right-hand side of the
+//    level's nodes, updates them with Delta t_l and adds each leaf's
+//    boundary-face fluxes, weighted by the stage's share of the step
+//    (TVD-RK3: 1/6, 1/6, 2/3; TVD-RK2: 1/2, 1/2) times Delta t_l, to its
+//    integrated fluxes;
+//  * after a micro step every level whose step ends there is synchronised:
+//    the internal nodes of that level and finer ones are replaced by the
+//    average of their children (Eq. Averaging), finest first;
+//  * at the end of the macro step the integrated fluxes of internal nodes are
+//    averaged from their children (bottom-up) and every leaf face that
+//    touches a refined neighbour exchanges its own integrated flux for the
+//    finer side's (Alg. ComputeLoop's adjustment of coarse cell values with
+//    the averaged fine fluxes), so the macro step is conservative; then the
+//    averaging once more.
+// With l_max = 0 this is global stepping.
+const double RK_W3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+const double RK_W2[2] = {0.5, 0.5};
+inline double rk_w(const Ctx& C, int s) { return rk_stages(C) == 2 ? RK_W2[s] : RK_W3[s]; }
+// Stage times as fractions of the step (TVD-RK3: 0, 1, 1/2; TVD-RK2: 0, 1).
+const double RK_C3[3] = {0.0, 1.0, 0.5};
+const double RK_C2[2] = {0.0, 1.0};
+inline double rk_c(const Ctx& C, int s) { return rk_stages(C) == 2 ? RK_C2[s] : RK_C3[s]; }
+
+// Averaging of the internal nodes of levels lo .. l_max - 1 (finest first).
+void project_from(Ctx& C, int lo) {
+  int lm = max_level(C);
+  for (int l = lm - 1; l >= lo; --l) {
+    std::vector<Node*> v = nodes_at(C, l, false);
+#pragma omp parallel for schedule(dynamic)
+    for (long t = 0; t < (long)v.size(); ++t) {
+      Node& P = *v[t];
+      if (P.leaf) continue;
+      average_children(C, P);
+    }
+  }
+}
+
+// A stage of level `level` at micro step r.
+void lts_level_stage(Ctx& C, int level, int r, int L, int s, const double* dtl) {
+  std::vector<Node*> coarse;
+  std::vector<double> theta;
+  for (int m = 0; m < level; ++m)
+    for (Node* n : nodes_at(C, m, false)) {
+      const int span = 1 << (L - m);
+      const int r0 = r - r % span;
+      coarse.push_back(n);
+      theta.push_back(((double)(r - r0) + rk_c(C, s) * (double)(1 << (L - level))) / (double)span);
+    }
+  std::vector<std::vector<double>> keep(coarse.size());
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < (long)coarse.size(); ++t) {
+    Node& n = *coarse[t];
+    const double th = theta[t];
+    keep[t].resize((size_t)NV * NINT);
+    for (int var = 0; var < NV; ++var)
+      for (int k = 0; k < NB; ++k)
+        for (int j = 0; j < NB; ++j)
+          for (int i = 0; i < NB; ++i) {
+            const size_t si = (size_t)var * NCELL + sidx(i, j, k), ii = (size_t)var * NINT + iidx(i, j, k);
+            keep[t][ii] = n.u[si];
+            n.u[si] = (1.0 - th) * n.un[ii] + th * n.u[si];
+          }
+  }
+  fill_halos(C);
+  std::vector<Node*> v = nodes_at(C, level, false);
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < (long)v.size(); ++t) leaf_rhs(C, *v[t]);
+  rk_update_nodes(C, v, s, dtl);
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < (long)v.size(); ++t) {
+    Node& n = *v[t];
+    if (!n.leaf) continue;
+    const double w = rk_w(C, s) * dtl[n.inst];
+    for (size_t e = 0; e < n.fmac.size(); ++e) n.fmac[e] = n.fmac[e] + w * n.face[e];
+  }
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < (long)coarse.size(); ++t) {
+    Node& n = *coarse[t];
+    for (int var = 0; var < NV; ++var)
+      for (int k = 0; k < NB; ++k)
+        for (int j = 0; j < NB; ++j)
+          for (int i = 0; i < NB; ++i)
+            n.u[(size_t)var * NCELL + sidx(i, j, k)] = keep[t][(size_t)var * NINT + iidx(i, j, k)];
+  }
+}
+
+// Integrated face fluxes of internal nodes: the mean of the four child faces
+// covering each parent face cell, bottom-up (as average_faces does per stage).
+void average_fmac(Ctx& C) {
+  int lm = max_level(C);
+  for (int l = lm - 1; l >= 0; --l) {
+    std::vector<Node*> v = nodes_at(C, l, false);
+#pragma omp parallel for schedule(dynamic)
+    for (long t = 0; t < (long)v.size(); ++t) {
+      Node& P = *v[t];
+      if (P.leaf) continue;
+      uint64_t inst = P.key >> 56;
+      for (int s = 0; s < 6; ++s) {
+        int d = s / 2, hi = s & 1;
+        int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+        for (int bb = 0; bb < NB; ++bb)
+          for (int aa = 0; aa < NB; ++aa) {
+            int ct1 = aa / 8, ct2 = bb / 8;
+            int cb[3];
+            cb[d] = hi;
+            cb[t1] = ct1;
+            cb[t2] = ct2;
+            int ch = cb[0] | (cb[1] << 1) | (cb[2] << 2);
+            uint64_t ck = (((P.key & MASK56) << 3) | (uint64_t)ch) | (inst << 56);
+            const Node* c = find(C, ck);
+            int fa = 2 * (aa - 8 * ct1), fb = 2 * (bb - 8 * ct2);
+            for (int v2 = 0; v2 < NV; ++v2) {
+              auto f = [&](int x, int y) { return c->fmac[(((size_t)s * NV + v2) * NB + fb + y) * NB + fa + x]; };
+              P.fmac[(((size_t)s * NV + v2) * NB + bb) * NB + aa] = 0.25 * ((f(0, 0) + f(1, 0)) + (f(0, 1) + f(1, 1)));
+            }
+          }
+      }
+    }
+  }
+}
+
+// The end-of-macro-step correction: a leaf face whose same-level neighbour is
+// refined takes the finer side's integrated flux, u += (F_c - F_f)/dx on an
+// upper face and (F_f - F_c)/dx on a lower one, sides x-, x+, y-, y+, z-, z+.
+void lts_reflux(Ctx& C) {
+  std::vector<Node*> v = nodes_at(C, -1, true);
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < (long)v.size(); ++t) {
+    Node& n = *v[t];
+    double dx = dx_of(C, n.level);
+    for (int s = 0; s < 6; ++s) {
+      int d = s / 2, hi = s & 1;
+      uint64_t nk;
+      if (!axis_step(C.c, n.key, d, hi ? 1 : -1, &nk)) continue;
+      const Node* nb = find(C, nk);
+      if (!nb || nb->leaf) continue;
+      int so = s ^ 1;
+      int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+      for (int bb = 0; bb < NB; ++bb)
+        for (int aa = 0; aa < NB; ++aa) {
+          int c[3];
+          c[d] = hi ? NB - 1 : 0;
+          c[t1] = aa;
+          c[t2] = bb;
+          for (int v2 = 0; v2 < NV; ++v2) {
+            double Fc = n.fmac[(((size_t)s * NV + v2) * NB + bb) * NB + aa];
+            double Ff = nb->fmac[(((size_t)so * NV + v2) * NB + bb) * NB + aa];
+            double dU = hi ? (Fc - Ff) / dx : (Ff - Fc) / dx;
+            double& ur = n.u[(size_t)v2 * NCELL + sidx(c[0], c[1], c[2])];
+            ur = ur + dU;
+          }
+        }
+    }
+  }
+}
+
+void lts_macro_step(Ctx& C, double* dt) {
+  cfl_dt(C, dt);
+  const int L = C.c.lmax[0];
+  for (auto& kv : C.nodes) std::fill(kv.second.fmac.begin(), kv.second.fmac.end(), 0.0);
+  std::vector<double> dtl((size_t)C.c.n_instances);
+  for (int r = 0; r < (1 << L); ++r) {
+    for (int l = 0; l <= L; ++l) {
+      if (r % (1 << (L - l)) != 0) continue;
+      if (nodes_at(C, l, true).empty()) continue;
+      for (int i = 0; i < C.c.n_instances; ++i) dtl[i] = std::ldexp(dt[i], L - l);
+      for (int s = 0; s < rk_stages(C); ++s) lts_level_stage(C, l, r, L, s, dtl.data());
+    }
+    // levels whose step ends with this micro step: synchronise them
+    int lo = L;
+    for (int l = L; l >= 0; --l)
+      if ((r + 1) % (1 << (L - l)) == 0) lo = l;
+    project_from(C, lo);
+  }
+  average_fmac(C);
+  lts_reflux(C);
   project(C);
 }
 
@@ -1758,9 +1962,13 @@ void orc_step(void* h, int32_t nsteps, double* dt_hist) {
   Ctx& C = *(Ctx*)h;
   std::vector<double> dt((size_t)C.c.n_instances);
   for (int st = 0; st < nsteps; ++st) {
-    cfl_dt(C, dt.data());
+    if (C.c.lts) {
+      lts_macro_step(C, dt.data());
+    } else {
+      cfl_dt(C, dt.data());
+      for (int s = 0; s < rk_stages(C); ++s) stage(C, s, dt.data());
+    }
     if (dt_hist) std::memcpy(dt_hist + (size_t)st * C.c.n_instances, dt.data(), sizeof(double) * C.c.n_instances);
-    for (int s = 0; s < rk_stages(C); ++s) stage(C, s, dt.data());
     if (any_mr(C)) {
       fill_halos(C);
       std::vector<int8_t> tags((size_t)orc_list(h, -1, 1, nullptr, 0));
@@ -1769,6 +1977,9 @@ void orc_step(void* h, int32_t nsteps, double* dt_hist) {
     }
   }
 }
+
+// One LTS macro step without the MR analysis (dt: [n_instances] out, Delta t_L).
+void orc_lts_macro_step(void* h, double* dt) { lts_macro_step(*(Ctx*)h, dt); }
 
 // Same-level neighbour by Alg. (NeighborLookup): returns 1 and the id, or 0 at
 // a non-periodic domain boundary.

@@ -45,6 +45,7 @@ class RunConfig:
     rk_stages: int = 3          # 3: TVD-RK3, 2: TVD-RK2
     flux: int = FLUX_ROE        # Roe with per-field LLF fallback, LLF, or HLLC
     mu: float = 0.0             # dynamic viscosity (Navier-Stokes terms); 0 = Euler
+    lts: int = 0                # 1: local time stepping per level (Eq. LtsTimestep)
     mlp_tau: float = 0.0
     name: str = "custom"
 

@@ -137,6 +137,17 @@ MUTATIONS = {
     "feature_compression_constant": ("double a = std::log10(1.0 + 1e6 * std::fabs(d)) / 8.0;",
                                      "double a = std::log10(1.0 + 1e5 * std::fabs(d)) / 8.0;",
                                      "test_selector_features_with_the_split_active_match_their_definition[2]"),
+    "lts_schedule": ("      if (r % (1 << (L - l)) != 0) continue;\n      if (nodes_at(C, l, true).empty()) continue;",
+                     "      if (r % (1 << l) != 0) continue;\n      if (nodes_at(C, l, true).empty()) continue;",
+                     "test_lts_density_wave_crosses_a_jump"),
+    "lts_no_reflux": ("  average_fmac(C);\n  lts_reflux(C);\n  project(C);", "  average_fmac(C);\n  project(C);",
+                      "test_lts_conserves_across_jumps[3]"),
+    "lts_frozen_coarse_levels": ("            n.u[si] = (1.0 - th) * n.un[ii] + th * n.u[si];",
+                                 "            n.u[si] = n.un[ii];",
+                                 "test_lts_density_wave_crosses_a_jump"),
+    "lts_stage_flux_weights": ("const double RK_W3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};",
+                               "const double RK_W3[3] = {1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0};",
+                               "test_lts_conserves_across_jumps[2]"),
     "rk2_weights": ("const double RK_B2[2] = {1.0, 0.5};", "const double RK_B2[2] = {1.0, 0.6};",
                     "test_rk2_is_second_order_in_time"),
 }
