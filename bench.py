@@ -327,10 +327,10 @@ def release(*ctxs):
     torch.cuda.empty_cache()
 
 
-def make_context(name, precision, lmax=None, recon=0, flux=0, tau=0.0, params=None, slots=None, stream=None):
+def make_context(name, precision, lmax=None, recon=0, flux=0, tau=0.0, params=None, slots=None, stream=None, lts=0):
     from paper_2012_04385_gb300 import mrb
     cfg, ic = workload_config(name, precision, lmax)
-    cfg.recon, cfg.flux, cfg.mlp_tau = recon, flux, tau
+    cfg.recon, cfg.flux, cfg.mlp_tau, cfg.lts = recon, flux, tau, lts
     ctx = mrb.Context(cfg, slots or slots_for(cfg), stream=stream, mlp_params=params if recon == 1 else None)
     t0 = time.perf_counter()
     mrb.init_tree(ctx, lambda c, geo: ic(c, geo))
@@ -565,6 +565,37 @@ def run_gpu(args, rank, world):
                                "ms_per_step": mv["ms"] / vsteps, "stage_kernel_ms": mv["stage_ms"],
                                "steps": vsteps}
 
+    # ---- local time stepping on the same workload (Eq. LtsTimestep): a macro
+    # step advances every level by 2^lmax finest steps, level l in 2^l steps
+    lts = None
+    if not args.no_side:
+        import torch as _t
+        ctx = make_context(name, I.FP32_ACC64, lmax=lmax, recon=I.RECON_LEARNED, tau=tau, params=params,
+                           stream=stream, lts=1)
+        L = ctx.cfg.lmax_of(0)
+        ctx.step(1)                                  # warm-up macro step
+        nmac = 2
+        dts = _t.empty((nmac, 1), dtype=_t.float64, device="cuda")
+        ev0, ev1 = _t.cuda.Event(enable_timing=True), _t.cuda.Event(enable_timing=True)
+        geo = ctx.geometry()
+        lcells = sum(int((geo[:, 0] == l).sum()) * 4096 * 3 * (1 << l) for l in range(L + 1))
+        _t.cuda.synchronize()
+        ev0.record(stream)
+        ctx.step(nmac, dt_hist=dts)
+        ev1.record(stream)
+        _t.cuda.synchronize()
+        ms_l = ev0.elapsed_time(ev1)
+        sim_t = float(dts.sum().item()) * (1 << L)
+        lts = {"path": "FP32 bulk + learned selector, local time stepping", "macro_steps": nmac,
+               "ms_per_macro_step": ms_l / nmac, "leaf_cell_updates_per_macro_step": lcells,
+               "leaf_cell_updates_per_s": lcells * nmac / (ms_l * 1e-3),
+               "simulated_time_per_s": sim_t / (ms_l * 1e-3),
+               "global_stepping_simulated_time_per_s": (sum(log_l[i]["dt"] for i in range(len(log_l))) /
+                                                         len(log_l)) / (m["ms"] / args.steps * 1e-3),
+               "leaves_per_level": [int((geo[:, 0] == l).sum()) for l in range(L + 1)]}
+        release(ctx)
+        ctx = None
+
     # ---- side lines: the other single-GPU workloads of the family
     side = None
     if not args.no_side:
@@ -643,6 +674,8 @@ def run_gpu(args, rank, world):
         result["fp32_variants"] = variants
     if side:
         result["side_lines"] = side
+    if lts:
+        result["local_time_stepping"] = lts
     if e2e:
         result["e2e"] = e2e
     # the host-core baseline is taken once, by the single rank of an N = 1 run

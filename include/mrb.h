@@ -121,6 +121,11 @@ typedef struct mrb_config {
   const void* mlp_weights;         /* device, learned selector weights (see mrb_mlp_*)     */
   double mlp_tau;                  /* logit threshold of the learned selector              */
   void* stream;                    /* cudaStream_t for all work                            */
+  int32_t lts;                     /* 0: every leaf steps with the finest level's Delta t; */
+                                   /* 1: local time stepping (Eq. LtsTimestep): level l    */
+                                   /* steps with 2^(lmax - l) Delta t_lmax within a macro  */
+                                   /* step (mrb_step advances one macro step); every       */
+                                   /* instance must have the same lmax (else EINVAL)       */
 } mrb_config;
 
 typedef struct mrb_ctx mrb_ctx;

@@ -1418,7 +1418,7 @@ void stage(Ctx& C, int s, const double* dt) {
 //    same for every instance), fixed for the macro step; level l advances in
 //    steps of Delta t_l = 2^(L - l) Delta t_L (Eq. LtsTimestep);
 //  * micro steps r = 0 .. 2^L - 1: every level whose step starts at r (r a
-//    multiple of 2^(L - l)) and that holds leaves takes one full Runge-Kutta
+//    multiple of 2^(L - l)) and that holds nodes takes one full Runge-Kutta
 //    step, coarse levels first;
 //  * a level's step advances all its nodes, leaves and internal nodes alike
 //    (an internal node carries that level's approximation of the finer region
@@ -1591,7 +1591,7 @@ void lts_macro_step(Ctx& C, double* dt) {
   for (int r = 0; r < (1 << L); ++r) {
     for (int l = 0; l <= L; ++l) {
       if (r % (1 << (L - l)) != 0) continue;
-      if (nodes_at(C, l, true).empty()) continue;
+      if (nodes_at(C, l, false).empty()) continue;
       for (int i = 0; i < C.c.n_instances; ++i) dtl[i] = std::ldexp(dt[i], L - l);
       for (int s = 0; s < rk_stages(C); ++s) lts_level_stage(C, l, r, L, s, dtl.data());
     }

@@ -291,6 +291,52 @@ struct mrb_ctx {
     }
   }
 
+  // Local time stepping, one macro step (Eq. LtsTimestep; the reading is the
+  // oracle's: coarse levels first, every node of a stepping level advances,
+  // coarser levels interpolated in time for the halo fills, levels averaged
+  // from their children when their step ends, integrated boundary-face fluxes
+  // exchanged at the end).  Direct launches; the stage kernels write the other
+  // stage buffer, copied back after each stage, so `cur` does not change.
+  void step_lts() {
+    launch_cfl(topo(), phys, P, cur, d_smax, d_dt, d_status, st);
+    launch_lts_fmac(topo(), phys, P, 0, 0, d_dt, 1, st);
+    const int L = max_lmax;
+    const int fmode = (cfg.precision == MRB_FP32_ACC64 && !(cfg.mu > 0.0)) ? FILL_STAGE : FILL_FULL;
+    const double cst[2][3] = {{0.0, 1.0, 0.5}, {0.0, 1.0, 0.0}};   // stage times, TVD-RK3 / TVD-RK2
+    const int row = (phys.rk == 2) ? 1 : 0;
+    for (int r = 0; r < (1 << L); ++r) {
+      for (int l = 0; l <= L; ++l) {
+        if (r % (1 << (L - l)) != 0) continue;
+        if (h_cnt[CNT_LVL + l + 1] - h_cnt[CNT_LVL + l] == 0) continue;
+        for (int s = 0; s < phys.rk; ++s) {
+          LevelTheta th{};
+          for (int m = 0; m < l; ++m) {
+            const int span = 1 << (L - m);
+            const int r0 = r - r % span;
+            th.th[m] = ((double)(r - r0) + cst[row][s] * (double)(1 << (L - l))) / (double)span;
+          }
+          launch_lts_interp(topo(), P, cur, l, th, 0, st);
+          fill_halos(fmode);
+          if (cfg.precision == MRB_FP32_ACC64) launch_rhs_rk_f32(topo(), phys, P, cur, s, d_dt, nullptr, st, l);
+          else launch_rhs_rk_f64(topo(), phys, P, cur, s, d_dt, nullptr, st, l);
+          launch_lts_copyback(topo(), P, cur, l, st);
+          launch_lts_fmac(topo(), phys, P, l, s, d_dt, 0, st);
+          launch_lts_interp(topo(), P, cur, l, th, 1, st);
+        }
+      }
+      // levels whose step ends with this micro step: averaged from their children
+      int lo = L;
+      for (int l = L; l >= 0; --l)
+        if ((r + 1) % (1 << (L - l)) == 0) lo = l;
+      for (int l = max_lmax - 1; l >= lo; --l) launch_project_level(topo(), P, cur, l, st);
+      launch_shadow(topo(), phys, P, cur, SH_INTERNAL, nullptr, 0, 0, st);
+    }
+    for (int l = max_lmax - 1; l >= 0; --l) launch_face_avg_level(topo(), P, l, st, 1);
+    launch_lts_reflux(topo(), phys, P, cur, st);
+    launch_shadow(topo(), phys, P, cur, SH_JUMP, nullptr, 0, 0, st);
+    project();
+  }
+
   void capture_graphs() {
     for (int g = 0; g < 2; ++g) {
       if (graph[g]) cudaGraphExecDestroy(graph[g]);
@@ -489,6 +535,10 @@ int check_config(const mrb_config* cfg) {
       (cfg->recon != MRB_RECON_WENO5 || cfg->flux != MRB_FLUX_ROE))
     return MRB_EINVAL;
   if (cfg->rk_stages != 0 && cfg->rk_stages != 2 && cfg->rk_stages != 3) return MRB_EINVAL;
+  if (cfg->lts != 0 && cfg->lts != 1) return MRB_EINVAL;
+  if (cfg->lts)
+    for (int i = 1; i < cfg->n_instances; ++i)
+      if (cfg->lmax[i] != cfg->lmax[0]) return MRB_EINVAL;   // one micro-step schedule for all instances
   if (!(cfg->dx0 > 0) || !(cfg->gamma > 1.0) || !(cfg->cfl > 0)) return MRB_EINVAL;
   return MRB_OK;
 }
@@ -504,8 +554,10 @@ size_t mrb_pool_bytes(const mrb_config* cfg, int64_t n_slots) {
   const size_t n = (size_t)n_slots;
   // the mixed-precision path also keeps FP32 records of both stage buffers' internal cells
   const size_t sh = (cfg->precision == MRB_FP32_ACC64) ? align256(n * SLOT_SH * 4) * 2 : 0;
+  // local time stepping also keeps the boundary-face fluxes integrated over a macro step
+  const size_t fm = cfg->lts ? align256(n * SLOT_F * 8) : 0;
   return align256(n * SLOT_U * 8) * 2 + align256(n * SLOT_N * 8) + align256(n * SLOT_F * 8) + align256(n * SLOT_SEL * 4) +
-         sh;
+         sh + fm;
 }
 
 int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ctx** out) {
@@ -550,7 +602,10 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
       c->P.sh[0] = (float*)q;
       q += align256(n * SLOT_SH * 4);
       c->P.sh[1] = (float*)q;
+      q += align256(n * SLOT_SH * 4);
     }
+    c->P.fmac = nullptr;
+    if (cfg->lts) c->P.fmac = (double*)q;
     Phys& p = c->phys;
     p.gamma = cfg->gamma;
     p.B = cfg->B;
@@ -573,6 +628,7 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
     p.mlp = (const float*)cfg->mlp_weights;
     p.mlp_tau = (float)cfg->mlp_tau;
     p.blocked = 0;
+    p.lts = cfg->lts ? 1 : 0;
     c->max_lmax = 0;
     for (int i = 0; i < cfg->n_instances; ++i) c->max_lmax = std::max(c->max_lmax, (int)cfg->lmax[i]);
     c->d_keys = c->dalloc<uint64_t>(n);
@@ -818,11 +874,15 @@ int mrb_step(mrb_ctx* c, int32_t nsteps, double* dt_hist_dev) {
   return guarded(c, [&] {
     bool mr = c->max_lmax > 0;
     for (int s = 0; s < nsteps; ++s) {
-      if (c->graph_dirty) c->capture_graphs();
       const int g = c->cur;
-      CK(cudaGraphLaunch(c->graph[g], c->st));
-      g_kernel_launches += c->graph_kernels[g];
-      if (c->phys.rk & 1) c->cur ^= 1;   // every stage flips the stage buffer
+      if (c->phys.lts) {
+        c->step_lts();
+      } else {
+        if (c->graph_dirty) c->capture_graphs();
+        CK(cudaGraphLaunch(c->graph[g], c->st));
+        g_kernel_launches += c->graph_kernels[g];
+        if (c->phys.rk & 1) c->cur ^= 1;   // every stage flips the stage buffer
+      }
       if (dt_hist_dev)
         CK(cudaMemcpyAsync(dt_hist_dev + (size_t)s * c->cfg.n_instances, c->d_dt, sizeof(double) * c->cfg.n_instances,
                            cudaMemcpyDeviceToDevice, c->st));
@@ -833,7 +893,7 @@ int mrb_step(mrb_ctx* c, int32_t nsteps, double* dt_hist_dev) {
                           c->st);
         c->remesh(c->d_tags);
       }
-      if (c->prof) {
+      if (c->prof && !c->phys.lts) {   // (the macro steps of local time stepping are not profiled per stage)
         CK(cudaStreamSynchronize(c->st));
         for (int q = 0; q < c->phys.rk; ++q) {
           float ms = 0.f;

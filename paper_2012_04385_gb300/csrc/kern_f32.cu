@@ -8,18 +8,18 @@
 namespace mrb {
 
 void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
-                       double* rhs_out, cudaStream_t st) {
-  if (p.mu > 0.0) launch_stage_f32<32>(t, p, pool, cur, stage, dt, rhs_out, st);   // WENO5, Roe, viscous
-  else if (p.flux == 1) launch_rhs_rk_f32_llf(t, p, pool, cur, stage, dt, rhs_out, st);
-  else if (p.flux == 2) launch_rhs_rk_f32_hllc(t, p, pool, cur, stage, dt, rhs_out, st);
-  else if (p.recon == 2) launch_stage_f32<2>(t, p, pool, cur, stage, dt, rhs_out, st);
-  else if (p.recon == 3) launch_stage_f32<4>(t, p, pool, cur, stage, dt, rhs_out, st);
-  else if (p.recon == 4) launch_stage_f32<5>(t, p, pool, cur, stage, dt, rhs_out, st);
+                       double* rhs_out, cudaStream_t st, int level) {
+  if (p.mu > 0.0) launch_stage_f32<32>(t, p, pool, cur, stage, dt, rhs_out, st, level);   // WENO5, Roe, viscous
+  else if (p.flux == 1) launch_rhs_rk_f32_llf(t, p, pool, cur, stage, dt, rhs_out, st, level);
+  else if (p.flux == 2) launch_rhs_rk_f32_hllc(t, p, pool, cur, stage, dt, rhs_out, st, level);
+  else if (p.recon == 2) launch_stage_f32<2>(t, p, pool, cur, stage, dt, rhs_out, st, level);
+  else if (p.recon == 3) launch_stage_f32<4>(t, p, pool, cur, stage, dt, rhs_out, st, level);
+  else if (p.recon == 4) launch_stage_f32<5>(t, p, pool, cur, stage, dt, rhs_out, st, level);
   else if (p.recon == 1 && p.mlp) {
     // the selector is evaluated on the stage-0 state; stages 1 and 2 use its decisions
-    if (stage == 0 || rhs_out) launch_stage_f32<1>(t, p, pool, cur, stage, dt, rhs_out, st);
-    else launch_stage_f32<3>(t, p, pool, cur, stage, dt, rhs_out, st);
-  } else launch_stage_f32<0>(t, p, pool, cur, stage, dt, rhs_out, st);
+    if (stage == 0 || rhs_out) launch_stage_f32<1>(t, p, pool, cur, stage, dt, rhs_out, st, level);
+    else launch_stage_f32<3>(t, p, pool, cur, stage, dt, rhs_out, st, level);
+  } else launch_stage_f32<0>(t, p, pool, cur, stage, dt, rhs_out, st, level);
 }
 
 void launch_fill_level_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int level, cudaStream_t st,

@@ -127,19 +127,19 @@ void launch_fill_list(const Topo& t, const Phys& p, const Pool& pool, int cur, c
 
 // ---------------------------------------------------------------- RHS + RK (FP64)
 void launch_rhs_rk_f64(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
-                       double* rhs_out, cudaStream_t st) {
-  launch_rhs_rk_impl<double>(t, p, pool, cur, stage, dt, rhs_out, st);
+                       double* rhs_out, cudaStream_t st, int level) {
+  launch_rhs_rk_impl<double>(t, p, pool, cur, stage, dt, rhs_out, st, level);
 }
 
 // ---------------------------------------------------------------- face fluxes of internal nodes
 // parent face cell = mean of the 2 x 2 covering child face cells, levels fine to coarse
-__global__ void k_face_avg_level(Topo t, Pool pool, int level) {
+__global__ void k_face_avg_level(Topo t, double* __restrict__ faces, int level) {
   const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
   for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
     const int node = t.lvl_nodes[w];
     const int c0 = t.child0[node];
     if (c0 < 0) continue;
-    double* F = pool.face + (size_t)t.slot[node] * SLOT_F;
+    double* F = faces + (size_t)t.slot[node] * SLOT_F;
     for (int e = threadIdx.x; e < 6 * NFACE; e += blockDim.x) {
       const int s = e / NFACE, aa = e % 16, bb = (e / 16) % 16;
       const int d = s / 2, hi = s & 1;
@@ -150,7 +150,7 @@ __global__ void k_face_avg_level(Topo t, Pool pool, int level) {
       cb[t1] = ct1;
       cb[t2] = ct2;
       const int ch = cb[0] | (cb[1] << 1) | (cb[2] << 2);
-      const double* C = pool.face + (size_t)t.slot[c0 + ch] * SLOT_F;
+      const double* C = faces + (size_t)t.slot[c0 + ch] * SLOT_F;
       const int fa = 2 * (aa - 8 * ct1), fbb = 2 * (bb - 8 * ct2);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -163,8 +163,144 @@ __global__ void k_face_avg_level(Topo t, Pool pool, int level) {
   }
 }
 
-void launch_face_avg_level(const Topo& t, const Pool& pool, int level, cudaStream_t st) {
-  k_face_avg_level<<<sm_count() * 4, 256, 0, st>>>(t, pool, level);
+void launch_face_avg_level(const Topo& t, const Pool& pool, int level, cudaStream_t st, int integrated) {
+  k_face_avg_level<<<sm_count() * 4, 256, 0, st>>>(t, integrated ? pool.fmac : pool.face, level);
+  ++g_kernel_launches;
+}
+
+// ---------------------------------------------------------------- local time stepping
+// (Eq. LtsTimestep; the reading: a level's step advances all its nodes, the
+// halo fill of each stage sees coarser levels interpolated in time, levels are
+// averaged from their children when their step ends, and the boundary-face
+// fluxes integrated over the macro step are exchanged at its end.)
+
+// Nodes of levels 0 .. below-1: their internal cells become (1 - theta) u^n +
+// theta u, the end state u kept in the other stage buffer (restore = 0), or are
+// put back from there (restore = 1).
+__global__ void k_lts_interp(Topo t, Pool pool, int cur, int below, LevelTheta th, int restore) {
+  const int end = t.cnt[CNT_LVL + below];
+  for (int w = t.cnt[CNT_LVL + 0] + blockIdx.x; w < end; w += gridDim.x) {
+    const int node = t.lvl_nodes[w];
+    const size_t slot = (size_t)t.slot[node];
+    double* U = pool.buf[cur] + slot * SLOT_U;
+    double* K = pool.buf[cur ^ 1] + slot * SLOT_U;
+    const double* N = pool.un + slot * SLOT_N;
+    const double q = th.th[t.level[node]];
+    for (int e = threadIdx.x; e < NV * NINT; e += blockDim.x) {
+      const int v = e / NINT, ii = e % NINT;
+      const int s = v * NCELL + sidx(ii % 16, (ii / 16) % 16, ii / 256);
+      if (restore) {
+        U[s] = K[s];
+      } else {
+        const double u = U[s];
+        K[s] = u;
+        U[s] = (1.0 - q) * N[e] + q * u;
+      }
+    }
+  }
+}
+
+void launch_lts_interp(const Topo& t, const Pool& pool, int cur, int below, const LevelTheta& th, int restore,
+                       cudaStream_t st) {
+  if (below <= 0) return;
+  k_lts_interp<<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, below, th, restore);
+  ++g_kernel_launches;
+}
+
+// Internal cells (and FP32 records) of the nodes of `level`: cur^1 -> cur.
+__global__ void k_lts_copyback(Topo t, Pool pool, int cur, int level) {
+  const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
+  for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
+    const size_t slot = (size_t)t.slot[t.lvl_nodes[w]];
+    double* U = pool.buf[cur] + slot * SLOT_U;
+    const double* O = pool.buf[cur ^ 1] + slot * SLOT_U;
+    for (int e = threadIdx.x; e < NV * NINT; e += blockDim.x) {
+      const int v = e / NINT, ii = e % NINT;
+      const int s = v * NCELL + sidx(ii % 16, (ii / 16) % 16, ii / 256);
+      U[s] = O[s];
+    }
+    if (pool.sh[0]) {
+      float* R = pool.sh[cur] + slot * SLOT_SH;
+      const float* Q = pool.sh[cur ^ 1] + slot * SLOT_SH;
+      for (int e = threadIdx.x; e < SLOT_SH; e += blockDim.x) R[e] = Q[e];
+    }
+  }
+}
+
+void launch_lts_copyback(const Topo& t, const Pool& pool, int cur, int level, cudaStream_t st) {
+  k_lts_copyback<<<sm_count() * 4, 256, 0, st>>>(t, pool, cur, level);
+  ++g_kernel_launches;
+}
+
+// Integrated boundary-face fluxes of leaves: zero all (zero = 1) or, for the
+// leaves of `level`, add (w_stage x dt 2^(lmax - level)) x the stage's face fluxes.
+__global__ void k_lts_fmac(Topo t, Phys p, Pool pool, int level, int stage, const double* __restrict__ dt, int zero) {
+  const int beg = zero ? 0 : t.cnt[CNT_LVL + level];
+  const int end = zero ? t.cnt[CNT_NLEAVES] : t.cnt[CNT_LVL + level + 1];
+  for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
+    const int node = zero ? t.leaves[w] : t.lvl_nodes[w];
+    if (t.child0[node] >= 0) continue;
+    const size_t slot = (size_t)t.slot[node];
+    double* M = pool.fmac + slot * SLOT_F;
+    if (zero) {
+      for (int e = threadIdx.x; e < SLOT_F; e += blockDim.x) M[e] = 0.0;
+      continue;
+    }
+    const double* F = pool.face + slot * SLOT_F;
+    const double wgt = kRkW[rk_row(p)][stage] * ldexp(dt[t.inst[node]], p.lmax[t.inst[node]] - level);
+    for (int e = threadIdx.x; e < SLOT_F; e += blockDim.x) M[e] = M[e] + wgt * F[e];
+  }
+}
+
+void launch_lts_fmac(const Topo& t, const Phys& p, const Pool& pool, int level, int stage, const double* dt,
+                     int zero, cudaStream_t st) {
+  k_lts_fmac<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, level, stage, dt, zero);
+  ++g_kernel_launches;
+}
+
+// u += (F_c - F_f)/dx on an upper face, (F_f - F_c)/dx on a lower one, with the
+// integrated fluxes of the leaf and of its refined same-level neighbour.
+__global__ void k_lts_reflux(Topo t, Phys p, Pool pool, int cur) {
+  const int nitems = t.cnt[CNT_JUMP];
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int li = t.jump[w] >> 6, mask = t.jump[w] & 63;
+    const int node = t.leaves[li];
+    const double* Fc_all = pool.fmac + (size_t)t.slot[node] * SLOT_F;
+    const double dx = ldexp(p.dx0, -t.level[node]);
+    double* U = pool.buf[cur] + (size_t)t.slot[node] * SLOT_U;
+#pragma unroll 1
+    for (int s = 0; s < 6; ++s) {
+      const int d = s / 2, hi = s & 1;
+      int sv[3] = {0, 0, 0};
+      sv[d] = hi ? 1 : -1;
+      const int r = (sv[2] + 1) * 9 + (sv[1] + 1) * 3 + (sv[0] + 1);
+      if (!((mask >> s) & 1)) continue;
+      const int nb = t.nbr[(size_t)node * 27 + r];
+      const double* Ff_all = pool.fmac + (size_t)t.slot[nb] * SLOT_F;
+      const int so = s ^ 1;
+      const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+      for (int e = threadIdx.x; e < NFACE; e += blockDim.x) {
+        const int aa = e % 16, bb = e / 16;
+        int c[3];
+        c[d] = hi ? NB - 1 : 0;
+        c[t1] = aa;
+        c[t2] = bb;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const double Fc = Fc_all[(s * NV + v) * NFACE + e];
+          const double Ff = Ff_all[(so * NV + v) * NFACE + e];
+          const double dU = hi ? (Fc - Ff) / dx : (Ff - Fc) / dx;
+          double& ur = U[v * NCELL + sidx(c[0], c[1], c[2])];
+          ur = ur + dU;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+void launch_lts_reflux(const Topo& t, const Phys& p, const Pool& pool, int cur, cudaStream_t st) {
+  k_lts_reflux<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, cur);
   ++g_kernel_launches;
 }
 

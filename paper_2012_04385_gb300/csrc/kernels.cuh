@@ -59,6 +59,7 @@ struct Phys {
   unsigned long long* lin_count;   // [0] faces sent to linear, [1] faces evaluated
   const int32_t* lmax;     // device [n_inst]
   int blocked;             // stage kernels: 1 = a contiguous run of work items per CTA, 0 = strided by the grid
+  int lts;                 // local time stepping (Eq. LtsTimestep)
 };
 
 // Launch shapes of the scheduling-only tunables (mrb_autotune): every choice
@@ -88,6 +89,24 @@ __device__ __forceinline__ ItemRange item_range(int nitems, int blocked) {
 __device__ __constant__ static const double kRkA[2][3] = {{0.0, 0.75, 1.0 / 3.0}, {0.0, 0.5, 0.0}};
 __device__ __constant__ static const double kRkB[2][3] = {{1.0, 0.25, 2.0 / 3.0}, {1.0, 0.5, 0.0}};
 __device__ __forceinline__ int rk_row(const Phys& p) { return p.rk == 2 ? 1 : 0; }
+// Weights of the stage right-hand sides in the step (u^(n+1) = u^n + dt sum_s
+// w_s L(u^(s))): TVD-RK3 1/6, 1/6, 2/3; TVD-RK2 1/2, 1/2.
+__device__ __constant__ static const double kRkW[2][3] = {{1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0}, {0.5, 0.5, 0.0}};
+
+// Work items of a stage launch: every leaf (level < 0) or every node of one
+// level (local time stepping); the node of item k and the item count.
+__device__ __forceinline__ int stage_nodes(const Topo& t, int level) {
+  return level < 0 ? t.cnt[CNT_NLEAVES] : t.cnt[CNT_LVL + level + 1] - t.cnt[CNT_LVL + level];
+}
+__device__ __forceinline__ int stage_node(const Topo& t, int level, int k) {
+  return level < 0 ? t.leaves[k] : t.lvl_nodes[t.cnt[CNT_LVL + level] + k];
+}
+// The time step of a node: dt of its instance, times 2^(lmax - level) under
+// local time stepping.
+__device__ __forceinline__ double node_dt(const Topo& t, const Phys& p, const double* dt, int node, int level) {
+  const int inst = t.inst[node];
+  return level < 0 ? dt[inst] : ldexp(dt[inst], p.lmax[inst] - level);
+}
 
 struct Pool {
   double* buf[2];          // stage buffers, [slot][5][24^3]
@@ -98,6 +117,9 @@ struct Pool {
   // buf[b], [slot][6][16^3]; kept by the mixed-precision path only (null
   // otherwise), rewritten by every kernel that writes internal cells
   float* sh[2];
+  // boundary-face fluxes integrated over a macro time step (local time
+  // stepping only), [slot][6][5][16][16]
+  double* fmac;
 };
 
 __device__ __forceinline__ double ldexp_(double x, int e) { return ldexp(x, e); }
@@ -115,17 +137,38 @@ void launch_fill_level(const Topo& t, const Phys& p, const Pool& pool, int cur, 
 // every halo region of the listed nodes (device list of n node indices), all variables
 void launch_fill_list(const Topo& t, const Phys& p, const Pool& pool, int cur, const int32_t* list, int n,
                       cudaStream_t st);
+// level < 0: every leaf with dt; level >= 0 (local time stepping): every node
+// of that level, leaves and internal nodes, with dt 2^(lmax - level)
 void launch_rhs_rk_f64(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
-                       double* rhs_out, cudaStream_t st);
+                       double* rhs_out, cudaStream_t st, int level = -1);
 void launch_rhs_rk_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
-                       double* rhs_out, cudaStream_t st);
+                       double* rhs_out, cudaStream_t st, int level = -1);
 // FP32 stage kernels of the flux variants (separate translation units):
 // LLF on every field, and HLLC, each with every non-learned reconstruction.
 void launch_rhs_rk_f32_llf(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
-                           double* rhs_out, cudaStream_t st);
+                           double* rhs_out, cudaStream_t st, int level = -1);
 void launch_rhs_rk_f32_hllc(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
-                            double* rhs_out, cudaStream_t st);
-void launch_face_avg_level(const Topo& t, const Pool& pool, int level, cudaStream_t st);
+                            double* rhs_out, cudaStream_t st, int level = -1);
+// internal nodes' face fluxes of `level` from their children (faces = pool.face,
+// or the macro step's integrated fluxes pool.fmac with integrated = 1)
+void launch_face_avg_level(const Topo& t, const Pool& pool, int level, cudaStream_t st, int integrated = 0);
+// ---- local time stepping
+// Interpolation in time of the nodes of levels < below (factor theta[m] per
+// level m; the end state kept in the other stage buffer), or its undoing.
+struct LevelTheta {
+  double th[MAXL + 1];
+};
+void launch_lts_interp(const Topo& t, const Pool& pool, int cur, int below, const LevelTheta& th, int restore,
+                       cudaStream_t st);
+// Internal cells (and FP32 records) of the nodes of `level`: buffer cur^1 -> cur.
+void launch_lts_copyback(const Topo& t, const Pool& pool, int cur, int level, cudaStream_t st);
+// Integrated fluxes: zero those of every leaf, or add weight x face fluxes to
+// those of the leaves of `level` (weight = kRkW[stage] x dt 2^(lmax - level)).
+void launch_lts_fmac(const Topo& t, const Phys& p, const Pool& pool, int level, int stage, const double* dt,
+                     int zero, cudaStream_t st);
+// End of the macro step: leaf faces next to refined neighbours take the finer
+// side's integrated flux.
+void launch_lts_reflux(const Topo& t, const Phys& p, const Pool& pool, int cur, cudaStream_t st);
 void launch_jump(const Topo& t, const Phys& p, const Pool& pool, int target, int stage, const double* dt,
                  double* rhs_out, cudaStream_t st);
 void launch_project_level(const Topo& t, const Pool& pool, int buf, int level, cudaStream_t st);

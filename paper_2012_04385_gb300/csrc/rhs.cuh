@@ -99,11 +99,11 @@ __device__ __forceinline__ void rhs_dir(const double* __restrict__ u, double* __
 
 template <class R>
 __global__ void __launch_bounds__(RHS_THREADS) k_rhs_rk(Topo t, Phys p, Pool pool, int cur, int stage,
-                                                       const double* __restrict__ dt, double* __restrict__ rhs_out) {
+                                                       const double* __restrict__ dt, double* __restrict__ rhs_out,
+                                                       int level) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* Fs = reinterpret_cast<R*>(smem_raw);
-  const int nleaves = t.cnt[CNT_NLEAVES];
-  const int nitems = nleaves * RHS_NSLAB;
+  const int nitems = stage_nodes(t, level) * RHS_NSLAB;
   const double* __restrict__ src = pool.buf[cur];
   double* __restrict__ dst = pool.buf[cur ^ 1];
   const R g = R(p.gamma), B = R(p.B);
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs_rk(Topo t, Phys p, Pool poo
   const ItemRange IR = item_range(nitems, p.blocked);
   for (int w = IR.first; w < IR.end; w += IR.step) {
     const int li = w / RHS_NSLAB, z0 = (w % RHS_NSLAB) * RHS_TZ;
-    const int node = t.leaves[li];
+    const int node = stage_node(t, level, li);
     const int slot = t.slot[node];
     const double* __restrict__ u = src + (size_t)slot * SLOT_U;
     double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs_rk(Topo t, Phys p, Pool poo
     rhs_dir<R, 2>(u, fb, Fs, z0, g, B, lin, flux, p.mu, dxn, acc);
     const int inst = t.inst[node];
     const double dx = ldexp(p.dx0, -t.level[node]);
-    const double h = dt ? dt[inst] : 0.0;
+    const double h = dt ? node_dt(t, p, dt, node, level) : 0.0;
+    (void)inst;
 #pragma unroll
     for (int kz = 0; kz < RHS_TZ; ++kz) {
       const int k = z0 + kz;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs_rk(Topo t, Phys p, Pool poo
 
 template <class R>
 void launch_rhs_rk_impl(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
-                        double* rhs_out, cudaStream_t st) {
+                        double* rhs_out, cudaStream_t st, int level) {
   const size_t smem = sizeof(R) * NV * RHS_FMAX;
   static bool attr = false;
   if (!attr) {
@@ -176,7 +177,7 @@ void launch_rhs_rk_impl(const Topo& t, const Phys& p, const Pool& pool, int cur,
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rhs_rk<R>, RHS_THREADS, smem);
   if (per_sm < 1) per_sm = 1;
   const int grid = sm_count() * per_sm * (g_tune.stage_waves < 1 ? 1 : g_tune.stage_waves);
-  k_rhs_rk<R><<<grid, RHS_THREADS, smem, st>>>(t, p, pool, cur, stage, dt, rhs_out);
+  k_rhs_rk<R><<<grid, RHS_THREADS, smem, st>>>(t, p, pool, cur, stage, dt, rhs_out, level);
   ++g_kernel_launches;
 }
 

@@ -966,11 +966,11 @@ __device__ __forceinline__ void sweep_z(const double* __restrict__ u, const Topo
 template <int MODE>
 __global__ void __launch_bounds__(SF_THREADS, 2)
     k_stage_f32(Topo t, Phys p, Pool pool, int cur, int stage, const double* __restrict__ dt,
-                double* __restrict__ rhs_out) {
+                double* __restrict__ rhs_out, int level) {
   extern __shared__ __align__(16) float sf_smem[];
   float* S = sf_smem;
   float* Fs = sf_smem + SF_NREC * SF_REG;
-  const int nitems = t.cnt[CNT_NLEAVES] * SF_NSLAB;
+  const int nitems = stage_nodes(t, level) * SF_NSLAB;
   const double* __restrict__ src = pool.buf[cur];
   double* __restrict__ dst = pool.buf[cur ^ 1];
   const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
@@ -1001,7 +1001,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
   const ItemRange IR = item_range(nitems, p.blocked);
   for (int w = IR.first; w < IR.end; w += IR.step) {
     const int li = w / SF_NSLAB, z0 = (w % SF_NSLAB) * SF_TZ;
-    const int node = t.leaves[li];
+    const int node = stage_node(t, level, li);
     const int slot = t.slot[node];
     // the update's per-block scalars, loaded here so that their latency is
     // hidden behind the sweeps (after them in the register-bound selector
@@ -1010,7 +1010,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     double h = 0.0;
     if (MODE != 1) {
       lvl = t.level[node];
-      h = dt ? dt[t.inst[node]] : 0.0;
+      h = dt ? node_dt(t, p, dt, node, level) : 0.0;
     }
     const double* __restrict__ u = src + (size_t)slot * SLOT_U;
     double* __restrict__ fb = pool.face + (size_t)slot * SLOT_F;
@@ -1034,7 +1034,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     }
     if (MODE == 1) {
       lvl = t.level[node];
-      h = dt ? dt[t.inst[node]] : 0.0;
+      h = dt ? node_dt(t, p, dt, node, level) : 0.0;
     }
     // 1 / dx = 2^level / dx0 (exact power-of-two scaling, no division)
     const double idx_ = ldexp(p.inv_dx0, lvl);
@@ -1111,7 +1111,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
 // Launch of one stage-kernel variant on a grid of (CTAs per SM) x SMs.
 template <int MODE>
 static void launch_stage_f32(const Topo& t, const Phys& p, const Pool& pool, int cur, int stage, const double* dt,
-                             double* rhs_out, cudaStream_t st) {
+                             double* rhs_out, cudaStream_t st, int level) {
   const size_t smem = (MODE == 1) ? SF_SMEM_LEARNED : SF_SMEM;
   static int resident = 0;
   if (resident == 0) {
@@ -1121,7 +1121,7 @@ static void launch_stage_f32(const Topo& t, const Phys& p, const Pool& pool, int
     resident = sm_count() * (per_sm < 1 ? 1 : per_sm);
   }
   const int grid = resident * (g_tune.stage_waves < 1 ? 1 : g_tune.stage_waves);
-  k_stage_f32<MODE><<<grid, SF_THREADS, smem, st>>>(t, p, pool, cur, stage, dt, rhs_out);
+  k_stage_f32<MODE><<<grid, SF_THREADS, smem, st>>>(t, p, pool, cur, stage, dt, rhs_out, level);
   ++g_kernel_launches;
 }
 

@@ -53,6 +53,7 @@ class MrbConfig(ctypes.Structure):
         ("mlp_weights", ctypes.c_void_p),
         ("mlp_tau", ctypes.c_double),
         ("stream", ctypes.c_void_p),
+        ("lts", ctypes.c_int32),
     ]
 
 
@@ -141,6 +142,7 @@ def make_config(cfg: RunConfig, stream_ptr: int = 0) -> MrbConfig:
     c.mlp_weights = None
     c.mlp_tau = float(cfg.mlp_tau)
     c.stream = stream_ptr or None
+    c.lts = int(getattr(cfg, "lts", 0))
     return c
 
 

@@ -137,8 +137,8 @@ MUTATIONS = {
     "feature_compression_constant": ("double a = std::log10(1.0 + 1e6 * std::fabs(d)) / 8.0;",
                                      "double a = std::log10(1.0 + 1e5 * std::fabs(d)) / 8.0;",
                                      "test_selector_features_with_the_split_active_match_their_definition[2]"),
-    "lts_schedule": ("      if (r % (1 << (L - l)) != 0) continue;\n      if (nodes_at(C, l, true).empty()) continue;",
-                     "      if (r % (1 << l) != 0) continue;\n      if (nodes_at(C, l, true).empty()) continue;",
+    "lts_schedule": ("      if (r % (1 << (L - l)) != 0) continue;\n      if (nodes_at(C, l, false).empty()) continue;",
+                     "      if (r % (1 << l) != 0) continue;\n      if (nodes_at(C, l, false).empty()) continue;",
                      "test_lts_density_wave_crosses_a_jump"),
     "lts_no_reflux": ("  average_fmac(C);\n  lts_reflux(C);\n  project(C);", "  average_fmac(C);\n  project(C);",
                       "test_lts_conserves_across_jumps[3]"),
