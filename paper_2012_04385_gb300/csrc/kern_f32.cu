@@ -58,8 +58,8 @@ __global__ void __launch_bounds__(256) k_shadow(Topo t, Phys p, Pool pool, int b
     } else {
       node = list[(size_t)w * stride];
     }
-    const double* U = pool.buf[b] + (size_t)t.slot[node] * SLOT_U;
-    float* R = pool.sh[b] + (size_t)t.slot[node] * SLOT_SH;
+    const double* U = pool.bufp(b) + (size_t)t.slot[node] * SLOT_U;
+    float* R = pool.shp(b) + (size_t)t.slot[node] * SLOT_SH;
     if (mode == SH_JUMP) {
       // the plane of cells next to each side whose neighbour is refined
       for (int sd = 0; sd < 6; ++sd) {
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) k_shadow(Topo t, Phys p, Pool pool, int b
 
 void launch_shadow(const Topo& t, const Phys& p, const Pool& pool, int b, int mode, const int32_t* list, int n,
                    int stride, cudaStream_t st) {
-  if (!pool.sh[0]) return;
+  if (!pool.shp(0)) return;
   k_shadow<<<sm_count() * 4, 256, 0, st>>>(t, p, pool, b, mode, list, n, stride);
   ++g_kernel_launches;
 }
@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(256) k_get_records(Topo t, Phys p, Pool pool, 
   const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
   for (int b = blockIdx.x; b < n; b += gridDim.x) {
     const int slot = t.slot[nodes[b]];
-    const double* U = pool.buf[cur] + (size_t)slot * SLOT_U;
-    const float* R = pool.sh[cur] + (size_t)slot * SLOT_SH;
+    const double* U = pool.bufp(cur) + (size_t)slot * SLOT_U;
+    const float* R = pool.shp(cur) + (size_t)slot * SLOT_SH;
     float* o = out + (size_t)b * SLOT_SH;
     for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
       if (fresh) {
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_cfl_f32(Topo t, Phys p, Pool pool, int 
   const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
   for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
     const int node = t.leaves[li];
-    const double* U = pool.buf[cur] + (size_t)t.slot[node] * SLOT_U;
+    const double* U = pool.bufp(cur) + (size_t)t.slot[node] * SLOT_U;
     float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;   // max |u_d| + c, max 1/rho
     bool bad = false;
     for (int e = threadIdx.x; e < NINT; e += blockDim.x) {

@@ -36,7 +36,7 @@ __global__ void k_set_state(Topo t, Phys p, Pool pool, int cur, const int32_t* _
     const double* P = prim + (size_t)b * NV * NINT;
     double rho = P[c], u = P[NINT + c], v = P[2 * NINT + c], w = P[3 * NINT + c], pr = P[4 * NINT + c];
     double q2 = (u * u + v * v) + w * w;
-    double* U = pool.buf[cur] + (size_t)t.slot[nodes[b]] * SLOT_U;
+    double* U = pool.bufp(cur) + (size_t)t.slot[nodes[b]] * SLOT_U;
     const int s = sidx(i, j, k);
     U[s] = rho;
     U[NCELL + s] = rho * u;
@@ -60,7 +60,7 @@ __global__ void k_set_cons(Topo t, Pool pool, int cur, const int32_t* __restrict
     const int b = (int)(e / ((size_t)NV * NINT));
     const int r = (int)(e % ((size_t)NV * NINT));
     const int v = r / NINT, c = r % NINT;
-    double* U = pool.buf[cur] + (size_t)t.slot[nodes[b]] * SLOT_U + (size_t)v * NCELL;
+    double* U = pool.bufp(cur) + (size_t)t.slot[nodes[b]] * SLOT_U + (size_t)v * NCELL;
     U[sidx(c % 16, (c / 16) % 16, c / 256)] = cons[e];
   }
 }
@@ -80,7 +80,7 @@ __global__ void k_get_state(Topo t, Pool pool, int cur, const int32_t* __restric
     const int b = (int)(e / ((size_t)NV * per));
     const int r = (int)(e % ((size_t)NV * per));
     const int v = r / per, c = r % per;
-    const double* U = pool.buf[cur] + (size_t)t.slot[nodes[b]] * SLOT_U + (size_t)v * NCELL;
+    const double* U = pool.bufp(cur) + (size_t)t.slot[nodes[b]] * SLOT_U + (size_t)v * NCELL;
     int s;
     if (with_halo) s = c;
     else s = sidx(c % 16, (c / 16) % 16, c / 256);
@@ -182,8 +182,8 @@ __global__ void k_lts_interp(Topo t, Pool pool, int cur, int below, LevelTheta t
   for (int w = t.cnt[CNT_LVL + 0] + blockIdx.x; w < end; w += gridDim.x) {
     const int node = t.lvl_nodes[w];
     const size_t slot = (size_t)t.slot[node];
-    double* U = pool.buf[cur] + slot * SLOT_U;
-    double* K = pool.buf[cur ^ 1] + slot * SLOT_U;
+    double* U = pool.bufp(cur) + slot * SLOT_U;
+    double* K = pool.bufp(cur ^ 1) + slot * SLOT_U;
     const double* N = pool.un + slot * SLOT_N;
     const double q = th.th[t.level[node]];
     for (int e = threadIdx.x; e < NV * NINT; e += blockDim.x) {
@@ -212,16 +212,16 @@ __global__ void k_lts_copyback(Topo t, Pool pool, int cur, int level) {
   const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
   for (int w = beg + blockIdx.x; w < end; w += gridDim.x) {
     const size_t slot = (size_t)t.slot[t.lvl_nodes[w]];
-    double* U = pool.buf[cur] + slot * SLOT_U;
-    const double* O = pool.buf[cur ^ 1] + slot * SLOT_U;
+    double* U = pool.bufp(cur) + slot * SLOT_U;
+    const double* O = pool.bufp(cur ^ 1) + slot * SLOT_U;
     for (int e = threadIdx.x; e < NV * NINT; e += blockDim.x) {
       const int v = e / NINT, ii = e % NINT;
       const int s = v * NCELL + sidx(ii % 16, (ii / 16) % 16, ii / 256);
       U[s] = O[s];
     }
-    if (pool.sh[0]) {
-      float* R = pool.sh[cur] + slot * SLOT_SH;
-      const float* Q = pool.sh[cur ^ 1] + slot * SLOT_SH;
+    if (pool.shp(0)) {
+      float* R = pool.shp(cur) + slot * SLOT_SH;
+      const float* Q = pool.shp(cur ^ 1) + slot * SLOT_SH;
       for (int e = threadIdx.x; e < SLOT_SH; e += blockDim.x) R[e] = Q[e];
     }
   }
@@ -267,7 +267,7 @@ __global__ void k_lts_reflux(Topo t, Phys p, Pool pool, int cur) {
     const int node = t.leaves[li];
     const double* Fc_all = pool.fmac + (size_t)t.slot[node] * SLOT_F;
     const double dx = ldexp(p.dx0, -t.level[node]);
-    double* U = pool.buf[cur] + (size_t)t.slot[node] * SLOT_U;
+    double* U = pool.bufp(cur) + (size_t)t.slot[node] * SLOT_U;
 #pragma unroll 1
     for (int s = 0; s < 6; ++s) {
       const int d = s / 2, hi = s & 1;
@@ -319,7 +319,7 @@ __global__ void k_jump(Topo t, Phys p, Pool pool, int target, int stage, const d
     const double dx = ldexp(p.dx0, -t.level[node]);
     const double h = dt ? dt[t.inst[node]] : 0.0;
     const double bs = kRkB[rk_row(p)][stage];
-    double* U = pool.buf[target] + (size_t)t.slot[node] * SLOT_U;
+    double* U = pool.bufp(target) + (size_t)t.slot[node] * SLOT_U;
 #pragma unroll 1
     for (int s = 0; s < 6; ++s) {
       const int d = s / 2, hi = s & 1;
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(256) k_cfl(Topo t, Phys p, Pool pool, int cur,
   const int nleaves = t.cnt[CNT_NLEAVES];
   for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
     const int node = t.leaves[li];
-    const double* U = pool.buf[cur] + (size_t)t.slot[node] * SLOT_U;
+    const double* U = pool.bufp(cur) + (size_t)t.slot[node] * SLOT_U;
     double m[4] = {0.0, 0.0, 0.0, 0.0};   // max |u_d| + c per direction, max 1/rho
     bool bad = false;
     for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(256) k_flux_census(Topo t, Phys p, Pool pool, 
     cl[(d == 2) ? 1 : 2] = b;
     const int step[3] = {1, NS, NS * NS};
     const int sL = sidx(cl[0], cl[1], cl[2]), sR = sL + step[d];
-    const double* U = pool.buf[cur] + (size_t)t.slot[t.leaves[li]] * SLOT_U;
+    const double* U = pool.bufp(cur) + (size_t)t.slot[t.leaves[li]] * SLOT_U;
     double UL[5], UR[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(256) k_sums_partial(Topo t, Phys p, Pool pool,
   const int nleaves = t.cnt[CNT_NLEAVES];
   for (int li = blockIdx.x; li < nleaves; li += gridDim.x) {
     const int node = t.leaves[li];
-    const double* U = pool.buf[cur] + (size_t)t.slot[node] * SLOT_U;
+    const double* U = pool.bufp(cur) + (size_t)t.slot[node] * SLOT_U;
     double s[5] = {0, 0, 0, 0, 0};
     for (int e = threadIdx.x; e < NINT; e += blockDim.x) {
       const int c = sidx(e % 16, (e / 16) % 16, e / 256);

@@ -120,6 +120,11 @@ struct Pool {
   // boundary-face fluxes integrated over a macro time step (local time
   // stepping only), [slot][6][5][16][16]
   double* fmac;
+  // The arrays of stage buffer b, chosen by selection: indexing the arrays
+  // above with a run-time b would make the compiler copy the whole kernel
+  // parameter into local memory and read the pointers back from there.
+  __host__ __device__ __forceinline__ double* bufp(int b) const { return b ? buf[1] : buf[0]; }
+  __host__ __device__ __forceinline__ float* shp(int b) const { return b ? sh[1] : sh[0]; }
 };
 
 __device__ __forceinline__ double ldexp_(double x, int e) { return ldexp(x, e); }

@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(SF_THREADS) k_face_samples(Topo t, Phys p, Poo
     // neighbour reads
     const int slot = t.slot[t.leaves[li]];
     RegionSrc RS;
-    RS.u = pool.buf[cur] + (size_t)slot * SLOT_U;
-    RS.sh = pool.sh[cur] ? pool.sh[cur] + (size_t)slot * SLOT_SH : nullptr;
+    RS.u = pool.bufp(cur) + (size_t)slot * SLOT_U;
+    RS.sh = pool.shp(cur) ? pool.shp(cur) + (size_t)slot * SLOT_SH : nullptr;
 #pragma unroll
     for (int q = 0; q < 6; ++q) RS.nsh[q] = nullptr;
 #pragma unroll 1

@@ -163,7 +163,7 @@ template <class R>
 __global__ void __launch_bounds__(256) k_fill_regions_t(Topo t, Pool pool, int cur, NodeSet ns, int mode) {
   int beg, cnt;
   nodeset_range(t, ns, beg, cnt);
-  double* buf = pool.buf[cur];
+  double* buf = pool.bufp(cur);
   const int nitems = cnt * 26;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) k_fill_predict_t(Topo t, Pool pool, int c
   __shared__ unsigned rmask;
   int beg, cnt;
   nodeset_range(t, ns, beg, cnt);
-  double* buf = pool.buf[cur];
+  double* buf = pool.bufp(cur);
   for (int w = blockIdx.x; w < cnt; w += gridDim.x) {
     const int node = nodeset_node(t, ns, beg, w);
     const int par = t.parent[node];
@@ -310,7 +310,7 @@ static __global__ void __launch_bounds__(256) k_fill_bc(Topo t, Phys p, Pool poo
     beg = t.cnt[CNT_BC + ns.level];
     cnt = t.cnt[CNT_BC + ns.level + 1] - beg;
   }
-  double* buf = pool.buf[cur];
+  double* buf = pool.bufp(cur);
   constexpr int NCHUNK = 9;                  // 2304 slab cells = 9 chunks of 256
   const int nitems = cnt * NCHUNK;
   const int lane = threadIdx.x & 31;
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(256) k_delta_t(Topo t, Phys p, Pool pool, int 
   __shared__ double sh[8];
   __shared__ R box[4096];           // the parent's cells 8 cb - 4 .. 8 cb + 11 per axis, one variable
   const int nitems = all_nodes ? t.cnt[CNT_NNODES] : t.cnt[CNT_NLEAVES];
-  const double* B = pool.buf[cur];
+  const double* B = pool.bufp(cur);
   for (int li = blockIdx.x; li < nitems; li += gridDim.x) {
     const int node = all_nodes ? li : t.leaves[li];
     const int lvl = t.level[node];
@@ -460,7 +460,7 @@ template <class R>
 __global__ void __launch_bounds__(256) k_refine_fill_t(Topo t, Pool pool, int cur, const int32_t* __restrict__ pairs,
                                                       int n) {
   __shared__ R box[4096];           // the parent's cells 8 cb - 4 .. 8 cb + 11 per axis, one variable
-  double* B = pool.buf[cur];
+  double* B = pool.bufp(cur);
   const int nitems = n * NV;
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int child = pairs[2 * (w / NV)], par = pairs[2 * (w / NV) + 1];
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(256) k_refine_fill_t(Topo t, Pool pool, int cu
 // (internal node, octant): the octant's 512 parent cells come from one child.
 static __global__ void __launch_bounds__(256) k_project_octants(Topo t, Pool pool, int buf, int level) {
   const int beg = t.cnt[CNT_LVL + level], end = t.cnt[CNT_LVL + level + 1];
-  double* B = pool.buf[buf];
+  double* B = pool.bufp(buf);
   const int nitems = (end - beg) * 8;
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int node = t.lvl_nodes[beg + w / 8];

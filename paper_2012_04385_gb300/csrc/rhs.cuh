@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs_rk(Topo t, Phys p, Pool poo
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* Fs = reinterpret_cast<R*>(smem_raw);
   const int nitems = stage_nodes(t, level) * RHS_NSLAB;
-  const double* __restrict__ src = pool.buf[cur];
-  double* __restrict__ dst = pool.buf[cur ^ 1];
+  const double* __restrict__ src = pool.bufp(cur);
+  double* __restrict__ dst = pool.bufp(cur ^ 1);
   const R g = R(p.gamma), B = R(p.B);
   const int lin = p.recon;   // reconstruction mode: 0 WENO5, 2 linear, 3 TENO5, 4 WENO-AO(5,3)
   const int flux = p.flux;   // FLUX_ROE, FLUX_LLF or FLUX_HLLC

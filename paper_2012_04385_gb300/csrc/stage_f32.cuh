@@ -724,13 +724,13 @@ __device__ __forceinline__ void load_xy_f32(const RegionSrc& R, float* __restric
 // buffer `cur`).
 __device__ __forceinline__ RegionSrc region_src(const Topo& t, const Pool& pool, int cur, int node, int slot) {
   RegionSrc R;
-  R.u = pool.buf[cur] + (size_t)slot * SLOT_U;
-  R.sh = pool.sh[cur] ? pool.sh[cur] + (size_t)slot * SLOT_SH : nullptr;
+  R.u = pool.bufp(cur) + (size_t)slot * SLOT_U;
+  R.sh = pool.shp(cur) ? pool.shp(cur) + (size_t)slot * SLOT_SH : nullptr;
   const int rn[6] = {12, 14, 10, 16, 4, 22};
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     const int nb = R.sh ? t.nbr[(size_t)node * 27 + rn[q]] : -1;
-    R.nsh[q] = (nb >= 0) ? pool.sh[cur] + (size_t)t.slot[nb] * SLOT_SH : nullptr;
+    R.nsh[q] = (nb >= 0) ? pool.shp(cur) + (size_t)t.slot[nb] * SLOT_SH : nullptr;
   }
   return R;
 }
@@ -895,7 +895,10 @@ __device__ __forceinline__ void sweep_f32(int D, const Topo& t, const Pool& pool
 }
 
 // x and y directions of the slab together (MODES 0, 2, 3): one region, one
-// loop over the 1088 x faces followed by the 1088 y faces.
+// loop over the 1088 x faces followed by the 1088 y faces, through a single
+// call site of the face flux (the two directions differ only in the stencil
+// stride and the rotation's offsets, so one inlined copy serves both; 1.5%
+// faster than one copy per direction).
 template <int MODE>
 __device__ __forceinline__ void sweep_xy(const double* __restrict__ u, const Topo& t, const Pool& pool, int cur,
                                          int node, int slot, double* __restrict__ fb, float* __restrict__ S,
@@ -906,23 +909,33 @@ __device__ __forceinline__ void sweep_xy(const double* __restrict__ u, const Top
   __syncthreads();
   for (int f = threadIdx.x; f < 2 * SF_NFX; f += blockDim.x) {
     float F[5];
-    if (f < SF_NFX) {                     // x face: warp-uniform (1088 = 34 warps)
-      const int fa = f % 17, r = f / 17;  // r = kz * 16 + j
-      const int c0 = xy_slot(fa - 3, r % 16, r / 16);
-      const bool lin = (MODE == 3) && ((L.selw[f >> 5] >> (threadIdx.x & 31)) & 1u);
-      face_flux_f32<MODE, false>(S, c0, 1, rot_of(0), gm1, g, B, lin, F);
-      if (MODE & 32) sub_viscous_f32<0>(u, sidx(fa - 1, r % 16, z0 + r / 16), L.mu, L.idx, F);
-      store_face(0, F, Fs, SF_FMAX, f, fa, r % 16, z0 + r / 16, fb);
-    } else {                              // y face
+    const bool isx = f < SF_NFX;          // warp-uniform (1088 = 34 warps)
+    int fa, c0, ta, tb, st, wi;
+    if (isx) {
+      fa = f % 17;
+      const int r = f / 17;               // r = kz * 16 + j
+      c0 = xy_slot(fa - 3, r % 16, r / 16);
+      ta = r % 16;
+      tb = z0 + r / 16;
+      st = 1;
+      wi = f >> 5;
+    } else {
       const int fy = f - SF_NFX;
       const int i = fy % 16, r = fy / 16; // r = kz * 17 + fa
-      const int fa = r % 17, kz = r / 17;
-      const int c0 = xy_slot(i, fa - 3, kz);
-      const bool lin = (MODE == 3) && ((L.selw[34 + (fy >> 5)] >> (threadIdx.x & 31)) & 1u);
-      face_flux_f32<MODE, false>(S, c0, 24, rot_of(1), gm1, g, B, lin, F);
-      if (MODE & 32) sub_viscous_f32<1>(u, sidx(i, fa - 1, z0 + kz), L.mu, L.idx, F);
-      store_face(1, F, Fs, SF_FMAX, f, fa, i, z0 + kz, fb);
+      fa = r % 17;
+      c0 = xy_slot(i, fa - 3, r / 17);
+      ta = i;
+      tb = z0 + r / 17;
+      st = 24;
+      wi = 34 + (fy >> 5);
     }
+    const bool lin = (MODE == 3) && ((L.selw[wi] >> (threadIdx.x & 31)) & 1u);
+    face_flux_f32<MODE, false>(S, c0, st, isx ? rot_of(0) : rot_of(1), gm1, g, B, lin, F);
+    if (MODE & 32) {
+      if (isx) sub_viscous_f32<0>(u, sidx(fa - 1, ta, tb), L.mu, L.idx, F);
+      else sub_viscous_f32<1>(u, sidx(ta, fa - 1, tb), L.mu, L.idx, F);
+    }
+    store_face(isx ? 0 : 1, F, Fs, SF_FMAX, f, fa, ta, tb, fb);
   }
   __syncthreads();
 #pragma unroll
@@ -971,8 +984,8 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
   float* S = sf_smem;
   float* Fs = sf_smem + SF_NREC * SF_REG;
   const int nitems = stage_nodes(t, level) * SF_NSLAB;
-  const double* __restrict__ src = pool.buf[cur];
-  double* __restrict__ dst = pool.buf[cur ^ 1];
+  const double* __restrict__ src = pool.bufp(cur);
+  double* __restrict__ dst = pool.bufp(cur ^ 1);
   const float g = (float)p.gamma, B = (float)p.B, gm1 = (float)(p.gamma - 1.0);
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   __shared__ uint32_t sel_sh[108];
@@ -1095,10 +1108,10 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
             o5[v] = out;
           }
           // the FP32 records of the new state, read by the next stage's regions
-          if (pool.sh[cur ^ 1]) {
+          if (pool.shp(cur ^ 1)) {
             float rec[6];
             make_record(o5[0], o5[1], o5[2], o5[3], o5[4], g, B, gm1, rec);
-            float* __restrict__ shw = pool.sh[cur ^ 1] + (size_t)slot * SLOT_SH;
+            float* __restrict__ shw = pool.shp(cur ^ 1) + (size_t)slot * SLOT_SH;
 #pragma unroll
             for (int f = 0; f < SF_NREC; ++f) shw[f * NINT + ii] = rec[f];
           }
