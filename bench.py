@@ -260,11 +260,11 @@ def roofline_numbers(linear_fraction=0.0, split=None, table=None):
 # DRAM bytes (read + write) per leaf cell of one launch of the stage kernels
 # on the shock-bubble workload (levels 0..4, 5,720 leaves), from the
 # full-size ncu capture summarised in
-# profiles/stage_kernels_shock_bubble_512.md.  The learned path's figure is
-# the mean over one step (k_stage_f32<1> 228.1, k_stage_f32<3> 230.1 twice),
-# the WENO5 path's that of k_stage_f32<0> (234.9 at stage 0, 232.1 at stages
-# 1 and 2); traffic grows in proportion to the leaf cells of a launch.
-TRAFFIC_BYTES_PER_CELL = {"learned": 229.4, "weno": 233.1}
+# profiles/stage_kernels_shock_bubble_512.md: the mean over one step, for the
+# learned path k_stage_f32<1> (247.2) and k_stage_f32<3> twice (219.9), for
+# the WENO5 path k_stage_f32<0> (248.5 at stage 0, 222.8 at stages 1 and 2).
+# Traffic grows in proportion to the leaf cells of a launch.
+TRAFFIC_BYTES_PER_CELL = {"learned": 229.0, "weno": 231.3}
 
 
 def measured_peaks():

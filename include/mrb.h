@@ -137,8 +137,10 @@ typedef struct mrb_ctx mrb_ctx;
  * step (432 words); with precision MRB_FP32_ACC64 also FP32 primitive
  * records (rho, u, v, w, p, E) of the internal cells of both stage buffers
  * (2 x 6 x 16^3 floats), which the mixed-precision stage kernel reads instead
- * of converting the FP64 state.  Each region 256-byte aligned.  Returns 0 for
- * a bad config. */
+ * of converting the FP64 state, and the FP32 increment u^(s) - u^n of the
+ * current RK stage (5 x 16^3 floats); with lts also the integrated boundary-face
+ * fluxes of a macro step (6 x 5 x 16^2 doubles).  Each region 256-byte
+ * aligned.  Returns 0 for a bad config. */
 size_t mrb_pool_bytes(const mrb_config* cfg, int64_t n_slots);
 
 /* Create a context: checks the config, builds the level-0 topology of every

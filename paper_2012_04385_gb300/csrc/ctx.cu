@@ -553,7 +553,7 @@ size_t mrb_pool_bytes(const mrb_config* cfg, int64_t n_slots) {
   if (check_config(cfg) != MRB_OK || n_slots <= 0) return 0;
   const size_t n = (size_t)n_slots;
   // the mixed-precision path also keeps FP32 records of both stage buffers' internal cells
-  const size_t sh = (cfg->precision == MRB_FP32_ACC64) ? align256(n * SLOT_SH * 4) * 2 : 0;
+  const size_t sh = (cfg->precision == MRB_FP32_ACC64) ? align256(n * SLOT_SH * 4) * 2 + align256(n * SLOT_N * 4) : 0;
   // local time stepping also keeps the boundary-face fluxes integrated over a macro step
   const size_t fm = cfg->lts ? align256(n * SLOT_F * 8) : 0;
   return align256(n * SLOT_U * 8) * 2 + align256(n * SLOT_N * 8) + align256(n * SLOT_F * 8) + align256(n * SLOT_SEL * 4) +
@@ -603,6 +603,8 @@ int mrb_init_blocks(const mrb_config* cfg, void* pool, size_t pool_bytes, mrb_ct
       q += align256(n * SLOT_SH * 4);
       c->P.sh[1] = (float*)q;
       q += align256(n * SLOT_SH * 4);
+      c->P.dl = (float*)q;
+      q += align256(n * SLOT_N * 4);
     }
     c->P.fmac = nullptr;
     if (cfg->lts) c->P.fmac = (double*)q;

@@ -348,6 +348,8 @@ __global__ void k_jump(Topo t, Phys p, Pool pool, int target, int stage, const d
           } else {
             double& ur = U[v * NCELL + sidx(c[0], c[1], c[2])];
             ur = ur + bs * (h * dL);
+            // the mixed-precision path's FP32 stage increment follows the correction
+            if (pool.dl) pool.dl[(size_t)t.slot[node] * SLOT_N + v * NINT + iidx(c[0], c[1], c[2])] += (float)(bs * (h * dL));
           }
         }
       }

@@ -120,6 +120,9 @@ struct Pool {
   // boundary-face fluxes integrated over a macro time step (local time
   // stepping only), [slot][6][5][16][16]
   double* fmac;
+  // FP32 increments u^(s) - u^n of the stage (mixed-precision path only, null
+  // otherwise), [slot][5][16^3]
+  float* dl;
   // The arrays of stage buffer b, chosen by selection: indexing the arrays
   // above with a run-time b would make the compiler copy the whole kernel
   // parameter into local memory and read the pointers back from there.

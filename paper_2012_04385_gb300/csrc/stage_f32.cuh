@@ -1,25 +1,34 @@
 // Mixed-precision fused stage kernel (MRB_FP32_ACC64): characteristic WENO5-JS
 // with the Roe / local Lax-Friedrichs switch (Sec. 2.2 of arXiv:2012.04385) in
 // FP32, flux differences accumulated per cell in FP32, and the Runge-Kutta
-// stage update of the FP64 state in FP64.  The same kernel template covers the
-// other reconstructions (TENO5, WENO-AO(5,3), linear, the learned selector),
-// the LLF and HLLC flux schemes and the viscous terms (see rec5 and MODE).
+// stage update of the FP64 state with one FP64 addition per value.  The same
+// kernel template covers the other reconstructions (TENO5, WENO-AO(5,3),
+// linear, the learned selector), the LLF and HLLC flux schemes and the
+// viscous terms (see rec5 and MODE).
 //
 // Work item = (leaf, z-slab of 16 x 16 x 4 cells); a CTA of 256 threads loops
-// over items.  The FP64 stage buffer is converted into FP32 primitive records
-// (rho, vx, vy, vz, p, E) in shared memory: for the x and y directions one
-// region holds the slab with 3 cells on each side in x and in y (the slab's
-// own cells are converted once for both), for z the slab with 3 planes
-// below and above.  One thread per face then computes the face flux from six
-// records (velocity read in the direction's frame: normal, tangential 1,
-// tangential 2), writes it to shared memory (and, on the block boundary, to
-// the block's face buffers), and each thread adds the flux differences of the
-// four cells of its (i, j) column.  The x and y faces form one loop of
-// 2 x 1088 faces (34 warps each, so every warp has one direction).
-// Reciprocals and square roots use the fast hardware approximations; WENO5
-// works on the consecutive differences of its five values and needs one
-// reciprocal: omega_k = d_k P_k / sum_j d_j P_j with P_k the product of the
-// other two (eps + beta)^2.
+// over items.  Every node keeps FP32 primitive records (rho, vx, vy, vz, p, E)
+// of its internal cells beside its FP64 state, written by the previous
+// stage's update; the kernel copies the records of a region into shared
+// memory with 16-byte asynchronous copies (the block's own stored halo,
+// converted from FP64, where a face has no same-level neighbour): for the x
+// and y directions one region holds the slab with 3 cells on each side in x
+// and in y, for z the slab with 3 planes below and above.  One thread per
+// face then computes the face flux from six records (velocity read in the
+// direction's frame: normal, tangential 1, tangential 2), writes it to shared
+// memory (and, on the block boundary, to the block's face buffers), and each
+// thread adds the flux differences of the four cells of its (i, j) column.
+// The x and y faces form one loop of 2 x 1088 faces (34 warps each, so every
+// warp has one direction).  Reciprocals and square roots use the fast
+// hardware approximations; WENO5 works on the consecutive differences of its
+// five values and needs one reciprocal: omega_k = d_k P_k / sum_j d_j P_j with
+// P_k the product of the other two (eps + beta)^2.
+//
+// The update keeps the stage's increment u^(s) - u^n of every cell in FP32
+// (pool.dl).  With a_s + b_s = 1 the Shu-Osher stage u^(s+1) = a_s u^n + b_s
+// (u^(s) + dt L) is u^n + b_s (increment + dt L): the new increment is formed
+// in FP32 and added to u^n in FP64, one FP64 operation per value, where the
+// FP64 pipe (1/64 of the FP32 rate on GB300) is the update's bottleneck.
 #pragma once
 
 #include "convert.cuh"
@@ -840,11 +849,15 @@ __device__ __forceinline__ void sweep_f32(int D, const Topo& t, const Pool& pool
                                           int z0, float g, float B, float gm1, float (&acc)[SF_TZ][NV],
                                           const LearnedCtx& L) {
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
-  // same-level face neighbours along D read directly (their records)
-  load_region_f32(D, region_src(t, pool, cur, node, slot), S, z0, g, B, gm1);
-  __syncthreads();
+  // the x-y region serves the x and the y faces (loaded for D = 0 and kept
+  // for D = 1), the z region the z faces
+  if (D != 1) {
+    if (D == 0) load_xy_f32(region_src(t, pool, cur, node, slot), S, z0, g, B, gm1);
+    else load_region_f32(2, region_src(t, pool, cur, node, slot), S, z0, g, B, gm1);
+    __syncthreads();
+  }
   const int nf = region_faces(D);
-  const int st = region_stride(D);
+  const int st = sel3i(D, 1, 24, 256);
   const Rot R = rot_of(D);
   const int nfr = ((nf + blockDim.x - 1) / blockDim.x) * blockDim.x;
   for (int f0 = threadIdx.x; f0 < nfr; f0 += blockDim.x) {
@@ -852,6 +865,8 @@ __device__ __forceinline__ void sweep_f32(int D, const Topo& t, const Pool& pool
     const int f = act ? f0 : 0;
     int fa, c0, ta, tb;
     face_of(D, f, z0, fa, c0, ta, tb);
+    if (D == 0) c0 = xy_slot(fa - 3, (f / 17) % 16, f / 17 / 16);
+    else if (D == 1) c0 = xy_slot(f % 16, fa - 3, f / 16 / 17);
     // decision word of this warp's 32 consecutive faces
     uint32_t* word = L.bits + (z0 / SF_TZ) * 108 + D * 34 + (f0 >> 5);
     // WENO5 fluxes and the selector's features of the same faces; flat
@@ -1052,10 +1067,14 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     // 1 / dx = 2^level / dx0 (exact power-of-two scaling, no division)
     const double idx_ = ldexp(p.inv_dx0, lvl);
     const double hdx = h * idx_;
-    // the stage increment b_s dt / dx (sum of flux differences) is formed in
-    // FP32 and accumulated into the FP64 state
+    // the stage's increment is formed in FP32: b_s dt / dx (sum of flux
+    // differences) at stage 0, b_s (previous increment + dt / dx sum) after it
+    // (read in place of u^(s), in the low word of its operand's register);
+    // with gravity the FP64 combination a_s u^n + b_s (u^(s) + dt L) is kept
+    // and the increment taken from its result
     const double ka = kRkA[rk_row(p)][stage], kb = kRkB[rk_row(p)][stage];
-    const float hf = d2f_fast(hdx), bhf = d2f_fast(kb * hdx);
+    const float hf = d2f_fast(hdx), bhf = d2f_fast(kb * hdx), kbf = d2f_fast(kb);
+    const bool incr = pool.dl && stage != 0 && !rhs_out && !p.has_grav;
     // the thread's four cells in groups of KC: every FP64 operand of a group is
     // loaded before its first store, so those loads are in flight together
     // (groups of one cell in the register-bound selector variant)
@@ -1068,7 +1087,9 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
         const int s = sidx(ti, tj, z0 + k0 + c), ii = iidx(ti, tj, z0 + k0 + c);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          us[c][v] = u[v * NCELL + s];
+          us[c][v] = incr ? __longlong_as_double((long long)(unsigned)__float_as_uint(
+                                pool.dl[(size_t)slot * SLOT_N + v * NINT + ii]))
+                           : u[v * NCELL + s];
           un[c][v] = (stage != 0 && !rhs_out) ? pool.un[(size_t)slot * SLOT_N + v * NINT + ii] : 0.0;
         }
       }
@@ -1090,6 +1111,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
             rhs_out[((size_t)li * NV + v) * NINT + ii] = fma(f2d_fast(acc[kz][v]), idx_, S4[v]);
         } else {
           double* __restrict__ unb = pool.un + (size_t)slot * SLOT_N;
+          float* __restrict__ dlw = pool.dl ? pool.dl + (size_t)slot * SLOT_N : nullptr;
           double* __restrict__ o = dst + (size_t)slot * SLOT_U;
           double o5[5];
 #pragma unroll
@@ -1097,12 +1119,20 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
             double out;
             if (stage == 0) {
               unb[v * NINT + ii] = us[c][v];
-              out = us[c][v] + f2d_fast(acc[kz][v] * hf);
+              const float d = acc[kz][v] * hf;
+              out = us[c][v] + f2d_fast(d);
               if (p.has_grav) out = fma(h, S4[v], out);
+              if (dlw) dlw[v * NINT + ii] = p.has_grav ? d2f_fast(out - us[c][v]) : d;
+            } else if (incr) {
+              const float dp = __uint_as_float((unsigned)__double_as_longlong(us[c][v]));
+              const float d = fmaf(kbf, dp, acc[kz][v] * bhf);
+              out = un[c][v] + f2d_fast(d);
+              dlw[v * NINT + ii] = d;
             } else {
               double inc = f2d_fast(acc[kz][v] * bhf);
               if (p.has_grav) inc = fma(kb * h, S4[v], inc);
               out = fma(ka, un[c][v], fma(kb, us[c][v], inc));
+              if (dlw) dlw[v * NINT + ii] = d2f_fast(out - un[c][v]);
             }
             o[v * NCELL + s] = out;
             o5[v] = out;

@@ -43,6 +43,11 @@ def test_pool_bytes_and_config_checks():
     b8 = mrb.pool_bytes(cfg, 8)
     per_slot = (2 * 5 * 24 ** 3 + 5 * 16 ** 3 + 6 * 5 * 256) * 8 + 432 * 4
     assert b8 >= 8 * per_slot and b8 < 8 * per_slot + 4 * 256
+    # the mixed-precision path adds the FP32 records of both stage buffers and
+    # the FP32 stage increments
+    per32 = per_slot + (2 * 6 * 16 ** 3 + 5 * 16 ** 3) * 4
+    b32 = mrb.pool_bytes(I.sod_config(precision=I.FP32_ACC64), 8)
+    assert b32 >= 8 * per32 and b32 < 8 * per32 + 7 * 256
     assert b1 > 0
     bad = I.sod_config(bc=(1, 0, 1, 1, 1, 1))          # periodic on one side only
     assert mrb.pool_bytes(bad, 8) == 0
