@@ -172,7 +172,7 @@ def _shard_worker(rank, world, port, q):
     dist.init_process_group("gloo")
     cfg = I.ensemble_config(n=5, lmax=(1, 2, 1, 2, 1))
     mine = shard.instance_shards(cfg, world)[rank]
-    sums = _oracle_ensemble_sums(shard.shard_config(cfg, mine), shard.shard_ic(I.ic_ensemble, mine), 2)
+    sums = _oracle_ensemble_sums(shard.shard_config(cfg, mine), shard.shard_ic(I.ic_ensemble, mine), 1)
     gathered = [None] * world
     dist.all_gather_object(gathered, (mine, sums.tolist()))
     q.put((rank, gathered))
@@ -182,7 +182,7 @@ def _shard_worker(rank, world, port, q):
 def test_ensemble_sharded_by_instance_over_two_ranks():
     """The batched ensemble splits by instance with no exchange: two gloo
     ranks each run their instances (the oracle standing in for each rank's
-    GPU), and the gathered per-instance conserved totals after two MR steps
+    GPU), and the gathered per-instance conserved totals after one MR step
     equal those of one batched run of the whole ensemble bit for bit.  The
     partition covers every instance once and balances the effective cells."""
     import numpy as np
@@ -214,5 +214,5 @@ def test_ensemble_sharded_by_instance_over_two_ranks():
     got = np.zeros((5, 5))
     for mine, sums in out[0]:
         got[mine] = np.array(sums)
-    ref = _oracle_ensemble_sums(cfg, I.ic_ensemble, 2)
+    ref = _oracle_ensemble_sums(cfg, I.ic_ensemble, 1)
     assert np.array_equal(got, ref)
