@@ -324,6 +324,18 @@ int mrb_learned_stats(mrb_ctx* ctx, int64_t* linear_faces, int64_t* evaluated_fa
  * logits_dev [n]; asynchronous on `stream`.  No context needed. */
 int mrb_mlp_logits(const float* params_dev, const float* feats_dev, int64_t n, float* logits_dev, void* stream);
 
+/* Threshold of the selector's decisions: the q-quantile of the logits of the
+ * samples with label 1 (logits_dev [n] float, labels_dev [n] bytes, device),
+ * interpolated linearly between the order statistics around position
+ * (m - 1) q of the m label-1 logits in ascending order, into *tau_out (host).
+ * With q = the tolerated share of label-1 faces sent to the linear scheme,
+ * logit < tau selects it.  0 when no sample has label 1.  work_dev: device
+ * scratch of MRB_THRESHOLD_WORK uint64.  Synchronises `stream`.  EINVAL for
+ * q outside [0, 1] or null pointers with n > 0. */
+#define MRB_THRESHOLD_WORK 256
+int mrb_mlp_threshold(const float* logits_dev, const uint8_t* labels_dev, int64_t n, double q, uint64_t* work_dev,
+                      float* tau_out, void* stream);
+
 /* One training step of the selector on n samples: forward and backward with
  * BF16-rounded inputs, weights and hidden activations and FP32 accumulation,
  * loss = mean over samples of the binary cross-entropy with logits weighted

@@ -1,6 +1,7 @@
 // Learned reconstruction selector: training-data generation from the solver's
 // own faces, training (forward and backward of the BF16-operand perceptron
 // with FP32 accumulation, Adam), and tensor-core inference.  See learned.cuh.
+#include <cstring>
 #include <algorithm>
 
 #include "learned.cuh"
@@ -317,6 +318,95 @@ extern "C" int mrb_mlp_logits(const float* params_dev, const float* feats_dev, i
   k_mlp_logits<<<grid, 256, 0, (cudaStream_t)stream>>>(params_dev, feats_dev, n, logits_dev);
   ++g_kernel_launches;
   return cudaGetLastError() == cudaSuccess ? MRB_OK : MRB_ECUDA;
+}
+
+// ---------------------------------------------------------------- threshold
+// Order statistics of the logits of label-1 samples by radix selection on
+// the float's order-preserving 32-bit key, eight bits per pass (most
+// significant first): each pass histograms the next digit of the keys that
+// share the digits chosen so far.
+__device__ __forceinline__ uint32_t order_key(float x) {
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+static float key_value(uint32_t k) {
+  const uint32_t b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+  float x;
+  std::memcpy(&x, &b, sizeof x);
+  return x;
+}
+
+__global__ void __launch_bounds__(256) k_key_hist(const float* __restrict__ z, const uint8_t* __restrict__ y,
+                                                  int64_t n, uint32_t prefix, int shift,
+                                                  unsigned long long* __restrict__ hist) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!y[i]) continue;
+    const uint32_t k = order_key(z[i]);
+    if (shift < 24 && (k >> (shift + 8)) != (prefix >> (shift + 8))) continue;
+    atomicAdd(&h[(k >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+}
+
+// The kth smallest (from 0) label-1 logit; *m receives the number of label-1
+// samples (from the first pass).
+static int select_kth(const float* z, const uint8_t* y, int64_t n, int64_t kth, unsigned long long* hist,
+                      cudaStream_t st, float* out, int64_t* m) {
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 4);
+  uint32_t prefix = 0;
+  unsigned long long h[256];
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    if (cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), st) != cudaSuccess) return MRB_ECUDA;
+    k_key_hist<<<grid, 256, 0, st>>>(z, y, n, prefix, shift, hist);
+    ++g_kernel_launches;
+    if (cudaMemcpyAsync(h, hist, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return MRB_ECUDA;
+    if (shift == 24) {
+      int64_t total = 0;
+      for (int d = 0; d < 256; ++d) total += (int64_t)h[d];
+      *m = total;
+      if (kth >= total) return MRB_EINVAL;
+    }
+    int d = 0;
+    for (; d < 256; ++d) {
+      if (kth < (int64_t)h[d]) break;
+      kth -= (int64_t)h[d];
+    }
+    prefix |= (uint32_t)d << shift;
+  }
+  *out = key_value(prefix);
+  return MRB_OK;
+}
+
+extern "C" int mrb_mlp_threshold(const float* logits_dev, const uint8_t* labels_dev, int64_t n, double q,
+                                 uint64_t* work_dev, float* tau_out, void* stream) {
+  if (!tau_out || n < 0 || !(q >= 0.0 && q <= 1.0) || (n > 0 && (!logits_dev || !labels_dev || !work_dev)))
+    return MRB_EINVAL;
+  *tau_out = 0.f;
+  if (n == 0) return MRB_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* hist = reinterpret_cast<unsigned long long*>(work_dev);
+  // count the label-1 samples with a first selection of the smallest one
+  float lo = 0.f;
+  int64_t m = 0;
+  int rc = select_kth(logits_dev, labels_dev, n, 0, hist, st, &lo, &m);
+  if (rc == MRB_EINVAL && m == 0) return MRB_OK;     // no label-1 sample: threshold 0
+  if (rc != MRB_OK) return rc;
+  // linear interpolation between the order statistics around (m - 1) q
+  const double pos = (double)(m - 1) * q;
+  const int64_t k = (int64_t)pos;
+  const float frac = (float)(pos - (double)k);
+  float a = lo, b = lo;
+  if (k > 0 && (rc = select_kth(logits_dev, labels_dev, n, k, hist, st, &a, &m)) != MRB_OK) return rc;
+  b = a;
+  if (k + 1 < m && (rc = select_kth(logits_dev, labels_dev, n, k + 1, hist, st, &b, &m)) != MRB_OK) return rc;
+  *tau_out = a + frac * (b - a);
+  return MRB_OK;
 }
 
 extern "C" int mrb_mlp_train_step(float* params_dev, float* adam_m_dev, float* adam_v_dev, int32_t t_step,

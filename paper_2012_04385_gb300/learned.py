@@ -84,8 +84,7 @@ def train(data: SelectorData, epochs: int = 20, batch: int = 16384, lr: float = 
     # threshold on held-out faces: at most `miss` of the positives below tau
     z = mrb.mlp_logits(params, data.feats[hold].contiguous())
     y = data.labels[hold]
-    zpos = z[y == 1]
-    tau = float(torch.quantile(zpos.float(), miss).item()) if zpos.numel() > 0 else 0.0
+    tau = mrb.mlp_threshold(z, y.contiguous(), miss)
     lin = (z < tau)
     report = {"samples": int(n), "positives": float(data.labels.float().mean().item()), "losses": losses,
               "tau": tau, "holdout_linear_fraction": float(lin.float().mean().item()),

@@ -102,6 +102,7 @@ def lib():
                 "mrb_face_samples": (ci, [vp, ctypes.c_float, i64, vp, vp, vp, i64, vp]),
                 "mrb_learned_stats": (ci, [vp, vp, vp, i32]),
                 "mrb_mlp_logits": (ci, [vp, vp, i64, vp, vp]),
+                "mrb_mlp_threshold": (ci, [vp, vp, i64, ctypes.c_double, vp, vp, vp]),
                 "mrb_mlp_train_step": (ci, [vp, vp, vp, i32, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp, vp, vp,
                                             vp]),
                 "mrb_status": (ci, [vp]),
@@ -178,6 +179,21 @@ def mlp_logits(params, feats, stream=None):
     if rc != MRB_OK:
         raise MrbError(rc, "mrb_mlp_logits failed")
     return out[:n]
+
+
+def mlp_threshold(logits, labels, q, stream=None) -> float:
+    """The q-quantile of the label-1 logits (mrb_mlp_threshold): the selector's
+    threshold tau, below which a face goes to the linear scheme."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    n = logits.shape[0]
+    work = torch.empty(256, dtype=torch.int64, device=logits.device)
+    out = ctypes.c_float()
+    rc = lib().mrb_mlp_threshold(logits.data_ptr(), labels.data_ptr(), n, float(q), work.data_ptr(),
+                                 ctypes.byref(out), st.cuda_stream)
+    if rc != MRB_OK:
+        raise MrbError(rc, "mrb_mlp_threshold failed")
+    return float(out.value)
 
 
 class MlpTrainer:

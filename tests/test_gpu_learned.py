@@ -206,3 +206,29 @@ def test_learned_path_vs_fp64_oracle_on_an_mr_tree(small_selector):
     print(f"learned FP32 vs FP64 oracle after 5 steps: L1 density {l1:.2e}, faces sent to linear {lin / tot:.3f}")
     assert 0 < lin < tot
     assert l1 <= 1e-4
+
+
+def test_threshold_is_the_quantile_of_the_label_1_logits():
+    """mrb_mlp_threshold (radix selection on the device) against the linear-
+    interpolation quantile of the label-1 logits: random logits with ties and
+    both signs, a single label-1 sample, none, and the ends q = 0 and 1."""
+    g = torch.Generator(device="cpu").manual_seed(7)
+    cases = []
+    for n, q, share in ((200_000, 1e-4, 0.3), (5_000, 0.5, 0.5), (777, 1.0, 0.2), (3_000, 0.0, 0.4),
+                        (1_000, 0.37, 1.0)):
+        z = (torch.randn(n, generator=g) * 3).float()
+        z[: n // 10] = torch.round(z[: n // 10])             # ties
+        y = (torch.rand(n, generator=g) < share).to(torch.uint8)
+        cases.append((z, y, q))
+    z1 = torch.randn(50, generator=g).float()
+    y1 = torch.zeros(50, dtype=torch.uint8)
+    y1[17] = 1
+    cases.append((z1, y1, 0.25))
+    for z, y, q in cases:
+        want = float(torch.quantile(z[y == 1].double(), q).item())
+        got = mrb.mlp_threshold(z.cuda(), y.cuda(), q)
+        assert abs(got - want) <= 1e-6 * abs(want) + 1e-6, (q, got, want)
+    none = mrb.mlp_threshold(z1.cuda(), torch.zeros(50, dtype=torch.uint8).cuda(), 0.5)
+    assert none == 0.0
+    with pytest.raises(mrb.MrbError):
+        mrb.mlp_threshold(z1.cuda(), y1.cuda(), 1.5)
