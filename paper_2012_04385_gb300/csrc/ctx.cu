@@ -316,7 +316,9 @@ struct mrb_ctx {
             th.th[m] = ((double)(r - r0) + cst[row][s] * (double)(1 << (L - l))) / (double)span;
           }
           launch_lts_interp(topo(), P, cur, l, th, 0, st);
-          fill_halos(fmode);
+          // the stepping level's halos, and those of the coarser levels its
+          // predictions read; finer levels are filled when they step
+          for (int ll = 0; ll <= l; ++ll) launch_fill_level(topo(), phys, P, cur, ll, st, fmode);
           if (cfg.precision == MRB_FP32_ACC64) launch_rhs_rk_f32(topo(), phys, P, cur, s, d_dt, nullptr, st, l);
           else launch_rhs_rk_f64(topo(), phys, P, cur, s, d_dt, nullptr, st, l);
           launch_lts_copyback(topo(), P, cur, l, st);
