@@ -83,6 +83,64 @@ __device__ __forceinline__ float weno5f(float a, float b, float c, float d, floa
   return fmaf(fmaf(w0, e0, fmaf(w1, e1, w2 * e2)), frcp(6.f * (w0 + w1 + w2)), c);
 }
 
+// Packed FP32 pairs (fma / add / sub / mul .rn.ftz.f32x2: two lanes' IEEE
+// operations in one instruction, flushing subnormals like the scalar FP32
+// code built with -ftz).
+__device__ __forceinline__ float2 f2s(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{.reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.ftz.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) {
+  float2 r;
+  asm("{.reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n add.rn.ftz.f32x2 rd, ra, rb;\n"
+      " mov.b64 {%0, %1}, rd;}" : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+  float2 r;
+  asm("{.reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n sub.rn.ftz.f32x2 rd, ra, rb;\n"
+      " mov.b64 {%0, %1}, rd;}" : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
+  float2 r;
+  asm("{.reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mul.rn.ftz.f32x2 rd, ra, rb;\n"
+      " mov.b64 {%0, %1}, rd;}" : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
+// Two WENO5 reconstructions in packed pairs, lane by lane the operations of
+// weno5f: where weno5f negates an operand (3 dc - dd, -2 dc - db) the pair
+// forms the exact negation instead (dd - 3 dc only enters squared; -e1 meets
+// -w1 in the product and w0 - (-w1) = w0 + w1), so every lane's result is
+// weno5f's bit for bit.
+__device__ __forceinline__ float2 weno5f2(float2 a, float2 b, float2 c, float2 d, float2 e) {
+  const float2 da = f2sub(a, b), db = f2sub(b, c), dc = f2sub(c, d), dd = f2sub(d, e);
+  const float2 eps12 = f2s(12e-6f);
+  float2 t1 = f2sub(da, db), t2 = f2fma(f2s(-3.f), db, da);
+  float2 s0 = f2fma(f2mul(f2s(13.f), t1), t1, f2fma(f2mul(f2s(3.f), t2), t2, eps12));
+  t1 = f2sub(db, dc);
+  t2 = f2add(db, dc);
+  float2 s1 = f2fma(f2mul(f2s(13.f), t1), t1, f2fma(f2mul(f2s(3.f), t2), t2, eps12));
+  t1 = f2sub(dc, dd);
+  t2 = f2fma(f2s(-3.f), dc, dd);
+  float2 s2 = f2fma(f2mul(f2s(13.f), t1), t1, f2fma(f2mul(f2s(3.f), t2), t2, eps12));
+  s0 = f2mul(s0, s0);
+  s1 = f2mul(s1, s1);
+  s2 = f2mul(s2, s2);
+  const float2 w0 = f2mul(f2s(0.1f), f2mul(s1, s2)), nw1 = f2mul(f2s(-0.6f), f2mul(s0, s2));
+  const float2 w2 = f2mul(f2s(0.3f), f2mul(s0, s1));
+  const float2 e0 = f2fma(f2s(2.f), da, f2mul(f2s(-5.f), db)), ne1 = f2fma(f2s(2.f), dc, db);
+  const float2 e2 = f2fma(f2s(-4.f), dc, dd);
+  const float2 num = f2fma(w0, e0, f2fma(nw1, ne1, f2mul(w2, e2)));
+  const float2 den = f2mul(f2s(6.f), f2add(f2sub(w0, nw1), w2));
+  return f2fma(num, make_float2(frcp(den.x), frcp(den.y)), c);
+}
+
 // TENO5 (Fu, Hu & Adams 2016) on the differences, with the smoothness
 // indicators scaled by 12 as in weno5f: stencil k is kept when gamma_k >=
 // C_T sum gamma, gamma_k = (1 + tau5 / (beta_k + eps))^6, tau5 = |beta0 -
@@ -465,7 +523,19 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
         fp[m] = fmaf(0.5f, G[m], ha * V[m]);
         fm[m] = fmaf(0.5f, G[m], -ha * V[m]);
       }
-      gh = rec5<MODE>(use_lin, fp[0], fp[1], fp[2], fp[3], fp[4]) + rec5<MODE>(use_lin, fm[5], fm[4], fm[3], fm[2], fm[1]);
+      constexpr int REC = MODE & 7;
+      if constexpr (REC == 0 || REC == 1 || REC == 3) {
+        // the split's two WENO5 reconstructions as one packed evaluation
+        if (REC == 3 && use_lin) {
+          gh = linear5f(fp[0], fp[1], fp[2], fp[3], fp[4]) + linear5f(fm[5], fm[4], fm[3], fm[2], fm[1]);
+        } else {
+          const float2 r = weno5f2(make_float2(fp[0], fm[5]), make_float2(fp[1], fm[4]), make_float2(fp[2], fm[3]),
+                                   make_float2(fp[3], fm[2]), make_float2(fp[4], fm[1]));
+          gh = r.x + r.y;
+        }
+      } else {
+        gh = rec5<MODE>(use_lin, fp[0], fp[1], fp[2], fp[3], fp[4]) + rec5<MODE>(use_lin, fm[5], fm[4], fm[3], fm[2], fm[1]);
+      }
     }
     // F_hat = R g_hat, columns r0 = (1, u-c, ut1, ut2, H-uc), r1 = (1, u, ut1, ut2, q2/2),
     // r2 = (0, 0, 1, 0, ut1), r3 = (0, 0, 0, 1, ut2), r4 = (1, u+c, ut1, ut2, H+uc)
