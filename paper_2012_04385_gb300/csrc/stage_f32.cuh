@@ -356,6 +356,20 @@ __device__ __forceinline__ void char014(const float X[5], const RoeF& e, float& 
   x1 = fmaf(-2.f, A, X[0]);
 }
 
+// Characteristic fluxes of fields 0, 1, 4 of two cells in packed pairs,
+// lane by lane the scalar evaluation: X4 = un (E + p) enters X4 - Sm as one
+// fused multiply-add (-Sm formed exactly by negating its products), and
+// x0, x4 = A -/+ B as fused multiply-adds.
+__device__ __forceinline__ void char014f2(const float2 X[4], float2 un, float2 Ep, const RoeF& e, float2& x0,
+                                          float2& x1, float2& x4) {
+  const float2 nSm = f2fma(f2s(-e.un), X[1], f2fma(f2s(-e.ut1), X[2], f2mul(f2s(-e.ut2), X[3])));
+  const float2 A = f2fma(f2s(0.5f * e.b2), X[0], f2mul(f2s(e.hb1), f2fma(un, Ep, nSm)));
+  const float2 nt = f2fma(f2s(-e.un), X[0], X[1]);
+  x0 = f2fma(f2s(-0.5f * e.ic), nt, A);
+  x4 = f2fma(f2s(0.5f * e.ic), nt, A);
+  x1 = f2fma(f2s(-2.f), A, X[0]);
+}
+
 // X += x times right eigenvector k of the face (columns r0 = (1, u-c, ut1,
 // ut2, H-uc), r1 = (1, u, ut1, ut2, q2/2), r2 = (0, 0, 1, 0, ut1), r3 = (0, 0,
 // 0, 1, ut2), r4 = (1, u+c, ut1, ut2, H+uc)).
@@ -472,10 +486,28 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
   // characteristic fluxes of all fields (l2 F = F2 - ut1 F0, l3 F = F3 - ut2 F0)
   float Gall[5][6];
 #pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    char014(Fr[m], e, Gall[0][m], Gall[1][m], Gall[4][m]);
-    Gall[2][m] = fmaf(-e.ut1, Fr[m][0], Fr[m][2]);
-    Gall[3][m] = fmaf(-e.ut2, Fr[m][0], Fr[m][3]);
+  for (int m = 0; m < 6; m += 2) {
+    // two cells in packed pairs (flux components 0-3, and u_n, E + p for the
+    // energy flux)
+    float2 X[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) X[v] = make_float2(Fr[m][v], Fr[m + 1][v]);
+    const int ca = c0 + m * st, cb = c0 + (m + 1) * st;
+    const float2 un = make_float2(S[R.n + ca], S[R.n + cb]);
+    const float2 Ep = make_float2(S[5 * SF_REG + ca] + S[4 * SF_REG + ca], S[5 * SF_REG + cb] + S[4 * SF_REG + cb]);
+    float2 g0, g1, g4;
+    char014f2(X, un, Ep, e, g0, g1, g4);
+    const float2 g2 = f2fma(f2s(-e.ut1), X[0], X[2]), g3 = f2fma(f2s(-e.ut2), X[0], X[3]);
+    Gall[0][m] = g0.x;
+    Gall[0][m + 1] = g0.y;
+    Gall[1][m] = g1.x;
+    Gall[1][m + 1] = g1.y;
+    Gall[2][m] = g2.x;
+    Gall[2][m + 1] = g2.y;
+    Gall[3][m] = g3.x;
+    Gall[3][m + 1] = g3.y;
+    Gall[4][m] = g4.x;
+    Gall[4][m + 1] = g4.y;
   }
   float Fh0 = 0.f, Fh1 = 0.f, Fh2 = 0.f, Fh3 = 0.f, Fh4 = 0.f;
 #pragma unroll
