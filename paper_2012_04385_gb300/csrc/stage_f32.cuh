@@ -306,6 +306,28 @@ __device__ __forceinline__ void cell_uf(const float* __restrict__ S, int c, Rot 
   F[4] = un * (E + p);
 }
 
+// Conserved states and physical fluxes of two records (ca, cb) in packed
+// pairs, lane by lane cell_uf's operations.
+__device__ __forceinline__ void cell_uf2(const float* __restrict__ S, int ca, int cb, Rot R, float Ua[5], float Ub[5],
+                                         float Fa[5], float Fb[5]) {
+  const float2 r = make_float2(S[ca], S[cb]), un = make_float2(S[R.n + ca], S[R.n + cb]);
+  const float2 u1 = make_float2(S[R.t1 + ca], S[R.t1 + cb]), u2 = make_float2(S[R.t2 + ca], S[R.t2 + cb]);
+  const float2 p = make_float2(S[4 * SF_REG + ca], S[4 * SF_REG + cb]);
+  const float2 E = make_float2(S[5 * SF_REG + ca], S[5 * SF_REG + cb]);
+  const float2 mn = f2mul(r, un), U2 = f2mul(r, u1), U3 = f2mul(r, u2);
+  const float2 F1 = f2fma(mn, un, p), F2 = f2mul(mn, u1), F3 = f2mul(mn, u2), F4 = f2mul(un, f2add(E, p));
+  Ua[0] = r.x; Ub[0] = r.y;
+  Ua[1] = mn.x; Ub[1] = mn.y;
+  Ua[2] = U2.x; Ub[2] = U2.y;
+  Ua[3] = U3.x; Ub[3] = U3.y;
+  Ua[4] = E.x; Ub[4] = E.y;
+  Fa[0] = mn.x; Fb[0] = mn.y;
+  Fa[1] = F1.x; Fb[1] = F1.y;
+  Fa[2] = F2.x; Fb[2] = F2.y;
+  Fa[3] = F3.x; Fb[3] = F3.y;
+  Fa[4] = F4.x; Fb[4] = F4.y;
+}
+
 // Kernel variants: MODE 0 WENO5, 2 linear, 4 TENO5, 1 learned selector at stage 0
 // (WENO5 fluxes; the selector is evaluated on the same faces and its
 // decisions stored), 3 learned selector at stages 1 and 2 (the stored
@@ -456,7 +478,7 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
   constexpr int FLUX = (MODE >> 3) & 3;
   float Ur[6][5], Fr[6][5];
 #pragma unroll
-  for (int m = 0; m < 6; ++m) cell_uf(S, c0 + m * st, R, Ur[m], Fr[m]);
+  for (int m = 0; m < 6; m += 2) cell_uf2(S, c0 + m * st, c0 + (m + 1) * st, R, Ur[m], Ur[m + 1], Fr[m], Fr[m + 1]);
   const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1, g, B, R);
   if constexpr (FLUX == 2) {
     // HLLC: characteristic variables reconstructed from both sides, back to states
