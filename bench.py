@@ -261,10 +261,10 @@ def roofline_numbers(linear_fraction=0.0, split=None, table=None):
 # on the shock-bubble workload (levels 0..4, 5,720 leaves), from the
 # full-size ncu capture summarised in
 # profiles/stage_kernels_shock_bubble_512.md: the mean over one step, for the
-# learned path k_stage_f32<1> (247.2) and k_stage_f32<3> twice (219.9), for
-# the WENO5 path k_stage_f32<0> (248.5 at stage 0, 222.8 at stages 1 and 2).
+# learned path k_stage_f32<1> (250.8) and k_stage_f32<3> twice (222.6), for
+# the WENO5 path k_stage_f32<0> (247.2 at stage 0, 222.2 at stages 1 and 2).
 # Traffic grows in proportion to the leaf cells of a launch.
-TRAFFIC_BYTES_PER_CELL = {"learned": 229.0, "weno": 231.3}
+TRAFFIC_BYTES_PER_CELL = {"learned": 232.0, "weno": 230.5}
 
 
 def measured_peaks():
