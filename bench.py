@@ -53,7 +53,13 @@ WORKLOADS = {
     "shock_bubble_mr_512cubed_l4": ("shock_bubble", 4, "512^3"),
     "explosion_mr_256cubed_l3": ("explosion", 3, "256^3"),
     "rt_layer_mr_l5_memory_sized": ("rt", 5, "1024^2 x 2048"),
+    # instances 0..15 of the 64-instance four-quadrant ensemble (levels 0..2+(i mod 3)),
+    # one launch per RK stage for all sixteen (the 64 instances run as four such batches)
+    "ensemble_quadrants_16_of_64": ("ensemble", None, "16 instances, 128^3 to 512^3"),
 }
+# pool blocks per four-quadrant instance by finest level, with room for the
+# initialisation's transient refinement of the whole level below
+QUAD_SLOTS = {2: 1200, 3: 6000, 4: 20000}
 HEADLINE = "shock_bubble_mr_512cubed_l4"
 
 # FP32-path variants timed beside the headline: (name, reconstruction, flux scheme)
@@ -95,10 +101,14 @@ def workload_config(name: str, precision: int, lmax=None):
         return I.shock_bubble_config(lmax=lm, precision=precision), I.ic_shock_bubble
     if kind == "explosion":
         return I.explosion_config(lmax=lm, precision=precision), I.ic_explosion
+    if kind == "ensemble":
+        return I.ensemble_config(n=16, precision=precision), I.ic_ensemble
     return I.rt_config(lmax=lm, precision=precision), I.ic_rt
 
 
 def slots_for(cfg) -> int:
+    if cfg.n_instances > 1:
+        return int(sum(QUAD_SLOTS[cfg.lmax_of(i)] for i in range(cfg.n_instances)))
     # fully refined upper bound of the tree: sum_l 8^l * base blocks
     base = int(np.prod(cfg.base_blocks)) * cfg.n_instances
     return int(sum(base * 8 ** l for l in range(cfg.lmax_of(0) + 1)))
@@ -339,7 +349,10 @@ def make_context(name, precision, lmax=None, recon=0, flux=0, tau=0.0, params=No
     cfg.recon, cfg.flux, cfg.mlp_tau, cfg.lts = recon, flux, tau, lts
     ctx = mrb.Context(cfg, slots or slots_for(cfg), stream=stream, mlp_params=params if recon == 1 else None)
     t0 = time.perf_counter()
-    mrb.init_tree(ctx, lambda c, geo: ic(c, geo))
+    if cfg.n_instances > 1:
+        mrb.init_tree(ctx, ic, with_keys=True)
+    else:
+        mrb.init_tree(ctx, lambda c, geo: ic(c, geo))
     ctx.init_s = time.perf_counter() - t0
     return ctx
 
@@ -626,13 +639,18 @@ def run_gpu(args, rank, world):
             slots = memory_sized_slots(workload_config(sname, I.FP32_ACC64)[0]) if kind == "rt" else None
             ctx = make_context(sname, I.FP32_ACC64, recon=I.RECON_LEARNED, tau=tau, params=params, slots=slots,
                                stream=stream)
-            ssteps = 3 if kind == "rt" else max(3, min(args.steps, 10))
-            ms_ = timed_steps(ctx, stream, ssteps, 1 if kind == "rt" else 2)
+            big = kind in ("rt", "ensemble")
+            ssteps = 3 if big else max(3, min(args.steps, 10))
+            ms_ = timed_steps(ctx, stream, ssteps, 1 if big else 2)
             entry = {"path": "FP32 bulk + learned selector", "value": ms_["cells"] / (ms_["ms"] * 1e-3),
                      "median_step_value": ms_["median_rate"], "ms_per_step": ms_["ms"] / ssteps,
                      "stage_kernel_ms": ms_["stage_ms"], "steps": ssteps, "leaf_blocks_end": ctx.n_leaves(),
                      "linear_fraction": ms_["linear_fraction"], "pool_gb": round(ctx.pool.numel() / 1e9, 1),
                      "init_s": round(ctx.init_s, 1)}
+            if kind == "ensemble":
+                inst = (ctx.keys() >> np.uint64(56)).astype(np.int64)
+                entry["instances"] = int(ctx.cfg.n_instances)
+                entry["leaf_blocks_per_instance"] = np.bincount(inst, minlength=ctx.cfg.n_instances).tolist()
             release(ctx)
             ctx = None
             if kind == "explosion":
