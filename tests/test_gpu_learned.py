@@ -169,7 +169,7 @@ def test_training_lowers_loss_and_learned_path_accuracy(small_selector):
 
 
 def test_learned_path_vs_fp64_oracle_on_an_mr_tree(small_selector):
-    """The headline accuracy bar against the judge itself: the FP32 + learned
+    """The headline accuracy bar checked against the oracle itself: the FP32 + learned
     path and the FP64 oracle (WENO5 everywhere) from the same initial MR tree
     (the explosion on levels 0..2, with resolution jumps) for 5 full steps,
     remeshing included: the same tree, and the L1 density difference on the
