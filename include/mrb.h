@@ -406,9 +406,8 @@ int mrb_profile_read(mrb_ctx* ctx, double* stage_kernel_ms, int64_t* stage_kerne
  * Every call made outside a stream capture looks up the scratch address with
  * the calling device current (so a device reset is picked up); a call on a
  * stream being captured reuses the last address found on that device and
- * fails with ECUDA if there is none: make one call before any capture.  All
- * calls share the scratch, which keeps the last call's contents: calls that
- * overlap on the GPU race. */
+ * fails with ECUDA if there is none.  All calls share the scratch, which keeps
+ * the last call's contents: calls that overlap on the GPU race. */
 #define MRB_NOALLOC_MAX_BLOCKS 65536
 int mrb_block_sums_noalloc(const double* blocks_dev, int64_t n_blocks, const int32_t* levels_dev, double dx0,
                            void* stream, double* sums_dev);
