@@ -49,26 +49,29 @@ __device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// GELU (tanh form) of two pre-activations in packed BF16 arithmetic; the
-// result is the packed BF16 A operand of the next layer.
+// Twice the GELU (tanh form) of two pre-activations, z (1 + tanh(k0 (z +
+// k1 z^3))), in packed BF16 arithmetic; the result is the packed BF16 A
+// operand of the next layer, whose weights carry the GELU's factor 1/2
+// (mlp_bval).  Scaling by a power of two is exact in BF16, so the layer's
+// products and sums are bitwise those of 1/2 z (1 + tanh(...)) with the
+// unscaled weights, one multiplication fewer per pair.
 __device__ __forceinline__ uint32_t gelu2_bf16(float z0, float z1) {
   const __nv_bfloat162 z = __floats2bfloat162_rn(z0, z1);
   const __nv_bfloat162 k0 = __float2bfloat162_rn(GELU_K0), k01 = __float2bfloat162_rn(GELU_K0 * GELU_K1);
-  const __nv_bfloat162 half = __float2bfloat162_rn(0.5f);
   const __nv_bfloat162 z2 = __hmul2(z, z);
   const __nv_bfloat162 arg = __hmul2(__hfma2(z2, k01, k0), z);   // k0 (z + k1 z^3)
   uint32_t th;
   asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(*reinterpret_cast<const uint32_t*>(&arg)));
-  const __nv_bfloat162 hz = __hmul2(z, half);
-  const __nv_bfloat162 out = __hfma2(*reinterpret_cast<const __nv_bfloat162*>(&th), hz, hz);
+  const __nv_bfloat162 out = __hfma2(*reinterpret_cast<const __nv_bfloat162*>(&th), z, z);
   return *reinterpret_cast<const uint32_t*>(&out);
 }
 
-// Weight element B(k, n) of layer L as the B operand (k = input, n = output).
+// Weight element B(k, n) of layer L as the B operand (k = input, n = output);
+// layers 2 and 3 read doubled activations (gelu2_bf16) and take half weights.
 __device__ __forceinline__ float mlp_bval(const float* __restrict__ P, int L, int k, int n) {
   if (L == 1) return (k < MLP_IN) ? P[OFF_W1 + n * MLP_IN + k] : 0.f;
-  if (L == 2) return P[OFF_W2 + n * MLP_H + k];
-  return (n == 0) ? P[OFF_W3 + k] : 0.f;
+  if (L == 2) return 0.5f * P[OFF_W2 + n * MLP_H + k];
+  return (n == 0) ? 0.5f * P[OFF_W3 + k] : 0.f;
 }
 
 // Build the per-lane B fragments of all three layers (BF16) into `frag`

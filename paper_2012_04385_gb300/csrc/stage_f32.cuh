@@ -470,11 +470,10 @@ __device__ __forceinline__ void hllc_f32(const float UL[5], const float UR[5], f
 }
 
 // Face flux between stencil cells 2 and 3 (cells at S index c0 + m*st, m = 0..5)
-// from the FP32 records; result in the direction frame.  With FEAT the
-// selector features of the face are returned as well.
-template <int MODE, bool FEAT>
+// from the FP32 records; result in the direction frame.
+template <int MODE>
 __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, Rot R, float gm1, float g,
-                                              float B, bool lin, float F[5], float* feat = nullptr) {
+                                              float B, bool lin, float F[5]) {
   constexpr int FLUX = (MODE >> 3) & 3;
   float Ur[6][5], Fr[6][5];
 #pragma unroll
@@ -614,17 +613,6 @@ __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c
       Fh4 = fmaf(e.ut2, gh, Fh4);
     }
   }
-  if (FEAT) {
-    float g[3][6], v[3][6];
-#pragma unroll
-    for (int m = 0; m < 6; ++m) {
-      g[0][m] = Gall[0][m];
-      g[1][m] = Gall[1][m];
-      g[2][m] = Gall[4][m];
-      char014(Ur[m], e, v[0][m], v[1][m], v[2][m]);
-    }
-    features_gv(g, v, e, feat);
-  }
   F[0] = Fh0;
   F[1] = Fh1;
   F[2] = Fh2;
@@ -681,17 +669,34 @@ __device__ __forceinline__ void sub_viscous_f32(const double* __restrict__ u, in
   F[4] -= E;
 }
 
-// Selector features of the face between records c0+2st and c0+3st (the
-// same arithmetic as the stage-0 kernel's).
+// Selector features of the face between records c0+2st and c0+3st, for the
+// stage-0 selector kernel and the training samples alike.  The characteristic
+// fluxes of fields 0, 1, 4 are the face flux's own (two cells per packed
+// instruction, bitwise the same values), so the features are those of the
+// fluxes the kernel computes.
 __device__ __forceinline__ void face_features_f32(const float* __restrict__ S, int c0, int st, Rot R, const RoeF& e,
                                                   float f[15]) {
   float g[3][6], v[3][6];
 #pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    float U[5], F[5];
-    cell_uf(S, c0 + m * st, R, U, F);
-    char014(F, e, g[0][m], g[1][m], g[2][m]);
-    char014(U, e, v[0][m], v[1][m], v[2][m]);
+  for (int m = 0; m < 6; m += 2) {
+    float Ua[5], Ub[5], Fa[5], Fb[5];
+    cell_uf2(S, c0 + m * st, c0 + (m + 1) * st, R, Ua, Ub, Fa, Fb);
+    float2 X[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) X[q] = make_float2(Fa[q], Fb[q]);
+    const int ca = c0 + m * st, cb = c0 + (m + 1) * st;
+    const float2 un = make_float2(S[R.n + ca], S[R.n + cb]);
+    const float2 Ep = make_float2(S[5 * SF_REG + ca] + S[4 * SF_REG + ca], S[5 * SF_REG + cb] + S[4 * SF_REG + cb]);
+    float2 g0, g1, g4;
+    char014f2(X, un, Ep, e, g0, g1, g4);
+    g[0][m] = g0.x;
+    g[0][m + 1] = g0.y;
+    g[1][m] = g1.x;
+    g[1][m + 1] = g1.y;
+    g[2][m] = g4.x;
+    g[2][m + 1] = g4.y;
+    char014(Ua, e, v[0][m], v[1][m], v[2][m]);
+    char014(Ub, e, v[0][m + 1], v[1][m + 1], v[2][m + 1]);
   }
   features_gv(g, v, e, f);
 }
@@ -971,7 +976,7 @@ template <int MODE>
 __device__ __forceinline__ void sweep_f32(int D, const Topo& t, const Pool& pool, int cur, int node, int slot,
                                           double* __restrict__ fb, float* __restrict__ S, float* __restrict__ Fs,
                                           int z0, float g, float B, float gm1, float (&acc)[SF_TZ][NV],
-                                          const LearnedCtx& L) {
+                                          const LearnedCtx& L, unsigned (&cnt)[2]) {   // cnt: the warp's census
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   // the x-y region serves the x and the y faces (loaded for D = 0 and kept
   // for D = 1), the z region the z faces
@@ -993,17 +998,22 @@ __device__ __forceinline__ void sweep_f32(int D, const Topo& t, const Pool& pool
     else if (D == 1) c0 = xy_slot(f % 16, fa - 3, f / 16 / 17);
     // decision word of this warp's 32 consecutive faces
     uint32_t* word = L.bits + (z0 / SF_TZ) * 108 + D * 34 + (f0 >> 5);
-    // WENO5 fluxes and the selector's features of the same faces; flat
-    // stencils have all-zero features, whose logit z0 is known, so the warp
-    // runs the tensor-core MLP only when one of its faces is not flat
+    // WENO5 fluxes, then the selector's features of the same faces.  Flat
+    // stencils have all-zero features, whose logit z0 is known: a warp
+    // computes features and runs the tensor-core MLP only when one of its
+    // faces is not flat (on the shock-bubble tree about 70% of the warps are
+    // all flat), and its flat lanes skip the features
     float F[5], fe[15];
     const bool flat = !act || stencil_flat(S, c0, st);
-    if (act) face_flux_f32<MODE, true>(S, c0, st, R, gm1, g, B, false, F, fe);
+    if (act) face_flux_f32<MODE>(S, c0, st, R, gm1, g, B, false, F);
     float z = L.z0;
     if (!__all_sync(0xffffffffu, flat)) {
       if (flat) {
 #pragma unroll
         for (int q = 0; q < 15; ++q) fe[q] = 0.f;
+      } else {
+        const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1, g, B, R);
+        face_features_f32(S, c0, st, R, e, fe);
       }
       const int wid = threadIdx.x >> 5;
       mlp_put_row(L.rows + wid * 32 * 9, fe);
@@ -1013,10 +1023,8 @@ __device__ __forceinline__ void sweep_f32(int D, const Topo& t, const Pool& pool
     const unsigned bl = __ballot_sync(0xffffffffu, dl), ba = __ballot_sync(0xffffffffu, act);
     if ((threadIdx.x & 31) == 0) {
       *word = bl;
-      if (L.count) {
-        atomicAdd(&L.count[0], (unsigned long long)__popc(bl));
-        atomicAdd(&L.count[1], (unsigned long long)__popc(ba));
-      }
+      cnt[0] += __popc(bl);
+      cnt[1] += __popc(ba);
     }
     if (!act) continue;
     store_face(D, F, Fs, SF_NFZ, f, (D == 2) ? z0 + fa : fa, ta, tb, fb);
@@ -1069,7 +1077,7 @@ __device__ __forceinline__ void sweep_xy(const double* __restrict__ u, const Top
       wi = 34 + (fy >> 5);
     }
     const bool lin = (MODE == 3) && ((L.selw[wi] >> (threadIdx.x & 31)) & 1u);
-    face_flux_f32<MODE, false>(S, c0, st, isx ? rot_of(0) : rot_of(1), gm1, g, B, lin, F);
+    face_flux_f32<MODE>(S, c0, st, isx ? rot_of(0) : rot_of(1), gm1, g, B, lin, F);
     if (MODE & 32) {
       if (isx) sub_viscous_f32<0>(u, sidx(fa - 1, ta, tb), L.mu, L.idx, F);
       else sub_viscous_f32<1>(u, sidx(ta, fa - 1, tb), L.mu, L.idx, F);
@@ -1102,7 +1110,7 @@ __device__ __forceinline__ void sweep_z(const double* __restrict__ u, const Topo
     const int c0 = (fa * 16 + j) * 16 + i;
     const bool lin = (MODE == 3) && ((L.selw[68 + (f >> 5)] >> (threadIdx.x & 31)) & 1u);
     float F[5];
-    face_flux_f32<MODE, false>(S, c0, 256, rot_of(2), gm1, g, B, lin, F);
+    face_flux_f32<MODE>(S, c0, 256, rot_of(2), gm1, g, B, lin, F);
     if (MODE & 32) sub_viscous_f32<2>(u, sidx(i, j, z0 + fa - 1), L.mu, L.idx, F);
     store_face(2, F, Fs, SF_FMAX, f, z0 + fa, i, j, fb);
   }
@@ -1151,6 +1159,11 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
     __syncthreads();
   }
   const ItemRange IR = item_range(nitems, p.blocked);
+  // selector census (faces sent to linear, faces evaluated), counted by each
+  // warp's lane 0 and added to the two global counters once at the end: one
+  // atomic pair per 32 faces, all on the same two addresses, serialised in L2
+  // and held the kernel up once the all-flat warps had become cheap
+  unsigned cnt[2] = {0u, 0u};
   for (int w = IR.first; w < IR.end; w += IR.step) {
     const int li = w / SF_NSLAB, z0 = (w % SF_NSLAB) * SF_TZ;
     const int node = stage_node(t, level, li);
@@ -1179,7 +1192,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[kz][v] = 0.f;
 #pragma unroll 1
-      for (int D = 0; D < 3; ++D) sweep_f32<MODE>(D, t, pool, cur, node, slot, fb, S, Fs, z0, g, B, gm1, acc, L);
+      for (int D = 0; D < 3; ++D) sweep_f32<MODE>(D, t, pool, cur, node, slot, fb, S, Fs, z0, g, B, gm1, acc, L, cnt);
     } else {
       sweep_xy<MODE>(u, t, pool, cur, node, slot, fb, S, Fs, z0, g, B, gm1, acc, L);
       sweep_z<MODE>(u, t, pool, cur, node, slot, fb, S, Fs, z0, g, B, gm1, acc, L);
@@ -1272,6 +1285,10 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
         }
       }
     }
+  }
+  if (MODE == 1 && L.count && (threadIdx.x & 31) == 0) {
+    atomicAdd(&L.count[0], (unsigned long long)cnt[0]);
+    atomicAdd(&L.count[1], (unsigned long long)cnt[1]);
   }
 }
 
