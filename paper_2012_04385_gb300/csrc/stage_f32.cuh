@@ -469,15 +469,32 @@ __device__ __forceinline__ void hllc_f32(const float UL[5], const float UR[5], f
   }
 }
 
+// True when the record at c equals the record at c0 in all six fields, read
+// through cell_uf2's own expressions so that the loads are shared with it.
+__device__ __forceinline__ bool same_record(const float* __restrict__ S, int c, int c0, Rot R) {
+  return (S[c] == S[c0]) & (S[R.n + c] == S[R.n + c0]) & (S[R.t1 + c] == S[R.t1 + c0]) &
+         (S[R.t2 + c] == S[R.t2 + c0]) & (S[4 * SF_REG + c] == S[4 * SF_REG + c0]) &
+         (S[5 * SF_REG + c] == S[5 * SF_REG + c0]);
+}
+
 // Face flux between stencil cells 2 and 3 (cells at S index c0 + m*st, m = 0..5)
-// from the FP32 records; result in the direction frame.
-template <int MODE>
+// from the FP32 records; result in the direction frame.  With FLAT, *flat
+// tells whether the six records are identical, in which case every selector
+// feature of the face is exactly zero (tested on the flux's own loads: a
+// separate test that read the 36 values again cost the selector stage 12%).
+template <int MODE, bool FLAT = false>
 __device__ __forceinline__ void face_flux_f32(const float* __restrict__ S, int c0, int st, Rot R, float gm1, float g,
-                                              float B, bool lin, float F[5]) {
+                                              float B, bool lin, float F[5], bool* flat = nullptr) {
   constexpr int FLUX = (MODE >> 3) & 3;
   float Ur[6][5], Fr[6][5];
 #pragma unroll
   for (int m = 0; m < 6; m += 2) cell_uf2(S, c0 + m * st, c0 + (m + 1) * st, R, Ur[m], Ur[m + 1], Fr[m], Fr[m + 1]);
+  if constexpr (FLAT) {
+    bool fl = true;
+#pragma unroll
+    for (int m = 1; m < 6; ++m) fl = fl & same_record(S, c0 + m * st, c0, R);
+    *flat = fl;
+  }
   const RoeF e = roe_f32(S, c0 + 2 * st, c0 + 3 * st, gm1, g, B, R);
   if constexpr (FLUX == 2) {
     // HLLC: characteristic variables reconstructed from both sides, back to states
@@ -914,19 +931,6 @@ struct LearnedCtx {
   float mu, idx;             // viscous variants: dynamic viscosity and 1 / dx of the block
 };
 
-// True when the six stencil records are identical, in which case every
-// selector feature is exactly zero.
-__device__ __forceinline__ bool stencil_flat(const float* __restrict__ S, int c0, int st) {
-  bool flat = true;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const float a = S[q * SF_REG + c0];
-#pragma unroll
-    for (int m = 1; m < 6; ++m) flat = flat && (S[q * SF_REG + c0 + m * st] == a);
-  }
-  return flat;
-}
-
 // Direction-frame flux components (normal, tangential 1, tangential 2) of
 // direction D -> lab components x, y, z.
 __device__ __forceinline__ void to_lab(int D, float n, float t1, float t2, float& x, float& y, float& z) {
@@ -1004,8 +1008,8 @@ __device__ __forceinline__ void sweep_f32(int D, const Topo& t, const Pool& pool
     // faces is not flat (on the shock-bubble tree about 70% of the warps are
     // all flat), and its flat lanes skip the features
     float F[5], fe[15];
-    const bool flat = !act || stencil_flat(S, c0, st);
-    if (act) face_flux_f32<MODE>(S, c0, st, R, gm1, g, B, false, F);
+    bool flat = true;
+    if (act) face_flux_f32<MODE, true>(S, c0, st, R, gm1, g, B, false, F, &flat);
     float z = L.z0;
     if (!__all_sync(0xffffffffu, flat)) {
       if (flat) {
