@@ -1025,7 +1025,9 @@ __device__ __forceinline__ void sweep_f32(int D, const Topo& t, const Pool& pool
     }
     const bool dl = act && (z < L.tau);
     const unsigned bl = __ballot_sync(0xffffffffu, dl), ba = __ballot_sync(0xffffffffu, act);
-    if ((threadIdx.x & 31) == 0) {
+    // (a warp past the direction's last face writes nothing: its word index
+    // would fall among the next direction's words)
+    if ((threadIdx.x & 31) == 0 && ba) {
       *word = bl;
       cnt[0] += __popc(bl);
       cnt[1] += __popc(ba);
