@@ -136,6 +136,12 @@ def test_tensor_core_logits_vs_oracle_forward():
     assert (err <= 2e-2 + 2e-2 * np.abs(zr)).all()
 
 
+# Faces the selector stage evaluates per leaf and step: 17 x 16 x 16 x faces and
+# as many y faces, and for each of the four 4-cell z slabs its 5 planes of 256
+# z faces (the planes between slabs are evaluated by both).
+SELECTOR_FACES_PER_LEAF_STEP = 2 * 17 * 16 * 16 + 4 * 5 * 256
+
+
 @pytest.fixture(scope="module")
 def small_selector():
     data = learned.generate(sod_steps=8, explosion_steps=6, every=3, stride=5, explosion_lmax=2)
@@ -161,7 +167,8 @@ def test_training_lowers_loss_and_learned_path_accuracy(small_selector):
         if recon == I.RECON_LEARNED:
             lin, tot = g.learned_stats()
             print("faces sent to linear:", lin, "of", tot)
-            assert tot > 0 and 0 < lin < tot
+            assert tot == 20 * len(k) * SELECTOR_FACES_PER_LEAF_STEP   # the census is exact
+            assert 0 < lin < tot
     a, b = res[I.RECON_LEARNED][:, 0], res[I.RECON_WENO][:, 0]
     l1 = np.abs(a - b).sum() / np.abs(b).sum()
     print("learned vs WENO L1 density difference:", l1)
