@@ -274,7 +274,7 @@ def roofline_numbers(linear_fraction=0.0, split=None, table=None):
 # learned path k_stage_f32<1> (250.8) and k_stage_f32<3> twice (222.6), for
 # the WENO5 path k_stage_f32<0> (247.2 at stage 0, 222.2 at stages 1 and 2).
 # Traffic grows in proportion to the leaf cells of a launch.
-TRAFFIC_BYTES_PER_CELL = {"learned": 232.1, "weno": 230.6}
+TRAFFIC_BYTES_PER_CELL = {"learned": 232.2, "weno": 230.6}
 
 
 def measured_peaks():
